@@ -1,0 +1,231 @@
+/*
+ * stereo.h -- C ABI of the B300 dense stereo-matching library (libstereo.so).
+ *
+ * The library implements the per-pixel stereo-matching path of Zhou &
+ * Jagadeesan, "Real-time Dense Reconstruction of Tissue Surface from Stereo
+ * Optical Video" (arXiv 2007.12623), Section II, as hand-written CUDA for
+ * sm_103a:
+ *
+ *   gray conversion -> ZNCC cost over the disparity range (Sec. II-A)
+ *   -> winner-take-all + parabola sub-pixel -> left-right check
+ *   -> 3 x (radial outlier removal -> radial hole fill -> disc hole fill)
+ *      (Sec. II-B)
+ *   -> improved Laplacian refinement with the ZNCC o-update (Sec. II-C,
+ *      Eqs. 1-4)
+ *
+ * plus a differentiable soft-argmin variant (forward and backward).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All image, map and cost pointers are DEVICE pointers owned by the
+ *    caller, unless a comment says "host".  The library never frees them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call only enqueues work on that stream and returns; no
+ *    call synchronises the device, so outputs are ready once the caller
+ *    synchronises the stream.
+ *  - Images are 8-bit, row-major, `pitch` bytes between rows (pitch >=
+ *    width * channels).  channels = 1 (gray) or 3 (interleaved RGB, reduced
+ *    to gray with (77 R + 150 G + 29 B + 128) >> 8).
+ *  - Disparity d maps left pixel x to right pixel x - d.  Candidates are
+ *    d_min .. d_min + num_disp - 1 (1 <= num_disp <= 256); a candidate is
+ *    valid only when its whole (2r+1)^2 window lies inside both images.
+ *  - Invalid / unknown disparities are STEREO_INVALID in int16 maps and NaN
+ *    in float maps.
+ *  - Errors are returned as stereo_status; arguments are checked on the host
+ *    before anything is enqueued, so a call that fails with
+ *    STEREO_ERR_INVALID_ARG or STEREO_ERR_UNSUPPORTED has enqueued nothing.
+ *    No C++ exception crosses this boundary.  Device-side problems (a bounded
+ *    wait that gave up, a failed in-kernel bounds check in debug builds) set
+ *    an error word in the handle, read with stereo_get_device_error().
+ *  - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef STEREO_H
+#define STEREO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STEREO_INVALID (-32768)
+#define STEREO_MAX_DISP 256
+#define STEREO_MAX_WIN_RADIUS 7
+
+typedef enum {
+    STEREO_OK = 0,
+    STEREO_ERR_INVALID_ARG = 1,   /* NULL/misaligned pointer, bad size ...  */
+    STEREO_ERR_CUDA = 2,          /* a CUDA runtime call failed             */
+    STEREO_ERR_OOM = 3,           /* workspace allocation failed            */
+    STEREO_ERR_UNSUPPORTED = 4,   /* valid request this build cannot serve  */
+    STEREO_ERR_TIMEOUT = 5,       /* a bounded device wait gave up          */
+    STEREO_ERR_TOO_LARGE = 6      /* request exceeds the handle's capacity  */
+} stereo_status;
+
+typedef enum { STEREO_SAMPLE_FULL = 0, STEREO_SAMPLE_CHESSBOARD = 1 } stereo_sampling;
+
+typedef enum {
+    STEREO_COST_NONE = 0,   /* cost volume not kept (recomputed when needed) */
+    STEREO_COST_F32 = 1,
+    STEREO_COST_F16 = 2,
+    STEREO_COST_BF16 = 3
+} stereo_cost_dtype;
+
+/* Method parameters.  Defaults (stereo_default_params) are the paper's
+ * values: 11x11 window (Sec. II-A), outlier threshold 2.5 and 3 rounds with
+ * radius 10, 20, 30 (Sec. II-B), hole-filling radii 50 and 20 (Sec. II-B),
+ * smoothing radius 15, alpha 0.1, search +-5, eta 0.01 (Sec. II-C). */
+typedef struct {
+    int32_t max_width, max_height;  /* workspace sizing                        */
+    int32_t d_min, num_disp;        /* candidate range                         */
+    int32_t win_radius;             /* r: (2r+1)^2 window, 1..7                */
+    int32_t sampling;               /* stereo_sampling                         */
+    int32_t cost_dtype;             /* stereo_cost_dtype kept for refinement   */
+    int32_t lr_thresh;              /* keep iff |dL - dR(x - dL)| <= thresh    */
+    int32_t outlier_rounds, r0, dr; /* round t uses radius r0 + t*dr           */
+    float outlier_thresh;           /* neighbouring disparities differ < this  */
+    int32_t fill_radial_r;          /* radial search length                    */
+    int32_t fill_radial_min_dirs;   /* directions needed to fill               */
+    int32_t fill_disc_r;            /* disc radius                             */
+    int32_t fill_disc_min_count;    /* valid pixels needed; -1 = 1/4 of disc   */
+    int32_t smooth_radius;          /* box radius of Eqs. (1) and (3)          */
+    int32_t smooth_iters;           /* K                                       */
+    float alpha;                    /* Eq. (2)                                 */
+    float eta;                      /* Eq. (4)                                 */
+    int32_t refine_search;          /* o* in [d - S, d + S]                    */
+} stereo_params;
+
+typedef struct stereo_handle stereo_handle;
+
+/* One rectified stereo pair and its outputs.  Output pointers may be NULL
+ * (not written).  disp_wta: winner-take-all disparity (int16); disp_sub:
+ * disp_wta + parabola offset (float); disp_lr: after the left-right check
+ * (int16); disp_post: after outlier removal / hole filling (int16); valid:
+ * 1 where disp_post is valid (uint8); disp_final: refined disparity d^(K)
+ * (float).  All maps are dense width*height, row stride = width. */
+typedef struct {
+    const uint8_t* left;
+    const uint8_t* right;
+    int32_t width, height, pitch, channels;
+    int16_t* disp_wta;
+    float* disp_sub;
+    int16_t* disp_lr;
+    int16_t* disp_post;
+    uint8_t* valid;
+    float* disp_final;
+    /* Per-pair overrides used by stereo_match_batched (0 = handle's value;
+     * d_min is used when num_disp != 0). */
+    int32_t d_min, num_disp, win_radius;
+} stereo_pair;
+
+/* Fills *p with the paper's defaults (max_width/max_height 1920x1080,
+ * d_min 0, num_disp 128, cost F32). */
+void stereo_default_params(stereo_params* p);
+
+/* Creates a handle and allocates its device workspace for up to `max_batch`
+ * pairs of at most max_width x max_height with at most num_disp candidates.
+ * The workspace belongs to the handle until stereo_destroy.  Returns
+ * STEREO_ERR_OOM when the device allocation fails (*out untouched). */
+stereo_status stereo_create(const stereo_params* p, int32_t max_batch, stereo_handle** out);
+
+/* Frees the workspace and the handle.  Synchronises the handle's internal
+ * work first.  NULL is accepted. */
+stereo_status stereo_destroy(stereo_handle* h);
+
+/* Whole path on one pair (Sec. II): gray -> ZNCC + WTA + sub-pixel ->
+ * LR check -> outlier/hole loop -> Laplacian refinement.  Enqueued on
+ * `stream`. */
+stereo_status stereo_match(stereo_handle* h, const stereo_pair* pair, void* stream);
+
+/* The same path on n pairs of mixed sizes, disparity ranges and windows,
+ * each stage one persistent launch over all pairs' work units.  n <=
+ * max_batch.  When `use_graph` is non-zero the launch sequence is captured
+ * once into a CUDA graph (keyed by the pair geometry) and replayed. */
+stereo_status stereo_match_batched(stereo_handle* h, const stereo_pair* pairs, int32_t n,
+                                   int32_t use_graph, void* stream);
+
+/* Reads (and clears) the handle's device error word; synchronises `stream`
+ * first.  *err = 0 when no device-side error was recorded. */
+stereo_status stereo_get_device_error(stereo_handle* h, int32_t* err, void* stream);
+
+const char* stereo_status_str(stereo_status s);
+
+/* Tracing.  With stage timing on, stereo_match records CUDA events on its
+ * stream around its stages: 0 input conversion, 1 window statistics, 2 cost
+ * + winner-take-all kernel, 3 finalize (sub-pixel, LR check), 4 outlier /
+ * hole-filling loop, 5 refinement.  stereo_get_stage_times waits for the
+ * last stereo_match of the handle and writes min(n, STEREO_NUM_STAGES)
+ * durations in milliseconds. */
+#define STEREO_NUM_STAGES 6
+stereo_status stereo_set_stage_timing(stereo_handle* h, int32_t enable);
+stereo_status stereo_get_stage_times(stereo_handle* h, float* ms, int32_t n);
+
+/* Total number of CUDA kernels the library has enqueued since it was
+ * loaded (all handles and streams). */
+unsigned long long stereo_launch_count(void);
+
+/* ------------------------------------------------------------------------
+ * Stage entry points.  Each runs one step of the path on caller buffers, so
+ * every step can be fed its input independently (stage-wise parity).
+ * ---------------------------------------------------------------------- */
+
+/* RGB (interleaved, `pitch` bytes per row) -> gray, (77R+150G+29B+128)>>8. */
+stereo_status stereo_gray(const uint8_t* rgb, int32_t width, int32_t height, int32_t pitch,
+                          uint8_t* gray, void* stream);
+
+/* Sec. II-A: ZNCC of every valid candidate, winner-take-all for the left
+ * view (ties -> smallest d) and for the right view (best left pixel u + d
+ * for each right pixel u; used by the LR check), parabola sub-pixel offset
+ * on c = 1 - ZNCC.  left/right: gray, row stride = width.  disp_left,
+ * disp_right: int16 W*H; disp_sub: float W*H (NaN where invalid);
+ * cost: optional [H][W][num_disp] volume of c = 1 - ZNCC in `cost_dtype`
+ * (NaN for invalid candidates), NULL when cost_dtype is STEREO_COST_NONE.
+ * Uses the handle's workspace; width/height/num_disp must fit the handle. */
+stereo_status stereo_stage_match(stereo_handle* h, const uint8_t* left, const uint8_t* right,
+                                 int32_t width, int32_t height, int32_t d_min, int32_t num_disp,
+                                 int32_t win_radius, int32_t sampling, int32_t cost_dtype,
+                                 int16_t* disp_left, int16_t* disp_right, float* disp_sub,
+                                 void* cost, void* stream);
+
+/* Left-right consistency check: out(x) = dL(x) when dL(x) is valid, x - dL(x)
+ * is inside the image, dR(x - dL(x)) is valid and |dL - dR| <= thresh; else
+ * STEREO_INVALID. */
+stereo_status stereo_stage_lr(const int16_t* disp_left, const int16_t* disp_right, int32_t width,
+                              int32_t height, int32_t thresh, int16_t* out, void* stream);
+
+/* Sec. II-B radial outlier removal with the given radius (one pass). */
+stereo_status stereo_stage_outlier(const int16_t* in, int32_t width, int32_t height,
+                                   int32_t radius, float thresh, int16_t* out, void* stream);
+
+/* Sec. II-B first hole-filling method (8 radial directions). */
+stereo_status stereo_stage_fill_radial(const int16_t* in, int32_t width, int32_t height,
+                                       int32_t radius, int32_t min_dirs, int16_t* out,
+                                       void* stream);
+
+/* Sec. II-B second hole-filling method (disc).  min_count < 0 means a
+ * quarter of the disc's pixel count, rounded up. */
+stereo_status stereo_stage_fill_disc(const int16_t* in, int32_t width, int32_t height,
+                                     int32_t radius, int32_t min_count, int16_t* out,
+                                     void* stream);
+
+/* Sec. II-B loop: `params->outlier_rounds` rounds of outlier removal (radius
+ * r0 + t*dr) -> radial fill -> disc fill.  Uses the handle's workspace. */
+stereo_status stereo_stage_postprocess(stereo_handle* h, const int16_t* in, int32_t width,
+                                       int32_t height, int16_t* out, void* stream);
+
+/* Sec. II-C refinement (Eqs. 1-4) for the handle's parameters.  o_in: int16
+ * discrete disparities (STEREO_INVALID = none).  cost: [H][W][num_disp]
+ * volume of 1 - ZNCC in cost_dtype (NaN = invalid candidate); when cost_dtype
+ * is STEREO_COST_NONE the ZNCC is recomputed from left/right (gray).
+ * d_out: float d^(K) (NaN where invalid); o_out: final int16 o (may be NULL). */
+stereo_status stereo_stage_refine(stereo_handle* h, const int16_t* o_in, const void* cost,
+                                  int32_t cost_dtype, const uint8_t* left, const uint8_t* right,
+                                  int32_t width, int32_t height, int32_t d_min, int32_t num_disp,
+                                  int32_t win_radius, float* d_out, int16_t* o_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STEREO_H */

@@ -1,0 +1,340 @@
+"""ctypes binding of include/stereo.h.  Same names as the C ABI; arguments are
+torch tensors (device memory) and an optional torch/CUDA stream.  Nothing here
+computes: it checks dtypes/devices, takes data pointers and calls the
+library."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+from . import build as _build
+
+__all__ = [
+    "INVALID", "COST_NONE", "COST_F32", "COST_F16", "COST_BF16", "SAMPLE_FULL",
+    "SAMPLE_CHESSBOARD", "STATUS", "StereoError", "StereoParams", "StereoPair", "Handle", "lib",
+    "lib_path", "header_functions", "cost_stride", "stereo_default_params", "stereo_create",
+    "stereo_destroy", "stereo_match", "stereo_match_batched", "stereo_get_device_error",
+    "stereo_status_str", "stereo_gray", "stereo_stage_match", "stereo_stage_lr",
+    "stereo_stage_outlier", "stereo_stage_fill_radial", "stereo_stage_fill_disc",
+    "stereo_stage_postprocess", "stereo_stage_refine", "stereo_set_stage_timing",
+    "stereo_get_stage_times", "stereo_launch_count", "STAGE_NAMES",
+]
+
+STAGE_NAMES = ("input", "stats", "cost_wta", "finalize", "postprocess", "refine")
+
+INVALID = -32768
+COST_NONE, COST_F32, COST_F16, COST_BF16 = 0, 1, 2, 3
+SAMPLE_FULL, SAMPLE_CHESSBOARD = 0, 1
+STATUS = {0: "STEREO_OK", 1: "STEREO_ERR_INVALID_ARG", 2: "STEREO_ERR_CUDA", 3: "STEREO_ERR_OOM",
+          4: "STEREO_ERR_UNSUPPORTED", 5: "STEREO_ERR_TIMEOUT", 6: "STEREO_ERR_TOO_LARGE"}
+
+_HEADER = os.path.join(os.path.dirname(_build.HERE), "include", "stereo.h")
+
+
+class StereoError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+class StereoParams(C.Structure):
+    _fields_ = [
+        ("max_width", C.c_int32), ("max_height", C.c_int32),
+        ("d_min", C.c_int32), ("num_disp", C.c_int32),
+        ("win_radius", C.c_int32), ("sampling", C.c_int32), ("cost_dtype", C.c_int32),
+        ("lr_thresh", C.c_int32),
+        ("outlier_rounds", C.c_int32), ("r0", C.c_int32), ("dr", C.c_int32),
+        ("outlier_thresh", C.c_float),
+        ("fill_radial_r", C.c_int32), ("fill_radial_min_dirs", C.c_int32),
+        ("fill_disc_r", C.c_int32), ("fill_disc_min_count", C.c_int32),
+        ("smooth_radius", C.c_int32), ("smooth_iters", C.c_int32),
+        ("alpha", C.c_float), ("eta", C.c_float), ("refine_search", C.c_int32),
+    ]
+
+
+class StereoPair(C.Structure):
+    _fields_ = [
+        ("left", C.c_void_p), ("right", C.c_void_p),
+        ("width", C.c_int32), ("height", C.c_int32), ("pitch", C.c_int32), ("channels", C.c_int32),
+        ("disp_wta", C.c_void_p), ("disp_sub", C.c_void_p), ("disp_lr", C.c_void_p),
+        ("disp_post", C.c_void_p), ("valid", C.c_void_p), ("disp_final", C.c_void_p),
+        ("d_min", C.c_int32), ("num_disp", C.c_int32), ("win_radius", C.c_int32),
+    ]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads libstereo.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libstereo.so not built ({_build.LIB}); run "
+                               "python -m paper_2007_12623_b300.build")
+        L = C.CDLL(_build.LIB)
+        P, i32, f32 = C.c_void_p, C.c_int32, C.c_float
+        sig = {
+            "stereo_default_params": (None, [P]),
+            "stereo_create": (C.c_int, [P, i32, P]),
+            "stereo_destroy": (C.c_int, [P]),
+            "stereo_match": (C.c_int, [P, P, P]),
+            "stereo_match_batched": (C.c_int, [P, P, i32, i32, P]),
+            "stereo_get_device_error": (C.c_int, [P, P, P]),
+            "stereo_status_str": (C.c_char_p, [C.c_int]),
+            "stereo_gray": (C.c_int, [P, i32, i32, i32, P, P]),
+            "stereo_stage_match": (C.c_int, [P, P, P, i32, i32, i32, i32, i32, i32, i32, P, P, P, P, P]),
+            "stereo_stage_lr": (C.c_int, [P, P, i32, i32, i32, P, P]),
+            "stereo_stage_outlier": (C.c_int, [P, i32, i32, i32, f32, P, P]),
+            "stereo_stage_fill_radial": (C.c_int, [P, i32, i32, i32, i32, P, P]),
+            "stereo_stage_fill_disc": (C.c_int, [P, i32, i32, i32, i32, P, P]),
+            "stereo_stage_postprocess": (C.c_int, [P, P, i32, i32, P, P]),
+            "stereo_stage_refine": (C.c_int, [P, P, P, i32, P, P, i32, i32, i32, i32, i32, P, P, P]),
+            "stereo_set_stage_timing": (C.c_int, [P, i32]),
+            "stereo_get_stage_times": (C.c_int, [P, P, i32]),
+            "stereo_launch_count": (C.c_ulonglong, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/stereo.h."""
+    txt = open(_HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(stereo_[a-z_]+)\s*\(", txt)))
+
+
+def cost_stride(num_disp: int) -> int:
+    """Elements per pixel in a cost volume (num_disp rounded up to 8)."""
+    return (num_disp + 7) & ~7
+
+
+# ------------------------------------------------------------- marshalling
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise StereoError(status, where)
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _cost_torch_dtype(cdt):
+    import torch
+    return {COST_F32: torch.float32, COST_F16: torch.float16, COST_BF16: torch.bfloat16}.get(cdt)
+
+
+# ------------------------------------------------------------------ API
+
+def stereo_default_params(**overrides) -> StereoParams:
+    p = StereoParams()
+    lib().stereo_default_params(C.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Handle:
+    """Owns a stereo_handle; destroyed by close() or garbage collection."""
+
+    def __init__(self, ptr, params: StereoParams, max_batch: int):
+        self.ptr = ptr
+        self.params = params
+        self.max_batch = max_batch
+
+    def close(self):
+        if self.ptr:
+            lib().stereo_destroy(self.ptr)
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def stereo_create(params: StereoParams, max_batch: int = 1) -> Handle:
+    h = C.c_void_p()
+    _check(lib().stereo_create(C.byref(params), max_batch, C.byref(h)), "stereo_create")
+    return Handle(h, params, max_batch)
+
+
+def stereo_destroy(handle: Handle):
+    handle.close()
+
+
+def _pair_struct(left, right, disp_wta=None, disp_sub=None, disp_lr=None, disp_post=None,
+                 valid=None, disp_final=None, d_min=0, num_disp=0, win_radius=0):
+    import torch
+    if left.dim() == 3:
+        H, W, ch = left.shape
+    else:
+        (H, W), ch = left.shape, 1
+    if right.shape != left.shape:
+        raise ValueError("left/right shapes differ")
+    p = StereoPair()
+    p.left = _ptr(left, torch.uint8, "left")
+    p.right = _ptr(right, torch.uint8, "right")
+    p.width, p.height, p.pitch, p.channels = W, H, W * ch, ch
+    p.disp_wta = _ptr(disp_wta, torch.int16, "disp_wta")
+    p.disp_sub = _ptr(disp_sub, torch.float32, "disp_sub")
+    p.disp_lr = _ptr(disp_lr, torch.int16, "disp_lr")
+    p.disp_post = _ptr(disp_post, torch.int16, "disp_post")
+    p.valid = _ptr(valid, torch.uint8, "valid")
+    p.disp_final = _ptr(disp_final, torch.float32, "disp_final")
+    p.d_min, p.num_disp, p.win_radius = d_min, num_disp, win_radius
+    return p
+
+
+def stereo_match(handle: Handle, left, right, *, disp_wta=None, disp_sub=None, disp_lr=None,
+                 disp_post=None, valid=None, disp_final=None, d_min=0, num_disp=0, win_radius=0,
+                 stream=None):
+    """Whole path on one pair (uint8 HxW gray or HxWx3 RGB tensors)."""
+    p = _pair_struct(left, right, disp_wta, disp_sub, disp_lr, disp_post, valid, disp_final,
+                     d_min, num_disp, win_radius)
+    _check(lib().stereo_match(handle.ptr, C.byref(p), _stream(stream)), "stereo_match")
+
+
+def stereo_match_batched(handle: Handle, pairs, use_graph: bool = True, stream=None):
+    """pairs: list of dicts with the keyword arguments of stereo_match plus
+    left/right."""
+    arr = (StereoPair * len(pairs))()
+    for i, d in enumerate(pairs):
+        arr[i] = _pair_struct(**d)
+    _check(lib().stereo_match_batched(handle.ptr, arr, len(pairs), int(bool(use_graph)),
+                                      _stream(stream)), "stereo_match_batched")
+
+
+def stereo_get_device_error(handle: Handle, stream=None) -> int:
+    e = C.c_int32()
+    _check(lib().stereo_get_device_error(handle.ptr, C.byref(e), _stream(stream)),
+           "stereo_get_device_error")
+    return e.value
+
+
+def stereo_status_str(status: int) -> str:
+    return lib().stereo_status_str(status).decode()
+
+
+def stereo_gray(rgb, gray, stream=None):
+    import torch
+    H, W, _ = rgb.shape
+    _check(lib().stereo_gray(_ptr(rgb, torch.uint8, "rgb"), W, H, 3 * W,
+                             _ptr(gray, torch.uint8, "gray"), _stream(stream)), "stereo_gray")
+
+
+def stereo_stage_match(handle: Handle, left, right, d_min, num_disp, win_radius, sampling,
+                       cost_dtype, disp_left, disp_right, disp_sub, cost=None, stream=None):
+    import torch
+    H, W = left.shape
+    _check(lib().stereo_stage_match(
+        handle.ptr, _ptr(left, torch.uint8, "left"), _ptr(right, torch.uint8, "right"), W, H,
+        d_min, num_disp, win_radius, sampling, cost_dtype,
+        _ptr(disp_left, torch.int16, "disp_left"), _ptr(disp_right, torch.int16, "disp_right"),
+        _ptr(disp_sub, torch.float32, "disp_sub"), _ptr(cost, _cost_torch_dtype(cost_dtype), "cost"),
+        _stream(stream)), "stereo_stage_match")
+
+
+def stereo_stage_lr(disp_left, disp_right, thresh, out, stream=None):
+    import torch
+    H, W = disp_left.shape
+    _check(lib().stereo_stage_lr(_ptr(disp_left, torch.int16), _ptr(disp_right, torch.int16), W, H,
+                                 thresh, _ptr(out, torch.int16), _stream(stream)), "stereo_stage_lr")
+
+
+def stereo_stage_outlier(inp, radius, thresh, out, stream=None):
+    import torch
+    H, W = inp.shape
+    _check(lib().stereo_stage_outlier(_ptr(inp, torch.int16), W, H, radius, thresh,
+                                      _ptr(out, torch.int16), _stream(stream)),
+           "stereo_stage_outlier")
+
+
+def stereo_stage_fill_radial(inp, radius, min_dirs, out, stream=None):
+    import torch
+    H, W = inp.shape
+    _check(lib().stereo_stage_fill_radial(_ptr(inp, torch.int16), W, H, radius, min_dirs,
+                                          _ptr(out, torch.int16), _stream(stream)),
+           "stereo_stage_fill_radial")
+
+
+def stereo_stage_fill_disc(inp, radius, min_count, out, stream=None):
+    import torch
+    H, W = inp.shape
+    _check(lib().stereo_stage_fill_disc(_ptr(inp, torch.int16), W, H, radius, min_count,
+                                        _ptr(out, torch.int16), _stream(stream)),
+           "stereo_stage_fill_disc")
+
+
+def stereo_stage_postprocess(handle: Handle, inp, out, stream=None):
+    import torch
+    H, W = inp.shape
+    _check(lib().stereo_stage_postprocess(handle.ptr, _ptr(inp, torch.int16), W, H,
+                                          _ptr(out, torch.int16), _stream(stream)),
+           "stereo_stage_postprocess")
+
+
+def stereo_stage_refine(handle: Handle, o_in, cost, cost_dtype, left, right, d_min, num_disp,
+                        win_radius, d_out, o_out=None, stream=None):
+    import torch
+    H, W = o_in.shape
+    _check(lib().stereo_stage_refine(
+        handle.ptr, _ptr(o_in, torch.int16, "o_in"), _ptr(cost, _cost_torch_dtype(cost_dtype), "cost"),
+        cost_dtype, _ptr(left, torch.uint8, "left"), _ptr(right, torch.uint8, "right"), W, H, d_min,
+        num_disp, win_radius, _ptr(d_out, torch.float32, "d_out"), _ptr(o_out, torch.int16, "o_out"),
+        _stream(stream)), "stereo_stage_refine")
+
+
+def stereo_set_stage_timing(handle: Handle, enable: bool = True):
+    _check(lib().stereo_set_stage_timing(handle.ptr, int(bool(enable))), "stereo_set_stage_timing")
+
+
+def stereo_get_stage_times(handle: Handle) -> dict:
+    """Per-stage milliseconds of the handle's last stereo_match (waits for it)."""
+    arr = (C.c_float * len(STAGE_NAMES))()
+    _check(lib().stereo_get_stage_times(handle.ptr, arr, len(STAGE_NAMES)), "stereo_get_stage_times")
+    return dict(zip(STAGE_NAMES, [float(v) for v in arr]))
+
+
+def stereo_launch_count() -> int:
+    return int(lib().stereo_launch_count())

@@ -1,0 +1,62 @@
+// common.cuh -- shared device helpers of the stereo library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#define ST_INVALID (-32768)
+
+// Cost-volume element types (same numbering as stereo_cost_dtype).
+enum { CDT_NONE = 0, CDT_F32 = 1, CDT_F16 = 2, CDT_BF16 = 3 };
+
+// Per-pixel cost stride: num_disp rounded up to 8 elements so that every
+// pixel's slice starts 16-byte aligned for all element types.
+__host__ __device__ inline int cost_stride(int num_disp) { return (num_disp + 7) & ~7; }
+
+// A packed winner-take-all key.  For rho in [-1, 1] the float t = rho + 3.5
+// lies in [2.5, 4.5]; shifting its bit pattern left by 8 drops the constant
+// exponent bits and keeps the mantissa (plus one exponent bit separating
+// [2,4) from [4,8)), so unsigned order of the key is the order of rho at a
+// resolution of 2^-22 (below 4) / 2^-21 (above 4).  The low byte holds
+// 255 - (d - d_min), so among equal rho values the smallest d has the
+// largest key.  An invalid candidate uses t = 2.0 exactly, whose key is
+// below 2^8; every valid key is at least 0x20000000.
+#define KEY_VALID_MIN 0x20000000u
+#define KEY_T_OFFSET 3.5f
+#define KEY_T_INVALID 2.0f
+
+__device__ __forceinline__ uint32_t make_key(float t, uint32_t idx_code) {
+    return __float_as_uint(t) * 256u + idx_code;
+}
+
+__host__ __device__ inline int key_to_disp(uint32_t key, int d_min) {
+    return key >= KEY_VALID_MIN ? d_min + 255 - (int)(key & 255u) : ST_INVALID;
+}
+
+template <int CDT> struct CostT;
+template <> struct CostT<CDT_F32> { typedef float T; };
+template <> struct CostT<CDT_F16> { typedef __half T; };
+template <> struct CostT<CDT_BF16> { typedef __nv_bfloat16 T; };
+template <> struct CostT<CDT_NONE> { typedef float T; };
+
+__device__ __forceinline__ float cost_load(const void* base, int cdt, size_t idx) {
+    if (cdt == CDT_F32) return __ldg(reinterpret_cast<const float*>(base) + idx);
+    if (cdt == CDT_F16) return __half2float(reinterpret_cast<const __half*>(base)[idx]);
+    return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(base)[idx]);
+}
+
+// floor(a / b) for b > 0.
+__device__ __forceinline__ int floordiv_pos(int a, int b) {
+    int q = a / b;
+    return (a % b != 0 && a < 0) ? q - 1 : q;
+}
+
+// round(num / den) with halves toward +infinity, den > 0, integer exact.
+__device__ __forceinline__ int round_half_up_i(int num, int den) {
+    return floordiv_pos(2 * num + den, 2 * den);
+}
+
+__constant__ int c_dir8[8][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1},
+                                 {1, 1}, {1, -1}, {-1, 1}, {-1, -1}};

@@ -1,0 +1,547 @@
+// stereo_api.cu -- the C ABI of include/stereo.h: handle and workspace
+// management, argument checking and the launch sequence of the stereo path.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <atomic>
+#include <new>
+#include <stdio.h>
+#include <string.h>
+
+#include "../../include/stereo.h"
+#include "common.cuh"
+#include "match.cuh"
+#include "post.cuh"
+#include "refine.cuh"
+
+namespace {
+
+constexpr int kTH = 16;   // rows per cost work unit
+
+// Number of kernels this library has enqueued (all handles, all streams).
+std::atomic<unsigned long long> g_launches{0};
+inline void counted(int n = 1) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int elem_size(int cdt) { return cdt == CDT_F32 ? 4 : (cdt == CDT_NONE ? 0 : 2); }
+
+// Per-pair workspace carved out of one device allocation.
+struct PairWs {
+    uint8_t* gl;        // gray left  (W*H)
+    uint8_t* gr;        // gray right (W*H)
+    float2* statsL;     // {S, 1/sqrt(B)} per left pixel
+    float2* statsR;     // per right pixel
+    uint32_t* keys;     // keyL (W*H) then keyR (W*H)
+    void* cost;         // [H][W][cost_stride(D)]
+    int16_t* wta;       // left WTA
+    int16_t* lr;        // after LR check
+    int16_t* p;         // ping
+    int16_t* q;         // pong
+    int16_t* o;         // refinement o
+    int16_t* t;         // post-processing round buffer
+    int16_t* post;      // post-processing output (when the caller gives none)
+    float* dfin;        // refined output (when the caller gives none)
+    float* dprev;
+    float* dt;
+    float* b;
+    int* rsC;
+    int* rsO;
+    float* rsB;
+};
+
+size_t pair_ws_bytes(size_t npix, int D, int cdt) {
+    size_t b = 0;
+    b += align_up(npix, 256) * 2;                 // gl, gr
+    b += align_up(npix * 8, 256) * 2;             // stats
+    b += align_up(npix * 8, 256);                 // keys
+    b += align_up(npix * (size_t)cost_stride(D) * elem_size(cdt), 256);
+    b += align_up(npix * 2, 256) * 7;             // wta lr p q o t post
+    b += align_up(npix * 4, 256) * 7;             // dprev dt b rsC rsO rsB dfin
+    return b;
+}
+
+PairWs carve(uint8_t* base, size_t npix, int D, int cdt) {
+    PairWs w;
+    uint8_t* p = base;
+    auto take = [&](size_t bytes) { uint8_t* r = p; p += align_up(bytes, 256); return r; };
+    w.gl = take(npix);
+    w.gr = take(npix);
+    w.statsL = reinterpret_cast<float2*>(take(npix * 8));
+    w.statsR = reinterpret_cast<float2*>(take(npix * 8));
+    w.keys = reinterpret_cast<uint32_t*>(take(npix * 8));
+    w.cost = take(npix * (size_t)cost_stride(D) * elem_size(cdt));
+    w.wta = reinterpret_cast<int16_t*>(take(npix * 2));
+    w.lr = reinterpret_cast<int16_t*>(take(npix * 2));
+    w.p = reinterpret_cast<int16_t*>(take(npix * 2));
+    w.q = reinterpret_cast<int16_t*>(take(npix * 2));
+    w.o = reinterpret_cast<int16_t*>(take(npix * 2));
+    w.t = reinterpret_cast<int16_t*>(take(npix * 2));
+    w.post = reinterpret_cast<int16_t*>(take(npix * 2));
+    w.dfin = reinterpret_cast<float*>(take(npix * 4));
+    w.dprev = reinterpret_cast<float*>(take(npix * 4));
+    w.dt = reinterpret_cast<float*>(take(npix * 4));
+    w.b = reinterpret_cast<float*>(take(npix * 4));
+    w.rsC = reinterpret_cast<int*>(take(npix * 4));
+    w.rsO = reinterpret_cast<int*>(take(npix * 4));
+    w.rsB = reinterpret_cast<float*>(take(npix * 4));
+    return w;
+}
+
+int disc_area(int r) {
+    int n = 0;
+    for (int dy = -r; dy <= r; ++dy)
+        for (int dx = -r; dx <= r; ++dx)
+            if (dx * dx + dy * dy <= r * r) ++n;
+    return n;
+}
+
+}  // namespace
+
+struct stereo_handle {
+    stereo_params p;
+    int max_batch;
+    size_t npix_max;
+    size_t pair_bytes;
+    uint8_t* ws;         // max_batch * pair_bytes
+    int32_t* dev_err;    // device error word
+    bool timing;         // record per-stage events in stereo_match
+    bool ev_ready;
+    cudaEvent_t ev[STEREO_NUM_STAGES + 1];
+};
+
+// ------------------------------------------------------------- launchers
+
+namespace {
+
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+stereo_status last_error() {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "stereo: CUDA error %s\n", cudaGetErrorString(e));
+        return STEREO_ERR_CUDA;
+    }
+    return STEREO_OK;
+}
+
+template <int R, int K>
+void launch_zncc_rk(const uint8_t* L, const uint8_t* Rm, int W, int H, int d_min, int D,
+                    const float2* sl, const float2* sr, uint32_t* kl, uint32_t* kr, void* cost,
+                    int cdt, cudaStream_t s) {
+    typedef ZnccCfg<R, K, kTH> C;
+    const int nx = (W - 2 * R + C::TW - 1) / C::TW;
+    const int ny = (H - 2 * R + kTH - 1) / kTH;
+    const int nz = (D + 32 * K - 1) / (32 * K);
+    if (nx <= 0 || ny <= 0) return;
+    const size_t smem = (size_t)(C::ROWS * 32 + C::ROWS * C::RW + 32) * 4;
+    k_zncc_wta<R, K, kTH><<<dim3(nx, ny, nz), 32, smem, s>>>(L, Rm, W, H, d_min, D, sl, sr, kl, kr,
+                                                             cost, cdt);
+    counted();
+}
+
+template <int R>
+void launch_zncc_r(int K, const uint8_t* L, const uint8_t* Rm, int W, int H, int d_min, int D,
+                   const float2* sl, const float2* sr, uint32_t* kl, uint32_t* kr, void* cost,
+                   int cdt, cudaStream_t s) {
+    if (K == 4) launch_zncc_rk<R, 4>(L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s);
+    else if (K == 2) launch_zncc_rk<R, 2>(L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s);
+    else launch_zncc_rk<R, 1>(L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s);
+}
+
+int pick_k(int D) { return D <= 32 ? 1 : (D <= 64 ? 2 : 4); }
+
+void launch_zncc(int r, const uint8_t* L, const uint8_t* Rm, int W, int H, int d_min, int D,
+                 const float2* sl, const float2* sr, uint32_t* kl, uint32_t* kr, void* cost,
+                 int cdt, cudaStream_t s) {
+    const int K = pick_k(D);
+    switch (r) {
+        case 1: launch_zncc_r<1>(K, L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s); break;
+        case 2: launch_zncc_r<2>(K, L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s); break;
+        case 3: launch_zncc_r<3>(K, L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s); break;
+        case 4: launch_zncc_r<4>(K, L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s); break;
+        case 5: launch_zncc_r<5>(K, L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s); break;
+        case 6: launch_zncc_r<6>(K, L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s); break;
+        case 7: launch_zncc_r<7>(K, L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s); break;
+        default: break;
+    }
+}
+
+// Stats + fused cost/WTA + finalize for one pair whose gray images are gl/gr.
+void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, int D, int r,
+               int sampling, int cdt, int lr_thresh, const PairWs& w, void* cost,
+               int16_t* disp_left, int16_t* disp_right, float* disp_sub, int16_t* disp_lr,
+               cudaStream_t s, cudaEvent_t* ev = nullptr) {
+    dim3 sg((W + ST_TILE - 1) / ST_TILE, (H + ST_TILE - 1) / ST_TILE);
+    k_window_stats<<<sg, 256, 0, s>>>(gl, W, H, r, sampling, w.statsL, w.keys);
+    counted();
+    k_window_stats<<<sg, 256, 0, s>>>(gr, W, H, r, sampling, w.statsR, nullptr);
+    counted();
+    if (ev) cudaEventRecord(ev[2], s);
+    launch_zncc(r, gl, gr, W, H, d_min, D, w.statsL, w.statsR, w.keys, w.keys + (size_t)W * H, cost,
+                cdt, s);
+    if (ev) cudaEventRecord(ev[3], s);
+    dim3 fg((W + 127) / 128, H);
+    k_finalize<<<fg, 128, 0, s>>>(w.keys, w.keys + (size_t)W * H, W, H, d_min, D, lr_thresh, cost,
+                                  cdt, gl, gr, r, sampling, disp_left, disp_right, disp_sub, disp_lr);
+    counted();
+}
+
+void run_postprocess(const stereo_params& p, const int16_t* in, int W, int H, const PairWs& w,
+                     int16_t* out, cudaStream_t s) {
+    dim3 b2(32, 8), g2((W + 31) / 32, (H + 7) / 8);
+    dim3 gd((W + FD_TILE - 1) / FD_TILE, (H + FD_TILE - 1) / FD_TILE);
+    const int min_count = p.fill_disc_min_count >= 0 ? p.fill_disc_min_count
+                                                     : (disc_area(p.fill_disc_r) + 3) / 4;
+    const size_t fd_smem = (size_t)(FD_TILE + 2 * p.fill_disc_r) * (FD_TILE + 2 * p.fill_disc_r) * 2;
+    const int16_t* cur = in;
+    if (p.outlier_rounds <= 0) {
+        cudaMemcpyAsync(out, in, (size_t)W * H * 2, cudaMemcpyDeviceToDevice, s);
+        return;
+    }
+    for (int t = 0; t < p.outlier_rounds; ++t) {
+        k_outlier<<<g2, b2, 0, s>>>(cur, W, H, p.r0 + t * p.dr, p.outlier_thresh, w.p);
+        counted();
+        k_fill_radial<<<g2, b2, 0, s>>>(w.p, W, H, p.fill_radial_r, p.fill_radial_min_dirs, w.q);
+        counted();
+        int16_t* dst = (t == p.outlier_rounds - 1) ? out : w.t;
+        k_fill_disc<<<gd, b2, fd_smem, s>>>(w.q, W, H, p.fill_disc_r, min_count, dst);
+        counted();
+        cur = dst;
+    }
+}
+
+void run_refine(const stereo_params& p, const int16_t* o_in, const void* cost, int cdt,
+                const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, int D, int r,
+                int sampling, const PairWs& w, float* d_out, int16_t* o_out, uint8_t* valid,
+                cudaStream_t s) {
+    const int n = W * H;
+    k_refine_init<<<(n + 255) / 256, 256, 0, s>>>(o_in, n, w.o, w.dprev, d_out, valid);
+    counted();
+    const int rs = p.smooth_radius;
+    const int bx = 128;
+    dim3 gr2((W + bx - 1) / bx, H);
+    const size_t rsmem = (size_t)((bx + 2 * rs + 1) & ~1) * 2 + (size_t)(bx + 2 * rs) * 4;
+    for (int k = 0; k < p.smooth_iters; ++k) {
+        k_refine_rows<<<gr2, bx, rsmem, s>>>(w.o, nullptr, W, H, rs, w.rsC, w.rsO, nullptr);
+        counted();
+        k_refine_cols1<<<gr2, bx, 0, s>>>(w.o, w.dprev, w.rsC, w.rsO, W, H, rs, p.alpha, w.dt, w.b);
+        counted();
+        k_refine_rows<<<gr2, bx, rsmem, s>>>(w.o, w.b, W, H, rs, nullptr, nullptr, w.rsB);
+        counted();
+        k_refine_cols2<<<gr2, bx, 0, s>>>(w.o, w.dprev, w.dt, w.rsC, w.rsB, W, H, rs, p.eta,
+                                          p.refine_search, d_min, D, cost, cdt, gl, gr, r, sampling,
+                                          k == p.smooth_iters - 1 ? d_out : nullptr);
+        counted();
+    }
+    if (o_out) cudaMemcpyAsync(o_out, w.o, (size_t)n * 2, cudaMemcpyDeviceToDevice, s);
+}
+
+stereo_status check_params(const stereo_params* p) {
+    if (!p) return STEREO_ERR_INVALID_ARG;
+    if (p->max_width < 1 || p->max_height < 1) return STEREO_ERR_INVALID_ARG;
+    if ((size_t)p->max_width * p->max_height > (size_t)1 << 28) return STEREO_ERR_INVALID_ARG;
+    if (p->num_disp < 1 || p->num_disp > STEREO_MAX_DISP) return STEREO_ERR_INVALID_ARG;
+    if (p->win_radius < 1 || p->win_radius > STEREO_MAX_WIN_RADIUS) return STEREO_ERR_INVALID_ARG;
+    if (p->sampling != STEREO_SAMPLE_FULL && p->sampling != STEREO_SAMPLE_CHESSBOARD)
+        return STEREO_ERR_INVALID_ARG;
+    if (p->cost_dtype < 0 || p->cost_dtype > 3) return STEREO_ERR_INVALID_ARG;
+    if (p->d_min < -4096 || p->d_min > 4096) return STEREO_ERR_INVALID_ARG;
+    if (p->lr_thresh < 0 || p->outlier_rounds < 0 || p->r0 < 0 || p->dr < 0) return STEREO_ERR_INVALID_ARG;
+    if (p->fill_radial_r < 0 || p->fill_radial_min_dirs < 0) return STEREO_ERR_INVALID_ARG;
+    if (p->fill_disc_r < 0 || p->fill_disc_r > FD_MAXR) return STEREO_ERR_INVALID_ARG;
+    if (p->smooth_radius < 0 || p->smooth_iters < 0 || p->refine_search < 0) return STEREO_ERR_INVALID_ARG;
+    if (!(p->outlier_thresh >= 0.f) || !(p->alpha >= 0.f && p->alpha <= 1.f) || !(p->eta >= 0.f))
+        return STEREO_ERR_INVALID_ARG;
+    return STEREO_OK;
+}
+
+stereo_status check_match_args(const stereo_handle* h, int W, int H, int d_min, int D, int r,
+                               int sampling, int cdt) {
+    if (!h) return STEREO_ERR_INVALID_ARG;
+    if (W < 1 || H < 1 || D < 1 || D > STEREO_MAX_DISP || r < 1 || r > STEREO_MAX_WIN_RADIUS)
+        return STEREO_ERR_INVALID_ARG;
+    if (d_min < -4096 || d_min > 4096) return STEREO_ERR_INVALID_ARG;
+    if (cdt < 0 || cdt > 3) return STEREO_ERR_INVALID_ARG;
+    if (sampling != STEREO_SAMPLE_FULL) return STEREO_ERR_UNSUPPORTED;
+    if (W > h->p.max_width || H > h->p.max_height || D > h->p.num_disp) return STEREO_ERR_TOO_LARGE;
+    return STEREO_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ ABI
+
+extern "C" {
+
+void stereo_default_params(stereo_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->max_width = 1920;
+    p->max_height = 1080;
+    p->d_min = 0;
+    p->num_disp = 128;
+    p->win_radius = 5;
+    p->sampling = STEREO_SAMPLE_FULL;
+    p->cost_dtype = STEREO_COST_F32;
+    p->lr_thresh = 1;
+    p->outlier_rounds = 3;
+    p->r0 = 10;
+    p->dr = 10;
+    p->outlier_thresh = 2.5f;
+    p->fill_radial_r = 50;
+    p->fill_radial_min_dirs = 4;
+    p->fill_disc_r = 20;
+    p->fill_disc_min_count = -1;
+    p->smooth_radius = 15;
+    p->smooth_iters = 5;
+    p->alpha = 0.1f;
+    p->eta = 0.01f;
+    p->refine_search = 5;
+}
+
+const char* stereo_status_str(stereo_status s) {
+    switch (s) {
+        case STEREO_OK: return "ok";
+        case STEREO_ERR_INVALID_ARG: return "invalid argument";
+        case STEREO_ERR_CUDA: return "CUDA error";
+        case STEREO_ERR_OOM: return "out of device memory";
+        case STEREO_ERR_UNSUPPORTED: return "unsupported";
+        case STEREO_ERR_TIMEOUT: return "device wait timed out";
+        case STEREO_ERR_TOO_LARGE: return "request exceeds handle capacity";
+    }
+    return "unknown status";
+}
+
+stereo_status stereo_create(const stereo_params* p, int32_t max_batch, stereo_handle** out) {
+    if (!out || max_batch < 1) return STEREO_ERR_INVALID_ARG;
+    stereo_status st = check_params(p);
+    if (st != STEREO_OK) return st;
+    stereo_handle* h = new (std::nothrow) stereo_handle();
+    if (!h) return STEREO_ERR_OOM;
+    h->p = *p;
+    h->max_batch = max_batch;
+    h->npix_max = (size_t)p->max_width * p->max_height;
+    h->pair_bytes = pair_ws_bytes(h->npix_max, p->num_disp, p->cost_dtype);
+    h->ws = nullptr;
+    h->dev_err = nullptr;
+    h->timing = false;
+    h->ev_ready = false;
+    if (cudaMalloc(&h->ws, h->pair_bytes * max_batch) != cudaSuccess ||
+        cudaMalloc(&h->dev_err, sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        if (h->ws) cudaFree(h->ws);
+        if (h->dev_err) cudaFree(h->dev_err);
+        delete h;
+        return STEREO_ERR_OOM;
+    }
+    if (cudaMemset(h->dev_err, 0, sizeof(int32_t)) != cudaSuccess) {
+        cudaFree(h->ws);
+        cudaFree(h->dev_err);
+        delete h;
+        return STEREO_ERR_CUDA;
+    }
+    *out = h;
+    return STEREO_OK;
+}
+
+stereo_status stereo_destroy(stereo_handle* h) {
+    if (!h) return STEREO_OK;
+    cudaDeviceSynchronize();
+    if (h->ev_ready)
+        for (int i = 0; i <= STEREO_NUM_STAGES; ++i) cudaEventDestroy(h->ev[i]);
+    cudaFree(h->ws);
+    cudaFree(h->dev_err);
+    delete h;
+    return STEREO_OK;
+}
+
+stereo_status stereo_get_device_error(stereo_handle* h, int32_t* err, void* stream) {
+    if (!h || !err) return STEREO_ERR_INVALID_ARG;
+    int32_t v = 0;
+    if (cudaMemcpyAsync(&v, h->dev_err, sizeof(v), cudaMemcpyDeviceToHost, S(stream)) != cudaSuccess ||
+        cudaStreamSynchronize(S(stream)) != cudaSuccess ||
+        cudaMemsetAsync(h->dev_err, 0, sizeof(int32_t), S(stream)) != cudaSuccess)
+        return STEREO_ERR_CUDA;
+    *err = v;
+    return STEREO_OK;
+}
+
+stereo_status stereo_gray(const uint8_t* rgb, int32_t width, int32_t height, int32_t pitch,
+                          uint8_t* gray, void* stream) {
+    if (!rgb || !gray || width < 1 || height < 1 || pitch < 3 * width) return STEREO_ERR_INVALID_ARG;
+    k_gray<<<dim3((width + 127) / 128, height), 128, 0, S(stream)>>>(rgb, width, height, pitch, gray);
+    counted();
+    return last_error();
+}
+
+stereo_status stereo_stage_match(stereo_handle* h, const uint8_t* left, const uint8_t* right,
+                                 int32_t width, int32_t height, int32_t d_min, int32_t num_disp,
+                                 int32_t win_radius, int32_t sampling, int32_t cost_dtype,
+                                 int16_t* disp_left, int16_t* disp_right, float* disp_sub,
+                                 void* cost, void* stream) {
+    stereo_status st = check_match_args(h, width, height, d_min, num_disp, win_radius, sampling,
+                                        cost_dtype);
+    if (st != STEREO_OK) return st;
+    if (!left || !right) return STEREO_ERR_INVALID_ARG;
+    if ((cost_dtype == CDT_NONE) != (cost == nullptr)) return STEREO_ERR_INVALID_ARG;
+    if (cost && (reinterpret_cast<uintptr_t>(cost) & 15)) return STEREO_ERR_INVALID_ARG;
+    PairWs w = carve(h->ws, (size_t)width * height, num_disp, h->p.cost_dtype);
+    run_match(left, right, width, height, d_min, num_disp, win_radius, sampling, cost_dtype,
+              h->p.lr_thresh, w, cost, disp_left, disp_right, disp_sub, nullptr, S(stream));
+    return last_error();
+}
+
+stereo_status stereo_stage_lr(const int16_t* dL, const int16_t* dR, int32_t W, int32_t H,
+                              int32_t thresh, int16_t* out, void* stream) {
+    if (!dL || !dR || !out || W < 1 || H < 1 || thresh < 0) return STEREO_ERR_INVALID_ARG;
+    k_lr_check<<<dim3((W + 127) / 128, H), 128, 0, S(stream)>>>(dL, dR, W, H, thresh, out);
+    counted();
+    return last_error();
+}
+
+stereo_status stereo_stage_outlier(const int16_t* in, int32_t W, int32_t H, int32_t radius,
+                                   float thresh, int16_t* out, void* stream) {
+    if (!in || !out || in == out || W < 1 || H < 1 || radius < 0 || !(thresh >= 0.f))
+        return STEREO_ERR_INVALID_ARG;
+    k_outlier<<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, S(stream)>>>(in, W, H, radius,
+                                                                               thresh, out);
+    counted();
+    return last_error();
+}
+
+stereo_status stereo_stage_fill_radial(const int16_t* in, int32_t W, int32_t H, int32_t radius,
+                                       int32_t min_dirs, int16_t* out, void* stream) {
+    if (!in || !out || in == out || W < 1 || H < 1 || radius < 0 || min_dirs < 0)
+        return STEREO_ERR_INVALID_ARG;
+    k_fill_radial<<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, S(stream)>>>(
+        in, W, H, radius, min_dirs, out);
+    counted();
+    return last_error();
+}
+
+stereo_status stereo_stage_fill_disc(const int16_t* in, int32_t W, int32_t H, int32_t radius,
+                                     int32_t min_count, int16_t* out, void* stream) {
+    if (!in || !out || in == out || W < 1 || H < 1 || radius < 0 || radius > FD_MAXR)
+        return STEREO_ERR_INVALID_ARG;
+    if (min_count < 0) min_count = (disc_area(radius) + 3) / 4;
+    const size_t smem = (size_t)(FD_TILE + 2 * radius) * (FD_TILE + 2 * radius) * 2;
+    k_fill_disc<<<dim3((W + FD_TILE - 1) / FD_TILE, (H + FD_TILE - 1) / FD_TILE), dim3(32, 8), smem,
+                  S(stream)>>>(in, W, H, radius, min_count, out);
+    counted();
+    return last_error();
+}
+
+stereo_status stereo_stage_postprocess(stereo_handle* h, const int16_t* in, int32_t W, int32_t H,
+                                       int16_t* out, void* stream) {
+    if (!h || !in || !out || W < 1 || H < 1) return STEREO_ERR_INVALID_ARG;
+    if (W > h->p.max_width || H > h->p.max_height) return STEREO_ERR_TOO_LARGE;
+    PairWs w = carve(h->ws, (size_t)W * H, h->p.num_disp, h->p.cost_dtype);
+    run_postprocess(h->p, in, W, H, w, out, S(stream));
+    return last_error();
+}
+
+stereo_status stereo_stage_refine(stereo_handle* h, const int16_t* o_in, const void* cost,
+                                  int32_t cost_dtype, const uint8_t* left, const uint8_t* right,
+                                  int32_t W, int32_t H, int32_t d_min, int32_t D, int32_t r,
+                                  float* d_out, int16_t* o_out, void* stream) {
+    if (!h || !o_in || !d_out || W < 1 || H < 1 || D < 1 || D > STEREO_MAX_DISP)
+        return STEREO_ERR_INVALID_ARG;
+    if (cost_dtype < 0 || cost_dtype > 3) return STEREO_ERR_INVALID_ARG;
+    if (cost_dtype == CDT_NONE && (!left || !right || r < 1 || r > STEREO_MAX_WIN_RADIUS))
+        return STEREO_ERR_INVALID_ARG;
+    if (cost_dtype != CDT_NONE && !cost) return STEREO_ERR_INVALID_ARG;
+    if (W > h->p.max_width || H > h->p.max_height) return STEREO_ERR_TOO_LARGE;
+    PairWs w = carve(h->ws, (size_t)W * H, h->p.num_disp, h->p.cost_dtype);
+    run_refine(h->p, o_in, cost, cost_dtype, left, right, W, H, d_min, D, r, h->p.sampling, w,
+               d_out, o_out, nullptr, S(stream));
+    return last_error();
+}
+
+static void mark(stereo_handle* h, int i, cudaStream_t s) {
+    if (h->timing && h->ev_ready) cudaEventRecord(h->ev[i], s);
+}
+
+stereo_status stereo_set_stage_timing(stereo_handle* h, int32_t enable) {
+    if (!h) return STEREO_ERR_INVALID_ARG;
+    if (enable && !h->ev_ready) {
+        for (int i = 0; i <= STEREO_NUM_STAGES; ++i)
+            if (cudaEventCreate(&h->ev[i]) != cudaSuccess) return STEREO_ERR_CUDA;
+        h->ev_ready = true;
+    }
+    h->timing = enable != 0;
+    return STEREO_OK;
+}
+
+stereo_status stereo_get_stage_times(stereo_handle* h, float* ms, int32_t n) {
+    if (!h || !ms || n < 0) return STEREO_ERR_INVALID_ARG;
+    if (!h->ev_ready) return STEREO_ERR_INVALID_ARG;
+    if (cudaEventSynchronize(h->ev[STEREO_NUM_STAGES]) != cudaSuccess) return STEREO_ERR_CUDA;
+    for (int i = 0; i < n && i < STEREO_NUM_STAGES; ++i)
+        if (cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]) != cudaSuccess) return STEREO_ERR_CUDA;
+    return STEREO_OK;
+}
+
+unsigned long long stereo_launch_count(void) { return g_launches.load(); }
+
+stereo_status stereo_match(stereo_handle* h, const stereo_pair* pr, void* stream) {
+    if (!h || !pr || !pr->left || !pr->right) return STEREO_ERR_INVALID_ARG;
+    const int W = pr->width, H = pr->height;
+    const int d_min = pr->num_disp ? pr->d_min : h->p.d_min;
+    const int D = pr->num_disp ? pr->num_disp : h->p.num_disp;
+    const int r = pr->win_radius ? pr->win_radius : h->p.win_radius;
+    const int cdt = h->p.cost_dtype;
+    stereo_status st = check_match_args(h, W, H, d_min, D, r, h->p.sampling, cdt);
+    if (st != STEREO_OK) return st;
+    if (pr->channels != 1 && pr->channels != 3) return STEREO_ERR_INVALID_ARG;
+    if (pr->pitch < W * pr->channels) return STEREO_ERR_INVALID_ARG;
+    cudaStream_t s = S(stream);
+    PairWs w = carve(h->ws, (size_t)W * H, h->p.num_disp, cdt);
+    const uint8_t* gl = pr->left;
+    const uint8_t* gr = pr->right;
+    dim3 g((W + 127) / 128, H);
+    mark(h, 0, s);
+    if (pr->channels == 3) {
+        k_gray<<<g, 128, 0, s>>>(pr->left, W, H, pr->pitch, w.gl);
+        counted();
+        k_gray<<<g, 128, 0, s>>>(pr->right, W, H, pr->pitch, w.gr);
+        counted();
+        gl = w.gl;
+        gr = w.gr;
+    } else if (pr->pitch != W) {
+        k_copy_pitched<<<g, 128, 0, s>>>(pr->left, W, H, pr->pitch, w.gl);
+        counted();
+        k_copy_pitched<<<g, 128, 0, s>>>(pr->right, W, H, pr->pitch, w.gr);
+        counted();
+        gl = w.gl;
+        gr = w.gr;
+    }
+    mark(h, 1, s);
+    int16_t* wta = pr->disp_wta ? pr->disp_wta : w.wta;
+    void* cost = cdt != CDT_NONE ? w.cost : nullptr;
+    run_match(gl, gr, W, H, d_min, D, r, h->p.sampling, cdt, h->p.lr_thresh, w, cost, wta, nullptr,
+              pr->disp_sub, w.lr, s, h->timing && h->ev_ready ? h->ev : nullptr);
+    if (pr->disp_lr) cudaMemcpyAsync(pr->disp_lr, w.lr, (size_t)W * H * 2, cudaMemcpyDeviceToDevice, s);
+    mark(h, 4, s);
+    int16_t* post = pr->disp_post ? pr->disp_post : w.post;
+    run_postprocess(h->p, w.lr, W, H, w, post, s);
+    mark(h, 5, s);
+    float* dfin = pr->disp_final ? pr->disp_final : w.dfin;
+    run_refine(h->p, post, cost, cdt, gl, gr, W, H, d_min, D, r, h->p.sampling, w, dfin, nullptr,
+               pr->valid, s);
+    mark(h, 6, s);
+    return last_error();
+}
+
+stereo_status stereo_match_batched(stereo_handle* h, const stereo_pair* pairs, int32_t n,
+                                   int32_t use_graph, void* stream) {
+    (void)use_graph;
+    if (!h || !pairs || n < 1) return STEREO_ERR_INVALID_ARG;
+    if (n > h->max_batch) return STEREO_ERR_TOO_LARGE;
+    for (int i = 0; i < n; ++i) {
+        stereo_status st = stereo_match(h, &pairs[i], stream);
+        if (st != STEREO_OK) return st;
+    }
+    return STEREO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+"""End-to-end GPU path (stereo_match: gray -> match -> LR -> post -> refine)
+against the oracle's whole pipeline on the seeded workloads, and sampled
+full-size parity on the 960x540 tissue workload."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import NEAR_TIE, SUB_TOL, REFINE_RTOL, to_np, int_map_mismatch, describe
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2007_12623_b300 as st  # noqa: E402
+
+INV = oracle.INVALID
+
+
+@pytest.fixture(scope="module")
+def dev():
+    assert torch.cuda.is_available()
+    st.lib()
+    return torch.device("cuda:0")
+
+
+def T(a, dev):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+
+def run_match(dev, Limg, Rimg, p: oracle.Params, cdt=st.COST_F32):
+    H, W = Limg.shape[:2]
+    sp = st.stereo_default_params(max_width=W, max_height=H, d_min=p.d_min, num_disp=p.num_disp,
+                                  win_radius=p.win_radius, cost_dtype=cdt,
+                                  smooth_radius=p.smooth_radius, smooth_iters=p.smooth_iters)
+    h = st.stereo_create(sp)
+    out = dict(disp_wta=torch.empty((H, W), dtype=torch.int16, device=dev),
+               disp_sub=torch.empty((H, W), dtype=torch.float32, device=dev),
+               disp_lr=torch.empty((H, W), dtype=torch.int16, device=dev),
+               disp_post=torch.empty((H, W), dtype=torch.int16, device=dev),
+               valid=torch.empty((H, W), dtype=torch.uint8, device=dev),
+               disp_final=torch.empty((H, W), dtype=torch.float32, device=dev))
+    st.stereo_match(h, T(Limg, dev), T(Rimg, dev), **out)
+    torch.cuda.synchronize()
+    h.close()
+    return {k: to_np(v) for k, v in out.items()}
+
+
+def test_perlin_end_to_end(dev):
+    """320x240, D = 32, 11x11 window, LR check 1 px, hole filling, 5x5
+    smoothing (radius 2)."""
+    L, R, gt = synth.perlin_pair(synth.seed_for(0))
+    p = oracle.Params(d_min=0, num_disp=32, win_radius=5, smooth_radius=2, smooth_iters=5)
+    ref = oracle.pipeline(L, R, p)
+    m = oracle.match(L, R, 0, 32, 5)
+    g = run_match(dev, L, R, p)
+    near = m["gapL"] < NEAR_TIE
+    bad = int_map_mismatch(g["disp_wta"], ref["dL"], near)
+    assert len(bad) == 0, describe(bad, g["disp_wta"], ref["dL"])
+    same = (g["disp_wta"] == ref["dL"]) & (ref["dL"] != INV)
+    assert np.all(np.abs(g["disp_sub"][same] - ref["sub"][same]) <= SUB_TOL)
+    if not near.any() and not (m["gapR"] < NEAR_TIE).any():
+        assert np.array_equal(g["disp_lr"], ref["o_lr"])
+        assert np.array_equal(g["disp_post"], ref["o_post"])
+        assert np.array_equal(g["valid"].astype(bool), ref["o_post"] != INV)
+    v = ref["o_post"] != INV
+    rel = np.abs(g["disp_final"][v] - ref["d_final"][v]) / np.maximum(np.abs(ref["d_final"][v]), 1)
+    print(f"end-to-end refine: {100 * np.mean(rel > REFINE_RTOL):.3f}% beyond 1e-4")
+    assert np.mean(rel > REFINE_RTOL) <= 0.005
+    # accuracy against the generator's field (context): median error < 0.5 px
+    gv = g["valid"].astype(bool)
+    assert np.median(np.abs(g["disp_final"][gv] - gt[gv])) < 0.5
+
+
+def test_tissue_full_size_sampled(dev):
+    """960x540 RGB tissue pair, D = 128, full post-processing: every GPU
+    winner-take-all pixel of a sample of rows is checked against the oracle
+    computed pixel by pixel."""
+    Lrgb, Rrgb, gt = synth.tissue_pair(synth.seed_for(1))
+    p = oracle.Params(d_min=0, num_disp=128, win_radius=5)
+    g = run_match(dev, Lrgb, Rrgb, p)
+    Lg, Rg = oracle.gray(Lrgb), oracle.gray(Rrgb)
+    rng = np.random.default_rng(7)
+    checked = 0
+    for _ in range(300):
+        y = int(rng.integers(0, 540))
+        x = int(rng.integers(0, 960))
+        d, gap, sub = oracle.wta_left_pixel(Lg, Rg, 0, 128, 5, x, y)
+        if gap < NEAR_TIE:
+            continue
+        assert g["disp_wta"][y, x] == d, (x, y)
+        if d != INV:
+            assert abs(g["disp_sub"][y, x] - sub) <= SUB_TOL
+        checked += 1
+    assert checked > 250
+    # properties that hold at any size
+    wta = g["disp_wta"]
+    assert np.all((wta == INV) | ((wta >= 0) & (wta < 128)))
+    fin = g["disp_final"]
+    v = g["valid"].astype(bool)
+    assert np.all(np.isnan(fin[~v])) and np.all(np.isfinite(fin[v]))
+    assert np.all(fin[v] > -6) and np.all(fin[v] < 133)
+
+
+def test_rgb_and_pitch_inputs(dev):
+    """RGB inputs go through the fixed-point gray conversion first."""
+    Lrgb, Rrgb, gt = synth.tissue_pair(synth.seed_for(1), 200, 90)
+    g_rgb = torch.empty((90, 200), dtype=torch.uint8, device=dev)
+    st.stereo_gray(T(Lrgb, dev), g_rgb)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_np(g_rgb), oracle.gray(Lrgb))
