@@ -2,6 +2,7 @@
 // management, argument checking and the launch sequence of the stereo path.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <algorithm>
 #include <atomic>
 #include <new>
 #include <stdio.h>
@@ -10,6 +11,7 @@
 #include "../../include/stereo.h"
 #include "common.cuh"
 #include "match.cuh"
+#include "cost.cuh"
 #include "post.cuh"
 #include "refine.cuh"
 
@@ -29,8 +31,10 @@ int elem_size(int cdt) { return cdt == CDT_F32 ? 4 : (cdt == CDT_NONE ? 0 : 2); 
 struct PairWs {
     uint8_t* gl;        // gray left  (W*H)
     uint8_t* gr;        // gray right (W*H)
-    float2* statsL;     // {S, 1/sqrt(B)} per left pixel
-    float2* statsR;     // per right pixel
+    float* Lf;          // float left image, row stride lstride(W)
+    float* Rf;          // float right image with padding, row stride <= W + 2*CMARGIN
+    float2* lstats;     // {S, 1/sqrt(B)} per left pixel
+    float4* ustats;     // {S_hi, S_lo, 1/sqrt(B), valid} per right pixel (padded rows)
     uint32_t* keys;     // keyL (W*H) then keyR (W*H)
     void* cost;         // [H][W][cost_stride(D)]
     int16_t* wta;       // left WTA
@@ -49,10 +53,16 @@ struct PairWs {
     float* rsB;
 };
 
-size_t pair_ws_bytes(size_t npix, int D, int cdt) {
+// Geometry-dependent buffers are sized from the handle's maximum width and
+// height (maxW, maxH).
+size_t pair_ws_bytes(size_t npix, int D, int cdt, int maxW = 0, int maxH = 0) {
     size_t b = 0;
+    b += align_up((size_t)maxH * ((maxW + 40 + 3) & ~3) * 4, 256);      // Lf
+    b += align_up((size_t)maxH * (maxW + 2 * CMARGIN) * 4, 256);        // Rf
+    b += align_up(npix * 8, 256);                                       // lstats
+    b += align_up((size_t)maxH * (maxW + 2 * CMARGIN) * 16, 256);       // ustats
     b += align_up(npix, 256) * 2;                 // gl, gr
-    b += align_up(npix * 8, 256) * 2;             // stats
+    b += 0;                                       // image-shaped buffers: see carve()
     b += align_up(npix * 8, 256);                 // keys
     b += align_up(npix * (size_t)cost_stride(D) * elem_size(cdt), 256);
     b += align_up(npix * 2, 256) * 7;             // wta lr p q o t post
@@ -60,14 +70,16 @@ size_t pair_ws_bytes(size_t npix, int D, int cdt) {
     return b;
 }
 
-PairWs carve(uint8_t* base, size_t npix, int D, int cdt) {
+PairWs carve(uint8_t* base, size_t npix, int D, int cdt, int maxW, int maxH) {
     PairWs w;
     uint8_t* p = base;
     auto take = [&](size_t bytes) { uint8_t* r = p; p += align_up(bytes, 256); return r; };
+    w.Lf = reinterpret_cast<float*>(take((size_t)maxH * ((maxW + 40 + 3) & ~3) * 4));
+    w.Rf = reinterpret_cast<float*>(take((size_t)maxH * (maxW + 2 * CMARGIN) * 4));
+    w.lstats = reinterpret_cast<float2*>(take(npix * 8));
+    w.ustats = reinterpret_cast<float4*>(take((size_t)maxH * (maxW + 2 * CMARGIN) * 16));
     w.gl = take(npix);
     w.gr = take(npix);
-    w.statsL = reinterpret_cast<float2*>(take(npix * 8));
-    w.statsR = reinterpret_cast<float2*>(take(npix * 8));
     w.keys = reinterpret_cast<uint32_t*>(take(npix * 8));
     w.cost = take(npix * (size_t)cost_stride(D) * elem_size(cdt));
     w.wta = reinterpret_cast<int16_t*>(take(npix * 2));
@@ -124,44 +136,37 @@ stereo_status last_error() {
     return STEREO_OK;
 }
 
+int pick_k(int D) { return D <= 32 ? 1 : (D <= 64 ? 2 : 4); }
+int pos_mod4(int v) { return ((v % 4) + 4) % 4; }
+
 template <int R, int K>
-void launch_zncc_rk(const uint8_t* L, const uint8_t* Rm, int W, int H, int d_min, int D,
-                    const float2* sl, const float2* sr, uint32_t* kl, uint32_t* kr, void* cost,
-                    int cdt, cudaStream_t s) {
-    typedef ZnccCfg<R, K, kTH> C;
-    const int nx = (W - 2 * R + C::TW - 1) / C::TW;
-    const int ny = (H - 2 * R + kTH - 1) / kTH;
-    const int nz = (D + 32 * K - 1) / (32 * K);
+void launch_cost_rk(const CostArgs& a, cudaStream_t s) {
+    typedef CostGeom<R> G;
+    typedef CostSmem<R, K> Sm;
+    const int nx = (a.W - 2 * R + G::TW - 1) / G::TW;
+    const int ny = (a.H - 2 * R + kTH - 1) / kTH;
+    const int nz = (a.D + 32 * K - 1) / (32 * K);
     if (nx <= 0 || ny <= 0) return;
-    const size_t smem = (size_t)(C::ROWS * 32 + C::ROWS * C::RW + 32) * 4;
-    k_zncc_wta<R, K, kTH><<<dim3(nx, ny, nz), 32, smem, s>>>(L, Rm, W, H, d_min, D, sl, sr, kl, kr,
-                                                             cost, cdt);
+    k_cost_wta<R, K, kTH><<<dim3(nx, ny, nz), 32, Sm::BYTES, s>>>(a);
     counted();
 }
 
 template <int R>
-void launch_zncc_r(int K, const uint8_t* L, const uint8_t* Rm, int W, int H, int d_min, int D,
-                   const float2* sl, const float2* sr, uint32_t* kl, uint32_t* kr, void* cost,
-                   int cdt, cudaStream_t s) {
-    if (K == 4) launch_zncc_rk<R, 4>(L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s);
-    else if (K == 2) launch_zncc_rk<R, 2>(L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s);
-    else launch_zncc_rk<R, 1>(L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s);
+void launch_cost_r(int K, const CostArgs& a, cudaStream_t s) {
+    if (K == 4) launch_cost_rk<R, 4>(a, s);
+    else if (K == 2) launch_cost_rk<R, 2>(a, s);
+    else launch_cost_rk<R, 1>(a, s);
 }
 
-int pick_k(int D) { return D <= 32 ? 1 : (D <= 64 ? 2 : 4); }
-
-void launch_zncc(int r, const uint8_t* L, const uint8_t* Rm, int W, int H, int d_min, int D,
-                 const float2* sl, const float2* sr, uint32_t* kl, uint32_t* kr, void* cost,
-                 int cdt, cudaStream_t s) {
-    const int K = pick_k(D);
+void launch_cost(int r, int K, const CostArgs& a, cudaStream_t s) {
     switch (r) {
-        case 1: launch_zncc_r<1>(K, L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s); break;
-        case 2: launch_zncc_r<2>(K, L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s); break;
-        case 3: launch_zncc_r<3>(K, L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s); break;
-        case 4: launch_zncc_r<4>(K, L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s); break;
-        case 5: launch_zncc_r<5>(K, L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s); break;
-        case 6: launch_zncc_r<6>(K, L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s); break;
-        case 7: launch_zncc_r<7>(K, L, Rm, W, H, d_min, D, sl, sr, kl, kr, cost, cdt, s); break;
+        case 1: launch_cost_r<1>(K, a, s); break;
+        case 2: launch_cost_r<2>(K, a, s); break;
+        case 3: launch_cost_r<3>(K, a, s); break;
+        case 4: launch_cost_r<4>(K, a, s); break;
+        case 5: launch_cost_r<5>(K, a, s); break;
+        case 6: launch_cost_r<6>(K, a, s); break;
+        case 7: launch_cost_r<7>(K, a, s); break;
         default: break;
     }
 }
@@ -171,14 +176,25 @@ void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, in
                int sampling, int cdt, int lr_thresh, const PairWs& w, void* cost,
                int16_t* disp_left, int16_t* disp_right, float* disp_sub, int16_t* disp_lr,
                cudaStream_t s, cudaEvent_t* ev = nullptr) {
-    dim3 sg((W + ST_TILE - 1) / ST_TILE, (H + ST_TILE - 1) / ST_TILE);
-    k_window_stats<<<sg, 256, 0, s>>>(gl, W, H, r, sampling, w.statsL, w.keys);
+    // layouts of the float images and statistics for this geometry
+    const int K = pick_k(D);
+    const int nz = (D + 32 * K - 1) / (32 * K);
+    const int lneed = std::max(0, d_min + nz * 32 * K + 3);          // columns read left of x = 0
+    const int rneed = std::max(0, -d_min) + 48;                      // columns read right of W - 1
+    PrepOut pl{w.Lf, (W + 40 + 3) & ~3, 0, w.lstats, nullptr, 0, 0};
+    const int rcol0 = ((lneed + 3) & ~3) + pos_mod4(d_min + 31 * K + 3);
+    PrepOut pr{w.Rf, (rcol0 + W + rneed + 3) & ~3, rcol0, nullptr, w.ustats, 0, 0};
+    pr.ucol0 = lneed + 4;
+    pr.ustride = pr.ucol0 + W + std::max(0, -d_min) + 48;
+    dim3 sg((W + PT - 1) / PT, (H + PT - 1) / PT);
+    k_prep<<<sg, 256, 0, s>>>(gl, W, H, r, pl, w.keys);
     counted();
-    k_window_stats<<<sg, 256, 0, s>>>(gr, W, H, r, sampling, w.statsR, nullptr);
+    k_prep<<<sg, 256, 0, s>>>(gr, W, H, r, pr, nullptr);
     counted();
     if (ev) cudaEventRecord(ev[2], s);
-    launch_zncc(r, gl, gr, W, H, d_min, D, w.statsL, w.statsR, w.keys, w.keys + (size_t)W * H, cost,
-                cdt, s);
+    CostArgs a{pl.img, pl.stride, pl.col0, pr.img, pr.stride, pr.col0, w.lstats, w.ustats,
+               pr.ustride, pr.ucol0, w.keys, w.keys + (size_t)W * H, cost, cdt, W, H, d_min, D};
+    launch_cost(r, K, a, s);
     if (ev) cudaEventRecord(ev[3], s);
     dim3 fg((W + 127) / 128, H);
     k_finalize<<<fg, 128, 0, s>>>(w.keys, w.keys + (size_t)W * H, W, H, d_min, D, lr_thresh, cost,
@@ -260,7 +276,7 @@ stereo_status check_match_args(const stereo_handle* h, int W, int H, int d_min, 
     if (!h) return STEREO_ERR_INVALID_ARG;
     if (W < 1 || H < 1 || D < 1 || D > STEREO_MAX_DISP || r < 1 || r > STEREO_MAX_WIN_RADIUS)
         return STEREO_ERR_INVALID_ARG;
-    if (d_min < -4096 || d_min > 4096) return STEREO_ERR_INVALID_ARG;
+    if (d_min < -CMAX_DMIN || d_min > CMAX_DMIN) return STEREO_ERR_INVALID_ARG;
     if (cdt < 0 || cdt > 3) return STEREO_ERR_INVALID_ARG;
     if (sampling != STEREO_SAMPLE_FULL) return STEREO_ERR_UNSUPPORTED;
     if (W > h->p.max_width || H > h->p.max_height || D > h->p.num_disp) return STEREO_ERR_TOO_LARGE;
@@ -321,7 +337,7 @@ stereo_status stereo_create(const stereo_params* p, int32_t max_batch, stereo_ha
     h->p = *p;
     h->max_batch = max_batch;
     h->npix_max = (size_t)p->max_width * p->max_height;
-    h->pair_bytes = pair_ws_bytes(h->npix_max, p->num_disp, p->cost_dtype);
+    h->pair_bytes = pair_ws_bytes(h->npix_max, p->num_disp, p->cost_dtype, p->max_width, p->max_height);
     h->ws = nullptr;
     h->dev_err = nullptr;
     h->timing = false;
@@ -385,7 +401,7 @@ stereo_status stereo_stage_match(stereo_handle* h, const uint8_t* left, const ui
     if (!left || !right) return STEREO_ERR_INVALID_ARG;
     if ((cost_dtype == CDT_NONE) != (cost == nullptr)) return STEREO_ERR_INVALID_ARG;
     if (cost && (reinterpret_cast<uintptr_t>(cost) & 15)) return STEREO_ERR_INVALID_ARG;
-    PairWs w = carve(h->ws, (size_t)width * height, num_disp, h->p.cost_dtype);
+    PairWs w = carve(h->ws, (size_t)width * height, num_disp, h->p.cost_dtype, h->p.max_width, h->p.max_height);
     run_match(left, right, width, height, d_min, num_disp, win_radius, sampling, cost_dtype,
               h->p.lr_thresh, w, cost, disp_left, disp_right, disp_sub, nullptr, S(stream));
     return last_error();
@@ -435,7 +451,7 @@ stereo_status stereo_stage_postprocess(stereo_handle* h, const int16_t* in, int3
                                        int16_t* out, void* stream) {
     if (!h || !in || !out || W < 1 || H < 1) return STEREO_ERR_INVALID_ARG;
     if (W > h->p.max_width || H > h->p.max_height) return STEREO_ERR_TOO_LARGE;
-    PairWs w = carve(h->ws, (size_t)W * H, h->p.num_disp, h->p.cost_dtype);
+    PairWs w = carve(h->ws, (size_t)W * H, h->p.num_disp, h->p.cost_dtype, h->p.max_width, h->p.max_height);
     run_postprocess(h->p, in, W, H, w, out, S(stream));
     return last_error();
 }
@@ -451,7 +467,7 @@ stereo_status stereo_stage_refine(stereo_handle* h, const int16_t* o_in, const v
         return STEREO_ERR_INVALID_ARG;
     if (cost_dtype != CDT_NONE && !cost) return STEREO_ERR_INVALID_ARG;
     if (W > h->p.max_width || H > h->p.max_height) return STEREO_ERR_TOO_LARGE;
-    PairWs w = carve(h->ws, (size_t)W * H, h->p.num_disp, h->p.cost_dtype);
+    PairWs w = carve(h->ws, (size_t)W * H, h->p.num_disp, h->p.cost_dtype, h->p.max_width, h->p.max_height);
     run_refine(h->p, o_in, cost, cost_dtype, left, right, W, H, d_min, D, r, h->p.sampling, w,
                d_out, o_out, nullptr, S(stream));
     return last_error();
@@ -495,7 +511,7 @@ stereo_status stereo_match(stereo_handle* h, const stereo_pair* pr, void* stream
     if (pr->channels != 1 && pr->channels != 3) return STEREO_ERR_INVALID_ARG;
     if (pr->pitch < W * pr->channels) return STEREO_ERR_INVALID_ARG;
     cudaStream_t s = S(stream);
-    PairWs w = carve(h->ws, (size_t)W * H, h->p.num_disp, cdt);
+    PairWs w = carve(h->ws, (size_t)W * H, h->p.num_disp, cdt, h->p.max_width, h->p.max_height);
     const uint8_t* gl = pr->left;
     const uint8_t* gr = pr->right;
     dim3 g((W + 127) / 128, H);
