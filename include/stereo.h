@@ -165,6 +165,11 @@ stereo_status stereo_get_stage_times(stereo_handle* h, float* ms, int32_t n);
  * loaded (all handles and streams). */
 unsigned long long stereo_launch_count(void);
 
+/* Process-wide tuning knobs (0 = automatic choice).  "cost_rows": output
+ * rows per work unit of the cost kernel (1..4096).  Returns
+ * STEREO_ERR_INVALID_ARG for an unknown name or value. */
+stereo_status stereo_set_tuning(const char* name, int32_t value);
+
 /* ------------------------------------------------------------------------
  * Stage entry points.  Each runs one step of the path on caller buffers, so
  * every step can be fed its input independently (stage-wise parity).

@@ -18,7 +18,7 @@ __all__ = [
     "stereo_status_str", "stereo_gray", "stereo_stage_match", "stereo_stage_lr",
     "stereo_stage_outlier", "stereo_stage_fill_radial", "stereo_stage_fill_disc",
     "stereo_stage_postprocess", "stereo_stage_refine", "stereo_set_stage_timing",
-    "stereo_get_stage_times", "stereo_launch_count", "STAGE_NAMES",
+    "stereo_get_stage_times", "stereo_launch_count", "STAGE_NAMES", "stereo_set_tuning",
 ]
 
 STAGE_NAMES = ("input", "stats", "cost_wta", "finalize", "postprocess", "refine")
@@ -98,6 +98,7 @@ def lib():
             "stereo_set_stage_timing": (C.c_int, [P, i32]),
             "stereo_get_stage_times": (C.c_int, [P, P, i32]),
             "stereo_launch_count": (C.c_ulonglong, []),
+            "stereo_set_tuning": (C.c_int, [C.c_char_p, i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -338,3 +339,8 @@ def stereo_get_stage_times(handle: Handle) -> dict:
 
 def stereo_launch_count() -> int:
     return int(lib().stereo_launch_count())
+
+
+def stereo_set_tuning(name: str, value: int):
+    """Process-wide tuning knob (see include/stereo.h), 0 = automatic."""
+    _check(lib().stereo_set_tuning(name.encode(), int(value)), "stereo_set_tuning")

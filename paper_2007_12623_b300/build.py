@@ -25,16 +25,36 @@ def needs_build() -> bool:
     return any(os.path.getmtime(s) > t for s in sources())
 
 
+def translation_units():
+    return [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith(".cu")]
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compiles every translation unit (in parallel) and links libstereo.so."""
     if not force and not needs_build():
         return LIB
+    from concurrent.futures import ThreadPoolExecutor
     nvcc = os.environ.get("NVCC", "nvcc")
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-o", tmp, os.path.join(CSRC, "stereo_api.cu")]
+    bdir = os.path.join(ROOT, "_build", "stereo")
+    os.makedirs(bdir, exist_ok=True)
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.check_call(cmd, cwd=CSRC)
+        flags.append("-Xptxas=-v")
+
+    def compile_one(src):
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
+        r = subprocess.run([nvcc, *flags, "-c", "-o", obj, src], cwd=CSRC, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
+        if verbose:
+            sys.stderr.write(r.stderr)
+        return obj
+
+    tus = translation_units()
+    with ThreadPoolExecutor(max_workers=min(8, len(tus))) as ex:
+        objs = list(ex.map(compile_one, tus))
+    tmp = LIB + f".{os.getpid()}.tmp"
+    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs], cwd=CSRC)
     os.replace(tmp, LIB)
     return LIB
 

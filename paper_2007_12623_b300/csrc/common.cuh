@@ -57,6 +57,3 @@ __device__ __forceinline__ int floordiv_pos(int a, int b) {
 __device__ __forceinline__ int round_half_up_i(int num, int den) {
     return floordiv_pos(2 * num + den, 2 * den);
 }
-
-__constant__ int c_dir8[8][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1},
-                                 {1, 1}, {1, -1}, {-1, 1}, {-1, -1}};

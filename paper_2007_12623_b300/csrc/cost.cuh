@@ -10,93 +10,6 @@
 constexpr int CMARGIN = 1024;      // workspace columns reserved on each side
 constexpr int CMAX_DMIN = 512;     // |d_min| supported by the fused kernel
 
-struct PrepOut {
-    float* img;        // float copy of the image, row stride `stride` floats,
-    int stride;        // image column x at row offset col0 + x; the columns
-    int col0;          // outside [col0, col0 + W) are zero
-    float2* lstats;    // left: {S, 1/sqrt(B)} per pixel (row stride W), or null
-    float4* ustats;    // right: {S_hi, S_lo, 1/sqrt(B), valid}, row stride
-    int ustride;       // ustride, pixel u at ucol0 + u; entries outside the
-    int ucol0;         // image are {0, 0, 0, 0}
-};
-
-// Window sums of one image (FULL sampling): S = sum I, B = N sum I^2 - S^2
-// (exact in uint32 arithmetic, 0 <= B < 2^32).  One block computes a 32x32
-// tile with separable sums in shared memory and writes the float image and
-// the statistics; blocks of the first tile column also zero the padding
-// columns.  Also clears the winner-take-all key maps when `key_clear` is
-// given (2 W H words).
-constexpr int PT = 32;
-constexpr int PMAXR = 7;
-constexpr int PSPAN = PT + 2 * PMAXR;
-
-__global__ void __launch_bounds__(256) k_prep(const uint8_t* __restrict__ img, int W, int H, int r,
-                                              PrepOut out, uint32_t* __restrict__ key_clear) {
-    __shared__ uint16_t t[PSPAN][PSPAN + 1];
-    __shared__ uint32_t rs[PSPAN][PT + 1];
-    __shared__ uint32_t rss[PSPAN][PT + 1];
-    const int x0 = blockIdx.x * PT, y0 = blockIdx.y * PT;
-    const int span = PT + 2 * r;
-    const int tid = threadIdx.x;
-    for (int i = tid; i < span * span; i += 256) {
-        const int ly = i / span, lx = i % span;
-        const int gx = x0 - r + lx, gy = y0 - r + ly;
-        t[ly][lx] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? img[(size_t)gy * W + gx] : 0;
-    }
-    __syncthreads();
-    for (int i = tid; i < span * PT; i += 256) {
-        const int ly = i / PT, lx = i % PT;
-        uint32_t s = 0, ss = 0;
-        for (int k = 0; k <= 2 * r; ++k) {
-            const uint32_t v = t[ly][lx + k];
-            s += v;
-            ss += v * v;
-        }
-        rs[ly][lx] = s;
-        rss[ly][lx] = ss;
-    }
-    __syncthreads();
-    const uint32_t N = (uint32_t)((2 * r + 1) * (2 * r + 1));
-    for (int i = tid; i < PT * PT; i += 256) {
-        const int ly = i / PT, lx = i % PT;
-        const int gx = x0 + lx, gy = y0 + ly;
-        if (gx >= W || gy >= H) continue;
-        const size_t gi = (size_t)gy * W + gx;
-        if (key_clear) { key_clear[gi] = 0u; key_clear[(size_t)W * H + gi] = 0u; }
-        out.img[(size_t)gy * out.stride + out.col0 + gx] = (float)t[ly + r][lx + r];
-        uint32_t s = 0, B = 0;
-        const bool interior = gx >= r && gx < W - r && gy >= r && gy < H - r;
-        if (interior) {
-            uint32_t ss = 0;
-            for (int k = 0; k <= 2 * r; ++k) { s += rs[ly + k][lx]; ss += rss[ly + k][lx]; }
-            B = N * ss - s * s;
-        }
-        const float is = B ? (float)(1.0 / sqrt((double)B)) : 0.f;
-        if (out.lstats) out.lstats[gi] = make_float2((float)s, is);
-        if (out.ustats)
-            out.ustats[(size_t)gy * out.ustride + out.ucol0 + gx] =
-                make_float4((float)(s & ~0xffu), (float)(s & 0xffu), is, interior ? 1.f : 0.f);
-    }
-    if (blockIdx.x == 0) {
-        const int npad = out.stride - W;                      // image padding columns
-        for (int i = tid; i < PT * npad; i += 256) {
-            const int gy = y0 + i / npad, m = i % npad;
-            if (gy >= H) break;
-            const int col = m < out.col0 ? m : W + m;
-            out.img[(size_t)gy * out.stride + col] = 0.f;
-        }
-        if (out.ustats) {
-            const int upad = out.ustride - W;
-            for (int i = tid; i < PT * upad; i += 256) {
-                const int gy = y0 + i / upad, m = i % upad;
-                if (gy >= H) break;
-                const int col = m < out.ucol0 ? m : W + m;
-                out.ustats[(size_t)gy * out.ustride + col] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        }
-    }
-}
-
 // ------------------------------------------------------- fused cost kernel
 //
 // One warp = one work unit: TW output columns [x0, x0+TW) (TW a multiple of
@@ -161,24 +74,39 @@ struct CostArgs {
     void* cost;
     int cdt;
     int W, H, d_min, D;
+    int rows;                                     // output rows per work unit
 };
 
-template <int R, int K, int TH, bool EDGE>
+// Statistics of right pixel i of a staged row (stored at float4 slot
+// i + i/8): window-sum split, 1/sqrt(B), and the key offset / cost value that
+// mark a candidate whose right window leaves the image as invalid.
+__device__ __forceinline__ void load_slot(const float4* U, int i, float& h, float& l, float& is,
+                                          float& ko, float& cf) {
+    const float4 q = U[i + (i >> 3)];
+    h = q.x;
+    l = q.y;
+    is = q.z;
+    const bool ok = q.w != 0.f;
+    ko = ok ? KEY_T_OFFSET : KEY_T_INVALID;
+    cf = ok ? 1.0f : __int_as_float(0x7fc00000);
+}
+
+template <int R, int K, int CDT, bool PARTIAL>
 __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0, int y0, int chunk) {
     typedef CostGeom<R> G;
     typedef CostSmem<R, K> S;
     constexpr int TW = G::TW, NC = G::NC, NCH = G::NCH, RING = G::RING;
     constexpr int LW = S::LW, RWc = S::RWc, NU4 = S::NU4, NUP = S::NUP;
-    float* sImg = smem;                                // [RING][LW + RWc]
-    float4* sU = reinterpret_cast<float4*>(smem + S::IMG);            // [2][NU4]
+    float* sImg = smem;                                               // [RING][LW + RWc]
+    float4* sU = reinterpret_cast<float4*>(smem + S::IMG);            // [2][NUP]
     float2* sLs = reinterpret_cast<float2*>(smem + S::IMG + S::US);   // [2][TW]
     uint32_t* sExit = reinterpret_cast<uint32_t*>(smem + S::IMG + S::US + S::LS);
 
     const int lane = threadIdx.x & 31;
     const int W = a.W, H = a.H;
     const int dc0 = a.d_min + chunk * 32 * K;
-    const int nsteps = min(TW, W - R - x0);
-    const int nrows = min(TH, H - R - y0);
+    const int nsteps = PARTIAL ? min(TW, W - R - x0) : TW;
+    const int nrows = min(a.rows, H - R - y0);
     // image column of staged right column 0 (16-byte aligned inside Rf rows);
     // lane l's first value, column x0-R-dc0-K*l-3, sits at index K*(31-l)
     const int rstart = x0 - R - dc0 - 31 * K - 3;
@@ -200,6 +128,7 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
         for (int i = lane; i < TW; i += 32) cp_async8(ld + i, lsrc + min(i, W - 1 - x0));
     };
 
+    // the first 2R+1 rows and the first statistics row
     for (int gy = y0 - R; gy <= y0 + R; ++gy) stage_img_row(gy);
     stage_stats_row(y0, 0);
     cp_async_commit();
@@ -208,15 +137,15 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
 
     const float Nf = (float)((2 * R + 1) * (2 * R + 1));
     const int idx0 = dc0 - a.d_min + K * lane;         // candidate index of k = 0
-    uint32_t idxc[K];
+    uint32_t idxc[K], mulk[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) idxc[k] = 255u - (uint32_t)(idx0 + k);
-    bool dval[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) dval[k] = (idx0 + k) < a.D;
+    for (int k = 0; k < K; ++k) {
+        idxc[k] = 255u - (uint32_t)(idx0 + k);
+        mulk[k] = (idx0 + k) < a.D ? 256u : 0u;        // a disparity beyond D: key < 256
+    }
     const int cstride = cost_stride(a.D);
-    const int esize = a.cdt == CDT_F32 ? 4 : 2;
-    const int lbase = K * (31 - lane);                 // this lane's first staged right column
+    constexpr int ESZ = CDT == CDT_F32 ? 4 : 2;
+    const int lbase = K * (31 - lane);
 
     float V[NC][K];
 #pragma unroll
@@ -224,6 +153,7 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
 #pragma unroll
         for (int k = 0; k < K; ++k) V[c][k] = 0.f;
 
+    // adds (SUB: subtracts) L(c, gy) * R(c - d, gy) to every vertical sum
     auto accumulate = [&](int gy, auto sub_tag) {
         constexpr bool SUB = decltype(sub_tag)::value;
         const float* row = sImg + ((gy - (y0 - R)) % RING) * (LW + RWc);
@@ -260,148 +190,152 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
         }
     };
 
-    for (int gy = y0 - R; gy <= y0 + R; ++gy) accumulate(gy, std::false_type());
-
-    for (int row = 0; row < nrows; ++row) {
-        const int y = y0 + row;
-        const int buf = row & 1;
-        if (row > 0) {
-            accumulate(y + R, std::false_type());
-            accumulate(y - R - 1, std::true_type());
-        }
+    // v < 0: prologue rows; v >= 0: output row y0 + v.  Row y0+v+R enters
+    // the vertical sums, row y0+v-R-1 leaves them.
+    for (int v = -2 * R; v < nrows; ++v) {
+        const int y = y0 + v;
+        accumulate(y + R, std::false_type());
+        if (v > 0) accumulate(y - R - 1, std::true_type());
+        if (v < 0) continue;
         __syncwarp();
-        // prefetch: image row y+R+1 into the slot just freed, statistics of y+1
-        if (row + 1 < nrows) {
+        const int buf = v & 1;
+        if (v + 1 < nrows) {           // prefetch into the slot just freed
             stage_img_row(y + R + 1);
             stage_stats_row(y + 1, buf ^ 1);
         }
         cp_async_commit();
 
         const float4* U = sU + buf * NUP;
-        auto uat = [&](int i) { return U[i + (i >> 3)]; };
         const float2* Ls = sLs + buf * TW;
         // slot k at step j holds right pixel u = x0 + j - dc0 - K*lane - k,
-        // i.e. sU index j - K*lane - k + 32K - 1; ring register index (j-k) mod K
-        float uh[K], ul[K], ui[K], uf[K];
-        uint32_t acc[K];
+        // statistics index j - K*lane - k + 32K - 1, register index (j-k) mod K
+        float uh[K], ul[K], ui[K], ko[K], cf[K];
 #pragma unroll
         for (int k = 1; k < K; ++k) {
-            const float4 v = uat(32 * K - 1 - K * lane - k);
-            const int s = (0 - k + K) % K;
-            uh[s] = v.x; ul[s] = v.y; ui[s] = v.z; uf[s] = v.w;
+            const int s = (K - k) % K;
+            load_slot(U, 32 * K - 1 - K * lane - k, uh[s], ul[s], ui[s], ko[s], cf[s]);
         }
+        uint32_t acc[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] = 0u;
         uint32_t myLeft = 0u;
         float Hs[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            float s = 0.f;
+            float t = 0.f;
 #pragma unroll
-            for (int c = 0; c <= 2 * R; ++c) s += V[c][k];
-            Hs[k] = s;
+            for (int c = 0; c <= 2 * R; ++c) t += V[c][k];
+            Hs[k] = t;
         }
-        char* crow = reinterpret_cast<char*>(a.cost) + (((size_t)y * W + x0) * cstride + idx0) * esize;
+        char* crow = reinterpret_cast<char*>(a.cost) + (((size_t)y * W + x0) * cstride + idx0) * ESZ;
+        const bool do_store = CDT != CDT_NONE && idx0 < cstride;
 #pragma unroll
         for (int j = 0; j < TW; ++j) {
             if (j > 0) {
 #pragma unroll
                 for (int k = 0; k < K; ++k) Hs[k] += V[j + 2 * R][k] - V[j - 1][k];
             }
-            if (j < nsteps) {
-                {
-                    const float4 v = uat(j + 32 * K - 1 - K * lane);
-                    const int s = j % K;
-                    uh[s] = v.x; ul[s] = v.y; ui[s] = v.z; uf[s] = v.w;
-                }
-                const float2 sl = Ls[j];
-                uint32_t best = 0u;
-                float cv[K];
+            if (PARTIAL && j >= nsteps) continue;
+            load_slot(U, j + 32 * K - 1 - K * lane, uh[j % K], ul[j % K], ui[j % K], ko[j % K], cf[j % K]);
+            const float2 sl = Ls[j];
+            uint32_t best = 0u;
+            float cv[K];
 #pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const int s = (j - k + 4 * K) % K;
-                    const float t1 = sl.x * uh[s];                       // exact
-                    const float num = fmaf(-sl.x, ul[s], fmaf(Nf, Hs[k], -t1));
-                    const float av = num * sl.y;
-                    const float t = fmaf(av, ui[s], KEY_T_OFFSET);
-                    uint32_t key = make_key(t, idxc[k]);
-                    float c = fmaf(-av, ui[s], 1.0f);
-                    if (EDGE) {
-                        const bool ok = dval[k] && uf[s] != 0.f;
-                        key = ok ? key : 0u;
-                        c = ok ? c : __int_as_float(0x7fc00000);
-                    }
-                    cv[k] = c;
-                    best = max(best, key);
-                    acc[s] = max(acc[s], key);
-                }
-                if (a.cdt != CDT_NONE && idx0 < cstride) {
-                    if (a.cdt == CDT_F32) {
-                        float* cp = reinterpret_cast<float*>(crow);
-                        if (K == 4) *reinterpret_cast<float4*>(cp) = make_float4(cv[0], cv[1 % K], cv[2 % K], cv[3 % K]);
-                        else if (K == 2) *reinterpret_cast<float2*>(cp) = make_float2(cv[0], cv[1 % K]);
-                        else cp[0] = cv[0];
-                    } else {
-                        uint32_t w[2];
-#pragma unroll
-                        for (int k = 0; k < K && k < 4; k += 2) {
-                            if (a.cdt == CDT_F16) {
-                                __half2 h = __floats2half2_rn(cv[k], cv[(k + 1) % K]);
-                                w[k / 2] = *reinterpret_cast<uint32_t*>(&h);
-                            } else {
-                                __nv_bfloat162 h = __floats2bfloat162_rn(cv[k], cv[(k + 1) % K]);
-                                w[k / 2] = *reinterpret_cast<uint32_t*>(&h);
-                            }
-                        }
-                        if (K == 4) *reinterpret_cast<uint2*>(crow) = make_uint2(w[0], w[1]);
-                        else if (K == 2) *reinterpret_cast<uint32_t*>(crow) = w[0];
-                        else *reinterpret_cast<uint16_t*>(crow) = (uint16_t)(w[0] & 0xffffu);
-                    }
-                }
-                crow += (size_t)cstride * esize;
-                const uint32_t red = __reduce_max_sync(0xffffffffu, best);
-                if (lane == j) myLeft = red;
-                // the oldest slot ((j+1) mod K) moves on to the next lane
-                const int so = (j + 1) % K;
-                const uint32_t in = __shfl_sync(0xffffffffu, acc[so], (lane + 31) & 31);
-                acc[so] = lane == 0 ? 0u : in;
-                if (lane == 0) sExit[j] = in;
+            for (int k = 0; k < K; ++k) {
+                const int s = (j - k + 4 * K) % K;
+                const float t1 = sl.x * uh[s];                             // exact
+                const float num = fmaf(-sl.x, ul[s], fmaf(Nf, Hs[k], -t1));
+                const float av = num * sl.y;
+                const float t = fmaf(av, ui[s], ko[s]);
+                const uint32_t key = __float_as_uint(t) * mulk[k] + idxc[k];
+                cv[k] = fmaf(-av, ui[s], cf[s]);
+                best = max(best, key);
+                acc[s] = max(acc[s], key);
             }
+            if (CDT != CDT_NONE && do_store) {
+                if (CDT == CDT_F32) {
+                    float* cp = reinterpret_cast<float*>(crow);
+                    if (K == 4) *reinterpret_cast<float4*>(cp) = make_float4(cv[0], cv[1 % K], cv[2 % K], cv[3 % K]);
+                    else if (K == 2) *reinterpret_cast<float2*>(cp) = make_float2(cv[0], cv[1 % K]);
+                    else cp[0] = cv[0];
+                } else {
+                    uint32_t w[2];
+#pragma unroll
+                    for (int k = 0; k < K && k < 4; k += 2) {
+                        if (CDT == CDT_F16) {
+                            __half2 hh = __floats2half2_rn(cv[k], cv[(k + 1) % K]);
+                            w[k / 2] = *reinterpret_cast<uint32_t*>(&hh);
+                        } else {
+                            __nv_bfloat162 hh = __floats2bfloat162_rn(cv[k], cv[(k + 1) % K]);
+                            w[k / 2] = *reinterpret_cast<uint32_t*>(&hh);
+                        }
+                    }
+                    if (K == 4) *reinterpret_cast<uint2*>(crow) = make_uint2(w[0], w[1]);
+                    else if (K == 2) *reinterpret_cast<uint32_t*>(crow) = w[0];
+                    else *reinterpret_cast<uint16_t*>(crow) = (uint16_t)(w[0] & 0xffffu);
+                }
+            }
+            crow += (size_t)cstride * ESZ;
+            const uint32_t red = __reduce_max_sync(0xffffffffu, best);
+            if (lane == j) myLeft = red;
+            // the oldest slot (register (j+1) mod K) moves on to the next lane
+            const int so = (j + 1) % K;
+            const uint32_t in = __shfl_sync(0xffffffffu, acc[so], (lane + 31) & 31);
+            acc[so] = lane == 0 ? 0u : in;
+            if (lane == 0) sExit[j] = in;
         }
         __syncwarp();
         if (lane < nsteps) {
             atomicMax(a.keyL + (size_t)y * W + x0 + lane, myLeft);
             const int u = x0 + lane - dc0 - 32 * K + 1;
-            const uint32_t v = sExit[lane];
-            if (u >= 0 && u < W && v) atomicMax(a.keyR + (size_t)y * W + u, v);
+            const uint32_t e = sExit[lane];
+            if (u >= 0 && u < W && e) atomicMax(a.keyR + (size_t)y * W + u, e);
         }
         // in-flight slots: slot k holds u = x0 + nsteps - dc0 - K*lane - k,
         // register index (nsteps - k) mod K
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int u = x0 + nsteps - dc0 - K * lane - k;
-            const uint32_t v = acc[(nsteps - k + 4 * K) % K];
-            if (v && u >= 0 && u < W) atomicMax(a.keyR + (size_t)y * W + u, v);
+            // (select instead of a dynamic register index, which would put
+            // acc in local memory)
+            uint32_t e = 0u;
+            const int si = ((PARTIAL ? nsteps : TW) - k + 4 * K) % K;
+#pragma unroll
+            for (int q = 0; q < K; ++q) e = (q == si) ? acc[q] : e;
+            if (e && u >= 0 && u < W) atomicMax(a.keyR + (size_t)y * W + u, e);
         }
         cp_async_wait_all();
         __syncwarp();
     }
 }
 
-template <int R, int K, int TH>
-__global__ void __launch_bounds__(32) k_cost_wta(CostArgs a) {
+// Work units: blockIdx.x = run of TW columns, blockIdx.y = band of a.rows
+// rows, blockIdx.z = disparity chunk.  A last run that would stick out of the
+// interior is moved left so that it is full, when the move keeps its first
+// column 16-byte aligned in the staged rows (x0 - R a multiple of 4);
+// otherwise it runs as a partial unit.  The last band is likewise moved up.
+// Overlapping columns/rows are computed twice with identical results, which
+// the max-combining key maps and the plain cost stores absorb.
+template <int R, int K, int CDT, int MINB>
+__global__ void __launch_bounds__(32, MINB) k_cost_wta(CostArgs a) {
     extern __shared__ __align__(16) float smem[];
     typedef CostGeom<R> G;
-    const int x0 = R + blockIdx.x * G::TW;
-    const int y0 = R + blockIdx.y * TH;
-    const int chunk = blockIdx.z;
+    const int inner_w = a.W - 2 * R, inner_h = a.H - 2 * R;
+    int x0 = R + blockIdx.x * G::TW;
+    int y0 = R + blockIdx.y * a.rows;
     if (x0 >= a.W - R || y0 >= a.H - R) return;
-    // a unit is an edge unit when some candidate it visits is invalid: a right
-    // pixel outside [R, W-R), or a disparity index beyond D
-    const int dc0 = a.d_min + chunk * 32 * K;
-    const int xl = min(x0 + G::TW, a.W - R) - 1;
-    const bool edge = (x0 - (dc0 + 32 * K - 1) < R) || (xl - dc0 >= a.W - R) ||
-                      (chunk * 32 * K + 32 * K > a.D);
-    if (edge) cost_unit<R, K, TH, true>(a, smem, x0, y0, chunk);
-    else cost_unit<R, K, TH, false>(a, smem, x0, y0, chunk);
+    bool partial = false;
+    if (x0 + G::TW > a.W - R) {
+        const int shifted = a.W - R - G::TW;
+        if (shifted >= R && ((shifted - R) & 3) == 0) x0 = shifted;
+        else partial = true;
+    }
+    if (inner_h >= a.rows) y0 = min(y0, a.H - R - a.rows);
+    if (partial) cost_unit<R, K, CDT, true>(a, smem, x0, y0, blockIdx.z);
+    else cost_unit<R, K, CDT, false>(a, smem, x0, y0, blockIdx.z);
 }
+
+// Host-side launch for one window radius, explicitly instantiated per radius
+// in cost_r<R>.cu so that the radii compile in parallel.
+template <int R>
+void launch_cost_radius(int K, int cdt, CostArgs a, int rows_override, cudaStream_t s);

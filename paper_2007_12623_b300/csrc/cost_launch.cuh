@@ -1,0 +1,61 @@
+// cost_launch.cuh -- host-side launch of the fused cost kernel for one window
+// radius (included by the per-radius translation units cost_r<R>.cu).
+#pragma once
+#include <algorithm>
+#include "cost.cuh"
+
+// Work-unit height: with `cap` units resident at once the kernel takes
+// ceil(units / cap) waves of units costing about (rows + 1.1) row times (the
+// 2R+1 prologue rows cost about one full row); pick the height in [8, 64]
+// that minimises that estimate.
+inline int cost_choose_rows(int units_x, int nz, int rows_total, int cap) {
+    int best = 16;
+    double best_t = 1e30;
+    for (int th = 8; th <= 64; ++th) {
+        const long units = (long)units_x * nz * ((rows_total + th - 1) / th);
+        const long waves = (units + cap - 1) / cap;
+        const double t = (double)waves * (th + 1.1);
+        if (t < best_t - 1e-9) { best_t = t; best = th; }
+    }
+    return best;
+}
+
+template <int K> struct CostMinBlocks { static constexpr int value = K == 4 ? 8 : (K == 2 ? 12 : 16); };
+
+template <int R, int K, int CDT>
+void launch_cost_rkc(CostArgs a, int rows_override, cudaStream_t s) {
+    typedef CostGeom<R> G;
+    typedef CostSmem<R, K> Sm;
+    constexpr int MINB = CostMinBlocks<K>::value;
+    const int nx = (a.W - 2 * R + G::TW - 1) / G::TW;
+    const int nz = (a.D + 32 * K - 1) / (32 * K);
+    if (nx <= 0 || a.H - 2 * R <= 0) return;
+    static int cap = 0;
+    if (cap == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cost_wta<R, K, CDT, MINB>, 32, Sm::BYTES);
+        cap = std::max(1, sms * std::max(1, per_sm));
+    }
+    a.rows = rows_override > 0 ? rows_override : cost_choose_rows(nx, nz, a.H - 2 * R, cap);
+    const int ny = (a.H - 2 * R + a.rows - 1) / a.rows;
+    k_cost_wta<R, K, CDT, MINB><<<dim3(nx, ny, nz), 32, Sm::BYTES, s>>>(a);
+}
+
+template <int R, int K>
+void launch_cost_rk(int cdt, const CostArgs& a, int rows_override, cudaStream_t s) {
+    switch (cdt) {
+        case CDT_F32: launch_cost_rkc<R, K, CDT_F32>(a, rows_override, s); break;
+        case CDT_F16: launch_cost_rkc<R, K, CDT_F16>(a, rows_override, s); break;
+        case CDT_BF16: launch_cost_rkc<R, K, CDT_BF16>(a, rows_override, s); break;
+        default: launch_cost_rkc<R, K, CDT_NONE>(a, rows_override, s); break;
+    }
+}
+
+template <int R>
+void launch_cost_radius(int K, int cdt, CostArgs a, int rows_override, cudaStream_t s) {
+    if (K == 4) launch_cost_rk<R, 4>(cdt, a, rows_override, s);
+    else if (K == 2) launch_cost_rk<R, 2>(cdt, a, rows_override, s);
+    else launch_cost_rk<R, 1>(cdt, a, rows_override, s);
+}

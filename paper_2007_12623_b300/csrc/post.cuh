@@ -5,6 +5,10 @@
 #pragma once
 #include "common.cuh"
 
+// The 8 radial directions of Sec. II-B (axis steps and diagonal steps).
+__constant__ int c_dir8[8][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1},
+                                 {1, 1}, {1, -1}, {-1, 1}, {-1, -1}};
+
 // A valid pixel is kept when, along at least one of its 8 radial directions,
 // the next `radius` pixels are inside the image, valid, and neighbouring
 // disparities differ by less than `thresh`.

@@ -1,0 +1,92 @@
+// prep.cuh -- per-image preparation for the fused cost kernel: float copy of
+// the image and exact window statistics (Sec. II-A).
+#pragma once
+#include "common.cuh"
+
+struct PrepOut {
+    float* img;        // float copy of the image, row stride `stride` floats,
+    int stride;        // image column x at row offset col0 + x; the columns
+    int col0;          // outside [col0, col0 + W) are zero
+    float2* lstats;    // left: {S, 1/sqrt(B)} per pixel (row stride W), or null
+    float4* ustats;    // right: {S_hi, S_lo, 1/sqrt(B), valid}, row stride
+    int ustride;       // ustride, pixel u at ucol0 + u; entries outside the
+    int ucol0;         // image are {0, 0, 0, 0}
+};
+
+// Window sums of one image (FULL sampling): S = sum I, B = N sum I^2 - S^2
+// (exact in uint32 arithmetic, 0 <= B < 2^32).  One block computes a 32x32
+// tile with separable sums in shared memory and writes the float image and
+// the statistics; blocks of the first tile column also zero the padding
+// columns.  Also clears the winner-take-all key maps when `key_clear` is
+// given (2 W H words).
+constexpr int PT = 32;
+constexpr int PMAXR = 7;
+constexpr int PSPAN = PT + 2 * PMAXR;
+
+__global__ void __launch_bounds__(256) k_prep(const uint8_t* __restrict__ img, int W, int H, int r,
+                                              PrepOut out, uint32_t* __restrict__ key_clear) {
+    __shared__ uint16_t t[PSPAN][PSPAN + 1];
+    __shared__ uint32_t rs[PSPAN][PT + 1];
+    __shared__ uint32_t rss[PSPAN][PT + 1];
+    const int x0 = blockIdx.x * PT, y0 = blockIdx.y * PT;
+    const int span = PT + 2 * r;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < span * span; i += 256) {
+        const int ly = i / span, lx = i % span;
+        const int gx = x0 - r + lx, gy = y0 - r + ly;
+        t[ly][lx] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? img[(size_t)gy * W + gx] : 0;
+    }
+    __syncthreads();
+    for (int i = tid; i < span * PT; i += 256) {
+        const int ly = i / PT, lx = i % PT;
+        uint32_t s = 0, ss = 0;
+        for (int k = 0; k <= 2 * r; ++k) {
+            const uint32_t v = t[ly][lx + k];
+            s += v;
+            ss += v * v;
+        }
+        rs[ly][lx] = s;
+        rss[ly][lx] = ss;
+    }
+    __syncthreads();
+    const uint32_t N = (uint32_t)((2 * r + 1) * (2 * r + 1));
+    for (int i = tid; i < PT * PT; i += 256) {
+        const int ly = i / PT, lx = i % PT;
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= W || gy >= H) continue;
+        const size_t gi = (size_t)gy * W + gx;
+        if (key_clear) { key_clear[gi] = 0u; key_clear[(size_t)W * H + gi] = 0u; }
+        out.img[(size_t)gy * out.stride + out.col0 + gx] = (float)t[ly + r][lx + r];
+        uint32_t s = 0, B = 0;
+        const bool interior = gx >= r && gx < W - r && gy >= r && gy < H - r;
+        if (interior) {
+            uint32_t ss = 0;
+            for (int k = 0; k <= 2 * r; ++k) { s += rs[ly + k][lx]; ss += rss[ly + k][lx]; }
+            B = N * ss - s * s;
+        }
+        const float is = B ? (float)(1.0 / sqrt((double)B)) : 0.f;
+        if (out.lstats) out.lstats[gi] = make_float2((float)s, is);
+        if (out.ustats)
+            out.ustats[(size_t)gy * out.ustride + out.ucol0 + gx] =
+                make_float4((float)(s & ~0xffu), (float)(s & 0xffu), is, interior ? 1.f : 0.f);
+    }
+    if (blockIdx.x == 0) {
+        const int npad = out.stride - W;                      // image padding columns
+        for (int i = tid; i < PT * npad; i += 256) {
+            const int gy = y0 + i / npad, m = i % npad;
+            if (gy >= H) break;
+            const int col = m < out.col0 ? m : W + m;
+            out.img[(size_t)gy * out.stride + col] = 0.f;
+        }
+        if (out.ustats) {
+            const int upad = out.ustride - W;
+            for (int i = tid; i < PT * upad; i += 256) {
+                const int gy = y0 + i / upad, m = i % upad;
+                if (gy >= H) break;
+                const int col = m < out.ucol0 ? m : W + m;
+                out.ustats[(size_t)gy * out.ustride + col] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    }
+}
+

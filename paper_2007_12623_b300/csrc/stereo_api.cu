@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "match.cuh"
 #include "cost.cuh"
+#include "prep.cuh"
 #include "post.cuh"
 #include "refine.cuh"
 
@@ -22,6 +23,9 @@ constexpr int kTH = 16;   // rows per cost work unit
 // Number of kernels this library has enqueued (all handles, all streams).
 std::atomic<unsigned long long> g_launches{0};
 inline void counted(int n = 1) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+// Tuning knobs (0 = automatic), set through stereo_set_tuning.
+int g_cost_rows = 0;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -139,36 +143,18 @@ stereo_status last_error() {
 int pick_k(int D) { return D <= 32 ? 1 : (D <= 64 ? 2 : 4); }
 int pos_mod4(int v) { return ((v % 4) + 4) % 4; }
 
-template <int R, int K>
-void launch_cost_rk(const CostArgs& a, cudaStream_t s) {
-    typedef CostGeom<R> G;
-    typedef CostSmem<R, K> Sm;
-    const int nx = (a.W - 2 * R + G::TW - 1) / G::TW;
-    const int ny = (a.H - 2 * R + kTH - 1) / kTH;
-    const int nz = (a.D + 32 * K - 1) / (32 * K);
-    if (nx <= 0 || ny <= 0) return;
-    k_cost_wta<R, K, kTH><<<dim3(nx, ny, nz), 32, Sm::BYTES, s>>>(a);
-    counted();
-}
-
-template <int R>
-void launch_cost_r(int K, const CostArgs& a, cudaStream_t s) {
-    if (K == 4) launch_cost_rk<R, 4>(a, s);
-    else if (K == 2) launch_cost_rk<R, 2>(a, s);
-    else launch_cost_rk<R, 1>(a, s);
-}
-
-void launch_cost(int r, int K, const CostArgs& a, cudaStream_t s) {
+void launch_cost(int r, int K, int cdt, const CostArgs& a, int rows, cudaStream_t s) {
     switch (r) {
-        case 1: launch_cost_r<1>(K, a, s); break;
-        case 2: launch_cost_r<2>(K, a, s); break;
-        case 3: launch_cost_r<3>(K, a, s); break;
-        case 4: launch_cost_r<4>(K, a, s); break;
-        case 5: launch_cost_r<5>(K, a, s); break;
-        case 6: launch_cost_r<6>(K, a, s); break;
-        case 7: launch_cost_r<7>(K, a, s); break;
-        default: break;
+        case 1: launch_cost_radius<1>(K, cdt, a, rows, s); break;
+        case 2: launch_cost_radius<2>(K, cdt, a, rows, s); break;
+        case 3: launch_cost_radius<3>(K, cdt, a, rows, s); break;
+        case 4: launch_cost_radius<4>(K, cdt, a, rows, s); break;
+        case 5: launch_cost_radius<5>(K, cdt, a, rows, s); break;
+        case 6: launch_cost_radius<6>(K, cdt, a, rows, s); break;
+        case 7: launch_cost_radius<7>(K, cdt, a, rows, s); break;
+        default: return;
     }
+    counted();
 }
 
 // Stats + fused cost/WTA + finalize for one pair whose gray images are gl/gr.
@@ -193,8 +179,8 @@ void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, in
     counted();
     if (ev) cudaEventRecord(ev[2], s);
     CostArgs a{pl.img, pl.stride, pl.col0, pr.img, pr.stride, pr.col0, w.lstats, w.ustats,
-               pr.ustride, pr.ucol0, w.keys, w.keys + (size_t)W * H, cost, cdt, W, H, d_min, D};
-    launch_cost(r, K, a, s);
+               pr.ustride, pr.ucol0, w.keys, w.keys + (size_t)W * H, cost, cdt, W, H, d_min, D, 0};
+    launch_cost(r, K, cdt, a, g_cost_rows, s);
     if (ev) cudaEventRecord(ev[3], s);
     dim3 fg((W + 127) / 128, H);
     k_finalize<<<fg, 128, 0, s>>>(w.keys, w.keys + (size_t)W * H, W, H, d_min, D, lr_thresh, cost,
@@ -498,6 +484,16 @@ stereo_status stereo_get_stage_times(stereo_handle* h, float* ms, int32_t n) {
 }
 
 unsigned long long stereo_launch_count(void) { return g_launches.load(); }
+
+stereo_status stereo_set_tuning(const char* name, int32_t value) {
+    if (!name) return STEREO_ERR_INVALID_ARG;
+    if (!strcmp(name, "cost_rows")) {
+        if (value < 0 || value > 4096) return STEREO_ERR_INVALID_ARG;
+        g_cost_rows = value;
+        return STEREO_OK;
+    }
+    return STEREO_ERR_INVALID_ARG;
+}
 
 stereo_status stereo_match(stereo_handle* h, const stereo_pair* pr, void* stream) {
     if (!h || !pr || !pr->left || !pr->right) return STEREO_ERR_INVALID_ARG;
