@@ -208,8 +208,8 @@ stereo_status stereo_stage_fill_radial(const int16_t* in, int32_t width, int32_t
                                        int32_t radius, int32_t min_dirs, int16_t* out,
                                        void* stream);
 
-/* Sec. II-B second hole-filling method (disc).  min_count < 0 means a
- * quarter of the disc's pixel count, rounded up. */
+/* Sec. II-B second hole-filling method (disc), radius <= 56.  min_count < 0
+ * means a quarter of the disc's pixel count, rounded up. */
 stereo_status stereo_stage_fill_disc(const int16_t* in, int32_t width, int32_t height,
                                      int32_t radius, int32_t min_count, int16_t* out,
                                      void* stream);

@@ -62,19 +62,6 @@ __global__ void k_finalize(const uint32_t* __restrict__ keyL, const uint32_t* __
     if (x >= W) return;
     const size_t i = (size_t)y * W + x;
     const int dl = key_to_disp(keyL[i], d_min);
-    // Pixels whose window leaves the image have no valid candidate; the cost
-    // kernel never visits them, so their cost slices are set to NaN here.
-    if (cdt != CDT_NONE && (x < r || x >= W - r || y < r || y >= H - r)) {
-        const int cs = cost_stride(D);
-        if (cdt == CDT_F32) {
-            float* c = reinterpret_cast<float*>(const_cast<void*>(cost)) + i * cs;
-            for (int k = 0; k < cs; ++k) c[k] = __int_as_float(0x7fc00000);
-        } else {
-            uint16_t* c = reinterpret_cast<uint16_t*>(const_cast<void*>(cost)) + i * cs;
-            const uint16_t nan16 = cdt == CDT_F16 ? 0x7e00 : 0x7fc0;
-            for (int k = 0; k < cs; ++k) c[k] = nan16;
-        }
-    }
     if (disp_left) disp_left[i] = (int16_t)dl;
     if (disp_right) disp_right[i] = (int16_t)key_to_disp(keyR[i], d_min);
     if (disp_lr) {

@@ -64,7 +64,12 @@ __global__ void __launch_bounds__(256) k_prep(const uint8_t* __restrict__ img, i
             for (int k = 0; k <= 2 * r; ++k) { s += rs[ly + k][lx]; ss += rss[ly + k][lx]; }
             B = N * ss - s * s;
         }
-        const float is = B ? (float)(1.0 / sqrt((double)B)) : 0.f;
+        float is = 0.f;
+        if (B) {   // 1/sqrt(B): hardware estimate plus one Newton step (FP64 is slow here)
+            const float fb = (float)B;
+            const float y = rsqrtf(fb);
+            is = y * fmaf(-0.5f * fb * y, y, 1.5f);
+        }
         if (out.lstats) out.lstats[gi] = make_float2((float)s, is);
         if (out.ustats)
             out.ustats[(size_t)gy * out.ustride + out.ucol0 + gx] =
@@ -90,3 +95,31 @@ __global__ void __launch_bounds__(256) k_prep(const uint8_t* __restrict__ img, i
     }
 }
 
+
+// Cost slices of the pixels whose window leaves the image (the cost kernel
+// never visits them) are set to NaN: no candidate is valid there.
+__global__ void k_cost_border_nan(void* __restrict__ cost, int cdt, int W, int H, int r, int cs) {
+    const bool all = W <= 2 * r || H <= 2 * r;             // every pixel is a border pixel
+    const int nb = all ? W * H : 2 * r * W + 2 * r * (H - 2 * r);
+    const long total = (long)nb * cs;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const int b = (int)(e / cs), k = (int)(e % cs);
+        int x, y;
+        if (all) {
+            x = b % W;
+            y = b / W;
+        } else if (b < 2 * r * W) {              // top and bottom rows
+            const int row = b / W;
+            y = row < r ? row : H - 2 * r + row;
+            x = b % W;
+        } else {                                 // left and right columns of the middle rows
+            const int m = b - 2 * r * W;
+            y = r + m / (2 * r);
+            const int c = m % (2 * r);
+            x = c < r ? c : W - 2 * r + c;
+        }
+        const size_t i = ((size_t)y * W + x) * cs + k;
+        if (cdt == CDT_F32) reinterpret_cast<float*>(cost)[i] = __int_as_float(0x7fc00000);
+        else reinterpret_cast<uint16_t*>(cost)[i] = cdt == CDT_F16 ? (uint16_t)0x7e00 : (uint16_t)0x7fc0;
+    }
+}

@@ -1,0 +1,196 @@
+// refine_tiled.cuh -- Sec. II-C on shared-memory tiles: one iteration of the
+// improved Laplacian refinement is two kernels, each a (2 rs + 1)^2 box sum
+// over a 32x32 output tile with an rs-pixel halo (row sums, then column
+// sums, sliding along 8-element segments):
+//   k_refine_box1: dt = mean of valid o (Eq. 1); b = dt - alpha o -
+//                  (1 - alpha) d_prev (Eq. 2); also the valid count
+//   k_refine_box2: d = dt - mean of valid b (Eq. 3); o-update (Eq. 4)
+// The same rules as refine.cuh (kept for radii beyond the tile halo).
+#pragma once
+#include "common.cuh"
+
+constexpr int RT = 32;              // output tile edge
+constexpr int RT_THREADS = 256;
+constexpr int RT_MAX_RS = 24;       // halo limit of the tiled path
+
+__device__ float zncc_direct(const uint8_t* __restrict__ L, const uint8_t* __restrict__ Rm, int W,
+                             int H, int r, int sampling, int x, int y, int d);
+
+// Box sums of `val` (float or int) over the tile: stage (RT+2rs)^2 values,
+// row sums into `rsum` ([RT+2rs][RT]), then column sums for each output.
+// Segment sliding: each thread owns 8 consecutive outputs of a row (column).
+template <typename T>
+__device__ __forceinline__ void box_rows(const T* tin, int sw, int sh, int rs, T* rsum) {
+    // rows: sh rows x RT columns, 4 segments of 8 per row
+    for (int job = threadIdx.x; job < sh * (RT / 8); job += RT_THREADS) {
+        const int y = job / (RT / 8), seg = job % (RT / 8);
+        const T* row = tin + y * sw + seg * 8;       // window of output seg*8 starts here
+        T s = T(0);
+        for (int k = 0; k <= 2 * rs; ++k) s += row[k];
+        T* o = rsum + y * RT + seg * 8;
+        o[0] = s;
+#pragma unroll
+        for (int j = 1; j < 8; ++j) {
+            s += row[j + 2 * rs] - row[j - 1];
+            o[j] = s;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void box_cols(const T* rsum, int rs, T* out /* [RT][RT] */) {
+    for (int job = threadIdx.x; job < RT * (RT / 8); job += RT_THREADS) {
+        const int x = job % RT, seg = job / RT;
+        const T* col = rsum + seg * 8 * RT + x;
+        T s = T(0);
+        for (int k = 0; k <= 2 * rs; ++k) s += col[k * RT];
+        out[(seg * 8) * RT + x] = s;
+#pragma unroll
+        for (int j = 1; j < 8; ++j) {
+            s += col[(j + 2 * rs) * RT] - col[(j - 1) * RT];
+            out[(seg * 8 + j) * RT + x] = s;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(RT_THREADS) k_refine_box1(const int16_t* __restrict__ o,
+                                                            const float* __restrict__ dprev, int W,
+                                                            int H, int rs, float alpha,
+                                                            float* __restrict__ dt,
+                                                            float* __restrict__ b,
+                                                            int16_t* __restrict__ cnt_out) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int sw = RT + 2 * rs, sh = RT + 2 * rs;
+    int* vo = reinterpret_cast<int*>(sm);                  // [sh][sw] valid o (0 if invalid)
+    int* vc = vo + sw * sh;                                // [sh][sw] valid flag
+    int* ro = vc + sw * sh;                                // [sh][RT]
+    int* rc = ro + sh * RT;                                // [sh][RT]
+    int* so = rc + sh * RT;                                // [RT][RT]
+    int* sc = so + RT * RT;                                // [RT][RT]
+    const int x0 = blockIdx.x * RT - rs, y0 = blockIdx.y * RT - rs;
+    for (int i = threadIdx.x; i < sw * sh; i += RT_THREADS) {
+        const int gx = x0 + i % sw, gy = y0 + i / sw;
+        int v = ST_INVALID;
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H) v = o[(size_t)gy * W + gx];
+        const bool ok = v != ST_INVALID;
+        vo[i] = ok ? v : 0;
+        vc[i] = ok ? 1 : 0;
+    }
+    __syncthreads();
+    box_rows<int>(vo, sw, sh, rs, ro);
+    box_rows<int>(vc, sw, sh, rs, rc);
+    __syncthreads();
+    box_cols<int>(ro, rs, so);
+    box_cols<int>(rc, rs, sc);
+    __syncthreads();
+    for (int i = threadIdx.x; i < RT * RT; i += RT_THREADS) {
+        const int gx = blockIdx.x * RT + i % RT, gy = blockIdx.y * RT + i / RT;
+        if (gx >= W || gy >= H) continue;
+        const size_t gi = (size_t)gy * W + gx;
+        const int ov = o[gi];
+        if (ov == ST_INVALID) {
+            b[gi] = 0.f;
+            dt[gi] = __int_as_float(0x7fc00000);
+            cnt_out[gi] = 0;
+            continue;
+        }
+        const float m = (float)so[i] / (float)sc[i];          // Eq. (1)
+        dt[gi] = m;
+        b[gi] = m - alpha * (float)ov - (1.f - alpha) * dprev[gi];   // Eq. (2)
+        cnt_out[gi] = (int16_t)sc[i];
+    }
+}
+
+__global__ void __launch_bounds__(RT_THREADS) k_refine_box2(
+    int16_t* __restrict__ o, float* __restrict__ dprev, const float* __restrict__ dt,
+    const float* __restrict__ b, const int16_t* __restrict__ cnt, int W, int H, int rs, float eta,
+    int search, int d_min, int D, const void* __restrict__ cost, int cdt,
+    const uint8_t* __restrict__ L, const uint8_t* __restrict__ Rm, int r, int sampling,
+    float* __restrict__ d_out) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int sw = RT + 2 * rs, sh = RT + 2 * rs;
+    float* vb = reinterpret_cast<float*>(sm);              // [sh][sw]
+    float* rb = vb + sw * sh;                              // [sh][RT]
+    float* sb = rb + sh * RT;                              // [RT][RT]
+    const int x0 = blockIdx.x * RT - rs, y0 = blockIdx.y * RT - rs;
+    for (int i = threadIdx.x; i < sw * sh; i += RT_THREADS) {
+        const int gx = x0 + i % sw, gy = y0 + i / sw;
+        float v = 0.f;
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H) v = b[(size_t)gy * W + gx];  // 0 if invalid
+        vb[i] = v;
+    }
+    __syncthreads();
+    box_rows<float>(vb, sw, sh, rs, rb);
+    __syncthreads();
+    box_cols<float>(rb, rs, sb);
+    __syncthreads();
+    const int cs = cost_stride(D);
+    for (int i = threadIdx.x; i < RT * RT; i += RT_THREADS) {
+        const int gx = blockIdx.x * RT + i % RT, gy = blockIdx.y * RT + i / RT;
+        if (gx >= W || gy >= H) continue;
+        const size_t gi = (size_t)gy * W + gx;
+        const int ov = o[gi];
+        if (ov == ST_INVALID) {
+            if (d_out) d_out[gi] = __int_as_float(0x7fc00000);
+            continue;
+        }
+        const float d = dt[gi] - sb[i] / (float)cnt[gi];      // Eq. (3)
+        dprev[gi] = d;
+        if (d_out) d_out[gi] = d;
+        // Eq. (4)
+        const int lo = max((int)ceilf(d - (float)search), d_min);
+        const int hi = min((int)floorf(d + (float)search), d_min + D - 1);
+        int best = ST_INVALID;
+        float bf = 0.f, bdist = 0.f;
+        const size_t cbase = gi * (size_t)cs;
+        if (cdt != CDT_NONE && search <= 8) {
+            // all candidate costs in flight at once (one memory round trip)
+            float rho[17];
+#pragma unroll
+            for (int j = 0; j < 17; ++j) {
+                const int cand = lo + j;
+                rho[j] = (j <= 2 * search && cand <= hi)
+                             ? 1.f - cost_load(cost, cdt, cbase + (cand - d_min))
+                             : __int_as_float(0x7fc00000);
+            }
+#pragma unroll
+            for (int j = 0; j < 17; ++j) {
+                if (!(rho[j] > 0.f)) continue;   // NaN (invalid / out of range) or non-positive
+                const int cand = lo + j;
+                const float diff = (float)cand - d;
+                const float f = 1.f / rho[j] + eta * diff * diff;
+                const float dist = fabsf(diff);
+                if (best == ST_INVALID || f < bf || (f == bf && dist < bdist)) {
+                    best = cand;
+                    bf = f;
+                    bdist = dist;
+                }
+            }
+        } else {
+            for (int cand = lo; cand <= hi; ++cand) {
+                float rho;
+                if (cdt != CDT_NONE) rho = 1.f - cost_load(cost, cdt, cbase + (cand - d_min));
+                else rho = zncc_direct(L, Rm, W, H, r, sampling, gx, gy, cand);
+                if (!(rho > 0.f)) continue;
+                const float diff = (float)cand - d;
+                const float f = 1.f / rho + eta * diff * diff;
+                const float dist = fabsf(diff);
+                if (best == ST_INVALID || f < bf || (f == bf && dist < bdist)) {
+                    best = cand;
+                    bf = f;
+                    bdist = dist;
+                }
+            }
+        }
+        if (best != ST_INVALID) o[gi] = (int16_t)best;
+    }
+}
+
+inline size_t refine_box1_smem(int rs) {
+    const size_t sw = RT + 2 * rs, sh = RT + 2 * rs;
+    return (2 * sw * sh + 2 * sh * RT + 2 * RT * RT) * 4;
+}
+inline size_t refine_box2_smem(int rs) {
+    const size_t sw = RT + 2 * rs, sh = RT + 2 * rs;
+    return (sw * sh + sh * RT + RT * RT) * 4;
+}

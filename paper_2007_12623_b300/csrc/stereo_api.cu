@@ -15,6 +15,8 @@
 #include "prep.cuh"
 #include "post.cuh"
 #include "refine.cuh"
+#include "post_tiled.cuh"
+#include "refine_tiled.cuh"
 
 namespace {
 
@@ -48,6 +50,7 @@ struct PairWs {
     int16_t* o;         // refinement o
     int16_t* t;         // post-processing round buffer
     int16_t* post;      // post-processing output (when the caller gives none)
+    int16_t* cnt;       // refinement: valid count of each box
     float* dfin;        // refined output (when the caller gives none)
     float* dprev;
     float* dt;
@@ -69,7 +72,7 @@ size_t pair_ws_bytes(size_t npix, int D, int cdt, int maxW = 0, int maxH = 0) {
     b += 0;                                       // image-shaped buffers: see carve()
     b += align_up(npix * 8, 256);                 // keys
     b += align_up(npix * (size_t)cost_stride(D) * elem_size(cdt), 256);
-    b += align_up(npix * 2, 256) * 7;             // wta lr p q o t post
+    b += align_up(npix * 2, 256) * 8;             // wta lr p q o t post cnt
     b += align_up(npix * 4, 256) * 7;             // dprev dt b rsC rsO rsB dfin
     return b;
 }
@@ -93,6 +96,7 @@ PairWs carve(uint8_t* base, size_t npix, int D, int cdt, int maxW, int maxH) {
     w.o = reinterpret_cast<int16_t*>(take(npix * 2));
     w.t = reinterpret_cast<int16_t*>(take(npix * 2));
     w.post = reinterpret_cast<int16_t*>(take(npix * 2));
+    w.cnt = reinterpret_cast<int16_t*>(take(npix * 2));
     w.dfin = reinterpret_cast<float*>(take(npix * 4));
     w.dprev = reinterpret_cast<float*>(take(npix * 4));
     w.dt = reinterpret_cast<float*>(take(npix * 4));
@@ -157,6 +161,18 @@ void launch_cost(int r, int K, int cdt, const CostArgs& a, int rows, cudaStream_
     counted();
 }
 
+// Opts the tiled kernels into more than 48 KB of dynamic shared memory.
+void set_smem_attributes() {
+    static bool done = false;
+    if (done) return;
+    done = true;
+    cudaFuncSetAttribute(k_outlier_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_fill_radial_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_fill_disc_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_refine_box1, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_refine_box2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
 // Stats + fused cost/WTA + finalize for one pair whose gray images are gl/gr.
 void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, int D, int r,
                int sampling, int cdt, int lr_thresh, const PairWs& w, void* cost,
@@ -177,6 +193,12 @@ void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, in
     counted();
     k_prep<<<sg, 256, 0, s>>>(gr, W, H, r, pr, nullptr);
     counted();
+    if (cost) {
+        const long nb = (W <= 2 * r || H <= 2 * r) ? (long)W * H : 2L * r * W + 2L * r * (H - 2 * r);
+        const int blocks = (int)std::min<long>(4096, (nb * cost_stride(D) + 255) / 256);
+        k_cost_border_nan<<<std::max(1, blocks), 256, 0, s>>>(cost, cdt, W, H, r, cost_stride(D));
+        counted();
+    }
     if (ev) cudaEventRecord(ev[2], s);
     CostArgs a{pl.img, pl.stride, pl.col0, pr.img, pr.stride, pr.col0, w.lstats, w.ustats,
                pr.ustride, pr.ucol0, w.keys, w.keys + (size_t)W * H, cost, cdt, W, H, d_min, D, 0};
@@ -200,13 +222,23 @@ void run_postprocess(const stereo_params& p, const int16_t* in, int W, int H, co
         cudaMemcpyAsync(out, in, (size_t)W * H * 2, cudaMemcpyDeviceToDevice, s);
         return;
     }
+    dim3 tg((W + PT_W - 1) / PT_W, (H + PT_H - 1) / PT_H);
     for (int t = 0; t < p.outlier_rounds; ++t) {
-        k_outlier<<<g2, b2, 0, s>>>(cur, W, H, p.r0 + t * p.dr, p.outlier_thresh, w.p);
+        const int rad = p.r0 + t * p.dr;
+        if (rad <= PT_MAX_HALO)
+            k_outlier_tiled<<<tg, PT_THREADS, outlier_tile_smem(rad), s>>>(cur, W, H, rad, p.outlier_thresh, w.p);
+        else
+            k_outlier<<<g2, b2, 0, s>>>(cur, W, H, rad, p.outlier_thresh, w.p);
         counted();
-        k_fill_radial<<<g2, b2, 0, s>>>(w.p, W, H, p.fill_radial_r, p.fill_radial_min_dirs, w.q);
+        if (p.fill_radial_r <= PT_MAX_HALO)
+            k_fill_radial_tiled<<<tg, PT_THREADS, radial_tile_smem(p.fill_radial_r), s>>>(
+                w.p, W, H, p.fill_radial_r, p.fill_radial_min_dirs, w.q);
+        else
+            k_fill_radial<<<g2, b2, 0, s>>>(w.p, W, H, p.fill_radial_r, p.fill_radial_min_dirs, w.q);
         counted();
         int16_t* dst = (t == p.outlier_rounds - 1) ? out : w.t;
-        k_fill_disc<<<gd, b2, fd_smem, s>>>(w.q, W, H, p.fill_disc_r, min_count, dst);
+        k_fill_disc_tiled<<<tg, PT_THREADS, disc_tile_smem(p.fill_disc_r), s>>>(w.q, W, H, p.fill_disc_r,
+                                                                               min_count, dst);
         counted();
         cur = dst;
     }
@@ -223,17 +255,29 @@ void run_refine(const stereo_params& p, const int16_t* o_in, const void* cost, i
     const int bx = 128;
     dim3 gr2((W + bx - 1) / bx, H);
     const size_t rsmem = (size_t)((bx + 2 * rs + 1) & ~1) * 2 + (size_t)(bx + 2 * rs) * 4;
+    const bool tiled = rs <= RT_MAX_RS;
+    dim3 rg((W + RT - 1) / RT, (H + RT - 1) / RT);
     for (int k = 0; k < p.smooth_iters; ++k) {
-        k_refine_rows<<<gr2, bx, rsmem, s>>>(w.o, nullptr, W, H, rs, w.rsC, w.rsO, nullptr);
-        counted();
-        k_refine_cols1<<<gr2, bx, 0, s>>>(w.o, w.dprev, w.rsC, w.rsO, W, H, rs, p.alpha, w.dt, w.b);
-        counted();
-        k_refine_rows<<<gr2, bx, rsmem, s>>>(w.o, w.b, W, H, rs, nullptr, nullptr, w.rsB);
-        counted();
-        k_refine_cols2<<<gr2, bx, 0, s>>>(w.o, w.dprev, w.dt, w.rsC, w.rsB, W, H, rs, p.eta,
-                                          p.refine_search, d_min, D, cost, cdt, gl, gr, r, sampling,
-                                          k == p.smooth_iters - 1 ? d_out : nullptr);
-        counted();
+        float* dk = k == p.smooth_iters - 1 ? d_out : nullptr;
+        if (tiled) {
+            k_refine_box1<<<rg, RT_THREADS, refine_box1_smem(rs), s>>>(w.o, w.dprev, W, H, rs, p.alpha,
+                                                                       w.dt, w.b, w.cnt);
+            counted();
+            k_refine_box2<<<rg, RT_THREADS, refine_box2_smem(rs), s>>>(
+                w.o, w.dprev, w.dt, w.b, w.cnt, W, H, rs, p.eta, p.refine_search, d_min, D, cost, cdt, gl,
+                gr, r, sampling, dk);
+            counted();
+        } else {
+            k_refine_rows<<<gr2, bx, rsmem, s>>>(w.o, nullptr, W, H, rs, w.rsC, w.rsO, nullptr);
+            counted();
+            k_refine_cols1<<<gr2, bx, 0, s>>>(w.o, w.dprev, w.rsC, w.rsO, W, H, rs, p.alpha, w.dt, w.b);
+            counted();
+            k_refine_rows<<<gr2, bx, rsmem, s>>>(w.o, w.b, W, H, rs, nullptr, nullptr, w.rsB);
+            counted();
+            k_refine_cols2<<<gr2, bx, 0, s>>>(w.o, w.dprev, w.dt, w.rsC, w.rsB, W, H, rs, p.eta,
+                                              p.refine_search, d_min, D, cost, cdt, gl, gr, r, sampling, dk);
+            counted();
+        }
     }
     if (o_out) cudaMemcpyAsync(o_out, w.o, (size_t)n * 2, cudaMemcpyDeviceToDevice, s);
 }
@@ -250,7 +294,7 @@ stereo_status check_params(const stereo_params* p) {
     if (p->d_min < -4096 || p->d_min > 4096) return STEREO_ERR_INVALID_ARG;
     if (p->lr_thresh < 0 || p->outlier_rounds < 0 || p->r0 < 0 || p->dr < 0) return STEREO_ERR_INVALID_ARG;
     if (p->fill_radial_r < 0 || p->fill_radial_min_dirs < 0) return STEREO_ERR_INVALID_ARG;
-    if (p->fill_disc_r < 0 || p->fill_disc_r > FD_MAXR) return STEREO_ERR_INVALID_ARG;
+    if (p->fill_disc_r < 0 || p->fill_disc_r > PT_MAX_HALO) return STEREO_ERR_INVALID_ARG;
     if (p->smooth_radius < 0 || p->smooth_iters < 0 || p->refine_search < 0) return STEREO_ERR_INVALID_ARG;
     if (!(p->outlier_thresh >= 0.f) || !(p->alpha >= 0.f && p->alpha <= 1.f) || !(p->eta >= 0.f))
         return STEREO_ERR_INVALID_ARG;
@@ -318,6 +362,7 @@ stereo_status stereo_create(const stereo_params* p, int32_t max_batch, stereo_ha
     if (!out || max_batch < 1) return STEREO_ERR_INVALID_ARG;
     stereo_status st = check_params(p);
     if (st != STEREO_OK) return st;
+    set_smem_attributes();
     stereo_handle* h = new (std::nothrow) stereo_handle();
     if (!h) return STEREO_ERR_OOM;
     h->p = *p;
@@ -405,8 +450,13 @@ stereo_status stereo_stage_outlier(const int16_t* in, int32_t W, int32_t H, int3
                                    float thresh, int16_t* out, void* stream) {
     if (!in || !out || in == out || W < 1 || H < 1 || radius < 0 || !(thresh >= 0.f))
         return STEREO_ERR_INVALID_ARG;
-    k_outlier<<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, S(stream)>>>(in, W, H, radius,
-                                                                               thresh, out);
+    set_smem_attributes();
+    if (radius <= PT_MAX_HALO)
+        k_outlier_tiled<<<dim3((W + PT_W - 1) / PT_W, (H + PT_H - 1) / PT_H), PT_THREADS,
+                          outlier_tile_smem(radius), S(stream)>>>(in, W, H, radius, thresh, out);
+    else
+        k_outlier<<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, S(stream)>>>(in, W, H, radius,
+                                                                                   thresh, out);
     counted();
     return last_error();
 }
@@ -415,20 +465,25 @@ stereo_status stereo_stage_fill_radial(const int16_t* in, int32_t W, int32_t H, 
                                        int32_t min_dirs, int16_t* out, void* stream) {
     if (!in || !out || in == out || W < 1 || H < 1 || radius < 0 || min_dirs < 0)
         return STEREO_ERR_INVALID_ARG;
-    k_fill_radial<<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, S(stream)>>>(
-        in, W, H, radius, min_dirs, out);
+    set_smem_attributes();
+    if (radius <= PT_MAX_HALO)
+        k_fill_radial_tiled<<<dim3((W + PT_W - 1) / PT_W, (H + PT_H - 1) / PT_H), PT_THREADS,
+                              radial_tile_smem(radius), S(stream)>>>(in, W, H, radius, min_dirs, out);
+    else
+        k_fill_radial<<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, S(stream)>>>(
+            in, W, H, radius, min_dirs, out);
     counted();
     return last_error();
 }
 
 stereo_status stereo_stage_fill_disc(const int16_t* in, int32_t W, int32_t H, int32_t radius,
                                      int32_t min_count, int16_t* out, void* stream) {
-    if (!in || !out || in == out || W < 1 || H < 1 || radius < 0 || radius > FD_MAXR)
+    if (!in || !out || in == out || W < 1 || H < 1 || radius < 0 || radius > PT_MAX_HALO)
         return STEREO_ERR_INVALID_ARG;
+    set_smem_attributes();
     if (min_count < 0) min_count = (disc_area(radius) + 3) / 4;
-    const size_t smem = (size_t)(FD_TILE + 2 * radius) * (FD_TILE + 2 * radius) * 2;
-    k_fill_disc<<<dim3((W + FD_TILE - 1) / FD_TILE, (H + FD_TILE - 1) / FD_TILE), dim3(32, 8), smem,
-                  S(stream)>>>(in, W, H, radius, min_count, out);
+    k_fill_disc_tiled<<<dim3((W + PT_W - 1) / PT_W, (H + PT_H - 1) / PT_H), PT_THREADS,
+                        disc_tile_smem(radius), S(stream)>>>(in, W, H, radius, min_count, out);
     counted();
     return last_error();
 }
@@ -454,6 +509,7 @@ stereo_status stereo_stage_refine(stereo_handle* h, const int16_t* o_in, const v
     if (cost_dtype != CDT_NONE && !cost) return STEREO_ERR_INVALID_ARG;
     if (W > h->p.max_width || H > h->p.max_height) return STEREO_ERR_TOO_LARGE;
     PairWs w = carve(h->ws, (size_t)W * H, h->p.num_disp, h->p.cost_dtype, h->p.max_width, h->p.max_height);
+    set_smem_attributes();
     run_refine(h->p, o_in, cost, cost_dtype, left, right, W, H, d_min, D, r, h->p.sampling, w,
                d_out, o_out, nullptr, S(stream));
     return last_error();

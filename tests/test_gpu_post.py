@@ -55,7 +55,7 @@ def _random_map(rng, H, W, lo, hi, p_inv):
     return m
 
 
-@pytest.mark.parametrize("radius", [1, 3, 10, 20, 30])
+@pytest.mark.parametrize("radius", [1, 3, 10, 20, 30, 60])
 def test_outlier(dev, radius):
     rng = np.random.default_rng(radius)
     m = _random_map(rng, 70, 90, 0, 60, 0.15)
@@ -66,7 +66,7 @@ def test_outlier(dev, radius):
     assert len(bad) == 0, describe(bad, to_np(out), want)
 
 
-@pytest.mark.parametrize("radius,min_dirs", [(50, 4), (5, 2), (50, 8)])
+@pytest.mark.parametrize("radius,min_dirs", [(50, 4), (5, 2), (50, 8), (70, 4)])
 def test_fill_radial(dev, radius, min_dirs):
     rng = np.random.default_rng(radius + min_dirs)
     m = _random_map(rng, 64, 100, -10, 60, 0.6)
@@ -76,7 +76,7 @@ def test_fill_radial(dev, radius, min_dirs):
     assert np.array_equal(to_np(out), want)
 
 
-@pytest.mark.parametrize("radius", [2, 7, 20, 24])
+@pytest.mark.parametrize("radius", [2, 7, 20, 24, 40])
 def test_fill_disc(dev, radius):
     rng = np.random.default_rng(100 + radius)
     m = _random_map(rng, 75, 83, -5, 50, 0.55)
@@ -159,3 +159,16 @@ def test_refine_identities(dev):
         d, oo = _refine_gpu(dev, o, cost, o.astype(np.uint8), o.astype(np.uint8), p)
         assert np.all(d[o != INV] == 12.0) and np.all(np.isnan(d[o == INV]))
         assert np.array_equal(oo, o)
+
+
+@pytest.mark.parametrize("rs", [15, 30])
+def test_refine_stage_paper_radius(dev, perlin_stages, rs):
+    """Smoothing radius 15 (the paper's) runs the shared-memory tiled path;
+    radius 30 exceeds its halo and runs the plain row/column path."""
+    L, R, p0, o = perlin_stages
+    p = oracle.Params(d_min=0, num_disp=32, win_radius=5, smooth_radius=rs, smooth_iters=5)
+    d_ref, _ = oracle.refine(o["o_post"], cost=o["cost"], p=p)
+    d, _ = _refine_gpu(dev, o["o_post"], o["cost"], L, R, p)
+    rel = _refine_compare(d, d_ref, o["o_post"] != INV)
+    print(f"refine rs={rs}: beyond 1e-4: {100 * np.mean(rel > REFINE_RTOL):.3f}%")
+    assert np.mean(rel > REFINE_RTOL) <= 0.005
