@@ -199,14 +199,17 @@ stereo_status stereo_stage_match(stereo_handle* h, const uint8_t* left, const ui
 stereo_status stereo_stage_lr(const int16_t* disp_left, const int16_t* disp_right, int32_t width,
                               int32_t height, int32_t thresh, int16_t* out, void* stream);
 
-/* Sec. II-B radial outlier removal with the given radius (one pass). */
-stereo_status stereo_stage_outlier(const int16_t* in, int32_t width, int32_t height,
-                                   int32_t radius, float thresh, int16_t* out, void* stream);
+/* Sec. II-B radial outlier removal with the given radius (one pass).  Uses
+ * the handle's workspace (line bitmasks); width/height must fit it. */
+stereo_status stereo_stage_outlier(stereo_handle* h, const int16_t* in, int32_t width,
+                                   int32_t height, int32_t radius, float thresh, int16_t* out,
+                                   void* stream);
 
-/* Sec. II-B first hole-filling method (8 radial directions). */
-stereo_status stereo_stage_fill_radial(const int16_t* in, int32_t width, int32_t height,
-                                       int32_t radius, int32_t min_dirs, int16_t* out,
-                                       void* stream);
+/* Sec. II-B first hole-filling method (8 radial directions).  Uses the
+ * handle's workspace; width/height must fit it. */
+stereo_status stereo_stage_fill_radial(stereo_handle* h, const int16_t* in, int32_t width,
+                                       int32_t height, int32_t radius, int32_t min_dirs,
+                                       int16_t* out, void* stream);
 
 /* Sec. II-B second hole-filling method (disc), radius <= 56.  min_count < 0
  * means a quarter of the disc's pixel count, rounded up. */

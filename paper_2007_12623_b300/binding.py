@@ -90,8 +90,8 @@ def lib():
             "stereo_gray": (C.c_int, [P, i32, i32, i32, P, P]),
             "stereo_stage_match": (C.c_int, [P, P, P, i32, i32, i32, i32, i32, i32, i32, P, P, P, P, P]),
             "stereo_stage_lr": (C.c_int, [P, P, i32, i32, i32, P, P]),
-            "stereo_stage_outlier": (C.c_int, [P, i32, i32, i32, f32, P, P]),
-            "stereo_stage_fill_radial": (C.c_int, [P, i32, i32, i32, i32, P, P]),
+            "stereo_stage_outlier": (C.c_int, [P, P, i32, i32, i32, f32, P, P]),
+            "stereo_stage_fill_radial": (C.c_int, [P, P, i32, i32, i32, i32, P, P]),
             "stereo_stage_fill_disc": (C.c_int, [P, i32, i32, i32, i32, P, P]),
             "stereo_stage_postprocess": (C.c_int, [P, P, i32, i32, P, P]),
             "stereo_stage_refine": (C.c_int, [P, P, P, i32, P, P, i32, i32, i32, i32, i32, P, P, P]),
@@ -283,18 +283,18 @@ def stereo_stage_lr(disp_left, disp_right, thresh, out, stream=None):
                                  thresh, _ptr(out, torch.int16), _stream(stream)), "stereo_stage_lr")
 
 
-def stereo_stage_outlier(inp, radius, thresh, out, stream=None):
+def stereo_stage_outlier(handle: Handle, inp, radius, thresh, out, stream=None):
     import torch
     H, W = inp.shape
-    _check(lib().stereo_stage_outlier(_ptr(inp, torch.int16), W, H, radius, thresh,
+    _check(lib().stereo_stage_outlier(handle.ptr, _ptr(inp, torch.int16), W, H, radius, thresh,
                                       _ptr(out, torch.int16), _stream(stream)),
            "stereo_stage_outlier")
 
 
-def stereo_stage_fill_radial(inp, radius, min_dirs, out, stream=None):
+def stereo_stage_fill_radial(handle: Handle, inp, radius, min_dirs, out, stream=None):
     import torch
     H, W = inp.shape
-    _check(lib().stereo_stage_fill_radial(_ptr(inp, torch.int16), W, H, radius, min_dirs,
+    _check(lib().stereo_stage_fill_radial(handle.ptr, _ptr(inp, torch.int16), W, H, radius, min_dirs,
                                           _ptr(out, torch.int16), _stream(stream)),
            "stereo_stage_fill_radial")
 

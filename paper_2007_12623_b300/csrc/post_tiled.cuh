@@ -9,7 +9,7 @@
 constexpr int PT_W = 32;          // tile width (outputs)
 constexpr int PT_H = 32;          // tile height (outputs)
 constexpr int PT_THREADS = 256;
-constexpr int PT_MAX_HALO = 56;   // (32 + 2*56)^2 * 2 B = 41.5 KB of shared memory
+constexpr int PT_MAX_HALO = 56;   // largest halo of the tiled passes (lines up to 144 px)
 
 __device__ __forceinline__ int16_t map_at(const int16_t* __restrict__ m, int W, int H, int x, int y) {
     return (x >= 0 && x < W && y >= 0 && y < H) ? m[(size_t)y * W + x] : (int16_t)ST_INVALID;
@@ -49,20 +49,76 @@ __device__ __forceinline__ void copy_tile_out(const int16_t* t, int halo, int W,
     }
 }
 
-// Radial outlier removal (Sec. II-B) on a tile; halo = radius.
-//
-// A direction passes when its `radius` steps are all "smooth edges": both
-// ends inside the image and valid, disparities differing by < thresh.  Edges
-// are kept per line family (horizontal, vertical, two diagonals) as prefix
-// counts of non-smooth edges along each line, so each of the 8 directions of
-// a pixel is one subtraction: the +step ray uses edges p .. p+(r-1)step, the
-// -step ray edges p-step .. p-r*step.  Pixels outside the image are staged
-// as invalid, so a ray that leaves the image fails like in the plain rule.
-__device__ __forceinline__ void family_step(int f, int& dx, int& dy) {
-    dx = (f == 1) ? 0 : 1;
-    dy = (f == 0) ? 0 : (f == 3 ? -1 : 1);
+// ---------------------------------------------------------------------------
+// Line bitmasks.  Every ray of the 8 radial directions from a tile pixel runs
+// along one line of four families: 0 rows (step (1,0)), 1 columns (step
+// (0,1)), 2 diagonals (step (1,1)), 3 anti-diagonals (step (1,-1)).  Only
+// the lines through the PT_W x PT_H core are needed: 32 rows, 32 columns,
+// 63 diagonals and 63 anti-diagonals.  Each keeps a bitmask over its
+// positions in the staged window (the x coordinate; y for columns) holding
+// one predicate per pixel, built 32 bits at a time with a warp ballot.  A
+// ray is then a run of bits on one line, tested with a shift and a mask.
+constexpr int MW = 3;                              // 64-bit words per line (<= 192 px)
+constexpr int NCORE_LINES = 2 * PT_W + 2 * (2 * PT_W - 1);   // 190 (square core)
+static_assert(PT_W == PT_H, "line indexing assumes a square core");
+
+__device__ __forceinline__ int fam_offset(int f) {   // first core line of family f
+    return f == 0 ? 0 : (f == 1 ? PT_W : (f == 2 ? 2 * PT_W : 4 * PT_W - 1));
+}
+__device__ __forceinline__ void fam_step(int f, int& dx, int& dy) {
+    dx = f == 1 ? 0 : 1;
+    dy = f == 0 ? 0 : (f == 3 ? -1 : 1);
+}
+// core line and position of staged pixel (x, y) (which lies on a core line)
+__device__ __forceinline__ void fam_line_pos(int f, int x, int y, int halo, int& line, int& pos) {
+    if (f == 0) { line = y - halo; pos = x; }
+    else if (f == 1) { line = x - halo; pos = y; }
+    else if (f == 2) { line = x - y + PT_W - 1; pos = x; }
+    else { line = x + y - 2 * halo; pos = x; }
+}
+// staged pixel at (core line, pos) of family f
+__device__ __forceinline__ void fam_pixel(int f, int line, int pos, int halo, int& x, int& y) {
+    if (f == 0) { x = pos; y = line + halo; }
+    else if (f == 1) { x = line + halo; y = pos; }
+    else if (f == 2) { x = pos; y = pos - (line - PT_W + 1); }
+    else { x = pos; y = line + 2 * halo - pos; }
+}
+// 64 bits of a line starting at bit s (s >= 0)
+__device__ __forceinline__ uint64_t line_bits(const uint64_t* w, int s) {
+    const int i = s >> 6, o = s & 63;
+    const uint64_t lo = w[i], hi = (i + 1 < MW) ? w[i + 1] : 0ull;
+    return o ? (lo >> o) | (hi << (64 - o)) : lo;
+}
+__device__ __forceinline__ uint64_t low_mask(int n) { return n >= 64 ? ~0ull : ((1ull << n) - 1ull); }
+
+// Builds the core lines' bitmasks of pred(f, x, y) over the staged window.
+template <typename Pred>
+__device__ __forceinline__ void build_line_masks(uint64_t* masks, int sw, int halo, Pred pred) {
+    uint32_t* m32 = reinterpret_cast<uint32_t*>(masks);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = PT_THREADS / 32;
+    const int nchunk = (sw + 31) / 32;
+    for (int job = warp; job < NCORE_LINES * 2 * MW; job += nwarps) {
+        const int gline = job / (2 * MW), c = job % (2 * MW);
+        const int f = gline < PT_W ? 0 : (gline < 2 * PT_W ? 1 : (gline < 4 * PT_W - 1 ? 2 : 3));
+        const int line = gline - fam_offset(f);
+        bool bit = false;
+        if (c < nchunk) {
+            const int pos = 32 * c + lane;
+            int x, y;
+            fam_pixel(f, line, pos, halo, x, y);
+            if (pos < sw && x >= 0 && x < sw && y >= 0 && y < sw) bit = pred(f, x, y);
+        }
+        const uint32_t word = __ballot_sync(0xffffffffu, bit);
+        if (lane == 0) m32[gline * 2 * MW + c] = word;
+    }
 }
 
+// Radial outlier removal (Sec. II-B) on a tile; halo = radius (<= 63).  The
+// predicate is a smooth edge: the pixel and its neighbour one step along the
+// family are both valid and differ by < thresh.  Direction +step from p uses
+// the edges at positions pos .. pos+r-1, direction -step those at pos-r ..
+// pos-1.  Out-of-image pixels are staged invalid, so a ray that leaves the
+// image fails, as in the plain rule.
 __global__ void __launch_bounds__(PT_THREADS) k_outlier_tiled(const int16_t* __restrict__ in, int W,
                                                               int H, int radius, float thresh,
                                                               int16_t* __restrict__ out) {
@@ -70,47 +126,19 @@ __global__ void __launch_bounds__(PT_THREADS) k_outlier_tiled(const int16_t* __r
     __shared__ int flag;
     const int halo = radius;
     const int sw = PT_W + 2 * halo;
-    int16_t* t = reinterpret_cast<int16_t*>(sm);
-    uint8_t* Z = sm + (((size_t)sw * sw * 2 + 15) & ~(size_t)15);   // [4][sw][sw]
+    uint64_t* masks = reinterpret_cast<uint64_t*>(sm);
+    int16_t* t = reinterpret_cast<int16_t*>(sm + (size_t)NCORE_LINES * MW * 8);
     stage_tile(in, W, H, halo, t, ST_INVALID, &flag);
-    // prefix counts of non-smooth edges along every line of the 4 families;
-    // a line is walked from its first staged pixel in the family's step order
-    const int nlines = 2 * sw + 2 * (2 * sw - 1);
-    for (int line = threadIdx.x; line < nlines; line += PT_THREADS) {
-        int f, x, y;
-        if (line < sw) { f = 0; x = 0; y = line; }                          // rows
-        else if (line < 2 * sw) { f = 1; x = line - sw; y = 0; }           // columns
-        else {
-            const int d = line - 2 * sw;
-            f = d < 2 * sw - 1 ? 2 : 3;
-            const int e = d % (2 * sw - 1);                                  // diagonal index
-            if (f == 2) { x = e < sw ? 0 : e - sw + 1; y = e < sw ? sw - 1 - e : 0; }
-            else { x = e < sw ? 0 : e - sw + 1; y = e < sw ? e : sw - 1; }
-        }
+    build_line_masks(masks, sw, halo, [&](int f, int x, int y) {
         int dx, dy;
-        family_step(f, dx, dy);
-        uint8_t* z = Z + (size_t)f * sw * sw;
-        int zeros = 0;
-        while (x >= 0 && x < sw && y >= 0 && y < sw) {
-            const int nx = x + dx, ny = y + dy;
-            bool smooth = false;
-            if (nx >= 0 && nx < sw && ny >= 0 && ny < sw) {
-                const int a = t[y * sw + x], b = t[ny * sw + nx];
-                smooth = a != ST_INVALID && b != ST_INVALID && fabsf((float)(b - a)) < thresh;
-            }
-            zeros += smooth ? 0 : 1;
-            z[y * sw + x] = (uint8_t)min(zeros, 255);
-            x = nx;
-            y = ny;
-        }
-    }
+        fam_step(f, dx, dy);
+        const int nx = x + dx, ny = y + dy;
+        if (nx < 0 || nx >= sw || ny < 0 || ny >= sw) return false;
+        const int a = t[y * sw + x], b = t[ny * sw + nx];
+        return a != ST_INVALID && b != ST_INVALID && fabsf((float)(b - a)) < thresh;
+    });
     __syncthreads();
-    // Zero count of the edges strictly before position (x, y) on its line
-    // (0 when (x, y) lies before the start of the staged line).
-    auto zat = [&](int f, int x, int y) -> int {
-        if (x < 0 || x >= sw || y < 0 || y >= sw) return 0;
-        return Z[(size_t)f * sw * sw + y * sw + x];
-    };
+    const uint64_t need = low_mask(radius);
     for (int i = threadIdx.x; i < PT_W * PT_H; i += PT_THREADS) {
         const int lx = i % PT_W, ly = i / PT_W;
         const int gx = blockIdx.x * PT_W + lx, gy = blockIdx.y * PT_H + ly;
@@ -118,29 +146,25 @@ __global__ void __launch_bounds__(PT_THREADS) k_outlier_tiled(const int16_t* __r
         const int cx = lx + halo, cy = ly + halo;
         const int v = t[cy * sw + cx];
         bool keep = false;
-        if (v != ST_INVALID && radius > 0) {
-            for (int f = 0; f < 4 && !keep; ++f) {
-                int dx, dy;
-                family_step(f, dx, dy);
-                // forward: edges p .. p+(r-1)step
-                const int fwd = zat(f, cx + (radius - 1) * dx, cy + (radius - 1) * dy) -
-                                zat(f, cx - dx, cy - dy);
-                // backward: edges p-r*step .. p-step
-                const int bwd = zat(f, cx - dx, cy - dy) -
-                                zat(f, cx - (radius + 1) * dx, cy - (radius + 1) * dy);
-                keep = fwd == 0 || bwd == 0;
+        if (v != ST_INVALID) {
+            keep = radius == 0;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                int line, pos;
+                fam_line_pos(f, cx, cy, halo, line, pos);
+                const uint64_t* w = masks + (size_t)(fam_offset(f) + line) * MW;
+                keep |= (line_bits(w, pos) & need) == need;            // +step
+                keep |= (line_bits(w, pos - radius) & need) == need;   // -step
             }
-        } else if (v != ST_INVALID) {
-            keep = true;                       // radius 0: every direction passes
         }
         out[(size_t)gy * W + gx] = keep ? (int16_t)v : (int16_t)ST_INVALID;
     }
 }
 
-// First hole-filling method (8 radial directions) on a tile; halo = radius.
-// Direction by direction, a backward scan along each line through the tile
-// core gives every position the distance to the next valid pixel in that
-// direction (capped at radius + 1); each hole then reads its hit directly.
+// First hole-filling method (8 radial directions) on a tile; halo = radius
+// (<= 63).  The predicate is "valid"; for a hole at position pos the nearest
+// valid pixel ahead is the lowest set bit of bits pos+1 .. pos+r, the one
+// behind the highest set bit of bits pos-r .. pos-1.
 __global__ void __launch_bounds__(PT_THREADS) k_fill_radial_tiled(const int16_t* __restrict__ in,
                                                                   int W, int H, int radius,
                                                                   int min_dirs,
@@ -149,80 +173,50 @@ __global__ void __launch_bounds__(PT_THREADS) k_fill_radial_tiled(const int16_t*
     __shared__ int flag;
     const int halo = radius;
     const int sw = PT_W + 2 * halo;
-    int16_t* t = reinterpret_cast<int16_t*>(sm);
-    uint8_t* nd = sm + (((size_t)sw * sw * 2 + 15) & ~(size_t)15);     // [sw][sw]
+    uint64_t* masks = reinterpret_cast<uint64_t*>(sm);
+    int16_t* t = reinterpret_cast<int16_t*>(sm + (size_t)NCORE_LINES * MW * 8);
     if (!stage_tile(in, W, H, halo, t, ST_INVALID, &flag)) {
         copy_tile_out(t, halo, W, H, out);
         return;
     }
-    const int dxs[8] = {1, -1, 0, 0, 1, 1, -1, -1};
-    const int dys[8] = {0, 0, 1, -1, 1, -1, 1, -1};
-    constexpr int PER = (PT_W * PT_H) / PT_THREADS;      // outputs per thread
-    int num[PER], den[PER], found[PER];
-#pragma unroll
-    for (int q = 0; q < PER; ++q) { num[q] = 0; den[q] = 0; found[q] = 0; }
-    const int cap = radius + 1;
-    for (int k = 0; k < 8; ++k) {
-        const int dx = dxs[k], dy = dys[k];
-        // lines of this direction that cross the core, walked against the
-        // direction starting `radius` steps beyond the core
-        const int nl = (dx != 0 && dy != 0) ? 2 * PT_W - 1 : PT_W;
-        for (int l = threadIdx.x; l < nl; l += PT_THREADS) {
-            // a point of the line inside the core
-            int px, py;
-            if (dy == 0) { px = halo; py = halo + l; }
-            else if (dx == 0) { px = halo + l; py = halo; }
-            else if (l < PT_W) { px = halo; py = halo + l; }
-            else { px = halo + (l - PT_W + 1); py = (dx * dy > 0) ? halo : halo + PT_H - 1; }
-            // core segment of the line: first point A and last point B (in the
-            // direction's order); the scan runs from B + radius*dir back to A
-            auto in_core = [&](int x, int y) {
-                return x >= halo && x < halo + PT_W && y >= halo && y < halo + PT_H;
-            };
-            int bx = px, by = py;
-            while (in_core(bx + dx, by + dy)) { bx += dx; by += dy; }
-            int ax = px, ay = py;
-            while (in_core(ax - dx, ay - dy)) { ax -= dx; ay -= dy; }
-            const int len = max(abs(bx - ax), abs(by - ay)) + 1 + radius;   // positions A .. B+r*dir
-            int x = bx + radius * dx, y = by + radius * dy;
-            int dist = cap;                    // distance to the next valid pixel ahead
-            for (int n = 0; n < len; ++n) {
-                nd[y * sw + x] = (uint8_t)min(dist, cap);
-                dist = (t[y * sw + x] != ST_INVALID) ? 1 : min(dist + 1, cap);
-                x -= dx;
-                y -= dy;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int i = threadIdx.x + q * PT_THREADS;
-            const int lx = i % PT_W, ly = i / PT_W;
-            const int gx = blockIdx.x * PT_W + lx, gy = blockIdx.y * PT_H + ly;
-            const int cx = lx + halo, cy = ly + halo;
-            if (gx >= W || gy >= H || t[cy * sw + cx] != ST_INVALID) continue;
-            const int s = nd[cy * sw + cx];
-            if (s > radius) continue;
-            // the hit must lie inside the image (out-of-image pixels are staged invalid)
-            const int q2 = t[(cy + s * dy) * sw + cx + s * dx];
-            const int w = radius + 1 - s;
-            num[q] += w * q2;
-            den[q] += w;
-            found[q] += 1;
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-        const int i = threadIdx.x + q * PT_THREADS;
+    build_line_masks(masks, sw, halo, [&](int f, int x, int y) { return t[y * sw + x] != ST_INVALID; });
+    __syncthreads();
+    const uint64_t m = low_mask(radius);
+    for (int i = threadIdx.x; i < PT_W * PT_H; i += PT_THREADS) {
         const int lx = i % PT_W, ly = i / PT_W;
         const int gx = blockIdx.x * PT_W + lx, gy = blockIdx.y * PT_H + ly;
         if (gx >= W || gy >= H) continue;
-        const int v = t[(ly + halo) * sw + lx + halo];
+        const int cx = lx + halo, cy = ly + halo;
+        const int v = t[cy * sw + cx];
         if (v != ST_INVALID) { out[(size_t)gy * W + gx] = (int16_t)v; continue; }
-        out[(size_t)gy * W + gx] = (found[q] >= min_dirs && den[q] > 0)
-                                       ? (int16_t)round_half_up_i(num[q], den[q])
-                                       : (int16_t)ST_INVALID;
+        int num = 0, den = 0, found = 0;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            int line, pos, dx, dy;
+            fam_line_pos(f, cx, cy, halo, line, pos);
+            fam_step(f, dx, dy);
+            const uint64_t* w = masks + (size_t)(fam_offset(f) + line) * MW;
+            const uint64_t ahead = line_bits(w, pos + 1) & m;
+            if (ahead) {
+                const int s = __ffsll((long long)ahead);             // 1-based: distance
+                const int q = t[(cy + s * dy) * sw + cx + s * dx];
+                const int wgt = radius + 1 - s;
+                num += wgt * q;
+                den += wgt;
+                ++found;
+            }
+            const uint64_t behind = line_bits(w, pos - radius) & m;
+            if (behind) {
+                const int s = radius - (63 - __clzll((long long)behind));   // distance
+                const int q = t[(cy - s * dy) * sw + cx - s * dx];
+                const int wgt = radius + 1 - s;
+                num += wgt * q;
+                den += wgt;
+                ++found;
+            }
+        }
+        out[(size_t)gy * W + gx] =
+            (found >= min_dirs && den > 0) ? (int16_t)round_half_up_i(num, den) : (int16_t)ST_INVALID;
     }
 }
 
@@ -293,12 +287,9 @@ inline size_t tile_map_smem(int halo) {
 }
 inline size_t outlier_tile_smem(int halo) {
     const size_t sw = PT_W + 2 * halo;
-    return ((sw * sw * 2 + 15) & ~(size_t)15) + 4 * sw * sw;
+    return (size_t)NCORE_LINES * MW * 8 + sw * sw * 2;
 }
-inline size_t radial_tile_smem(int halo) {
-    const size_t sw = PT_W + 2 * halo;
-    return ((sw * sw * 2 + 15) & ~(size_t)15) + sw * sw;
-}
+inline size_t radial_tile_smem(int halo) { return outlier_tile_smem(halo); }
 inline size_t disc_tile_smem(int halo) {
     const size_t sw = PT_W + 2 * halo, sh = PT_H + 2 * halo;
     return ((sw * sh * 2 + 15) & ~(size_t)15) + sh * (sw + 1) * 4 + sh * (sw + 1) * 2;

@@ -51,6 +51,7 @@ struct PairWs {
     int16_t* t;         // post-processing round buffer
     int16_t* post;      // post-processing output (when the caller gives none)
     int16_t* cnt;       // refinement: valid count of each box
+    uint32_t* masks;    // line bitmasks of the radial passes
     float* dfin;        // refined output (when the caller gives none)
     float* dprev;
     float* dt;
@@ -59,6 +60,10 @@ struct PairWs {
     int* rsO;
     float* rsB;
 };
+
+// Words of the line bitmasks for a W x H map (the largest W x H of a
+// handle bounds every smaller geometry).
+size_t mask_words(int W, int H) { return make_line_masks(nullptr, W, H).total(); }
 
 // Geometry-dependent buffers are sized from the handle's maximum width and
 // height (maxW, maxH).
@@ -73,6 +78,7 @@ size_t pair_ws_bytes(size_t npix, int D, int cdt, int maxW = 0, int maxH = 0) {
     b += align_up(npix * 8, 256);                 // keys
     b += align_up(npix * (size_t)cost_stride(D) * elem_size(cdt), 256);
     b += align_up(npix * 2, 256) * 8;             // wta lr p q o t post cnt
+    b += align_up(mask_words(maxW, maxH) * 4, 256);   // line bitmasks
     b += align_up(npix * 4, 256) * 7;             // dprev dt b rsC rsO rsB dfin
     return b;
 }
@@ -97,6 +103,7 @@ PairWs carve(uint8_t* base, size_t npix, int D, int cdt, int maxW, int maxH) {
     w.t = reinterpret_cast<int16_t*>(take(npix * 2));
     w.post = reinterpret_cast<int16_t*>(take(npix * 2));
     w.cnt = reinterpret_cast<int16_t*>(take(npix * 2));
+    w.masks = reinterpret_cast<uint32_t*>(take(mask_words(maxW, maxH) * 4));
     w.dfin = reinterpret_cast<float*>(take(npix * 4));
     w.dprev = reinterpret_cast<float*>(take(npix * 4));
     w.dt = reinterpret_cast<float*>(take(npix * 4));
@@ -210,6 +217,45 @@ void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, in
     counted();
 }
 
+// One outlier pass / radial fill pass: mask build + query for radii up to
+// 63 (64 for the outlier test), the direction-parallel walk beyond.
+// Builds the line bitmasks of `in` (mode 0 valid, 1 smooth edge).
+void build_masks(const int16_t* in, int W, int H, int mode, float thresh, uint32_t* words, cudaStream_t s) {
+    LineMasks m = make_line_masks(words, W, H);
+    cudaMemsetAsync(words, 0, m.total() * 4, s);
+    k_line_masks_tiled<<<dim3((W + 31) / 32, (H + 31) / 32 + 2), 256, 0, s>>>(in, m, mode, thresh);
+    counted();
+}
+
+// One outlier pass / radial fill pass: mask build + query for radii up to
+// 63 (64 for the outlier test), the direction-parallel walk beyond.
+void run_outlier(const int16_t* in, int W, int H, int radius, float thresh, uint32_t* masks, int16_t* out,
+                 cudaStream_t s) {
+    const long npix = (long)W * H;
+    if (radius <= 64) {
+        build_masks(in, W, H, 1, thresh, masks, s);
+        k_outlier_masks<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(in, make_line_masks(masks, W, H),
+                                                                       radius, out);
+    } else {
+        k_outlier_dirs<<<(unsigned)((npix * 8 + 255) / 256), 256, 0, s>>>(in, W, H, radius, thresh, out);
+    }
+    counted();
+}
+
+void run_fill_radial(const int16_t* in, int W, int H, int radius, int min_dirs, uint32_t* masks,
+                     int16_t* out, cudaStream_t s) {
+    const long npix = (long)W * H;
+    if (radius <= 63) {
+        build_masks(in, W, H, 0, 0.f, masks, s);
+        k_fill_radial_masks<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(
+            in, make_line_masks(masks, W, H), radius, min_dirs, out);
+    } else {
+        k_fill_radial_dirs<<<(unsigned)((npix * 8 + 255) / 256), 256, 0, s>>>(in, W, H, radius, min_dirs,
+                                                                              out);
+    }
+    counted();
+}
+
 void run_postprocess(const stereo_params& p, const int16_t* in, int W, int H, const PairWs& w,
                      int16_t* out, cudaStream_t s) {
     dim3 b2(32, 8), g2((W + 31) / 32, (H + 7) / 8);
@@ -225,17 +271,8 @@ void run_postprocess(const stereo_params& p, const int16_t* in, int W, int H, co
     dim3 tg((W + PT_W - 1) / PT_W, (H + PT_H - 1) / PT_H);
     for (int t = 0; t < p.outlier_rounds; ++t) {
         const int rad = p.r0 + t * p.dr;
-        if (rad <= PT_MAX_HALO)
-            k_outlier_tiled<<<tg, PT_THREADS, outlier_tile_smem(rad), s>>>(cur, W, H, rad, p.outlier_thresh, w.p);
-        else
-            k_outlier<<<g2, b2, 0, s>>>(cur, W, H, rad, p.outlier_thresh, w.p);
-        counted();
-        if (p.fill_radial_r <= PT_MAX_HALO)
-            k_fill_radial_tiled<<<tg, PT_THREADS, radial_tile_smem(p.fill_radial_r), s>>>(
-                w.p, W, H, p.fill_radial_r, p.fill_radial_min_dirs, w.q);
-        else
-            k_fill_radial<<<g2, b2, 0, s>>>(w.p, W, H, p.fill_radial_r, p.fill_radial_min_dirs, w.q);
-        counted();
+        run_outlier(cur, W, H, rad, p.outlier_thresh, w.masks, w.p, s);
+        run_fill_radial(w.p, W, H, p.fill_radial_r, p.fill_radial_min_dirs, w.masks, w.q, s);
         int16_t* dst = (t == p.outlier_rounds - 1) ? out : w.t;
         k_fill_disc_tiled<<<tg, PT_THREADS, disc_tile_smem(p.fill_disc_r), s>>>(w.q, W, H, p.fill_disc_r,
                                                                                min_count, dst);
@@ -446,33 +483,23 @@ stereo_status stereo_stage_lr(const int16_t* dL, const int16_t* dR, int32_t W, i
     return last_error();
 }
 
-stereo_status stereo_stage_outlier(const int16_t* in, int32_t W, int32_t H, int32_t radius,
-                                   float thresh, int16_t* out, void* stream) {
-    if (!in || !out || in == out || W < 1 || H < 1 || radius < 0 || !(thresh >= 0.f))
+stereo_status stereo_stage_outlier(stereo_handle* h, const int16_t* in, int32_t W, int32_t H,
+                                   int32_t radius, float thresh, int16_t* out, void* stream) {
+    if (!h || !in || !out || in == out || W < 1 || H < 1 || radius < 0 || !(thresh >= 0.f))
         return STEREO_ERR_INVALID_ARG;
-    set_smem_attributes();
-    if (radius <= PT_MAX_HALO)
-        k_outlier_tiled<<<dim3((W + PT_W - 1) / PT_W, (H + PT_H - 1) / PT_H), PT_THREADS,
-                          outlier_tile_smem(radius), S(stream)>>>(in, W, H, radius, thresh, out);
-    else
-        k_outlier<<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, S(stream)>>>(in, W, H, radius,
-                                                                                   thresh, out);
-    counted();
+    if (W > h->p.max_width || H > h->p.max_height) return STEREO_ERR_TOO_LARGE;
+    PairWs w = carve(h->ws, (size_t)W * H, h->p.num_disp, h->p.cost_dtype, h->p.max_width, h->p.max_height);
+    run_outlier(in, W, H, radius, thresh, w.masks, out, S(stream));
     return last_error();
 }
 
-stereo_status stereo_stage_fill_radial(const int16_t* in, int32_t W, int32_t H, int32_t radius,
-                                       int32_t min_dirs, int16_t* out, void* stream) {
-    if (!in || !out || in == out || W < 1 || H < 1 || radius < 0 || min_dirs < 0)
+stereo_status stereo_stage_fill_radial(stereo_handle* h, const int16_t* in, int32_t W, int32_t H,
+                                       int32_t radius, int32_t min_dirs, int16_t* out, void* stream) {
+    if (!h || !in || !out || in == out || W < 1 || H < 1 || radius < 0 || min_dirs < 0)
         return STEREO_ERR_INVALID_ARG;
-    set_smem_attributes();
-    if (radius <= PT_MAX_HALO)
-        k_fill_radial_tiled<<<dim3((W + PT_W - 1) / PT_W, (H + PT_H - 1) / PT_H), PT_THREADS,
-                              radial_tile_smem(radius), S(stream)>>>(in, W, H, radius, min_dirs, out);
-    else
-        k_fill_radial<<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, S(stream)>>>(
-            in, W, H, radius, min_dirs, out);
-    counted();
+    if (W > h->p.max_width || H > h->p.max_height) return STEREO_ERR_TOO_LARGE;
+    PairWs w = carve(h->ws, (size_t)W * H, h->p.num_disp, h->p.cost_dtype, h->p.max_width, h->p.max_height);
+    run_fill_radial(in, W, H, radius, min_dirs, w.masks, out, S(stream));
     return last_error();
 }
 

@@ -55,23 +55,29 @@ def _random_map(rng, H, W, lo, hi, p_inv):
     return m
 
 
-@pytest.mark.parametrize("radius", [1, 3, 10, 20, 30, 60])
+def _handle(H, W):
+    return st.stereo_create(st.stereo_default_params(max_width=W, max_height=H, num_disp=32))
+
+
+@pytest.mark.parametrize("radius", [0, 1, 3, 10, 20, 30, 33, 63, 64, 70])
 def test_outlier(dev, radius):
+    """Radii up to 64 run the line-bitmask test, larger ones the ray walk."""
     rng = np.random.default_rng(radius)
-    m = _random_map(rng, 70, 90, 0, 60, 0.15)
+    m = _random_map(rng, 70, 150, 0, 60, 0.15)
     out = torch.empty_like(T(m, dev))
-    st.stereo_stage_outlier(T(m, dev), radius, 2.5, out)
+    st.stereo_stage_outlier(_handle(*m.shape), T(m, dev), radius, 2.5, out)
     want = oracle.outlier_removal(m, radius, 2.5)
     bad = int_map_mismatch(to_np(out), want)
     assert len(bad) == 0, describe(bad, to_np(out), want)
 
 
-@pytest.mark.parametrize("radius,min_dirs", [(50, 4), (5, 2), (50, 8), (70, 4)])
+@pytest.mark.parametrize("radius,min_dirs", [(50, 4), (5, 2), (50, 8), (63, 3), (70, 4), (1, 1)])
 def test_fill_radial(dev, radius, min_dirs):
+    """Radii up to 63 run the line-bitmask search, larger ones the ray walk."""
     rng = np.random.default_rng(radius + min_dirs)
-    m = _random_map(rng, 64, 100, -10, 60, 0.6)
+    m = _random_map(rng, 64, 130, -10, 60, 0.6)
     out = torch.empty_like(T(m, dev))
-    st.stereo_stage_fill_radial(T(m, dev), radius, min_dirs, out)
+    st.stereo_stage_fill_radial(_handle(*m.shape), T(m, dev), radius, min_dirs, out)
     want = oracle.fill_radial(m, radius, min_dirs)
     assert np.array_equal(to_np(out), want)
 
