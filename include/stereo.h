@@ -135,7 +135,11 @@ stereo_status stereo_destroy(stereo_handle* h);
 
 /* Whole path on one pair (Sec. II): gray -> ZNCC + WTA + sub-pixel ->
  * LR check -> outlier/hole loop -> Laplacian refinement.  Enqueued on
- * `stream`. */
+ * `stream`.  On a non-default stream the launch sequence is captured into a
+ * CUDA graph on the first call and replayed while the pair's pointers and
+ * sizes stay the same (the first call with new arguments captures again);
+ * when the caller's stream is itself being captured the kernels are
+ * enqueued into the caller's capture. */
 stereo_status stereo_match(stereo_handle* h, const stereo_pair* pair, void* stream);
 
 /* The same path on n pairs of mixed sizes, disparity ranges and windows,
@@ -165,9 +169,11 @@ stereo_status stereo_get_stage_times(stereo_handle* h, float* ms, int32_t n);
  * loaded (all handles and streams). */
 unsigned long long stereo_launch_count(void);
 
-/* Process-wide tuning knobs (0 = automatic choice).  "cost_rows": output
- * rows per work unit of the cost kernel (1..4096).  Returns
- * STEREO_ERR_INVALID_ARG for an unknown name or value. */
+/* Process-wide tuning knobs.  "cost_rows": output rows per work unit of the
+ * cost kernel (1..4096; 0 = automatic).  "graphs": 1 (default) replays
+ * stereo_match / stereo_match_batched as captured CUDA graphs on non-default
+ * streams, 0 launches kernels one by one.  Returns STEREO_ERR_INVALID_ARG
+ * for an unknown name or value. */
 stereo_status stereo_set_tuning(const char* name, int32_t value);
 
 /* ------------------------------------------------------------------------

@@ -4,6 +4,7 @@
 #include <math.h>
 #include <algorithm>
 #include <atomic>
+#include <vector>
 #include <new>
 #include <stdio.h>
 #include <string.h>
@@ -28,6 +29,7 @@ inline void counted(int n = 1) { g_launches.fetch_add((unsigned long long)n, std
 
 // Tuning knobs (0 = automatic), set through stereo_set_tuning.
 int g_cost_rows = 0;
+int g_use_graphs = 1;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -124,8 +126,17 @@ int disc_area(int r) {
 
 }  // namespace
 
+// One captured launch sequence, keyed by the bytes of its arguments.
+struct GraphCache {
+    std::vector<uint8_t> key;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long kernels = 0;   // kernels in the graph (launch accounting)
+};
+
 struct stereo_handle {
     stereo_params p;
+    GraphCache single;   // stereo_match
+    GraphCache batch;    // stereo_match_batched
     int max_batch;
     size_t npix_max;
     size_t pair_bytes;
@@ -354,6 +365,103 @@ stereo_status check_match_args(const stereo_handle* h, int W, int H, int d_min, 
 
 // ------------------------------------------------------------------ ABI
 
+static void mark(stereo_handle* h, int i, cudaStream_t s) {
+    if (h->timing && h->ev_ready) cudaEventRecord(h->ev[i], s);
+}
+
+// Validates one pair against the handle; resolves the per-pair overrides.
+static stereo_status resolve_pair(const stereo_handle* h, const stereo_pair* pr, int& d_min, int& D, int& r) {
+    if (!h || !pr || !pr->left || !pr->right) return STEREO_ERR_INVALID_ARG;
+    d_min = pr->num_disp ? pr->d_min : h->p.d_min;
+    D = pr->num_disp ? pr->num_disp : h->p.num_disp;
+    r = pr->win_radius ? pr->win_radius : h->p.win_radius;
+    stereo_status st = check_match_args(h, pr->width, pr->height, d_min, D, r, h->p.sampling, h->p.cost_dtype);
+    if (st != STEREO_OK) return st;
+    if (pr->channels != 1 && pr->channels != 3) return STEREO_ERR_INVALID_ARG;
+    if (pr->pitch < pr->width * pr->channels) return STEREO_ERR_INVALID_ARG;
+    return STEREO_OK;
+}
+
+// Enqueues the whole path for one (validated) pair using workspace slot `slot`.
+static void enqueue_match(stereo_handle* h, const stereo_pair* pr, int slot, cudaStream_t s, bool timed) {
+    int d_min, D, r;
+    resolve_pair(h, pr, d_min, D, r);
+    const int W = pr->width, H = pr->height;
+    const int cdt = h->p.cost_dtype;
+    PairWs w = carve(h->ws + (size_t)slot * h->pair_bytes, (size_t)W * H, h->p.num_disp, cdt,
+                     h->p.max_width, h->p.max_height);
+    const uint8_t* gl = pr->left;
+    const uint8_t* gr = pr->right;
+    dim3 g((W + 127) / 128, H);
+    if (timed) mark(h, 0, s);
+    if (pr->channels == 3) {
+        k_gray<<<g, 128, 0, s>>>(pr->left, W, H, pr->pitch, w.gl);
+        counted();
+        k_gray<<<g, 128, 0, s>>>(pr->right, W, H, pr->pitch, w.gr);
+        counted();
+        gl = w.gl;
+        gr = w.gr;
+    } else if (pr->pitch != W) {
+        k_copy_pitched<<<g, 128, 0, s>>>(pr->left, W, H, pr->pitch, w.gl);
+        counted();
+        k_copy_pitched<<<g, 128, 0, s>>>(pr->right, W, H, pr->pitch, w.gr);
+        counted();
+        gl = w.gl;
+        gr = w.gr;
+    }
+    if (timed) mark(h, 1, s);
+    int16_t* wta = pr->disp_wta ? pr->disp_wta : w.wta;
+    void* cost = cdt != CDT_NONE ? w.cost : nullptr;
+    run_match(gl, gr, W, H, d_min, D, r, h->p.sampling, cdt, h->p.lr_thresh, w, cost, wta, nullptr,
+              pr->disp_sub, w.lr, s, timed && h->ev_ready ? h->ev : nullptr);
+    if (pr->disp_lr) cudaMemcpyAsync(pr->disp_lr, w.lr, (size_t)W * H * 2, cudaMemcpyDeviceToDevice, s);
+    if (timed) mark(h, 4, s);
+    int16_t* post = pr->disp_post ? pr->disp_post : w.post;
+    run_postprocess(h->p, w.lr, W, H, w, post, s);
+    if (timed) mark(h, 5, s);
+    float* dfin = pr->disp_final ? pr->disp_final : w.dfin;
+    run_refine(h->p, post, cost, cdt, gl, gr, W, H, d_min, D, r, h->p.sampling, w, dfin, nullptr,
+               pr->valid, s);
+    if (timed) mark(h, 6, s);
+}
+
+// Replays a CUDA graph of `enqueue` (captured on first use, and again
+// whenever `key` changes); enqueues directly on the legacy default stream,
+// inside a caller's own capture, or when graphs are switched off.
+template <typename Enqueue>
+static stereo_status run_with_graph(stereo_handle* h, GraphCache& gc, const void* key, size_t key_len,
+                                    cudaStream_t s, Enqueue enqueue) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (s != nullptr) cudaStreamIsCapturing(s, &cs);
+    if (!g_use_graphs || s == nullptr || cs != cudaStreamCaptureStatusNone) {
+        enqueue(s);
+        return last_error();
+    }
+    if (!gc.exec || gc.key.size() != key_len || memcmp(gc.key.data(), key, key_len) != 0) {
+        if (gc.exec) { cudaGraphExecDestroy(gc.exec); gc.exec = nullptr; }
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return last_error();
+        enqueue(s);
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (e != cudaSuccess || !graph) {
+            cudaGetLastError();
+            if (graph) cudaGraphDestroy(graph);
+            return STEREO_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&gc.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            gc.exec = nullptr;
+            return STEREO_ERR_CUDA;
+        }
+        gc.key.assign(reinterpret_cast<const uint8_t*>(key), reinterpret_cast<const uint8_t*>(key) + key_len);
+    }
+    if (cudaGraphLaunch(gc.exec, s) != cudaSuccess) return last_error();
+    g_launches.fetch_add(gc.kernels, std::memory_order_relaxed);
+    return last_error();
+}
+
 extern "C" {
 
 void stereo_default_params(stereo_params* p) {
@@ -431,6 +539,8 @@ stereo_status stereo_create(const stereo_params* p, int32_t max_batch, stereo_ha
 stereo_status stereo_destroy(stereo_handle* h) {
     if (!h) return STEREO_OK;
     cudaDeviceSynchronize();
+    if (h->single.exec) cudaGraphExecDestroy(h->single.exec);
+    if (h->batch.exec) cudaGraphExecDestroy(h->batch.exec);
     if (h->ev_ready)
         for (int i = 0; i <= STEREO_NUM_STAGES; ++i) cudaEventDestroy(h->ev[i]);
     cudaFree(h->ws);
@@ -542,10 +652,6 @@ stereo_status stereo_stage_refine(stereo_handle* h, const int16_t* o_in, const v
     return last_error();
 }
 
-static void mark(stereo_handle* h, int i, cudaStream_t s) {
-    if (h->timing && h->ev_ready) cudaEventRecord(h->ev[i], s);
-}
-
 stereo_status stereo_set_stage_timing(stereo_handle* h, int32_t enable) {
     if (!h) return STEREO_ERR_INVALID_ARG;
     if (enable && !h->ev_ready) {
@@ -575,56 +681,32 @@ stereo_status stereo_set_tuning(const char* name, int32_t value) {
         g_cost_rows = value;
         return STEREO_OK;
     }
+    if (!strcmp(name, "graphs")) {
+        if (value < 0 || value > 1) return STEREO_ERR_INVALID_ARG;
+        g_use_graphs = value;
+        return STEREO_OK;
+    }
     return STEREO_ERR_INVALID_ARG;
 }
 
 stereo_status stereo_match(stereo_handle* h, const stereo_pair* pr, void* stream) {
-    if (!h || !pr || !pr->left || !pr->right) return STEREO_ERR_INVALID_ARG;
-    const int W = pr->width, H = pr->height;
-    const int d_min = pr->num_disp ? pr->d_min : h->p.d_min;
-    const int D = pr->num_disp ? pr->num_disp : h->p.num_disp;
-    const int r = pr->win_radius ? pr->win_radius : h->p.win_radius;
-    const int cdt = h->p.cost_dtype;
-    stereo_status st = check_match_args(h, W, H, d_min, D, r, h->p.sampling, cdt);
+    int d_min, D, r;
+    stereo_status st = resolve_pair(h, pr, d_min, D, r);
     if (st != STEREO_OK) return st;
-    if (pr->channels != 1 && pr->channels != 3) return STEREO_ERR_INVALID_ARG;
-    if (pr->pitch < W * pr->channels) return STEREO_ERR_INVALID_ARG;
     cudaStream_t s = S(stream);
-    PairWs w = carve(h->ws, (size_t)W * H, h->p.num_disp, cdt, h->p.max_width, h->p.max_height);
-    const uint8_t* gl = pr->left;
-    const uint8_t* gr = pr->right;
-    dim3 g((W + 127) / 128, H);
-    mark(h, 0, s);
-    if (pr->channels == 3) {
-        k_gray<<<g, 128, 0, s>>>(pr->left, W, H, pr->pitch, w.gl);
-        counted();
-        k_gray<<<g, 128, 0, s>>>(pr->right, W, H, pr->pitch, w.gr);
-        counted();
-        gl = w.gl;
-        gr = w.gr;
-    } else if (pr->pitch != W) {
-        k_copy_pitched<<<g, 128, 0, s>>>(pr->left, W, H, pr->pitch, w.gl);
-        counted();
-        k_copy_pitched<<<g, 128, 0, s>>>(pr->right, W, H, pr->pitch, w.gr);
-        counted();
-        gl = w.gl;
-        gr = w.gr;
+    if (h->timing) {                      // per-stage events: plain launches
+        enqueue_match(h, pr, 0, s, true);
+        return last_error();
     }
-    mark(h, 1, s);
-    int16_t* wta = pr->disp_wta ? pr->disp_wta : w.wta;
-    void* cost = cdt != CDT_NONE ? w.cost : nullptr;
-    run_match(gl, gr, W, H, d_min, D, r, h->p.sampling, cdt, h->p.lr_thresh, w, cost, wta, nullptr,
-              pr->disp_sub, w.lr, s, h->timing && h->ev_ready ? h->ev : nullptr);
-    if (pr->disp_lr) cudaMemcpyAsync(pr->disp_lr, w.lr, (size_t)W * H * 2, cudaMemcpyDeviceToDevice, s);
-    mark(h, 4, s);
-    int16_t* post = pr->disp_post ? pr->disp_post : w.post;
-    run_postprocess(h->p, w.lr, W, H, w, post, s);
-    mark(h, 5, s);
-    float* dfin = pr->disp_final ? pr->disp_final : w.dfin;
-    run_refine(h->p, post, cost, cdt, gl, gr, W, H, d_min, D, r, h->p.sampling, w, dfin, nullptr,
-               pr->valid, s);
-    mark(h, 6, s);
-    return last_error();
+    struct { stereo_pair p; int cost_rows; } key{*pr, g_cost_rows};
+    const unsigned long long before = g_launches.load();
+    stereo_status rs = run_with_graph(h, h->single, &key, sizeof(key), s, [&](cudaStream_t cs) {
+        const unsigned long long b0 = g_launches.load();
+        enqueue_match(h, pr, 0, cs, false);
+        h->single.kernels = g_launches.load() - b0;
+    });
+    (void)before;
+    return rs;
 }
 
 stereo_status stereo_match_batched(stereo_handle* h, const stereo_pair* pairs, int32_t n,

@@ -108,3 +108,33 @@ def test_rgb_and_pitch_inputs(dev):
     st.stereo_gray(T(Lrgb, dev), g_rgb)
     torch.cuda.synchronize()
     assert np.array_equal(to_np(g_rgb), oracle.gray(Lrgb))
+
+
+def test_graph_replay_matches_direct_launches(dev):
+    """On a non-default stream stereo_match replays a captured CUDA graph;
+    its outputs equal those of plain launches, also after the buffers
+    change (which captures a new graph)."""
+    L, R, gt = synth.perlin_pair(synth.seed_for(0))
+    H, W = L.shape
+    sp = st.stereo_default_params(max_width=W, max_height=H, num_disp=32, smooth_radius=2)
+    h = st.stereo_create(sp)
+    tL, tR = T(L, dev), T(R, dev)
+
+    def outs():
+        return dict(disp_wta=torch.empty((H, W), dtype=torch.int16, device=dev),
+                    disp_post=torch.empty((H, W), dtype=torch.int16, device=dev),
+                    disp_final=torch.empty((H, W), dtype=torch.float32, device=dev))
+
+    ref = outs()
+    st.stereo_match(h, tL, tR, **ref)           # default stream: plain launches
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    for _ in range(2):
+        for trial in range(3):                  # capture, replay, replay
+            o = outs() if trial == 0 else o
+            with torch.cuda.stream(s):
+                st.stereo_match(h, tL, tR, **o, stream=s)
+            s.synchronize()
+            for k in ref:
+                assert torch.equal(o[k].nan_to_num(-1), ref[k].nan_to_num(-1)), k
+    h.close()
