@@ -50,6 +50,10 @@ WORKLOADS = {
                       disp=None),
 }
 COST_CODE = {"none": 0, "f32": 1, "f16": 2, "bf16": 3}
+# DRAM bytes (read + write) of one k_cost_wta launch from an ncu capture of the
+# current kernel on the same workload (profiles/k_cost_wta_<workload>.md);
+# None where no capture of the current kernel exists.
+COST_KERNEL_TRAFFIC = {"tissue960": 226.3e6}
 COST_BYTES = {"none": 0, "f32": 4, "f16": 2, "bf16": 2}
 METRIC = "Gpix*disp/s and ms per 960x540 pair (1 B300), % of roofline, vs oracle"
 UNIT = "Gpix*disp/s"
@@ -141,7 +145,7 @@ class ClockSampler:
 
 # --------------------------------------------------------------- roofline
 
-def cost_kernel_roofline(wl, cost_ms, peaks, sm_count, sm_mhz):
+def cost_kernel_roofline(wl, cost_ms, peaks, sm_count, sm_mhz, traffic=None):
     """Roofline of the fused cost + winner-take-all kernel.
 
     Algorithmic work per pixel-disparity (p,d): 12 FP32/INT32 issue slots
@@ -165,13 +169,13 @@ def cost_kernel_roofline(wl, cost_ms, peaks, sm_count, sm_mhz):
     if t_hbm >= t_alu:
         achieved = bytes_ / dur / 1e9
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
-                "kernel": "k_zncc_wta", "algorithmic_bytes": bytes_,
+                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                "kernel": "k_cost_wta", "algorithmic_bytes": bytes_,
                 "peak_source": peaks["source"] + " (hbm_gbs)"}
     achieved = ops / dur / 1e12
     return {"bound": "alu", "achieved": round(achieved, 2), "peak": round(alu_peak / 1e12, 2),
-            "unit": "Tops/s", "frac": round(achieved / (alu_peak / 1e12), 4), "traffic": None,
-            "kernel": "k_zncc_wta", "algorithmic_ops": ops,
+            "unit": "Tops/s", "frac": round(achieved / (alu_peak / 1e12), 4), "traffic": traffic,
+            "kernel": "k_cost_wta", "algorithmic_ops": ops,
             "peak_source": f"{sm_count} SMs x 128 lanes x {peaks['sm_max_mhz']:.0f} MHz"}
 
 
@@ -278,7 +282,8 @@ def run_ours(args, wl, rank, world):
     peaks = load_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     clocks = clk.summary()
-    roof = cost_kernel_roofline(wl, stage_ms["cost_wta"], peaks, sm_count, clocks.get("sm_mhz"))
+    roof = cost_kernel_roofline(wl, stage_ms["cost_wta"], peaks, sm_count, clocks.get("sm_mhz"),
+                                COST_KERNEL_TRAFFIC.get(args.workload))
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max * 1e3 / args.steps, 4),

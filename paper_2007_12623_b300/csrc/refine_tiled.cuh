@@ -4,8 +4,9 @@
 // sums, sliding along 8-element segments):
 //   k_refine_box1: dt = mean of valid o (Eq. 1); b = dt - alpha o -
 //                  (1 - alpha) d_prev (Eq. 2); also the valid count
-//   k_refine_box2: d = dt - mean of valid b (Eq. 3); o-update (Eq. 4)
-// The same rules as refine.cuh (kept for radii beyond the tile halo).
+//   k_refine_box2: d = dt - mean of valid b (Eq. 3)
+// followed by k_refine_oupdate (Eq. 4, one thread per pixel).  The same
+// rules as refine.cuh (kept for radii beyond the tile halo).
 #pragma once
 #include "common.cuh"
 
@@ -102,10 +103,8 @@ __global__ void __launch_bounds__(RT_THREADS) k_refine_box1(const int16_t* __res
 }
 
 __global__ void __launch_bounds__(RT_THREADS) k_refine_box2(
-    int16_t* __restrict__ o, float* __restrict__ dprev, const float* __restrict__ dt,
-    const float* __restrict__ b, const int16_t* __restrict__ cnt, int W, int H, int rs, float eta,
-    int search, int d_min, int D, const void* __restrict__ cost, int cdt,
-    const uint8_t* __restrict__ L, const uint8_t* __restrict__ Rm, int r, int sampling,
+    const int16_t* __restrict__ o, float* __restrict__ dprev, const float* __restrict__ dt,
+    const float* __restrict__ b, const int16_t* __restrict__ cnt, int W, int H, int rs,
     float* __restrict__ d_out) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int sw = RT + 2 * rs, sh = RT + 2 * rs;
@@ -124,7 +123,6 @@ __global__ void __launch_bounds__(RT_THREADS) k_refine_box2(
     __syncthreads();
     box_cols<float>(rb, rs, sb);
     __syncthreads();
-    const int cs = cost_stride(D);
     for (int i = threadIdx.x; i < RT * RT; i += RT_THREADS) {
         const int gx = blockIdx.x * RT + i % RT, gy = blockIdx.y * RT + i / RT;
         if (gx >= W || gy >= H) continue;
@@ -137,52 +135,6 @@ __global__ void __launch_bounds__(RT_THREADS) k_refine_box2(
         const float d = dt[gi] - sb[i] / (float)cnt[gi];      // Eq. (3)
         dprev[gi] = d;
         if (d_out) d_out[gi] = d;
-        // Eq. (4)
-        const int lo = max((int)ceilf(d - (float)search), d_min);
-        const int hi = min((int)floorf(d + (float)search), d_min + D - 1);
-        int best = ST_INVALID;
-        float bf = 0.f, bdist = 0.f;
-        const size_t cbase = gi * (size_t)cs;
-        if (cdt != CDT_NONE && search <= 8) {
-            // all candidate costs in flight at once (one memory round trip)
-            float rho[17];
-#pragma unroll
-            for (int j = 0; j < 17; ++j) {
-                const int cand = lo + j;
-                rho[j] = (j <= 2 * search && cand <= hi)
-                             ? 1.f - cost_load(cost, cdt, cbase + (cand - d_min))
-                             : __int_as_float(0x7fc00000);
-            }
-#pragma unroll
-            for (int j = 0; j < 17; ++j) {
-                if (!(rho[j] > 0.f)) continue;   // NaN (invalid / out of range) or non-positive
-                const int cand = lo + j;
-                const float diff = (float)cand - d;
-                const float f = 1.f / rho[j] + eta * diff * diff;
-                const float dist = fabsf(diff);
-                if (best == ST_INVALID || f < bf || (f == bf && dist < bdist)) {
-                    best = cand;
-                    bf = f;
-                    bdist = dist;
-                }
-            }
-        } else {
-            for (int cand = lo; cand <= hi; ++cand) {
-                float rho;
-                if (cdt != CDT_NONE) rho = 1.f - cost_load(cost, cdt, cbase + (cand - d_min));
-                else rho = zncc_direct(L, Rm, W, H, r, sampling, gx, gy, cand);
-                if (!(rho > 0.f)) continue;
-                const float diff = (float)cand - d;
-                const float f = 1.f / rho + eta * diff * diff;
-                const float dist = fabsf(diff);
-                if (best == ST_INVALID || f < bf || (f == bf && dist < bdist)) {
-                    best = cand;
-                    bf = f;
-                    bdist = dist;
-                }
-            }
-        }
-        if (best != ST_INVALID) o[gi] = (int16_t)best;
     }
 }
 
@@ -193,4 +145,87 @@ inline size_t refine_box1_smem(int rs) {
 inline size_t refine_box2_smem(int rs) {
     const size_t sw = RT + 2 * rs, sh = RT + 2 * rs;
     return (sw * sh + sh * RT + RT * RT) * 4;
+}
+
+// Eq. (4), one thread per pixel: o = argmin over integer o* in [d - S, d + S]
+// (clipped to the candidate range) of 1/ZNCC(o*) + eta (o* - d)^2, skipping
+// invalid candidates and ZNCC <= 0; ties -> smaller |o* - d|, then smaller
+// o*.  With a stored cost volume the 2S+1 <= 13 costs come in as four
+// aligned 16-byte loads (8-byte for 16-bit storage) issued together.
+__device__ __forceinline__ void oupdate_consider(int cand, float rho, float d, float eta, int& best,
+                                                 float& bf, float& bdist) {
+    if (!(rho > 0.f)) return;                           // NaN (invalid) or non-positive
+    const float diff = (float)cand - d;
+    const float f = 1.f / rho + eta * diff * diff;
+    const float dist = fabsf(diff);
+    if (best == ST_INVALID || f < bf || (f == bf && dist < bdist)) {
+        best = cand;
+        bf = f;
+        bdist = dist;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_refine_oupdate(int16_t* __restrict__ o, const float* __restrict__ dk,
+                                                        int n, float eta, int search, int d_min, int D,
+                                                        const void* __restrict__ cost, int cdt,
+                                                        const uint8_t* __restrict__ L,
+                                                        const uint8_t* __restrict__ Rm, int W, int H,
+                                                        int r, int sampling) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int ov = o[i];
+    if (ov == ST_INVALID) return;
+    const float d = dk[i];
+    const int lo = max((int)ceilf(d - (float)search), d_min);
+    const int hi = min((int)floorf(d + (float)search), d_min + D - 1);
+    if (lo > hi) return;
+    int best = ST_INVALID;
+    float bf = 0.f, bdist = 0.f;
+    const int cs = cost_stride(D);
+    if (cdt != CDT_NONE && hi - lo < 13) {
+        const int k0 = (lo - d_min) & ~3;                   // 16 candidates from k0
+        float c[16];
+        if (cdt == CDT_F32) {
+            const float4* p = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(cost) +
+                                                              (size_t)i * cs + k0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 v = (k0 + 4 * q < cs) ? __ldg(p + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+            }
+        } else {
+            const uint2* p = reinterpret_cast<const uint2*>(reinterpret_cast<const uint16_t*>(cost) +
+                                                            (size_t)i * cs + k0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint2 v = (k0 + 4 * q < cs) ? __ldg(p + q) : make_uint2(0u, 0u);
+                const uint32_t w[2] = {v.x, v.y};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint16_t a = (uint16_t)(w[h] & 0xffffu), b = (uint16_t)(w[h] >> 16);
+                    if (cdt == CDT_F16) {
+                        c[4 * q + 2 * h] = __half2float(__ushort_as_half(a));
+                        c[4 * q + 2 * h + 1] = __half2float(__ushort_as_half(b));
+                    } else {
+                        c[4 * q + 2 * h] = __bfloat162float(__ushort_as_bfloat16(a));
+                        c[4 * q + 2 * h + 1] = __bfloat162float(__ushort_as_bfloat16(b));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int cand = d_min + k0 + j;
+            if (cand >= lo && cand <= hi) oupdate_consider(cand, 1.f - c[j], d, eta, best, bf, bdist);
+        }
+    } else {
+        const int x = i % W, y = i / W;
+        for (int cand = lo; cand <= hi; ++cand) {
+            const float rho = cdt != CDT_NONE
+                                  ? 1.f - cost_load(cost, cdt, (size_t)i * cs + (cand - d_min))
+                                  : zncc_direct(L, Rm, W, H, r, sampling, x, y, cand);
+            oupdate_consider(cand, rho, d, eta, best, bf, bdist);
+        }
+    }
+    if (best != ST_INVALID) o[i] = (int16_t)best;
 }

@@ -311,9 +311,11 @@ void run_refine(const stereo_params& p, const int16_t* o_in, const void* cost, i
             k_refine_box1<<<rg, RT_THREADS, refine_box1_smem(rs), s>>>(w.o, w.dprev, W, H, rs, p.alpha,
                                                                        w.dt, w.b, w.cnt);
             counted();
-            k_refine_box2<<<rg, RT_THREADS, refine_box2_smem(rs), s>>>(
-                w.o, w.dprev, w.dt, w.b, w.cnt, W, H, rs, p.eta, p.refine_search, d_min, D, cost, cdt, gl,
-                gr, r, sampling, dk);
+            k_refine_box2<<<rg, RT_THREADS, refine_box2_smem(rs), s>>>(w.o, w.dprev, w.dt, w.b, w.cnt, W,
+                                                                       H, rs, dk);
+            counted();
+            k_refine_oupdate<<<(n + 255) / 256, 256, 0, s>>>(w.o, w.dprev, n, p.eta, p.refine_search, d_min,
+                                                             D, cost, cdt, gl, gr, W, H, r, sampling);
             counted();
         } else {
             k_refine_rows<<<gr2, bx, rsmem, s>>>(w.o, nullptr, W, H, rs, w.rsC, w.rsO, nullptr);
