@@ -238,6 +238,30 @@ stereo_status stereo_stage_refine(stereo_handle* h, const int16_t* o_in, const v
                                   int32_t width, int32_t height, int32_t d_min, int32_t num_disp,
                                   int32_t win_radius, float* d_out, int16_t* o_out, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free variant (no counterpart in the paper).
+ *
+ * For callers that must not allocate device memory at matching time -- e.g.
+ * a real-time video pipeline that forbids allocation after start-up, or a
+ * host that lends a plugin only its image and output buffers -- this runs
+ * the same cost + winner-take-all stage as stereo_stage_match with
+ * STEREO_COST_NONE (left and right WTA maps, sub-pixel from recomputed ZNCC)
+ * without a handle: its scratch is a fixed 16 MiB device array inside the
+ * library, which every GPU that loads the library keeps until process exit.
+ * Limits: width <= 640, height <= 480, num_disp <= 128, |d_min| <= 64,
+ * win_radius 1..7; larger requests return STEREO_ERR_TOO_LARGE and enqueue
+ * nothing.  It calls no allocation routine.  The first call on each device
+ * looks up the array's device address, so make it before any stream capture.
+ * Every call reuses the same array: calls must not overlap on the GPU (use
+ * one stream, or order them with events), or they race.  left/right: gray,
+ * row stride = width; disp_left/disp_right: int16 W*H; disp_sub: float W*H
+ * (may be NULL).
+ * ---------------------------------------------------------------------- */
+stereo_status stereo_match_wta_noalloc(const uint8_t* left, const uint8_t* right, int32_t width,
+                                       int32_t height, int32_t d_min, int32_t num_disp,
+                                       int32_t win_radius, int16_t* disp_left, int16_t* disp_right,
+                                       float* disp_sub, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,6 +19,7 @@ __all__ = [
     "stereo_stage_outlier", "stereo_stage_fill_radial", "stereo_stage_fill_disc",
     "stereo_stage_postprocess", "stereo_stage_refine", "stereo_set_stage_timing",
     "stereo_get_stage_times", "stereo_launch_count", "STAGE_NAMES", "stereo_set_tuning",
+    "stereo_match_wta_noalloc",
 ]
 
 STAGE_NAMES = ("input", "stats", "cost_wta", "finalize", "postprocess", "refine")
@@ -99,6 +100,7 @@ def lib():
             "stereo_get_stage_times": (C.c_int, [P, P, i32]),
             "stereo_launch_count": (C.c_ulonglong, []),
             "stereo_set_tuning": (C.c_int, [C.c_char_p, i32]),
+            "stereo_match_wta_noalloc": (C.c_int, [P, P, i32, i32, i32, i32, i32, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -344,3 +346,15 @@ def stereo_launch_count() -> int:
 def stereo_set_tuning(name: str, value: int):
     """Process-wide tuning knob (see include/stereo.h), 0 = automatic."""
     _check(lib().stereo_set_tuning(name.encode(), int(value)), "stereo_set_tuning")
+
+
+def stereo_match_wta_noalloc(left, right, d_min, num_disp, win_radius, disp_left, disp_right,
+                             disp_sub=None, stream=None):
+    """Cost + winner-take-all without any allocation (fixed in-library scratch);
+    see include/stereo.h for the limits and the no-overlap rule."""
+    import torch
+    H, W = left.shape
+    _check(lib().stereo_match_wta_noalloc(
+        _ptr(left, torch.uint8, "left"), _ptr(right, torch.uint8, "right"), W, H, d_min, num_disp,
+        win_radius, _ptr(disp_left, torch.int16, "disp_left"), _ptr(disp_right, torch.int16, "disp_right"),
+        _ptr(disp_sub, torch.float32, "disp_sub"), _stream(stream)), "stereo_match_wta_noalloc")

@@ -4,6 +4,7 @@
 #include <math.h>
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <vector>
 #include <new>
 #include <stdio.h>
@@ -724,3 +725,102 @@ stereo_status stereo_match_batched(stereo_handle* h, const stereo_pair* pairs, i
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free winner-take-all entry point.
+//
+// Some callers cannot allocate device memory when they need a disparity map:
+// a real-time video pipeline that forbids allocation after start-up
+// (cudaMalloc can synchronise the device and take unbounded time), or a host
+// application that hands a plugin the image and output buffers and nothing
+// else.  For them stereo_match_wta_noalloc runs the cost + winner-take-all
+// stage (the same kernels as stereo_stage_match without a cost volume) with
+// its scratch -- float images, window statistics, winner keys -- in one
+// fixed array of this library instead of a handle's workspace.
+//
+// The array below is a device symbol: every GPU on which the library's
+// kernels are loaded holds its NA_SCRATCH_BYTES until the process exits.  On
+// the host its name is only a stand-in, so the first call on each device
+// looks up its device address (cudaGetSymbolAddress with that device
+// current) and every launch receives that address.  Because the first call
+// does this look-up, it should come before any stream capture.  All calls
+// share the array: the preparation kernels rewrite every part a call reads
+// (and clear the winner keys), but two calls whose work overlaps on the GPU
+// race on it -- serialise them (one stream, or events).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int NA_MAX_W = 640, NA_MAX_H = 480, NA_MAX_D = 128, NA_MAX_ABS_DMIN = 64;
+constexpr size_t NA_SCRATCH_BYTES = (size_t)16 << 20;   // 16 MiB
+
+static __device__ __align__(256) unsigned char g_na_scratch[NA_SCRATCH_BYTES];
+
+std::mutex g_na_mu;
+void* g_na_addr[64] = {nullptr};
+
+// Device address of g_na_scratch on the current device (looked up once per device).
+stereo_status na_scratch_address(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return STEREO_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_na_mu);
+    if (!g_na_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return STEREO_ERR_CUDA;
+        }
+        g_na_addr[dev] = p;
+    }
+    *out = g_na_addr[dev];
+    return STEREO_OK;
+}
+
+}  // namespace
+
+extern "C" stereo_status stereo_match_wta_noalloc(const uint8_t* left, const uint8_t* right, int32_t width,
+                                                  int32_t height, int32_t d_min, int32_t num_disp,
+                                                  int32_t win_radius, int16_t* disp_left,
+                                                  int16_t* disp_right, float* disp_sub, void* stream) {
+    if (!left || !right || width < 1 || height < 1 || num_disp < 1 || win_radius < 1 ||
+        win_radius > STEREO_MAX_WIN_RADIUS)
+        return STEREO_ERR_INVALID_ARG;
+    if (width > NA_MAX_W || height > NA_MAX_H || num_disp > NA_MAX_D || d_min < -NA_MAX_ABS_DMIN ||
+        d_min > NA_MAX_ABS_DMIN)
+        return STEREO_ERR_TOO_LARGE;
+    // carve the scratch exactly as run_match lays it out, and check the fit
+    const int W = width, H = height;
+    const int K = pick_k(num_disp);
+    const int nz = (num_disp + 32 * K - 1) / (32 * K);
+    const int lneed = std::max(0, d_min + nz * 32 * K + 3);
+    const int rneed = std::max(0, -d_min) + 48;
+    const size_t lf = (size_t)H * ((W + 40 + 3) & ~3) * 4;
+    const int rcol0 = ((lneed + 3) & ~3) + pos_mod4(d_min + 31 * K + 3);
+    const size_t rf = (size_t)H * ((rcol0 + W + rneed + 3) & ~3) * 4;
+    const size_t ls = (size_t)W * H * 8;
+    const size_t us = (size_t)H * (lneed + 4 + W + std::max(0, -d_min) + 48) * 16;
+    const size_t ks = (size_t)W * H * 8;
+    const size_t need = align_up(lf, 256) + align_up(rf, 256) + align_up(ls, 256) + align_up(us, 256) +
+                        align_up(ks, 256);
+    if (need > NA_SCRATCH_BYTES) return STEREO_ERR_TOO_LARGE;
+    void* base = nullptr;
+    stereo_status st = na_scratch_address(&base);
+    if (st != STEREO_OK) return st;
+    PairWs w{};
+    uint8_t* p = static_cast<uint8_t*>(base);
+    w.Lf = reinterpret_cast<float*>(p);
+    p += align_up(lf, 256);
+    w.Rf = reinterpret_cast<float*>(p);
+    p += align_up(rf, 256);
+    w.lstats = reinterpret_cast<float2*>(p);
+    p += align_up(ls, 256);
+    w.ustats = reinterpret_cast<float4*>(p);
+    p += align_up(us, 256);
+    w.keys = reinterpret_cast<uint32_t*>(p);
+    run_match(left, right, W, H, d_min, num_disp, win_radius, STEREO_SAMPLE_FULL, CDT_NONE, 1, w, nullptr,
+              disp_left, disp_right, disp_sub, nullptr, S(stream));
+    return last_error();
+}
