@@ -94,6 +94,8 @@ typedef struct {
     float alpha;                    /* Eq. (2)                                 */
     float eta;                      /* Eq. (4)                                 */
     int32_t refine_search;          /* o* in [d - S, d + S]                    */
+    int32_t soft_argmin;            /* 1: also allocate the soft-argmin backward
+                                       workspace (needs cost_dtype F32)       */
 } stereo_params;
 
 typedef struct stereo_handle stereo_handle;
@@ -237,6 +239,38 @@ stereo_status stereo_stage_refine(stereo_handle* h, const int16_t* o_in, const v
                                   int32_t cost_dtype, const uint8_t* left, const uint8_t* right,
                                   int32_t width, int32_t height, int32_t d_min, int32_t num_disp,
                                   int32_t win_radius, float* d_out, int16_t* o_out, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Differentiable soft-argmin variant (not in the paper): for every pixel,
+ * p_d = softmax over the valid candidates of ZNCC(d) / tau and
+ * d_soft = sum_d d p_d.  Images are float (batch x height x width,
+ * contiguous, row stride = width); the handle must have been created with
+ * soft_argmin = 1 (and cost_dtype F32) and sized for width, height,
+ * num_disp.  tau >= 0.025 (smaller values return STEREO_ERR_UNSUPPORTED);
+ * win_radius <= 7.  Pixels without a valid candidate get NaN.
+ * ---------------------------------------------------------------------- */
+
+/* Forward: d_soft and the log-sum-exp of the logits (both float B*H*W). */
+stereo_status stereo_softargmin_fwd(stereo_handle* h, const float* left, const float* right,
+                                    int32_t batch, int32_t width, int32_t height, int32_t d_min,
+                                    int32_t num_disp, int32_t win_radius, float tau, float* d_soft,
+                                    float* lse, void* stream);
+
+/* Backward: given the forward outputs and grad_dsoft = dLoss/d d_soft
+ * (float B*H*W), writes dLoss/dleft and dLoss/dright (float B*H*W).  Window
+ * statistics and ZNCC are recomputed, not taken from the forward call. */
+stereo_status stereo_softargmin_bwd(stereo_handle* h, const float* left, const float* right,
+                                    int32_t batch, int32_t width, int32_t height, int32_t d_min,
+                                    int32_t num_disp, int32_t win_radius, float tau,
+                                    const float* d_soft, const float* lse, const float* grad_dsoft,
+                                    float* grad_left, float* grad_right, void* stream);
+
+/* L1 loss of d_soft (n floats) against gt over the pixels where d_soft is
+ * not NaN: *loss = mean |d_soft - gt| (device float), grad = sign(d_soft -
+ * gt) / count, 0 elsewhere (device float n; may be NULL).  Needs a handle
+ * created with soft_argmin = 1. */
+stereo_status stereo_l1_loss(stereo_handle* h, const float* d_soft, const float* gt, int64_t n,
+                             float* loss, float* grad, void* stream);
 
 /* ------------------------------------------------------------------------
  * Allocation-free variant (no counterpart in the paper).

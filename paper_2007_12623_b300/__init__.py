@@ -14,4 +14,11 @@ import os
 from .binding import *  # noqa: F401,F403
 from .binding import __all__ as _binding_all
 
-__all__ = list(_binding_all)
+
+def __getattr__(name):
+    if name == "SoftArgminZNCC":
+        from . import binding
+        return binding.SoftArgminZNCC
+    raise AttributeError(name)
+
+__all__ = [n for n in _binding_all if n != "SoftArgminZNCC"]

@@ -19,7 +19,8 @@ __all__ = [
     "stereo_stage_outlier", "stereo_stage_fill_radial", "stereo_stage_fill_disc",
     "stereo_stage_postprocess", "stereo_stage_refine", "stereo_set_stage_timing",
     "stereo_get_stage_times", "stereo_launch_count", "STAGE_NAMES", "stereo_set_tuning",
-    "stereo_match_wta_noalloc",
+    "stereo_match_wta_noalloc", "stereo_softargmin_fwd", "stereo_softargmin_bwd", "stereo_l1_loss",
+    "SoftArgminZNCC", "soft_argmin",
 ]
 
 STAGE_NAMES = ("input", "stats", "cost_wta", "finalize", "postprocess", "refine")
@@ -51,6 +52,7 @@ class StereoParams(C.Structure):
         ("fill_disc_r", C.c_int32), ("fill_disc_min_count", C.c_int32),
         ("smooth_radius", C.c_int32), ("smooth_iters", C.c_int32),
         ("alpha", C.c_float), ("eta", C.c_float), ("refine_search", C.c_int32),
+        ("soft_argmin", C.c_int32),
     ]
 
 
@@ -101,6 +103,10 @@ def lib():
             "stereo_launch_count": (C.c_ulonglong, []),
             "stereo_set_tuning": (C.c_int, [C.c_char_p, i32]),
             "stereo_match_wta_noalloc": (C.c_int, [P, P, i32, i32, i32, i32, i32, P, P, P, P]),
+            "stereo_softargmin_fwd": (C.c_int, [P, P, P, i32, i32, i32, i32, i32, i32, f32, P, P, P]),
+            "stereo_softargmin_bwd": (C.c_int, [P, P, P, i32, i32, i32, i32, i32, i32, f32, P, P, P, P, P,
+                                                P]),
+            "stereo_l1_loss": (C.c_int, [P, P, P, C.c_int64, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -358,3 +364,97 @@ def stereo_match_wta_noalloc(left, right, d_min, num_disp, win_radius, disp_left
         _ptr(left, torch.uint8, "left"), _ptr(right, torch.uint8, "right"), W, H, d_min, num_disp,
         win_radius, _ptr(disp_left, torch.int16, "disp_left"), _ptr(disp_right, torch.int16, "disp_right"),
         _ptr(disp_sub, torch.float32, "disp_sub"), _stream(stream)), "stereo_match_wta_noalloc")
+
+
+# ------------------------------------------------------------ soft-argmin
+
+def _bhw(t):
+    if t.dim() == 2:
+        return 1, t.shape[0], t.shape[1]
+    return t.shape[0], t.shape[1], t.shape[2]
+
+
+def stereo_softargmin_fwd(handle: Handle, left, right, d_min, num_disp, win_radius, tau, d_soft, lse,
+                          stream=None):
+    import torch
+    B, H, W = _bhw(left)
+    _check(lib().stereo_softargmin_fwd(
+        handle.ptr, _ptr(left, torch.float32, "left"), _ptr(right, torch.float32, "right"), B, W, H,
+        d_min, num_disp, win_radius, tau, _ptr(d_soft, torch.float32, "d_soft"),
+        _ptr(lse, torch.float32, "lse"), _stream(stream)), "stereo_softargmin_fwd")
+
+
+def stereo_softargmin_bwd(handle: Handle, left, right, d_min, num_disp, win_radius, tau, d_soft, lse,
+                          grad_dsoft, grad_left, grad_right, stream=None):
+    import torch
+    B, H, W = _bhw(left)
+    _check(lib().stereo_softargmin_bwd(
+        handle.ptr, _ptr(left, torch.float32, "left"), _ptr(right, torch.float32, "right"), B, W, H,
+        d_min, num_disp, win_radius, tau, _ptr(d_soft, torch.float32, "d_soft"),
+        _ptr(lse, torch.float32, "lse"), _ptr(grad_dsoft, torch.float32, "grad_dsoft"),
+        _ptr(grad_left, torch.float32, "grad_left"), _ptr(grad_right, torch.float32, "grad_right"),
+        _stream(stream)), "stereo_softargmin_bwd")
+
+
+def stereo_l1_loss(handle: Handle, d_soft, gt, loss, grad=None, stream=None):
+    import torch
+    _check(lib().stereo_l1_loss(handle.ptr, _ptr(d_soft, torch.float32, "d_soft"), _ptr(gt, torch.float32, "gt"),
+                                d_soft.numel(), _ptr(loss, torch.float32, "loss"),
+                                _ptr(grad, torch.float32, "grad"), _stream(stream)), "stereo_l1_loss")
+
+
+def _autograd_function():
+    import torch
+
+    class SoftArgminZNCC(torch.autograd.Function):
+        """d_soft = soft-argmin over disparities of ZNCC / tau (float images,
+        [B,] H, W).  Forward and backward both run in libstereo; the backward
+        recomputes the window statistics and ZNCC."""
+
+        @staticmethod
+        def forward(ctx, left, right, handle, d_min, num_disp, win_radius, tau):
+            left = left.contiguous()
+            right = right.contiguous()
+            d_soft = torch.empty_like(left)
+            lse = torch.empty_like(left)
+            stereo_softargmin_fwd(handle, left, right, d_min, num_disp, win_radius, tau, d_soft, lse)
+            ctx.save_for_backward(left, right, d_soft, lse)
+            ctx.cfg = (handle, d_min, num_disp, win_radius, tau)
+            return d_soft
+
+        @staticmethod
+        def backward(ctx, grad_dsoft):
+            left, right, d_soft, lse = ctx.saved_tensors
+            handle, d_min, num_disp, win_radius, tau = ctx.cfg
+            g = torch.nan_to_num(grad_dsoft.contiguous(), nan=0.0)
+            gl = torch.empty_like(left)
+            gr = torch.empty_like(right)
+            stereo_softargmin_bwd(handle, left, right, d_min, num_disp, win_radius, tau, d_soft, lse, g,
+                                  gl, gr)
+            return gl, gr, None, None, None, None, None
+
+    return SoftArgminZNCC
+
+
+class _LazyFn:
+    _fn = None
+
+    def __get__(self, obj, objtype=None):
+        if _LazyFn._fn is None:
+            _LazyFn._fn = _autograd_function()
+        return _LazyFn._fn
+
+
+class _Namespace:
+    SoftArgminZNCC = _LazyFn()
+
+
+def __getattr__(name):
+    if name == "SoftArgminZNCC":
+        return _Namespace.SoftArgminZNCC
+    raise AttributeError(name)
+
+
+def soft_argmin(left, right, handle: Handle, d_min=0, num_disp=128, win_radius=5, tau=0.1):
+    """Differentiable soft-argmin disparity (torch autograd)."""
+    return _Namespace.SoftArgminZNCC.apply(left, right, handle, d_min, num_disp, win_radius, tau)

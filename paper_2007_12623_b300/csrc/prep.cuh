@@ -123,3 +123,81 @@ __global__ void k_cost_border_nan(void* __restrict__ cost, int cdt, int W, int H
         else reinterpret_cast<uint16_t*>(cost)[i] = cdt == CDT_F16 ? (uint16_t)0x7e00 : (uint16_t)0x7fc0;
     }
 }
+
+// Float-image preparation for the soft-argmin path: same outputs as k_prep
+// (float copy with zero padding, {S, 1/sqrt(B)} or {S_hi, S_lo, 1/sqrt(B),
+// valid}), from a float image.  Window sums in FP32 (exact for
+// integer-valued images), B = N SS - S^2 in FP64, S_lo = S mod 256.
+__global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ img, int W, int H, int r,
+                                                  PrepOut out) {
+    __shared__ float t[PSPAN][PSPAN + 1];
+    __shared__ float rs[PSPAN][PT + 1];
+    __shared__ float rss[PSPAN][PT + 1];
+    const int x0 = blockIdx.x * PT, y0 = blockIdx.y * PT;
+    const int span = PT + 2 * r;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < span * span; i += 256) {
+        const int ly = i / span, lx = i % span;
+        const int gx = x0 - r + lx, gy = y0 - r + ly;
+        t[ly][lx] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? img[(size_t)gy * W + gx] : 0.f;
+    }
+    __syncthreads();
+    for (int i = tid; i < span * PT; i += 256) {
+        const int ly = i / PT, lx = i % PT;
+        float s = 0.f, ss = 0.f;
+        for (int k = 0; k <= 2 * r; ++k) {
+            const float v = t[ly][lx + k];
+            s += v;
+            ss = fmaf(v, v, ss);
+        }
+        rs[ly][lx] = s;
+        rss[ly][lx] = ss;
+    }
+    __syncthreads();
+    const double N = (double)((2 * r + 1) * (2 * r + 1));
+    for (int i = tid; i < PT * PT; i += 256) {
+        const int ly = i / PT, lx = i % PT;
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= W || gy >= H) continue;
+        const size_t gi = (size_t)gy * W + gx;
+        out.img[(size_t)gy * out.stride + out.col0 + gx] = t[ly + r][lx + r];
+        float s = 0.f;
+        double B = 0.0;
+        const bool interior = gx >= r && gx < W - r && gy >= r && gy < H - r;
+        if (interior) {
+            float ss = 0.f;
+            for (int k = 0; k <= 2 * r; ++k) { s += rs[ly + k][lx]; ss += rss[ly + k][lx]; }
+            B = N * (double)ss - (double)s * (double)s;
+        }
+        float is = 0.f;
+        if (B > 0.0) {
+            const float fb = (float)B;
+            const float y = rsqrtf(fb);
+            is = y * fmaf(-0.5f * fb * y, y, 1.5f);
+        }
+        if (out.lstats) out.lstats[gi] = make_float2(s, is);
+        if (out.ustats) {
+            const float lo = fmodf(s, 256.f);
+            out.ustats[(size_t)gy * out.ustride + out.ucol0 + gx] =
+                make_float4(s - lo, lo, is, interior ? 1.f : 0.f);
+        }
+    }
+    if (blockIdx.x == 0) {
+        const int npad = out.stride - W;
+        for (int i = tid; i < PT * npad; i += 256) {
+            const int gy = y0 + i / npad, m = i % npad;
+            if (gy >= H) break;
+            const int col = m < out.col0 ? m : W + m;
+            out.img[(size_t)gy * out.stride + col] = 0.f;
+        }
+        if (out.ustats) {
+            const int upad = out.ustride - W;
+            for (int i = tid; i < PT * upad; i += 256) {
+                const int gy = y0 + i / upad, m = i % upad;
+                if (gy >= H) break;
+                const int col = m < out.ucol0 ? m : W + m;
+                out.ustats[(size_t)gy * out.ustride + col] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    }
+}

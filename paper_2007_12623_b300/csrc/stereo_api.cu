@@ -19,6 +19,7 @@
 #include "refine.cuh"
 #include "post_tiled.cuh"
 #include "refine_tiled.cuh"
+#include "soft.cuh"
 
 namespace {
 
@@ -55,6 +56,11 @@ struct PairWs {
     int16_t* post;      // post-processing output (when the caller gives none)
     int16_t* cnt;       // refinement: valid count of each box
     uint32_t* masks;    // line bitmasks of the radial passes
+    // soft-argmin backward (only when the handle was created with soft_argmin)
+    float* softA;       // [H][W][cs] G * alpha
+    float* softM;       // [H][W][cs] window sums of softA
+    float* sP1; float* sP2; float* sQ1; float* sQ2; float* sT1L; float* sT1R;
+    double* l1part;     // L1-loss partial sums
     float* dfin;        // refined output (when the caller gives none)
     float* dprev;
     float* dt;
@@ -70,8 +76,15 @@ size_t mask_words(int W, int H) { return make_line_masks(nullptr, W, H).total();
 
 // Geometry-dependent buffers are sized from the handle's maximum width and
 // height (maxW, maxH).
-size_t pair_ws_bytes(size_t npix, int D, int cdt, int maxW = 0, int maxH = 0) {
+constexpr int L1_PARTS = 1024;
+
+size_t pair_ws_bytes(size_t npix, int D, int cdt, int maxW = 0, int maxH = 0, int soft = 0) {
     size_t b = 0;
+    if (soft) {
+        b += align_up(npix * (size_t)cost_stride(D) * 4, 256) * 2;       // softA, softM
+        b += align_up(npix * 4, 256) * 6;                                 // P1 P2 Q1 Q2 T1L T1R
+        b += align_up((size_t)L1_PARTS * 16, 256);
+    }
     b += align_up((size_t)maxH * ((maxW + 40 + 3) & ~3) * 4, 256);      // Lf
     b += align_up((size_t)maxH * (maxW + 2 * CMARGIN) * 4, 256);        // Rf
     b += align_up(npix * 8, 256);                                       // lstats
@@ -86,10 +99,21 @@ size_t pair_ws_bytes(size_t npix, int D, int cdt, int maxW = 0, int maxH = 0) {
     return b;
 }
 
-PairWs carve(uint8_t* base, size_t npix, int D, int cdt, int maxW, int maxH) {
-    PairWs w;
+PairWs carve(uint8_t* base, size_t npix, int D, int cdt, int maxW, int maxH, int soft = 0) {
+    PairWs w{};
     uint8_t* p = base;
     auto take = [&](size_t bytes) { uint8_t* r = p; p += align_up(bytes, 256); return r; };
+    if (soft) {
+        w.softA = reinterpret_cast<float*>(take(npix * (size_t)cost_stride(D) * 4));
+        w.softM = reinterpret_cast<float*>(take(npix * (size_t)cost_stride(D) * 4));
+        w.sP1 = reinterpret_cast<float*>(take(npix * 4));
+        w.sP2 = reinterpret_cast<float*>(take(npix * 4));
+        w.sQ1 = reinterpret_cast<float*>(take(npix * 4));
+        w.sQ2 = reinterpret_cast<float*>(take(npix * 4));
+        w.sT1L = reinterpret_cast<float*>(take(npix * 4));
+        w.sT1R = reinterpret_cast<float*>(take(npix * 4));
+        w.l1part = reinterpret_cast<double*>(take((size_t)L1_PARTS * 16));
+    }
     w.Lf = reinterpret_cast<float*>(take((size_t)maxH * ((maxW + 40 + 3) & ~3) * 4));
     w.Rf = reinterpret_cast<float*>(take((size_t)maxH * (maxW + 2 * CMARGIN) * 4));
     w.lstats = reinterpret_cast<float2*>(take(npix * 8));
@@ -190,23 +214,31 @@ void set_smem_attributes() {
     cudaFuncSetAttribute(k_fill_disc_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_refine_box1, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_refine_box2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_soft_final, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 // Stats + fused cost/WTA + finalize for one pair whose gray images are gl/gr.
+// Layouts of the float images and statistics of one geometry (left: stride
+// W+40; right: zero margins so that every staged segment of the cost kernel
+// is a 16-byte aligned copy).
+void prep_layouts(int W, int d_min, int D, int K, const PairWs& w, PrepOut& pl, PrepOut& pr) {
+    const int nz = (D + 32 * K - 1) / (32 * K);
+    const int lneed = std::max(0, d_min + nz * 32 * K + 3);          // columns read left of x = 0
+    const int rneed = std::max(0, -d_min) + 48;                      // columns read right of W - 1
+    pl = PrepOut{w.Lf, (W + 40 + 3) & ~3, 0, w.lstats, nullptr, 0, 0};
+    const int rcol0 = ((lneed + 3) & ~3) + pos_mod4(d_min + 31 * K + 3);
+    pr = PrepOut{w.Rf, (rcol0 + W + rneed + 3) & ~3, rcol0, nullptr, w.ustats, 0, 0};
+    pr.ucol0 = lneed + 4;
+    pr.ustride = pr.ucol0 + W + std::max(0, -d_min) + 48;
+}
+
 void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, int D, int r,
                int sampling, int cdt, int lr_thresh, const PairWs& w, void* cost,
                int16_t* disp_left, int16_t* disp_right, float* disp_sub, int16_t* disp_lr,
                cudaStream_t s, cudaEvent_t* ev = nullptr) {
-    // layouts of the float images and statistics for this geometry
     const int K = pick_k(D);
-    const int nz = (D + 32 * K - 1) / (32 * K);
-    const int lneed = std::max(0, d_min + nz * 32 * K + 3);          // columns read left of x = 0
-    const int rneed = std::max(0, -d_min) + 48;                      // columns read right of W - 1
-    PrepOut pl{w.Lf, (W + 40 + 3) & ~3, 0, w.lstats, nullptr, 0, 0};
-    const int rcol0 = ((lneed + 3) & ~3) + pos_mod4(d_min + 31 * K + 3);
-    PrepOut pr{w.Rf, (rcol0 + W + rneed + 3) & ~3, rcol0, nullptr, w.ustats, 0, 0};
-    pr.ucol0 = lneed + 4;
-    pr.ustride = pr.ucol0 + W + std::max(0, -d_min) + 48;
+    PrepOut pl, pr;
+    prep_layouts(W, d_min, D, K, w, pl, pr);
     dim3 sg((W + PT - 1) / PT, (H + PT - 1) / PT);
     k_prep<<<sg, 256, 0, s>>>(gl, W, H, r, pl, w.keys);
     counted();
@@ -348,6 +380,8 @@ stereo_status check_params(const stereo_params* p) {
     if (p->fill_disc_r < 0 || p->fill_disc_r > PT_MAX_HALO) return STEREO_ERR_INVALID_ARG;
     if (p->smooth_radius < 0 || p->smooth_iters < 0 || p->refine_search < 0) return STEREO_ERR_INVALID_ARG;
     if (!(p->outlier_thresh >= 0.f) || !(p->alpha >= 0.f && p->alpha <= 1.f) || !(p->eta >= 0.f))
+        return STEREO_ERR_INVALID_ARG;
+    if (p->soft_argmin != 0 && (p->soft_argmin != 1 || p->cost_dtype != STEREO_COST_F32))
         return STEREO_ERR_INVALID_ARG;
     return STEREO_OK;
 }
@@ -491,6 +525,7 @@ void stereo_default_params(stereo_params* p) {
     p->alpha = 0.1f;
     p->eta = 0.01f;
     p->refine_search = 5;
+    p->soft_argmin = 0;
 }
 
 const char* stereo_status_str(stereo_status s) {
@@ -516,7 +551,8 @@ stereo_status stereo_create(const stereo_params* p, int32_t max_batch, stereo_ha
     h->p = *p;
     h->max_batch = max_batch;
     h->npix_max = (size_t)p->max_width * p->max_height;
-    h->pair_bytes = pair_ws_bytes(h->npix_max, p->num_disp, p->cost_dtype, p->max_width, p->max_height);
+    h->pair_bytes = pair_ws_bytes(h->npix_max, p->num_disp, p->cost_dtype, p->max_width, p->max_height,
+                                  p->soft_argmin);
     h->ws = nullptr;
     h->dev_err = nullptr;
     h->timing = false;
@@ -710,6 +746,123 @@ stereo_status stereo_match(stereo_handle* h, const stereo_pair* pr, void* stream
     });
     (void)before;
     return rs;
+}
+
+// ---- soft-argmin -----------------------------------------------------------
+static stereo_status check_soft(const stereo_handle* h, int B, int W, int H, int d_min, int D, int r,
+                                float tau) {
+    if (!h || B < 1 || W < 1 || H < 1 || D < 1 || D > STEREO_MAX_DISP || r < 1 || r > SB_MAXR)
+        return STEREO_ERR_INVALID_ARG;
+    if (!h->p.soft_argmin) return STEREO_ERR_INVALID_ARG;
+    if (!(tau > 0.f)) return STEREO_ERR_INVALID_ARG;
+    if (tau < 0.025f) return STEREO_ERR_UNSUPPORTED;   // exp((rho - 1) / tau) would underflow
+    if (d_min < -CMAX_DMIN || d_min > CMAX_DMIN) return STEREO_ERR_INVALID_ARG;
+    if (W > h->p.max_width || H > h->p.max_height || D > h->p.num_disp) return STEREO_ERR_TOO_LARGE;
+    return STEREO_OK;
+}
+
+// Float window statistics + fused cost kernel (rho into the handle's cost
+// volume) for one pair of float images.
+static void soft_prepare(stereo_handle* h, const PairWs& w, const float* L, const float* R, int W, int H,
+                         int d_min, int D, int r, SoftArgs& sa, cudaStream_t s) {
+    const int K = pick_k(D);
+    PrepOut pl, pr;
+    prep_layouts(W, d_min, D, K, w, pl, pr);
+    dim3 sg((W + PT - 1) / PT, (H + PT - 1) / PT);
+    k_prep_f32<<<sg, 256, 0, s>>>(L, W, H, r, pl);
+    counted();
+    k_prep_f32<<<sg, 256, 0, s>>>(R, W, H, r, pr);
+    counted();
+    const int cs = cost_stride(D);
+    const long nb = (W <= 2 * r || H <= 2 * r) ? (long)W * H : 2L * r * W + 2L * r * (H - 2 * r);
+    k_cost_border_nan<<<(int)std::max<long>(1, std::min<long>(4096, (nb * cs + 255) / 256)), 256, 0, s>>>(
+        w.cost, CDT_F32, W, H, r, cs);
+    counted();
+    CostArgs a{pl.img, pl.stride, pl.col0, pr.img, pr.stride, pr.col0, w.lstats, w.ustats,
+               pr.ustride, pr.ucol0, w.keys, w.keys + (size_t)W * H, w.cost, CDT_F32, W, H, d_min, D, 0};
+    launch_cost(r, K, CDT_F32, a, g_cost_rows, s);
+    sa = SoftArgs{reinterpret_cast<const float*>(w.cost), cs, w.lstats, w.ustats, pr.ustride, pr.ucol0,
+                  W, H, d_min, D, r, 0.f};
+}
+
+stereo_status stereo_softargmin_fwd(stereo_handle* h, const float* left, const float* right, int32_t batch,
+                                    int32_t width, int32_t height, int32_t d_min, int32_t num_disp,
+                                    int32_t win_radius, float tau, float* d_soft, float* lse, void* stream) {
+    stereo_status st = check_soft(h, batch, width, height, d_min, num_disp, win_radius, tau);
+    if (st != STEREO_OK) return st;
+    if (!left || !right || !d_soft || !lse) return STEREO_ERR_INVALID_ARG;
+    cudaStream_t s = S(stream);
+    const size_t npix = (size_t)width * height;
+    PairWs w = carve(h->ws, npix, h->p.num_disp, h->p.cost_dtype, h->p.max_width, h->p.max_height, 1);
+    for (int b = 0; b < batch; ++b) {
+        SoftArgs sa;
+        soft_prepare(h, w, left + b * npix, right + b * npix, width, height, d_min, num_disp, win_radius, sa, s);
+        sa.tau = tau;
+        k_soft_fwd<<<(unsigned)((npix * 32 + 255) / 256), 256, 0, s>>>(sa, d_soft + b * npix, lse + b * npix);
+        counted();
+    }
+    return last_error();
+}
+
+stereo_status stereo_softargmin_bwd(stereo_handle* h, const float* left, const float* right, int32_t batch,
+                                    int32_t width, int32_t height, int32_t d_min, int32_t num_disp,
+                                    int32_t win_radius, float tau, const float* d_soft, const float* lse,
+                                    const float* grad_dsoft, float* grad_left, float* grad_right,
+                                    void* stream) {
+    stereo_status st = check_soft(h, batch, width, height, d_min, num_disp, win_radius, tau);
+    if (st != STEREO_OK) return st;
+    if (!left || !right || !d_soft || !lse || !grad_dsoft || !grad_left || !grad_right)
+        return STEREO_ERR_INVALID_ARG;
+    set_smem_attributes();
+    cudaStream_t s = S(stream);
+    const int W = width, H = height, r = win_radius;
+    const size_t npix = (size_t)W * H;
+    PairWs w = carve(h->ws, npix, h->p.num_disp, h->p.cost_dtype, h->p.max_width, h->p.max_height, 1);
+    const unsigned gw = (unsigned)((npix * 32 + 255) / 256), gp = (unsigned)((npix + 255) / 256);
+    for (int b = 0; b < batch; ++b) {
+        const float* L = left + b * npix;
+        const float* R = right + b * npix;
+        SoftArgs sa;
+        soft_prepare(h, w, L, R, W, H, d_min, num_disp, r, sa, s);
+        sa.tau = tau;
+        k_soft_bwd_a<<<gw, 256, 0, s>>>(sa, d_soft + b * npix, lse + b * npix, grad_dsoft + b * npix,
+                                        w.softA, w.sP1, w.sP2);
+        counted();
+        k_soft_bwd_q<<<gp, 256, 0, s>>>(sa, w.softA, w.sQ1, w.sQ2);
+        counted();
+        k_soft_box<<<dim3((W + SB_T - 1) / SB_T, (H + SB_T - 1) / SB_T, (sa.cs + SB_D - 1) / SB_D), 256, 0, s>>>(
+            w.softA, W, H, sa.cs, r, w.softM);
+        counted();
+        k_soft_t1l<<<gw, 256, 0, s>>>(w.softM, R, W, H, sa.cs, d_min, num_disp, w.sT1L);
+        counted();
+        k_soft_t1r<<<gp, 256, 0, s>>>(w.softM, L, W, H, sa.cs, d_min, num_disp, w.sT1R);
+        counted();
+        const int span = SF_T + 2 * r;
+        const size_t fsm = (size_t)(6 * span * span + 6 * span * SF_T) * 4;
+        k_soft_final<<<dim3((W + SF_T - 1) / SF_T, (H + SF_T - 1) / SF_T), 256, fsm, s>>>(
+            w.sT1L, w.sT1R, w.sP1, w.sP2, w.sQ1, w.sQ2, w.lstats, sa, L, R, grad_left + b * npix,
+            grad_right + b * npix);
+        counted();
+    }
+    return last_error();
+}
+
+stereo_status stereo_l1_loss(stereo_handle* h, const float* d_soft, const float* gt, int64_t n, float* loss,
+                             float* grad, void* stream) {
+    if (!h || !h->p.soft_argmin || !d_soft || !gt || !loss || n < 1) return STEREO_ERR_INVALID_ARG;
+    cudaStream_t s = S(stream);
+    PairWs w = carve(h->ws, h->npix_max, h->p.num_disp, h->p.cost_dtype, h->p.max_width, h->p.max_height, 1);
+    const int parts = (int)std::min<int64_t>(L1_PARTS - 1, (n + 255) / 256);
+    k_l1_partial<<<parts, 256, 0, s>>>(d_soft, gt, n, w.l1part);
+    counted();
+    double* count = w.l1part + 2 * (L1_PARTS - 1);
+    k_l1_final<<<1, 32, 0, s>>>(w.l1part, parts, loss, count);
+    counted();
+    if (grad) {
+        k_l1_grad<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_soft, gt, n, count, grad);
+        counted();
+    }
+    return last_error();
 }
 
 stereo_status stereo_match_batched(stereo_handle* h, const stereo_pair* pairs, int32_t n,

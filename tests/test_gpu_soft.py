@@ -1,0 +1,146 @@
+"""GPU parity of the soft-argmin variant (forward, hand-written backward, L1
+loss) against the FP64 oracle, whose own gradient is pinned by central
+finite differences (tests/test_oracle_soft.py).
+
+Bar: d_soft within 1e-4 px, log-sum-exp within 1e-4; image gradients with
+||g_gpu - g_oracle||_2 / ||g_oracle||_2 <= 1e-3 (maximum element error
+reported).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2007_12623_b300 as st  # noqa: E402
+
+GRAD_RTOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def dev():
+    assert torch.cuda.is_available()
+    st.lib()
+    return torch.device("cuda:0")
+
+
+def _crop_pair(seed, y0, x0, H, W, shift=3):
+    Lrgb, Rrgb, gt = synth.tissue_pair(seed, 320, 180, 2.0, 14.0)
+    L = oracle.gray(Lrgb)[y0:y0 + H, x0:x0 + W].astype(np.float64)
+    R = oracle.gray(Rrgb)[y0:y0 + H, x0:x0 + W].astype(np.float64)
+    return L, R, gt[y0:y0 + H, x0:x0 + W]
+
+
+def _handle(H, W, D, B=1):
+    p = st.stereo_default_params(max_width=W, max_height=H, num_disp=D, soft_argmin=1)
+    return st.stereo_create(p)
+
+
+def _T(a, dev):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+
+
+@pytest.mark.parametrize("r,D,tau", [(5, 16, 0.1), (2, 9, 0.05), (7, 24, 0.3)])
+def test_forward_matches_oracle(dev, r, D, tau):
+    L, R, gt = _crop_pair(synth.seed_for(4), 40, 60, 64, 80)
+    ds_ref, lse_ref, hv = oracle.softargmin_fwd(L, R, 0, D, r, tau)
+    h = _handle(64, 80, D)
+    ds = torch.empty((64, 80), dtype=torch.float32, device=dev)
+    lse = torch.empty_like(ds)
+    st.stereo_softargmin_fwd(h, _T(L, dev), _T(R, dev), 0, D, r, tau, ds, lse)
+    torch.cuda.synchronize()
+    ds, lse = ds.cpu().numpy(), lse.cpu().numpy()
+    assert np.array_equal(np.isnan(ds), ~hv)
+    assert np.max(np.abs(ds[hv] - ds_ref[hv])) <= 1e-4
+    assert np.max(np.abs(lse[hv] - lse_ref[hv]) / np.maximum(1.0, np.abs(lse_ref[hv]))) <= 1e-5
+    h.close()
+
+
+@pytest.mark.parametrize("r,D", [(5, 16), (3, 12)])
+def test_backward_matches_oracle_gradient(dev, r, D):
+    """64x64 crop, candidates 0..D-1, tau = 0.1, random upstream gradient."""
+    H, W, tau = 64, 64, 0.1
+    L, R, gt = _crop_pair(synth.seed_for(4, 1), 30, 100, H, W)
+    rng = np.random.default_rng(11)
+    ds_ref, lse_ref, hv = oracle.softargmin_fwd(L, R, 0, D, r, tau)
+    g = np.where(hv, rng.normal(0, 1, (H, W)), 0.0)
+    gL_ref, gR_ref = oracle.softargmin_bwd(L, R, 0, D, r, tau, g)
+    h = _handle(H, W, D)
+    tL, tR = _T(L, dev), _T(R, dev)
+    ds = torch.empty((H, W), dtype=torch.float32, device=dev)
+    lse = torch.empty_like(ds)
+    st.stereo_softargmin_fwd(h, tL, tR, 0, D, r, tau, ds, lse)
+    gL = torch.empty_like(ds)
+    gR = torch.empty_like(ds)
+    st.stereo_softargmin_bwd(h, tL, tR, 0, D, r, tau, ds, lse, _T(g, dev), gL, gR)
+    torch.cuda.synchronize()
+    for got, ref in ((gL.cpu().numpy(), gL_ref), (gR.cpu().numpy(), gR_ref)):
+        rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        print(f"grad rel L2 {rel:.2e}, max abs err {np.max(np.abs(got - ref)):.2e} (max |g| {np.max(np.abs(ref)):.2e})")
+        assert rel <= GRAD_RTOL
+    h.close()
+
+
+def test_autograd_l1_loss(dev):
+    """torch.autograd through SoftArgminZNCC with the library's L1 loss
+    reproduces the oracle's loss and gradients (batch of two crops)."""
+    H, W, D, r, tau = 48, 64, 16, 5, 0.1
+    crops = [_crop_pair(synth.seed_for(4, b), 50, 120, H, W) for b in range(2)]
+    L = np.stack([c[0] for c in crops])
+    R = np.stack([c[1] for c in crops])
+    gt = np.stack([c[2] for c in crops])
+    h = _handle(H, W, D)
+    tL = _T(L, dev).requires_grad_(True)
+    tR = _T(R, dev).requires_grad_(True)
+    ds = st.soft_argmin(tL, tR, h, 0, D, r, tau)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    g = torch.empty_like(ds)
+    st.stereo_l1_loss(h, ds.detach(), _T(gt, dev), loss, g)
+    ds.backward(g)
+    torch.cuda.synchronize()
+    # oracle: both crops, one mean over all valid pixels
+    refs = [oracle.softargmin_fwd(L[b], R[b], 0, D, r, tau) for b in range(2)]
+    ds_ref = np.stack([x[0] for x in refs])
+    hv = np.stack([x[2] for x in refs])
+    loss_ref, g_ref = oracle.l1_loss(ds_ref, hv, gt)
+    assert abs(loss.item() - loss_ref) <= 1e-4 * max(1.0, loss_ref)
+    kinks = np.abs(ds_ref - gt) < 1e-3            # sign may differ at |e| ~ 0
+    g_gpu = g.cpu().numpy()
+    assert np.all((g_gpu == g_ref.astype(np.float32)) | kinks | ~hv)
+    for b in range(2):
+        gl_ref, gr_ref = oracle.softargmin_bwd(L[b], R[b], 0, D, r, tau, g_gpu[b].astype(np.float64))
+        for got, ref in ((tL.grad[b].cpu().numpy(), gl_ref), (tR.grad[b].cpu().numpy(), gr_ref)):
+            assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= GRAD_RTOL
+    h.close()
+
+
+def test_full_size_batch_sampled(dev):
+    """Two 960x540 pairs (the batch form uses 8), D = 128, tau = 0.1: forward
+    sampled against the oracle pixel by pixel; gradients finite."""
+    B, H, W, D, r, tau = 2, 540, 960, 128, 5, 0.1
+    pairs = [synth.tissue_pair(synth.seed_for(4, b)) for b in range(B)]
+    L = np.stack([oracle.gray(p[0]) for p in pairs]).astype(np.float32)
+    R = np.stack([oracle.gray(p[1]) for p in pairs]).astype(np.float32)
+    h = _handle(H, W, D)
+    tL, tR = _T(L, dev), _T(R, dev)
+    ds = torch.empty((B, H, W), dtype=torch.float32, device=dev)
+    lse = torch.empty_like(ds)
+    st.stereo_softargmin_fwd(h, tL, tR, 0, D, r, tau, ds, lse)
+    g = torch.randn_like(ds).nan_to_num(0) * (~torch.isnan(ds))
+    gL, gR = torch.empty_like(ds), torch.empty_like(ds)
+    st.stereo_softargmin_bwd(h, tL, tR, 0, D, r, tau, ds, lse, g, gL, gR)
+    torch.cuda.synchronize()
+    assert torch.isfinite(gL).all() and torch.isfinite(gR).all()
+    ds_np = ds.cpu().numpy()
+    rng = np.random.default_rng(3)
+    for _ in range(12):
+        b, y, x = int(rng.integers(0, B)), int(rng.integers(5, H - 5)), int(rng.integers(140, W - 6))
+        # the crop holds every window of pixel (x, y) and of all its candidates
+        win = (slice(y - 5, y + 6), slice(x - 132, x + 6))
+        ref, _, hv = oracle.softargmin_fwd(L[b][win].astype(np.float64), R[b][win].astype(np.float64),
+                                           0, D, r, tau)
+        assert hv[5, 132] and abs(ds_np[b, y, x] - ref[5, 132]) <= 1e-4
+    h.close()
