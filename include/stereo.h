@@ -144,12 +144,32 @@ stereo_status stereo_destroy(stereo_handle* h);
  * enqueued into the caller's capture. */
 stereo_status stereo_match(stereo_handle* h, const stereo_pair* pair, void* stream);
 
-/* The same path on n pairs of mixed sizes, disparity ranges and windows,
- * each stage one persistent launch over all pairs' work units.  n <=
- * max_batch.  When `use_graph` is non-zero the launch sequence is captured
- * once into a CUDA graph (keyed by the pair geometry) and replayed. */
+/* The same path on n pairs of mixed sizes, disparity ranges (per-pair
+ * d_min/num_disp) and windows (per-pair win_radius), n <= max_batch; pair i
+ * uses workspace slot i.  The cost + winner-take-all stage of all pairs is
+ * ONE persistent launch: resident warps take work units (pair, column run,
+ * row band, disparity chunk) from a device counter.  The unit table is
+ * rebuilt (and uploaded, outside any capture) when the pairs or the batch
+ * configuration change.  When `use_graph` is non-zero and `stream` is not the
+ * legacy default stream, the whole launch sequence is captured once into a
+ * CUDA graph (keyed by the pairs' bytes) and replayed.  Returns
+ * STEREO_ERR_UNSUPPORTED when called inside a caller's capture with pairs
+ * that need new tables. */
 stereo_status stereo_match_batched(stereo_handle* h, const stereo_pair* pairs, int32_t n,
                                    int32_t use_graph, void* stream);
+
+/* Batch configuration: output rows per work unit (0 = default 16) and
+ * disparities per lane K (2 or 4; 0 = automatic: 2 when every pair has at
+ * most 64 candidates, else 4). */
+stereo_status stereo_set_batch_config(stereo_handle* h, int32_t rows, int32_t K);
+
+/* Autotuner of the batched form: runs the batch once per candidate
+ * configuration (K in {2, 4} x rows in {8, 12, 16, 24, 32, 48}), times the
+ * persistent cost stage with CUDA events, and keeps the fastest in the
+ * handle.  Synchronises `stream`; not allowed inside a capture.  Writes the
+ * choice and its time (ms) when the pointers are non-NULL. */
+stereo_status stereo_autotune_batched(stereo_handle* h, const stereo_pair* pairs, int32_t n, void* stream,
+                                      int32_t* best_rows, int32_t* best_K, float* best_ms);
 
 /* Reads (and clears) the handle's device error word; synchronises `stream`
  * first.  *err = 0 when no device-side error was recorded. */

@@ -20,7 +20,7 @@ __all__ = [
     "stereo_stage_postprocess", "stereo_stage_refine", "stereo_set_stage_timing",
     "stereo_get_stage_times", "stereo_launch_count", "STAGE_NAMES", "stereo_set_tuning",
     "stereo_match_wta_noalloc", "stereo_softargmin_fwd", "stereo_softargmin_bwd", "stereo_l1_loss",
-    "SoftArgminZNCC", "soft_argmin",
+    "SoftArgminZNCC", "soft_argmin", "stereo_set_batch_config", "stereo_autotune_batched",
 ]
 
 STAGE_NAMES = ("input", "stats", "cost_wta", "finalize", "postprocess", "refine")
@@ -107,6 +107,8 @@ def lib():
             "stereo_softargmin_bwd": (C.c_int, [P, P, P, i32, i32, i32, i32, i32, i32, f32, P, P, P, P, P,
                                                 P]),
             "stereo_l1_loss": (C.c_int, [P, P, P, C.c_int64, P, P, P]),
+            "stereo_set_batch_config": (C.c_int, [P, i32, i32]),
+            "stereo_autotune_batched": (C.c_int, [P, P, i32, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -244,14 +246,33 @@ def stereo_match(handle: Handle, left, right, *, disp_wta=None, disp_sub=None, d
     _check(lib().stereo_match(handle.ptr, C.byref(p), _stream(stream)), "stereo_match")
 
 
-def stereo_match_batched(handle: Handle, pairs, use_graph: bool = True, stream=None):
-    """pairs: list of dicts with the keyword arguments of stereo_match plus
-    left/right."""
+def _pair_array(pairs):
     arr = (StereoPair * len(pairs))()
     for i, d in enumerate(pairs):
         arr[i] = _pair_struct(**d)
+    return arr
+
+
+def stereo_match_batched(handle: Handle, pairs, use_graph: bool = True, stream=None):
+    """pairs: list of dicts with the keyword arguments of stereo_match plus
+    left/right (per-pair d_min / num_disp / win_radius allowed)."""
+    arr = _pair_array(pairs)
     _check(lib().stereo_match_batched(handle.ptr, arr, len(pairs), int(bool(use_graph)),
                                       _stream(stream)), "stereo_match_batched")
+
+
+def stereo_set_batch_config(handle: Handle, rows: int = 0, K: int = 0):
+    _check(lib().stereo_set_batch_config(handle.ptr, rows, K), "stereo_set_batch_config")
+
+
+def stereo_autotune_batched(handle: Handle, pairs, stream=None):
+    """Times the batched cost stage for each candidate configuration and keeps
+    the fastest; returns dict(rows, K, ms)."""
+    arr = _pair_array(pairs)
+    rows, K, ms = C.c_int32(), C.c_int32(), C.c_float()
+    _check(lib().stereo_autotune_batched(handle.ptr, arr, len(pairs), _stream(stream), C.byref(rows),
+                                         C.byref(K), C.byref(ms)), "stereo_autotune_batched")
+    return dict(rows=rows.value, K=K.value, ms=ms.value)
 
 
 def stereo_get_device_error(handle: Handle, stream=None) -> int:

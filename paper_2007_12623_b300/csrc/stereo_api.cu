@@ -20,6 +20,7 @@
 #include "post_tiled.cuh"
 #include "refine_tiled.cuh"
 #include "soft.cuh"
+#include "batch.cuh"
 
 namespace {
 
@@ -167,6 +168,17 @@ struct stereo_handle {
     size_t pair_bytes;
     uint8_t* ws;         // max_batch * pair_bytes
     int32_t* dev_err;    // device error word
+    // batched form: unit / pair tables (device) and the tuned configuration
+    int4* units = nullptr;
+    CostArgs* pair_args = nullptr;
+    int* pair_radius = nullptr;
+    int* counter = nullptr;
+    size_t max_units = 0;
+    int batch_rows = 0;          // 0 = automatic
+    int batch_K = 0;             // 0 = automatic
+    std::vector<uint8_t> table_key;
+    int n_units = 0;
+    int tables_K = 4;
     bool timing;         // record per-stage events in stereo_match
     bool ev_ready;
     cudaEvent_t ev[STEREO_NUM_STAGES + 1];
@@ -565,6 +577,23 @@ stereo_status stereo_create(const stereo_params* p, int32_t max_batch, stereo_ha
         delete h;
         return STEREO_ERR_OOM;
     }
+    if (max_batch > 1) {
+        // work units of the persistent batched kernel: at most ceil(W/16) column
+        // runs x ceil(H/8) bands x ceil(D/64) chunks per pair
+        h->max_units = (size_t)max_batch * ((p->max_width + 15) / 16) * ((p->max_height + 7) / 8) *
+                       ((p->num_disp + 63) / 64);
+        if (cudaMalloc(&h->units, h->max_units * sizeof(int4)) != cudaSuccess ||
+            cudaMalloc(&h->pair_args, (size_t)max_batch * sizeof(CostArgs)) != cudaSuccess ||
+            cudaMalloc(&h->pair_radius, (size_t)max_batch * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&h->counter, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(h->units); cudaFree(h->pair_args); cudaFree(h->pair_radius); cudaFree(h->counter);
+            cudaFree(h->ws);
+            cudaFree(h->dev_err);
+            delete h;
+            return STEREO_ERR_OOM;
+        }
+    }
     if (cudaMemset(h->dev_err, 0, sizeof(int32_t)) != cudaSuccess) {
         cudaFree(h->ws);
         cudaFree(h->dev_err);
@@ -584,6 +613,10 @@ stereo_status stereo_destroy(stereo_handle* h) {
         for (int i = 0; i <= STEREO_NUM_STAGES; ++i) cudaEventDestroy(h->ev[i]);
     cudaFree(h->ws);
     cudaFree(h->dev_err);
+    if (h->units) cudaFree(h->units);
+    if (h->pair_args) cudaFree(h->pair_args);
+    if (h->pair_radius) cudaFree(h->pair_radius);
+    if (h->counter) cudaFree(h->counter);
     delete h;
     return STEREO_OK;
 }
@@ -728,6 +761,157 @@ stereo_status stereo_set_tuning(const char* name, int32_t value) {
     return STEREO_ERR_INVALID_ARG;
 }
 
+// ---- batched form --------------------------------------------------------
+// Disparity chunk per lane (K) and unit height for a batch: the tuned values
+// when set, else K = 4 unless every pair has at most 64 candidates, and a
+// height from the wave estimate of the largest pair.
+static void batch_config(const stereo_handle* h, const stereo_pair* pairs, int n, int& K, int& rows) {
+    int maxD = 0;
+    for (int i = 0; i < n; ++i) {
+        int d_min, D, r;
+        resolve_pair(h, &pairs[i], d_min, D, r);
+        maxD = std::max(maxD, D);
+    }
+    K = h->batch_K ? h->batch_K : (maxD <= 64 ? 2 : 4);
+    rows = h->batch_rows ? h->batch_rows : 16;
+}
+
+// Builds the unit table and the per-pair kernel arguments for a batch and
+// uploads them (stream-ordered on s; must not run inside a capture).
+static stereo_status build_batch_tables(stereo_handle* h, const stereo_pair* pairs, int n, int K, int rows,
+                                        cudaStream_t s) {
+    std::vector<int4> units;
+    std::vector<CostArgs> args(n);
+    std::vector<int> radius(n);
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        return (long)pairs[a].width * pairs[a].height > (long)pairs[b].width * pairs[b].height;
+    });
+    for (int i = 0; i < n; ++i) {
+        const stereo_pair* pr = &pairs[i];
+        int d_min, D, r;
+        resolve_pair(h, pr, d_min, D, r);
+        const int W = pr->width, H = pr->height;
+        PairWs w = carve(h->ws + (size_t)i * h->pair_bytes, (size_t)W * H, h->p.num_disp, h->p.cost_dtype,
+                         h->p.max_width, h->p.max_height);
+        PrepOut pl, prr;
+        prep_layouts(W, d_min, D, K, w, pl, prr);
+        void* cost = h->p.cost_dtype != CDT_NONE ? w.cost : nullptr;
+        args[i] = CostArgs{pl.img, pl.stride, pl.col0, prr.img, prr.stride, prr.col0, w.lstats, w.ustats,
+                           prr.ustride, prr.ucol0, w.keys, w.keys + (size_t)W * H, cost, h->p.cost_dtype,
+                           W, H, d_min, D, rows};
+        radius[i] = r;
+    }
+    for (int oi = 0; oi < n; ++oi) {
+        const int i = order[oi];
+        const CostArgs& a = args[i];
+        const int r = radius[i];
+        const int TW = cost_run_width(r);
+        const int inner_w = a.W - 2 * r, inner_h = a.H - 2 * r;
+        if (inner_w <= 0 || inner_h <= 0) continue;
+        const int nx = (inner_w + TW - 1) / TW, ny = (inner_h + rows - 1) / rows;
+        const int nz = (a.D + 32 * K - 1) / (32 * K);
+        for (int bz = 0; bz < nz; ++bz)
+            for (int by = 0; by < ny; ++by)
+                for (int bx = 0; bx < nx; ++bx) {
+                    int x0 = r + bx * TW, y0 = r + by * rows;
+                    int partial = 0;
+                    if (x0 + TW > a.W - r) {
+                        const int shifted = a.W - r - TW;
+                        if (shifted >= r && ((shifted - r) & 3) == 0) x0 = shifted;
+                        else partial = 1;
+                    }
+                    if (inner_h >= rows) y0 = std::min(y0, a.H - r - rows);
+                    units.push_back(make_int4(i, x0, y0, bz | (partial << 16)));
+                }
+    }
+    if (units.size() > h->max_units) return STEREO_ERR_TOO_LARGE;
+    if (!units.empty() &&
+        cudaMemcpyAsync(h->units, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return last_error();
+    if (cudaMemcpyAsync(h->pair_args, args.data(), n * sizeof(CostArgs), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(h->pair_radius, radius.data(), n * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return last_error();
+    cudaStreamSynchronize(s);           // host vectors go out of scope
+    h->n_units = (int)units.size();
+    h->tables_K = K;
+    return STEREO_OK;
+}
+
+// Whole path for a batch: per pair input conversion, statistics and border
+// costs; one persistent launch of the cost kernel over all pairs' units; then
+// per pair finalize, post-processing and refinement.
+static void enqueue_batched(stereo_handle* h, const stereo_pair* pairs, int n, cudaStream_t s,
+                            bool cost_only = false) {
+    const int K = h->tables_K;
+    for (int i = 0; i < n && !cost_only; ++i) {
+        const stereo_pair* pr = &pairs[i];
+        int d_min, D, r;
+        resolve_pair(h, pr, d_min, D, r);
+        const int W = pr->width, H = pr->height;
+        PairWs w = carve(h->ws + (size_t)i * h->pair_bytes, (size_t)W * H, h->p.num_disp, h->p.cost_dtype,
+                         h->p.max_width, h->p.max_height);
+        const uint8_t* gl = pr->left;
+        const uint8_t* gr = pr->right;
+        dim3 g((W + 127) / 128, H);
+        if (pr->channels == 3 || pr->pitch != W) {
+            if (pr->channels == 3) {
+                k_gray<<<g, 128, 0, s>>>(pr->left, W, H, pr->pitch, w.gl);
+                k_gray<<<g, 128, 0, s>>>(pr->right, W, H, pr->pitch, w.gr);
+            } else {
+                k_copy_pitched<<<g, 128, 0, s>>>(pr->left, W, H, pr->pitch, w.gl);
+                k_copy_pitched<<<g, 128, 0, s>>>(pr->right, W, H, pr->pitch, w.gr);
+            }
+            counted(2);
+            gl = w.gl;
+            gr = w.gr;
+        }
+        PrepOut pl, prr;
+        prep_layouts(W, d_min, D, K, w, pl, prr);
+        dim3 sg((W + PT - 1) / PT, (H + PT - 1) / PT);
+        k_prep<<<sg, 256, 0, s>>>(gl, W, H, r, pl, w.keys);
+        k_prep<<<sg, 256, 0, s>>>(gr, W, H, r, prr, nullptr);
+        counted(2);
+        if (h->p.cost_dtype != CDT_NONE) {
+            const long nb = (W <= 2 * r || H <= 2 * r) ? (long)W * H : 2L * r * W + 2L * r * (H - 2 * r);
+            k_cost_border_nan<<<(int)std::max<long>(1, std::min<long>(4096, (nb * cost_stride(D) + 255) / 256)),
+                                256, 0, s>>>(w.cost, h->p.cost_dtype, W, H, r, cost_stride(D));
+            counted();
+        }
+    }
+    cudaMemsetAsync(h->counter, 0, sizeof(int), s);
+    if (K == 4) launch_cost_batched_k4(h->p.cost_dtype, h->pair_args, h->pair_radius, h->units, h->n_units,
+                                       h->counter, s);
+    else launch_cost_batched_k2(h->p.cost_dtype, h->pair_args, h->pair_radius, h->units, h->n_units,
+                                h->counter, s);
+    counted();
+    if (cost_only) return;
+    for (int i = 0; i < n; ++i) {
+        const stereo_pair* pr = &pairs[i];
+        int d_min, D, r;
+        resolve_pair(h, pr, d_min, D, r);
+        const int W = pr->width, H = pr->height;
+        const int cdt = h->p.cost_dtype;
+        PairWs w = carve(h->ws + (size_t)i * h->pair_bytes, (size_t)W * H, h->p.num_disp, cdt,
+                         h->p.max_width, h->p.max_height);
+        const uint8_t* gl = (pr->channels == 3 || pr->pitch != W) ? w.gl : pr->left;
+        const uint8_t* gr = (pr->channels == 3 || pr->pitch != W) ? w.gr : pr->right;
+        void* cost = cdt != CDT_NONE ? w.cost : nullptr;
+        int16_t* wta = pr->disp_wta ? pr->disp_wta : w.wta;
+        dim3 fg((W + 127) / 128, H);
+        k_finalize<<<fg, 128, 0, s>>>(w.keys, w.keys + (size_t)W * H, W, H, d_min, D, h->p.lr_thresh, cost,
+                                      cdt, gl, gr, r, h->p.sampling, wta, nullptr, pr->disp_sub, w.lr);
+        counted();
+        if (pr->disp_lr) cudaMemcpyAsync(pr->disp_lr, w.lr, (size_t)W * H * 2, cudaMemcpyDeviceToDevice, s);
+        int16_t* post = pr->disp_post ? pr->disp_post : w.post;
+        run_postprocess(h->p, w.lr, W, H, w, post, s);
+        float* dfin = pr->disp_final ? pr->disp_final : w.dfin;
+        run_refine(h->p, post, cost, cdt, gl, gr, W, H, d_min, D, r, h->p.sampling, w, dfin, nullptr,
+                   pr->valid, s);
+    }
+}
+
 stereo_status stereo_match(stereo_handle* h, const stereo_pair* pr, void* stream) {
     int d_min, D, r;
     stereo_status st = resolve_pair(h, pr, d_min, D, r);
@@ -867,14 +1051,95 @@ stereo_status stereo_l1_loss(stereo_handle* h, const float* d_soft, const float*
 
 stereo_status stereo_match_batched(stereo_handle* h, const stereo_pair* pairs, int32_t n,
                                    int32_t use_graph, void* stream) {
-    (void)use_graph;
     if (!h || !pairs || n < 1) return STEREO_ERR_INVALID_ARG;
     if (n > h->max_batch) return STEREO_ERR_TOO_LARGE;
     for (int i = 0; i < n; ++i) {
-        stereo_status st = stereo_match(h, &pairs[i], stream);
+        int d_min, D, r;
+        stereo_status st = resolve_pair(h, &pairs[i], d_min, D, r);
         if (st != STEREO_OK) return st;
     }
+    cudaStream_t s = S(stream);
+    if (n == 1 || !h->units) {                 // a single pair: the one-pair path
+        return n == 1 ? stereo_match(h, pairs, stream) : STEREO_ERR_INVALID_ARG;
+    }
+    int K, rows;
+    batch_config(h, pairs, n, K, rows);
+    // the tables depend on the pairs' geometry and pointers and the configuration
+    std::vector<uint8_t> key(reinterpret_cast<const uint8_t*>(pairs),
+                             reinterpret_cast<const uint8_t*>(pairs) + n * sizeof(stereo_pair));
+    const int cfg[3] = {K, rows, g_cost_rows};
+    key.insert(key.end(), reinterpret_cast<const uint8_t*>(cfg), reinterpret_cast<const uint8_t*>(cfg) + sizeof(cfg));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (s != nullptr) cudaStreamIsCapturing(s, &cs);
+    if (key != h->table_key) {
+        if (cs != cudaStreamCaptureStatusNone) return STEREO_ERR_UNSUPPORTED;   // cannot upload while captured
+        stereo_status st = build_batch_tables(h, pairs, n, K, rows, s);
+        if (st != STEREO_OK) return st;
+        h->table_key = key;
+    }
+    if (!use_graph) {
+        enqueue_batched(h, pairs, n, s);
+        return last_error();
+    }
+    return run_with_graph(h, h->batch, key.data(), key.size(), s, [&](cudaStream_t cs2) {
+        const unsigned long long b0 = g_launches.load();
+        enqueue_batched(h, pairs, n, cs2);
+        h->batch.kernels = g_launches.load() - b0;
+    });
+}
+
+stereo_status stereo_set_batch_config(stereo_handle* h, int32_t rows, int32_t K) {
+    if (!h || rows < 0 || rows > 4096 || (K != 0 && K != 2 && K != 4)) return STEREO_ERR_INVALID_ARG;
+    h->batch_rows = rows;
+    h->batch_K = K;
     return STEREO_OK;
+}
+
+stereo_status stereo_autotune_batched(stereo_handle* h, const stereo_pair* pairs, int32_t n, void* stream,
+                                      int32_t* best_rows, int32_t* best_K, float* best_ms) {
+    if (!h || !pairs || n < 2 || n > h->max_batch || !h->units) return STEREO_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        int d_min, D, r;
+        stereo_status st = resolve_pair(h, &pairs[i], d_min, D, r);
+        if (st != STEREO_OK) return st;
+    }
+    cudaStream_t s = S(stream);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (s != nullptr) cudaStreamIsCapturing(s, &cs);
+    if (cs != cudaStreamCaptureStatusNone) return STEREO_ERR_UNSUPPORTED;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int rows_c[] = {8, 12, 16, 24, 32, 48};
+    const int K_c[] = {2, 4};
+    float best = 1e30f;
+    int br = 16, bk = 4;
+    for (int K : K_c) {
+        for (int rows : rows_c) {
+            stereo_status st = build_batch_tables(h, pairs, n, K, rows, s);
+            if (st != STEREO_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+            enqueue_batched(h, pairs, n, s);               // full pass: inputs for this K
+            float ms = 0.f, sum = 0.f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, s);
+                enqueue_batched(h, pairs, n, s, true);       // the batched cost stage alone
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);
+                sum += ms;
+            }
+            if (sum / 3 < best) { best = sum / 3; br = rows; bk = K; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->batch_rows = br;
+    h->batch_K = bk;
+    h->table_key.clear();                                  // rebuild with the choice on next use
+    if (best_rows) *best_rows = br;
+    if (best_K) *best_K = bk;
+    if (best_ms) *best_ms = best;
+    return last_error();
 }
 
 }  // extern "C"
