@@ -83,7 +83,7 @@ def _bumps(rng, H, W, n, sig_lo, sig_hi):
 
 # ------------------------------------------------------------ right view
 
-def render_right(left: np.ndarray, disp: np.ndarray, iters: int = 30) -> np.ndarray:
+def render_right(left: np.ndarray, disp: np.ndarray, iters: int = 12) -> np.ndarray:
     """Backward-warp the left view into the right view.
 
     A left pixel x with disparity d(x) appears at x - d(x) in the right view, so
@@ -129,6 +129,16 @@ def perlin_pair(seed: int, W: int = 320, H: int = 240):
     return L, R, gt
 
 
+def _smooth_coarse(a, sigma, f=4):
+    """Gaussian blur of width sigma computed on an f-times coarser grid."""
+    H, W = a.shape
+    Hc, Wc = (H + f - 1) // f, (W + f - 1) // f
+    pad = np.pad(a, ((0, Hc * f - H), (0, Wc * f - W)), mode="edge")
+    c = pad.reshape(Hc, f, Wc, f).mean(axis=(1, 3))
+    c = ndimage.gaussian_filter(c, sigma / f)
+    return ndimage.zoom(c, f, order=1)[:H, :W]
+
+
 def tissue_texture(rng, H, W):
     """Gray tissue-like texture in [0, 255]: band-limited noise with 40..80
     smooth vessel ridges (Gaussian cross-section, amplitude -40..-80) and 30 %
@@ -163,10 +173,11 @@ def tissue_texture(rng, H, W):
             # cross-section of peak A / (sqrt(2 pi) w); rescale to peak A.
             tex -= ndimage.gaussian_filter(mask, width) * np.sqrt(2 * np.pi) * width
     # low-texture blobs covering 30 % of the area, blended to smooth shading
-    blob = ndimage.gaussian_filter(rng.normal(0, 1, (H, W)), max(6.0, 25.0 * scale))
+    # (the wide blurs run on a 4x coarser grid and are upsampled)
+    blob = _smooth_coarse(rng.normal(0, 1, (H, W)), max(6.0, 25.0 * scale))
     thr = np.quantile(blob, 0.70)
     wgt = np.clip((blob - thr) / (blob.std() * 0.15 + 1e-12), 0, 1)
-    smooth = ndimage.gaussian_filter(tex, max(4.0, 12.0 * scale))
+    smooth = _smooth_coarse(tex, max(4.0, 12.0 * scale))
     tex = tex * (1 - wgt) + smooth * wgt
     return np.clip(tex, 0, 255)
 
@@ -198,3 +209,25 @@ def tissue_pair(seed: int, W: int = 960, H: int = 540, disp_lo: float = 10.0,
     L = np.clip(np.rint(chan), 0, 255).astype(np.uint8)
     R = np.clip(np.rint(right), 0, 255).astype(np.uint8)
     return L, R, gt
+
+
+# ------------------------------------------------------------ batch workload
+
+BATCH_SIZES = ((640, 480), (960, 540), (1280, 720), (1920, 1080))
+
+
+def batch_pair_spec(i: int):
+    """Pair i of the 64-pair mixed batch: 16 pairs of each size, disparity
+    range drawn from {64, 128, 192} and window radius from {4, 5, 7} by the
+    pair's seed, ground truth mapped to [0.08 D, 0.86 D]."""
+    W, H = BATCH_SIZES[(i // 16) % 4]
+    rng = np.random.default_rng(seed_for(3, i))
+    D = int(rng.choice([64, 128, 192]))
+    r = int(rng.choice([4, 5, 7]))
+    return dict(W=W, H=H, D=D, r=r, seed=seed_for(3, i), lo=0.08 * D, hi=0.86 * D)
+
+
+def batch_pair(i: int):
+    sp = batch_pair_spec(i)
+    L, R, gt = tissue_pair(sp["seed"], sp["W"], sp["H"], sp["lo"], sp["hi"])
+    return L, R, gt, sp
