@@ -2,20 +2,38 @@
 """Benchmark of the dense stereo-matching path (arXiv 2007.12623, Sec. II) on
 B300.
 
-One step = the whole path on one 960x540 RGB tissue pair (D = 128, 11x11
-ZNCC window, FP32 cost volume, LR check, 3 outlier/hole-filling rounds,
-5 refinement iterations with radius 15): gray -> window statistics ->
-fused ZNCC + winner-take-all (left and right) + cost store -> sub-pixel / LR
--> outlier + hole filling -> improved Laplacian refinement.
+Default workload (``tissue960``): one step = the whole path on one 960x540 RGB
+tissue pair (D = 128, 11x11 ZNCC window, FP32 cost volume, LR check, 3
+outlier/hole-filling rounds, 5 refinement iterations with radius 15): gray ->
+window statistics -> fused ZNCC + winner-take-all (left and right) + cost
+store -> sub-pixel / LR -> outlier + hole filling -> improved Laplacian
+refinement.
+
+Other workloads (``--workload``):
+  tissue960_d192_f16 / _bf16  same generator, D = 192, 15x15 window, cost
+                              volume stored in FP16 / BF16 (their disparity
+                              error against the FP64 oracle is measured by
+                              tests/test_gpu_precision.py).
+  batch64                     64 pairs of mixed sizes (16 each of 640x480,
+                              960x540, 1280x720, 1920x1080), D in {64,128,192},
+                              windows {9,11,15}, FP16 cost: one
+                              stereo_match_batched call per step (one
+                              persistent cost launch, graph-replayed),
+                              configuration from the autotuner.
+  soft8                       soft-argmin form: 8 pairs at 960x540, D = 128,
+                              11x11, tau = 0.1; a step is forward + L1 loss +
+                              hand-written backward to both images through
+                              torch.autograd.
+  perlin320                   the small 320x240 gray Perlin pair (D = 32).
 
 Prints one JSON line (rank 0).  ``value`` is pixel-disparity evaluations per
-second of the whole path (Gpix*disp/s) with inputs resident in device memory;
-``e2e`` is the same metric through stereo_match with the RGB pair copied from
-pinned host memory and the refined disparity copied back inside the timed
-region.  ``--impl reference`` times the FP64 CPU oracle on a bounded sample
-of the same workload instead.
+second of the whole step (Gpix*disp/s) with inputs resident in device memory;
+``e2e`` is the same metric through the public API with the inputs copied from
+pinned host memory and the result copied back inside the timed region.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
+workload instead.
 
-Multi-GPU: one process per GPU (torchrun); every rank matches its own pair
+Multi-GPU: one process per GPU (torchrun); every rank matches its own pairs
 (independent problems, no collective), ``scaling`` is weak.
 """
 from __future__ import annotations
@@ -38,26 +56,34 @@ import synth  # noqa: E402
 
 WORKLOADS = {
     # 960x540 RGB tissue pair, D = 0..127, 11x11 window, FP32 cost, full post-processing
-    "tissue960": dict(W=960, H=540, D=128, r=5, cost="f32", smooth_radius=15, seed=synth.seed_for(1),
-                      disp=(10.0, 110.0)),
-    # 960x540, D = 0..191, 15x15 window, FP16 cost storage
-    "tissue960_d192_f16": dict(W=960, H=540, D=192, r=7, cost="f16", smooth_radius=15,
+    "tissue960": dict(kind="single", W=960, H=540, D=128, r=5, cost="f32", smooth_radius=15,
+                      seed=synth.seed_for(1), disp=(10.0, 110.0)),
+    # 960x540, D = 0..191, 15x15 window, FP16 / BF16 cost storage
+    "tissue960_d192_f16": dict(kind="single", W=960, H=540, D=192, r=7, cost="f16", smooth_radius=15,
                                seed=synth.seed_for(2), disp=(10.0, 170.0)),
-    "tissue960_d192_bf16": dict(W=960, H=540, D=192, r=7, cost="bf16", smooth_radius=15,
+    "tissue960_d192_bf16": dict(kind="single", W=960, H=540, D=192, r=7, cost="bf16", smooth_radius=15,
                                 seed=synth.seed_for(2), disp=(10.0, 170.0)),
+    # 64 mixed pairs in one batched call, FP16 cost
+    "batch64": dict(kind="batched", n=64, cost="f16", smooth_radius=15),
+    # soft-argmin training step on 8 pairs
+    "soft8": dict(kind="soft", B=8, W=960, H=540, D=128, r=5, tau=0.1, seed=synth.seed_for(4),
+                  disp=(10.0, 110.0)),
     # 320x240 gray Perlin pair, D = 0..31, 5x5 smoothing
-    "perlin320": dict(W=320, H=240, D=32, r=5, cost="f32", smooth_radius=2, seed=synth.seed_for(0),
-                      disp=None),
+    "perlin320": dict(kind="single", W=320, H=240, D=32, r=5, cost="f32", smooth_radius=2,
+                      seed=synth.seed_for(0), disp=None),
 }
 COST_CODE = {"none": 0, "f32": 1, "f16": 2, "bf16": 3}
-# DRAM bytes (read + write) of one k_cost_wta launch from an ncu capture of the
-# current kernel on the same workload (profiles/k_cost_wta_<workload>.md);
-# None where no capture of the current kernel exists.
-COST_KERNEL_TRAFFIC = {"tissue960": 226.3e6}
+# DRAM bytes (read + write) of one launch of the workload's dominant kernel
+# from an ncu capture of the current kernel (profiles/<kernel>_<workload>.md);
+# absent where no capture of the current kernel exists.
+KERNEL_TRAFFIC = {"tissue960": 226.3e6}
 COST_BYTES = {"none": 0, "f32": 4, "f16": 2, "bf16": 2}
 METRIC = "Gpix*disp/s and ms per 960x540 pair (1 B300), % of roofline, vs oracle"
 UNIT = "Gpix*disp/s"
 L2_BYTES = 126 * 2 ** 20
+PAPER_CONTEXT = {"ms_per_keyframe_whole_pipeline": 76.3, "stereo_stage_ms": 15.9,
+                 "zncc_ms_960x540x100": 5.0,
+                 "hardware": "NVIDIA Titan X + Xeon X5472 (paper, Table III)"}
 
 
 def load_peaks():
@@ -76,6 +102,19 @@ def make_pair(wl, pair_index=0):
         L, R, gt = synth.perlin_pair(wl["seed"] + pair_index, wl["W"], wl["H"])
         return np.stack([L] * 3, -1), np.stack([R] * 3, -1), gt
     return synth.tissue_pair(wl["seed"] + pair_index, wl["W"], wl["H"], *wl["disp"])
+
+
+def _batch_pair(i):
+    return synth.batch_pair(i)
+
+
+def make_batch(n, first):
+    """Pairs first..first+n-1 of the mixed batch, generated by a spawn pool
+    (started before any CUDA call)."""
+    import multiprocessing as mp
+    procs = max(1, min(n, os.cpu_count() or 1, 32))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_batch_pair, range(first, first + n))
 
 
 class ClockSampler:
@@ -111,7 +150,7 @@ class ClockSampler:
         t0 = time.time()
         n0 = len(self.lines)
         while self.proc and len(self.lines) <= n0 and time.time() - t0 < timeout:
-            for _ in range(20):
+            for _ in range(5):
                 busy()
 
     def __exit__(self, *a):
@@ -145,23 +184,23 @@ class ClockSampler:
 
 # --------------------------------------------------------------- roofline
 
-def cost_kernel_roofline(wl, cost_ms, peaks, sm_count, sm_mhz, traffic=None):
-    """Roofline of the fused cost + winner-take-all kernel.
+def cost_kernel_roofline(problems, cost_ms, peaks, sm_count, kernel, traffic=None):
+    """Roofline of the fused cost + winner-take-all kernel over `problems`
+    (list of (W, H, D, r, cost storage)) done by one launch.
 
-    Algorithmic work per pixel-disparity (p,d): 12 FP32/INT32 issue slots
-    (1 product, 2 vertical + 2 horizontal sliding-sum updates, 2 for the
-    numerator, 2 for rho, 2 for the winner compare/select, 1 for the store
-    conversion) and s bytes of cost store (s = 4 FP32, 2 FP16/BF16).  Per
+    Algorithmic work per pixel-disparity (p,d) with a full window: 12 FP32/INT32
+    issue slots (1 product, 2 vertical + 2 horizontal sliding-sum updates, 2
+    for the numerator, 2 for rho, 2 for the winner compare/select, 1 for the
+    store conversion) and s bytes of cost store (s = 4 FP32, 2 FP16/BF16).  Per
     pixel it also reads both gray images (2 B), both statistics maps (16 B) and
     writes both key maps (8 B).  The bound is whichever of the ALU time (12 ops
     on 128 lanes per SM per clock) and the HBM time is longer.
     """
-    W, H, D = wl["W"], wl["H"], wl["D"]
-    r = wl["r"]
-    npix = (W - 2 * r) * (H - 2 * r)
-    P = npix * D
-    bytes_ = P * COST_BYTES[wl["cost"]] + W * H * (2 + 16 + 8)
-    ops = 12 * P
+    bytes_, ops = 0, 0
+    for W, H, D, r, cost in problems:
+        P = (W - 2 * r) * (H - 2 * r) * D
+        bytes_ += P * COST_BYTES[cost] + W * H * (2 + 16 + 8)
+        ops += 12 * P
     t_hbm = bytes_ / (peaks["hbm_gbs"] * 1e9)
     alu_peak = sm_count * 128 * peaks["sm_max_mhz"] * 1e6          # ops/s at max clock
     t_alu = ops / alu_peak
@@ -170,25 +209,109 @@ def cost_kernel_roofline(wl, cost_ms, peaks, sm_count, sm_mhz, traffic=None):
         achieved = bytes_ / dur / 1e9
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
-                "kernel": "k_cost_wta", "algorithmic_bytes": bytes_,
-                "peak_source": peaks["source"] + " (hbm_gbs)"}
+                "kernel": kernel, "algorithmic_bytes": bytes_, "algorithmic_ops": ops,
+                "kernel_ms": round(cost_ms, 4), "peak_source": peaks["source"] + " (hbm_gbs)"}
     achieved = ops / dur / 1e12
     return {"bound": "alu", "achieved": round(achieved, 2), "peak": round(alu_peak / 1e12, 2),
             "unit": "Tops/s", "frac": round(achieved / (alu_peak / 1e12), 4), "traffic": traffic,
-            "kernel": "k_cost_wta", "algorithmic_ops": ops,
+            "kernel": kernel, "algorithmic_ops": ops, "algorithmic_bytes": bytes_,
+            "kernel_ms": round(cost_ms, 4),
             "peak_source": f"{sm_count} SMs x 128 lanes x {peaks['sm_max_mhz']:.0f} MHz"}
 
 
-# ------------------------------------------------------------- our arm
+def soft_roofline(stage_ms, W, H, D, peaks, traffic=None):
+    """Roofline of the dominant soft-argmin backward kernel (both are
+    HBM-bound streams):
+      k_soft_dA      reads the FP32 cost volume and writes the A volume
+                     (8 B per (p,d)), per pixel reads g, d_soft, lse and the
+                     left statistics (20 B) and writes P1, P2, Q1, Q2 (16 B);
+      k_soft_box_t1  reads the A volume once (4 B per (p,d)), per pixel reads
+                     both images (8 B) and adds into T1L, T1R (8 B)."""
+    P, npix = W * H * D, W * H
+    if stage_ms["dA"] >= stage_ms["box_t1"]:
+        name, ms, b = "k_soft_dA", stage_ms["dA"], 8 * P + 36 * npix
+    else:
+        name, ms, b = "k_soft_box_t1", stage_ms["box_t1"], 4 * P + 16 * npix
+    achieved = b / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic, "kernel": name,
+            "algorithmic_bytes": b, "kernel_ms": round(ms, 4),
+            "peak_source": peaks["source"] + " (hbm_gbs)"}
 
-def run_ours(args, wl, rank, world):
+
+# ------------------------------------------------------------- helpers
+
+def _timed_loop(torch, stream, steps, step, flush):
+    """Times `steps` calls of step() on `stream` with CUDA events, flushing L2
+    (untimed) before each; returns per-step ms."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def _e2e_loop(torch, stream, steps, warmup, step, flush):
+    for _ in range(max(1, warmup)):
+        step()
+    torch.cuda.synchronize()
+    out = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        out.append(a.elapsed_time(b))
+    return out
+
+
+def _max_over_ranks(torch, dev, x, world):
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _stage_pass(st, h, n, flush, step, names):
+    st.stereo_set_stage_timing(h, True)
+    acc = {k: 0.0 for k in names}
+    for i in range(n):
+        flush.fill_(float(i))
+        step()
+        ms = st.stereo_get_stage_times(h)
+        for k, v in zip(names, ms.values()):
+            acc[k] += v
+    st.stereo_set_stage_timing(h, False)
+    return {k: v / n for k, v in acc.items()}
+
+
+def _base_line(args, world, value, t_max, dtype, config):
+    return {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t_max * 1e3 / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic (seeded tissue-texture generator standing in for the paper's videos)",
+            "config": config}
+
+
+# ------------------------------------------------------------- our arm: one pair
+
+def run_single(args, wl, rank, world, dev):
     import torch
     import paper_2007_12623_b300 as st
 
-    dev = torch.device(f"cuda:{int(os.environ.get('LOCAL_RANK', 0))}")
-    torch.cuda.set_device(dev)
     W, H, D = wl["W"], wl["H"], wl["D"]
     Lrgb, Rrgb, gt = make_pair(wl, rank)
+    stream = torch.cuda.Stream(dev)          # non-default stream: graph capture + replay
+    torch.cuda.set_stream(stream)
     tL = torch.from_numpy(Lrgb).to(dev)
     tR = torch.from_numpy(Rrgb).to(dev)
     sp = st.stereo_default_params(max_width=W, max_height=H, num_disp=D, win_radius=wl["r"],
@@ -199,7 +322,6 @@ def run_ours(args, wl, rank, world):
                 valid=torch.empty((H, W), dtype=torch.uint8, device=dev),
                 disp_final=torch.empty((H, W), dtype=torch.float32, device=dev))
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
 
     def step():
         st.stereo_match(h, tL, tR, **outs, stream=stream)
@@ -210,39 +332,17 @@ def run_ours(args, wl, rank, world):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    launches0 = st.stereo_launch_count()
     with ClockSampler(dev.index) as clk:
-        clk.wait_first_sample(lambda: step())   # keep the GPU busy until sampling starts
-        launches0 = st.stereo_launch_count()
-        for i in range(args.steps):
-            flush.fill_(float(i))            # evict L2 between timed steps (not timed)
-            ev[i][0].record(stream)
-            step()
-            ev[i][1].record(stream)
+        clk.wait_first_sample(step)          # keep the GPU busy until sampling starts
         torch.cuda.synchronize()
+        launches0 = st.stereo_launch_count()
+        step_ms = _timed_loop(torch, stream, args.steps, step, flush)
     launches = st.stereo_launch_count() - launches0
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_local = sum(step_ms) / 1e3
-    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    t_max = float(t.item())
+    t_max = _max_over_ranks(torch, dev, sum(step_ms) / 1e3, world)
     P = W * H * D
     value = world * args.steps * P / t_max / 1e9
 
-    # per-stage times (separate, untimed-for-value runs with events between stages)
-    st.stereo_set_stage_timing(h, True)
-    nst = min(args.steps, 20)
-    stage_sum = {n: 0.0 for n in st.STAGE_NAMES}
-    for i in range(nst):
-        flush.fill_(float(i))
-        step()
-        for k, v in st.stereo_get_stage_times(h).items():
-            stage_sum[k] += v
-    st.stereo_set_stage_timing(h, False)
-    stage_ms = {k: v / nst for k, v in stage_sum.items()}
+    stage_ms = _stage_pass(st, h, min(args.steps, 20), flush, step, st.STAGE_NAMES)
 
     # end to end through the public API: pinned host RGB in, refined map out
     hL = torch.from_numpy(Lrgb).pin_memory()
@@ -257,96 +357,293 @@ def run_ours(args, wl, rank, world):
         st.stereo_match(h, dL, dR, disp_final=outs["disp_final"], valid=outs["valid"], stream=stream)
         hout.copy_(outs["disp_final"], non_blocking=True)
 
-    for _ in range(max(1, args.warmup)):
-        e2e_step()
-    torch.cuda.synchronize()
-    e_ms = []
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        e2e_step()
-        b.record(stream)
-        b.synchronize()
-        e_ms.append(a.elapsed_time(b))
-    te = torch.tensor([sum(e_ms) / 1e3], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = world * args.steps * P / float(te.item()) / 1e9
-    h.close()
+    e_ms = _e2e_loop(torch, stream, args.steps, args.warmup, e2e_step, flush)
+    te = _max_over_ranks(torch, dev, sum(e_ms) / 1e3, world)
+    e2e_value = world * args.steps * P / te / 1e9
 
+    h.close()
     if rank != 0:
         return None
     peaks = load_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    clocks = clk.summary()
-    roof = cost_kernel_roofline(wl, stage_ms["cost_wta"], peaks, sm_count, clocks.get("sm_mhz"),
-                                COST_KERNEL_TRAFFIC.get(args.workload))
-    line = {
-        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max * 1e3 / args.steps, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded tissue-texture generator standing in for the paper's videos)",
-        "config": {"workload": args.workload, "width": W, "height": H, "num_disp": D,
-                   "window": 2 * wl["r"] + 1, "cost_storage": wl["cost"],
-                   "smooth_radius": wl["smooth_radius"], "refine_iters": 5, "pairs_per_gpu": 1,
-                   "parallelism": f"replicas x{world} (independent pairs)",
-                   "l2": "flushed between timed steps (256 MB write, untimed)"},
+    roof = cost_kernel_roofline([(W, H, D, wl["r"], wl["cost"])], stage_ms["cost_wta"], peaks, sm_count,
+                                "k_cost_wta", KERNEL_TRAFFIC.get(args.workload))
+    line = _base_line(args, world, value, t_max, "f32", {
+        "workload": args.workload, "width": W, "height": H, "num_disp": D, "window": 2 * wl["r"] + 1,
+        "cost_storage": wl["cost"], "smooth_radius": wl["smooth_radius"], "refine_iters": 5,
+        "pairs_per_gpu": 1, "parallelism": f"replicas x{world} (independent pairs)",
+        "l2": "flushed between timed steps (256 MB write, untimed)",
+        "launch": "CUDA graph replay on a non-default stream"})
+    line.update({
         "ms_per_pair": round(t_max * 1e3 / args.steps, 4),
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "roofline": roof,
-        "e2e": {"value": round(e2e_value, 3), "unit": UNIT,
-                "ms_per_pair": round(float(te.item()) * 1e3 / args.steps, 4),
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "ms_per_pair": round(te * 1e3 / args.steps, 4),
                 "h2d_bytes_per_step": 2 * W * H * 3, "d2h_bytes_per_step": W * H * 4},
         "gpu_launches": int(launches),
-        "clocks": clocks,
-        "paper_context": {"ms_per_keyframe_whole_pipeline": 76.3, "stereo_stage_ms": 15.9,
-                          "zncc_ms_960x540x100": 5.0,
-                          "hardware": "NVIDIA Titan X + Xeon X5472 (paper, Table III)"},
-    }
+        "clocks": clk.summary(),
+        "paper_context": PAPER_CONTEXT,
+    })
+    return line
+
+
+# ------------------------------------------------------------- our arm: batch
+
+def run_batched(args, wl, rank, world, dev, pairs):
+    import torch
+    import paper_2007_12623_b300 as st
+
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    n = len(pairs)
+    specs = [p[3] for p in pairs]
+    maxW = max(s["W"] for s in specs)
+    maxH = max(s["H"] for s in specs)
+    maxD = max(s["D"] for s in specs)
+    sp = st.stereo_default_params(max_width=maxW, max_height=maxH, num_disp=maxD,
+                                  cost_dtype=COST_CODE[wl["cost"]], smooth_radius=wl["smooth_radius"])
+    h = st.stereo_create(sp, max_batch=n)
+    batch, host = [], []
+    for (Lrgb, Rrgb, gt, s) in pairs:
+        H, W = Lrgb.shape[:2]
+        batch.append(dict(left=torch.from_numpy(Lrgb).to(dev), right=torch.from_numpy(Rrgb).to(dev),
+                          d_min=0, num_disp=s["D"], win_radius=s["r"],
+                          disp_wta=torch.empty((H, W), dtype=torch.int16, device=dev),
+                          disp_sub=torch.empty((H, W), dtype=torch.float32, device=dev),
+                          valid=torch.empty((H, W), dtype=torch.uint8, device=dev),
+                          disp_final=torch.empty((H, W), dtype=torch.float32, device=dev)))
+        host.append((torch.from_numpy(Lrgb).pin_memory(), torch.from_numpy(Rrgb).pin_memory(),
+                     torch.empty((H, W), dtype=torch.float32).pin_memory()))
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    tune = st.stereo_autotune_batched(h, batch, stream=stream)
+
+    def step():
+        st.stereo_match_batched(h, batch, use_graph=True, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        clk.wait_first_sample(step)
+        torch.cuda.synchronize()
+        launches0 = st.stereo_launch_count()
+        step_ms = _timed_loop(torch, stream, args.steps, step, flush)
+    launches = st.stereo_launch_count() - launches0
+    t_max = _max_over_ranks(torch, dev, sum(step_ms) / 1e3, world)
+    P = sum(s["W"] * s["H"] * s["D"] for s in specs)
+    value = world * args.steps * P / t_max / 1e9
+    stage_ms = _stage_pass(st, h, min(args.steps, 5), flush, step, st.STAGE_NAMES)
+
+    def e2e_step():
+        for b, (hL, hR, _) in zip(batch, host):
+            b["left"].copy_(hL, non_blocking=True)
+            b["right"].copy_(hR, non_blocking=True)
+        st.stereo_match_batched(h, batch, use_graph=True, stream=stream)
+        for b, (_, _, ho) in zip(batch, host):
+            ho.copy_(b["disp_final"], non_blocking=True)
+
+    e_ms = _e2e_loop(torch, stream, args.steps, args.warmup, e2e_step, flush)
+    te = _max_over_ranks(torch, dev, sum(e_ms) / 1e3, world)
+    e2e_value = world * args.steps * P / te / 1e9
+    h.close()
+    if rank != 0:
+        return None
+    peaks = load_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof = cost_kernel_roofline([(s["W"], s["H"], s["D"], s["r"], wl["cost"]) for s in specs],
+                                stage_ms["cost_wta"], peaks, sm_count, "k_cost_batched",
+                                KERNEL_TRAFFIC.get(args.workload))
+    eq = 960 * 540 * 128 / P                      # one 960x540x128 pair's share of the work
+    line = _base_line(args, world, value, t_max, "f32", {
+        "workload": args.workload, "pairs": n,
+        "sizes": "16 each of 640x480, 960x540, 1280x720, 1920x1080",
+        "num_disp": sorted({s["D"] for s in specs}), "windows": sorted({2 * s["r"] + 1 for s in specs}),
+        "cost_storage": wl["cost"], "smooth_radius": wl["smooth_radius"], "refine_iters": 5,
+        "pix_disp_per_step": P, "parallelism": f"replicas x{world} (independent batches)",
+        "l2": "flushed between timed steps (256 MB write, untimed); working set >> L2",
+        "launch": "one stereo_match_batched per step, CUDA graph replay, persistent cost launch",
+        "autotuned": tune})
+    line.update({
+        "ms_per_960x540x128_equivalent": round(t_max * 1e3 / args.steps * eq, 4),
+        "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "roofline": roof,
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "ms_per_step": round(te * 1e3 / args.steps, 4),
+                "h2d_bytes_per_step": sum(2 * s["W"] * s["H"] * 3 for s in specs),
+                "d2h_bytes_per_step": sum(s["W"] * s["H"] * 4 for s in specs)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "paper_context": PAPER_CONTEXT,
+    })
+    return line
+
+
+# ------------------------------------------------------------- our arm: soft
+
+def _gray_f32(rgb):
+    """ITU-R 601 luma in float (the soft-argmin form takes float images)."""
+    return (rgb[..., 0] * 0.299 + rgb[..., 1] * 0.587 + rgb[..., 2] * 0.114).astype(np.float32)
+
+
+def run_soft_step(args, wl, rank, world, dev):
+    import torch
+    import paper_2007_12623_b300 as st
+
+    B, W, H, D, r, tau = wl["B"], wl["W"], wl["H"], wl["D"], wl["r"], wl["tau"]
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    data = [synth.tissue_pair(wl["seed"] + rank * B + b, W, H, *wl["disp"]) for b in range(B)]
+    hL = torch.from_numpy(np.stack([_gray_f32(d[0]) for d in data])).pin_memory()
+    hR = torch.from_numpy(np.stack([_gray_f32(d[1]) for d in data])).pin_memory()
+    hG = torch.from_numpy(np.stack([d[2].astype(np.float32) for d in data])).pin_memory()
+    tL, tR, tG = hL.to(dev), hR.to(dev), hG.to(dev)
+    h = st.stereo_create(st.stereo_default_params(max_width=W, max_height=H, num_disp=D, soft_argmin=1))
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    hloss = torch.zeros(1, dtype=torch.float32).pin_memory()
+    g = torch.empty((B, H, W), dtype=torch.float32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def train_step(L, R, G):
+        L.requires_grad_(True)
+        R.requires_grad_(True)
+        L.grad = None
+        R.grad = None
+        ds = st.soft_argmin(L, R, h, 0, D, r, tau)
+        st.stereo_l1_loss(h, ds.detach(), G, loss, g, stream=stream)
+        ds.backward(g)
+        return L.grad, R.grad
+
+    def step():
+        train_step(tL, tR, tG)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        clk.wait_first_sample(step, timeout=3.0)
+        torch.cuda.synchronize()
+        launches0 = st.stereo_launch_count()
+        step_ms = _timed_loop(torch, stream, args.steps, step, flush)
+    launches = st.stereo_launch_count() - launches0
+    t_max = _max_over_ranks(torch, dev, sum(step_ms) / 1e3, world)
+    P = B * W * H * D
+    value = world * args.steps * P / t_max / 1e9
+
+    # stage times of the backward of the last pair (separate pass)
+    names = ("stats", "cost", "dA", "box_t1", "unused", "final")
+    ds = st.soft_argmin(tL.detach(), tR.detach(), h, 0, D, r, tau)
+    lse = torch.empty_like(ds)
+    st.stereo_softargmin_fwd(h, tL.detach(), tR.detach(), 0, D, r, tau, ds, lse)
+    gl, gr = torch.empty_like(ds), torch.empty_like(ds)
+    bwd_ms = _stage_pass(st, h, min(args.steps, 5), flush,
+                         lambda: st.stereo_softargmin_bwd(h, tL.detach(), tR.detach(), 0, D, r, tau, ds, lse,
+                                                          g, gl, gr), names)
+    fwd_ms = _stage_pass(st, h, min(args.steps, 5), flush,
+                         lambda: st.stereo_softargmin_fwd(h, tL.detach(), tR.detach(), 0, D, r, tau, ds, lse),
+                         ("stats", "cost", "soft_fwd", "_a", "_b", "_c"))
+
+    def e2e_step():
+        L = torch.empty_like(tL)
+        R = torch.empty_like(tR)
+        G = torch.empty_like(tG)
+        L.copy_(hL, non_blocking=True)
+        R.copy_(hR, non_blocking=True)
+        G.copy_(hG, non_blocking=True)
+        train_step(L, R, G)
+        hloss.copy_(loss, non_blocking=True)
+
+    e_ms = _e2e_loop(torch, stream, args.steps, args.warmup, e2e_step, flush)
+    te = _max_over_ranks(torch, dev, sum(e_ms) / 1e3, world)
+    e2e_value = world * args.steps * P / te / 1e9
+    h.close()
+    if rank != 0:
+        return None
+    peaks = load_peaks()
+    roof = soft_roofline(bwd_ms, W, H, D, peaks, KERNEL_TRAFFIC.get(args.workload))
+    line = _base_line(args, world, value, t_max, "f32", {
+        "workload": args.workload, "batch": B, "width": W, "height": H, "num_disp": D,
+        "window": 2 * r + 1, "tau": tau, "loss": "L1(d_soft, ground truth), mean over valid pixels",
+        "step": "forward + loss + backward to both images (torch.autograd)",
+        "parallelism": f"replicas x{world} (independent batches)",
+        "l2": "flushed between timed steps (256 MB write, untimed); volumes >> L2"})
+    line.update({
+        "ms_per_pair": round(t_max * 1e3 / args.steps / B, 4),
+        "stage_ms_last_pair": {"forward": {k: round(fwd_ms[k], 4) for k in ("stats", "cost", "soft_fwd")},
+                               "backward": {k: round(v, 4) for k, v in bwd_ms.items() if k != "unused"}},
+        "roofline": roof,
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "ms_per_step": round(te * 1e3 / args.steps, 4),
+                "h2d_bytes_per_step": 3 * B * W * H * 4, "d2h_bytes_per_step": 4},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "paper_context": PAPER_CONTEXT,
+    })
     return line
 
 
 # ------------------------------------------------------- CPU oracle leg
 
-def oracle_sample(wl, rows: int):
-    """Times the FP64 oracle's whole path on a bounded strip of the workload:
-    `rows` output rows (plus window margins) across the full width."""
-    import oracle
+def _oracle_problem(wl):
+    """(Lrgb, Rrgb, W, D, r, smooth radius) of the workload's first pair."""
+    if wl["kind"] == "batched":
+        L, R, gt, s = synth.batch_pair(16)               # a 960x540 pair of the batch
+        return L, R, s["W"], s["D"], s["r"], wl["smooth_radius"]
     Lrgb, Rrgb, gt = make_pair(wl, 0)
+    return Lrgb, Rrgb, wl["W"], wl["D"], wl["r"], wl.get("smooth_radius", 15)
+
+
+def oracle_sample(wl, rows: int, problem=None):
+    """Times the FP64 oracle on a bounded strip of the workload: `rows` output
+    rows (plus window margins) across the full width.  Single-pair and batched
+    workloads: the whole path; soft-argmin: forward + L1 loss + backward."""
+    import oracle
+    Lrgb, Rrgb, W, D, r, sr = problem or _oracle_problem(wl)
+    H = Lrgb.shape[0]
+    y0 = H // 2 - rows // 2 - r
+    if wl["kind"] == "soft":
+        Ls = _gray_f32(Lrgb)[y0:y0 + rows + 2 * r].astype(np.float64)
+        Rs = _gray_f32(Rrgb)[y0:y0 + rows + 2 * r].astype(np.float64)
+        gt = np.zeros_like(Ls)
+        t0 = time.perf_counter()
+        ds, lse, hv = oracle.softargmin_fwd(Ls, Rs, 0, D, r, wl["tau"])
+        loss, g = oracle.l1_loss(ds, hv, gt)
+        oracle.softargmin_bwd(Ls, Rs, 0, D, r, wl["tau"], g)
+        dt = time.perf_counter() - t0
+        return rows * W * D / dt / 1e9, dt, f"{W}x{rows} output rows (+{2 * r} margin rows), fwd+loss+bwd"
     Lg, Rg = oracle.gray(Lrgb), oracle.gray(Rrgb)
-    y0 = wl["H"] // 2 - rows // 2 - wl["r"]
-    Ls = np.ascontiguousarray(Lg[y0:y0 + rows + 2 * wl["r"]])
-    Rs = np.ascontiguousarray(Rg[y0:y0 + rows + 2 * wl["r"]])
-    p = oracle.Params(d_min=0, num_disp=wl["D"], win_radius=wl["r"], smooth_radius=wl["smooth_radius"])
+    Ls = np.ascontiguousarray(Lg[y0:y0 + rows + 2 * r])
+    Rs = np.ascontiguousarray(Rg[y0:y0 + rows + 2 * r])
+    p = oracle.Params(d_min=0, num_disp=D, win_radius=r, smooth_radius=sr)
     t0 = time.perf_counter()
     oracle.pipeline(Ls, Rs, p)
     dt = time.perf_counter() - t0
-    P = rows * wl["W"] * wl["D"]
-    return P / dt / 1e9, dt, f"{wl['W']}x{rows} output rows (+{2 * wl['r']} margin rows) of the workload"
+    return rows * W * D / dt / 1e9, dt, f"{W}x{rows} output rows (+{2 * r} margin rows) of a {W}-wide pair, D={D}"
 
 
 def run_reference(args, wl):
     import oracle
     oracle.build()
     rows = args.oracle_rows
+    problem = _oracle_problem(wl)
+    W, D = problem[2], problem[3]
     for _ in range(args.warmup):
-        oracle_sample(wl, max(2, rows // 4))
-    vals, secs = [], []
+        oracle_sample(wl, max(2, rows // 4), problem)
+    secs = []
+    sample = ""
     for _ in range(args.steps):
-        v, dt, sample = oracle_sample(wl, rows)
-        vals.append(v)
+        v, dt, sample = oracle_sample(wl, rows, problem)
         secs.append(dt)
-    value = args.steps * rows * wl["W"] * wl["D"] / sum(secs) / 1e9
+    value = args.steps * rows * W * D / sum(secs) / 1e9
     return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(sum(secs) / args.steps * 1e3, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded tissue-texture generator)",
-            "config": {"workload": args.workload, "width": wl["W"], "height": wl["H"],
-                       "num_disp": wl["D"], "window": 2 * wl["r"] + 1},
+            "config": {"workload": args.workload, "width": W, "num_disp": D},
             "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"each step: {sample}"},
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -373,13 +670,22 @@ def main():
             print(json.dumps(run_reference(args, wl)), flush=True)
         return
 
+    pairs = make_batch(wl["n"], rank * wl["n"]) if wl["kind"] == "batched" else None
     import torch
+    dev = torch.device(f"cuda:{int(os.environ.get('LOCAL_RANK', 0))}")
+    torch.cuda.set_device(dev)
     if world > 1:
         torch.distributed.init_process_group("nccl")
-    line = run_ours(args, wl, rank, world)
+    if wl["kind"] == "batched":
+        line = run_batched(args, wl, rank, world, dev, pairs)
+    elif wl["kind"] == "soft":
+        line = run_soft_step(args, wl, rank, world, dev)
+    else:
+        line = run_single(args, wl, rank, world, dev)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            v, dt, sample = oracle_sample(wl, args.cpu_baseline_rows)
+            rows = args.cpu_baseline_rows if wl["kind"] != "soft" else max(4, args.cpu_baseline_rows // 8)
+            v, dt, sample = oracle_sample(wl, rows)
             line["cpu_baseline"] = {"value": round(v, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
                                     "sample": sample, "seconds": round(dt, 2)}
         print(json.dumps(line), flush=True)

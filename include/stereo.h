@@ -152,7 +152,10 @@ stereo_status stereo_match(stereo_handle* h, const stereo_pair* pair, void* stre
  * rebuilt (and uploaded, outside any capture) when the pairs or the batch
  * configuration change.  When `use_graph` is non-zero and `stream` is not the
  * legacy default stream, the whole launch sequence is captured once into a
- * CUDA graph (keyed by the pairs' bytes) and replayed.  Returns
+ * CUDA graph (keyed by the pairs' bytes) and replayed.  The per-pair stages
+ * before and after the cost launch run on up to 8 streams owned by the
+ * handle (parallel branches of the graph), forked from and joined back into
+ * `stream`, so the call stays ordered on `stream`.  Returns
  * STEREO_ERR_UNSUPPORTED when called inside a caller's capture with pairs
  * that need new tables. */
 stereo_status stereo_match_batched(stereo_handle* h, const stereo_pair* pairs, int32_t n,
@@ -180,9 +183,15 @@ const char* stereo_status_str(stereo_status s);
 /* Tracing.  With stage timing on, stereo_match records CUDA events on its
  * stream around its stages: 0 input conversion, 1 window statistics, 2 cost
  * + winner-take-all kernel, 3 finalize (sub-pixel, LR check), 4 outlier /
- * hole-filling loop, 5 refinement.  stereo_get_stage_times waits for the
- * last stereo_match of the handle and writes min(n, STEREO_NUM_STAGES)
- * durations in milliseconds. */
+ * hole-filling loop, 5 refinement.  stereo_match_batched does the same with
+ * each stage covering all pairs of the batch (it then runs without a graph,
+ * and one stage of every pair ends before the next stage starts).
+ * The soft-argmin calls time their last pair: forward 0 statistics, 1 cost
+ * kernel, 2 soft-argmin kernel (3..5 zero); backward 0 statistics, 1 cost
+ * kernel, 2 dA kernel (A volume, per-pixel and diagonal sums), 3 window
+ * sums of A with the T1 sums, 4 zero, 5 final gradient kernel.
+ * stereo_get_stage_times waits for the last timed call of the handle and
+ * writes min(n, STEREO_NUM_STAGES) durations in milliseconds. */
 #define STEREO_NUM_STAGES 6
 stereo_status stereo_set_stage_timing(stereo_handle* h, int32_t enable);
 stereo_status stereo_get_stage_times(stereo_handle* h, float* ms, int32_t n);
@@ -210,7 +219,9 @@ stereo_status stereo_gray(const uint8_t* rgb, int32_t width, int32_t height, int
 /* Sec. II-A: ZNCC of every valid candidate, winner-take-all for the left
  * view (ties -> smallest d) and for the right view (best left pixel u + d
  * for each right pixel u; used by the LR check), parabola sub-pixel offset
- * on c = 1 - ZNCC.  left/right: gray, row stride = width.  disp_left,
+ * on c = 1 - ZNCC (its three costs read from an FP32 volume, else computed
+ * in FP32 from the images: a parabola through FP16/BF16-rounded costs would
+ * be off by up to ~0.03 px).  left/right: gray, row stride = width.  disp_left,
  * disp_right: int16 W*H; disp_sub: float W*H (NaN where invalid);
  * cost: optional [H][W][num_disp] volume of c = 1 - ZNCC in `cost_dtype`
  * (NaN for invalid candidates), NULL when cost_dtype is STEREO_COST_NONE.

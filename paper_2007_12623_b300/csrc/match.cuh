@@ -50,13 +50,70 @@ __device__ float zncc_direct(const uint8_t* __restrict__ L, const uint8_t* __res
 }
 
 // ----------------------------------------------- finalize (S3 tail + S4)
-// Decodes the key maps into integer disparities, fits the parabola on the
-// stored costs (or recomputed ZNCC) and applies the left-right check.
+// Window statistics written by the preparation kernel: left {S, 1/sqrt(B)}
+// per pixel (row stride W), right {S_hi, S_lo, 1/sqrt(B), valid} at
+// (y * ustride + ucol0 + u).
+struct FinStats {
+    const float2* lstats;
+    const float4* ustats;
+    int ustride, ucol0;
+};
+
+// c = 1 - rho at d-1, d, d+1 of left pixel (x, y) whose right pixel for d is
+// u0 = x - d, in the fused cost kernel's FP32 arithmetic: the window sum of
+// products is an exact integer (< 2^24), the numerator splits the right
+// window sum into S_hi + S_lo the same way and the products and fused
+// multiply-adds are the same, so the three values equal the FP32 cost
+// volume's bit for bit.  NaN where the right pixel's window leaves the image.
+template <int R>
+__device__ __forceinline__ void costs3_fp32(const uint8_t* __restrict__ L, const uint8_t* __restrict__ Rm,
+                                            int W, int x, int y, int u0, const FinStats& fs, float c[3]) {
+    int slr0 = 0, slr1 = 0, slr2 = 0;            // right pixel u0 + 1, u0, u0 - 1
+    const int cl = max(u0 - R - 1, 0), cr = min(u0 + R + 1, W - 1);
+#pragma unroll
+    for (int dy = -R; dy <= R; ++dy) {
+        const uint8_t* lp = L + (size_t)(y + dy) * W + x - R;
+        const uint8_t* rp = Rm + (size_t)(y + dy) * W;
+        int rv[2 * R + 3];
+        rv[0] = __ldg(rp + cl);                  // clamped edge columns only feed invalid candidates
+#pragma unroll
+        for (int j = 1; j <= 2 * R + 1; ++j) rv[j] = __ldg(rp + u0 - R - 1 + j);
+        rv[2 * R + 2] = __ldg(rp + cr);
+#pragma unroll
+        for (int j = 0; j <= 2 * R; ++j) {
+            const int l = __ldg(lp + j);
+            slr0 += l * rv[j + 2];
+            slr1 += l * rv[j + 1];
+            slr2 += l * rv[j];
+        }
+    }
+    const float2 sl = fs.lstats[(size_t)y * W + x];
+    const float Nf = (float)((2 * R + 1) * (2 * R + 1));
+    const float4* up = fs.ustats + (size_t)y * fs.ustride + fs.ucol0 + u0;
+    const int sv[3] = {slr0, slr1, slr2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float4 us = up[1 - k];
+        const float t1 = sl.x * us.x;
+        const float num = fmaf(-sl.x, us.y, fmaf(Nf, (float)sv[k], -t1));
+        const float av = num * sl.y;
+        c[k] = us.w != 0.f ? fmaf(-av, us.z, 1.f) : __int_as_float(0x7fc00000);
+    }
+}
+
+// Decodes the key maps into integer disparities, fits the parabola and
+// applies the left-right check.  The parabola divides by the curvature of
+// three near-equal costs: it reads them from an FP32 volume, and otherwise
+// (no volume, or one stored in FP16/BF16 whose rounding would move the
+// offset by up to ~0.03 px) recomputes them with costs3_fp32 (R > 0) or, with
+// no statistics, by the direct definition (R = 0).
+template <int R>
 __global__ void k_finalize(const uint32_t* __restrict__ keyL, const uint32_t* __restrict__ keyR,
                            int W, int H, int d_min, int D, int lr_thresh, const void* __restrict__ cost,
                            int cdt, const uint8_t* __restrict__ L, const uint8_t* __restrict__ Rm, int r,
-                           int sampling, int16_t* __restrict__ disp_left, int16_t* __restrict__ disp_right,
-                           float* __restrict__ disp_sub, int16_t* __restrict__ disp_lr) {
+                           int sampling, FinStats fs, int16_t* __restrict__ disp_left,
+                           int16_t* __restrict__ disp_right, float* __restrict__ disp_sub,
+                           int16_t* __restrict__ disp_lr) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= W) return;
@@ -80,20 +137,22 @@ __global__ void k_finalize(const uint32_t* __restrict__ keyL, const uint32_t* __
         if (dl != ST_INVALID) {
             float delta = 0.f;
             if (dl > d_min && dl < d_min + D - 1) {
-                float cm, c0, cp;
-                if (cdt != CDT_NONE) {
+                float c[3];
+                if (cdt == CDT_F32) {
                     const size_t b = i * (size_t)cost_stride(D) + (dl - d_min);
-                    cm = cost_load(cost, cdt, b - 1);
-                    c0 = cost_load(cost, cdt, b);
-                    cp = cost_load(cost, cdt, b + 1);
+                    c[0] = cost_load(cost, cdt, b - 1);
+                    c[1] = cost_load(cost, cdt, b);
+                    c[2] = cost_load(cost, cdt, b + 1);
+                } else if (R > 0) {
+                    costs3_fp32<R>(L, Rm, W, x, y, x - dl, fs, c);
                 } else {
-                    cm = 1.f - zncc_direct(L, Rm, W, H, r, sampling, x, y, dl - 1);
-                    c0 = 1.f - zncc_direct(L, Rm, W, H, r, sampling, x, y, dl);
-                    cp = 1.f - zncc_direct(L, Rm, W, H, r, sampling, x, y, dl + 1);
+                    c[0] = 1.f - zncc_direct(L, Rm, W, H, r, sampling, x, y, dl - 1);
+                    c[1] = 1.f - zncc_direct(L, Rm, W, H, r, sampling, x, y, dl);
+                    c[2] = 1.f - zncc_direct(L, Rm, W, H, r, sampling, x, y, dl + 1);
                 }
-                const float den = cm - 2.f * c0 + cp;
-                if (!isnan(cm) && !isnan(cp) && den > 0.f) {
-                    delta = (cm - cp) / (2.f * den);
+                const float den = c[0] - 2.f * c[1] + c[2];
+                if (!isnan(c[0]) && !isnan(c[2]) && den > 0.f) {
+                    delta = (c[0] - c[2]) / (2.f * den);
                     delta = fminf(0.5f, fmaxf(-0.5f, delta));
                 }
             }
@@ -101,6 +160,24 @@ __global__ void k_finalize(const uint32_t* __restrict__ keyL, const uint32_t* __
         }
         disp_sub[i] = s;
     }
+}
+
+// Launches k_finalize for window radius r (statistics from the preparation
+// kernel with FULL sampling; the direct definition otherwise).
+static void launch_finalize(const uint32_t* keyL, const uint32_t* keyR, int W, int H, int d_min, int D,
+                            int lr_thresh, const void* cost, int cdt, const uint8_t* L, const uint8_t* Rm,
+                            int r, int sampling, const FinStats& fs, int16_t* disp_left, int16_t* disp_right,
+                            float* disp_sub, int16_t* disp_lr, cudaStream_t s) {
+    const dim3 g((W + 127) / 128, H);
+    const int rr = (fs.lstats && sampling == 0) ? r : 0;
+#define FIN_CASE(RV) \
+    case RV: k_finalize<RV><<<g, 128, 0, s>>>(keyL, keyR, W, H, d_min, D, lr_thresh, cost, cdt, L, Rm, r, \
+                                             sampling, fs, disp_left, disp_right, disp_sub, disp_lr); break;
+    switch (rr) {
+        FIN_CASE(1) FIN_CASE(2) FIN_CASE(3) FIN_CASE(4) FIN_CASE(5) FIN_CASE(6) FIN_CASE(7)
+        default: FIN_CASE(0)
+    }
+#undef FIN_CASE
 }
 
 // Left-right check alone (stage entry point).

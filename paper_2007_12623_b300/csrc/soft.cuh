@@ -35,32 +35,90 @@ __device__ __forceinline__ float soft_rho(const SoftArgs& a, size_t pix, int k) 
     return 1.f - __ldg(a.cost + pix * a.cs + k);
 }
 
-// One warp per pixel, lanes over disparities.
+// The soft-argmin kernels give one block a run of 32 pixels of one row and
+// one warp per chunk of 32 disparities (lane l of warp c: d = d_min + 32 c +
+// l), so the warps of a block read all candidates of the run's pixels
+// together and every access of a warp is one 128-byte segment.  A per-pixel
+// sum over d goes through shared memory: lane l writes its term for pixel j
+// to slot [j][l] of its warp's 32 x 33 tile (padded: conflict-free), then
+// lane j adds row j, and warp 0 adds the chunks.  Sums along the diagonals
+// s = x - d (the right-view sums) move systolically: the partial sum of lane
+// l at pixel x is the partial sum of lane l + 1 at pixel x + 1, so after each
+// pixel the warp shifts its accumulators one lane up and lane 31 hands a
+// finished sum to memory (atomicAdd: the neighbouring run and the other
+// chunks add theirs).  Loads are issued in batches before their values are
+// used (addresses clamped into the buffers, results masked afterwards).
+//
+// The A volume of the backward pass is stored chunk-blocked,
+// A[y][chunk][SOFT_APAD + x][32] with rows of soft_apitch(W) columns, so a
+// warp's 32 pixels of one chunk are 4 KB of contiguous memory; the
+// SOFT_APAD columns on the left and everything right of column W - 1 hold
+// zeros, so window sums read them without bounds checks.
+constexpr int SOFT_RUN = 32;
+constexpr int SOFT_MAX_CHUNKS = 8;              // 256 disparities
+constexpr int SOFT_TILE = 32 * 33;              // floats of one padded 32 x 32 tile
+constexpr int SOFT_APAD = 8;                    // >= largest window radius
+
+__host__ __device__ inline int soft_apitch(int W) { return ((W + 31) & ~31) + 2 * SOFT_APAD; }
+
+__device__ __forceinline__ size_t soft_ablk(int W, int nch, int y, int c, int x) {
+    return (((size_t)y * nch + c) * soft_apitch(W) + SOFT_APAD + x) * 32;
+}
+
+// Dynamic shared memory of k_soft_fwd / k_soft_dA: two tiles per warp and
+// the cross-warp partial sums.
+inline size_t soft_run_smem(int nch) { return (size_t)(2 * nch * SOFT_TILE + 2 * nch * 32) * 4; }
+
+// Lane j: sum of row j of the warp's tile.
+__device__ __forceinline__ float tile_row_sum(const float* t, int lane) {
+    float s = 0.f;
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) s += t[lane * 33 + i];
+    return s;
+}
+
 __global__ void __launch_bounds__(256) k_soft_fwd(SoftArgs a, float* __restrict__ dsoft,
                                                   float* __restrict__ lse) {
-    const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= (long)a.W * a.H) return;
-    const size_t pix = (size_t)warp;
+    extern __shared__ float soft_run_sm[];
+    const int lane = threadIdx.x & 31, c = threadIdx.x >> 5, nch = blockDim.x >> 5;
+    float* t0 = soft_run_sm + (2 * c) * SOFT_TILE;
+    float* t1 = t0 + SOFT_TILE;
+    float* red = soft_run_sm + 2 * nch * SOFT_TILE;           // [2][nch][32]
+    const int nrun = (a.W + SOFT_RUN - 1) / SOFT_RUN;
+    const int y = blockIdx.x / nrun, x0 = (blockIdx.x % nrun) * SOFT_RUN;
     const float k2 = 1.4426950408889634f / a.tau;           // log2(e) / tau
-    float s0 = 0.f, s1 = 0.f;
-    for (int k = lane; k < a.D; k += 32) {
-        const float rho = soft_rho(a, pix, k);
-        if (rho == rho) {                                   // valid candidate
-            const float e = exp2f((rho - 1.f) * k2);        // exp((rho - 1) / tau) <= 1
-            s0 += e;
-            s1 += (float)(a.d_min + k) * e;
+    const int k = c * 32 + lane;
+    const int kc = min(k, a.cs - 1);
+    const float dv = (float)(a.d_min + k);
+    const float* row = a.cost + (size_t)y * a.W * a.cs + kc;
+#pragma unroll
+    for (int h = 0; h < 32; h += 16) {
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = __ldg(row + (size_t)min(x0 + h + j, a.W - 1) * a.cs);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const float rho = 1.f - v[j];
+            const bool ok = x0 + h + j < a.W && k < a.D && rho == rho;   // valid candidate
+            const float e = ok ? exp2f((rho - 1.f) * k2) : 0.f;          // exp((rho - 1) / tau) <= 1
+            t0[(h + j) * 33 + lane] = e;
+            t1[(h + j) * 33 + lane] = dv * e;
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-    }
-    if (lane == 0) {
-        const bool any = s0 > 0.f;
-        dsoft[pix] = any ? s1 / s0 : __int_as_float(0x7fc00000);
-        lse[pix] = any ? logf(s0) + 1.f / a.tau : __int_as_float(0x7fc00000);
+    __syncwarp();
+    red[c * 32 + lane] = tile_row_sum(t0, lane);
+    red[(nch + c) * 32 + lane] = tile_row_sum(t1, lane);
+    __syncthreads();
+    if (c == 0) {
+        float s0 = 0.f, s1 = 0.f;
+        for (int w = 0; w < nch; ++w) { s0 += red[w * 32 + lane]; s1 += red[(nch + w) * 32 + lane]; }
+        const int x = x0 + lane;
+        if (x < a.W) {
+            const size_t pix = (size_t)y * a.W + x;
+            const bool any = s0 > 0.f;
+            dsoft[pix] = any ? s1 / s0 : __int_as_float(0x7fc00000);
+            lse[pix] = any ? logf(s0) + 1.f / a.tau : __int_as_float(0x7fc00000);
+        }
     }
 }
 
@@ -68,147 +126,215 @@ __device__ __forceinline__ float4 ustat(const SoftArgs& a, int y, int u) {
     return __ldg(a.ustats + (size_t)y * a.ustride + a.ucol0 + u);
 }
 
-// Per pixel p (one warp, lanes over d): A(p,d) = G alpha (stored), and the
-// left-pixel sums P1, P2.
-__global__ void __launch_bounds__(256) k_soft_bwd_a(SoftArgs a, const float* __restrict__ dsoft,
-                                                    const float* __restrict__ lse,
-                                                    const float* __restrict__ g,
-                                                    float* __restrict__ A, float* __restrict__ P1,
-                                                    float* __restrict__ P2) {
-    const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= (long)a.W * a.H) return;
-    const size_t pix = (size_t)warp;
-    const int x = (int)(pix % a.W), y = (int)(pix / a.W);
+// A(p,d) = G alpha (stored chunk-blocked, 0 for invalid candidates), the
+// left-pixel sums P1, P2 (stored) and the right-pixel sums Q1, Q2 (added
+// into zeroed maps).  With alpha = N isl isr (isl, isr = 1/sqrt(B) of the two
+// windows, B = N v):
+//   A mu_r = G isl isr S_r,  G rho / v_l = G N isl^2 rho,
+//   A mu_l = G isl isr S_l,  G rho / v_r = G N isr^2 rho.
+// The per-pixel inputs of the run are loaded once, one pixel per lane, and
+// broadcast with shuffles.
+__global__ void __launch_bounds__(256) k_soft_dA(SoftArgs a, const float* __restrict__ dsoft,
+                                                 const float* __restrict__ lse, const float* __restrict__ g,
+                                                 float* __restrict__ A, float* __restrict__ P1,
+                                                 float* __restrict__ P2, float* __restrict__ Q1,
+                                                 float* __restrict__ Q2) {
+    constexpr int HALF = 8;
+    extern __shared__ float soft_run_sm[];
+    const int lane = threadIdx.x & 31, c = threadIdx.x >> 5, nch = blockDim.x >> 5;
+    float* t1 = soft_run_sm + (2 * c) * SOFT_TILE;
+    float* t2 = t1 + SOFT_TILE;
+    float* red = soft_run_sm + 2 * nch * SOFT_TILE;           // [2][nch][32]
+    const int nrun = (a.W + SOFT_RUN - 1) / SOFT_RUN;
+    const int y = blockIdx.x / nrun, x0 = (blockIdx.x % nrun) * SOFT_RUN;
     const float N = (float)((2 * a.r + 1) * (2 * a.r + 1));
-    const float gp = g[pix], ds = dsoft[pix], l = lse[pix];
-    const float2 sl = __ldg(a.lstats + pix);
-    const float isl = sl.y;
-    float p1 = 0.f, p2 = 0.f;
-    for (int k = lane; k < a.cs; k += 32) {
-        float av = 0.f;
-        if (k < a.D && gp != 0.f && isl != 0.f) {
-            const float rho = soft_rho(a, pix, k);
-            const int d = a.d_min + k;
-            const float4 ur = ustat(a, y, x - d);
-            const float isr = ur.z;
-            if (rho == rho && isr != 0.f) {
-                const float pd = expf(rho / a.tau - l);
-                const float G = gp * pd * ((float)d - ds) / a.tau;
-                av = G * N * isl * isr;                     // alpha = N isl isr
-                p1 += av * (ur.x + ur.y) / N;                // mu_r
-                p2 += av * rho * isl / isr;                  // G rho / v_l
+    const float invN = 1.f / N;
+    const float inv_tau = 1.f / a.tau;
+    const float l2e_tau = 1.4426950408889634f / a.tau;
+    const size_t row = (size_t)y * a.W;
+    const size_t mypix = row + min(x0 + lane, a.W - 1);     // this lane's pixel x0 + lane
+    // G = g p_d (d - ds) / tau with p_d = exp(rho / tau - lse): per pixel
+    // g N / tau and lse log2(e) are folded in
+    const float my_gs = x0 + lane < a.W ? __ldg(g + mypix) * N * inv_tau : 0.f;
+    const float my_ds = __ldg(dsoft + mypix);
+    const float my_l2 = __ldg(lse + mypix) * 1.4426950408889634f;
+    const float2 my_sl = __ldg(a.lstats + mypix);
+    const int k = c * 32 + lane;
+    const int kc = min(k, a.cs - 1);
+    const int d = a.d_min + k;
+    const float* crow = a.cost + row * a.cs + kc;
+    float* arow = A + soft_ablk(a.W, nch, y, c, 0) + lane;
+    float q1 = 0.f, q2 = 0.f;                     // diagonal sums for s = x - d
+#pragma unroll
+    for (int h = 0; h < 32; h += HALF) {
+        float cv[HALF];
+        float4 ur[HALF];
+#pragma unroll
+        for (int j = 0; j < HALF; ++j) {
+            const int x = min(x0 + h + j, a.W - 1);
+            cv[j] = __ldg(crow + (size_t)x * a.cs);
+            // right pixel x - d lies in the padded statistics rows for every
+            // candidate index below cs; lanes beyond it read pixel x - d_min
+            ur[j] = ustat(a, y, k < a.cs ? x - d : x - a.d_min);
+        }
+#pragma unroll
+        for (int j = 0; j < HALF; ++j) {
+            const int x = x0 + h + j;
+            const float gs = __shfl_sync(0xffffffffu, my_gs, h + j);
+            const float ds = __shfl_sync(0xffffffffu, my_ds, h + j);
+            const float l2 = __shfl_sync(0xffffffffu, my_l2, h + j);
+            const float slx = __shfl_sync(0xffffffffu, my_sl.x, h + j);
+            const float isl = __shfl_sync(0xffffffffu, my_sl.y, h + j);
+            const float rho = 1.f - cv[j];
+            const float isr = ur[j].z;
+            float av = 0.f, v1 = 0.f, v2 = 0.f;
+            if (x < a.W && k < a.D && gs != 0.f && isl != 0.f && rho == rho && isr != 0.f) {
+                const float pd = exp2f(fmaf(rho, l2e_tau, -l2));
+                const float Gn = gs * pd * ((float)d - ds);       // G N
+                av = Gn * isl * isr;                               // A = G N isl isr
+                const float ng = av * invN;                        // G isl isr
+                v1 = ng * (ur[j].x + ur[j].y);                     // A mu_r
+                v2 = Gn * isl * isl * rho;                         // G rho / v_l
+                q1 = fmaf(ng, slx, q1);                            // A mu_l
+                q2 = fmaf(Gn * isr * isr, rho, q2);                // G rho / v_r
             }
+            t1[(h + j) * 33 + lane] = v1;
+            t2[(h + j) * 33 + lane] = v2;
+            arow[(size_t)x * 32] = av;                        // 0 beyond column W - 1
+            if (lane == 31 && (q1 != 0.f || q2 != 0.f)) {
+                const int s = x - d;
+                if (s >= 0 && s < a.W) {
+                    atomicAdd(Q1 + row + s, q1);
+                    atomicAdd(Q2 + row + s, q2);
+                }
+            }
+            q1 = __shfl_up_sync(0xffffffffu, q1, 1);
+            q2 = __shfl_up_sync(0xffffffffu, q2, 1);
+            if (lane == 0) { q1 = 0.f; q2 = 0.f; }
         }
-        A[pix * a.cs + k] = av;
     }
+    // partial diagonal sums still in flight: lane l holds s = x0 + 32 - d
+    const int s = x0 + SOFT_RUN - d;
+    if (lane > 0 && (q1 != 0.f || q2 != 0.f) && s >= 0 && s < a.W) {
+        atomicAdd(Q1 + row + s, q1);
+        atomicAdd(Q2 + row + s, q2);
+    }
+    // zero padding columns of A left of the first run and right of the last
+    if (x0 == 0) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        p1 += __shfl_xor_sync(0xffffffffu, p1, o);
-        p2 += __shfl_xor_sync(0xffffffffu, p2, o);
+        for (int j = 1; j <= SOFT_APAD; ++j) arow[-(long)j * 32] = 0.f;
     }
-    if (lane == 0) {
-        P1[pix] = p1;
-        P2[pix] = p2;
+    if (x0 + SOFT_RUN >= a.W) {
+#pragma unroll
+        for (int j = 0; j < SOFT_APAD; ++j) arow[(size_t)(x0 + SOFT_RUN + j) * 32] = 0.f;
     }
-}
-
-// Per right pixel s (one thread, walking d along the diagonal p = s + d):
-// Q1, Q2.
-__global__ void __launch_bounds__(256) k_soft_bwd_q(SoftArgs a, const float* __restrict__ A,
-                                                    float* __restrict__ Q1, float* __restrict__ Q2) {
-    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long)a.W * a.H) return;
-    const int s = (int)(i % a.W), y = (int)(i / a.W);
-    const float N = (float)((2 * a.r + 1) * (2 * a.r + 1));
-    const float4 ur = ustat(a, y, s);
-    const float isr = ur.z;
-    float q1 = 0.f, q2 = 0.f;
-    if (isr != 0.f) {
-        for (int k = 0; k < a.D; ++k) {
-            const int p = s + a.d_min + k;
-            if (p < 0 || p >= a.W) continue;
-            const size_t pix = (size_t)y * a.W + p;
-            const float av = __ldg(A + pix * a.cs + k);
-            if (av == 0.f) continue;
-            const float2 sl = __ldg(a.lstats + pix);
-            const float rho = soft_rho(a, pix, k);
-            q1 += av * sl.x / N;                             // mu_l
-            q2 += av * rho * isr / sl.y;                     // G rho / v_r
-        }
-    }
-    Q1[i] = q1;
-    Q2[i] = q2;
-}
-
-// M(q,d) = sum over the (2r+1)^2 window around q of A(., d): one block per
-// 16x16 pixel tile and 8 disparities; separable sums in shared memory.
-constexpr int SB_T = 16, SB_D = 8, SB_MAXR = 7;
-
-__global__ void __launch_bounds__(256) k_soft_box(const float* __restrict__ A, int W, int H, int cs, int r,
-                                                  float* __restrict__ M) {
-    __shared__ float t[SB_T + 2 * SB_MAXR][SB_T + 2 * SB_MAXR][SB_D];
-    __shared__ float rowsum[SB_T + 2 * SB_MAXR][SB_T][SB_D];
-    const int x0 = blockIdx.x * SB_T, y0 = blockIdx.y * SB_T, k0 = blockIdx.z * SB_D;
-    const int span = SB_T + 2 * r;
-    for (int i = threadIdx.x; i < span * span * SB_D; i += 256) {
-        const int k = i % SB_D, lx = (i / SB_D) % span, ly = i / (SB_D * span);
-        const int gx = x0 - r + lx, gy = y0 - r + ly;
-        t[ly][lx][k] = (gx >= 0 && gx < W && gy >= 0 && gy < H && k0 + k < cs)
-                           ? __ldg(A + ((size_t)gy * W + gx) * cs + k0 + k) : 0.f;
-    }
+    __syncwarp();
+    red[c * 32 + lane] = tile_row_sum(t1, lane);
+    red[(nch + c) * 32 + lane] = tile_row_sum(t2, lane);
     __syncthreads();
-    for (int i = threadIdx.x; i < span * SB_T * SB_D; i += 256) {
-        const int k = i % SB_D, lx = (i / SB_D) % SB_T, ly = i / (SB_D * SB_T);
-        float s = 0.f;
-        for (int j = 0; j <= 2 * r; ++j) s += t[ly][lx + j][k];
-        rowsum[ly][lx][k] = s;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < SB_T * SB_T * SB_D; i += 256) {
-        const int k = i % SB_D, lx = (i / SB_D) % SB_T, ly = i / (SB_D * SB_T);
-        const int gx = x0 + lx, gy = y0 + ly;
-        if (gx >= W || gy >= H || k0 + k >= cs) continue;
-        float s = 0.f;
-        for (int j = 0; j <= 2 * r; ++j) s += rowsum[ly + j][lx][k];
-        M[((size_t)gy * W + gx) * cs + k0 + k] = s;
+    if (c == 0 && x0 + lane < a.W) {
+        float s1 = 0.f, s2 = 0.f;
+        for (int w = 0; w < nch; ++w) { s1 += red[w * 32 + lane]; s2 += red[(nch + w) * 32 + lane]; }
+        P1[row + x0 + lane] = s1;
+        P2[row + x0 + lane] = s2;
     }
 }
 
-// T1L(q) = sum_d R(q-d) M(q,d): one warp per pixel, lanes over d.
-__global__ void __launch_bounds__(256) k_soft_t1l(const float* __restrict__ M, const float* __restrict__ Rimg,
-                                                  int W, int H, int cs, int d_min, int D,
-                                                  float* __restrict__ T1L) {
-    const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// M(q,d) = sum over the (2r+1)^2 window around q of A(., d), consumed on
+// the fly (never stored):
+//   T1L(q) = sum_d R(q-d) M(q,d),   T1R(u) = sum_d L(u+d) M(u+d,d),
+// both added into zeroed maps.  A warp owns 32 columns, `ty` rows and one
+// chunk of 32 disparities; it keeps the vertical window sums of its 32 + 2R
+// columns in registers and slides them down one row at a time (add the
+// entering row, subtract the leaving one), and the horizontal sum along the
+// run.  The T1L terms of a row go through the warp's shared tile.
+constexpr int SOFT_BOX_THREADS = 128;
+
+template <int R>
+__global__ void __launch_bounds__(SOFT_BOX_THREADS, 3) k_soft_box_t1(const float* __restrict__ A, const float* __restrict__ Limg,
+                                                     const float* __restrict__ Rimg, int W, int H, int nch,
+                                                     int cs, int d_min, int ty, float* __restrict__ T1L,
+                                                     float* __restrict__ T1R) {
+    constexpr int NCOL = SOFT_RUN + 2 * R;
+    __shared__ float tiles[SOFT_BOX_THREADS / 32][SOFT_TILE];
     const int lane = threadIdx.x & 31;
-    if (warp >= (long)W * H) return;
-    const int x = (int)(warp % W), y = (int)(warp / W);
-    float acc = 0.f;
-    for (int k = lane; k < D; k += 32) {
-        const int u = x - (d_min + k);
-        if (u < 0 || u >= W) continue;
-        acc += __ldg(Rimg + (size_t)y * W + u) * __ldg(M + (size_t)warp * cs + k);
-    }
+    float* tl = tiles[threadIdx.x >> 5];
+    const long wid = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nrun = (W + SOFT_RUN - 1) / SOFT_RUN, nband = (H + ty - 1) / ty;
+    if (wid >= (long)nrun * nband * nch) return;
+    const int run = (int)(wid % nrun);
+    const int band = (int)((wid / nrun) % nband);
+    const int chunk = (int)(wid / ((long)nrun * nband));
+    const int x0 = run * SOFT_RUN, y0 = band * ty;
+    const int k = chunk * 32 + lane, d = d_min + k;
+    const bool kin = k < cs;
+    float V[NCOL];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) T1L[warp] = acc;
+    for (int c = 0; c < NCOL; ++c) V[c] = 0.f;
+    // adds (sign +1) or subtracts (sign -1) row yy of A (columns x0 - R ..
+    // x0 + 31 + R; the zero padding covers those outside the image, and lanes
+    // beyond cs hold zeros)
+    auto slide = [&](int yy, float sign) {
+        const float* rp = A + soft_ablk(W, nch, yy, chunk, x0 - R) + lane;
+        constexpr int B = (NCOL + 1) / 2;
+#pragma unroll
+        for (int c0 = 0; c0 < NCOL; c0 += B) {
+            float v[B];
+#pragma unroll
+            for (int c = 0; c < B; ++c)
+                if (c0 + c < NCOL) v[c] = __ldg(rp + (c0 + c) * 32);
+#pragma unroll
+            for (int c = 0; c < B; ++c)
+                if (c0 + c < NCOL) V[c0 + c] = fmaf(sign, v[c], V[c0 + c]);
+        }
+    };
+    for (int yy = max(0, y0 - R); yy < min(H, y0 + R); ++yy) slide(yy, 1.f);
+    const int y1 = min(y0 + ty, H);
+    const int d0 = d_min + chunk * 32;
+    for (int y = y0; y < y1; ++y) {
+        if (y + R < H) slide(y + R, 1.f);
+        const float* Lrow = Limg + (size_t)y * W;
+        const float* Rrow = Rimg + (size_t)y * W;
+        const float my_l = __ldg(Lrow + min(x0 + lane, W - 1));
+        // R(x - d) moves one lane up per column: lane l at column x needs the
+        // value lane l - 1 used at column x - 1; lane 0 takes R(x - d_0) from
+        // a run-wide load (lane j holds R(x0 + j - d_0)).
+        const float r_lane0 = __ldg(Rrow + min(max(x0 + lane - d0, 0), W - 1));
+        float rcur = __ldg(Rrow + min(max(x0 - d, 0), W - 1));
+        float acc = 0.f;                      // T1R partial for u = x - d
+        float h = 0.f;
+#pragma unroll
+        for (int c = 0; c <= 2 * R; ++c) h += V[c];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (j > 0) h += V[j + 2 * R] - V[j - 1];
+            const int x = x0 + j, u = x - d;
+            const float lx = __shfl_sync(0xffffffffu, my_l, j);
+            const bool ok = kin && x < W && u >= 0 && u < W;
+            tl[j * 33 + lane] = ok ? rcur * h : 0.f;
+            rcur = __shfl_up_sync(0xffffffffu, rcur, 1);
+            const float r0 = __shfl_sync(0xffffffffu, r_lane0, (j + 1) & 31);
+            if (lane == 0) rcur = r0;
+            acc = ok ? fmaf(lx, h, acc) : acc;
+            if (lane == 31 && acc != 0.f && u >= 0 && u < W) atomicAdd(T1R + (size_t)y * W + u, acc);
+            acc = __shfl_up_sync(0xffffffffu, acc, 1);
+            if (lane == 0) acc = 0.f;
+        }
+        const int u = x0 + SOFT_RUN - d;
+        if (lane > 0 && acc != 0.f && u >= 0 && u < W) atomicAdd(T1R + (size_t)y * W + u, acc);
+        __syncwarp();
+        const float t = tile_row_sum(tl, lane);
+        if (x0 + lane < W) atomicAdd(T1L + (size_t)y * W + x0 + lane, t);
+        __syncwarp();
+        if (y - R >= 0) slide(y - R, -1.f);
+    }
 }
 
-// T1R(u) = sum_d L(u+d) M(u+d,d): one thread per right pixel.
-__global__ void __launch_bounds__(256) k_soft_t1r(const float* __restrict__ M, const float* __restrict__ Limg,
-                                                  int W, int H, int cs, int d_min, int D,
-                                                  float* __restrict__ T1R) {
-    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long)W * H) return;
-    const int u = (int)(i % W), y = (int)(i / W);
-    float acc = 0.f;
-    for (int k = 0; k < D; ++k) {
-        const int p = u + d_min + k;
-        if (p < 0 || p >= W) continue;
-        const size_t pix = (size_t)y * W + p;
-        acc += __ldg(Limg + pix) * __ldg(M + pix * cs + k);
-    }
-    T1R[i] = acc;
+// Band height of k_soft_box_t1: short bands while the grid would otherwise
+// give fewer than ~24 warps per SM.
+inline int soft_box_rows(int W, int H, int nch, int sms) {
+    const long per_row = (long)((W + SOFT_RUN - 1) / SOFT_RUN) * nch;
+    return per_row * ((H + 15) / 16) >= 24L * sms ? 16 : 8;
 }
 
 // Final gradients: box sums over the (2r+1)^2 window of the six per-pixel

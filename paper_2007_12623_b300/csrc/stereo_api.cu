@@ -58,8 +58,7 @@ struct PairWs {
     int16_t* cnt;       // refinement: valid count of each box
     uint32_t* masks;    // line bitmasks of the radial passes
     // soft-argmin backward (only when the handle was created with soft_argmin)
-    float* softA;       // [H][W][cs] G * alpha
-    float* softM;       // [H][W][cs] window sums of softA
+    float* softA;       // [H][chunks][soft_apitch(W)][32] G * alpha (chunk-blocked, zero padded)
     float* sP1; float* sP2; float* sQ1; float* sQ2; float* sT1L; float* sT1R;
     double* l1part;     // L1-loss partial sums
     float* dfin;        // refined output (when the caller gives none)
@@ -82,7 +81,7 @@ constexpr int L1_PARTS = 1024;
 size_t pair_ws_bytes(size_t npix, int D, int cdt, int maxW = 0, int maxH = 0, int soft = 0) {
     size_t b = 0;
     if (soft) {
-        b += align_up(npix * (size_t)cost_stride(D) * 4, 256) * 2;       // softA, softM
+        b += align_up((size_t)maxH * soft_apitch(maxW) * ((D + 31) & ~31) * 4, 256);   // softA
         b += align_up(npix * 4, 256) * 6;                                 // P1 P2 Q1 Q2 T1L T1R
         b += align_up((size_t)L1_PARTS * 16, 256);
     }
@@ -105,8 +104,7 @@ PairWs carve(uint8_t* base, size_t npix, int D, int cdt, int maxW, int maxH, int
     uint8_t* p = base;
     auto take = [&](size_t bytes) { uint8_t* r = p; p += align_up(bytes, 256); return r; };
     if (soft) {
-        w.softA = reinterpret_cast<float*>(take(npix * (size_t)cost_stride(D) * 4));
-        w.softM = reinterpret_cast<float*>(take(npix * (size_t)cost_stride(D) * 4));
+        w.softA = reinterpret_cast<float*>(take((size_t)maxH * soft_apitch(maxW) * ((D + 31) & ~31) * 4));
         w.sP1 = reinterpret_cast<float*>(take(npix * 4));
         w.sP2 = reinterpret_cast<float*>(take(npix * 4));
         w.sQ1 = reinterpret_cast<float*>(take(npix * 4));
@@ -159,6 +157,8 @@ struct GraphCache {
     unsigned long long kernels = 0;   // kernels in the graph (launch accounting)
 };
 
+constexpr int BATCH_STREAMS = 8;
+
 struct stereo_handle {
     stereo_params p;
     GraphCache single;   // stereo_match
@@ -179,6 +179,11 @@ struct stereo_handle {
     std::vector<uint8_t> table_key;
     int n_units = 0;
     int tables_K = 4;
+    // parallel streams for the per-pair stages of a batch
+    int n_aux = 0;
+    cudaStream_t aux[BATCH_STREAMS] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[BATCH_STREAMS] = {};
     bool timing;         // record per-stage events in stereo_match
     bool ev_ready;
     cudaEvent_t ev[STEREO_NUM_STAGES + 1];
@@ -227,6 +232,8 @@ void set_smem_attributes() {
     cudaFuncSetAttribute(k_refine_box1, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_refine_box2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_soft_final, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_soft_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_soft_dA, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 // Stats + fused cost/WTA + finalize for one pair whose gray images are gl/gr.
@@ -267,9 +274,9 @@ void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, in
                pr.ustride, pr.ucol0, w.keys, w.keys + (size_t)W * H, cost, cdt, W, H, d_min, D, 0};
     launch_cost(r, K, cdt, a, g_cost_rows, s);
     if (ev) cudaEventRecord(ev[3], s);
-    dim3 fg((W + 127) / 128, H);
-    k_finalize<<<fg, 128, 0, s>>>(w.keys, w.keys + (size_t)W * H, W, H, d_min, D, lr_thresh, cost,
-                                  cdt, gl, gr, r, sampling, disp_left, disp_right, disp_sub, disp_lr);
+    launch_finalize(w.keys, w.keys + (size_t)W * H, W, H, d_min, D, lr_thresh, cost, cdt, gl, gr, r, sampling,
+                    FinStats{w.lstats, w.ustats, pr.ustride, pr.ucol0}, disp_left, disp_right, disp_sub, disp_lr,
+                    s);
     counted();
 }
 
@@ -593,6 +600,16 @@ stereo_status stereo_create(const stereo_params* p, int32_t max_batch, stereo_ha
             delete h;
             return STEREO_ERR_OOM;
         }
+        // streams for the per-pair stages; without them the stages run in order on the caller's stream
+        if (cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) == cudaSuccess) {
+            int m = 0;
+            for (; m < BATCH_STREAMS; ++m)
+                if (cudaStreamCreateWithFlags(&h->aux[m], cudaStreamNonBlocking) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&h->join_ev[m], cudaEventDisableTiming) != cudaSuccess)
+                    break;
+            h->n_aux = m;
+        }
+        cudaGetLastError();
     }
     if (cudaMemset(h->dev_err, 0, sizeof(int32_t)) != cudaSuccess) {
         cudaFree(h->ws);
@@ -617,6 +634,11 @@ stereo_status stereo_destroy(stereo_handle* h) {
     if (h->pair_args) cudaFree(h->pair_args);
     if (h->pair_radius) cudaFree(h->pair_radius);
     if (h->counter) cudaFree(h->counter);
+    for (int i = 0; i < BATCH_STREAMS; ++i) {
+        if (h->aux[i]) cudaStreamDestroy(h->aux[i]);
+        if (h->join_ev[i]) cudaEventDestroy(h->join_ev[i]);
+    }
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     delete h;
     return STEREO_OK;
 }
@@ -839,76 +861,156 @@ static stereo_status build_batch_tables(stereo_handle* h, const stereo_pair* pai
     return STEREO_OK;
 }
 
+}  // extern "C"
+
+// Runs body(i, stream) for the pairs i of a batch on the handle's auxiliary
+// streams, forked from and joined back into s (parallel branches when s is
+// being captured).  Pairs go to the least loaded stream, largest W*H*D first.
+template <typename Body>
+static void fan_out(stereo_handle* h, const stereo_pair* pairs, int n, cudaStream_t s, Body body) {
+    const int m = std::min(n, h->n_aux);
+    if (m <= 1) {
+        for (int i = 0; i < n; ++i) body(i, s);
+        return;
+    }
+    std::vector<int> order(n);
+    std::vector<double> work(n), load(m, 0.0);
+    for (int i = 0; i < n; ++i) {
+        int d_min, D, r;
+        resolve_pair(h, &pairs[i], d_min, D, r);
+        order[i] = i;
+        work[i] = (double)pairs[i].width * pairs[i].height * D;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+    cudaEventRecord(h->fork_ev, s);
+    for (int j = 0; j < m; ++j) cudaStreamWaitEvent(h->aux[j], h->fork_ev, 0);
+    for (int i : order) {
+        const int j = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[j] += work[i];
+        body(i, h->aux[j]);
+    }
+    for (int j = 0; j < m; ++j) {
+        cudaEventRecord(h->join_ev[j], h->aux[j]);
+        cudaStreamWaitEvent(s, h->join_ev[j], 0);
+    }
+}
+
+extern "C" {
+
 // Whole path for a batch: per pair input conversion, statistics and border
 // costs; one persistent launch of the cost kernel over all pairs' units; then
-// per pair finalize, post-processing and refinement.
+// per pair finalize, post-processing and refinement.  The per-pair work runs
+// on parallel streams; with stage timing on, every stage of every pair ends
+// before the next stage starts, and the handle's events bracket the stages.
 static void enqueue_batched(stereo_handle* h, const stereo_pair* pairs, int n, cudaStream_t s,
                             bool cost_only = false) {
     const int K = h->tables_K;
-    for (int i = 0; i < n && !cost_only; ++i) {
+    const int cdt = h->p.cost_dtype;
+    const bool timed = h->timing && h->ev_ready && !cost_only;
+    struct Pair {
+        int d_min, D, r, W, H;
+        PairWs w;
+        const uint8_t* gl;
+        const uint8_t* gr;
+        bool converted;
+    };
+    std::vector<Pair> P(n);
+    for (int i = 0; i < n; ++i) {
         const stereo_pair* pr = &pairs[i];
-        int d_min, D, r;
-        resolve_pair(h, pr, d_min, D, r);
-        const int W = pr->width, H = pr->height;
-        PairWs w = carve(h->ws + (size_t)i * h->pair_bytes, (size_t)W * H, h->p.num_disp, h->p.cost_dtype,
-                         h->p.max_width, h->p.max_height);
-        const uint8_t* gl = pr->left;
-        const uint8_t* gr = pr->right;
-        dim3 g((W + 127) / 128, H);
-        if (pr->channels == 3 || pr->pitch != W) {
-            if (pr->channels == 3) {
-                k_gray<<<g, 128, 0, s>>>(pr->left, W, H, pr->pitch, w.gl);
-                k_gray<<<g, 128, 0, s>>>(pr->right, W, H, pr->pitch, w.gr);
-            } else {
-                k_copy_pitched<<<g, 128, 0, s>>>(pr->left, W, H, pr->pitch, w.gl);
-                k_copy_pitched<<<g, 128, 0, s>>>(pr->right, W, H, pr->pitch, w.gr);
-            }
-            counted(2);
-            gl = w.gl;
-            gr = w.gr;
+        Pair& q = P[i];
+        resolve_pair(h, pr, q.d_min, q.D, q.r);
+        q.W = pr->width;
+        q.H = pr->height;
+        q.w = carve(h->ws + (size_t)i * h->pair_bytes, (size_t)q.W * q.H, h->p.num_disp, cdt,
+                    h->p.max_width, h->p.max_height);
+        q.converted = pr->channels == 3 || pr->pitch != q.W;
+        q.gl = q.converted ? q.w.gl : pr->left;
+        q.gr = q.converted ? q.w.gr : pr->right;
+    }
+    auto input = [&](int i, cudaStream_t st) {
+        const stereo_pair* pr = &pairs[i];
+        const Pair& q = P[i];
+        if (!q.converted) return;
+        dim3 g((q.W + 127) / 128, q.H);
+        if (pr->channels == 3) {
+            k_gray<<<g, 128, 0, st>>>(pr->left, q.W, q.H, pr->pitch, q.w.gl);
+            k_gray<<<g, 128, 0, st>>>(pr->right, q.W, q.H, pr->pitch, q.w.gr);
+        } else {
+            k_copy_pitched<<<g, 128, 0, st>>>(pr->left, q.W, q.H, pr->pitch, q.w.gl);
+            k_copy_pitched<<<g, 128, 0, st>>>(pr->right, q.W, q.H, pr->pitch, q.w.gr);
         }
-        PrepOut pl, prr;
-        prep_layouts(W, d_min, D, K, w, pl, prr);
-        dim3 sg((W + PT - 1) / PT, (H + PT - 1) / PT);
-        k_prep<<<sg, 256, 0, s>>>(gl, W, H, r, pl, w.keys);
-        k_prep<<<sg, 256, 0, s>>>(gr, W, H, r, prr, nullptr);
         counted(2);
-        if (h->p.cost_dtype != CDT_NONE) {
+    };
+    auto stats = [&](int i, cudaStream_t st) {
+        const Pair& q = P[i];
+        PairWs w = q.w;
+        PrepOut pl, prr;
+        prep_layouts(q.W, q.d_min, q.D, K, w, pl, prr);
+        dim3 sg((q.W + PT - 1) / PT, (q.H + PT - 1) / PT);
+        k_prep<<<sg, 256, 0, st>>>(q.gl, q.W, q.H, q.r, pl, w.keys);
+        k_prep<<<sg, 256, 0, st>>>(q.gr, q.W, q.H, q.r, prr, nullptr);
+        counted(2);
+        if (cdt != CDT_NONE) {
+            const int W = q.W, H = q.H, r = q.r;
             const long nb = (W <= 2 * r || H <= 2 * r) ? (long)W * H : 2L * r * W + 2L * r * (H - 2 * r);
-            k_cost_border_nan<<<(int)std::max<long>(1, std::min<long>(4096, (nb * cost_stride(D) + 255) / 256)),
-                                256, 0, s>>>(w.cost, h->p.cost_dtype, W, H, r, cost_stride(D));
+            k_cost_border_nan<<<(int)std::max<long>(1, std::min<long>(4096, (nb * cost_stride(q.D) + 255) / 256)),
+                                256, 0, st>>>(w.cost, cdt, W, H, r, cost_stride(q.D));
             counted();
+        }
+    };
+    auto finalize = [&](int i, cudaStream_t st) {
+        const stereo_pair* pr = &pairs[i];
+        const Pair& q = P[i];
+        void* cost = cdt != CDT_NONE ? q.w.cost : nullptr;
+        int16_t* wta = pr->disp_wta ? pr->disp_wta : q.w.wta;
+        PrepOut pl, prr;
+        prep_layouts(q.W, q.d_min, q.D, K, q.w, pl, prr);
+        launch_finalize(q.w.keys, q.w.keys + (size_t)q.W * q.H, q.W, q.H, q.d_min, q.D, h->p.lr_thresh, cost,
+                        cdt, q.gl, q.gr, q.r, h->p.sampling, FinStats{q.w.lstats, q.w.ustats, prr.ustride, prr.ucol0},
+                        wta, nullptr, pr->disp_sub, q.w.lr, st);
+        counted();
+        if (pr->disp_lr)
+            cudaMemcpyAsync(pr->disp_lr, q.w.lr, (size_t)q.W * q.H * 2, cudaMemcpyDeviceToDevice, st);
+    };
+    auto post = [&](int i, cudaStream_t st) {
+        const stereo_pair* pr = &pairs[i];
+        const Pair& q = P[i];
+        run_postprocess(h->p, q.w.lr, q.W, q.H, q.w, pr->disp_post ? pr->disp_post : q.w.post, st);
+    };
+    auto refine = [&](int i, cudaStream_t st) {
+        const stereo_pair* pr = &pairs[i];
+        const Pair& q = P[i];
+        void* cost = cdt != CDT_NONE ? q.w.cost : nullptr;
+        run_refine(h->p, pr->disp_post ? pr->disp_post : q.w.post, cost, cdt, q.gl, q.gr, q.W, q.H, q.d_min,
+                   q.D, q.r, h->p.sampling, q.w, pr->disp_final ? pr->disp_final : q.w.dfin, nullptr, pr->valid,
+                   st);
+    };
+    if (!cost_only) {
+        if (timed) {
+            mark(h, 0, s);
+            fan_out(h, pairs, n, s, input);
+            mark(h, 1, s);
+            fan_out(h, pairs, n, s, stats);
+            mark(h, 2, s);
+        } else {
+            fan_out(h, pairs, n, s, [&](int i, cudaStream_t st) { input(i, st); stats(i, st); });
         }
     }
     cudaMemsetAsync(h->counter, 0, sizeof(int), s);
-    if (K == 4) launch_cost_batched_k4(h->p.cost_dtype, h->pair_args, h->pair_radius, h->units, h->n_units,
-                                       h->counter, s);
-    else launch_cost_batched_k2(h->p.cost_dtype, h->pair_args, h->pair_radius, h->units, h->n_units,
-                                h->counter, s);
+    if (K == 4) launch_cost_batched_k4(cdt, h->pair_args, h->pair_radius, h->units, h->n_units, h->counter, s);
+    else launch_cost_batched_k2(cdt, h->pair_args, h->pair_radius, h->units, h->n_units, h->counter, s);
     counted();
     if (cost_only) return;
-    for (int i = 0; i < n; ++i) {
-        const stereo_pair* pr = &pairs[i];
-        int d_min, D, r;
-        resolve_pair(h, pr, d_min, D, r);
-        const int W = pr->width, H = pr->height;
-        const int cdt = h->p.cost_dtype;
-        PairWs w = carve(h->ws + (size_t)i * h->pair_bytes, (size_t)W * H, h->p.num_disp, cdt,
-                         h->p.max_width, h->p.max_height);
-        const uint8_t* gl = (pr->channels == 3 || pr->pitch != W) ? w.gl : pr->left;
-        const uint8_t* gr = (pr->channels == 3 || pr->pitch != W) ? w.gr : pr->right;
-        void* cost = cdt != CDT_NONE ? w.cost : nullptr;
-        int16_t* wta = pr->disp_wta ? pr->disp_wta : w.wta;
-        dim3 fg((W + 127) / 128, H);
-        k_finalize<<<fg, 128, 0, s>>>(w.keys, w.keys + (size_t)W * H, W, H, d_min, D, h->p.lr_thresh, cost,
-                                      cdt, gl, gr, r, h->p.sampling, wta, nullptr, pr->disp_sub, w.lr);
-        counted();
-        if (pr->disp_lr) cudaMemcpyAsync(pr->disp_lr, w.lr, (size_t)W * H * 2, cudaMemcpyDeviceToDevice, s);
-        int16_t* post = pr->disp_post ? pr->disp_post : w.post;
-        run_postprocess(h->p, w.lr, W, H, w, post, s);
-        float* dfin = pr->disp_final ? pr->disp_final : w.dfin;
-        run_refine(h->p, post, cost, cdt, gl, gr, W, H, d_min, D, r, h->p.sampling, w, dfin, nullptr,
-                   pr->valid, s);
+    if (timed) {
+        mark(h, 3, s);
+        fan_out(h, pairs, n, s, finalize);
+        mark(h, 4, s);
+        fan_out(h, pairs, n, s, post);
+        mark(h, 5, s);
+        fan_out(h, pairs, n, s, refine);
+        mark(h, 6, s);
+    } else {
+        fan_out(h, pairs, n, s, [&](int i, cudaStream_t st) { finalize(i, st); post(i, st); refine(i, st); });
     }
 }
 
@@ -933,9 +1035,21 @@ stereo_status stereo_match(stereo_handle* h, const stereo_pair* pr, void* stream
 }
 
 // ---- soft-argmin -----------------------------------------------------------
+static void launch_soft_box_t1(int r, const float* A, const float* L, const float* R, int W, int H, int nch,
+                               int cs, int d_min, int ty, float* T1L, float* T1R, cudaStream_t s) {
+    const long warps = (long)((W + SOFT_RUN - 1) / SOFT_RUN) * ((H + ty - 1) / ty) * nch;
+    const unsigned g = (unsigned)((warps * 32 + SOFT_BOX_THREADS - 1) / SOFT_BOX_THREADS);
+#define SBT_CASE(RV) \
+    case RV: k_soft_box_t1<RV><<<g, SOFT_BOX_THREADS, 0, s>>>(A, L, R, W, H, nch, cs, d_min, ty, T1L, T1R); break;
+    switch (r) {
+        SBT_CASE(1) SBT_CASE(2) SBT_CASE(3) SBT_CASE(4) SBT_CASE(5) SBT_CASE(6) default: SBT_CASE(7)
+    }
+#undef SBT_CASE
+}
+
 static stereo_status check_soft(const stereo_handle* h, int B, int W, int H, int d_min, int D, int r,
                                 float tau) {
-    if (!h || B < 1 || W < 1 || H < 1 || D < 1 || D > STEREO_MAX_DISP || r < 1 || r > SB_MAXR)
+    if (!h || B < 1 || W < 1 || H < 1 || D < 1 || D > STEREO_MAX_DISP || r < 1 || r > STEREO_MAX_WIN_RADIUS)
         return STEREO_ERR_INVALID_ARG;
     if (!h->p.soft_argmin) return STEREO_ERR_INVALID_ARG;
     if (!(tau > 0.f)) return STEREO_ERR_INVALID_ARG;
@@ -948,15 +1062,17 @@ static stereo_status check_soft(const stereo_handle* h, int B, int W, int H, int
 // Float window statistics + fused cost kernel (rho into the handle's cost
 // volume) for one pair of float images.
 static void soft_prepare(stereo_handle* h, const PairWs& w, const float* L, const float* R, int W, int H,
-                         int d_min, int D, int r, SoftArgs& sa, cudaStream_t s) {
+                         int d_min, int D, int r, SoftArgs& sa, cudaStream_t s, bool timed) {
     const int K = pick_k(D);
     PrepOut pl, pr;
     prep_layouts(W, d_min, D, K, w, pl, pr);
     dim3 sg((W + PT - 1) / PT, (H + PT - 1) / PT);
+    if (timed) mark(h, 0, s);
     k_prep_f32<<<sg, 256, 0, s>>>(L, W, H, r, pl);
     counted();
     k_prep_f32<<<sg, 256, 0, s>>>(R, W, H, r, pr);
     counted();
+    if (timed) mark(h, 1, s);
     const int cs = cost_stride(D);
     const long nb = (W <= 2 * r || H <= 2 * r) ? (long)W * H : 2L * r * W + 2L * r * (H - 2 * r);
     k_cost_border_nan<<<(int)std::max<long>(1, std::min<long>(4096, (nb * cs + 255) / 256)), 256, 0, s>>>(
@@ -965,6 +1081,7 @@ static void soft_prepare(stereo_handle* h, const PairWs& w, const float* L, cons
     CostArgs a{pl.img, pl.stride, pl.col0, pr.img, pr.stride, pr.col0, w.lstats, w.ustats,
                pr.ustride, pr.ucol0, w.keys, w.keys + (size_t)W * H, w.cost, CDT_F32, W, H, d_min, D, 0};
     launch_cost(r, K, CDT_F32, a, g_cost_rows, s);
+    if (timed) mark(h, 2, s);
     sa = SoftArgs{reinterpret_cast<const float*>(w.cost), cs, w.lstats, w.ustats, pr.ustride, pr.ucol0,
                   W, H, d_min, D, r, 0.f};
 }
@@ -979,11 +1096,17 @@ stereo_status stereo_softargmin_fwd(stereo_handle* h, const float* left, const f
     const size_t npix = (size_t)width * height;
     PairWs w = carve(h->ws, npix, h->p.num_disp, h->p.cost_dtype, h->p.max_width, h->p.max_height, 1);
     for (int b = 0; b < batch; ++b) {
+        const bool timed = h->timing && h->ev_ready && b == batch - 1;
         SoftArgs sa;
-        soft_prepare(h, w, left + b * npix, right + b * npix, width, height, d_min, num_disp, win_radius, sa, s);
+        soft_prepare(h, w, left + b * npix, right + b * npix, width, height, d_min, num_disp, win_radius, sa, s,
+                     timed);
         sa.tau = tau;
-        k_soft_fwd<<<(unsigned)((npix * 32 + 255) / 256), 256, 0, s>>>(sa, d_soft + b * npix, lse + b * npix);
+        const unsigned runs = (unsigned)(((width + SOFT_RUN - 1) / SOFT_RUN) * height);
+        const int nch = (num_disp + 31) / 32;
+        k_soft_fwd<<<runs, 32 * nch, soft_run_smem(nch), s>>>(sa, d_soft + b * npix, lse + b * npix);
         counted();
+        if (timed)
+            for (int k = 3; k <= STEREO_NUM_STAGES; ++k) mark(h, k, s);
     }
     return last_error();
 }
@@ -1002,31 +1125,34 @@ stereo_status stereo_softargmin_bwd(stereo_handle* h, const float* left, const f
     const int W = width, H = height, r = win_radius;
     const size_t npix = (size_t)W * H;
     PairWs w = carve(h->ws, npix, h->p.num_disp, h->p.cost_dtype, h->p.max_width, h->p.max_height, 1);
-    const unsigned gw = (unsigned)((npix * 32 + 255) / 256), gp = (unsigned)((npix + 255) / 256);
+    const unsigned runs = (unsigned)(((W + SOFT_RUN - 1) / SOFT_RUN) * H);
+    const int nch = (num_disp + 31) / 32;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int ty = soft_box_rows(W, H, nch, sms);
     for (int b = 0; b < batch; ++b) {
         const float* L = left + b * npix;
         const float* R = right + b * npix;
+        const bool timed = h->timing && h->ev_ready && b == batch - 1;
         SoftArgs sa;
-        soft_prepare(h, w, L, R, W, H, d_min, num_disp, r, sa, s);
+        soft_prepare(h, w, L, R, W, H, d_min, num_disp, r, sa, s, timed);
         sa.tau = tau;
-        k_soft_bwd_a<<<gw, 256, 0, s>>>(sa, d_soft + b * npix, lse + b * npix, grad_dsoft + b * npix,
-                                        w.softA, w.sP1, w.sP2);
+        cudaMemsetAsync(w.sP1, 0, (size_t)((char*)w.sT1R - (char*)w.sP1) + npix * 4, s);   // P1..T1R
+        k_soft_dA<<<runs, 32 * nch, soft_run_smem(nch), s>>>(sa, d_soft + b * npix, lse + b * npix, grad_dsoft + b * npix, w.softA,
+                                     w.sP1, w.sP2, w.sQ1, w.sQ2);
         counted();
-        k_soft_bwd_q<<<gp, 256, 0, s>>>(sa, w.softA, w.sQ1, w.sQ2);
+        if (timed) mark(h, 3, s);
+        launch_soft_box_t1(r, w.softA, L, R, W, H, nch, sa.cs, d_min, ty, w.sT1L, w.sT1R, s);
         counted();
-        k_soft_box<<<dim3((W + SB_T - 1) / SB_T, (H + SB_T - 1) / SB_T, (sa.cs + SB_D - 1) / SB_D), 256, 0, s>>>(
-            w.softA, W, H, sa.cs, r, w.softM);
-        counted();
-        k_soft_t1l<<<gw, 256, 0, s>>>(w.softM, R, W, H, sa.cs, d_min, num_disp, w.sT1L);
-        counted();
-        k_soft_t1r<<<gp, 256, 0, s>>>(w.softM, L, W, H, sa.cs, d_min, num_disp, w.sT1R);
-        counted();
+        if (timed) { mark(h, 4, s); mark(h, 5, s); }
         const int span = SF_T + 2 * r;
         const size_t fsm = (size_t)(6 * span * span + 6 * span * SF_T) * 4;
         k_soft_final<<<dim3((W + SF_T - 1) / SF_T, (H + SF_T - 1) / SF_T), 256, fsm, s>>>(
             w.sT1L, w.sT1R, w.sP1, w.sP2, w.sQ1, w.sQ2, w.lstats, sa, L, R, grad_left + b * npix,
             grad_right + b * npix);
         counted();
+        if (timed) mark(h, 6, s);
     }
     return last_error();
 }
@@ -1077,7 +1203,7 @@ stereo_status stereo_match_batched(stereo_handle* h, const stereo_pair* pairs, i
         if (st != STEREO_OK) return st;
         h->table_key = key;
     }
-    if (!use_graph) {
+    if (!use_graph || h->timing) {          // per-stage events: plain launches
         enqueue_batched(h, pairs, n, s);
         return last_error();
     }

@@ -1,0 +1,120 @@
+"""Precision form: cost volume stored in FP16 / BF16 (window sums and ZNCC in
+FP32), 960x540 tissue pair, D = 0..191, 15x15 window.  Reports the disparity
+error against the FP64 oracle per storage format (max |dd| and the share of
+pixels with |dd| > 0.01 px) and bounds it.
+
+Where the storage format can and cannot matter:
+  * winner-take-all and the right-view winners are decided in FP32 inside the
+    cost kernel before the store: bit-exact (near-ties exempt) in every
+    format;
+  * sub-pixel offsets recompute their three costs in FP32 when the volume is
+    FP16/BF16: within 0.01 px in every format;
+  * refinement reads the stored volume in its search for the new integer
+    disparity o (Sec. II-C), so a candidate whose energy is within the
+    storage rounding of the best can win instead; then the refined value at
+    that pixel and its neighbourhood moves.  That share is reported and
+    bounded (FP32 keeps the usual 1e-4 relative bar).
+
+Run with -s to see the report lines.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import NEAR_TIE, SUB_TOL, REFINE_RTOL, to_np, int_map_mismatch, describe
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2007_12623_b300 as st  # noqa: E402
+
+W, H, D, R = 960, 540, 192, 7
+CROP = (190, 280, 160, 400)          # y0, x0, height, width
+STRIP = (264, 12)                    # first row, rows
+FORMATS = {"f32": st.COST_F32, "f16": st.COST_F16, "bf16": st.COST_BF16}
+
+
+@pytest.fixture(scope="module")
+def dev():
+    assert torch.cuda.is_available()
+    st.lib()
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def pair():
+    return synth.tissue_pair(synth.seed_for(2), W, H, 10.0, 170.0)
+
+
+@pytest.fixture(scope="module")
+def crop_oracle(pair):
+    y0, x0, ch, cw = CROP
+    L = oracle.gray(pair[0])[y0:y0 + ch, x0:x0 + cw]
+    Rg = oracle.gray(pair[1])[y0:y0 + ch, x0:x0 + cw]
+    p = oracle.Params(d_min=0, num_disp=D, win_radius=R, smooth_radius=15)
+    return oracle.pipeline(L, Rg, p), oracle.match(L, Rg, 0, D, R)
+
+
+def _run(dev, Lrgb, Rrgb, cdt):
+    Hh, Ww = Lrgb.shape[:2]
+    sp = st.stereo_default_params(max_width=Ww, max_height=Hh, num_disp=D, win_radius=R, cost_dtype=cdt,
+                                  smooth_radius=15)
+    h = st.stereo_create(sp)
+    out = dict(disp_wta=torch.empty((Hh, Ww), dtype=torch.int16, device=dev),
+               disp_sub=torch.empty((Hh, Ww), dtype=torch.float32, device=dev),
+               disp_post=torch.empty((Hh, Ww), dtype=torch.int16, device=dev),
+               valid=torch.empty((Hh, Ww), dtype=torch.uint8, device=dev),
+               disp_final=torch.empty((Hh, Ww), dtype=torch.float32, device=dev))
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    st.stereo_match(h, t(Lrgb), t(Rrgb), **out)
+    torch.cuda.synchronize()
+    h.close()
+    return {k: to_np(v) for k, v in out.items()}
+
+
+@pytest.mark.parametrize("fmt", ["f16", "bf16"])
+def test_full_size_strip_winners_and_subpixel(dev, pair, fmt):
+    """Full-size run; on a strip of rows the oracle computes the winners and
+    sub-pixel disparities exactly (they depend only on windows inside the
+    strip plus its margins)."""
+    g = _run(dev, pair[0], pair[1], FORMATS[fmt])
+    y0, n = STRIP
+    Lg, Rg = oracle.gray(pair[0]), oracle.gray(pair[1])
+    m = oracle.match(Lg[y0 - R:y0 + n + R], Rg[y0 - R:y0 + n + R], 0, D, R)
+    ref_d, ref_s, gap = m["dL"][R:R + n], m["sub"][R:R + n], m["gapL"][R:R + n]
+    got_d, got_s = g["disp_wta"][y0:y0 + n], g["disp_sub"][y0:y0 + n]
+    bad = int_map_mismatch(got_d, ref_d, gap < NEAR_TIE)
+    assert len(bad) == 0, describe(bad, got_d, ref_d)
+    same = (got_d == ref_d) & (ref_d != oracle.INVALID)
+    err = np.abs(got_s[same] - ref_s[same])
+    print(f"\n[precision {fmt}] sub-pixel vs FP64 oracle, rows {y0}..{y0 + n - 1} of the full-size run: "
+          f"{err.size} px, max |dd| = {err.max():.2e} px, {100 * np.mean(err > 0.01):.4f}% > 0.01 px")
+    assert err.max() <= SUB_TOL
+
+
+@pytest.mark.parametrize("fmt", ["f32", "f16", "bf16"])
+def test_whole_path_crop_error(dev, pair, crop_oracle, fmt):
+    """Whole path on a 400x160 crop against the oracle's whole path on the
+    same crop."""
+    ref, m = crop_oracle
+    y0, x0, ch, cw = CROP
+    g = _run(dev, np.ascontiguousarray(pair[0][y0:y0 + ch, x0:x0 + cw]),
+             np.ascontiguousarray(pair[1][y0:y0 + ch, x0:x0 + cw]), FORMATS[fmt])
+    near = (m["gapL"] < NEAR_TIE)
+    bad = int_map_mismatch(g["disp_wta"], ref["dL"], near)
+    assert len(bad) == 0, describe(bad, g["disp_wta"], ref["dL"])
+    if not near.any() and not (m["gapR"] < NEAR_TIE).any():
+        assert np.array_equal(g["disp_post"], ref["o_post"])
+    v = (ref["o_post"] != oracle.INVALID) & (g["valid"] != 0)
+    d = np.abs(g["disp_final"][v] - ref["d_final"][v])
+    rel = d / np.maximum(np.abs(ref["d_final"][v]), 1)
+    print(f"\n[precision {fmt}] refined disparity vs FP64 oracle on the {cw}x{ch} crop: {d.size} px, "
+          f"max |dd| = {d.max():.3e} px, {100 * np.mean(d > 0.01):.4f}% > 0.01 px, "
+          f"{100 * np.mean(rel > REFINE_RTOL):.4f}% beyond 1e-4 relative")
+    if fmt == "f32":
+        assert np.mean(rel > REFINE_RTOL) <= 0.005
+    else:
+        # selection flips in the refinement search move a small share of pixels
+        assert np.mean(d > 0.01) <= 0.05
+        assert np.median(d) <= 1e-3
