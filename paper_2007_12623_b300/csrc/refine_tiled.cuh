@@ -2,11 +2,15 @@
 // improved Laplacian refinement is two kernels, each a (2 rs + 1)^2 box sum
 // over a 32x32 output tile with an rs-pixel halo (row sums, then column
 // sums, sliding along 8-element segments):
-//   k_refine_box1: dt = mean of valid o (Eq. 1); b = dt - alpha o -
-//                  (1 - alpha) d_prev (Eq. 2); also the valid count
-//   k_refine_box2: d = dt - mean of valid b (Eq. 3)
-// followed by k_refine_oupdate (Eq. 4, one thread per pixel).  The same
-// rules as refine.cuh (kept for radii beyond the tile halo).
+//   k_refine_box1:  dt = mean of valid o (Eq. 1); b = dt - alpha o -
+//                   (1 - alpha) d_prev (Eq. 2); also the valid count.  o and
+//                   the valid flag travel packed in one 32-bit integer,
+//                   (o - d_min) << 12 | 1, whose box sum holds both sums
+//                   exactly (count < 4096, sum of (o - d_min) < 2^20).
+//   k_refine_box2o: d = dt - mean of valid b (Eq. 3), then the new integer
+//                   disparity o (Eq. 4) of the same pixel.
+// The first iteration reads the post-processed map directly (d_prev = o).
+// The same rules as refine.cuh (kept for radii beyond the tile halo).
 #pragma once
 #include "common.cuh"
 
@@ -54,35 +58,29 @@ __device__ __forceinline__ void box_cols(const T* rsum, int rs, T* out /* [RT][R
     }
 }
 
+// dprev == nullptr: first iteration, d_prev = o.
 __global__ void __launch_bounds__(RT_THREADS) k_refine_box1(const int16_t* __restrict__ o,
                                                             const float* __restrict__ dprev, int W,
-                                                            int H, int rs, float alpha,
+                                                            int H, int rs, float alpha, int d_min,
                                                             float* __restrict__ dt,
                                                             float* __restrict__ b,
                                                             int16_t* __restrict__ cnt_out) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int sw = RT + 2 * rs, sh = RT + 2 * rs;
-    int* vo = reinterpret_cast<int*>(sm);                  // [sh][sw] valid o (0 if invalid)
-    int* vc = vo + sw * sh;                                // [sh][sw] valid flag
-    int* ro = vc + sw * sh;                                // [sh][RT]
-    int* rc = ro + sh * RT;                                // [sh][RT]
-    int* so = rc + sh * RT;                                // [RT][RT]
-    int* sc = so + RT * RT;                                // [RT][RT]
+    uint32_t* vp = reinterpret_cast<uint32_t*>(sm);        // [sh][sw] packed (o - d_min) << 12 | valid
+    uint32_t* rp = vp + sw * sh;                           // [sh][RT]
+    uint32_t* sp = rp + sh * RT;                           // [RT][RT]
     const int x0 = blockIdx.x * RT - rs, y0 = blockIdx.y * RT - rs;
     for (int i = threadIdx.x; i < sw * sh; i += RT_THREADS) {
-        const int gx = x0 + i % sw, gy = y0 + i / sw;
+        const int gy = y0 + i / sw, gx = x0 + i % sw;
         int v = ST_INVALID;
         if (gx >= 0 && gx < W && gy >= 0 && gy < H) v = o[(size_t)gy * W + gx];
-        const bool ok = v != ST_INVALID;
-        vo[i] = ok ? v : 0;
-        vc[i] = ok ? 1 : 0;
+        vp[i] = v != ST_INVALID ? ((uint32_t)(v - d_min) << 12) | 1u : 0u;
     }
     __syncthreads();
-    box_rows<int>(vo, sw, sh, rs, ro);
-    box_rows<int>(vc, sw, sh, rs, rc);
+    box_rows<uint32_t>(vp, sw, sh, rs, rp);
     __syncthreads();
-    box_cols<int>(ro, rs, so);
-    box_cols<int>(rc, rs, sc);
+    box_cols<uint32_t>(rp, rs, sp);
     __syncthreads();
     for (int i = threadIdx.x; i < RT * RT; i += RT_THREADS) {
         const int gx = blockIdx.x * RT + i % RT, gy = blockIdx.y * RT + i / RT;
@@ -95,52 +93,20 @@ __global__ void __launch_bounds__(RT_THREADS) k_refine_box1(const int16_t* __res
             cnt_out[gi] = 0;
             continue;
         }
-        const float m = (float)so[i] / (float)sc[i];          // Eq. (1)
+        const uint32_t sum = sp[i];
+        const int c = (int)(sum & 4095u);
+        const int osum = (int)(sum >> 12) + d_min * c;
+        const float m = (float)osum / (float)c;              // Eq. (1)
         dt[gi] = m;
-        b[gi] = m - alpha * (float)ov - (1.f - alpha) * dprev[gi];   // Eq. (2)
-        cnt_out[gi] = (int16_t)sc[i];
-    }
-}
-
-__global__ void __launch_bounds__(RT_THREADS) k_refine_box2(
-    const int16_t* __restrict__ o, float* __restrict__ dprev, const float* __restrict__ dt,
-    const float* __restrict__ b, const int16_t* __restrict__ cnt, int W, int H, int rs,
-    float* __restrict__ d_out) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int sw = RT + 2 * rs, sh = RT + 2 * rs;
-    float* vb = reinterpret_cast<float*>(sm);              // [sh][sw]
-    float* rb = vb + sw * sh;                              // [sh][RT]
-    float* sb = rb + sh * RT;                              // [RT][RT]
-    const int x0 = blockIdx.x * RT - rs, y0 = blockIdx.y * RT - rs;
-    for (int i = threadIdx.x; i < sw * sh; i += RT_THREADS) {
-        const int gx = x0 + i % sw, gy = y0 + i / sw;
-        float v = 0.f;
-        if (gx >= 0 && gx < W && gy >= 0 && gy < H) v = b[(size_t)gy * W + gx];  // 0 if invalid
-        vb[i] = v;
-    }
-    __syncthreads();
-    box_rows<float>(vb, sw, sh, rs, rb);
-    __syncthreads();
-    box_cols<float>(rb, rs, sb);
-    __syncthreads();
-    for (int i = threadIdx.x; i < RT * RT; i += RT_THREADS) {
-        const int gx = blockIdx.x * RT + i % RT, gy = blockIdx.y * RT + i / RT;
-        if (gx >= W || gy >= H) continue;
-        const size_t gi = (size_t)gy * W + gx;
-        const int ov = o[gi];
-        if (ov == ST_INVALID) {
-            if (d_out) d_out[gi] = __int_as_float(0x7fc00000);
-            continue;
-        }
-        const float d = dt[gi] - sb[i] / (float)cnt[gi];      // Eq. (3)
-        dprev[gi] = d;
-        if (d_out) d_out[gi] = d;
+        const float dp = dprev ? dprev[gi] : (float)ov;
+        b[gi] = m - alpha * (float)ov - (1.f - alpha) * dp;  // Eq. (2)
+        cnt_out[gi] = (int16_t)c;
     }
 }
 
 inline size_t refine_box1_smem(int rs) {
     const size_t sw = RT + 2 * rs, sh = RT + 2 * rs;
-    return (2 * sw * sh + 2 * sh * RT + 2 * RT * RT) * 4;
+    return (sw * sh + sh * RT + RT * RT) * 4;
 }
 inline size_t refine_box2_smem(int rs) {
     const size_t sw = RT + 2 * rs, sh = RT + 2 * rs;
@@ -165,20 +131,15 @@ __device__ __forceinline__ void oupdate_consider(int cand, float rho, float d, f
     }
 }
 
-__global__ void __launch_bounds__(256) k_refine_oupdate(int16_t* __restrict__ o, const float* __restrict__ dk,
-                                                        int n, float eta, int search, int d_min, int D,
-                                                        const void* __restrict__ cost, int cdt,
-                                                        const uint8_t* __restrict__ L,
-                                                        const uint8_t* __restrict__ Rm, int W, int H,
-                                                        int r, int sampling) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int ov = o[i];
-    if (ov == ST_INVALID) return;
-    const float d = dk[i];
+// New integer disparity of valid pixel i (Eq. 4) given its refined d; returns
+// `ov` when no candidate qualifies.
+__device__ __forceinline__ int oupdate_pixel(size_t i, int ov, float d, float eta, int search, int d_min,
+                                             int D, const void* __restrict__ cost, int cdt,
+                                             const uint8_t* __restrict__ L, const uint8_t* __restrict__ Rm,
+                                             int W, int H, int r, int sampling) {
     const int lo = max((int)ceilf(d - (float)search), d_min);
     const int hi = min((int)floorf(d + (float)search), d_min + D - 1);
-    if (lo > hi) return;
+    if (lo > hi) return ov;
     int best = ST_INVALID;
     float bf = 0.f, bdist = 0.f;
     const int cs = cost_stride(D);
@@ -227,5 +188,53 @@ __global__ void __launch_bounds__(256) k_refine_oupdate(int16_t* __restrict__ o,
             oupdate_consider(cand, rho, d, eta, best, bf, bdist);
         }
     }
-    if (best != ST_INVALID) o[i] = (int16_t)best;
+    return best != ST_INVALID ? best : ov;
+}
+
+// Eq. (3) and Eq. (4) for one tile: o_src is read at the block's own pixels
+// only, so o_dst may alias it.  First iteration: o_src is the
+// post-processed map, o_dst the working copy (written at every pixel), and
+// `valid` (optional) receives the validity mask.
+__global__ void __launch_bounds__(RT_THREADS) k_refine_box2o(
+    const int16_t* o_src, int16_t* o_dst, float* __restrict__ dprev,
+    const float* __restrict__ dt, const float* __restrict__ b, const int16_t* __restrict__ cnt, int W, int H,
+    int rs, float* __restrict__ d_out, uint8_t* __restrict__ valid, float eta, int search, int d_min, int D,
+    const void* __restrict__ cost, int cdt, const uint8_t* __restrict__ L, const uint8_t* __restrict__ Rm,
+    int r, int sampling) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int sw = RT + 2 * rs, sh = RT + 2 * rs;
+    float* vb = reinterpret_cast<float*>(sm);              // [sh][sw]
+    float* rb = vb + sw * sh;                              // [sh][RT]
+    float* sb = rb + sh * RT;                              // [RT][RT]
+    const int x0 = blockIdx.x * RT - rs, y0 = blockIdx.y * RT - rs;
+    for (int i = threadIdx.x; i < sw * sh; i += RT_THREADS) {
+        const int gy = y0 + i / sw, gx = x0 + i % sw;
+        float v = 0.f;
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H) v = b[(size_t)gy * W + gx];  // 0 if invalid
+        vb[i] = v;
+    }
+    __syncthreads();
+    box_rows<float>(vb, sw, sh, rs, rb);
+    __syncthreads();
+    box_cols<float>(rb, rs, sb);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < RT * RT / RT_THREADS; ++q) {
+        const int i = threadIdx.x + q * RT_THREADS;
+        const int gx = blockIdx.x * RT + i % RT, gy = blockIdx.y * RT + i / RT;
+        if (gx >= W || gy >= H) continue;
+        const size_t gi = (size_t)gy * W + gx;
+        const int ov = o_src[gi];
+        if (valid) valid[gi] = ov != ST_INVALID;
+        if (ov == ST_INVALID) {
+            if (d_out) d_out[gi] = __int_as_float(0x7fc00000);
+            if (o_dst != o_src) o_dst[gi] = (int16_t)ST_INVALID;
+            continue;
+        }
+        const float d = dt[gi] - sb[i] / (float)cnt[gi];      // Eq. (3)
+        dprev[gi] = d;
+        if (d_out) d_out[gi] = d;
+        o_dst[gi] = (int16_t)oupdate_pixel(gi, ov, d, eta, search, d_min, D, cost, cdt, L, Rm, W, H, r,
+                                           sampling);          // Eq. (4)
+    }
 }

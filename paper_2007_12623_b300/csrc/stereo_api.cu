@@ -230,7 +230,7 @@ void set_smem_attributes() {
     cudaFuncSetAttribute(k_fill_radial_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_fill_disc_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_refine_box1, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_refine_box2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_refine_box2o, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_soft_final, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_soft_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_soft_dA, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -349,25 +349,26 @@ void run_refine(const stereo_params& p, const int16_t* o_in, const void* cost, i
                 int sampling, const PairWs& w, float* d_out, int16_t* o_out, uint8_t* valid,
                 cudaStream_t s) {
     const int n = W * H;
-    k_refine_init<<<(n + 255) / 256, 256, 0, s>>>(o_in, n, w.o, w.dprev, d_out, valid);
-    counted();
     const int rs = p.smooth_radius;
+    const bool tiled = rs <= RT_MAX_RS;
+    if (!tiled || p.smooth_iters == 0) {
+        k_refine_init<<<(n + 255) / 256, 256, 0, s>>>(o_in, n, w.o, w.dprev, d_out, valid);
+        counted();
+    }
     const int bx = 128;
     dim3 gr2((W + bx - 1) / bx, H);
     const size_t rsmem = (size_t)((bx + 2 * rs + 1) & ~1) * 2 + (size_t)(bx + 2 * rs) * 4;
-    const bool tiled = rs <= RT_MAX_RS;
     dim3 rg((W + RT - 1) / RT, (H + RT - 1) / RT);
     for (int k = 0; k < p.smooth_iters; ++k) {
         float* dk = k == p.smooth_iters - 1 ? d_out : nullptr;
         if (tiled) {
-            k_refine_box1<<<rg, RT_THREADS, refine_box1_smem(rs), s>>>(w.o, w.dprev, W, H, rs, p.alpha,
-                                                                       w.dt, w.b, w.cnt);
+            const int16_t* osrc = k == 0 ? o_in : w.o;
+            k_refine_box1<<<rg, RT_THREADS, refine_box1_smem(rs), s>>>(osrc, k == 0 ? nullptr : w.dprev, W, H,
+                                                                       rs, p.alpha, d_min, w.dt, w.b, w.cnt);
             counted();
-            k_refine_box2<<<rg, RT_THREADS, refine_box2_smem(rs), s>>>(w.o, w.dprev, w.dt, w.b, w.cnt, W,
-                                                                       H, rs, dk);
-            counted();
-            k_refine_oupdate<<<(n + 255) / 256, 256, 0, s>>>(w.o, w.dprev, n, p.eta, p.refine_search, d_min,
-                                                             D, cost, cdt, gl, gr, W, H, r, sampling);
+            k_refine_box2o<<<rg, RT_THREADS, refine_box2_smem(rs), s>>>(
+                osrc, w.o, w.dprev, w.dt, w.b, w.cnt, W, H, rs, dk, k == 0 ? valid : nullptr, p.eta,
+                p.refine_search, d_min, D, cost, cdt, gl, gr, r, sampling);
             counted();
         } else {
             k_refine_rows<<<gr2, bx, rsmem, s>>>(w.o, nullptr, W, H, rs, w.rsC, w.rsO, nullptr);
