@@ -95,7 +95,7 @@ def lib():
             "stereo_stage_lr": (C.c_int, [P, P, i32, i32, i32, P, P]),
             "stereo_stage_outlier": (C.c_int, [P, P, i32, i32, i32, f32, P, P]),
             "stereo_stage_fill_radial": (C.c_int, [P, P, i32, i32, i32, i32, P, P]),
-            "stereo_stage_fill_disc": (C.c_int, [P, i32, i32, i32, i32, P, P]),
+            "stereo_stage_fill_disc": (C.c_int, [P, P, i32, i32, i32, i32, P, P]),
             "stereo_stage_postprocess": (C.c_int, [P, P, i32, i32, P, P]),
             "stereo_stage_refine": (C.c_int, [P, P, P, i32, P, P, i32, i32, i32, i32, i32, P, P, P]),
             "stereo_set_stage_timing": (C.c_int, [P, i32]),
@@ -328,10 +328,10 @@ def stereo_stage_fill_radial(handle: Handle, inp, radius, min_dirs, out, stream=
            "stereo_stage_fill_radial")
 
 
-def stereo_stage_fill_disc(inp, radius, min_count, out, stream=None):
+def stereo_stage_fill_disc(handle: Handle, inp, radius, min_count, out, stream=None):
     import torch
     H, W = inp.shape
-    _check(lib().stereo_stage_fill_disc(_ptr(inp, torch.int16), W, H, radius, min_count,
+    _check(lib().stereo_stage_fill_disc(handle.ptr, _ptr(inp, torch.int16), W, H, radius, min_count,
                                         _ptr(out, torch.int16), _stream(stream)),
            "stereo_stage_fill_disc")
 

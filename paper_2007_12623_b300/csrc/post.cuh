@@ -5,143 +5,19 @@
 #pragma once
 #include "common.cuh"
 
-// The 8 radial directions of Sec. II-B (axis steps and diagonal steps).
-__constant__ int c_dir8[8][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1},
-                                 {1, 1}, {1, -1}, {-1, 1}, {-1, -1}};
-
-// A valid pixel is kept when, along at least one of its 8 radial directions,
-// the next `radius` pixels are inside the image, valid, and neighbouring
-// disparities differ by less than `thresh`.
-__global__ void k_outlier(const int16_t* __restrict__ in, int W, int H, int radius, float thresh,
-                          int16_t* __restrict__ out) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= W || y >= H) return;
-    const size_t i = (size_t)y * W + x;
-    const int v = in[i];
-    if (v == ST_INVALID) { out[i] = (int16_t)ST_INVALID; return; }
-    bool keep = false;
-    for (int k = 0; k < 8 && !keep; ++k) {
-        const int dx = c_dir8[k][0], dy = c_dir8[k][1];
-        // the whole ray must be inside the image
-        const int ex = x + radius * dx, ey = y + radius * dy;
-        if (ex < 0 || ex >= W || ey < 0 || ey >= H) continue;
-        int prev = v;
-        bool ok = true;
-        const int16_t* p = in + i;
-        const ptrdiff_t step = (ptrdiff_t)dy * W + dx;
-        for (int s = 1; s <= radius; ++s) {
-            p += step;
-            const int q = __ldg(p);
-            if (q == ST_INVALID || !(fabsf((float)(q - prev)) < thresh)) { ok = false; break; }
-            prev = q;
-        }
-        keep = ok;
-    }
-    out[i] = keep ? (int16_t)v : (int16_t)ST_INVALID;
-}
-
-// First method: each hole takes the first valid pixel along each of its 8
-// directions within `radius`; with at least `min_dirs` hits it receives the
-// weighted mean with weights radius + 1 - distance, rounded half up.
-__global__ void k_fill_radial(const int16_t* __restrict__ in, int W, int H, int radius,
-                              int min_dirs, int16_t* __restrict__ out) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= W || y >= H) return;
-    const size_t i = (size_t)y * W + x;
-    const int v = in[i];
-    if (v != ST_INVALID) { out[i] = (int16_t)v; return; }
-    int num = 0, den = 0, found = 0;
-    for (int k = 0; k < 8; ++k) {
-        const int dx = c_dir8[k][0], dy = c_dir8[k][1];
-        // steps that stay inside the image
-        int smax = radius;
-        if (dx > 0) smax = min(smax, W - 1 - x);
-        if (dx < 0) smax = min(smax, x);
-        if (dy > 0) smax = min(smax, H - 1 - y);
-        if (dy < 0) smax = min(smax, y);
-        const int16_t* p = in + i;
-        const ptrdiff_t step = (ptrdiff_t)dy * W + dx;
-        for (int s = 1; s <= smax; ++s) {
-            p += step;
-            const int q = __ldg(p);
-            if (q != ST_INVALID) {
-                const int w = radius + 1 - s;
-                num += w * q;
-                den += w;
-                ++found;
-                break;
-            }
-        }
-    }
-    out[i] = (found >= min_dirs && den > 0) ? (int16_t)round_half_up_i(num, den) : (int16_t)ST_INVALID;
-}
-
-// Second method: each hole counts the valid pixels within Euclidean
-// distance `radius`; with at least `min_count` of them it receives their
-// mean, rounded half up.  Shared-memory tile with a `radius` halo.
-constexpr int FD_TILE = 32;
-constexpr int FD_MAXR = 24;
-
-__global__ void __launch_bounds__(256) k_fill_disc(const int16_t* __restrict__ in, int W, int H,
-                                                   int radius, int min_count,
-                                                   int16_t* __restrict__ out) {
-    extern __shared__ int16_t tile[];   // (FD_TILE + 2 radius)^2
-    const int span = FD_TILE + 2 * radius;
-    const int x0 = blockIdx.x * FD_TILE, y0 = blockIdx.y * FD_TILE;
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nthr = blockDim.x * blockDim.y;
-    // skip tiles without holes quickly
-    __shared__ int any_hole;
-    if (tid == 0) any_hole = 0;
-    __syncthreads();
-    for (int i = tid; i < FD_TILE * FD_TILE; i += nthr) {
-        const int gx = x0 + i % FD_TILE, gy = y0 + i / FD_TILE;
-        if (gx < W && gy < H && in[(size_t)gy * W + gx] == ST_INVALID) any_hole = 1;
-    }
-    __syncthreads();
-    if (!any_hole) {
-        for (int i = tid; i < FD_TILE * FD_TILE; i += nthr) {
-            const int gx = x0 + i % FD_TILE, gy = y0 + i / FD_TILE;
-            if (gx < W && gy < H) out[(size_t)gy * W + gx] = in[(size_t)gy * W + gx];
-        }
-        return;
-    }
-    for (int i = tid; i < span * span; i += nthr) {
-        const int gx = x0 - radius + i % span, gy = y0 - radius + i / span;
-        tile[i] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? in[(size_t)gy * W + gx]
-                                                            : (int16_t)ST_INVALID;
-    }
-    __syncthreads();
-    const int r2 = radius * radius;
-    for (int i = tid; i < FD_TILE * FD_TILE; i += nthr) {
-        const int lx = i % FD_TILE, ly = i / FD_TILE;
-        const int gx = x0 + lx, gy = y0 + ly;
-        if (gx >= W || gy >= H) continue;
-        const int v = tile[(ly + radius) * span + lx + radius];
-        if (v != ST_INVALID) { out[(size_t)gy * W + gx] = (int16_t)v; continue; }
-        int sum = 0, cnt = 0;
-        for (int dy = -radius; dy <= radius; ++dy) {
-            int w = 0;
-            while ((w + 1) * (w + 1) + dy * dy <= r2) ++w;
-            const int16_t* row = tile + (ly + radius + dy) * span + lx + radius;
-            for (int dx = -w; dx <= w; ++dx) {
-                const int q = row[dx];
-                if (q != ST_INVALID) { sum += q; ++cnt; }
-            }
-        }
-        out[(size_t)gy * W + gx] = (cnt >= min_count && cnt > 0) ? (int16_t)round_half_up_i(sum, cnt)
-                                                                 : (int16_t)ST_INVALID;
-    }
-}
-
+// The rules.  Outlier removal: a valid pixel is kept when, along at least one
+// of its 8 radial directions (axis and diagonal steps), the next `radius`
+// pixels are inside the image, valid, and neighbouring disparities differ by
+// less than `thresh`.  First hole-filling method (radial): each hole takes
+// the first valid pixel along each of its 8 directions within `radius`;
+// with at least `min_dirs` hits it receives the weighted mean with weights
+// radius + 1 - distance, rounded half up.  (The second, disc method is in
+// post_tiled.cuh.)
+//
 // ---------------------------------------------------------------------------
-// Direction-parallel forms: 8 consecutive lanes of a warp take the 8 radial
-// directions of one pixel, each lane walks its ray with 8 loads in flight,
-// and the lanes combine their results with shuffles.  No halo staging, any
-// radius; same rules as k_outlier / k_fill_radial above.
-
+// Direction-parallel forms (any radius): 8 consecutive lanes of a warp take
+// the 8 radial directions of one pixel, each lane walks its ray with 8 loads
+// in flight, and the lanes combine their results with shuffles.
 __device__ __forceinline__ void dir8(int k, int& dx, int& dy) {
     dx = (k == 0 || k == 4 || k == 5) ? 1 : ((k == 1 || k == 6 || k == 7) ? -1 : 0);
     dy = (k == 2 || k == 4 || k == 6) ? 1 : ((k == 3 || k == 5 || k == 7) ? -1 : 0);
@@ -244,13 +120,29 @@ __global__ void __launch_bounds__(256) k_fill_radial_dirs(const int16_t* __restr
 // 32 per word by a warp ballot; bits outside the image are 0.  A ray is then
 // a run of bits on one line: the outlier test asks for r set bits, the fill
 // for the nearest set bit, each a few word loads instead of a walk.
+//
+// Layout: word k of line l of family f is words[off[f] + (k + LM_PAD_LO) *
+// lines(f) + l], k in [-LM_PAD_LO, nw[f] + LM_PAD_HI): word-major, so the 32
+// pixels of a row segment (consecutive lines of families 1-3, one word of
+// family 0) read consecutive words; the zero pad words let every lookup of
+// a 64-bit window starting in [-64, 32 nw] run without bounds checks.  The
+// whole buffer is zeroed once per pipeline call; the builder writes the
+// same words (those with a pixel in the image) every time, so the pads and
+// the words outside the image stay 0.
+constexpr int LM_PAD_LO = 2, LM_PAD_HI = 3;
+
 struct LineMasks {
     uint32_t* words;
     int W, H;
-    int nw[4];          // 32-bit words per line of each family
+    int nw[4];          // data words per line of each family
     size_t off[4];      // first word of each family
     __host__ __device__ int lines(int f) const { return f == 0 ? H : (f == 1 ? W : W + H - 1); }
-    __host__ __device__ size_t total() const { return off[3] + (size_t)lines(3) * nw[3]; }
+    __host__ __device__ size_t total() const {
+        return off[3] + (size_t)lines(3) * (nw[3] + LM_PAD_LO + LM_PAD_HI);
+    }
+    __host__ __device__ size_t index(int f, int line, int k) const {
+        return off[f] + (size_t)(k + LM_PAD_LO) * lines(f) + line;
+    }
 };
 
 inline LineMasks make_line_masks(uint32_t* words, int W, int H) {
@@ -262,7 +154,7 @@ inline LineMasks make_line_masks(uint32_t* words, int W, int H) {
     for (int f = 0; f < 4; ++f) {
         m.nw[f] = f == 1 ? (H + 31) / 32 : (W + 31) / 32;
         m.off[f] = o;
-        o += (size_t)m.lines(f) * m.nw[f];
+        o += (size_t)m.lines(f) * (m.nw[f] + LM_PAD_LO + LM_PAD_HI);
     }
     return m;
 }
@@ -277,64 +169,17 @@ __device__ __forceinline__ void fam_coords(const LineMasks& m, int f, int x, int
     else if (f == 2) { line = x - y + m.H - 1; pos = x; }
     else { line = x + y; pos = x; }
 }
-__device__ __forceinline__ void fam_pixel_at(const LineMasks& m, int f, int line, int pos, int& x, int& y) {
-    if (f == 0) { x = pos; y = line; }
-    else if (f == 1) { x = line; y = pos; }
-    else if (f == 2) { x = pos; y = pos - (line - m.H + 1); }
-    else { x = pos; y = line - pos; }
-}
 
-// mode 0: bit = pixel valid; mode 1: bit = pixel and its next pixel along
-// the line both valid with |difference| < thresh.
-__global__ void __launch_bounds__(256) k_line_masks(const int16_t* __restrict__ in, LineMasks m, int mode,
-                                                    float thresh) {
-    const long warp_id = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    long rem = warp_id;
-    int f = 0;
-    for (; f < 4; ++f) {
-        const long n = (long)m.lines(f) * m.nw[f];
-        if (rem < n) break;
-        rem -= n;
-    }
-    if (f >= 4) return;                                  // whole warp beyond the last word
-    const int line = (int)(rem / m.nw[f]), wi = (int)(rem % m.nw[f]);
-    int x, y;
-    fam_pixel_at(m, f, line, 32 * wi + lane, x, y);
-    bool bit = false;
-    if (x >= 0 && x < m.W && y >= 0 && y < m.H) {
-        const int v = in[(size_t)y * m.W + x];
-        if (mode == 0) {
-            bit = v != ST_INVALID;
-        } else {
-            int dx, dy;
-            fam_dir(f, dx, dy);
-            const int nx = x + dx, ny = y + dy;
-            if (v != ST_INVALID && nx >= 0 && nx < m.W && ny >= 0 && ny < m.H) {
-                const int q = in[(size_t)ny * m.W + nx];
-                bit = q != ST_INVALID && fabsf((float)(q - v)) < thresh;
-            }
-        }
-    }
-    const uint32_t word = __ballot_sync(0xffffffffu, bit);
-    if (lane == 0) m.words[m.off[f] + (size_t)line * m.nw[f] + wi] = word;
-}
-
-// 64 bits of line `line` of family f starting at position s (bits before
-// position 0 or past the line's last word read as 0).
+// 64 bits of line `line` of family f starting at position s, -64 <= s <=
+// 32 nw[f] (bits before position 0 or past the line's last word read as 0).
 __device__ __forceinline__ uint64_t mask_bits64(const LineMasks& m, int f, int line, int s) {
-    const uint32_t* w = m.words + m.off[f] + (size_t)line * m.nw[f];
-    const int nw = m.nw[f];
-    const int i = s >= 0 ? s / 32 : -((31 - s) / 32);    // floor(s / 32)
-    const int o = s - 32 * i;                            // 0..31
-    uint32_t a[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const int k = i + j;
-        a[j] = (k >= 0 && k < nw) ? __ldg(w + k) : 0u;
-    }
-    const uint64_t lo = (uint64_t)a[0] | ((uint64_t)a[1] << 32);
-    return o ? (lo >> o) | ((uint64_t)a[2] << (64 - o)) : lo;
+    const int k = s >> 5;                                // floor(s / 32)
+    const int o = s & 31;
+    const size_t L = (size_t)m.lines(f);
+    const uint32_t* w = m.words + m.index(f, line, k);
+    const uint32_t a0 = __ldg(w), a1 = __ldg(w + L), a2 = __ldg(w + 2 * L);
+    const uint32_t lo = __funnelshift_r(a0, a1, o), hi = __funnelshift_r(a1, a2, o);
+    return (uint64_t)lo | ((uint64_t)hi << 32);
 }
 __device__ __forceinline__ uint64_t low_bits(int n) { return n >= 64 ? ~0ull : ((1ull << n) - 1ull); }
 
@@ -434,8 +279,9 @@ __global__ void __launch_bounds__(256) k_line_masks_tiled(const int16_t* __restr
         const int q = t[ly + dy][lx + dx];
         return v != ST_INVALID && q != ST_INVALID && fabsf((float)(q - v)) < thresh;
     };
-    for (int job = warp; job < 4 * 32; job += 8) {
-        const int f = job >> 5, i = job & 31;
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+    for (int i = warp; i < 32; i += 8) {
         int lx, ly, line, wi;
         bool ok = true;
         if (f == 0) {                 // row 32 br + i, columns 32 bc + lane
@@ -460,6 +306,6 @@ __global__ void __launch_bounds__(256) k_line_masks_tiled(const int16_t* __restr
         const bool inside = gx < m.W && gy >= 0 && gy < m.H;
         const bool bit = inside && pred(f, lx, ly);
         const uint32_t word = __ballot_sync(0xffffffffu, bit);
-        if (lane == 0) m.words[m.off[f] + (size_t)line * m.nw[f] + wi] = word;
+        if (lane == 0) m.words[m.index(f, line, wi)] = word;
     }
 }

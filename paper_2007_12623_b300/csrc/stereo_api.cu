@@ -226,9 +226,6 @@ void set_smem_attributes() {
     static bool done = false;
     if (done) return;
     done = true;
-    cudaFuncSetAttribute(k_outlier_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_fill_radial_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_fill_disc_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_refine_box1, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_refine_box2o, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_soft_final, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -283,9 +280,14 @@ void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, in
 // One outlier pass / radial fill pass: mask build + query for radii up to
 // 63 (64 for the outlier test), the direction-parallel walk beyond.
 // Builds the line bitmasks of `in` (mode 0 valid, 1 smooth edge).
+// Zeroes the line-mask buffer of a W x H map (pads and words outside the
+// image stay 0 through every build of the same geometry).
+void zero_masks(uint32_t* words, int W, int H, cudaStream_t s) {
+    cudaMemsetAsync(words, 0, make_line_masks(words, W, H).total() * 4, s);
+}
+
 void build_masks(const int16_t* in, int W, int H, int mode, float thresh, uint32_t* words, cudaStream_t s) {
     LineMasks m = make_line_masks(words, W, H);
-    cudaMemsetAsync(words, 0, m.total() * 4, s);
     k_line_masks_tiled<<<dim3((W + 31) / 32, (H + 31) / 32 + 2), 256, 0, s>>>(in, m, mode, thresh);
     counted();
 }
@@ -319,27 +321,33 @@ void run_fill_radial(const int16_t* in, int W, int H, int radius, int min_dirs, 
     counted();
 }
 
+// Disc fill: row prefixes of the packed map into the (otherwise unused
+// during post-processing) refinement row-sum buffer, then the queries.
+void run_fill_disc(const int16_t* in, int W, int H, int radius, int min_count, const PairWs& w, int16_t* out,
+                   cudaStream_t s) {
+    uint32_t* S = reinterpret_cast<uint32_t*>(w.rsC);
+    k_row_prefix<<<H, DISC_PREFIX_THREADS, 0, s>>>(in, W, S);
+    k_fill_disc_prefix<<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, s>>>(in, S, W, H, radius, min_count,
+                                                                              out);
+    counted(2);
+}
+
 void run_postprocess(const stereo_params& p, const int16_t* in, int W, int H, const PairWs& w,
                      int16_t* out, cudaStream_t s) {
-    dim3 b2(32, 8), g2((W + 31) / 32, (H + 7) / 8);
-    dim3 gd((W + FD_TILE - 1) / FD_TILE, (H + FD_TILE - 1) / FD_TILE);
     const int min_count = p.fill_disc_min_count >= 0 ? p.fill_disc_min_count
                                                      : (disc_area(p.fill_disc_r) + 3) / 4;
-    const size_t fd_smem = (size_t)(FD_TILE + 2 * p.fill_disc_r) * (FD_TILE + 2 * p.fill_disc_r) * 2;
     const int16_t* cur = in;
     if (p.outlier_rounds <= 0) {
         cudaMemcpyAsync(out, in, (size_t)W * H * 2, cudaMemcpyDeviceToDevice, s);
         return;
     }
-    dim3 tg((W + PT_W - 1) / PT_W, (H + PT_H - 1) / PT_H);
+    zero_masks(w.masks, W, H, s);
     for (int t = 0; t < p.outlier_rounds; ++t) {
         const int rad = p.r0 + t * p.dr;
         run_outlier(cur, W, H, rad, p.outlier_thresh, w.masks, w.p, s);
         run_fill_radial(w.p, W, H, p.fill_radial_r, p.fill_radial_min_dirs, w.masks, w.q, s);
         int16_t* dst = (t == p.outlier_rounds - 1) ? out : w.t;
-        k_fill_disc_tiled<<<tg, PT_THREADS, disc_tile_smem(p.fill_disc_r), s>>>(w.q, W, H, p.fill_disc_r,
-                                                                               min_count, dst);
-        counted();
+        run_fill_disc(w.q, W, H, p.fill_disc_r, min_count, w, dst, s);
         cur = dst;
     }
 }
@@ -694,6 +702,7 @@ stereo_status stereo_stage_outlier(stereo_handle* h, const int16_t* in, int32_t 
         return STEREO_ERR_INVALID_ARG;
     if (W > h->p.max_width || H > h->p.max_height) return STEREO_ERR_TOO_LARGE;
     PairWs w = carve(h->ws, (size_t)W * H, h->p.num_disp, h->p.cost_dtype, h->p.max_width, h->p.max_height);
+    zero_masks(w.masks, W, H, S(stream));
     run_outlier(in, W, H, radius, thresh, w.masks, out, S(stream));
     return last_error();
 }
@@ -704,19 +713,19 @@ stereo_status stereo_stage_fill_radial(stereo_handle* h, const int16_t* in, int3
         return STEREO_ERR_INVALID_ARG;
     if (W > h->p.max_width || H > h->p.max_height) return STEREO_ERR_TOO_LARGE;
     PairWs w = carve(h->ws, (size_t)W * H, h->p.num_disp, h->p.cost_dtype, h->p.max_width, h->p.max_height);
+    zero_masks(w.masks, W, H, S(stream));
     run_fill_radial(in, W, H, radius, min_dirs, w.masks, out, S(stream));
     return last_error();
 }
 
-stereo_status stereo_stage_fill_disc(const int16_t* in, int32_t W, int32_t H, int32_t radius,
-                                     int32_t min_count, int16_t* out, void* stream) {
-    if (!in || !out || in == out || W < 1 || H < 1 || radius < 0 || radius > PT_MAX_HALO)
+stereo_status stereo_stage_fill_disc(stereo_handle* h, const int16_t* in, int32_t W, int32_t H,
+                                     int32_t radius, int32_t min_count, int16_t* out, void* stream) {
+    if (!h || !in || !out || in == out || W < 1 || H < 1 || radius < 0 || radius > PT_MAX_HALO)
         return STEREO_ERR_INVALID_ARG;
-    set_smem_attributes();
+    if (W > h->p.max_width || H > h->p.max_height) return STEREO_ERR_TOO_LARGE;
     if (min_count < 0) min_count = (disc_area(radius) + 3) / 4;
-    k_fill_disc_tiled<<<dim3((W + PT_W - 1) / PT_W, (H + PT_H - 1) / PT_H), PT_THREADS,
-                        disc_tile_smem(radius), S(stream)>>>(in, W, H, radius, min_count, out);
-    counted();
+    PairWs w = carve(h->ws, (size_t)W * H, h->p.num_disp, h->p.cost_dtype, h->p.max_width, h->p.max_height);
+    run_fill_disc(in, W, H, radius, min_count, w, out, S(stream));
     return last_error();
 }
 

@@ -51,7 +51,7 @@ def test_host_side_argument_checks(L):
     # stage calls validate sizes and pointers before any launch
     assert L.stereo_stage_lr(None, None, 10, 10, 1, None, None) == 1
     assert L.stereo_stage_outlier(None, C.c_void_p(16), 0, 10, 10, 2.5, C.c_void_p(32), None) == 1
-    assert L.stereo_stage_fill_disc(C.c_void_p(16), 8, 8, 99, -1, C.c_void_p(32), None) == 1
+    assert L.stereo_stage_fill_disc(None, C.c_void_p(16), 8, 8, 20, -1, C.c_void_p(32), None) == 1
     assert L.stereo_match(None, None, None) == 1
     assert L.stereo_gray(None, 4, 4, 12, None, None) == 1
     assert L.stereo_destroy(None) == 0

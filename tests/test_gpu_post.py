@@ -82,13 +82,26 @@ def test_fill_radial(dev, radius, min_dirs):
     assert np.array_equal(to_np(out), want)
 
 
-@pytest.mark.parametrize("radius", [2, 7, 20, 24, 40])
+@pytest.mark.parametrize("radius", [0, 2, 7, 20, 24, 40, 56])
 def test_fill_disc(dev, radius):
     rng = np.random.default_rng(100 + radius)
     m = _random_map(rng, 75, 83, -5, 50, 0.55)
     out = torch.empty_like(T(m, dev))
-    st.stereo_stage_fill_disc(T(m, dev), radius, -1, out)
+    st.stereo_stage_fill_disc(_handle(*m.shape), T(m, dev), radius, -1, out)
     want = oracle.fill_disc(m, radius)
+    assert np.array_equal(to_np(out), want)
+
+
+def test_fill_disc_wide_rows_large_values(dev):
+    """1920-wide rows of disparities near 4300 (the row prefixes wrap around
+    32 bits; every disc span stays exact) and negative values."""
+    rng = np.random.default_rng(7)
+    m = rng.integers(4200, 4352, (12, 1920)).astype(np.int16)
+    m[:, :40] = rng.integers(-4096, -4000, (12, 40)).astype(np.int16)
+    m[rng.random(m.shape) < 0.3] = INV
+    out = torch.empty_like(T(m, dev))
+    st.stereo_stage_fill_disc(_handle(*m.shape), T(m, dev), 20, -1, out)
+    want = oracle.fill_disc(m, 20)
     assert np.array_equal(to_np(out), want)
 
 
