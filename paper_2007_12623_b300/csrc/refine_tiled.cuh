@@ -122,7 +122,7 @@ __device__ __forceinline__ void oupdate_consider(int cand, float rho, float d, f
                                                  float& bf, float& bdist) {
     if (!(rho > 0.f)) return;                           // NaN (invalid) or non-positive
     const float diff = (float)cand - d;
-    const float f = 1.f / rho + eta * diff * diff;
+    const float f = __frcp_rn(rho) + eta * diff * diff;   // __frcp_rn(rho) == 1.f / rho
     const float dist = fabsf(diff);
     if (best == ST_INVALID || f < bf || (f == bf && dist < bdist)) {
         best = cand;
@@ -194,7 +194,8 @@ __device__ __forceinline__ int oupdate_pixel(size_t i, int ov, float d, float et
 // Eq. (3) and Eq. (4) for one tile: o_src is read at the block's own pixels
 // only, so o_dst may alias it.  First iteration: o_src is the
 // post-processed map, o_dst the working copy (written at every pixel), and
-// `valid` (optional) receives the validity mask.
+// `valid` (optional) receives the validity mask.  o_dst == nullptr: Eq. (4)
+// is skipped (last iteration when nobody reads the final o).
 __global__ void __launch_bounds__(RT_THREADS) k_refine_box2o(
     const int16_t* o_src, int16_t* o_dst, float* __restrict__ dprev,
     const float* __restrict__ dt, const float* __restrict__ b, const int16_t* __restrict__ cnt, int W, int H,
@@ -228,13 +229,13 @@ __global__ void __launch_bounds__(RT_THREADS) k_refine_box2o(
         if (valid) valid[gi] = ov != ST_INVALID;
         if (ov == ST_INVALID) {
             if (d_out) d_out[gi] = __int_as_float(0x7fc00000);
-            if (o_dst != o_src) o_dst[gi] = (int16_t)ST_INVALID;
+            if (o_dst && o_dst != o_src) o_dst[gi] = (int16_t)ST_INVALID;
             continue;
         }
         const float d = dt[gi] - sb[i] / (float)cnt[gi];      // Eq. (3)
         dprev[gi] = d;
         if (d_out) d_out[gi] = d;
-        o_dst[gi] = (int16_t)oupdate_pixel(gi, ov, d, eta, search, d_min, D, cost, cdt, L, Rm, W, H, r,
+        if (o_dst) o_dst[gi] = (int16_t)oupdate_pixel(gi, ov, d, eta, search, d_min, D, cost, cdt, L, Rm, W, H, r,
                                            sampling);          // Eq. (4)
     }
 }

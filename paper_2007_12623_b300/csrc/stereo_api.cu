@@ -374,8 +374,10 @@ void run_refine(const stereo_params& p, const int16_t* o_in, const void* cost, i
             k_refine_box1<<<rg, RT_THREADS, refine_box1_smem(rs), s>>>(osrc, k == 0 ? nullptr : w.dprev, W, H,
                                                                        rs, p.alpha, d_min, w.dt, w.b, w.cnt);
             counted();
+            // the o after the last iteration only matters when the caller reads it
+            int16_t* odst = (k == p.smooth_iters - 1 && !o_out) ? nullptr : w.o;
             k_refine_box2o<<<rg, RT_THREADS, refine_box2_smem(rs), s>>>(
-                osrc, w.o, w.dprev, w.dt, w.b, w.cnt, W, H, rs, dk, k == 0 ? valid : nullptr, p.eta,
+                osrc, odst, w.dprev, w.dt, w.b, w.cnt, W, H, rs, dk, k == 0 ? valid : nullptr, p.eta,
                 p.refine_search, d_min, D, cost, cdt, gl, gr, r, sampling);
             counted();
         } else {
