@@ -138,10 +138,12 @@ stereo_status stereo_destroy(stereo_handle* h);
 /* Whole path on one pair (Sec. II): gray -> ZNCC + WTA + sub-pixel ->
  * LR check -> outlier/hole loop -> Laplacian refinement.  Enqueued on
  * `stream`.  On a non-default stream the launch sequence is captured into a
- * CUDA graph on the first call and replayed while the pair's pointers and
- * sizes stay the same (the first call with new arguments captures again);
- * when the caller's stream is itself being captured the kernels are
- * enqueued into the caller's capture. */
+ * CUDA graph on the first call with given pointers and sizes and replayed
+ * on later calls with the same arguments; the handle keeps the graphs of the
+ * 4 most recently used argument sets (e.g. the buffer sets of a
+ * double-buffered loop).  When the caller's stream is itself being captured
+ * the kernels are enqueued into the caller's capture.  Calls on one handle
+ * share its workspace: they must be ordered (same stream, or synchronised). */
 stereo_status stereo_match(stereo_handle* h, const stereo_pair* pair, void* stream);
 
 /* The same path on n pairs of mixed sizes, disparity ranges (per-pair

@@ -150,11 +150,41 @@ int disc_area(int r) {
 
 }  // namespace
 
-// One captured launch sequence, keyed by the bytes of its arguments.
-struct GraphCache {
+// Captured launch sequences, keyed by the bytes of their arguments; up to
+// GRAPH_SLOTS of them (e.g. the two buffer sets of a double-buffered video
+// loop), the least recently used one replaced first.
+constexpr int GRAPH_SLOTS = 4;
+
+struct GraphEntry {
     std::vector<uint8_t> key;
     cudaGraphExec_t exec = nullptr;
     unsigned long long kernels = 0;   // kernels in the graph (launch accounting)
+    unsigned long long used = 0;
+};
+
+struct GraphCache {
+    GraphEntry e[GRAPH_SLOTS];
+    unsigned long long tick = 0;
+    GraphEntry* find(const void* key, size_t len) {
+        for (auto& g : e)
+            if (g.exec && g.key.size() == len && memcmp(g.key.data(), key, len) == 0) return &g;
+        return nullptr;
+    }
+    GraphEntry* victim() {
+        GraphEntry* v = &e[0];
+        for (auto& g : e) {
+            if (!g.exec) return &g;
+            if (g.used < v->used) v = &g;
+        }
+        return v;
+    }
+    void clear() {
+        for (auto& g : e) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+            g.key.clear();
+        }
+    }
 };
 
 constexpr int BATCH_STREAMS = 8;
@@ -504,28 +534,35 @@ static stereo_status run_with_graph(stereo_handle* h, GraphCache& gc, const void
         enqueue(s);
         return last_error();
     }
-    if (!gc.exec || gc.key.size() != key_len || memcmp(gc.key.data(), key, key_len) != 0) {
-        if (gc.exec) { cudaGraphExecDestroy(gc.exec); gc.exec = nullptr; }
+    GraphEntry* g = gc.find(key, key_len);
+    if (!g) {
+        g = gc.victim();
+        if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
+        g->key.clear();
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return last_error();
+        const unsigned long long b0 = g_launches.load();
         enqueue(s);
+        g->kernels = g_launches.load() - b0;
+        g_launches.fetch_sub(g->kernels, std::memory_order_relaxed);   // counted when replayed
         cudaError_t e = cudaStreamEndCapture(s, &graph);
         if (e != cudaSuccess || !graph) {
             cudaGetLastError();
             if (graph) cudaGraphDestroy(graph);
             return STEREO_ERR_CUDA;
         }
-        e = cudaGraphInstantiate(&gc.exec, graph, 0);
+        e = cudaGraphInstantiate(&g->exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            gc.exec = nullptr;
+            g->exec = nullptr;
             return STEREO_ERR_CUDA;
         }
-        gc.key.assign(reinterpret_cast<const uint8_t*>(key), reinterpret_cast<const uint8_t*>(key) + key_len);
+        g->key.assign(reinterpret_cast<const uint8_t*>(key), reinterpret_cast<const uint8_t*>(key) + key_len);
     }
-    if (cudaGraphLaunch(gc.exec, s) != cudaSuccess) return last_error();
-    g_launches.fetch_add(gc.kernels, std::memory_order_relaxed);
+    g->used = ++gc.tick;
+    if (cudaGraphLaunch(g->exec, s) != cudaSuccess) return last_error();
+    g_launches.fetch_add(g->kernels, std::memory_order_relaxed);
     return last_error();
 }
 
@@ -635,8 +672,8 @@ stereo_status stereo_create(const stereo_params* p, int32_t max_batch, stereo_ha
 stereo_status stereo_destroy(stereo_handle* h) {
     if (!h) return STEREO_OK;
     cudaDeviceSynchronize();
-    if (h->single.exec) cudaGraphExecDestroy(h->single.exec);
-    if (h->batch.exec) cudaGraphExecDestroy(h->batch.exec);
+    h->single.clear();
+    h->batch.clear();
     if (h->ev_ready)
         for (int i = 0; i <= STEREO_NUM_STAGES; ++i) cudaEventDestroy(h->ev[i]);
     cudaFree(h->ws);
@@ -1036,14 +1073,8 @@ stereo_status stereo_match(stereo_handle* h, const stereo_pair* pr, void* stream
         return last_error();
     }
     struct { stereo_pair p; int cost_rows; } key{*pr, g_cost_rows};
-    const unsigned long long before = g_launches.load();
-    stereo_status rs = run_with_graph(h, h->single, &key, sizeof(key), s, [&](cudaStream_t cs) {
-        const unsigned long long b0 = g_launches.load();
-        enqueue_match(h, pr, 0, cs, false);
-        h->single.kernels = g_launches.load() - b0;
-    });
-    (void)before;
-    return rs;
+    return run_with_graph(h, h->single, &key, sizeof(key), s,
+                          [&](cudaStream_t cs) { enqueue_match(h, pr, 0, cs, false); });
 }
 
 // ---- soft-argmin -----------------------------------------------------------
@@ -1214,16 +1245,14 @@ stereo_status stereo_match_batched(stereo_handle* h, const stereo_pair* pairs, i
         stereo_status st = build_batch_tables(h, pairs, n, K, rows, s);
         if (st != STEREO_OK) return st;
         h->table_key = key;
+        h->batch.clear();                  // captured batches read the device tables just replaced
     }
     if (!use_graph || h->timing) {          // per-stage events: plain launches
         enqueue_batched(h, pairs, n, s);
         return last_error();
     }
-    return run_with_graph(h, h->batch, key.data(), key.size(), s, [&](cudaStream_t cs2) {
-        const unsigned long long b0 = g_launches.load();
-        enqueue_batched(h, pairs, n, cs2);
-        h->batch.kernels = g_launches.load() - b0;
-    });
+    return run_with_graph(h, h->batch, key.data(), key.size(), s,
+                          [&](cudaStream_t cs2) { enqueue_batched(h, pairs, n, cs2); });
 }
 
 stereo_status stereo_set_batch_config(stereo_handle* h, int32_t rows, int32_t K) {

@@ -138,3 +138,43 @@ def test_graph_replay_matches_direct_launches(dev):
             for k in ref:
                 assert torch.equal(o[k].nan_to_num(-1), ref[k].nan_to_num(-1)), k
     h.close()
+
+
+def test_graph_cache_alternating_buffer_sets(dev):
+    """A double-buffered loop alternates two argument sets (two cached
+    graphs): every call writes the same maps as plain launches, and the
+    launch counter counts each call's kernels once, capturing calls
+    included."""
+    H, W = 96, 160
+    pairs = []
+    for i in range(2):
+        Lrgb, Rrgb, gt = synth.tissue_pair(synth.seed_for(1, 10 + i), W, H, 2.0, 20.0)
+        pairs.append((T(Lrgb, dev), T(Rrgb, dev)))
+    sp = st.stereo_default_params(max_width=W, max_height=H, num_disp=32, smooth_radius=4)
+    h = st.stereo_create(sp)
+
+    def outs():
+        return dict(disp_wta=torch.empty((H, W), dtype=torch.int16, device=dev),
+                    disp_final=torch.empty((H, W), dtype=torch.float32, device=dev))
+
+    refs = []
+    for tL, tR in pairs:
+        o = outs()
+        st.stereo_match(h, tL, tR, **o)          # default stream: plain launches
+        torch.cuda.synchronize()
+        refs.append(o)
+    bufs = [outs(), outs()]
+    s = torch.cuda.Stream()
+    per_call = None
+    for it in range(6):
+        i = it % 2
+        n0 = st.stereo_launch_count()
+        with torch.cuda.stream(s):
+            st.stereo_match(h, *pairs[i], **bufs[i], stream=s)
+        s.synchronize()
+        n = st.stereo_launch_count() - n0
+        per_call = per_call or n
+        assert n == per_call
+        for k in refs[i]:
+            assert torch.equal(bufs[i][k].nan_to_num(-1), refs[i][k].nan_to_num(-1)), (it, k)
+    h.close()
