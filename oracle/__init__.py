@@ -66,6 +66,7 @@ def lib():
         P = C.c_void_p
         i, d = C.c_int, C.c_double
         sig = {
+            "or_depth_points": (None, [P, i, i, d, d, d, d, d, P, P]),
             "or_gray": (None, [P, i, i, P]),
             "or_candidate_valid": (i, [i, i, i, i, i, i]),
             "or_zncc": (d, [P, P, i, i, i, i, i, i, i]),
@@ -316,3 +317,16 @@ def l1_loss(dsoft, has_valid, gt):
     g = np.empty_like(ds)
     loss = lib().or_l1_loss(_p(ds), _p(hv), _p(gt), ds.size, _p(g))
     return loss, g.reshape(np.shape(dsoft))
+
+
+def depth_points(disp, f, cx, cy, B, doffs=0.0):
+    """Disparity -> points and normals in the left camera frame (Sec. II,
+    reprojection of a rectified pair).  Returns (xyz [H, W, 3], normals
+    [H, W, 3]), NaN where undefined."""
+    d = np.ascontiguousarray(disp, np.float64)
+    H, W = d.shape
+    xyz = np.empty((H, W, 3))
+    nrm = np.empty((H, W, 3))
+    lib().or_depth_points(_p(d), W, H, float(f), float(cx), float(cy), float(B), float(doffs),
+                          _p(xyz), _p(nrm))
+    return xyz, nrm

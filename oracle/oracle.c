@@ -663,3 +663,60 @@ double or_l1_loss(const double* dsoft, const uint8_t* has_valid,
     }
     return nv ? s / (double)nv : 0.0;
 }
+
+/* Disparity -> 3-D points in the left rectified camera frame, the
+ * reprojection of a calibrated rectified pair (Sec. II: physical depths are
+ * computed directly from the disparities after calibration, equivalently to
+ * Matlab's reconstructScene):
+ *     Z = f B / (d + doffs),  X = (u - cx) Z / f,  Y = (v - cy) Z / f,
+ * with doffs = right principal point minus left principal point.  NaN (all
+ * three coordinates) where d is NaN or d + doffs <= 0.
+ * Normals: the cross product of the central differences
+ *     (P(u+1,v) - P(u-1,v)) x (P(u,v+1) - P(u,v-1)),
+ * turned to face the camera (n . P <= 0) and normalised; NaN where one of
+ * the four neighbours is missing (image border or NaN point) or the cross
+ * product vanishes.  xyz and nrm are [H][W][3]; either may be NULL. */
+void or_depth_points(const double* d, int W, int H, double f, double cx, double cy,
+                     double B, double doffs, double* xyz, double* nrm) {
+    const double nan = NAN;
+    double* P = (double*)malloc(sizeof(double) * 3 * (size_t)W * H);
+    for (int v = 0; v < H; ++v)
+        for (int u = 0; u < W; ++u) {
+            double* p = P + 3 * ((size_t)v * W + u);
+            const double dv = d[(size_t)v * W + u];
+            if (isnan(dv) || !(dv + doffs > 0.0)) {
+                p[0] = p[1] = p[2] = nan;
+                continue;
+            }
+            const double Z = f * B / (dv + doffs);
+            p[0] = (u - cx) * Z / f;
+            p[1] = (v - cy) * Z / f;
+            p[2] = Z;
+        }
+    if (xyz) memcpy(xyz, P, sizeof(double) * 3 * (size_t)W * H);
+    if (nrm) {
+        for (int v = 0; v < H; ++v)
+            for (int u = 0; u < W; ++u) {
+                double* n = nrm + 3 * ((size_t)v * W + u);
+                n[0] = n[1] = n[2] = nan;
+                if (u < 1 || u > W - 2 || v < 1 || v > H - 2) continue;
+                const double* pc = P + 3 * ((size_t)v * W + u);
+                const double* pl = P + 3 * ((size_t)v * W + u - 1);
+                const double* pr = P + 3 * ((size_t)v * W + u + 1);
+                const double* pu = P + 3 * ((size_t)(v - 1) * W + u);
+                const double* pd = P + 3 * ((size_t)(v + 1) * W + u);
+                if (isnan(pc[2]) || isnan(pl[2]) || isnan(pr[2]) || isnan(pu[2]) || isnan(pd[2])) continue;
+                const double a[3] = {pr[0] - pl[0], pr[1] - pl[1], pr[2] - pl[2]};
+                const double b[3] = {pd[0] - pu[0], pd[1] - pu[1], pd[2] - pu[2]};
+                double c[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+                const double len = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+                if (!(len > 0.0)) continue;
+                double s = 1.0 / len;
+                if (c[0] * pc[0] + c[1] * pc[1] + c[2] * pc[2] > 0.0) s = -s;
+                n[0] = c[0] * s;
+                n[1] = c[1] * s;
+                n[2] = c[2] * s;
+            }
+    }
+    free(P);
+}

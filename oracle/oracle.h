@@ -70,5 +70,7 @@ void or_softargmin_bwd(const double* L, const double* R, int W, int H,
                        const double* grad_dsoft, double* gL, double* gR);
 double or_l1_loss(const double* dsoft, const uint8_t* has_valid,
                   const double* gt, size_t n, double* grad);
+void or_depth_points(const double* d, int W, int H, double f, double cx, double cy,
+                     double B, double doffs, double* xyz, double* nrm);
 
 #endif
