@@ -308,6 +308,26 @@ stereo_status stereo_softargmin_bwd(stereo_handle* h, const float* left, const f
 stereo_status stereo_l1_loss(stereo_handle* h, const float* d_soft, const float* gt, int64_t n,
                              float* loss, float* grad, void* stream);
 
+/* Calibration of a rectified pair: focal length f (pixels), principal point
+ * (cx, cy) of the left camera (pixels), baseline (any length unit; points
+ * come out in it), doffs = right principal point x minus left principal
+ * point x (pixels). */
+typedef struct {
+    float f, cx, cy, baseline, doffs;
+} stereo_camera;
+
+/* Sec. II, depth from disparity (the reprojection of a rectified pair): for
+ * every pixel (u, v) of the float disparity map `disp` (W*H, NaN = invalid,
+ * e.g. disp_final) the point in the left camera frame
+ *     Z = f baseline / (d + doffs), X = (u - cx) Z / f, Y = (v - cy) Z / f
+ * (NaN where d is NaN or d + doffs <= 0), and its normal: the cross product
+ * of the central differences (P(u+1,v) - P(u-1,v)) x (P(u,v+1) - P(u,v-1)),
+ * turned to face the camera and normalised (NaN on the image border, next
+ * to a NaN point, or where the product vanishes).  xyz and normals are
+ * float [H][W][3] device arrays; either may be NULL.  No handle needed. */
+stereo_status stereo_depth_points(const float* disp, int32_t width, int32_t height, const stereo_camera* cam,
+                                  float* xyz, float* normals, void* stream);
+
 /* ------------------------------------------------------------------------
  * Allocation-free variant (no counterpart in the paper).
  *

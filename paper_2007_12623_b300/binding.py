@@ -21,6 +21,7 @@ __all__ = [
     "stereo_get_stage_times", "stereo_launch_count", "STAGE_NAMES", "stereo_set_tuning",
     "stereo_match_wta_noalloc", "stereo_softargmin_fwd", "stereo_softargmin_bwd", "stereo_l1_loss",
     "SoftArgminZNCC", "soft_argmin", "stereo_set_batch_config", "stereo_autotune_batched",
+    "StereoCamera", "stereo_depth_points",
 ]
 
 STAGE_NAMES = ("input", "stats", "cost_wta", "finalize", "postprocess", "refine")
@@ -66,6 +67,11 @@ class StereoPair(C.Structure):
     ]
 
 
+class StereoCamera(C.Structure):
+    _fields_ = [("f", C.c_float), ("cx", C.c_float), ("cy", C.c_float), ("baseline", C.c_float),
+                ("doffs", C.c_float)]
+
+
 _lib = None
 
 
@@ -107,6 +113,7 @@ def lib():
             "stereo_softargmin_bwd": (C.c_int, [P, P, P, i32, i32, i32, i32, i32, i32, f32, P, P, P, P, P,
                                                 P]),
             "stereo_l1_loss": (C.c_int, [P, P, P, C.c_int64, P, P, P]),
+            "stereo_depth_points": (C.c_int, [P, i32, i32, P, P, P, P]),
             "stereo_set_batch_config": (C.c_int, [P, i32, i32]),
             "stereo_autotune_batched": (C.c_int, [P, P, i32, P, P, P, P]),
         }
@@ -422,6 +429,19 @@ def stereo_l1_loss(handle: Handle, d_soft, gt, loss, grad=None, stream=None):
     _check(lib().stereo_l1_loss(handle.ptr, _ptr(d_soft, torch.float32, "d_soft"), _ptr(gt, torch.float32, "gt"),
                                 d_soft.numel(), _ptr(loss, torch.float32, "loss"),
                                 _ptr(grad, torch.float32, "grad"), _stream(stream)), "stereo_l1_loss")
+
+
+def stereo_depth_points(disp, camera: StereoCamera, xyz=None, normals=None, stream=None):
+    """Sec. II depth from disparity: points and normals [H, W, 3] (float32,
+    NaN where undefined) of a float disparity map [H, W]."""
+    import torch
+    H, W = disp.shape
+    for name, t in (("xyz", xyz), ("normals", normals)):
+        if t is not None and tuple(t.shape) != (H, W, 3):
+            raise ValueError(f"{name}: expected shape {(H, W, 3)}")
+    _check(lib().stereo_depth_points(_ptr(disp, torch.float32, "disp"), W, H, C.byref(camera),
+                                     _ptr(xyz, torch.float32, "xyz"), _ptr(normals, torch.float32, "normals"),
+                                     _stream(stream)), "stereo_depth_points")
 
 
 def _autograd_function():

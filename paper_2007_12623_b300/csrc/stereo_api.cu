@@ -21,6 +21,7 @@
 #include "refine_tiled.cuh"
 #include "soft.cuh"
 #include "batch.cuh"
+#include "depth.cuh"
 
 namespace {
 
@@ -1215,6 +1216,17 @@ stereo_status stereo_l1_loss(stereo_handle* h, const float* d_soft, const float*
         k_l1_grad<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_soft, gt, n, count, grad);
         counted();
     }
+    return last_error();
+}
+
+stereo_status stereo_depth_points(const float* disp, int32_t W, int32_t H, const stereo_camera* cam, float* xyz,
+                                  float* normals, void* stream) {
+    if (!disp || !cam || W < 1 || H < 1 || (!xyz && !normals)) return STEREO_ERR_INVALID_ARG;
+    if (!(cam->f > 0.f) || !(cam->baseline > 0.f)) return STEREO_ERR_INVALID_ARG;
+    const DepthCam c{cam->f, cam->cx, cam->cy, cam->f * cam->baseline, cam->doffs};
+    k_depth_points<<<dim3((W + DEPTH_TX - 1) / DEPTH_TX, (H + DEPTH_TY - 1) / DEPTH_TY), dim3(DEPTH_TX, DEPTH_TY), 0,
+                     S(stream)>>>(disp, W, H, c, xyz, normals);
+    counted();
     return last_error();
 }
 

@@ -54,4 +54,9 @@ def test_host_side_argument_checks(L):
     assert L.stereo_stage_fill_disc(None, C.c_void_p(16), 8, 8, 20, -1, C.c_void_p(32), None) == 1
     assert L.stereo_match(None, None, None) == 1
     assert L.stereo_gray(None, 4, 4, 12, None, None) == 1
+    cam = st.StereoCamera(500.0, 10.0, 10.0, 5.0, 0.0)
+    assert L.stereo_depth_points(None, 8, 8, C.byref(cam), C.c_void_p(16), None, None) == 1
+    assert L.stereo_depth_points(C.c_void_p(16), 8, 8, C.byref(cam), None, None, None) == 1   # no output
+    bad = st.StereoCamera(0.0, 10.0, 10.0, 5.0, 0.0)
+    assert L.stereo_depth_points(C.c_void_p(16), 8, 8, C.byref(bad), C.c_void_p(16), None, None) == 1
     assert L.stereo_destroy(None) == 0
