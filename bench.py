@@ -24,6 +24,8 @@ Other workloads (``--workload``):
                               11x11, tau = 0.1; a step is forward + L1 loss +
                               hand-written backward to both images through
                               torch.autograd.
+  paper960                    the paper's own setting: chessboard-sampled 11x11
+                              window, d in [-20, 80), smoothing radius 15.
   perlin320                   the small 320x240 gray Perlin pair (D = 32).
 
 Prints one JSON line (rank 0).  ``value`` is pixel-disparity evaluations per
@@ -68,6 +70,10 @@ WORKLOADS = {
     # soft-argmin training step on 8 pairs
     "soft8": dict(kind="soft", B=8, W=960, H=540, D=128, r=5, tau=0.1, seed=synth.seed_for(4),
                   disp=(10.0, 110.0)),
+    # the paper's own configuration: chessboard-sampled 11x11 window, candidates
+    # d in [-20, 80), smoothing radius 15, 960x540 tissue pair (field -10..70)
+    "paper960": dict(kind="single", W=960, H=540, D=100, d_min=-20, r=5, cost="f32", smooth_radius=15,
+                     sampling=1, seed=synth.seed_for(5), disp=(-10.0, 70.0)),
     # 320x240 gray Perlin pair, D = 0..31, 5x5 smoothing
     "perlin320": dict(kind="single", W=320, H=240, D=32, r=5, cost="f32", smooth_radius=2,
                       seed=synth.seed_for(0), disp=None),
@@ -315,6 +321,7 @@ def run_single(args, wl, rank, world, dev):
     tL = torch.from_numpy(Lrgb).to(dev)
     tR = torch.from_numpy(Rrgb).to(dev)
     sp = st.stereo_default_params(max_width=W, max_height=H, num_disp=D, win_radius=wl["r"],
+                                  d_min=wl.get("d_min", 0), sampling=wl.get("sampling", 0),
                                   cost_dtype=COST_CODE[wl["cost"]], smooth_radius=wl["smooth_radius"])
     h = st.stereo_create(sp)
     outs = dict(disp_wta=torch.empty((H, W), dtype=torch.int16, device=dev),
@@ -410,7 +417,8 @@ def run_single(args, wl, rank, world, dev):
     roof = cost_kernel_roofline([(W, H, D, wl["r"], wl["cost"])], stage_ms["cost_wta"], peaks, sm_count,
                                 "k_cost_wta", KERNEL_TRAFFIC.get(args.workload))
     line = _base_line(args, world, value, t_max, "f32", {
-        "workload": args.workload, "width": W, "height": H, "num_disp": D, "window": 2 * wl["r"] + 1,
+        "workload": args.workload, "width": W, "height": H, "num_disp": D, "d_min": wl.get("d_min", 0),
+        "window": 2 * wl["r"] + 1, "sampling": "chessboard" if wl.get("sampling", 0) else "full",
         "cost_storage": wl["cost"], "smooth_radius": wl["smooth_radius"], "refine_iters": 5,
         "pairs_per_gpu": 1, "parallelism": f"replicas x{world} (independent pairs)",
         "l2": "flushed between timed steps (256 MB write, untimed)",
@@ -650,6 +658,12 @@ def _oracle_problem(wl):
     return Lrgb, Rrgb, wl["W"], wl["D"], wl["r"], wl.get("smooth_radius", 15)
 
 
+def _oracle_params(wl, D, r, sr):
+    import oracle
+    return oracle.Params(d_min=wl.get("d_min", 0), num_disp=D, win_radius=r, smooth_radius=sr,
+                         sampling=wl.get("sampling", 0))
+
+
 def oracle_sample(wl, rows: int, problem=None):
     """Times the FP64 oracle on a bounded strip of the workload: `rows` output
     rows (plus window margins) across the full width.  Single-pair and batched
@@ -671,7 +685,7 @@ def oracle_sample(wl, rows: int, problem=None):
     Lg, Rg = oracle.gray(Lrgb), oracle.gray(Rrgb)
     Ls = np.ascontiguousarray(Lg[y0:y0 + rows + 2 * r])
     Rs = np.ascontiguousarray(Rg[y0:y0 + rows + 2 * r])
-    p = oracle.Params(d_min=0, num_disp=D, win_radius=r, smooth_radius=sr)
+    p = _oracle_params(wl, D, r, sr)
     t0 = time.perf_counter()
     oracle.pipeline(Ls, Rs, p)
     dt = time.perf_counter() - t0

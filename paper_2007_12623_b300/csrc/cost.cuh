@@ -91,8 +91,13 @@ __device__ __forceinline__ void load_slot(const float4* U, int i, float& h, floa
     cf = ok ? 1.0f : __int_as_float(0x7fc00000);
 }
 
-template <int R, int K, int CDT, bool PARTIAL>
+// CB (CHESSBOARD sampling): the window keeps the offsets with dx + dy even,
+// i.e. the pixels of the centre's colour on the chessboard of (x + y) & 1.
+// The vertical sums are kept per colour (V: colour 0, V2: colour 1) and so
+// are the horizontal ones; an output pixel takes the pair of its own colour.
+template <int R, int K, int CDT, bool PARTIAL, bool CB = false>
 __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0, int y0, int chunk) {
+    static_assert(!CB || K == 2, "the CHESSBOARD form keeps two colours of sums: K = 2");
     typedef CostGeom<R> G;
     typedef CostSmem<R, K> S;
     constexpr int TW = G::TW, NC = G::NC, NCH = G::NCH, RING = G::RING;
@@ -135,7 +140,7 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
     cp_async_wait_all();
     __syncwarp();
 
-    const float Nf = (float)((2 * R + 1) * (2 * R + 1));
+    const float Nf = (float)(CB ? ((2 * R + 1) * (2 * R + 1) + 1) / 2 : (2 * R + 1) * (2 * R + 1));
     const int idx0 = dc0 - a.d_min + K * lane;         // candidate index of k = 0
     uint32_t idxc[K], mulk[K];
 #pragma unroll
@@ -148,14 +153,55 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
     const int lbase = K * (31 - lane);
 
     float V[NC][K];
+    float V2[CB ? NC : 1][K];
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int k = 0; k < K; ++k) V[c][k] = 0.f;
+        for (int k = 0; k < K; ++k) {
+            V[c][k] = 0.f;
+            if (CB) V2[c][k] = 0.f;
+        }
 
     // adds (SUB: subtracts) L(c, gy) * R(c - d, gy) to every vertical sum
+    auto accumulate_cb = [&](int gy, auto sub_tag, auto base_tag) {
+        // column c of the unit has colour (c + BASE) & 1 on row gy
+        constexpr bool SUB = decltype(sub_tag)::value;
+        constexpr int BASE = decltype(base_tag)::value;
+        const float* row = sImg + ((gy - (y0 - R)) % RING) * (LW + RWc);
+        const float* lr = row;
+        const float* rr = row + LW + lbase;
+#pragma unroll
+        for (int cc = 0; cc < NCH; ++cc) {
+            const float4 l4 = *reinterpret_cast<const float4*>(lr + 4 * cc);
+            const float lv[4] = {SUB ? -l4.x : l4.x, SUB ? -l4.y : l4.y, SUB ? -l4.z : l4.z,
+                                 SUB ? -l4.w : l4.w};
+            float rv[8];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const float2 p = *reinterpret_cast<const float2*>(rr + 4 * cc + 2 * m);
+                rv[2 * m] = p.x; rv[2 * m + 1] = p.y;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (4 * cc + j >= NC) break;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    if (((4 * cc + j + BASE) & 1) == 0)
+                        V[4 * cc + j][k] = fmaf(lv[j], rv[j - k + 3], V[4 * cc + j][k]);
+                    else
+                        V2[(4 * cc + j) % (CB ? NC : 1)][k] =
+                            fmaf(lv[j], rv[j - k + 3], V2[(4 * cc + j) % (CB ? NC : 1)][k]);
+                }
+            }
+        }
+    };
     auto accumulate = [&](int gy, auto sub_tag) {
         constexpr bool SUB = decltype(sub_tag)::value;
+        if (CB) {
+            if (((x0 - R + gy) & 1) == 0) accumulate_cb(gy, sub_tag, std::integral_constant<int, 0>());
+            else accumulate_cb(gy, sub_tag, std::integral_constant<int, 1>());
+            return;
+        }
         const float* row = sImg + ((gy - (y0 - R)) % RING) * (LW + RWc);
         const float* lr = row;
         const float* rr = row + LW + lbase;
@@ -219,21 +265,29 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] = 0u;
         uint32_t myLeft = 0u;
-        float Hs[K];
+        float Hs[K], Hs2[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            float t = 0.f;
+            float t = 0.f, t2 = 0.f;
 #pragma unroll
-            for (int c = 0; c <= 2 * R; ++c) t += V[c][k];
+            for (int c = 0; c <= 2 * R; ++c) {
+                t += V[c][k];
+                if (CB) t2 += V2[c % (CB ? NC : 1)][k];
+            }
             Hs[k] = t;
+            Hs2[k] = t2;
         }
+        const int qbase = (x0 + y) & 1;              // colour of output column j is (j + qbase) & 1
         char* crow = reinterpret_cast<char*>(a.cost) + (((size_t)y * W + x0) * cstride + idx0) * ESZ;
         const bool do_store = CDT != CDT_NONE && idx0 < cstride;
 #pragma unroll
         for (int j = 0; j < TW; ++j) {
             if (j > 0) {
 #pragma unroll
-                for (int k = 0; k < K; ++k) Hs[k] += V[j + 2 * R][k] - V[j - 1][k];
+                for (int k = 0; k < K; ++k) {
+                    Hs[k] += V[j + 2 * R][k] - V[j - 1][k];
+                    if (CB) Hs2[k] += V2[(j + 2 * R) % (CB ? NC : 1)][k] - V2[(j - 1) % (CB ? NC : 1)][k];
+                }
             }
             if (PARTIAL && j >= nsteps) continue;
             load_slot(U, j + 32 * K - 1 - K * lane, uh[j % K], ul[j % K], ui[j % K], ko[j % K], cf[j % K]);
@@ -244,7 +298,8 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
             for (int k = 0; k < K; ++k) {
                 const int s = (j - k + 4 * K) % K;
                 const float t1 = sl.x * uh[s];                             // exact
-                const float num = fmaf(-sl.x, ul[s], fmaf(Nf, Hs[k], -t1));
+                const float hsum = CB ? (((j + qbase) & 1) ? Hs2[k] : Hs[k]) : Hs[k];
+                const float num = fmaf(-sl.x, ul[s], fmaf(Nf, hsum, -t1));
                 const float av = num * sl.y;
                 const float t = fmaf(av, ui[s], ko[s]);
                 const uint32_t key = __float_as_uint(t) * mulk[k] + idxc[k];
@@ -316,7 +371,7 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
 // otherwise it runs as a partial unit.  The last band is likewise moved up.
 // Overlapping columns/rows are computed twice with identical results, which
 // the max-combining key maps and the plain cost stores absorb.
-template <int R, int K, int CDT, int MINB>
+template <int R, int K, int CDT, int MINB, bool CB = false>
 __global__ void __launch_bounds__(32, MINB) k_cost_wta(CostArgs a) {
     extern __shared__ __align__(16) float smem[];
     typedef CostGeom<R> G;
@@ -331,11 +386,14 @@ __global__ void __launch_bounds__(32, MINB) k_cost_wta(CostArgs a) {
         else partial = true;
     }
     if (inner_h >= a.rows) y0 = min(y0, a.H - R - a.rows);
-    if (partial) cost_unit<R, K, CDT, true>(a, smem, x0, y0, blockIdx.z);
-    else cost_unit<R, K, CDT, false>(a, smem, x0, y0, blockIdx.z);
+    if (partial) cost_unit<R, K, CDT, true, CB>(a, smem, x0, y0, blockIdx.z);
+    else cost_unit<R, K, CDT, false, CB>(a, smem, x0, y0, blockIdx.z);
 }
 
 // Host-side launch for one window radius, explicitly instantiated per radius
 // in cost_r<R>.cu so that the radii compile in parallel.
 template <int R>
 void launch_cost_radius(int K, int cdt, CostArgs a, int rows_override, cudaStream_t s);
+// CHESSBOARD sampling (K = 2), instantiated per radius in cost_cb_r<R>.cu.
+template <int R>
+void launch_cost_cb_radius(int cdt, CostArgs a, int rows_override, cudaStream_t s);

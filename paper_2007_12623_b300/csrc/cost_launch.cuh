@@ -22,7 +22,7 @@ inline int cost_choose_rows(int units_x, int nz, int rows_total, int cap) {
 
 template <int K> struct CostMinBlocks { static constexpr int value = K == 4 ? 8 : (K == 2 ? 12 : 16); };
 
-template <int R, int K, int CDT>
+template <int R, int K, int CDT, bool CB = false>
 void launch_cost_rkc(CostArgs a, int rows_override, cudaStream_t s) {
     typedef CostGeom<R> G;
     typedef CostSmem<R, K> Sm;
@@ -35,12 +35,12 @@ void launch_cost_rkc(CostArgs a, int rows_override, cudaStream_t s) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cost_wta<R, K, CDT, MINB>, 32, Sm::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cost_wta<R, K, CDT, MINB, CB>, 32, Sm::BYTES);
         cap = std::max(1, sms * std::max(1, per_sm));
     }
     a.rows = rows_override > 0 ? rows_override : cost_choose_rows(nx, nz, a.H - 2 * R, cap);
     const int ny = (a.H - 2 * R + a.rows - 1) / a.rows;
-    k_cost_wta<R, K, CDT, MINB><<<dim3(nx, ny, nz), 32, Sm::BYTES, s>>>(a);
+    k_cost_wta<R, K, CDT, MINB, CB><<<dim3(nx, ny, nz), 32, Sm::BYTES, s>>>(a);
 }
 
 template <int R, int K>
@@ -58,4 +58,14 @@ void launch_cost_radius(int K, int cdt, CostArgs a, int rows_override, cudaStrea
     if (K == 4) launch_cost_rk<R, 4>(cdt, a, rows_override, s);
     else if (K == 2) launch_cost_rk<R, 2>(cdt, a, rows_override, s);
     else launch_cost_rk<R, 1>(cdt, a, rows_override, s);
+}
+
+template <int R>
+void launch_cost_cb_radius(int cdt, CostArgs a, int rows_override, cudaStream_t s) {
+    switch (cdt) {
+        case CDT_F32: launch_cost_rkc<R, 2, CDT_F32, true>(a, rows_override, s); break;
+        case CDT_F16: launch_cost_rkc<R, 2, CDT_F16, true>(a, rows_override, s); break;
+        case CDT_BF16: launch_cost_rkc<R, 2, CDT_BF16, true>(a, rows_override, s); break;
+        default: launch_cost_rkc<R, 2, CDT_NONE, true>(a, rows_override, s); break;
+    }
 }

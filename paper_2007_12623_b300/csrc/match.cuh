@@ -65,7 +65,8 @@ struct FinStats {
 // window sum into S_hi + S_lo the same way and the products and fused
 // multiply-adds are the same, so the three values equal the FP32 cost
 // volume's bit for bit.  NaN where the right pixel's window leaves the image.
-template <int R>
+// CB: CHESSBOARD sampling, only the offsets with dx + dy even contribute.
+template <int R, bool CB>
 __device__ __forceinline__ void costs3_fp32(const uint8_t* __restrict__ L, const uint8_t* __restrict__ Rm,
                                             int W, int x, int y, int u0, const FinStats& fs, float c[3]) {
     int slr0 = 0, slr1 = 0, slr2 = 0;            // right pixel u0 + 1, u0, u0 - 1
@@ -80,7 +81,8 @@ __device__ __forceinline__ void costs3_fp32(const uint8_t* __restrict__ L, const
         for (int j = 1; j <= 2 * R + 1; ++j) rv[j] = __ldg(rp + u0 - R - 1 + j);
         rv[2 * R + 2] = __ldg(rp + cr);
 #pragma unroll
-        for (int j = 0; j <= 2 * R; ++j) {
+        for (int j = 0; j <= 2 * R; ++j) {                 // dx = j - R
+            if (CB && ((j - R + dy) & 1)) continue;
             const int l = __ldg(lp + j);
             slr0 += l * rv[j + 2];
             slr1 += l * rv[j + 1];
@@ -88,7 +90,7 @@ __device__ __forceinline__ void costs3_fp32(const uint8_t* __restrict__ L, const
         }
     }
     const float2 sl = fs.lstats[(size_t)y * W + x];
-    const float Nf = (float)((2 * R + 1) * (2 * R + 1));
+    const float Nf = (float)(CB ? ((2 * R + 1) * (2 * R + 1) + 1) / 2 : (2 * R + 1) * (2 * R + 1));
     const float4* up = fs.ustats + (size_t)y * fs.ustride + fs.ucol0 + u0;
     const int sv[3] = {slr0, slr1, slr2};
 #pragma unroll
@@ -107,7 +109,7 @@ __device__ __forceinline__ void costs3_fp32(const uint8_t* __restrict__ L, const
 // (no volume, or one stored in FP16/BF16 whose rounding would move the
 // offset by up to ~0.03 px) recomputes them with costs3_fp32 (R > 0) or, with
 // no statistics, by the direct definition (R = 0).
-template <int R>
+template <int R, bool CB>
 __global__ void k_finalize(const uint32_t* __restrict__ keyL, const uint32_t* __restrict__ keyR,
                            int W, int H, int d_min, int D, int lr_thresh, const void* __restrict__ cost,
                            int cdt, const uint8_t* __restrict__ L, const uint8_t* __restrict__ Rm, int r,
@@ -144,7 +146,7 @@ __global__ void k_finalize(const uint32_t* __restrict__ keyL, const uint32_t* __
                     c[1] = cost_load(cost, cdt, b);
                     c[2] = cost_load(cost, cdt, b + 1);
                 } else if (R > 0) {
-                    costs3_fp32<R>(L, Rm, W, x, y, x - dl, fs, c);
+                    costs3_fp32<R, CB>(L, Rm, W, x, y, x - dl, fs, c);
                 } else {
                     c[0] = 1.f - zncc_direct(L, Rm, W, H, r, sampling, x, y, dl - 1);
                     c[1] = 1.f - zncc_direct(L, Rm, W, H, r, sampling, x, y, dl);
@@ -162,20 +164,30 @@ __global__ void k_finalize(const uint32_t* __restrict__ keyL, const uint32_t* __
     }
 }
 
-// Launches k_finalize for window radius r (statistics from the preparation
-// kernel with FULL sampling; the direct definition otherwise).
+// Launches k_finalize for window radius r (FP32 recompute from the
+// preparation kernel's statistics of either sampling; the direct definition
+// when there are none).
 static void launch_finalize(const uint32_t* keyL, const uint32_t* keyR, int W, int H, int d_min, int D,
                             int lr_thresh, const void* cost, int cdt, const uint8_t* L, const uint8_t* Rm,
                             int r, int sampling, const FinStats& fs, int16_t* disp_left, int16_t* disp_right,
                             float* disp_sub, int16_t* disp_lr, cudaStream_t s) {
     const dim3 g((W + 127) / 128, H);
-    const int rr = (fs.lstats && sampling == 0) ? r : 0;
-#define FIN_CASE(RV) \
-    case RV: k_finalize<RV><<<g, 128, 0, s>>>(keyL, keyR, W, H, d_min, D, lr_thresh, cost, cdt, L, Rm, r, \
-                                             sampling, fs, disp_left, disp_right, disp_sub, disp_lr); break;
-    switch (rr) {
-        FIN_CASE(1) FIN_CASE(2) FIN_CASE(3) FIN_CASE(4) FIN_CASE(5) FIN_CASE(6) FIN_CASE(7)
-        default: FIN_CASE(0)
+    const int rr = fs.lstats ? r : 0;
+#define FIN_CASE(RV, CBV) \
+    case RV: k_finalize<RV, CBV><<<g, 128, 0, s>>>(keyL, keyR, W, H, d_min, D, lr_thresh, cost, cdt, L, Rm, r, \
+                                                  sampling, fs, disp_left, disp_right, disp_sub, disp_lr); break;
+    if (sampling == 1) {
+        switch (rr) {
+            FIN_CASE(1, true) FIN_CASE(2, true) FIN_CASE(3, true) FIN_CASE(4, true) FIN_CASE(5, true)
+            FIN_CASE(6, true) FIN_CASE(7, true)
+            default: FIN_CASE(0, true)
+        }
+    } else {
+        switch (rr) {
+            FIN_CASE(1, false) FIN_CASE(2, false) FIN_CASE(3, false) FIN_CASE(4, false) FIN_CASE(5, false)
+            FIN_CASE(6, false) FIN_CASE(7, false)
+            default: FIN_CASE(0, false)
+        }
     }
 #undef FIN_CASE
 }

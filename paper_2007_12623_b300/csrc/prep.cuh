@@ -23,11 +23,18 @@ constexpr int PT = 32;
 constexpr int PMAXR = 7;
 constexpr int PSPAN = PT + 2 * PMAXR;
 
+//
+// CHESSBOARD sampling (CB): the window keeps the offsets (dx, dy) with dx + dy
+// even, centre included, N = ((2r+1)^2 + 1) / 2 samples; the row pass keeps
+// the sums over even and over odd dx apart and the column pass takes the
+// even-dx sum on rows with even dy and the odd-dx sum on the others.
+template <bool CB>
 __global__ void __launch_bounds__(256) k_prep(const uint8_t* __restrict__ img, int W, int H, int r,
                                               PrepOut out, uint32_t* __restrict__ key_clear) {
+    constexpr int NP = CB ? 2 : 1;
     __shared__ uint16_t t[PSPAN][PSPAN + 1];
-    __shared__ uint32_t rs[PSPAN][PT + 1];
-    __shared__ uint32_t rss[PSPAN][PT + 1];
+    __shared__ uint32_t rs[NP][PSPAN][PT + 1];
+    __shared__ uint32_t rss[NP][PSPAN][PT + 1];
     const int x0 = blockIdx.x * PT, y0 = blockIdx.y * PT;
     const int span = PT + 2 * r;
     const int tid = threadIdx.x;
@@ -39,17 +46,21 @@ __global__ void __launch_bounds__(256) k_prep(const uint8_t* __restrict__ img, i
     __syncthreads();
     for (int i = tid; i < span * PT; i += 256) {
         const int ly = i / PT, lx = i % PT;
-        uint32_t s = 0, ss = 0;
-        for (int k = 0; k <= 2 * r; ++k) {
+        uint32_t s0 = 0, ss0 = 0, s1 = 0, ss1 = 0;
+        for (int k = 0; k <= 2 * r; ++k) {              // dx = k - r
             const uint32_t v = t[ly][lx + k];
-            s += v;
-            ss += v * v;
+            if (CB && ((k - r) & 1)) { s1 += v; ss1 += v * v; }
+            else { s0 += v; ss0 += v * v; }
         }
-        rs[ly][lx] = s;
-        rss[ly][lx] = ss;
+        rs[0][ly][lx] = s0;
+        rss[0][ly][lx] = ss0;
+        if (CB) {
+            rs[NP - 1][ly][lx] = s1;
+            rss[NP - 1][ly][lx] = ss1;
+        }
     }
     __syncthreads();
-    const uint32_t N = (uint32_t)((2 * r + 1) * (2 * r + 1));
+    const uint32_t N = (uint32_t)(CB ? ((2 * r + 1) * (2 * r + 1) + 1) / 2 : (2 * r + 1) * (2 * r + 1));
     for (int i = tid; i < PT * PT; i += 256) {
         const int ly = i / PT, lx = i % PT;
         const int gx = x0 + lx, gy = y0 + ly;
@@ -61,7 +72,11 @@ __global__ void __launch_bounds__(256) k_prep(const uint8_t* __restrict__ img, i
         const bool interior = gx >= r && gx < W - r && gy >= r && gy < H - r;
         if (interior) {
             uint32_t ss = 0;
-            for (int k = 0; k <= 2 * r; ++k) { s += rs[ly + k][lx]; ss += rss[ly + k][lx]; }
+            for (int k = 0; k <= 2 * r; ++k) {          // dy = k - r: same parity of dx
+                const int q = CB ? ((k - r) & 1) : 0;
+                s += rs[q][ly + k][lx];
+                ss += rss[q][ly + k][lx];
+            }
             B = N * ss - s * s;
         }
         float is = 0.f;

@@ -238,7 +238,22 @@ stereo_status last_error() {
 int pick_k(int D) { return D <= 32 ? 1 : (D <= 64 ? 2 : 4); }
 int pos_mod4(int v) { return ((v % 4) + 4) % 4; }
 
-void launch_cost(int r, int K, int cdt, const CostArgs& a, int rows, cudaStream_t s) {
+void launch_cost(int r, int K, int cdt, const CostArgs& a, int rows, cudaStream_t s,
+                 int sampling = STEREO_SAMPLE_FULL) {
+    if (sampling == STEREO_SAMPLE_CHESSBOARD) {        // K = 2
+        switch (r) {
+            case 1: launch_cost_cb_radius<1>(cdt, a, rows, s); break;
+            case 2: launch_cost_cb_radius<2>(cdt, a, rows, s); break;
+            case 3: launch_cost_cb_radius<3>(cdt, a, rows, s); break;
+            case 4: launch_cost_cb_radius<4>(cdt, a, rows, s); break;
+            case 5: launch_cost_cb_radius<5>(cdt, a, rows, s); break;
+            case 6: launch_cost_cb_radius<6>(cdt, a, rows, s); break;
+            case 7: launch_cost_cb_radius<7>(cdt, a, rows, s); break;
+            default: return;
+        }
+        counted();
+        return;
+    }
     switch (r) {
         case 1: launch_cost_radius<1>(K, cdt, a, rows, s); break;
         case 2: launch_cost_radius<2>(K, cdt, a, rows, s); break;
@@ -283,14 +298,18 @@ void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, in
                int sampling, int cdt, int lr_thresh, const PairWs& w, void* cost,
                int16_t* disp_left, int16_t* disp_right, float* disp_sub, int16_t* disp_lr,
                cudaStream_t s, cudaEvent_t* ev = nullptr) {
-    const int K = pick_k(D);
+    const int K = sampling == STEREO_SAMPLE_CHESSBOARD ? 2 : pick_k(D);
     PrepOut pl, pr;
     prep_layouts(W, d_min, D, K, w, pl, pr);
     dim3 sg((W + PT - 1) / PT, (H + PT - 1) / PT);
-    k_prep<<<sg, 256, 0, s>>>(gl, W, H, r, pl, w.keys);
-    counted();
-    k_prep<<<sg, 256, 0, s>>>(gr, W, H, r, pr, nullptr);
-    counted();
+    if (sampling == STEREO_SAMPLE_CHESSBOARD) {
+        k_prep<true><<<sg, 256, 0, s>>>(gl, W, H, r, pl, w.keys);
+        k_prep<true><<<sg, 256, 0, s>>>(gr, W, H, r, pr, nullptr);
+    } else {
+        k_prep<false><<<sg, 256, 0, s>>>(gl, W, H, r, pl, w.keys);
+        k_prep<false><<<sg, 256, 0, s>>>(gr, W, H, r, pr, nullptr);
+    }
+    counted(2);
     if (cost) {
         const long nb = (W <= 2 * r || H <= 2 * r) ? (long)W * H : 2L * r * W + 2L * r * (H - 2 * r);
         const int blocks = (int)std::min<long>(4096, (nb * cost_stride(D) + 255) / 256);
@@ -300,7 +319,7 @@ void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, in
     if (ev) cudaEventRecord(ev[2], s);
     CostArgs a{pl.img, pl.stride, pl.col0, pr.img, pr.stride, pr.col0, w.lstats, w.ustats,
                pr.ustride, pr.ucol0, w.keys, w.keys + (size_t)W * H, cost, cdt, W, H, d_min, D, 0};
-    launch_cost(r, K, cdt, a, g_cost_rows, s);
+    launch_cost(r, K, cdt, a, g_cost_rows, s, sampling);
     if (ev) cudaEventRecord(ev[3], s);
     launch_finalize(w.keys, w.keys + (size_t)W * H, W, H, d_min, D, lr_thresh, cost, cdt, gl, gr, r, sampling,
                     FinStats{w.lstats, w.ustats, pr.ustride, pr.ucol0}, disp_left, disp_right, disp_sub, disp_lr,
@@ -454,7 +473,7 @@ stereo_status check_match_args(const stereo_handle* h, int W, int H, int d_min, 
         return STEREO_ERR_INVALID_ARG;
     if (d_min < -CMAX_DMIN || d_min > CMAX_DMIN) return STEREO_ERR_INVALID_ARG;
     if (cdt < 0 || cdt > 3) return STEREO_ERR_INVALID_ARG;
-    if (sampling != STEREO_SAMPLE_FULL) return STEREO_ERR_UNSUPPORTED;
+    if (sampling != STEREO_SAMPLE_FULL && sampling != STEREO_SAMPLE_CHESSBOARD) return STEREO_ERR_INVALID_ARG;
     if (W > h->p.max_width || H > h->p.max_height || D > h->p.num_disp) return STEREO_ERR_TOO_LARGE;
     return STEREO_OK;
 }
@@ -997,8 +1016,8 @@ static void enqueue_batched(stereo_handle* h, const stereo_pair* pairs, int n, c
         PrepOut pl, prr;
         prep_layouts(q.W, q.d_min, q.D, K, w, pl, prr);
         dim3 sg((q.W + PT - 1) / PT, (q.H + PT - 1) / PT);
-        k_prep<<<sg, 256, 0, st>>>(q.gl, q.W, q.H, q.r, pl, w.keys);
-        k_prep<<<sg, 256, 0, st>>>(q.gr, q.W, q.H, q.r, prr, nullptr);
+        k_prep<false><<<sg, 256, 0, st>>>(q.gl, q.W, q.H, q.r, pl, w.keys);
+        k_prep<false><<<sg, 256, 0, st>>>(q.gr, q.W, q.H, q.r, prr, nullptr);
         counted(2);
         if (cdt != CDT_NONE) {
             const int W = q.W, H = q.H, r = q.r;
@@ -1233,6 +1252,7 @@ stereo_status stereo_depth_points(const float* disp, int32_t W, int32_t H, const
 stereo_status stereo_match_batched(stereo_handle* h, const stereo_pair* pairs, int32_t n,
                                    int32_t use_graph, void* stream) {
     if (!h || !pairs || n < 1) return STEREO_ERR_INVALID_ARG;
+    if (h->p.sampling != STEREO_SAMPLE_FULL && n > 1) return STEREO_ERR_UNSUPPORTED;
     if (n > h->max_batch) return STEREO_ERR_TOO_LARGE;
     for (int i = 0; i < n; ++i) {
         int d_min, D, r;
@@ -1277,6 +1297,7 @@ stereo_status stereo_set_batch_config(stereo_handle* h, int32_t rows, int32_t K)
 stereo_status stereo_autotune_batched(stereo_handle* h, const stereo_pair* pairs, int32_t n, void* stream,
                                       int32_t* best_rows, int32_t* best_K, float* best_ms) {
     if (!h || !pairs || n < 2 || n > h->max_batch || !h->units) return STEREO_ERR_INVALID_ARG;
+    if (h->p.sampling != STEREO_SAMPLE_FULL) return STEREO_ERR_UNSUPPORTED;
     for (int i = 0; i < n; ++i) {
         int d_min, D, r;
         stereo_status st = resolve_pair(h, &pairs[i], d_min, D, r);

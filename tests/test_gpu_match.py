@@ -25,10 +25,10 @@ def dev():
     return torch.device("cuda:0")
 
 
-def run_stage_match(dev, L, R, d_min, D, r, cdt=st.COST_F32):
+def run_stage_match(dev, L, R, d_min, D, r, cdt=st.COST_F32, sampling=st.SAMPLE_FULL):
     H, W = L.shape
     p = st.stereo_default_params(max_width=W, max_height=H, num_disp=D, d_min=d_min, win_radius=r,
-                                 cost_dtype=cdt)
+                                 cost_dtype=cdt, sampling=sampling)
     h = st.stereo_create(p)
     tL = torch.from_numpy(np.ascontiguousarray(L)).to(dev)
     tR = torch.from_numpy(np.ascontiguousarray(R)).to(dev)
@@ -40,7 +40,7 @@ def run_stage_match(dev, L, R, d_min, D, r, cdt=st.COST_F32):
         tdt = {st.COST_F32: torch.float32, st.COST_F16: torch.float16, st.COST_BF16: torch.bfloat16}[cdt]
         # zero-filled: the library itself must write NaN for invalid candidates
         cost = torch.zeros((H, W, st.cost_stride(D)), dtype=tdt, device=dev)
-    st.stereo_stage_match(h, tL, tR, d_min, D, r, st.SAMPLE_FULL, cdt, dl, dr, sub, cost)
+    st.stereo_stage_match(h, tL, tR, d_min, D, r, sampling, cdt, dl, dr, sub, cost)
     torch.cuda.synchronize()
     assert st.stereo_get_device_error(h) == 0
     h.close()
@@ -143,3 +143,39 @@ def test_deterministic(dev):
         assert np.array_equal(a[k], b[k])
     assert np.array_equal(a["sub"], b["sub"], equal_nan=True)
     assert np.array_equal(a["cost"], b["cost"], equal_nan=True)
+
+
+@pytest.mark.parametrize("shape,d_min,D,r,cdt", [
+    ((23, 37), 0, 5, 1, st.COST_F32),
+    ((40, 61), -3, 33, 3, st.COST_F32),
+    ((30, 150), 0, 100, 5, st.COST_F16),
+    ((26, 230), -20, 100, 5, st.COST_NONE),
+    ((33, 80), 0, 16, 7, st.COST_BF16),
+])
+def test_chessboard_sampling(dev, shape, d_min, D, r, cdt):
+    """CHESSBOARD sampling (Sec. II-A: only window offsets with dx + dy even,
+    centre included): winners, sub-pixel and the stored volume against the
+    oracle's chessboard ZNCC."""
+    rng = np.random.default_rng(hash((shape, d_min, D, r, 7)) & 0xFFFF)
+    H, W = shape
+    L = rng.integers(0, 256, (H, W), dtype=np.uint8)
+    R = rng.integers(0, 256, (H, W), dtype=np.uint8)
+    g = run_stage_match(dev, L, R, d_min, D, r, cdt, sampling=st.SAMPLE_CHESSBOARD)
+    m = oracle.match(L, R, d_min, D, r, sampling=oracle.SAMPLE_CHESSBOARD)
+    check_against_oracle(g, m, D)
+    if cdt != st.COST_NONE:
+        cv = oracle.cost_volume(L, R, d_min, D, r, sampling=oracle.SAMPLE_CHESSBOARD)
+        assert np.array_equal(np.isnan(g["cost"]), np.isnan(cv))
+        ok = ~np.isnan(cv)
+        eps = {st.COST_F32: 0.0, st.COST_F16: 2 ** -11, st.COST_BF16: 2 ** -8}[cdt]
+        assert np.all(np.abs(g["cost"][ok] - cv[ok]) <= eps * np.abs(cv[ok]) + 1e-6)
+
+
+def test_chessboard_differs_from_full(dev):
+    """The two samplings are different windows (guards against the option
+    being ignored)."""
+    L, R, gt = synth.perlin_pair(synth.seed_for(0))
+    L, R = L[:60], R[:60]
+    a = run_stage_match(dev, L, R, 0, 32, 5, sampling=st.SAMPLE_CHESSBOARD)
+    b = run_stage_match(dev, L, R, 0, 32, 5)
+    assert np.nanmax(np.abs(a["cost"] - b["cost"])) > 1e-3

@@ -30,7 +30,7 @@ def T(a, dev):
 def run_match(dev, Limg, Rimg, p: oracle.Params, cdt=st.COST_F32):
     H, W = Limg.shape[:2]
     sp = st.stereo_default_params(max_width=W, max_height=H, d_min=p.d_min, num_disp=p.num_disp,
-                                  win_radius=p.win_radius, cost_dtype=cdt,
+                                  win_radius=p.win_radius, cost_dtype=cdt, sampling=p.sampling,
                                   smooth_radius=p.smooth_radius, smooth_iters=p.smooth_iters)
     h = st.stereo_create(sp)
     out = dict(disp_wta=torch.empty((H, W), dtype=torch.int16, device=dev),
@@ -69,6 +69,31 @@ def test_perlin_end_to_end(dev):
     # accuracy against the generator's field (context): median error < 0.5 px
     gv = g["valid"].astype(bool)
     assert np.median(np.abs(g["disp_final"][gv] - gt[gv])) < 0.5
+
+
+def test_paper_configuration_chessboard(dev):
+    """The paper's own setting (Sec. II-A, Sec. III): chessboard-sampled
+    11x11 window, candidates d in [-20, 80), smoothing radius 15, on a
+    320x160 tissue crop shifted so that some disparities are negative."""
+    Lrgb, Rrgb, gt = synth.tissue_pair(synth.seed_for(1, 5), 320, 160, 4.0, 60.0)
+    Lg, Rg = oracle.gray(Lrgb), oracle.gray(Rrgb)
+    Lg = np.ascontiguousarray(Lg[:, 10:])          # shift: disparities move by -10
+    Rg = np.ascontiguousarray(Rg[:, :-10])
+    p = oracle.Params(d_min=-20, num_disp=100, win_radius=5, sampling=oracle.SAMPLE_CHESSBOARD,
+                      smooth_radius=15)
+    ref = oracle.pipeline(Lg, Rg, p)
+    m = oracle.match(Lg, Rg, -20, 100, 5, sampling=oracle.SAMPLE_CHESSBOARD)
+    g = run_match(dev, Lg, Rg, p)
+    near = m["gapL"] < NEAR_TIE
+    bad = int_map_mismatch(g["disp_wta"], ref["dL"], near)
+    assert len(bad) == 0, describe(bad, g["disp_wta"], ref["dL"])
+    same = (g["disp_wta"] == ref["dL"]) & (ref["dL"] != INV)
+    assert np.all(np.abs(g["disp_sub"][same] - ref["sub"][same]) <= SUB_TOL)
+    assert (ref["dL"][ref["dL"] != INV] < 0).any()
+    v = (ref["o_post"] != INV) & (g["valid"] != 0)
+    rel = np.abs(g["disp_final"][v] - ref["d_final"][v]) / np.maximum(np.abs(ref["d_final"][v]), 1)
+    print(f"paper configuration: {100 * np.mean(rel > REFINE_RTOL):.3f}% beyond 1e-4")
+    assert np.mean(rel > REFINE_RTOL) <= 0.005
 
 
 def test_tissue_full_size_sampled(dev):
