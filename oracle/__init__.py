@@ -66,6 +66,7 @@ def lib():
         P = C.c_void_p
         i, d = C.c_int, C.c_double
         sig = {
+            "or_mosaic_frame": (i, [P, P, P, P, P, i, P, P, i, i, C.c_float, C.c_float, C.c_float, P, P, C.c_float, C.c_float, C.c_float]),
             "or_depth_points": (None, [P, i, i, d, d, d, d, d, P, P]),
             "or_gray": (None, [P, i, i, P]),
             "or_candidate_valid": (i, [i, i, i, i, i, i]),
@@ -330,3 +331,32 @@ def depth_points(disp, f, cx, cy, B, doffs=0.0):
     lib().or_depth_points(_p(d), W, H, float(f), float(cx), float(cy), float(B), float(doffs),
                           _p(xyz), _p(nrm))
     return xyz, nrm
+
+
+class PointModel:
+    """The mosaicked surface model of the oracle: float64 arrays of a fixed
+    capacity and the number of points in use."""
+
+    def __init__(self, capacity: int):
+        self.pos = np.zeros((capacity, 3))
+        self.rgb = np.zeros((capacity, 3))
+        self.wpos = np.zeros(capacity)
+        self.wrgb = np.zeros(capacity)
+        self.count = 0
+        self.capacity = capacity
+
+
+def mosaic_frame(model: PointModel, xyz, img, f, cx, cy, R, t, tau, r0=0.5, gmin=0.1) -> int:
+    """Point-based TSDF mosaicking of one frame (Sec. II); updates `model` in
+    place and returns the number of appends that did not fit."""
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    img = np.ascontiguousarray(img, np.uint8)
+    H, W = xyz.shape[:2]
+    R = np.ascontiguousarray(R, np.float32).reshape(9)
+    t = np.ascontiguousarray(t, np.float32).reshape(3)
+    cnt = C.c_int(model.count)
+    dropped = lib().or_mosaic_frame(_p(model.pos), _p(model.rgb), _p(model.wpos), _p(model.wrgb),
+                                    C.byref(cnt), model.capacity, _p(xyz), _p(img), W, H, float(f),
+                                    float(cx), float(cy), _p(R), _p(t), float(tau), float(r0), float(gmin))
+    model.count = cnt.value
+    return dropped

@@ -720,3 +720,103 @@ void or_depth_points(const double* d, int W, int H, double f, double cx, double 
     }
     free(P);
 }
+
+/* ------------------------------------------------------------------------
+ * Point-based TSDF mosaicking of one key frame into the surface model
+ * (Sec. II, GPU-based TSDF mosaicking).  The model is a list of points with
+ * a world position, an RGB colour, a position weight and a colour weight.
+ *
+ *  1. Rasterise the model into the current image: X = R P + t (world ->
+ *     camera); a point with X.z > 0 lands on pixel u = floor(f X.x / X.z + cx
+ *     + 1/2), v = floor(f X.y / X.z + cy + 1/2); per pixel the nearest point
+ *     (smallest X.z, ties -> smallest index) is kept.  These decisions are
+ *     taken in single precision with a fixed operation order (the same
+ *     decisions as the GPU's).
+ *  2. Every pixel with a valid stereo point Q (camera frame) whose kept
+ *     model point lies within the truncation distance (|Q.z - X.z| <= tau)
+ *     merges into it: P <- (w P + Pw) / (w + 1), w <- w + 1 with Pw = R^T
+ *     (Q - t), and C <- (c C + g I) / (c + g), c <- c + g, where I is the
+ *     pixel's colour and g its colour weight: 1 inside the central disc
+ *     (normalised radius rr <= r0, rr = 1 at the corners), falling linearly
+ *     to gmin at the corners.
+ *  3. Every other pixel with a valid point is appended as a new point
+ *     (Pw, I, w = 1, c = g), in row-major pixel order, while capacity lasts.
+ * Returns the number of appends that did not fit (0 normally).
+ * pos/rgb: [capacity][3]; wpos/wrgb: [capacity]; *count in/out. */
+static float or_f32_dot3(const float* r, float a, float b, float c) {
+    float s = r[0] * a;
+    s = s + r[1] * b;
+    s = s + r[2] * c;
+    return s;
+}
+
+int or_mosaic_frame(double* pos, double* rgb, double* wpos, double* wrgb, int* count, int capacity,
+                    const float* xyz, const uint8_t* img, int W, int H, float f, float cx, float cy,
+                    const float* R, const float* t, float tau, float r0, float gmin) {
+    const int n = *count;
+    int* win = (int*)malloc(sizeof(int) * (size_t)W * H);
+    float* winz = (float*)malloc(sizeof(float) * (size_t)W * H);
+    for (size_t k = 0; k < (size_t)W * H; ++k) win[k] = -1;
+    for (int i = 0; i < n; ++i) {
+        const float P0 = (float)pos[3 * (size_t)i], P1 = (float)pos[3 * (size_t)i + 1],
+                    P2 = (float)pos[3 * (size_t)i + 2];
+        const float X0 = or_f32_dot3(R, P0, P1, P2) + t[0];
+        const float X1 = or_f32_dot3(R + 3, P0, P1, P2) + t[1];
+        const float X2 = or_f32_dot3(R + 6, P0, P1, P2) + t[2];
+        if (!(X2 > 0.0f)) continue;
+        float pu = f * X0;
+        pu = pu / X2;
+        pu = pu + cx;
+        float pv = f * X1;
+        pv = pv / X2;
+        pv = pv + cy;
+        const float fu = floorf(pu + 0.5f), fv = floorf(pv + 0.5f);
+        if (!(fu >= 0.0f && fu < (float)W && fv >= 0.0f && fv < (float)H)) continue;
+        const size_t k = (size_t)fv * W + (size_t)fu;
+        if (win[k] < 0 || X2 < winz[k]) {     /* equal depth: the smaller index stays */
+            win[k] = i;
+            winz[k] = X2;
+        }
+    }
+    const double cxc = (W - 1) / 2.0, cyc = (H - 1) / 2.0;
+    int appended = 0, dropped = 0;
+    for (int v = 0; v < H; ++v)
+        for (int u = 0; u < W; ++u) {
+            const size_t k = (size_t)v * W + u;
+            const float Qx = xyz[3 * k], Qy = xyz[3 * k + 1], Qz = xyz[3 * k + 2];
+            if (isnan(Qz) || !(Qz > 0.0f)) continue;
+            /* world point R^T (Q - t) */
+            const double q0 = (double)Qx - t[0], q1 = (double)Qy - t[1], q2 = (double)Qz - t[2];
+            double Pw[3];
+            for (int a = 0; a < 3; ++a) Pw[a] = R[a] * q0 + R[3 + a] * q1 + R[6 + a] * q2;
+            const double du = (u - cxc) / (W / 2.0), dv = (v - cyc) / (H / 2.0);
+            const double rr = sqrt(du * du + dv * dv) / sqrt(2.0);
+            double g = 1.0;
+            if (rr > r0) g = 1.0 - (1.0 - gmin) * (rr - r0) / (1.0 - r0);
+            if (g < gmin) g = gmin;
+            const int i = win[k];
+            if (i >= 0 && fabsf(Qz - winz[k]) <= tau) {
+                const double w = wpos[i], c = wrgb[i];
+                for (int a = 0; a < 3; ++a) {
+                    pos[3 * (size_t)i + a] = (w * pos[3 * (size_t)i + a] + Pw[a]) / (w + 1.0);
+                    rgb[3 * (size_t)i + a] = (c * rgb[3 * (size_t)i + a] + g * img[3 * k + a]) / (c + g);
+                }
+                wpos[i] = w + 1.0;
+                wrgb[i] = c + g;
+                continue;
+            }
+            if (n + appended >= capacity) { ++dropped; continue; }
+            const size_t j = (size_t)(n + appended);
+            for (int a = 0; a < 3; ++a) {
+                pos[3 * j + a] = Pw[a];
+                rgb[3 * j + a] = img[3 * k + a];
+            }
+            wpos[j] = 1.0;
+            wrgb[j] = g;
+            ++appended;
+        }
+    *count = n + appended;
+    free(win);
+    free(winz);
+    return dropped;
+}
