@@ -328,6 +328,41 @@ typedef struct {
 stereo_status stereo_depth_points(const float* disp, int32_t width, int32_t height, const stereo_camera* cam,
                                   float* xyz, float* normals, void* stream);
 
+/* Surface model of the point-based TSDF mosaicking (Sec. II, GPU-based TSDF
+ * mosaicking): caller-owned device arrays of `capacity` points -- world
+ * position (float [capacity][3]), RGB colour 0..255 (float [capacity][3]),
+ * position weight and colour weight (float [capacity]) -- and two device
+ * int32: count (points in use; read and updated) and dropped (written: new
+ * points of the last call that did not fit). */
+typedef struct {
+    float* pos;
+    float* rgb;
+    float* wpos;
+    float* wrgb;
+    int32_t* count;
+    int32_t* dropped;
+    int32_t capacity;
+} stereo_point_model;
+
+/* Mosaics one key frame into the model: xyz = the frame's points in its
+ * camera frame (float [H][W][3], NaN = no depth; e.g. stereo_depth_points of
+ * disp_final), rgb = its colour image (u8 [H][W][3]), cam = its intrinsics
+ * (f, cx, cy), R (9 floats, row-major) and t (3 floats) = the pose mapping
+ * world to camera coordinates (host arrays).  Model points are projected
+ * into the image (nearest point per pixel, in single precision: u =
+ * floor(f X/Z + cx + 1/2)); a pixel with a point whose camera depth is
+ * within `tau` of the projected model point's merges into it (position:
+ * running mean, weight + 1; colour: mean weighted by the pixel's colour
+ * weight, 1 inside the central disc of normalised radius r0 -- 1 at the
+ * corners -- falling linearly to gmin at the corners); every other pixel
+ * with a point is appended (row-major order) while capacity lasts.  Uses
+ * the handle's workspace (width/height must fit the handle); ordered with
+ * the handle's other calls. */
+stereo_status stereo_mosaic_frame(stereo_handle* h, const stereo_point_model* model, const float* xyz,
+                                  const uint8_t* rgb, int32_t width, int32_t height, const stereo_camera* cam,
+                                  const float* R, const float* t, float tau, float r0, float gmin,
+                                  void* stream);
+
 /* ------------------------------------------------------------------------
  * Allocation-free variant (no counterpart in the paper).
  *

@@ -21,7 +21,7 @@ __all__ = [
     "stereo_get_stage_times", "stereo_launch_count", "STAGE_NAMES", "stereo_set_tuning",
     "stereo_match_wta_noalloc", "stereo_softargmin_fwd", "stereo_softargmin_bwd", "stereo_l1_loss",
     "SoftArgminZNCC", "soft_argmin", "stereo_set_batch_config", "stereo_autotune_batched",
-    "StereoCamera", "stereo_depth_points",
+    "StereoCamera", "stereo_depth_points", "PointModel", "stereo_mosaic_frame",
 ]
 
 STAGE_NAMES = ("input", "stats", "cost_wta", "finalize", "postprocess", "refine")
@@ -72,6 +72,11 @@ class StereoCamera(C.Structure):
                 ("doffs", C.c_float)]
 
 
+class _PointModelC(C.Structure):
+    _fields_ = [("pos", C.c_void_p), ("rgb", C.c_void_p), ("wpos", C.c_void_p), ("wrgb", C.c_void_p),
+                ("count", C.c_void_p), ("dropped", C.c_void_p), ("capacity", C.c_int32)]
+
+
 _lib = None
 
 
@@ -114,6 +119,8 @@ def lib():
                                                 P]),
             "stereo_l1_loss": (C.c_int, [P, P, P, C.c_int64, P, P, P]),
             "stereo_depth_points": (C.c_int, [P, i32, i32, P, P, P, P]),
+            "stereo_mosaic_frame": (C.c_int, [P, P, P, P, i32, i32, P, P, P, C.c_float, C.c_float,
+                                              C.c_float, P]),
             "stereo_set_batch_config": (C.c_int, [P, i32, i32]),
             "stereo_autotune_batched": (C.c_int, [P, P, i32, P, P, P, P]),
         }
@@ -442,6 +449,43 @@ def stereo_depth_points(disp, camera: StereoCamera, xyz=None, normals=None, stre
     _check(lib().stereo_depth_points(_ptr(disp, torch.float32, "disp"), W, H, C.byref(camera),
                                      _ptr(xyz, torch.float32, "xyz"), _ptr(normals, torch.float32, "normals"),
                                      _stream(stream)), "stereo_depth_points")
+
+
+class PointModel:
+    """Device arrays of a mosaicked surface model (torch tensors): pos, rgb
+    [capacity, 3], wpos, wrgb [capacity] (float32), count, dropped (int32
+    scalars on the device)."""
+
+    def __init__(self, capacity: int, device):
+        import torch
+        self.capacity = capacity
+        self.pos = torch.zeros((capacity, 3), dtype=torch.float32, device=device)
+        self.rgb = torch.zeros((capacity, 3), dtype=torch.float32, device=device)
+        self.wpos = torch.zeros(capacity, dtype=torch.float32, device=device)
+        self.wrgb = torch.zeros(capacity, dtype=torch.float32, device=device)
+        self.count = torch.zeros(1, dtype=torch.int32, device=device)
+        self.dropped = torch.zeros(1, dtype=torch.int32, device=device)
+
+    def _c(self):
+        return _PointModelC(self.pos.data_ptr(), self.rgb.data_ptr(), self.wpos.data_ptr(),
+                            self.wrgb.data_ptr(), self.count.data_ptr(), self.dropped.data_ptr(),
+                            self.capacity)
+
+
+def stereo_mosaic_frame(handle: Handle, model: PointModel, xyz, rgb, camera: StereoCamera, R, t, tau,
+                        r0=0.5, gmin=0.1, stream=None):
+    """Point-based TSDF mosaicking of one key frame (Sec. II): xyz [H, W, 3]
+    float32 camera-frame points (NaN = no depth), rgb [H, W, 3] uint8, R (3x3)
+    and t (3) the world-to-camera pose."""
+    import torch
+    H, W = xyz.shape[:2]
+    import numpy as np
+    Rf = (C.c_float * 9)(*np.asarray(R, dtype=np.float32).reshape(9).tolist())
+    tf = (C.c_float * 3)(*np.asarray(t, dtype=np.float32).reshape(3).tolist())
+    mc = model._c()
+    _check(lib().stereo_mosaic_frame(handle.ptr, C.byref(mc), _ptr(xyz, torch.float32, "xyz"),
+                                     _ptr(rgb, torch.uint8, "rgb"), W, H, C.byref(camera), Rf, tf, float(tau),
+                                     float(r0), float(gmin), _stream(stream)), "stereo_mosaic_frame")
 
 
 def _autograd_function():

@@ -22,6 +22,7 @@
 #include "soft.cuh"
 #include "batch.cuh"
 #include "depth.cuh"
+#include "mosaic.cuh"
 
 namespace {
 
@@ -1246,6 +1247,42 @@ stereo_status stereo_depth_points(const float* disp, int32_t W, int32_t H, const
     k_depth_points<<<dim3((W + DEPTH_TX - 1) / DEPTH_TX, (H + DEPTH_TY - 1) / DEPTH_TY), dim3(DEPTH_TX, DEPTH_TY), 0,
                      S(stream)>>>(disp, W, H, c, xyz, normals);
     counted();
+    return last_error();
+}
+
+stereo_status stereo_mosaic_frame(stereo_handle* h, const stereo_point_model* pm, const float* xyz,
+                                  const uint8_t* rgb, int32_t W, int32_t H, const stereo_camera* cam,
+                                  const float* R, const float* t, float tau, float r0, float gmin,
+                                  void* stream) {
+    if (!h || !pm || !xyz || !rgb || !cam || !R || !t || W < 1 || H < 1) return STEREO_ERR_INVALID_ARG;
+    if (!pm->pos || !pm->rgb || !pm->wpos || !pm->wrgb || !pm->count || !pm->dropped || pm->capacity < 0)
+        return STEREO_ERR_INVALID_ARG;
+    if (!(cam->f > 0.f) || !(tau >= 0.f) || !(r0 >= 0.f && r0 < 1.f) || !(gmin > 0.f && gmin <= 1.f))
+        return STEREO_ERR_INVALID_ARG;
+    if (W > h->p.max_width || H > h->p.max_height) return STEREO_ERR_TOO_LARGE;
+    cudaStream_t s = S(stream);
+    PairWs w = carve(h->ws, (size_t)W * H, h->p.num_disp, h->p.cost_dtype, h->p.max_width, h->p.max_height,
+                     h->p.soft_argmin);
+    MosaicFrame fr;
+    for (int i = 0; i < 9; ++i) fr.R[i] = R[i];
+    for (int i = 0; i < 3; ++i) fr.t[i] = t[i];
+    fr.f = cam->f; fr.cx = cam->cx; fr.cy = cam->cy;
+    fr.tau = tau; fr.r0 = r0; fr.gmin = gmin;
+    fr.W = W; fr.H = H;
+    const MosaicModel m{pm->pos, pm->rgb, pm->wpos, pm->wrgb, pm->count, pm->dropped, pm->capacity};
+    auto* zbuf = reinterpret_cast<unsigned long long*>(w.keys);     // W*H*8 bytes
+    int* pref = reinterpret_cast<int*>(w.dt);
+    int* rowtot = reinterpret_cast<int*>(w.b);
+    int* rowoff = reinterpret_cast<int*>(w.rsC);
+    cudaMemsetAsync(zbuf, 0xff, (size_t)W * H * 8, s);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_mosaic_project<<<4 * sms, 256, 0, s>>>(m, fr, zbuf);
+    k_mosaic_merge_row<<<H, MOSAIC_ROW_THREADS, 0, s>>>(m, fr, xyz, rgb, zbuf, pref, rowtot);
+    k_mosaic_offsets<<<1, 1024, 0, s>>>(m, H, rowtot, rowoff);
+    k_mosaic_append<<<dim3((W + 255) / 256, H), 256, 0, s>>>(m, fr, xyz, rgb, pref, rowoff);
+    counted(4);
     return last_error();
 }
 
