@@ -66,6 +66,8 @@ def lib():
         P = C.c_void_p
         i, d = C.c_int, C.c_double
         sig = {
+            "or_vote_nbins": (i, [C.c_float, C.c_float]),
+            "or_vote_matches": (None, [P, P, i, C.c_float, C.c_float, P, P, P]),
             "or_mosaic_frame": (i, [P, P, P, P, P, i, P, P, i, i, C.c_float, C.c_float, C.c_float, P, P, C.c_float, C.c_float, C.c_float]),
             "or_depth_points": (None, [P, i, i, d, d, d, d, d, P, P]),
             "or_gray": (None, [P, i, i, P]),
@@ -360,3 +362,17 @@ def mosaic_frame(model: PointModel, xyz, img, f, cx, cy, R, t, tau, r0=0.5, gmin
                                     float(cx), float(cy), _p(R), _p(t), float(tau), float(r0), float(gmin))
     model.count = cnt.value
     return dropped
+
+
+def vote_matches(uv1, uv2, bin=4.0, range_=128.0):
+    """Histogram-voting preselection (Sec. II): returns (hist [nb, nb],
+    score [n], order [n])."""
+    uv1 = np.ascontiguousarray(uv1, np.float32)
+    uv2 = np.ascontiguousarray(uv2, np.float32)
+    n = uv1.shape[0]
+    nb = lib().or_vote_nbins(float(bin), float(range_))
+    hist = np.empty((nb, nb), np.int32)
+    score = np.empty(n, np.int32)
+    order = np.empty(n, np.int32)
+    lib().or_vote_matches(_p(uv1), _p(uv2), n, float(bin), float(range_), _p(hist), _p(score), _p(order))
+    return hist, score, order

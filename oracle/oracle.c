@@ -820,3 +820,56 @@ int or_mosaic_frame(double* pos, double* rgb, double* wpos, double* wrgb, int* c
     free(winz);
     return dropped;
 }
+
+/* ------------------------------------------------------------------------
+ * Histogram-voting preselection of feature-match inliers (Sec. II,
+ * histogram voting-based matching inliers preselection): correct matches
+ * between adjacent frames share nearly the same displacement (du, dv) =
+ * (u2 - u1, v2 - v1).  Displacements are binned into a 2-D histogram of
+ * bins of side `bin` over [-range, range)^2 (bin index floor((du + range) /
+ * bin), single precision; a displacement outside the range votes for no
+ * bin); the score of a match is the histogram count summed over the 3x3
+ * bins around its own (0 outside the range), and the matches are ranked by
+ * score, higher first, ties by index.  hist: nb x nb counts (nb =
+ * ceil(2 range / bin)); score, order: n entries. */
+static const int* or_vote_score_ptr;
+static int or_vote_cmp(const void* a, const void* b) {
+    const int i = *(const int*)a, j = *(const int*)b;
+    if (or_vote_score_ptr[i] != or_vote_score_ptr[j]) return or_vote_score_ptr[i] > or_vote_score_ptr[j] ? -1 : 1;
+    return i < j ? -1 : (i > j ? 1 : 0);
+}
+
+int or_vote_nbins(float bin, float range) {
+    return (int)ceilf((2.0f * range) / bin);
+}
+
+void or_vote_matches(const float* uv1, const float* uv2, int n, float bin, float range, int* hist,
+                     int* score, int* order) {
+    const int nb = or_vote_nbins(bin, range);
+    int* bx = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    int* by = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    for (int k = 0; k < nb * nb; ++k) hist[k] = 0;
+    for (int i = 0; i < n; ++i) {
+        const float du = uv2[2 * i] - uv1[2 * i], dv = uv2[2 * i + 1] - uv1[2 * i + 1];
+        const float fx = floorf((du + range) / bin), fy = floorf((dv + range) / bin);
+        bx[i] = by[i] = -1;
+        if (fx >= 0.0f && fx < (float)nb && fy >= 0.0f && fy < (float)nb) {
+            bx[i] = (int)fx;
+            by[i] = (int)fy;
+            hist[by[i] * nb + bx[i]] += 1;
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        int s = 0;
+        if (bx[i] >= 0)
+            for (int y = by[i] - 1; y <= by[i] + 1; ++y)
+                for (int x = bx[i] - 1; x <= bx[i] + 1; ++x)
+                    if (x >= 0 && x < nb && y >= 0 && y < nb) s += hist[y * nb + x];
+        score[i] = s;
+        order[i] = i;
+    }
+    or_vote_score_ptr = score;
+    qsort(order, (size_t)n, sizeof(int), or_vote_cmp);
+    free(bx);
+    free(by);
+}

@@ -72,6 +72,9 @@ double or_l1_loss(const double* dsoft, const uint8_t* has_valid,
                   const double* gt, size_t n, double* grad);
 void or_depth_points(const double* d, int W, int H, double f, double cx, double cy,
                      double B, double doffs, double* xyz, double* nrm);
+int or_vote_nbins(float bin, float range);
+void or_vote_matches(const float* uv1, const float* uv2, int n, float bin, float range, int* hist,
+                     int* score, int* order);
 int or_mosaic_frame(double* pos, double* rgb, double* wpos, double* wrgb, int* count, int capacity,
                     const float* xyz, const uint8_t* img, int W, int H, float f, float cx, float cy,
                     const float* R, const float* t, float tau, float r0, float gmin);

@@ -231,3 +231,17 @@ def batch_pair(i: int):
     sp = batch_pair_spec(i)
     L, R, gt = tissue_pair(sp["seed"], sp["W"], sp["H"], sp["lo"], sp["hi"])
     return L, R, gt, sp
+
+
+def feature_matches(seed: int, n: int = 2000, inlier_frac: float = 0.15, shift=(6.0, -3.0),
+                    noise: float = 1.0, W: int = 960, H: int = 540, max_disp: float = 120.0):
+    """Synthetic feature matches between two adjacent frames: keypoints
+    uniform in the image; inliers move by `shift` plus N(0, noise) per
+    coordinate, outliers by a uniform displacement in [-max_disp, max_disp)^2.
+    Returns (uv1 [n, 2], uv2 [n, 2], is_inlier [n]) as float32 / bool."""
+    rng = np.random.default_rng(seed)
+    uv1 = np.stack([rng.uniform(0, W, n), rng.uniform(0, H, n)], -1)
+    inl = rng.random(n) < inlier_frac
+    d = rng.uniform(-max_disp, max_disp, (n, 2))
+    d[inl] = np.asarray(shift) + rng.normal(0.0, noise, (int(inl.sum()), 2))
+    return uv1.astype(np.float32), (uv1 + d).astype(np.float32), inl
