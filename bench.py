@@ -377,6 +377,15 @@ def run_single(args, wl, rank, world, dev):
     mosaic_ms = sorted(mosaic_ms)[len(mosaic_ms) // 2]
     model_points = int(model.count.item())
 
+    # histogram-voting preselection of 2000 feature matches (85 % outliers)
+    uv1, uv2, _ = synth.feature_matches(synth.seed_for(7), n=2000, inlier_frac=0.15)
+    tuv1, tuv2 = torch.from_numpy(uv1).to(dev), torch.from_numpy(uv2).to(dev)
+    vh, vs, vo = st.stereo_vote_matches(tuv1, tuv2, stream=stream)
+    vote_ms = _timed_loop(torch, stream, min(args.steps, 20),
+                          lambda: st.stereo_vote_matches(tuv1, tuv2, hist=vh, score=vs, order=vo, stream=stream),
+                          flush)
+    vote_ms = sorted(vote_ms)[len(vote_ms) // 2]
+
     # end to end through the public API, run the way a video loop runs it:
     # every step uploads a pinned host RGB pair, matches it and reads the
     # refined map back; two device buffer sets let the upload of the next
@@ -456,6 +465,8 @@ def run_single(args, wl, rank, world, dev):
                          "frame_pixels": W * H,
                          "note": "point-based TSDF merge of the refined map's points into the model; "
                                  "event-timed, L2 flushed; not part of the step"},
+        "vote_matches": {"ms_median": round(vote_ms, 4), "matches": 2000,
+                         "note": "histogram-voting inlier preselection, 85 % outliers; not part of the step"},
     })
     return line
 

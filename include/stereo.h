@@ -328,6 +328,20 @@ typedef struct {
 stereo_status stereo_depth_points(const float* disp, int32_t width, int32_t height, const stereo_camera* cam,
                                   float* xyz, float* normals, void* stream);
 
+/* Histogram-voting preselection of feature-match inliers (Sec. II):
+ * displacements (u2 - u1, v2 - v1) of n matches (uv1, uv2: float [n][2]
+ * device arrays) are binned into an nb x nb histogram of bins of side `bin`
+ * over [-range, range)^2, nb = stereo_vote_nbins(bin, range) (bin index
+ * floor((d + range) / bin) in single precision; a displacement outside the
+ * range votes for no bin); score[i] = the counts of the 3x3 bins around
+ * match i's own (0 without a bin); order = the match indices by score,
+ * higher first, ties by index.  hist (int32 nb*nb), score and order (int32
+ * n) are caller-owned device arrays and all three are written.  n <= 16384
+ * (STEREO_ERR_TOO_LARGE beyond), nb <= 4096. */
+int32_t stereo_vote_nbins(float bin, float range);
+stereo_status stereo_vote_matches(const float* uv1, const float* uv2, int32_t n, float bin, float range,
+                                  int32_t* hist, int32_t* score, int32_t* order, void* stream);
+
 /* Surface model of the point-based TSDF mosaicking (Sec. II, GPU-based TSDF
  * mosaicking): caller-owned device arrays of `capacity` points -- world
  * position (float [capacity][3]), RGB colour 0..255 (float [capacity][3]),

@@ -21,7 +21,8 @@ __all__ = [
     "stereo_get_stage_times", "stereo_launch_count", "STAGE_NAMES", "stereo_set_tuning",
     "stereo_match_wta_noalloc", "stereo_softargmin_fwd", "stereo_softargmin_bwd", "stereo_l1_loss",
     "SoftArgminZNCC", "soft_argmin", "stereo_set_batch_config", "stereo_autotune_batched",
-    "StereoCamera", "stereo_depth_points", "PointModel", "stereo_mosaic_frame",
+    "StereoCamera", "stereo_depth_points", "PointModel", "stereo_mosaic_frame", "stereo_vote_nbins",
+    "stereo_vote_matches",
 ]
 
 STAGE_NAMES = ("input", "stats", "cost_wta", "finalize", "postprocess", "refine")
@@ -119,6 +120,8 @@ def lib():
                                                 P]),
             "stereo_l1_loss": (C.c_int, [P, P, P, C.c_int64, P, P, P]),
             "stereo_depth_points": (C.c_int, [P, i32, i32, P, P, P, P]),
+            "stereo_vote_nbins": (i32, [C.c_float, C.c_float]),
+            "stereo_vote_matches": (C.c_int, [P, P, i32, C.c_float, C.c_float, P, P, P, P]),
             "stereo_mosaic_frame": (C.c_int, [P, P, P, P, i32, i32, P, P, P, C.c_float, C.c_float,
                                               C.c_float, P]),
             "stereo_set_batch_config": (C.c_int, [P, i32, i32]),
@@ -449,6 +452,27 @@ def stereo_depth_points(disp, camera: StereoCamera, xyz=None, normals=None, stre
     _check(lib().stereo_depth_points(_ptr(disp, torch.float32, "disp"), W, H, C.byref(camera),
                                      _ptr(xyz, torch.float32, "xyz"), _ptr(normals, torch.float32, "normals"),
                                      _stream(stream)), "stereo_depth_points")
+
+
+def stereo_vote_nbins(bin: float, range_: float) -> int:
+    return int(lib().stereo_vote_nbins(float(bin), float(range_)))
+
+
+def stereo_vote_matches(uv1, uv2, bin=4.0, range_=128.0, hist=None, score=None, order=None, stream=None):
+    """Histogram-voting inlier preselection (Sec. II) of n matches (uv1, uv2:
+    float32 [n, 2] device tensors).  Returns (hist [nb, nb], score [n],
+    order [n]) int32 device tensors."""
+    import torch
+    n = uv1.shape[0]
+    nb = stereo_vote_nbins(bin, range_)
+    hist = hist if hist is not None else torch.empty((nb, nb), dtype=torch.int32, device=uv1.device)
+    score = score if score is not None else torch.empty(n, dtype=torch.int32, device=uv1.device)
+    order = order if order is not None else torch.empty(n, dtype=torch.int32, device=uv1.device)
+    _check(lib().stereo_vote_matches(_ptr(uv1, torch.float32, "uv1"), _ptr(uv2, torch.float32, "uv2"), n,
+                                     float(bin), float(range_), _ptr(hist, torch.int32, "hist"),
+                                     _ptr(score, torch.int32, "score"), _ptr(order, torch.int32, "order"),
+                                     _stream(stream)), "stereo_vote_matches")
+    return hist, score, order
 
 
 class PointModel:

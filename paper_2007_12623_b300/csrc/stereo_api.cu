@@ -23,6 +23,7 @@
 #include "batch.cuh"
 #include "depth.cuh"
 #include "mosaic.cuh"
+#include "vote.cuh"
 
 namespace {
 
@@ -277,6 +278,7 @@ void set_smem_attributes() {
     cudaFuncSetAttribute(k_refine_box2o, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_soft_final, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_soft_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_vote_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, VOTE_MAX_N * 8);
     cudaFuncSetAttribute(k_soft_dA, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
@@ -1247,6 +1249,32 @@ stereo_status stereo_depth_points(const float* disp, int32_t W, int32_t H, const
     k_depth_points<<<dim3((W + DEPTH_TX - 1) / DEPTH_TX, (H + DEPTH_TY - 1) / DEPTH_TY), dim3(DEPTH_TX, DEPTH_TY), 0,
                      S(stream)>>>(disp, W, H, c, xyz, normals);
     counted();
+    return last_error();
+}
+
+int32_t stereo_vote_nbins(float bin, float range) {
+    if (!(bin > 0.f) || !(range > 0.f)) return 0;
+    const float q = (2.0f * range) / bin;
+    return q > 4096.f ? 4097 : (int32_t)ceilf(q);
+}
+
+stereo_status stereo_vote_matches(const float* uv1, const float* uv2, int32_t n, float bin, float range,
+                                  int32_t* hist, int32_t* score, int32_t* order, void* stream) {
+    if (!uv1 || !uv2 || !hist || !score || !order || n < 0 || !(bin > 0.f) || !(range > 0.f))
+        return STEREO_ERR_INVALID_ARG;
+    const int nb = stereo_vote_nbins(bin, range);
+    if (nb < 1 || nb > 4096 || n > VOTE_MAX_N) return STEREO_ERR_TOO_LARGE;
+    set_smem_attributes();
+    cudaStream_t s = S(stream);
+    cudaMemsetAsync(hist, 0, (size_t)nb * nb * 4, s);
+    if (n == 0) return last_error();
+    const unsigned g = (unsigned)((n + 255) / 256);
+    k_vote_hist<<<g, 256, 0, s>>>(uv1, uv2, n, bin, range, nb, hist);
+    k_vote_score<<<g, 256, 0, s>>>(uv1, uv2, n, bin, range, nb, hist, score);
+    int m = 1;
+    while (m < n) m <<= 1;
+    k_vote_sort<<<1, VOTE_SORT_THREADS, (size_t)m * 8, s>>>(score, n, order);
+    counted(3);
     return last_error();
 }
 

@@ -59,4 +59,6 @@ def test_host_side_argument_checks(L):
     assert L.stereo_depth_points(C.c_void_p(16), 8, 8, C.byref(cam), None, None, None) == 1   # no output
     bad = st.StereoCamera(0.0, 10.0, 10.0, 5.0, 0.0)
     assert L.stereo_depth_points(C.c_void_p(16), 8, 8, C.byref(bad), C.c_void_p(16), None, None) == 1
+    assert L.stereo_vote_nbins(4.0, 128.0) == 64 and L.stereo_vote_nbins(0.0, 1.0) == 0
+    assert L.stereo_vote_matches(None, None, 10, 4.0, 128.0, None, None, None, None) == 1
     assert L.stereo_destroy(None) == 0
