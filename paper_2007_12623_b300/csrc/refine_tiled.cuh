@@ -1,123 +1,133 @@
 // refine_tiled.cuh -- Sec. II-C on shared-memory tiles: one iteration of the
-// improved Laplacian refinement is two kernels, each a (2 rs + 1)^2 box sum
-// over a 32x32 output tile with an rs-pixel halo (row sums, then column
-// sums, sliding along 8-element segments):
-//   k_refine_box1:  dt = mean of valid o (Eq. 1); b = dt - alpha o -
-//                   (1 - alpha) d_prev (Eq. 2); also the valid count.  o and
-//                   the valid flag travel packed in one 32-bit integer,
-//                   (o - d_min) << 12 | 1, whose box sum holds both sums
-//                   exactly (count < 4096, sum of (o - d_min) < 2^20).
-//   k_refine_box2o: d = dt - mean of valid b (Eq. 3), then the new integer
-//                   disparity o (Eq. 4) of the same pixel.
-// The first iteration reads the post-processed map directly (d_prev = o).
-// The same rules as refine.cuh (kept for radii beyond the tile halo).
+// improved Laplacian refinement is two kernels over 32x32 output tiles, each
+// a (2 rs + 1)^2 box sum (rs <= RB_MAX_RS) followed by per-pixel work:
+//   k_refine_eq12: dt = mean of the valid o in the box (Eq. 1) and
+//                  b = dt - alpha o - (1 - alpha) d_prev (Eq. 2).
+//   k_refine_eq34: d = dt - mean of the valid b in the box (Eq. 3), then the
+//                  new integer disparity o of the pixel (Eq. 4).
+// o and its valid flag travel packed in one 32-bit word,
+// (o - d_min) << 12 | 1 (0 where invalid), whose box sum holds both the count
+// (< 4096) and the sum of o - d_min (< 2^20) exactly.  The first iteration
+// reads the post-processed int16 map and writes the packed map and the valid
+// counts.  The o-update reads each pixel's candidates from the cost volume
+// with warp-cooperative loads: every 16-byte load instruction fetches a
+// whole 64-byte run of candidates for each of 8 pixels, and the runs reach
+// their pixels' lanes through shared memory.
+//
+// Box sums: the block stages the (32 + 2 rs) rows x (32 + 2 SPAD) columns
+// around its tile; one thread per staged row slides the horizontal sums
+// along the row, then one thread per (column, half tile) slides the vertical
+// sums down the column.
 #pragma once
+#include <algorithm>
 #include "common.cuh"
 
-constexpr int RT = 32;              // output tile edge
-constexpr int RT_THREADS = 256;
-constexpr int RT_MAX_RS = 24;       // halo limit of the tiled path
+constexpr int RB_T = 32;            // output tile edge
+constexpr int RB_THREADS = 256;
+constexpr int RB_MAX_RS = 32;       // halo limit of the tiled path
 
 __device__ float zncc_direct(const uint8_t* __restrict__ L, const uint8_t* __restrict__ Rm, int W,
                              int H, int r, int sampling, int x, int y, int d);
 
-// Box sums of `val` (float or int) over the tile: stage (RT+2rs)^2 values,
-// row sums into `rsum` ([RT+2rs][RT]), then column sums for each output.
-// Segment sliding: each thread owns 8 consecutive outputs of a row (column).
-template <typename T>
-__device__ __forceinline__ void box_rows(const T* tin, int sw, int sh, int rs, T* rsum) {
-    // rows: sh rows x RT columns, 4 segments of 8 per row
-    for (int job = threadIdx.x; job < sh * (RT / 8); job += RT_THREADS) {
-        const int y = job / (RT / 8), seg = job % (RT / 8);
-        const T* row = tin + y * sw + seg * 8;       // window of output seg*8 starts here
+__device__ __forceinline__ uint32_t pack_o(int o, int d_min) {
+    return o == ST_INVALID ? 0u : (((uint32_t)(o - d_min) << 12) | 1u);
+}
+__device__ __forceinline__ int unpack_o(uint32_t p, int d_min) {
+    return p ? (int)(p >> 12) + d_min : ST_INVALID;
+}
+
+// Shared memory of the tile kernels (4-byte elements): staged rows with a
+// padded stride (conflict-free row-per-lane access), horizontal sums, box sums.
+__host__ __device__ inline int rb_spad(int rs) { return rs <= 16 ? 16 : 32; }
+__host__ __device__ inline int rb_rows(int rs) { return RB_T + 2 * rs; }
+inline size_t refine_tile_smem(int rs) {
+    const size_t rows = rb_rows(rs), swp = RB_T + 2 * rb_spad(rs) + 1;
+    // the o-update reuses the first 20 KB for its candidate runs
+    return std::max<size_t>((rows * swp + rows * (RB_T + 1) + RB_T * (RB_T + 1)) * 4, 8 * 32 * 80);
+}
+
+// Stages rows [y0 - rs, y0 + 32 + rs) x columns [x0 - SPAD, x0 + 32 + SPAD)
+// of `src` (zero outside the image); CONV turns an int16 disparity into the
+// packed form.  Interior tiles of maps whose rows are 16-byte aligned use
+// 16-byte loads.
+template <typename T, typename S, bool CONV, int SPAD>
+__device__ __forceinline__ void rb_stage(const S* __restrict__ src, int W, int H, int x0, int y0, int rs,
+                                         int d_min, T* tile) {
+    constexpr int SW = RB_T + 2 * SPAD, SWP = SW + 1;
+    const int rows = rb_rows(rs);
+    const int gx0 = x0 - SPAD;
+    const bool vec = !CONV && gx0 >= 0 && gx0 + SW <= W && (W & 3) == 0;
+    if (vec) {
+        for (int i = threadIdx.x; i < rows * (SW / 4); i += RB_THREADS) {
+            const int ry = i / (SW / 4), c4 = i % (SW / 4);
+            const int gy = y0 - rs + ry;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (gy >= 0 && gy < H)
+                v = __ldg(reinterpret_cast<const uint4*>(src + (size_t)gy * W + gx0) + c4);
+            T* d = tile + ry * SWP + 4 * c4;
+            d[0] = *reinterpret_cast<T*>(&v.x);
+            d[1] = *reinterpret_cast<T*>(&v.y);
+            d[2] = *reinterpret_cast<T*>(&v.z);
+            d[3] = *reinterpret_cast<T*>(&v.w);
+        }
+    } else {
+        for (int i = threadIdx.x; i < rows * SW; i += RB_THREADS) {
+            const int ry = i / SW, cx = i % SW;
+            const int gy = y0 - rs + ry, gx = gx0 + cx;
+            T v = T(0);
+            if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+                if (CONV) {
+                    const uint32_t p = pack_o(src[(size_t)gy * W + gx], d_min);
+                    v = *reinterpret_cast<const T*>(&p);
+                } else {
+                    v = *reinterpret_cast<const T*>(src + (size_t)gy * W + gx);
+                }
+            }
+            tile[ry * SWP + cx] = v;
+        }
+    }
+}
+
+// Box sums of the staged tile into box[32][33] (row-major, padded).
+template <typename T, int SPAD>
+__device__ __forceinline__ void rb_box(const T* tile, int rs, T* hsum, T* box) {
+    constexpr int SWP = RB_T + 2 * SPAD + 1;
+    const int rows = rb_rows(rs);
+    // horizontal: one thread per staged row, 32 outputs
+    if (threadIdx.x < rows) {
+        const T* a = tile + threadIdx.x * SWP + (SPAD - rs);
         T s = T(0);
-        for (int k = 0; k <= 2 * rs; ++k) s += row[k];
-        T* o = rsum + y * RT + seg * 8;
+        for (int i = 0; i <= 2 * rs; ++i) s += a[i];
+        T* h = hsum + threadIdx.x * (RB_T + 1);
+        h[0] = s;
+#pragma unroll 8
+        for (int j = 1; j < RB_T; ++j) {
+            s += a[j + 2 * rs] - a[j - 1];
+            h[j] = s;
+        }
+    }
+    __syncthreads();
+    // vertical: one thread per (column, half of the tile), 16 outputs
+    if (threadIdx.x < 2 * RB_T) {
+        const int c = threadIdx.x & (RB_T - 1), half = threadIdx.x / RB_T;
+        const T* a = hsum + 16 * half * (RB_T + 1) + c;
+        T s = T(0);
+        for (int i = 0; i <= 2 * rs; ++i) s += a[i * (RB_T + 1)];
+        T* o = box + 16 * half * (RB_T + 1) + c;
         o[0] = s;
 #pragma unroll
-        for (int j = 1; j < 8; ++j) {
-            s += row[j + 2 * rs] - row[j - 1];
-            o[j] = s;
+        for (int j = 1; j < 16; ++j) {
+            s += a[(j + 2 * rs) * (RB_T + 1)] - a[(j - 1) * (RB_T + 1)];
+            o[j * (RB_T + 1)] = s;
         }
     }
-}
-
-template <typename T>
-__device__ __forceinline__ void box_cols(const T* rsum, int rs, T* out /* [RT][RT] */) {
-    for (int job = threadIdx.x; job < RT * (RT / 8); job += RT_THREADS) {
-        const int x = job % RT, seg = job / RT;
-        const T* col = rsum + seg * 8 * RT + x;
-        T s = T(0);
-        for (int k = 0; k <= 2 * rs; ++k) s += col[k * RT];
-        out[(seg * 8) * RT + x] = s;
-#pragma unroll
-        for (int j = 1; j < 8; ++j) {
-            s += col[(j + 2 * rs) * RT] - col[(j - 1) * RT];
-            out[(seg * 8 + j) * RT + x] = s;
-        }
-    }
-}
-
-// dprev == nullptr: first iteration, d_prev = o.
-__global__ void __launch_bounds__(RT_THREADS) k_refine_box1(const int16_t* __restrict__ o,
-                                                            const float* __restrict__ dprev, int W,
-                                                            int H, int rs, float alpha, int d_min,
-                                                            float* __restrict__ dt,
-                                                            float* __restrict__ b,
-                                                            int16_t* __restrict__ cnt_out) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int sw = RT + 2 * rs, sh = RT + 2 * rs;
-    uint32_t* vp = reinterpret_cast<uint32_t*>(sm);        // [sh][sw] packed (o - d_min) << 12 | valid
-    uint32_t* rp = vp + sw * sh;                           // [sh][RT]
-    uint32_t* sp = rp + sh * RT;                           // [RT][RT]
-    const int x0 = blockIdx.x * RT - rs, y0 = blockIdx.y * RT - rs;
-    for (int i = threadIdx.x; i < sw * sh; i += RT_THREADS) {
-        const int gy = y0 + i / sw, gx = x0 + i % sw;
-        int v = ST_INVALID;
-        if (gx >= 0 && gx < W && gy >= 0 && gy < H) v = o[(size_t)gy * W + gx];
-        vp[i] = v != ST_INVALID ? ((uint32_t)(v - d_min) << 12) | 1u : 0u;
-    }
     __syncthreads();
-    box_rows<uint32_t>(vp, sw, sh, rs, rp);
-    __syncthreads();
-    box_cols<uint32_t>(rp, rs, sp);
-    __syncthreads();
-    for (int i = threadIdx.x; i < RT * RT; i += RT_THREADS) {
-        const int gx = blockIdx.x * RT + i % RT, gy = blockIdx.y * RT + i / RT;
-        if (gx >= W || gy >= H) continue;
-        const size_t gi = (size_t)gy * W + gx;
-        const int ov = o[gi];
-        if (ov == ST_INVALID) {
-            b[gi] = 0.f;
-            dt[gi] = __int_as_float(0x7fc00000);
-            cnt_out[gi] = 0;
-            continue;
-        }
-        const uint32_t sum = sp[i];
-        const int c = (int)(sum & 4095u);
-        const int osum = (int)(sum >> 12) + d_min * c;
-        const float m = (float)osum / (float)c;              // Eq. (1)
-        dt[gi] = m;
-        const float dp = dprev ? dprev[gi] : (float)ov;
-        b[gi] = m - alpha * (float)ov - (1.f - alpha) * dp;  // Eq. (2)
-        cnt_out[gi] = (int16_t)c;
-    }
-}
-
-inline size_t refine_box1_smem(int rs) {
-    const size_t sw = RT + 2 * rs, sh = RT + 2 * rs;
-    return (sw * sh + sh * RT + RT * RT) * 4;
-}
-inline size_t refine_box2_smem(int rs) {
-    const size_t sw = RT + 2 * rs, sh = RT + 2 * rs;
-    return (sw * sh + sh * RT + RT * RT) * 4;
 }
 
 // Eq. (4), one thread per pixel: o = argmin over integer o* in [d - S, d + S]
 // (clipped to the candidate range) of 1/ZNCC(o*) + eta (o* - d)^2, skipping
 // invalid candidates and ZNCC <= 0; ties -> smaller |o* - d|, then smaller
-// o*.  With a stored cost volume the 2S+1 <= 13 costs come in as four
-// aligned 16-byte loads (8-byte for 16-bit storage) issued together.
+// o*.
 __device__ __forceinline__ void oupdate_consider(int cand, float rho, float d, float eta, int& best,
                                                  float& bf, float& bdist) {
     if (!(rho > 0.f)) return;                           // NaN (invalid) or non-positive
@@ -131,8 +141,41 @@ __device__ __forceinline__ void oupdate_consider(int cand, float rho, float d, f
     }
 }
 
+// Candidate costs come as four aligned 16-byte (FP32) or 8-byte (16-bit)
+// loads from `row`, a pointer to cost index 0 of the pixel in either the
+// pixel's window copy or the volume; `lim` bounds the readable indexes.
+__device__ __forceinline__ void load16_costs(const void* row, int cdt, int k0, int lim, float c[16]) {
+    if (cdt == CDT_F32) {
+        const float4* p = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(row) + k0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 v = (k0 + 4 * q < lim) ? __ldg(p + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+        }
+    } else {
+        const uint2* p = reinterpret_cast<const uint2*>(reinterpret_cast<const uint16_t*>(row) + k0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint2 v = (k0 + 4 * q < lim) ? __ldg(p + q) : make_uint2(0u, 0u);
+            const uint32_t w[2] = {v.x, v.y};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint16_t a = (uint16_t)(w[h] & 0xffffu), b = (uint16_t)(w[h] >> 16);
+                if (cdt == CDT_F16) {
+                    c[4 * q + 2 * h] = __half2float(__ushort_as_half(a));
+                    c[4 * q + 2 * h + 1] = __half2float(__ushort_as_half(b));
+                } else {
+                    c[4 * q + 2 * h] = __bfloat162float(__ushort_as_bfloat16(a));
+                    c[4 * q + 2 * h + 1] = __bfloat162float(__ushort_as_bfloat16(b));
+                }
+            }
+        }
+    }
+}
+
 // New integer disparity of valid pixel i (Eq. 4) given its refined d; returns
-// `ov` when no candidate qualifies.
+// `ov` when no candidate qualifies (the general path: any search radius, or
+// no stored volume).
 __device__ __forceinline__ int oupdate_pixel(size_t i, int ov, float d, float eta, int search, int d_min,
                                              int D, const void* __restrict__ cost, int cdt,
                                              const uint8_t* __restrict__ L, const uint8_t* __restrict__ Rm,
@@ -146,34 +189,8 @@ __device__ __forceinline__ int oupdate_pixel(size_t i, int ov, float d, float et
     if (cdt != CDT_NONE && hi - lo < 13) {
         const int k0 = (lo - d_min) & ~3;                   // 16 candidates from k0
         float c[16];
-        if (cdt == CDT_F32) {
-            const float4* p = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(cost) +
-                                                              (size_t)i * cs + k0);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 v = (k0 + 4 * q < cs) ? __ldg(p + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-                c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
-            }
-        } else {
-            const uint2* p = reinterpret_cast<const uint2*>(reinterpret_cast<const uint16_t*>(cost) +
-                                                            (size_t)i * cs + k0);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint2 v = (k0 + 4 * q < cs) ? __ldg(p + q) : make_uint2(0u, 0u);
-                const uint32_t w[2] = {v.x, v.y};
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint16_t a = (uint16_t)(w[h] & 0xffffu), b = (uint16_t)(w[h] >> 16);
-                    if (cdt == CDT_F16) {
-                        c[4 * q + 2 * h] = __half2float(__ushort_as_half(a));
-                        c[4 * q + 2 * h + 1] = __half2float(__ushort_as_half(b));
-                    } else {
-                        c[4 * q + 2 * h] = __bfloat162float(__ushort_as_bfloat16(a));
-                        c[4 * q + 2 * h + 1] = __bfloat162float(__ushort_as_bfloat16(b));
-                    }
-                }
-            }
-        }
+        load16_costs(reinterpret_cast<const char*>(cost) + i * (size_t)cs * (cdt == CDT_F32 ? 4 : 2), cdt,
+                     k0, cs, c);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const int cand = d_min + k0 + j;
@@ -191,51 +208,256 @@ __device__ __forceinline__ int oupdate_pixel(size_t i, int ov, float d, float et
     return best != ST_INVALID ? best : ov;
 }
 
-// Eq. (3) and Eq. (4) for one tile: o_src is read at the block's own pixels
-// only, so o_dst may alias it.  First iteration: o_src is the
-// post-processed map, o_dst the working copy (written at every pixel), and
-// `valid` (optional) receives the validity mask.  o_dst == nullptr: Eq. (4)
-// is skipped (last iteration when nobody reads the final o).
-__global__ void __launch_bounds__(RT_THREADS) k_refine_box2o(
-    const int16_t* o_src, int16_t* o_dst, float* __restrict__ dprev,
-    const float* __restrict__ dt, const float* __restrict__ b, const int16_t* __restrict__ cnt, int W, int H,
-    int rs, float* __restrict__ d_out, uint8_t* __restrict__ valid, float eta, int search, int d_min, int D,
-    const void* __restrict__ cost, int cdt, const uint8_t* __restrict__ L, const uint8_t* __restrict__ Rm,
-    int r, int sampling) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int sw = RT + 2 * rs, sh = RT + 2 * rs;
-    float* vb = reinterpret_cast<float*>(sm);              // [sh][sw]
-    float* rb = vb + sw * sh;                              // [sh][RT]
-    float* sb = rb + sh * RT;                              // [RT][RT]
-    const int x0 = blockIdx.x * RT - rs, y0 = blockIdx.y * RT - rs;
-    for (int i = threadIdx.x; i < sw * sh; i += RT_THREADS) {
-        const int gy = y0 + i / sw, gx = x0 + i % sw;
-        float v = 0.f;
-        if (gx >= 0 && gx < W && gy >= 0 && gy < H) v = b[(size_t)gy * W + gx];  // 0 if invalid
-        vb[i] = v;
-    }
-    __syncthreads();
-    box_rows<float>(vb, sw, sh, rs, rb);
-    __syncthreads();
-    box_cols<float>(rb, rs, sb);
-    __syncthreads();
+struct RefineArgs {
+    int W, H, rs, d_min, D;
+    float alpha, eta;
+    int search;
+    const void* cost; int cdt;            // cost volume (or CDT_NONE)
+    const uint8_t* L; const uint8_t* Rm;  // gray images for the direct ZNCC
+    int r, sampling;
+    uint32_t* op;                         // packed o
+    float* dprev; float* dt; float* b;
+    int16_t* cnt;
+};
+
+// Eqs. (1)-(2).  FIRST: o comes from the int16 map o_in (d_prev = o); the
+// kernel also writes the packed map, the counts and the valid mask.  The
+// per-pixel loads of the epilogue are issued before the box sums.
+template <bool FIRST, int SPAD>
+__global__ void __launch_bounds__(RB_THREADS) k_refine_eq12(RefineArgs a, const int16_t* __restrict__ o_in,
+                                                            uint8_t* __restrict__ valid) {
+    extern __shared__ __align__(16) uint32_t rsm[];
+    constexpr int SWP = RB_T + 2 * SPAD + 1;
+    const int rows = rb_rows(a.rs);
+    uint32_t* tile = rsm;
+    uint32_t* hsum = tile + rows * SWP;
+    uint32_t* box = hsum + rows * (RB_T + 1);
+    const int x0 = blockIdx.x * RB_T, y0 = blockIdx.y * RB_T;
+    constexpr int NQ = RB_T * RB_T / RB_THREADS;
+    float dpv[NQ];
 #pragma unroll
-    for (int q = 0; q < RT * RT / RT_THREADS; ++q) {
-        const int i = threadIdx.x + q * RT_THREADS;
-        const int gx = blockIdx.x * RT + i % RT, gy = blockIdx.y * RT + i / RT;
-        if (gx >= W || gy >= H) continue;
-        const size_t gi = (size_t)gy * W + gx;
-        const int ov = o_src[gi];
-        if (valid) valid[gi] = ov != ST_INVALID;
-        if (ov == ST_INVALID) {
-            if (d_out) d_out[gi] = __int_as_float(0x7fc00000);
-            if (o_dst && o_dst != o_src) o_dst[gi] = (int16_t)ST_INVALID;
+    for (int q = 0; q < NQ; ++q) {
+        const int t = threadIdx.x + q * RB_THREADS;
+        const int gx = x0 + t % RB_T, gy = y0 + t / RB_T;
+        dpv[q] = (!FIRST && gx < a.W && gy < a.H) ? a.dprev[(size_t)gy * a.W + gx] : 0.f;
+    }
+    if (FIRST) rb_stage<uint32_t, int16_t, true, SPAD>(o_in, a.W, a.H, x0, y0, a.rs, a.d_min, tile);
+    else rb_stage<uint32_t, uint32_t, false, SPAD>(a.op, a.W, a.H, x0, y0, a.rs, a.d_min, tile);
+    __syncthreads();
+    rb_box<uint32_t, SPAD>(tile, a.rs, hsum, box);
+#pragma unroll
+    for (int q = 0; q < RB_T * RB_T / RB_THREADS; ++q) {
+        const int t = threadIdx.x + q * RB_THREADS;
+        const int lx = t % RB_T, ly = t / RB_T;
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= a.W || gy >= a.H) continue;
+        const size_t gi = (size_t)gy * a.W + gx;
+        const uint32_t pk = tile[(ly + a.rs) * SWP + SPAD + lx];
+        if (FIRST) {
+            a.op[gi] = pk;
+            if (valid) valid[gi] = pk != 0u;
+        }
+        if (!pk) {
+            a.b[gi] = 0.f;
+            a.dt[gi] = __int_as_float(0x7fc00000);
+            if (FIRST) a.cnt[gi] = 0;
             continue;
         }
-        const float d = dt[gi] - sb[i] / (float)cnt[gi];      // Eq. (3)
-        dprev[gi] = d;
-        if (d_out) d_out[gi] = d;
-        if (o_dst) o_dst[gi] = (int16_t)oupdate_pixel(gi, ov, d, eta, search, d_min, D, cost, cdt, L, Rm, W, H, r,
-                                           sampling);          // Eq. (4)
+        const int ov = unpack_o(pk, a.d_min);
+        const uint32_t sum = box[ly * (RB_T + 1) + lx];
+        const int c = (int)(sum & 4095u);
+        const int osum = (int)(sum >> 12) + a.d_min * c;
+        const float m = (float)osum / (float)c;              // Eq. (1)
+        a.dt[gi] = m;
+        const float dp = FIRST ? (float)ov : dpv[q];
+        a.b[gi] = m - a.alpha * (float)ov - (1.f - a.alpha) * dp;  // Eq. (2)
+        if (FIRST) a.cnt[gi] = (int16_t)c;
     }
 }
+
+// Eqs. (3)-(4).  UPDATE: run the o-update (skipped after the last iteration
+// unless the caller reads o); o_out: int16 copy of the new o (or nullptr).
+template <bool UPDATE, int SPAD>
+__global__ void __launch_bounds__(RB_THREADS) k_refine_eq34(RefineArgs a, float* __restrict__ d_out,
+                                                            int16_t* __restrict__ o_out) {
+    extern __shared__ __align__(16) float fsm[];
+    constexpr int SWP = RB_T + 2 * SPAD + 1;
+    const int rows = rb_rows(a.rs);
+    float* tile = fsm;
+    float* hsum = tile + rows * SWP;
+    float* box = hsum + rows * (RB_T + 1);
+    const int x0 = blockIdx.x * RB_T, y0 = blockIdx.y * RB_T;
+    constexpr int NQ = RB_T * RB_T / RB_THREADS;
+    uint32_t pkv[NQ];
+    float dtv[NQ], cntv[NQ], dv[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int t = threadIdx.x + q * RB_THREADS;
+        const int gx = x0 + t % RB_T, gy = y0 + t / RB_T;
+        pkv[q] = 0u;
+        dtv[q] = cntv[q] = 1.f;
+        dv[q] = 0.f;
+        if (gx < a.W && gy < a.H) {
+            const size_t gi = (size_t)gy * a.W + gx;
+            pkv[q] = a.op[gi];
+            dtv[q] = a.dt[gi];
+            cntv[q] = (float)a.cnt[gi];
+        }
+    }
+    rb_stage<float, float, false, SPAD>(a.b, a.W, a.H, x0, y0, a.rs, a.d_min, tile);
+    __syncthreads();
+    rb_box<float, SPAD>(tile, a.rs, hsum, box);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int t = threadIdx.x + q * RB_THREADS;
+        const int lx = t % RB_T, ly = t / RB_T;
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= a.W || gy >= a.H) continue;
+        const size_t gi = (size_t)gy * a.W + gx;
+        const uint32_t pk = pkv[q];
+        if (!pk) {
+            if (d_out) d_out[gi] = __int_as_float(0x7fc00000);
+            if (o_out) o_out[gi] = (int16_t)ST_INVALID;
+            continue;
+        }
+        const float d = dtv[q] - box[ly * (RB_T + 1) + lx] / cntv[q];   // Eq. (3)
+        a.dprev[gi] = d;
+        if (d_out) d_out[gi] = d;
+        dv[q] = d;
+    }
+    if (!UPDATE) return;
+    // Eq. (4).  Fast path (stored volume, search radius <= 5): in round q,
+    // warp w owns the 32 pixels of tile row w + 8 q (lane = column); each
+    // needs at most 11 candidates from o_lo, inside the 64-byte run that
+    // starts at k0 = (o_lo - d_min) & ~3 (FP32) or & ~7 (16-bit).  Load i of
+    // a round fetches 16-byte chunk (lane & 3) of pixel 8 i + lane / 4; the
+    // next round's loads are issued before a round is evaluated.  1/ZNCC is
+    // the hardware reciprocal (within 1 ulp).
+    const bool fast = a.cdt != CDT_NONE && a.search <= 5;
+    if (!fast) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int t = threadIdx.x + q * RB_THREADS;
+            const int gx = x0 + t % RB_T, gy = y0 + t / RB_T;
+            if (gx >= a.W || gy >= a.H || !pkv[q]) continue;
+            const size_t gi = (size_t)gy * a.W + gx;
+            const int on = oupdate_pixel(gi, unpack_o(pkv[q], a.d_min), dv[q], a.eta, a.search, a.d_min, a.D,
+                                         a.cost, a.cdt, a.L, a.Rm, a.W, a.H, a.r, a.sampling);
+            a.op[gi] = pack_o(on, a.d_min);
+            if (o_out) o_out[gi] = (int16_t)on;
+        }
+        return;
+    }
+    __syncthreads();                        // every warp is done with the box sums
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cs = cost_stride(a.D);
+    const int esz = a.cdt == CDT_F32 ? 4 : 2;
+    // [32 pixels][5 x 16 bytes]: the 80-byte pixel stride keeps the 16-byte
+    // writes and reads of each quarter warp on distinct banks
+    uint4* run = reinterpret_cast<uint4*>(fsm) + warp * 32 * 5;
+    auto issue = [&](int q, int& lo, int& n, int& k0, uint4 (&ld)[4]) {
+        const int gx = x0 + lane, gy = y0 + warp + 8 * q;
+        const bool live = gx < a.W && gy < a.H && pkv[q] != 0u;
+        int hi = -1;
+        lo = 0;
+        if (live) {
+            lo = max((int)ceilf(dv[q] - (float)a.search), a.d_min);
+            hi = min((int)floorf(dv[q] + (float)a.search), a.d_min + a.D - 1);
+        }
+        n = live ? hi - lo + 1 : 0;
+        const int kb = (lo - a.d_min) & ~3;
+        k0 = esz == 4 ? kb : (kb & ~7);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int p = 8 * i + (lane >> 2), ch = lane & 3;
+            const int pk0 = __shfl_sync(0xffffffffu, k0, p);
+            const int pn = __shfl_sync(0xffffffffu, n, p);
+            const int kc = pk0 + ch * (16 / esz);                     // first cost index of the chunk
+            ld[i] = make_uint4(0u, 0u, 0u, 0u);
+            if (pn > 0 && kc < cs) {
+                const size_t gp = (size_t)gy * a.W + x0 + p;
+                ld[i] = __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(a.cost) +
+                                                             (gp * (size_t)cs + kc) * esz));
+            }
+        }
+    };
+    int lo_c, n_c, k0_c, lo_n = 0, n_n = 0, k0_n = 0;
+    uint4 ld_c[4], ld_n[4];
+    issue(0, lo_c, n_c, k0_c, ld_c);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        if (q + 1 < NQ) issue(q + 1, lo_n, n_n, k0_n, ld_n);        // next round's loads in flight
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) run[(8 * i + (lane >> 2)) * 5 + (lane & 3)] = ld_c[i];
+        __syncwarp();
+        if (n_c > 0) {
+            // the pixel's 16 costs from kb = (lo - d_min) & ~3, then shifted by
+            // lo - d_min - kb so that c[j] is candidate lo + j
+            const int kb = (lo_c - a.d_min) & ~3;
+            float c[16];
+            if (esz == 4) {
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const uint4 v = run[lane * 5 + m];
+                    c[4 * m] = __uint_as_float(v.x); c[4 * m + 1] = __uint_as_float(v.y);
+                    c[4 * m + 2] = __uint_as_float(v.z); c[4 * m + 3] = __uint_as_float(v.w);
+                }
+            } else {
+                // 16-bit: the run starts at k0 = kb or kb - 4 (two words earlier)
+                const uint4 v0 = run[lane * 5], v1 = run[lane * 5 + 1], v2 = run[lane * 5 + 2];
+                const uint32_t wa[10] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y};
+                const bool sh = kb != k0_c;
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    const uint32_t wm = sh ? wa[m + 2] : wa[m];
+                    const unsigned short e0 = (unsigned short)(wm & 0xffffu), e1 = (unsigned short)(wm >> 16);
+                    c[2 * m] = a.cdt == CDT_F16 ? __half2float(__ushort_as_half(e0))
+                                                : __bfloat162float(__ushort_as_bfloat16(e0));
+                    c[2 * m + 1] = a.cdt == CDT_F16 ? __half2float(__ushort_as_half(e1))
+                                                    : __bfloat162float(__ushort_as_bfloat16(e1));
+                }
+            }
+            const int off = lo_c - a.d_min - kb;                      // 0 .. 3
+            if (off & 1) {
+#pragma unroll
+                for (int j = 0; j < 15; ++j) c[j] = c[j + 1];
+            }
+            if (off & 2) {
+#pragma unroll
+                for (int j = 0; j < 13; ++j) c[j] = c[j + 2];
+            }
+            // candidates lo .. lo + n - 1 in increasing order: a smaller f
+            // wins, then (equal f) the one nearer to d; invalid candidates
+            // and ZNCC <= 0 never win
+            const float base = (float)lo_c - dv[q];
+            int on = unpack_o(pkv[q], a.d_min);
+            float bf = __int_as_float(0x7f800000), bdist = -1.f;
+#pragma unroll
+            for (int j = 0; j < 11; ++j) {
+                const float rho = 1.f - c[j];
+                if (j < n_c && rho > 0.f) {
+                    float g;
+                    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(g) : "f"(rho));
+                    const float diff = base + (float)j;
+                    const float f = g + a.eta * diff * diff;
+                    const float dist = fabsf(diff);
+                    if (f < bf || (f == bf && dist < bdist)) {
+                        on = lo_c + j;
+                        bf = f;
+                        bdist = dist;
+                    }
+                }
+            }
+            const size_t gi = (size_t)(y0 + warp + 8 * q) * a.W + x0 + lane;
+            a.op[gi] = pack_o(on, a.d_min);
+            if (o_out) o_out[gi] = (int16_t)on;
+        }
+        lo_c = lo_n; n_c = n_n; k0_c = k0_n;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ld_c[i] = ld_n[i];
+    }
+}
+
+
+

@@ -71,6 +71,7 @@ struct PairWs {
     int* rsC;
     int* rsO;
     float* rsB;
+    uint32_t* op;       // refinement on tiles: packed o (aliases rsO)
 };
 
 // Words of the line bitmasks for a W x H map (the largest W x H of a
@@ -140,6 +141,7 @@ PairWs carve(uint8_t* base, size_t npix, int D, int cdt, int maxW, int maxH, int
     w.rsC = reinterpret_cast<int*>(take(npix * 4));
     w.rsO = reinterpret_cast<int*>(take(npix * 4));
     w.rsB = reinterpret_cast<float*>(take(npix * 4));
+    w.op = reinterpret_cast<uint32_t*>(w.rsO);
     return w;
 }
 
@@ -274,8 +276,14 @@ void set_smem_attributes() {
     static bool done = false;
     if (done) return;
     done = true;
-    cudaFuncSetAttribute(k_refine_box1, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_refine_box2o, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_refine_eq12<true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_refine_eq12<false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_refine_eq12<true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_refine_eq12<false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_refine_eq34<true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_refine_eq34<false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_refine_eq34<true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_refine_eq34<false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_soft_final, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_soft_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_vote_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, VOTE_MAX_N * 8);
@@ -405,45 +413,59 @@ void run_postprocess(const stereo_params& p, const int16_t* in, int W, int H, co
     }
 }
 
+// One refinement pass pair per iteration on 32x32 tiles (box radius up to
+// RB_MAX_RS), else the row/column passes of refine.cuh.
+template <int SPAD>
+void launch_refine_tiled(const stereo_params& p, const RefineArgs& a, const int16_t* o_in, float* d_out,
+                         int16_t* o_out, uint8_t* valid, cudaStream_t s) {
+    dim3 g((a.W + RB_T - 1) / RB_T, (a.H + RB_T - 1) / RB_T);
+    const size_t sm = refine_tile_smem(a.rs);
+    for (int k = 0; k < p.smooth_iters; ++k) {
+        const bool last = k == p.smooth_iters - 1;
+        if (k == 0) k_refine_eq12<true, SPAD><<<g, RB_THREADS, sm, s>>>(a, o_in, valid);
+        else k_refine_eq12<false, SPAD><<<g, RB_THREADS, sm, s>>>(a, nullptr, nullptr);
+        // the o after the last iteration only matters when the caller reads it
+        if (!last || o_out)
+            k_refine_eq34<true, SPAD><<<g, RB_THREADS, sm, s>>>(a, last ? d_out : nullptr, last ? o_out : nullptr);
+        else
+            k_refine_eq34<false, SPAD><<<g, RB_THREADS, sm, s>>>(a, d_out, nullptr);
+        counted(2);
+    }
+}
+
 void run_refine(const stereo_params& p, const int16_t* o_in, const void* cost, int cdt,
                 const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, int D, int r,
                 int sampling, const PairWs& w, float* d_out, int16_t* o_out, uint8_t* valid,
                 cudaStream_t s) {
     const int n = W * H;
     const int rs = p.smooth_radius;
-    const bool tiled = rs <= RT_MAX_RS;
+    const bool tiled = rs <= RB_MAX_RS;
     if (!tiled || p.smooth_iters == 0) {
         k_refine_init<<<(n + 255) / 256, 256, 0, s>>>(o_in, n, w.o, w.dprev, d_out, valid);
         counted();
+        if (p.smooth_iters == 0) {
+            if (o_out) cudaMemcpyAsync(o_out, w.o, (size_t)n * 2, cudaMemcpyDeviceToDevice, s);
+            return;
+        }
+    }
+    if (tiled) {
+        RefineArgs a{W, H, rs, d_min, D, p.alpha, p.eta, p.refine_search, cost, cdt, gl, gr, r, sampling,
+                     w.op, w.dprev, w.dt, w.b, w.cnt};
+        if (rb_spad(rs) == 16) launch_refine_tiled<16>(p, a, o_in, d_out, o_out, valid, s);
+        else launch_refine_tiled<32>(p, a, o_in, d_out, o_out, valid, s);
+        return;
     }
     const int bx = 128;
     dim3 gr2((W + bx - 1) / bx, H);
     const size_t rsmem = (size_t)((bx + 2 * rs + 1) & ~1) * 2 + (size_t)(bx + 2 * rs) * 4;
-    dim3 rg((W + RT - 1) / RT, (H + RT - 1) / RT);
     for (int k = 0; k < p.smooth_iters; ++k) {
         float* dk = k == p.smooth_iters - 1 ? d_out : nullptr;
-        if (tiled) {
-            const int16_t* osrc = k == 0 ? o_in : w.o;
-            k_refine_box1<<<rg, RT_THREADS, refine_box1_smem(rs), s>>>(osrc, k == 0 ? nullptr : w.dprev, W, H,
-                                                                       rs, p.alpha, d_min, w.dt, w.b, w.cnt);
-            counted();
-            // the o after the last iteration only matters when the caller reads it
-            int16_t* odst = (k == p.smooth_iters - 1 && !o_out) ? nullptr : w.o;
-            k_refine_box2o<<<rg, RT_THREADS, refine_box2_smem(rs), s>>>(
-                osrc, odst, w.dprev, w.dt, w.b, w.cnt, W, H, rs, dk, k == 0 ? valid : nullptr, p.eta,
-                p.refine_search, d_min, D, cost, cdt, gl, gr, r, sampling);
-            counted();
-        } else {
-            k_refine_rows<<<gr2, bx, rsmem, s>>>(w.o, nullptr, W, H, rs, w.rsC, w.rsO, nullptr);
-            counted();
-            k_refine_cols1<<<gr2, bx, 0, s>>>(w.o, w.dprev, w.rsC, w.rsO, W, H, rs, p.alpha, w.dt, w.b);
-            counted();
-            k_refine_rows<<<gr2, bx, rsmem, s>>>(w.o, w.b, W, H, rs, nullptr, nullptr, w.rsB);
-            counted();
-            k_refine_cols2<<<gr2, bx, 0, s>>>(w.o, w.dprev, w.dt, w.rsC, w.rsB, W, H, rs, p.eta,
-                                              p.refine_search, d_min, D, cost, cdt, gl, gr, r, sampling, dk);
-            counted();
-        }
+        k_refine_rows<<<gr2, bx, rsmem, s>>>(w.o, nullptr, W, H, rs, w.rsC, w.rsO, nullptr);
+        k_refine_cols1<<<gr2, bx, 0, s>>>(w.o, w.dprev, w.rsC, w.rsO, W, H, rs, p.alpha, w.dt, w.b);
+        k_refine_rows<<<gr2, bx, rsmem, s>>>(w.o, w.b, W, H, rs, nullptr, nullptr, w.rsB);
+        k_refine_cols2<<<gr2, bx, 0, s>>>(w.o, w.dprev, w.dt, w.rsC, w.rsB, W, H, rs, p.eta,
+                                          p.refine_search, d_min, D, cost, cdt, gl, gr, r, sampling, dk);
+        counted(4);
     }
     if (o_out) cudaMemcpyAsync(o_out, w.o, (size_t)n * 2, cudaMemcpyDeviceToDevice, s);
 }
