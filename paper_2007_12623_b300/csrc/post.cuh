@@ -207,17 +207,43 @@ __global__ void __launch_bounds__(256) k_outlier_masks(const int16_t* __restrict
     out[pix] = keep ? (int16_t)v : (int16_t)ST_INVALID;
 }
 
+// The same test for radius <= 32 (the paper's radii): per family, the three
+// words around the pixel's position give the 32 edge bits from pos (forward
+// ray) and the 32 before pos (backward ray) with one funnel shift each;
+// 32-bit word offsets (a mask buffer holds fewer than 2^32 words).
+__global__ void __launch_bounds__(256) k_outlier_masks32(const int16_t* __restrict__ in, LineMasks m,
+                                                         int radius, int16_t* __restrict__ out) {
+    const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= m.W * m.H) return;
+    const int y = pix / m.W, x = pix - y * m.W;
+    const int v = in[pix];
+    bool keep = radius == 0;
+    if (v != ST_INVALID && radius > 0) {
+        const uint32_t need = radius >= 32 ? 0xffffffffu : ((1u << radius) - 1u);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            int line, pos;
+            fam_coords(m, f, x, y, line, pos);
+            const uint32_t L = (uint32_t)m.lines(f);
+            const uint32_t* w = m.words + (uint32_t)m.off[f] + (uint32_t)((pos >> 5) + LM_PAD_LO - 1) * L + line;
+            const uint32_t a0 = __ldg(w), a1 = __ldg(w + L), a2 = __ldg(w + 2 * L);
+            const int o = pos & 31;
+            const uint32_t fw = __funnelshift_r(a1, a2, o);          // edge bits pos .. pos + 31
+            const uint32_t bw = __funnelshift_r(a0, a1, o);          // edge bits pos - 32 .. pos - 1
+            keep |= (fw & need) == need;
+            keep |= (bw >> (32 - radius)) == need;
+        }
+    }
+    out[pix] = keep ? (int16_t)v : (int16_t)ST_INVALID;
+}
+
 // First hole-filling method (radius <= 63) from valid masks: the nearest
 // valid pixel ahead is the lowest set bit of positions pos+1 .. pos+R, the
-// one behind the highest set bit of positions pos-R .. pos-1.
-__global__ void __launch_bounds__(256) k_fill_radial_masks(const int16_t* __restrict__ in, LineMasks m,
-                                                           int radius, int min_dirs,
-                                                           int16_t* __restrict__ out) {
-    const long pix = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pix >= (long)m.W * m.H) return;
-    const int x = (int)(pix % m.W), y = (int)(pix / m.W);
-    const int v = in[pix];
-    if (v != ST_INVALID) { out[pix] = (int16_t)v; return; }
+// one behind the highest set bit of positions pos-R .. pos-1.  Returns the
+// output value of pixel (x, y) whose input value is v.
+__device__ __forceinline__ int radial_fill_at(const int16_t* __restrict__ in, const LineMasks& m, int radius,
+                                              int min_dirs, int x, int y, int v) {
+    if (v != ST_INVALID) return v;
     const uint64_t msk = low_bits(radius);
     int num = 0, den = 0, found = 0;
 #pragma unroll
@@ -244,68 +270,90 @@ __global__ void __launch_bounds__(256) k_fill_radial_masks(const int16_t* __rest
             ++found;
         }
     }
-    out[pix] = (found >= min_dirs && den > 0) ? (int16_t)round_half_up_i(num, den) : (int16_t)ST_INVALID;
+    return (found >= min_dirs && den > 0) ? round_half_up_i(num, den) : ST_INVALID;
 }
 
-// Tiled build of the same line bitmasks: block (bc, br) stages image columns
-// [32 bc, 32 bc + 33) x rows [32 br - 32, 32 br + 64) and writes, with one
-// warp ballot per word: the row and column words of its own 32x32 tile, the
-// diagonal words whose first pixel (position 32 bc) lies in rows
-// [32 br, 32 br + 32), and the anti-diagonal words likewise.  Block rows run
-// from -1 to H/32 so that every word with a pixel inside the image is
-// written; the caller zeroes the buffer first, which leaves the words
-// wholly outside the image at 0.
-constexpr int LM_ROWS = 96, LM_COLS = 33;
+__global__ void __launch_bounds__(256) k_fill_radial_masks(const int16_t* __restrict__ in, LineMasks m,
+                                                           int radius, int min_dirs,
+                                                           int16_t* __restrict__ out) {
+    const long pix = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= (long)m.W * m.H) return;
+    const int x = (int)(pix % m.W), y = (int)(pix / m.W);
+    out[pix] = (int16_t)radial_fill_at(in, m, radius, min_dirs, x, y, in[pix]);
+}
+
+// Tiled build of the line bitmasks: block (bc, br) stages image columns
+// [32 bc, 32 bc + 33) x rows [32 br - 1, 32 br + 64) and writes, one warp
+// ballot per word: the row and column words of its 32x32 tile, the
+// diagonal words whose FIRST pixel (position 32 bc) lies in rows
+// [32 br, 32 br + 32), and the anti-diagonal words whose LAST pixel
+// (position 32 bc + 31) lies in those rows -- both run down into the next
+// tile row, so every word a block writes is inside its staged rows.  Block
+// rows run from -1 so that every word with a pixel inside the image is
+// written; the caller zeroes the buffer first, which leaves the words wholly
+// outside the image at 0.  Each warp builds the words of one family.  mode
+// 0: valid bits; mode 1: smooth-edge bits, |next - v| <= ithr (the largest
+// integer below the threshold, disparities being integers).
+constexpr int LM_ROWS = 65, LM_COLS = 34;
 
 __global__ void __launch_bounds__(256) k_line_masks_tiled(const int16_t* __restrict__ in, LineMasks m,
-                                                          int mode, float thresh) {
-    __shared__ int16_t t[LM_ROWS][LM_COLS + 1];
+                                                          int mode, int ithr) {
+    __shared__ __align__(4) int16_t t[LM_ROWS][LM_COLS];
     const int bc = blockIdx.x, br = (int)blockIdx.y - 1;
-    const int X0 = 32 * bc, Y0 = 32 * br - 32;
-    for (int i = threadIdx.x; i < LM_ROWS * LM_COLS; i += 256) {
-        const int ly = i / LM_COLS, lx = i % LM_COLS;
-        const int gx = X0 + lx, gy = Y0 + ly;
-        t[ly][lx] = (gx >= 0 && gx < m.W && gy >= 0 && gy < m.H) ? in[(size_t)gy * m.W + gx]
-                                                                  : (int16_t)ST_INVALID;
+    const int X0 = 32 * bc, Y0 = 32 * br - 1;            // staged row 0 is image row Y0
+    const bool pairs = (m.W & 1) == 0 && (reinterpret_cast<uintptr_t>(in) & 3) == 0;
+    for (int i = threadIdx.x; i < LM_ROWS * (LM_COLS / 2); i += 256) {
+        const int ly = i / (LM_COLS / 2), cp = i % (LM_COLS / 2);
+        const int gx = X0 + 2 * cp, gy = Y0 + ly;
+        uint32_t v = 0x80008000u;                        // two ST_INVALID
+        if (gy >= 0 && gy < m.H) {
+            const int16_t* row = in + (size_t)gy * m.W;
+            if (pairs && gx + 1 < m.W) {
+                v = __ldg(reinterpret_cast<const uint32_t*>(row + gx));
+            } else {
+                const uint32_t a = gx < m.W ? (uint16_t)row[gx] : 0x8000u;
+                const uint32_t b = gx + 1 < m.W ? (uint16_t)row[gx + 1] : 0x8000u;
+                v = a | (b << 16);
+            }
+        }
+        *reinterpret_cast<uint32_t*>(&t[ly][2 * cp]) = v;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // predicate of staged pixel (lx, ly) for family f; out-of-image pixels are invalid
-    auto pred = [&](int f, int lx, int ly) -> bool {
-        const int v = t[ly][lx];
-        if (mode == 0) return v != ST_INVALID;
-        int dx, dy;
-        fam_dir(f, dx, dy);
-        const int q = t[ly + dy][lx + dx];
-        return v != ST_INVALID && q != ST_INVALID && fabsf((float)(q - v)) < thresh;
-    };
-#pragma unroll
-    for (int f = 0; f < 4; ++f)
-    for (int i = warp; i < 32; i += 8) {
-        int lx, ly, line, wi;
-        bool ok = true;
-        if (f == 0) {                 // row 32 br + i, columns 32 bc + lane
-            ly = 32 + i; lx = lane;
+    const int f = warp >> 1;                             // two warps per family
+    const uint32_t L = (uint32_t)m.lines(f);
+    uint32_t* wf = m.words + (uint32_t)m.off[f];
+#pragma unroll 4
+    for (int it = 0; it < 16; ++it) {
+        const int i = (warp & 1) * 16 + it;
+        int ly, lx, qy, qx, line, wi;
+        bool ok;
+        if (f == 0) {                 // row 32 br + i, positions 32 bc + lane
+            ly = i + 1; lx = lane; qy = ly; qx = lx + 1;
             line = 32 * br + i; wi = bc;
             ok = br >= 0 && line < m.H;
-        } else if (f == 1) {          // column 32 bc + i, rows 32 br + lane
-            ly = 32 + lane; lx = i;
+        } else if (f == 1) {          // column 32 bc + i, positions 32 br + lane
+            ly = lane + 1; lx = i; qy = ly + 1; qx = lx;
             line = X0 + i; wi = br;
             ok = br >= 0 && 32 * br < m.H && line < m.W;
-        } else if (f == 2) {          // first pixel row 32 br + i, then (+1, +1)
-            ly = 32 + i + lane; lx = lane;
+        } else if (f == 2) {          // first pixel (32 bc, 32 br + i), then (+1, +1)
+            ly = i + lane + 1; lx = lane; qy = ly + 1; qx = lx + 1;
             line = X0 - (32 * br + i) + m.H - 1; wi = bc;
-            ok = line >= 0 && line < m.lines(2);
-        } else {                      // first pixel row 32 br + i, then (+1, -1)
-            ly = 32 + i - lane; lx = lane;
-            line = X0 + 32 * br + i; wi = bc;
-            ok = line >= 0 && line < m.lines(3);
+            ok = line >= 0 && line < m.W + m.H - 1;
+        } else {                      // last pixel (32 bc + 31, 32 br + i), pixel j at row 32 br + i + 31 - j
+            ly = i + 32 - lane; lx = lane; qy = ly - 1; qx = lx + 1;
+            line = X0 + 32 * br + i + 31; wi = bc;
+            ok = line >= 0 && line < m.W + m.H - 1;
         }
         if (!ok) continue;            // warp-uniform
-        const int gx = X0 + lx, gy = Y0 + ly;
-        const bool inside = gx < m.W && gy >= 0 && gy < m.H;
-        const bool bit = inside && pred(f, lx, ly);
+        const int v = t[ly][lx];
+        bool bit = v != ST_INVALID;
+        if (mode == 1) {
+            const int q = t[qy][qx];
+            const int dlt = q - v;
+            bit = bit && q != ST_INVALID && dlt <= ithr && -dlt <= ithr;
+        }
         const uint32_t word = __ballot_sync(0xffffffffu, bit);
-        if (lane == 0) m.words[m.index(f, line, wi)] = word;
+        if (lane == 0) wf[(uint32_t)(wi + LM_PAD_LO) * L + (uint32_t)line] = word;
     }
 }

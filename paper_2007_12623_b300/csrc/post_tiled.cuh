@@ -2,6 +2,7 @@
 // prefix sums.
 #pragma once
 #include "common.cuh"
+#include "post.cuh"
 
 constexpr int PT_THREADS = 256;
 constexpr int PT_MAX_HALO = 56;   // largest disc radius

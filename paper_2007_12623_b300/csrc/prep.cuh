@@ -13,12 +13,25 @@ struct PrepOut {
     int ucol0;         // image are {0, 0, 0, 0}
 };
 
-// Window sums of one image (FULL sampling): S = sum I, B = N sum I^2 - S^2
-// (exact in uint32 arithmetic, 0 <= B < 2^32).  One block computes a 32x32
-// tile with separable sums in shared memory and writes the float image and
-// the statistics; blocks of the first tile column also zero the padding
-// columns.  Also clears the winner-take-all key maps when `key_clear` is
-// given (2 W H words).
+// Input image of the preparation kernel: 8-bit gray, or interleaved RGB
+// converted on the fly with (77 R + 150 G + 29 B + 128) >> 8; `gray`, when
+// given, receives the dense (row stride W) gray copy.
+struct PrepIn {
+    const uint8_t* img;
+    int pitch;         // bytes per row
+    int rgb;
+    uint8_t* gray;
+};
+
+// Window sums of both images of a pair (blockIdx.z = 0 left, 1 right):
+// S = sum I, B = N sum I^2 - S^2 (exact in uint32 arithmetic, 0 <= B < 2^32).
+// One block computes a 32x32 tile with separable sums in shared memory and
+// writes the float image and the statistics; the padding columns of its
+// tile row are shared out among the blocks of that row.  The left image's
+// blocks also clear the winner-take-all key maps (key_clear, 2 W H words)
+// and, in tiles that touch the image border, set the cost slices of the
+// pixels whose window leaves the image to NaN (the cost kernel never visits
+// them: no candidate is valid there).
 constexpr int PT = 32;
 constexpr int PMAXR = 7;
 constexpr int PSPAN = PT + 2 * PMAXR;
@@ -28,28 +41,43 @@ constexpr int PSPAN = PT + 2 * PMAXR;
 // even, centre included, N = ((2r+1)^2 + 1) / 2 samples; the row pass keeps
 // the sums over even and over odd dx apart and the column pass takes the
 // even-dx sum on rows with even dy and the odd-dx sum on the others.
-template <bool CB>
-__global__ void __launch_bounds__(256) k_prep(const uint8_t* __restrict__ img, int W, int H, int r,
-                                              PrepOut out, uint32_t* __restrict__ key_clear) {
+template <bool CB, int R>
+__global__ void __launch_bounds__(256) k_prep(PrepIn in0, PrepIn in1, int W, int H, PrepOut out0, PrepOut out1,
+                                              uint32_t* __restrict__ key_clear, void* __restrict__ cost, int cdt,
+                                              int cs) {
     constexpr int NP = CB ? 2 : 1;
-    __shared__ uint16_t t[PSPAN][PSPAN + 1];
-    __shared__ uint32_t rs[NP][PSPAN][PT + 1];
-    __shared__ uint32_t rss[NP][PSPAN][PT + 1];
+    constexpr int SPAN = PT + 2 * R;
+    __shared__ uint16_t t[SPAN][SPAN + 1];
+    __shared__ uint32_t rs[NP][SPAN][PT + 1];
+    __shared__ uint32_t rss[NP][SPAN][PT + 1];
+    const bool left = blockIdx.z == 0;
+    const PrepIn in = left ? in0 : in1;
+    const PrepOut out = left ? out0 : out1;
     const int x0 = blockIdx.x * PT, y0 = blockIdx.y * PT;
-    const int span = PT + 2 * r;
     const int tid = threadIdx.x;
-    for (int i = tid; i < span * span; i += 256) {
-        const int ly = i / span, lx = i % span;
-        const int gx = x0 - r + lx, gy = y0 - r + ly;
-        t[ly][lx] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? img[(size_t)gy * W + gx] : 0;
+    for (int i = tid; i < SPAN * SPAN; i += 256) {
+        const int ly = i / SPAN, lx = i % SPAN;
+        const int gx = x0 - R + lx, gy = y0 - R + ly;
+        uint32_t v = 0;
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+            const uint8_t* p = in.img + (size_t)gy * in.pitch;
+            if (in.rgb) {
+                p += 3 * gx;
+                v = (77u * p[0] + 150u * p[1] + 29u * p[2] + 128u) >> 8;
+            } else {
+                v = p[gx];
+            }
+        }
+        t[ly][lx] = (uint16_t)v;
     }
     __syncthreads();
-    for (int i = tid; i < span * PT; i += 256) {
+    for (int i = tid; i < SPAN * PT; i += 256) {
         const int ly = i / PT, lx = i % PT;
         uint32_t s0 = 0, ss0 = 0, s1 = 0, ss1 = 0;
-        for (int k = 0; k <= 2 * r; ++k) {              // dx = k - r
+#pragma unroll
+        for (int k = 0; k <= 2 * R; ++k) {              // dx = k - R
             const uint32_t v = t[ly][lx + k];
-            if (CB && ((k - r) & 1)) { s1 += v; ss1 += v * v; }
+            if (CB && ((k - R) & 1)) { s1 += v; ss1 += v * v; }
             else { s0 += v; ss0 += v * v; }
         }
         rs[0][ly][lx] = s0;
@@ -60,20 +88,23 @@ __global__ void __launch_bounds__(256) k_prep(const uint8_t* __restrict__ img, i
         }
     }
     __syncthreads();
-    const uint32_t N = (uint32_t)(CB ? ((2 * r + 1) * (2 * r + 1) + 1) / 2 : (2 * r + 1) * (2 * r + 1));
+    const uint32_t N = (uint32_t)(CB ? ((2 * R + 1) * (2 * R + 1) + 1) / 2 : (2 * R + 1) * (2 * R + 1));
     for (int i = tid; i < PT * PT; i += 256) {
         const int ly = i / PT, lx = i % PT;
         const int gx = x0 + lx, gy = y0 + ly;
         if (gx >= W || gy >= H) continue;
         const size_t gi = (size_t)gy * W + gx;
-        if (key_clear) { key_clear[gi] = 0u; key_clear[(size_t)W * H + gi] = 0u; }
-        out.img[(size_t)gy * out.stride + out.col0 + gx] = (float)t[ly + r][lx + r];
+        if (left && key_clear) { key_clear[gi] = 0u; key_clear[(size_t)W * H + gi] = 0u; }
+        const uint32_t c = t[ly + R][lx + R];
+        if (in.gray) in.gray[gi] = (uint8_t)c;
+        out.img[(size_t)gy * out.stride + out.col0 + gx] = (float)c;
         uint32_t s = 0, B = 0;
-        const bool interior = gx >= r && gx < W - r && gy >= r && gy < H - r;
+        const bool interior = gx >= R && gx < W - R && gy >= R && gy < H - R;
         if (interior) {
             uint32_t ss = 0;
-            for (int k = 0; k <= 2 * r; ++k) {          // dy = k - r: same parity of dx
-                const int q = CB ? ((k - r) & 1) : 0;
+#pragma unroll
+            for (int k = 0; k <= 2 * R; ++k) {          // dy = k - R: same parity of dx
+                const int q = CB ? ((k - R) & 1) : 0;
                 s += rs[q][ly + k][lx];
                 ss += rss[q][ly + k][lx];
             }
@@ -90,35 +121,48 @@ __global__ void __launch_bounds__(256) k_prep(const uint8_t* __restrict__ img, i
             out.ustats[(size_t)gy * out.ustride + out.ucol0 + gx] =
                 make_float4((float)(s & ~0xffu), (float)(s & 0xffu), is, interior ? 1.f : 0.f);
     }
-    if (blockIdx.x == 0) {
-        const int npad = out.stride - W;                      // image padding columns
-        for (int i = tid; i < PT * npad; i += 256) {
-            const int gy = y0 + i / npad, m = i % npad;
-            if (gy >= H) break;
-            const int col = m < out.col0 ? m : W + m;
-            out.img[(size_t)gy * out.stride + col] = 0.f;
+    // padding columns of rows y0 .. y0 + 31, shared among the tile row's blocks
+    const int rows = min(PT, H - y0);
+    const int npad = out.stride - W;
+    for (int i = blockIdx.x * 256 + tid; i < rows * npad; i += gridDim.x * 256) {
+        const int gy = y0 + i / npad, m = i % npad;
+        out.img[(size_t)gy * out.stride + (m < out.col0 ? m : W + m)] = 0.f;
+    }
+    if (out.ustats) {
+        const int upad = out.ustride - W;
+        for (int i = blockIdx.x * 256 + tid; i < rows * upad; i += gridDim.x * 256) {
+            const int gy = y0 + i / upad, m = i % upad;
+            out.ustats[(size_t)gy * out.ustride + (m < out.ucol0 ? m : W + m)] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (out.ustats) {
-            const int upad = out.ustride - W;
-            for (int i = tid; i < PT * upad; i += 256) {
-                const int gy = y0 + i / upad, m = i % upad;
-                if (gy >= H) break;
-                const int col = m < out.ucol0 ? m : W + m;
-                out.ustats[(size_t)gy * out.ustride + col] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+    }
+    if (left && cost && (x0 < R || x0 + PT > W - R || y0 < R || y0 + PT > H - R)) {
+        const int warp = tid >> 5, lane = tid & 31;
+        const int esz = cdt == CDT_F32 ? 4 : 2;
+        const int nvec = cs * esz / 16;                  // 16-byte chunks per pixel (cs is a multiple of 8)
+        const uint32_t nan = cdt == CDT_F32 ? 0x7fc00000u : (cdt == CDT_F16 ? 0x7e007e00u : 0x7fc07fc0u);
+        const uint4 nv = make_uint4(nan, nan, nan, nan);
+        for (int p = warp; p < PT * PT; p += 8) {
+            const int gx = x0 + (p & (PT - 1)), gy = y0 + p / PT;
+            if (gx >= W || gy >= H) continue;
+            if (gx >= R && gx < W - R && gy >= R && gy < H - R) continue;
+            uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<char*>(cost) + ((size_t)gy * W + gx) * cs * esz);
+            for (int c = lane; c < nvec; c += 32) dst[c] = nv;
         }
     }
 }
 
-
 // Cost slices of the pixels whose window leaves the image (the cost kernel
-// never visits them) are set to NaN: no candidate is valid there.
+// never visits them) are set to NaN: no candidate is valid there.  One warp
+// per border pixel, 16-byte stores.
 __global__ void k_cost_border_nan(void* __restrict__ cost, int cdt, int W, int H, int r, int cs) {
     const bool all = W <= 2 * r || H <= 2 * r;             // every pixel is a border pixel
     const int nb = all ? W * H : 2 * r * W + 2 * r * (H - 2 * r);
-    const long total = (long)nb * cs;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-        const int b = (int)(e / cs), k = (int)(e % cs);
+    const int esz = cdt == CDT_F32 ? 4 : 2;
+    const int nvec = cs * esz / 16;
+    const uint32_t nan = cdt == CDT_F32 ? 0x7fc00000u : (cdt == CDT_F16 ? 0x7e007e00u : 0x7fc07fc0u);
+    const uint4 nv = make_uint4(nan, nan, nan, nan);
+    const int lane = threadIdx.x & 31;
+    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += (gridDim.x * blockDim.x) >> 5) {
         int x, y;
         if (all) {
             x = b % W;
@@ -133,9 +177,8 @@ __global__ void k_cost_border_nan(void* __restrict__ cost, int cdt, int W, int H
             const int c = m % (2 * r);
             x = c < r ? c : W - 2 * r + c;
         }
-        const size_t i = ((size_t)y * W + x) * cs + k;
-        if (cdt == CDT_F32) reinterpret_cast<float*>(cost)[i] = __int_as_float(0x7fc00000);
-        else reinterpret_cast<uint16_t*>(cost)[i] = cdt == CDT_F16 ? (uint16_t)0x7e00 : (uint16_t)0x7fc0;
+        uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<char*>(cost) + ((size_t)y * W + x) * cs * esz);
+        for (int c = lane; c < nvec; c += 32) dst[c] = nv;
     }
 }
 

@@ -305,28 +305,45 @@ void prep_layouts(int W, int d_min, int D, int K, const PairWs& w, PrepOut& pl, 
     pr.ustride = pr.ucol0 + W + std::max(0, -d_min) + 48;
 }
 
+// Window statistics of both images of a pair in one launch (k_prep), which
+// also clears the key maps and writes the NaN border slices of `cost`.
+template <bool CB>
+void launch_prep_cb(int r, const PrepIn& inL, const PrepIn& inR, int W, int H, const PrepOut& pl,
+                    const PrepOut& pr, uint32_t* keys, void* cost, int cdt, int cs, cudaStream_t s) {
+    dim3 g((W + PT - 1) / PT, (H + PT - 1) / PT, 2);
+    switch (r) {
+        case 1: k_prep<CB, 1><<<g, 256, 0, s>>>(inL, inR, W, H, pl, pr, keys, cost, cdt, cs); break;
+        case 2: k_prep<CB, 2><<<g, 256, 0, s>>>(inL, inR, W, H, pl, pr, keys, cost, cdt, cs); break;
+        case 3: k_prep<CB, 3><<<g, 256, 0, s>>>(inL, inR, W, H, pl, pr, keys, cost, cdt, cs); break;
+        case 4: k_prep<CB, 4><<<g, 256, 0, s>>>(inL, inR, W, H, pl, pr, keys, cost, cdt, cs); break;
+        case 5: k_prep<CB, 5><<<g, 256, 0, s>>>(inL, inR, W, H, pl, pr, keys, cost, cdt, cs); break;
+        case 6: k_prep<CB, 6><<<g, 256, 0, s>>>(inL, inR, W, H, pl, pr, keys, cost, cdt, cs); break;
+        case 7: k_prep<CB, 7><<<g, 256, 0, s>>>(inL, inR, W, H, pl, pr, keys, cost, cdt, cs); break;
+        default: return;
+    }
+    counted();
+}
+
+void launch_prep(int r, int sampling, const PrepIn& inL, const PrepIn& inR, int W, int H, const PrepOut& pl,
+                 const PrepOut& pr, uint32_t* keys, void* cost, int cdt, int D, cudaStream_t s) {
+    if (sampling == STEREO_SAMPLE_CHESSBOARD)
+        launch_prep_cb<true>(r, inL, inR, W, H, pl, pr, keys, cost, cdt, cost_stride(D), s);
+    else
+        launch_prep_cb<false>(r, inL, inR, W, H, pl, pr, keys, cost, cdt, cost_stride(D), s);
+}
+
+// inL/inR (optional): the caller's raw images (RGB or pitched gray) that the
+// preparation kernel converts into the dense gray copies gl/gr on the way.
 void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, int D, int r,
                int sampling, int cdt, int lr_thresh, const PairWs& w, void* cost,
                int16_t* disp_left, int16_t* disp_right, float* disp_sub, int16_t* disp_lr,
-               cudaStream_t s, cudaEvent_t* ev = nullptr) {
+               cudaStream_t s, cudaEvent_t* ev = nullptr, const PrepIn* inL = nullptr,
+               const PrepIn* inR = nullptr) {
     const int K = sampling == STEREO_SAMPLE_CHESSBOARD ? 2 : pick_k(D);
     PrepOut pl, pr;
     prep_layouts(W, d_min, D, K, w, pl, pr);
-    dim3 sg((W + PT - 1) / PT, (H + PT - 1) / PT);
-    if (sampling == STEREO_SAMPLE_CHESSBOARD) {
-        k_prep<true><<<sg, 256, 0, s>>>(gl, W, H, r, pl, w.keys);
-        k_prep<true><<<sg, 256, 0, s>>>(gr, W, H, r, pr, nullptr);
-    } else {
-        k_prep<false><<<sg, 256, 0, s>>>(gl, W, H, r, pl, w.keys);
-        k_prep<false><<<sg, 256, 0, s>>>(gr, W, H, r, pr, nullptr);
-    }
-    counted(2);
-    if (cost) {
-        const long nb = (W <= 2 * r || H <= 2 * r) ? (long)W * H : 2L * r * W + 2L * r * (H - 2 * r);
-        const int blocks = (int)std::min<long>(4096, (nb * cost_stride(D) + 255) / 256);
-        k_cost_border_nan<<<std::max(1, blocks), 256, 0, s>>>(cost, cdt, W, H, r, cost_stride(D));
-        counted();
-    }
+    const PrepIn dl{gl, W, 0, nullptr}, dr{gr, W, 0, nullptr};
+    launch_prep(r, sampling, inL ? *inL : dl, inR ? *inR : dr, W, H, pl, pr, w.keys, cost, cdt, D, s);
     if (ev) cudaEventRecord(ev[2], s);
     CostArgs a{pl.img, pl.stride, pl.col0, pr.img, pr.stride, pr.col0, w.lstats, w.ustats,
                pr.ustride, pr.ucol0, w.keys, w.keys + (size_t)W * H, cost, cdt, W, H, d_min, D, 0};
@@ -349,7 +366,9 @@ void zero_masks(uint32_t* words, int W, int H, cudaStream_t s) {
 
 void build_masks(const int16_t* in, int W, int H, int mode, float thresh, uint32_t* words, cudaStream_t s) {
     LineMasks m = make_line_masks(words, W, H);
-    k_line_masks_tiled<<<dim3((W + 31) / 32, (H + 31) / 32 + 2), 256, 0, s>>>(in, m, mode, thresh);
+    // integer disparities: |d| < thresh <=> |d| <= ceil(thresh) - 1
+    const int ithr = mode == 1 ? (int)std::min(ceilf(thresh), 65536.f) - 1 : 0;
+    k_line_masks_tiled<<<dim3((W + 31) / 32, (H + 31) / 32 + 1), 256, 0, s>>>(in, m, mode, ithr);
     counted();
 }
 
@@ -358,7 +377,11 @@ void build_masks(const int16_t* in, int W, int H, int mode, float thresh, uint32
 void run_outlier(const int16_t* in, int W, int H, int radius, float thresh, uint32_t* masks, int16_t* out,
                  cudaStream_t s) {
     const long npix = (long)W * H;
-    if (radius <= 64) {
+    if (radius <= 32) {
+        build_masks(in, W, H, 1, thresh, masks, s);
+        k_outlier_masks32<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(in, make_line_masks(masks, W, H),
+                                                                         radius, out);
+    } else if (radius <= 64) {
         build_masks(in, W, H, 1, thresh, masks, s);
         k_outlier_masks<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(in, make_line_masks(masks, W, H),
                                                                        radius, out);
@@ -388,9 +411,10 @@ void run_fill_disc(const int16_t* in, int W, int H, int radius, int min_count, c
                    cudaStream_t s) {
     uint32_t* S = reinterpret_cast<uint32_t*>(w.rsC);
     k_row_prefix<<<H, DISC_PREFIX_THREADS, 0, s>>>(in, W, S);
+    counted();
     k_fill_disc_prefix<<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, s>>>(in, S, W, H, radius, min_count,
                                                                               out);
-    counted(2);
+    counted();
 }
 
 void run_postprocess(const stereo_params& p, const int16_t* in, int W, int H, const PairWs& w,
@@ -532,30 +556,18 @@ static void enqueue_match(stereo_handle* h, const stereo_pair* pr, int slot, cud
     const int cdt = h->p.cost_dtype;
     PairWs w = carve(h->ws + (size_t)slot * h->pair_bytes, (size_t)W * H, h->p.num_disp, cdt,
                      h->p.max_width, h->p.max_height);
-    const uint8_t* gl = pr->left;
-    const uint8_t* gr = pr->right;
-    dim3 g((W + 127) / 128, H);
+    // RGB or pitched gray input is converted inside the preparation kernel
+    const bool conv = pr->channels == 3 || pr->pitch != W;
+    const uint8_t* gl = conv ? w.gl : pr->left;
+    const uint8_t* gr = conv ? w.gr : pr->right;
+    const PrepIn inL{pr->left, pr->pitch, pr->channels == 3, conv ? w.gl : nullptr};
+    const PrepIn inR{pr->right, pr->pitch, pr->channels == 3, conv ? w.gr : nullptr};
     if (timed) mark(h, 0, s);
-    if (pr->channels == 3) {
-        k_gray<<<g, 128, 0, s>>>(pr->left, W, H, pr->pitch, w.gl);
-        counted();
-        k_gray<<<g, 128, 0, s>>>(pr->right, W, H, pr->pitch, w.gr);
-        counted();
-        gl = w.gl;
-        gr = w.gr;
-    } else if (pr->pitch != W) {
-        k_copy_pitched<<<g, 128, 0, s>>>(pr->left, W, H, pr->pitch, w.gl);
-        counted();
-        k_copy_pitched<<<g, 128, 0, s>>>(pr->right, W, H, pr->pitch, w.gr);
-        counted();
-        gl = w.gl;
-        gr = w.gr;
-    }
     if (timed) mark(h, 1, s);
     int16_t* wta = pr->disp_wta ? pr->disp_wta : w.wta;
     void* cost = cdt != CDT_NONE ? w.cost : nullptr;
     run_match(gl, gr, W, H, d_min, D, r, h->p.sampling, cdt, h->p.lr_thresh, w, cost, wta, nullptr,
-              pr->disp_sub, w.lr, s, timed && h->ev_ready ? h->ev : nullptr);
+              pr->disp_sub, w.lr, s, timed && h->ev_ready ? h->ev : nullptr, &inL, &inR);
     if (pr->disp_lr) cudaMemcpyAsync(pr->disp_lr, w.lr, (size_t)W * H * 2, cudaMemcpyDeviceToDevice, s);
     if (timed) mark(h, 4, s);
     int16_t* post = pr->disp_post ? pr->disp_post : w.post;
@@ -1021,36 +1033,19 @@ static void enqueue_batched(stereo_handle* h, const stereo_pair* pairs, int n, c
         q.gl = q.converted ? q.w.gl : pr->left;
         q.gr = q.converted ? q.w.gr : pr->right;
     }
-    auto input = [&](int i, cudaStream_t st) {
-        const stereo_pair* pr = &pairs[i];
-        const Pair& q = P[i];
-        if (!q.converted) return;
-        dim3 g((q.W + 127) / 128, q.H);
-        if (pr->channels == 3) {
-            k_gray<<<g, 128, 0, st>>>(pr->left, q.W, q.H, pr->pitch, q.w.gl);
-            k_gray<<<g, 128, 0, st>>>(pr->right, q.W, q.H, pr->pitch, q.w.gr);
-        } else {
-            k_copy_pitched<<<g, 128, 0, st>>>(pr->left, q.W, q.H, pr->pitch, q.w.gl);
-            k_copy_pitched<<<g, 128, 0, st>>>(pr->right, q.W, q.H, pr->pitch, q.w.gr);
-        }
-        counted(2);
-    };
+    // gray conversion (RGB or pitched input), statistics, key clearing and
+    // the NaN border slices: one preparation launch per pair
+    auto input = [&](int, cudaStream_t) {};
     auto stats = [&](int i, cudaStream_t st) {
+        const stereo_pair* pr = &pairs[i];
         const Pair& q = P[i];
         PairWs w = q.w;
         PrepOut pl, prr;
         prep_layouts(q.W, q.d_min, q.D, K, w, pl, prr);
-        dim3 sg((q.W + PT - 1) / PT, (q.H + PT - 1) / PT);
-        k_prep<false><<<sg, 256, 0, st>>>(q.gl, q.W, q.H, q.r, pl, w.keys);
-        k_prep<false><<<sg, 256, 0, st>>>(q.gr, q.W, q.H, q.r, prr, nullptr);
-        counted(2);
-        if (cdt != CDT_NONE) {
-            const int W = q.W, H = q.H, r = q.r;
-            const long nb = (W <= 2 * r || H <= 2 * r) ? (long)W * H : 2L * r * W + 2L * r * (H - 2 * r);
-            k_cost_border_nan<<<(int)std::max<long>(1, std::min<long>(4096, (nb * cost_stride(q.D) + 255) / 256)),
-                                256, 0, st>>>(w.cost, cdt, W, H, r, cost_stride(q.D));
-            counted();
-        }
+        const PrepIn inL{pr->left, pr->pitch, pr->channels == 3, q.converted ? q.w.gl : nullptr};
+        const PrepIn inR{pr->right, pr->pitch, pr->channels == 3, q.converted ? q.w.gr : nullptr};
+        launch_prep(q.r, STEREO_SAMPLE_FULL, inL, inR, q.W, q.H, pl, prr, w.keys,
+                    cdt != CDT_NONE ? w.cost : nullptr, cdt, q.D, st);
     };
     auto finalize = [&](int i, cudaStream_t st) {
         const stereo_pair* pr = &pairs[i];
