@@ -296,6 +296,50 @@ __global__ void __launch_bounds__(256) k_fill_radial_masks(const int16_t* __rest
 // integer below the threshold, disparities being integers).
 constexpr int LM_ROWS = 65, LM_COLS = 34;
 
+// The 16 words of family F that warp (threadIdx.x / 32) builds from the
+// staged rows t.
+template <int F>
+__device__ __forceinline__ void line_mask_words(const int16_t (*t)[LM_COLS], const LineMasks& m, int mode,
+                                                int ithr, int bc, int br) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int X0 = 32 * bc;
+    const uint32_t L = (uint32_t)m.lines(F);
+    uint32_t* wf = m.words + (uint32_t)m.off[F];
+#pragma unroll 4
+    for (int it = 0; it < 16; ++it) {
+        const int i = (warp & 1) * 16 + it;
+        int ly, lx, qy, qx, line, wi;
+        bool ok;
+        if (F == 0) {                 // row 32 br + i, positions 32 bc + lane
+            ly = i + 1; lx = lane; qy = ly; qx = lx + 1;
+            line = 32 * br + i; wi = bc;
+            ok = br >= 0 && line < m.H;
+        } else if (F == 1) {          // column 32 bc + i, positions 32 br + lane
+            ly = lane + 1; lx = i; qy = ly + 1; qx = lx;
+            line = X0 + i; wi = br;
+            ok = br >= 0 && 32 * br < m.H && line < m.W;
+        } else if (F == 2) {          // first pixel (32 bc, 32 br + i), then (+1, +1)
+            ly = i + lane + 1; lx = lane; qy = ly + 1; qx = lx + 1;
+            line = X0 - (32 * br + i) + m.H - 1; wi = bc;
+            ok = line >= 0 && line < m.W + m.H - 1;
+        } else {                      // last pixel (32 bc + 31, 32 br + i), pixel j at row 32 br + i + 31 - j
+            ly = i + 32 - lane; lx = lane; qy = ly - 1; qx = lx + 1;
+            line = X0 + 32 * br + i + 31; wi = bc;
+            ok = line >= 0 && line < m.W + m.H - 1;
+        }
+        if (!ok) continue;            // warp-uniform
+        const int v = t[ly][lx];
+        bool bit = v != ST_INVALID;
+        if (mode == 1) {
+            const int q = t[qy][qx];
+            const int dlt = q - v;
+            bit = bit && q != ST_INVALID && dlt <= ithr && -dlt <= ithr;
+        }
+        const uint32_t word = __ballot_sync(0xffffffffu, bit);
+        if (lane == 0) wf[(uint32_t)(wi + LM_PAD_LO) * L + (uint32_t)line] = word;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_line_masks_tiled(const int16_t* __restrict__ in, LineMasks m,
                                                           int mode, int ithr) {
     __shared__ __align__(4) int16_t t[LM_ROWS][LM_COLS];
@@ -319,41 +363,11 @@ __global__ void __launch_bounds__(256) k_line_masks_tiled(const int16_t* __restr
         *reinterpret_cast<uint32_t*>(&t[ly][2 * cp]) = v;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int f = warp >> 1;                             // two warps per family
-    const uint32_t L = (uint32_t)m.lines(f);
-    uint32_t* wf = m.words + (uint32_t)m.off[f];
-#pragma unroll 4
-    for (int it = 0; it < 16; ++it) {
-        const int i = (warp & 1) * 16 + it;
-        int ly, lx, qy, qx, line, wi;
-        bool ok;
-        if (f == 0) {                 // row 32 br + i, positions 32 bc + lane
-            ly = i + 1; lx = lane; qy = ly; qx = lx + 1;
-            line = 32 * br + i; wi = bc;
-            ok = br >= 0 && line < m.H;
-        } else if (f == 1) {          // column 32 bc + i, positions 32 br + lane
-            ly = lane + 1; lx = i; qy = ly + 1; qx = lx;
-            line = X0 + i; wi = br;
-            ok = br >= 0 && 32 * br < m.H && line < m.W;
-        } else if (f == 2) {          // first pixel (32 bc, 32 br + i), then (+1, +1)
-            ly = i + lane + 1; lx = lane; qy = ly + 1; qx = lx + 1;
-            line = X0 - (32 * br + i) + m.H - 1; wi = bc;
-            ok = line >= 0 && line < m.W + m.H - 1;
-        } else {                      // last pixel (32 bc + 31, 32 br + i), pixel j at row 32 br + i + 31 - j
-            ly = i + 32 - lane; lx = lane; qy = ly - 1; qx = lx + 1;
-            line = X0 + 32 * br + i + 31; wi = bc;
-            ok = line >= 0 && line < m.W + m.H - 1;
-        }
-        if (!ok) continue;            // warp-uniform
-        const int v = t[ly][lx];
-        bool bit = v != ST_INVALID;
-        if (mode == 1) {
-            const int q = t[qy][qx];
-            const int dlt = q - v;
-            bit = bit && q != ST_INVALID && dlt <= ithr && -dlt <= ithr;
-        }
-        const uint32_t word = __ballot_sync(0xffffffffu, bit);
-        if (lane == 0) wf[(uint32_t)(wi + LM_PAD_LO) * L + (uint32_t)line] = word;
+    const int warp = threadIdx.x >> 5;
+    switch (warp >> 1) {              // two warps per family
+        case 0: line_mask_words<0>(t, m, mode, ithr, bc, br); break;
+        case 1: line_mask_words<1>(t, m, mode, ithr, bc, br); break;
+        case 2: line_mask_words<2>(t, m, mode, ithr, bc, br); break;
+        default: line_mask_words<3>(t, m, mode, ithr, bc, br); break;
     }
 }

@@ -71,45 +71,20 @@ __global__ void __launch_bounds__(256) k_prep(PrepIn in0, PrepIn in1, int W, int
         t[ly][lx] = (uint16_t)v;
     }
     __syncthreads();
-    for (int i = tid; i < SPAN * PT; i += 256) {
-        const int ly = i / PT, lx = i % PT;
-        uint32_t s0 = 0, ss0 = 0, s1 = 0, ss1 = 0;
-#pragma unroll
-        for (int k = 0; k <= 2 * R; ++k) {              // dx = k - R
-            const uint32_t v = t[ly][lx + k];
-            if (CB && ((k - R) & 1)) { s1 += v; ss1 += v * v; }
-            else { s0 += v; ss0 += v * v; }
-        }
-        rs[0][ly][lx] = s0;
-        rss[0][ly][lx] = ss0;
-        if (CB) {
-            rs[NP - 1][ly][lx] = s1;
-            rss[NP - 1][ly][lx] = ss1;
-        }
-    }
-    __syncthreads();
     const uint32_t N = (uint32_t)(CB ? ((2 * R + 1) * (2 * R + 1) + 1) / 2 : (2 * R + 1) * (2 * R + 1));
-    for (int i = tid; i < PT * PT; i += 256) {
-        const int ly = i / PT, lx = i % PT;
+    // per-pixel outputs of tile pixel (lx, ly) with window sums s, ss
+    auto emit = [&](int lx, int ly, uint32_t s, uint32_t ss) {
         const int gx = x0 + lx, gy = y0 + ly;
-        if (gx >= W || gy >= H) continue;
+        if (gx >= W || gy >= H) return;
         const size_t gi = (size_t)gy * W + gx;
         if (left && key_clear) { key_clear[gi] = 0u; key_clear[(size_t)W * H + gi] = 0u; }
         const uint32_t c = t[ly + R][lx + R];
         if (in.gray) in.gray[gi] = (uint8_t)c;
         out.img[(size_t)gy * out.stride + out.col0 + gx] = (float)c;
-        uint32_t s = 0, B = 0;
         const bool interior = gx >= R && gx < W - R && gy >= R && gy < H - R;
-        if (interior) {
-            uint32_t ss = 0;
-#pragma unroll
-            for (int k = 0; k <= 2 * R; ++k) {          // dy = k - R: same parity of dx
-                const int q = CB ? ((k - R) & 1) : 0;
-                s += rs[q][ly + k][lx];
-                ss += rss[q][ly + k][lx];
-            }
-            B = N * ss - s * s;
-        }
+        uint32_t B = 0;
+        if (interior) B = N * ss - s * s;
+        else s = 0;
         float is = 0.f;
         if (B) {   // 1/sqrt(B): hardware estimate plus one Newton step (FP64 is slow here)
             const float fb = (float)B;
@@ -120,6 +95,69 @@ __global__ void __launch_bounds__(256) k_prep(PrepIn in0, PrepIn in1, int W, int
         if (out.ustats)
             out.ustats[(size_t)gy * out.ustride + out.ucol0 + gx] =
                 make_float4((float)(s & ~0xffu), (float)(s & 0xffu), is, interior ? 1.f : 0.f);
+    };
+    if (!CB) {
+        // row sums: thread = (staged row, segment of 8 outputs), sliding
+        for (int job = tid; job < SPAN * (PT / 8); job += 256) {
+            const int ly = job / (PT / 8), xs = (job % (PT / 8)) * 8;
+            const uint16_t* a = &t[ly][xs];
+            uint32_t s = 0, ss = 0;
+#pragma unroll
+            for (int k = 0; k <= 2 * R; ++k) { const uint32_t v = a[k]; s += v; ss += v * v; }
+            rs[0][ly][xs] = s;
+            rss[0][ly][xs] = ss;
+#pragma unroll
+            for (int j = 1; j < 8; ++j) {
+                const uint32_t vi = a[j + 2 * R], vo = a[j - 1];
+                s += vi - vo;
+                ss += vi * vi - vo * vo;
+                rs[0][ly][xs + j] = s;
+                rss[0][ly][xs + j] = ss;
+            }
+        }
+        __syncthreads();
+        // column sums and outputs: thread = (column, segment of 4 rows), sliding
+        {
+            const int lx = tid & (PT - 1), ys = (tid >> 5) * 4;
+            uint32_t s = 0, ss = 0;
+#pragma unroll
+            for (int k = 0; k <= 2 * R; ++k) { s += rs[0][ys + k][lx]; ss += rss[0][ys + k][lx]; }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (j > 0) {
+                    s += rs[0][ys + j + 2 * R][lx] - rs[0][ys + j - 1][lx];
+                    ss += rss[0][ys + j + 2 * R][lx] - rss[0][ys + j - 1][lx];
+                }
+                emit(lx, ys + j, s, ss);
+            }
+        }
+    } else {
+        for (int i = tid; i < SPAN * PT; i += 256) {
+            const int ly = i / PT, lx = i % PT;
+            uint32_t s0 = 0, ss0 = 0, s1 = 0, ss1 = 0;
+#pragma unroll
+            for (int k = 0; k <= 2 * R; ++k) {              // dx = k - R
+                const uint32_t v = t[ly][lx + k];
+                if ((k - R) & 1) { s1 += v; ss1 += v * v; }
+                else { s0 += v; ss0 += v * v; }
+            }
+            rs[0][ly][lx] = s0;
+            rss[0][ly][lx] = ss0;
+            rs[NP - 1][ly][lx] = s1;
+            rss[NP - 1][ly][lx] = ss1;
+        }
+        __syncthreads();
+        for (int i = tid; i < PT * PT; i += 256) {
+            const int ly = i / PT, lx = i % PT;
+            uint32_t s = 0, ss = 0;
+#pragma unroll
+            for (int k = 0; k <= 2 * R; ++k) {          // dy = k - R: same parity of dx
+                const int q = (k - R) & 1;
+                s += rs[q][ly + k][lx];
+                ss += rss[q][ly + k][lx];
+            }
+            emit(lx, ly, s, ss);
+        }
     }
     // padding columns of rows y0 .. y0 + 31, shared among the tile row's blocks
     const int rows = min(PT, H - y0);
@@ -136,17 +174,26 @@ __global__ void __launch_bounds__(256) k_prep(PrepIn in0, PrepIn in1, int W, int
         }
     }
     if (left && cost && (x0 < R || x0 + PT > W - R || y0 < R || y0 + PT > H - R)) {
+        // the tile's border pixels: whole rows above R / below H - R, else the
+        // columns left of R and right of W - R; one warp per pixel
         const int warp = tid >> 5, lane = tid & 31;
         const int esz = cdt == CDT_F32 ? 4 : 2;
         const int nvec = cs * esz / 16;                  // 16-byte chunks per pixel (cs is a multiple of 8)
         const uint32_t nan = cdt == CDT_F32 ? 0x7fc00000u : (cdt == CDT_F16 ? 0x7e007e00u : 0x7fc07fc0u);
         const uint4 nv = make_uint4(nan, nan, nan, nan);
-        for (int p = warp; p < PT * PT; p += 8) {
-            const int gx = x0 + (p & (PT - 1)), gy = y0 + p / PT;
-            if (gx >= W || gy >= H) continue;
-            if (gx >= R && gx < W - R && gy >= R && gy < H - R) continue;
-            uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<char*>(cost) + ((size_t)gy * W + gx) * cs * esz);
-            for (int c = lane; c < nvec; c += 32) dst[c] = nv;
+        const int xl = min(max(R - x0, 0), PT);          // tile columns [0, xl) lie left of R
+        const int xr = min(max(W - R - x0, xl), PT);     // tile columns [xr, 32) lie right of W - R
+        for (int ly = warp; ly < rows; ly += 8) {
+            const int gy = y0 + ly;
+            const bool full = gy < R || gy >= H - R;
+            const int nl = full ? min(PT, W - x0) : xl;
+            const int nr = full ? 0 : max(0, min(PT, W - x0) - xr);
+            for (int q = 0; q < nl + nr; ++q) {
+                const int lx = q < nl ? q : xr + (q - nl);
+                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<char*>(cost) +
+                                                      ((size_t)gy * W + x0 + lx) * cs * esz);
+                for (int c = lane; c < nvec; c += 32) dst[c] = nv;
+            }
         }
     }
 }
