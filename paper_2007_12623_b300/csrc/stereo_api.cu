@@ -239,7 +239,15 @@ stereo_status last_error() {
     return STEREO_OK;
 }
 
-int pick_k(int D) { return D <= 32 ? 1 : (D <= 64 ? 2 : 4); }
+// Disparities per lane of the cost kernel (a warp covers 32 K per chunk):
+// K = 4 unless K = 2 leaves fewer lanes beyond the range (e.g. D = 192:
+// three chunks of 64 instead of two of 128 with a quarter of the lanes idle).
+int pick_k(int D) {
+    if (D <= 32) return 1;
+    if (D <= 64) return 2;
+    const int w4 = (D + 127) / 128 * 128 - D, w2 = (D + 63) / 64 * 64 - D;
+    return w2 < w4 ? 2 : 4;
+}
 int pos_mod4(int v) { return ((v % 4) + 4) % 4; }
 
 void launch_cost(int r, int K, int cdt, const CostArgs& a, int rows, cudaStream_t s,
