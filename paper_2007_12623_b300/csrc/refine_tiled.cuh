@@ -15,9 +15,8 @@
 // their pixels' lanes through shared memory.
 //
 // Box sums: the block stages the (32 + 2 rs) rows x (32 + 2 SPAD) columns
-// around its tile; one thread per staged row slides the horizontal sums
-// along the row, then one thread per (column, half tile) slides the vertical
-// sums down the column.
+// around its tile; threads slide the horizontal sums along 8-output row
+// segments, then the vertical sums down 4-output column segments.
 #pragma once
 #include <algorithm>
 #include "common.cuh"
@@ -88,35 +87,37 @@ __device__ __forceinline__ void rb_stage(const S* __restrict__ src, int W, int H
     }
 }
 
-// Box sums of the staged tile into box[32][33] (row-major, padded).
+// Box sums of the staged tile into box[32][33] (row-major, padded): the
+// horizontal pass gives each thread 8 consecutive outputs of one staged row
+// (4 segments per row), the vertical pass 4 consecutive outputs of one
+// column (8 segments per column), so all threads work with short chains.
 template <typename T, int SPAD>
 __device__ __forceinline__ void rb_box(const T* tile, int rs, T* hsum, T* box) {
     constexpr int SWP = RB_T + 2 * SPAD + 1;
     const int rows = rb_rows(rs);
-    // horizontal: one thread per staged row, 32 outputs
-    if (threadIdx.x < rows) {
-        const T* a = tile + threadIdx.x * SWP + (SPAD - rs);
+    for (int job = threadIdx.x; job < rows * 4; job += RB_THREADS) {
+        const int r = job >> 2, x0 = (job & 3) * 8;
+        const T* a = tile + r * SWP + (SPAD - rs) + x0;
         T s = T(0);
         for (int i = 0; i <= 2 * rs; ++i) s += a[i];
-        T* h = hsum + threadIdx.x * (RB_T + 1);
+        T* h = hsum + r * (RB_T + 1) + x0;
         h[0] = s;
-#pragma unroll 8
-        for (int j = 1; j < RB_T; ++j) {
+#pragma unroll
+        for (int j = 1; j < 8; ++j) {
             s += a[j + 2 * rs] - a[j - 1];
             h[j] = s;
         }
     }
     __syncthreads();
-    // vertical: one thread per (column, half of the tile), 16 outputs
-    if (threadIdx.x < 2 * RB_T) {
-        const int c = threadIdx.x & (RB_T - 1), half = threadIdx.x / RB_T;
-        const T* a = hsum + 16 * half * (RB_T + 1) + c;
+    {
+        const int c = threadIdx.x & (RB_T - 1), y0 = (threadIdx.x >> 5) * 4;   // 8 warps x 4 rows
+        const T* a = hsum + y0 * (RB_T + 1) + c;
         T s = T(0);
         for (int i = 0; i <= 2 * rs; ++i) s += a[i * (RB_T + 1)];
-        T* o = box + 16 * half * (RB_T + 1) + c;
+        T* o = box + y0 * (RB_T + 1) + c;
         o[0] = s;
 #pragma unroll
-        for (int j = 1; j < 16; ++j) {
+        for (int j = 1; j < 4; ++j) {
             s += a[(j + 2 * rs) * (RB_T + 1)] - a[(j - 1) * (RB_T + 1)];
             o[j * (RB_T + 1)] = s;
         }
