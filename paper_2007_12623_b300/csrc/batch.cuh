@@ -4,15 +4,15 @@
 // unit from a device counter until the table is exhausted, so large and
 // small pairs share one launch without tail effects.
 #pragma once
-#include "cost.cuh"
+#include "cost_i8.cuh"
 
 // A unit: x = pair, y = x0, z = y0 (both already placed by the host),
 // w = disparity chunk | (partial << 16).
 template <int R, int K, int CDT>
 __device__ __forceinline__ void batched_unit(const CostArgs& a, float* smem, int4 u) {
     const int chunk = u.w & 0xffff;
-    if (u.w >> 16) cost_unit<R, K, CDT, true>(a, smem, u.y, u.z, chunk);
-    else cost_unit<R, K, CDT, false>(a, smem, u.y, u.z, chunk);
+    if (u.w >> 16) cost_unit_i8<R, K, CDT, true>(a, smem, u.y, u.z, chunk);
+    else cost_unit_i8<R, K, CDT, false>(a, smem, u.y, u.z, chunk);
 }
 
 template <int K, int CDT, int MINB>
@@ -43,15 +43,16 @@ __global__ void __launch_bounds__(32, MINB) k_cost_batched(const CostArgs* __res
 }
 
 // Shared memory of the largest radius (units of every radius run in it).
+// The batched form runs the integer units (8-bit images, FULL sampling).
 template <int K> constexpr size_t batched_smem() {
     size_t m = 0;
-    m = CostSmem<1, K>::BYTES > m ? CostSmem<1, K>::BYTES : m;
-    m = CostSmem<2, K>::BYTES > m ? CostSmem<2, K>::BYTES : m;
-    m = CostSmem<3, K>::BYTES > m ? CostSmem<3, K>::BYTES : m;
-    m = CostSmem<4, K>::BYTES > m ? CostSmem<4, K>::BYTES : m;
-    m = CostSmem<5, K>::BYTES > m ? CostSmem<5, K>::BYTES : m;
-    m = CostSmem<6, K>::BYTES > m ? CostSmem<6, K>::BYTES : m;
-    m = CostSmem<7, K>::BYTES > m ? CostSmem<7, K>::BYTES : m;
+    m = CostI8Smem<1, K>::BYTES > m ? CostI8Smem<1, K>::BYTES : m;
+    m = CostI8Smem<2, K>::BYTES > m ? CostI8Smem<2, K>::BYTES : m;
+    m = CostI8Smem<3, K>::BYTES > m ? CostI8Smem<3, K>::BYTES : m;
+    m = CostI8Smem<4, K>::BYTES > m ? CostI8Smem<4, K>::BYTES : m;
+    m = CostI8Smem<5, K>::BYTES > m ? CostI8Smem<5, K>::BYTES : m;
+    m = CostI8Smem<6, K>::BYTES > m ? CostI8Smem<6, K>::BYTES : m;
+    m = CostI8Smem<7, K>::BYTES > m ? CostI8Smem<7, K>::BYTES : m;
     return m;
 }
 

@@ -35,6 +35,12 @@ __host__ __device__ inline int key_to_disp(uint32_t key, int d_min) {
     return key >= KEY_VALID_MIN ? d_min + 255 - (int)(key & 255u) : ST_INVALID;
 }
 
+// Integer window sums of shifted pixels (|S| < 2^22) kept biased by
+// 1.5 * 2^23: the bit pattern of the biased integer read as a float is
+// exactly 1.5 * 2^23 + S.
+constexpr int I8_BIAS_BITS = 0x4B400000;          // float bits of 1.5 * 2^23
+constexpr float I8_BIAS = 12582912.0f;            // 1.5 * 2^23
+
 template <int CDT> struct CostT;
 template <> struct CostT<CDT_F32> { typedef float T; };
 template <> struct CostT<CDT_F16> { typedef __half T; };

@@ -67,6 +67,10 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 struct CostArgs {
     const float* Lf; int lstride; int lcol0;      // float left image
     const float* Rf; int rstride; int rcol0;      // float right image (with margins)
+    // i8 = 1: the images are signed bytes (pixel - 128) with the same strides
+    // and column offsets, and the statistics are those of the shifted pixels
+    // (integer path, cost_i8.cuh); 0: float images (float path below)
+    int i8;
     const float2* lstats;                         // W*H
     const float4* ustats; int ustride; int ucol0; // right statistics (padded rows)
     uint32_t* keyL;

@@ -3,6 +3,7 @@
 #pragma once
 #include <algorithm>
 #include "cost.cuh"
+#include "cost_i8.cuh"
 
 // Work-unit height: with `cap` units resident at once the kernel takes
 // ceil(units / cap) waves of units costing about (rows + 1.1) row times (the
@@ -22,11 +23,12 @@ inline int cost_choose_rows(int units_x, int nz, int rows_total, int cap) {
 
 template <int K> struct CostMinBlocks { static constexpr int value = K == 4 ? 8 : (K == 2 ? 12 : 16); };
 
-template <int R, int K, int CDT, bool CB = false>
+// I8: the integer form (cost_i8.cuh; K even, FULL sampling, 8-bit images).
+template <int R, int K, int CDT, bool CB = false, bool I8 = false>
 void launch_cost_rkc(CostArgs a, int rows_override, cudaStream_t s) {
     typedef CostGeom<R> G;
-    typedef CostSmem<R, K> Sm;
     constexpr int MINB = CostMinBlocks<K>::value;
+    constexpr int BYTES = I8 ? CostI8Smem<R, K>::BYTES : CostSmem<R, K>::BYTES;
     const int nx = (a.W - 2 * R + G::TW - 1) / G::TW;
     const int nz = (a.D + 32 * K - 1) / (32 * K);
     if (nx <= 0 || a.H - 2 * R <= 0) return;
@@ -35,16 +37,31 @@ void launch_cost_rkc(CostArgs a, int rows_override, cudaStream_t s) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cost_wta<R, K, CDT, MINB, CB>, 32, Sm::BYTES);
+        if constexpr (I8)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cost_wta_i8<R, K, CDT, MINB>, 32, BYTES);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cost_wta<R, K, CDT, MINB, CB>, 32, BYTES);
         cap = std::max(1, sms * std::max(1, per_sm));
     }
     a.rows = rows_override > 0 ? rows_override : cost_choose_rows(nx, nz, a.H - 2 * R, cap);
     const int ny = (a.H - 2 * R + a.rows - 1) / a.rows;
-    k_cost_wta<R, K, CDT, MINB, CB><<<dim3(nx, ny, nz), 32, Sm::BYTES, s>>>(a);
+    if constexpr (I8) k_cost_wta_i8<R, K, CDT, MINB><<<dim3(nx, ny, nz), 32, BYTES, s>>>(a);
+    else k_cost_wta<R, K, CDT, MINB, CB><<<dim3(nx, ny, nz), 32, BYTES, s>>>(a);
 }
 
 template <int R, int K>
 void launch_cost_rk(int cdt, const CostArgs& a, int rows_override, cudaStream_t s) {
+    if constexpr (K != 1) {
+        if (a.i8) {
+            switch (cdt) {
+                case CDT_F32: launch_cost_rkc<R, K, CDT_F32, false, true>(a, rows_override, s); break;
+                case CDT_F16: launch_cost_rkc<R, K, CDT_F16, false, true>(a, rows_override, s); break;
+                case CDT_BF16: launch_cost_rkc<R, K, CDT_BF16, false, true>(a, rows_override, s); break;
+                default: launch_cost_rkc<R, K, CDT_NONE, false, true>(a, rows_override, s); break;
+            }
+            return;
+        }
+    }
     switch (cdt) {
         case CDT_F32: launch_cost_rkc<R, K, CDT_F32>(a, rows_override, s); break;
         case CDT_F16: launch_cost_rkc<R, K, CDT_F16>(a, rows_override, s); break;

@@ -61,9 +61,10 @@ struct FinStats {
 
 // c = 1 - rho at d-1, d, d+1 of left pixel (x, y) whose right pixel for d is
 // u0 = x - d, in the fused cost kernel's FP32 arithmetic: the window sum of
-// products is an exact integer (< 2^24), the numerator splits the right
-// window sum into S_hi + S_lo the same way and the products and fused
-// multiply-adds are the same, so the three values equal the FP32 cost
+// products is an exact integer (of the pixels shifted by -128 for FULL
+// sampling, as the integer kernel and its statistics use them), the
+// numerator splits the right window sum the same way and the products and
+// fused multiply-adds are the same, so the three values equal the FP32 cost
 // volume's bit for bit.  NaN where the right pixel's window leaves the image.
 // CB: CHESSBOARD sampling, only the offsets with dx + dy even contribute.
 template <int R, bool CB>
@@ -83,10 +84,11 @@ __device__ __forceinline__ void costs3_fp32(const uint8_t* __restrict__ L, const
 #pragma unroll
         for (int j = 0; j <= 2 * R; ++j) {                 // dx = j - R
             if (CB && ((j - R + dy) & 1)) continue;
-            const int l = __ldg(lp + j);
-            slr0 += l * rv[j + 2];
-            slr1 += l * rv[j + 1];
-            slr2 += l * rv[j];
+            const int l = __ldg(lp + j) - (CB ? 0 : 128);
+            const int sh = CB ? 0 : 128;
+            slr0 += l * (rv[j + 2] - sh);
+            slr1 += l * (rv[j + 1] - sh);
+            slr2 += l * (rv[j] - sh);
         }
     }
     const float2 sl = fs.lstats[(size_t)y * W + x];
@@ -96,8 +98,14 @@ __device__ __forceinline__ void costs3_fp32(const uint8_t* __restrict__ L, const
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const float4 us = up[1 - k];
-        const float t1 = sl.x * us.x;
-        const float num = fmaf(-sl.x, us.y, fmaf(Nf, (float)sv[k], -t1));
+        float num;
+        if (CB) {      // the float cost kernel's arithmetic
+            const float t1 = sl.x * us.x;
+            num = fmaf(-sl.x, us.y, fmaf(Nf, (float)sv[k], -t1));
+        } else {       // the integer kernel's (cost_i8.cuh): shifted pixels, biased sum
+            const float t1 = fmaf(sl.x, us.x, Nf * I8_BIAS);
+            num = fmaf(-sl.x, us.y, fmaf(Nf, __int_as_float(sv[k] + I8_BIAS_BITS), -t1));
+        }
         const float av = num * sl.y;
         c[k] = us.w != 0.f ? fmaf(-av, us.z, 1.f) : __int_as_float(0x7fc00000);
     }

@@ -4,9 +4,11 @@
 #include "common.cuh"
 
 struct PrepOut {
-    float* img;        // float copy of the image, row stride `stride` floats,
+    float* img;        // copy of the image, row stride `stride` elements,
     int stride;        // image column x at row offset col0 + x; the columns
-    int col0;          // outside [col0, col0 + W) are zero
+    int col0;          // outside [col0, col0 + W) are zero.  FULL sampling of
+                       // 8-bit images: signed bytes p - 128 (the integer cost
+                       // form); otherwise floats
     float2* lstats;    // left: {S, 1/sqrt(B)} per pixel (row stride W), or null
     float4* ustats;    // right: {S_hi, S_lo, 1/sqrt(B), valid}, row stride
     int ustride;       // ustride, pixel u at ucol0 + u; entries outside the
@@ -80,7 +82,8 @@ __global__ void __launch_bounds__(256) k_prep(PrepIn in0, PrepIn in1, int W, int
         if (left && key_clear) { key_clear[gi] = 0u; key_clear[(size_t)W * H + gi] = 0u; }
         const uint32_t c = t[ly + R][lx + R];
         if (in.gray) in.gray[gi] = (uint8_t)c;
-        out.img[(size_t)gy * out.stride + out.col0 + gx] = (float)c;
+        if (CB) out.img[(size_t)gy * out.stride + out.col0 + gx] = (float)c;
+        else reinterpret_cast<int8_t*>(out.img)[(size_t)gy * out.stride + out.col0 + gx] = (int8_t)((int)c - 128);
         const bool interior = gx >= R && gx < W - R && gy >= R && gy < H - R;
         uint32_t B = 0;
         if (interior) B = N * ss - s * s;
@@ -91,10 +94,18 @@ __global__ void __launch_bounds__(256) k_prep(PrepIn in0, PrepIn in1, int W, int
             const float y = rsqrtf(fb);
             is = y * fmaf(-0.5f * fb * y, y, 1.5f);
         }
-        if (out.lstats) out.lstats[gi] = make_float2((float)s, is);
+        // window sums of the pixels as stored: S, split S_hi + S_lo with S_hi a
+        // multiple of 256; shifted pixels (FULL sampling): S' = S - 128 N with
+        // N odd, split into S_hi - 128 (N - 1) and S_lo - 128
+        float sl = (float)s, shi = (float)(s & ~0xffu), slo = (float)(s & 0xffu);
+        if (!CB && interior) {
+            sl = (float)((int)s - 128 * (int)N);
+            shi = (float)((int)(s & ~0xffu) - 128 * ((int)N - 1));
+            slo = (float)((int)(s & 0xffu) - 128);
+        }
+        if (out.lstats) out.lstats[gi] = make_float2(sl, is);
         if (out.ustats)
-            out.ustats[(size_t)gy * out.ustride + out.ucol0 + gx] =
-                make_float4((float)(s & ~0xffu), (float)(s & 0xffu), is, interior ? 1.f : 0.f);
+            out.ustats[(size_t)gy * out.ustride + out.ucol0 + gx] = make_float4(shi, slo, is, interior ? 1.f : 0.f);
     };
     if (!CB) {
         // row sums: thread = (staged row, segment of 8 outputs), sliding
@@ -164,7 +175,9 @@ __global__ void __launch_bounds__(256) k_prep(PrepIn in0, PrepIn in1, int W, int
     const int npad = out.stride - W;
     for (int i = blockIdx.x * 256 + tid; i < rows * npad; i += gridDim.x * 256) {
         const int gy = y0 + i / npad, m = i % npad;
-        out.img[(size_t)gy * out.stride + (m < out.col0 ? m : W + m)] = 0.f;
+        const size_t o = (size_t)gy * out.stride + (m < out.col0 ? m : W + m);
+        if (CB) out.img[o] = 0.f;
+        else reinterpret_cast<int8_t*>(out.img)[o] = 0;
     }
     if (out.ustats) {
         const int upad = out.ustride - W;

@@ -298,19 +298,46 @@ void set_smem_attributes() {
     cudaFuncSetAttribute(k_soft_dA, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-// Stats + fused cost/WTA + finalize for one pair whose gray images are gl/gr.
-// Layouts of the float images and statistics of one geometry (left: stride
-// W+40; right: zero margins so that every staged segment of the cost kernel
-// is a 16-byte aligned copy).
-void prep_layouts(int W, int d_min, int D, int K, const PairWs& w, PrepOut& pl, PrepOut& pr) {
+// Disparities per lane of the cost kernel for a sampling: the integer form
+// (FULL sampling) needs an even count, CHESSBOARD sampling runs with K = 2.
+int cost_k(int D, int sampling) {
+    return sampling == STEREO_SAMPLE_CHESSBOARD ? 2 : std::max(2, pick_k(D));
+}
+
+// Row strides and column offsets of the staged images and statistics of one
+// geometry.  Float images (i8 = 0): left stride W+40, right zero margins so
+// that every staged segment of the float cost kernel is a 16-byte aligned
+// copy.  Byte images (i8 = 1): 16-byte multiple strides and margins wide
+// enough for the integer kernel's aligned-down 16-byte copies.  Statistics:
+// the same for both.
+struct PairLayout {
+    int lstride, lcol0, rstride, rcol0, ustride, ucol0;
+};
+PairLayout pair_layout(int W, int d_min, int D, int K, bool i8) {
     const int nz = (D + 32 * K - 1) / (32 * K);
     const int lneed = std::max(0, d_min + nz * 32 * K + 3);          // columns read left of x = 0
-    const int rneed = std::max(0, -d_min) + 48;                      // columns read right of W - 1
-    pl = PrepOut{w.Lf, (W + 40 + 3) & ~3, 0, w.lstats, nullptr, 0, 0};
-    const int rcol0 = ((lneed + 3) & ~3) + pos_mod4(d_min + 31 * K + 3);
-    pr = PrepOut{w.Rf, (rcol0 + W + rneed + 3) & ~3, rcol0, nullptr, w.ustats, 0, 0};
-    pr.ucol0 = lneed + 4;
-    pr.ustride = pr.ucol0 + W + std::max(0, -d_min) + 48;
+    PairLayout l;
+    if (i8) {
+        l.lstride = (W + 64 + 15) & ~15;
+        l.lcol0 = 0;
+        l.rcol0 = std::max(0, d_min + nz * 32 * K) + 16;
+        l.rstride = (l.rcol0 + W + std::max(0, -d_min) + 96 + 15) & ~15;
+    } else {
+        const int rneed = std::max(0, -d_min) + 48;                  // columns read right of W - 1
+        l.lstride = (W + 40 + 3) & ~3;
+        l.lcol0 = 0;
+        l.rcol0 = ((lneed + 3) & ~3) + pos_mod4(d_min + 31 * K + 3);
+        l.rstride = (l.rcol0 + W + rneed + 3) & ~3;
+    }
+    l.ucol0 = lneed + 4;
+    l.ustride = l.ucol0 + W + std::max(0, -d_min) + 48;
+    return l;
+}
+
+void prep_layouts(int W, int d_min, int D, int K, const PairWs& w, PrepOut& pl, PrepOut& pr, bool i8 = false) {
+    const PairLayout l = pair_layout(W, d_min, D, K, i8);
+    pl = PrepOut{w.Lf, l.lstride, l.lcol0, w.lstats, nullptr, 0, 0};
+    pr = PrepOut{w.Rf, l.rstride, l.rcol0, nullptr, w.ustats, l.ustride, l.ucol0};
 }
 
 // Window statistics of both images of a pair in one launch (k_prep), which
@@ -347,13 +374,14 @@ void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, in
                int16_t* disp_left, int16_t* disp_right, float* disp_sub, int16_t* disp_lr,
                cudaStream_t s, cudaEvent_t* ev = nullptr, const PrepIn* inL = nullptr,
                const PrepIn* inR = nullptr) {
-    const int K = sampling == STEREO_SAMPLE_CHESSBOARD ? 2 : pick_k(D);
+    const int K = cost_k(D, sampling);
+    const bool i8 = sampling != STEREO_SAMPLE_CHESSBOARD;     // 8-bit images: the integer cost form
     PrepOut pl, pr;
-    prep_layouts(W, d_min, D, K, w, pl, pr);
+    prep_layouts(W, d_min, D, K, w, pl, pr, i8);
     const PrepIn dl{gl, W, 0, nullptr}, dr{gr, W, 0, nullptr};
     launch_prep(r, sampling, inL ? *inL : dl, inR ? *inR : dr, W, H, pl, pr, w.keys, cost, cdt, D, s);
     if (ev) cudaEventRecord(ev[2], s);
-    CostArgs a{pl.img, pl.stride, pl.col0, pr.img, pr.stride, pr.col0, w.lstats, w.ustats,
+    CostArgs a{pl.img, pl.stride, pl.col0, pr.img, pr.stride, pr.col0, i8 ? 1 : 0, w.lstats, w.ustats,
                pr.ustride, pr.ucol0, w.keys, w.keys + (size_t)W * H, cost, cdt, W, H, d_min, D, 0};
     launch_cost(r, K, cdt, a, g_cost_rows, s, sampling);
     if (ev) cudaEventRecord(ev[3], s);
@@ -932,9 +960,9 @@ static stereo_status build_batch_tables(stereo_handle* h, const stereo_pair* pai
         PairWs w = carve(h->ws + (size_t)i * h->pair_bytes, (size_t)W * H, h->p.num_disp, h->p.cost_dtype,
                          h->p.max_width, h->p.max_height);
         PrepOut pl, prr;
-        prep_layouts(W, d_min, D, K, w, pl, prr);
+        prep_layouts(W, d_min, D, K, w, pl, prr, true);
         void* cost = h->p.cost_dtype != CDT_NONE ? w.cost : nullptr;
-        args[i] = CostArgs{pl.img, pl.stride, pl.col0, prr.img, prr.stride, prr.col0, w.lstats, w.ustats,
+        args[i] = CostArgs{pl.img, pl.stride, pl.col0, prr.img, prr.stride, prr.col0, 1, w.lstats, w.ustats,
                            prr.ustride, prr.ucol0, w.keys, w.keys + (size_t)W * H, cost, h->p.cost_dtype,
                            W, H, d_min, D, rows};
         radius[i] = r;
@@ -955,7 +983,7 @@ static stereo_status build_batch_tables(stereo_handle* h, const stereo_pair* pai
                     int partial = 0;
                     if (x0 + TW > a.W - r) {
                         const int shifted = a.W - r - TW;
-                        if (shifted >= r && ((shifted - r) & 3) == 0) x0 = shifted;
+                        if (shifted >= r) x0 = shifted;      // the integer units need no alignment
                         else partial = 1;
                     }
                     if (inner_h >= rows) y0 = std::min(y0, a.H - r - rows);
@@ -1049,7 +1077,7 @@ static void enqueue_batched(stereo_handle* h, const stereo_pair* pairs, int n, c
         const Pair& q = P[i];
         PairWs w = q.w;
         PrepOut pl, prr;
-        prep_layouts(q.W, q.d_min, q.D, K, w, pl, prr);
+        prep_layouts(q.W, q.d_min, q.D, K, w, pl, prr, true);
         const PrepIn inL{pr->left, pr->pitch, pr->channels == 3, q.converted ? q.w.gl : nullptr};
         const PrepIn inR{pr->right, pr->pitch, pr->channels == 3, q.converted ? q.w.gr : nullptr};
         launch_prep(q.r, STEREO_SAMPLE_FULL, inL, inR, q.W, q.H, pl, prr, w.keys,
@@ -1061,7 +1089,7 @@ static void enqueue_batched(stereo_handle* h, const stereo_pair* pairs, int n, c
         void* cost = cdt != CDT_NONE ? q.w.cost : nullptr;
         int16_t* wta = pr->disp_wta ? pr->disp_wta : q.w.wta;
         PrepOut pl, prr;
-        prep_layouts(q.W, q.d_min, q.D, K, q.w, pl, prr);
+        prep_layouts(q.W, q.d_min, q.D, K, q.w, pl, prr, true);
         launch_finalize(q.w.keys, q.w.keys + (size_t)q.W * q.H, q.W, q.H, q.d_min, q.D, h->p.lr_thresh, cost,
                         cdt, q.gl, q.gr, q.r, h->p.sampling, FinStats{q.w.lstats, q.w.ustats, prr.ustride, prr.ucol0},
                         wta, nullptr, pr->disp_sub, q.w.lr, st);
@@ -1169,7 +1197,7 @@ static void soft_prepare(stereo_handle* h, const PairWs& w, const float* L, cons
     k_cost_border_nan<<<(int)std::max<long>(1, std::min<long>(4096, (nb * cs + 255) / 256)), 256, 0, s>>>(
         w.cost, CDT_F32, W, H, r, cs);
     counted();
-    CostArgs a{pl.img, pl.stride, pl.col0, pr.img, pr.stride, pr.col0, w.lstats, w.ustats,
+    CostArgs a{pl.img, pl.stride, pl.col0, pr.img, pr.stride, pr.col0, 0, w.lstats, w.ustats,
                pr.ustride, pr.ucol0, w.keys, w.keys + (size_t)W * H, w.cost, CDT_F32, W, H, d_min, D, 0};
     launch_cost(r, K, CDT_F32, a, g_cost_rows, s);
     if (timed) mark(h, 2, s);
@@ -1501,15 +1529,11 @@ extern "C" stereo_status stereo_match_wta_noalloc(const uint8_t* left, const uin
         return STEREO_ERR_TOO_LARGE;
     // carve the scratch exactly as run_match lays it out, and check the fit
     const int W = width, H = height;
-    const int K = pick_k(num_disp);
-    const int nz = (num_disp + 32 * K - 1) / (32 * K);
-    const int lneed = std::max(0, d_min + nz * 32 * K + 3);
-    const int rneed = std::max(0, -d_min) + 48;
-    const size_t lf = (size_t)H * ((W + 40 + 3) & ~3) * 4;
-    const int rcol0 = ((lneed + 3) & ~3) + pos_mod4(d_min + 31 * K + 3);
-    const size_t rf = (size_t)H * ((rcol0 + W + rneed + 3) & ~3) * 4;
+    const PairLayout lay = pair_layout(W, d_min, num_disp, cost_k(num_disp, STEREO_SAMPLE_FULL), true);
+    const size_t lf = (size_t)H * lay.lstride;        // byte images
+    const size_t rf = (size_t)H * lay.rstride;
     const size_t ls = (size_t)W * H * 8;
-    const size_t us = (size_t)H * (lneed + 4 + W + std::max(0, -d_min) + 48) * 16;
+    const size_t us = (size_t)H * lay.ustride * 16;
     const size_t ks = (size_t)W * H * 8;
     const size_t need = align_up(lf, 256) + align_up(rf, 256) + align_up(ls, 256) + align_up(us, 256) +
                         align_up(ks, 256);
