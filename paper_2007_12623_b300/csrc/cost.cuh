@@ -79,6 +79,7 @@ struct CostArgs {
     int cdt;
     int W, H, d_min, D;
     int rows;                                     // output rows per work unit
+    int dbase, dcount;                            // this launch covers disparities d_min + [dbase, dbase + dcount)
 };
 
 // Statistics of right pixel i of a staged row (stored at float4 slot
@@ -113,7 +114,7 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
 
     const int lane = threadIdx.x & 31;
     const int W = a.W, H = a.H;
-    const int dc0 = a.d_min + chunk * 32 * K;
+    const int dc0 = a.d_min + a.dbase + chunk * 32 * K;
     const int nsteps = PARTIAL ? min(TW, W - R - x0) : TW;
     const int nrows = min(a.rows, H - R - y0);
     // image column of staged right column 0 (16-byte aligned inside Rf rows);

@@ -80,7 +80,7 @@ __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, i
 
     const int lane = threadIdx.x & 31;
     const int W = a.W, H = a.H;
-    const int dc0 = a.d_min + chunk * 32 * K;
+    const int dc0 = a.d_min + a.dbase + chunk * 32 * K;
     const int nsteps = PARTIAL ? min(TW, W - R - x0) : TW;
     const int nrows = min(a.rows, H - R - y0);
     const int8_t* L8 = reinterpret_cast<const int8_t*>(a.Lf);

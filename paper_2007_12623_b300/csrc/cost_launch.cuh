@@ -30,8 +30,8 @@ void launch_cost_rkc(CostArgs a, int rows_override, cudaStream_t s) {
     constexpr int MINB = CostMinBlocks<K>::value;
     constexpr int BYTES = I8 ? CostI8Smem<R, K>::BYTES : CostSmem<R, K>::BYTES;
     const int nx = (a.W - 2 * R + G::TW - 1) / G::TW;
-    const int nz = (a.D + 32 * K - 1) / (32 * K);
-    if (nx <= 0 || a.H - 2 * R <= 0) return;
+    const int nz = (a.dcount + 32 * K - 1) / (32 * K);
+    if (nx <= 0 || a.H - 2 * R <= 0 || nz <= 0) return;
     static int cap = 0;
     if (cap == 0) {
         int dev = 0, sms = 0, per_sm = 0;

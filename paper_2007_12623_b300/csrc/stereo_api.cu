@@ -382,7 +382,16 @@ void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, in
     launch_prep(r, sampling, inL ? *inL : dl, inR ? *inR : dr, W, H, pl, pr, w.keys, cost, cdt, D, s);
     if (ev) cudaEventRecord(ev[2], s);
     CostArgs a{pl.img, pl.stride, pl.col0, pr.img, pr.stride, pr.col0, i8 ? 1 : 0, w.lstats, w.ustats,
-               pr.ustride, pr.ucol0, w.keys, w.keys + (size_t)W * H, cost, cdt, W, H, d_min, D, 0};
+               pr.ustride, pr.ucol0, w.keys, w.keys + (size_t)W * H, cost, cdt, W, H, d_min, D, 0, 0, D};
+    if (i8 && K == 2 && D > 128) {
+        // 128-disparity chunks at K = 4 for the bulk of the range and 64-disparity
+        // chunks at K = 2 for the rest (e.g. D = 192: 128 + 64 with no idle lane)
+        CostArgs a4 = a;
+        a4.dcount = D / 128 * 128;
+        launch_cost(r, 4, cdt, a4, g_cost_rows, s, sampling);
+        a.dbase = a4.dcount;
+        a.dcount = D - a4.dcount;
+    }
     launch_cost(r, K, cdt, a, g_cost_rows, s, sampling);
     if (ev) cudaEventRecord(ev[3], s);
     launch_finalize(w.keys, w.keys + (size_t)W * H, W, H, d_min, D, lr_thresh, cost, cdt, gl, gr, r, sampling,
@@ -964,7 +973,7 @@ static stereo_status build_batch_tables(stereo_handle* h, const stereo_pair* pai
         void* cost = h->p.cost_dtype != CDT_NONE ? w.cost : nullptr;
         args[i] = CostArgs{pl.img, pl.stride, pl.col0, prr.img, prr.stride, prr.col0, 1, w.lstats, w.ustats,
                            prr.ustride, prr.ucol0, w.keys, w.keys + (size_t)W * H, cost, h->p.cost_dtype,
-                           W, H, d_min, D, rows};
+                           W, H, d_min, D, rows, 0, D};
         radius[i] = r;
     }
     for (int oi = 0; oi < n; ++oi) {
@@ -1198,7 +1207,7 @@ static void soft_prepare(stereo_handle* h, const PairWs& w, const float* L, cons
         w.cost, CDT_F32, W, H, r, cs);
     counted();
     CostArgs a{pl.img, pl.stride, pl.col0, pr.img, pr.stride, pr.col0, 0, w.lstats, w.ustats,
-               pr.ustride, pr.ucol0, w.keys, w.keys + (size_t)W * H, w.cost, CDT_F32, W, H, d_min, D, 0};
+               pr.ustride, pr.ucol0, w.keys, w.keys + (size_t)W * H, w.cost, CDT_F32, W, H, d_min, D, 0, 0, D};
     launch_cost(r, K, CDT_F32, a, g_cost_rows, s);
     if (timed) mark(h, 2, s);
     sa = SoftArgs{reinterpret_cast<const float*>(w.cost), cs, w.lstats, w.ustats, pr.ustride, pr.ucol0,
