@@ -85,6 +85,7 @@ COST_CODE = {"none": 0, "f32": 1, "f16": 2, "bf16": 3}
 KERNEL_TRAFFIC = {"tissue960": 221.7e6}
 COST_BYTES = {"none": 0, "f32": 4, "f16": 2, "bf16": 2}
 METRIC = "Gpix*disp/s and ms per 960x540 pair (1 B300), % of roofline, vs oracle"
+DATA = "synthetic (seeded tissue-texture generator standing in for the paper's videos)"
 UNIT = "Gpix*disp/s"
 L2_BYTES = 126 * 2 ** 20
 PAPER_CONTEXT = {"ms_per_keyframe_whole_pipeline": 76.3, "stereo_stage_ms": 15.9,
@@ -304,11 +305,22 @@ def _base_line(args, world, value, t_max, dtype, config):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(t_max * 1e3 / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype,
-            "data": "synthetic (seeded tissue-texture generator standing in for the paper's videos)",
+            "data": DATA,
             "config": config}
 
 
 # ------------------------------------------------------------- our arm: one pair
+
+def single_config(name, wl, world):
+    """The `config` of a single-pair workload's line (both arms)."""
+    return {
+        "workload": name, "width": wl["W"], "height": wl["H"], "num_disp": wl["D"], "d_min": wl.get("d_min", 0),
+        "window": 2 * wl["r"] + 1, "sampling": "chessboard" if wl.get("sampling", 0) else "full",
+        "cost_storage": wl["cost"], "smooth_radius": wl["smooth_radius"], "refine_iters": 5,
+        "pairs_per_gpu": 1, "parallelism": f"replicas x{world} (independent pairs)",
+        "l2": "flushed between timed steps (256 MB write, untimed)",
+        "launch": "CUDA graph replay on a non-default stream"}
+
 
 def run_single(args, wl, rank, world, dev):
     import torch
@@ -442,13 +454,7 @@ def run_single(args, wl, rank, world, dev):
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     roof = cost_kernel_roofline([(W, H, D, wl["r"], wl["cost"])], stage_ms["cost_wta"], peaks, sm_count,
                                 "k_cost_wta", KERNEL_TRAFFIC.get(args.workload))
-    line = _base_line(args, world, value, t_max, "f32", {
-        "workload": args.workload, "width": W, "height": H, "num_disp": D, "d_min": wl.get("d_min", 0),
-        "window": 2 * wl["r"] + 1, "sampling": "chessboard" if wl.get("sampling", 0) else "full",
-        "cost_storage": wl["cost"], "smooth_radius": wl["smooth_radius"], "refine_iters": 5,
-        "pairs_per_gpu": 1, "parallelism": f"replicas x{world} (independent pairs)",
-        "l2": "flushed between timed steps (256 MB write, untimed)",
-        "launch": "CUDA graph replay on a non-default stream"})
+    line = _base_line(args, world, value, t_max, "f32", single_config(args.workload, wl, world))
     line.update({
         "ms_per_pair": round(t_max * 1e3 / args.steps, 4),
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
@@ -742,8 +748,9 @@ def run_reference(args, wl):
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(sum(secs) / args.steps * 1e3, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded tissue-texture generator)",
-            "config": {"workload": args.workload, "width": W, "num_disp": D},
+            "data": DATA,
+            "config": (single_config(args.workload, wl, 1) if wl["kind"] == "single"
+                       else {"workload": args.workload, "width": W, "num_disp": D}),
             "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"each step: {sample}"},
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
