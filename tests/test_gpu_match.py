@@ -73,6 +73,7 @@ def check_against_oracle(g, m, D, sub_check=True):
     ((30, 150), 0, 100, 5),     # K = 4, ragged D
     ((26, 230), -20, 150, 5),   # two chunks of 128, negative d_min
     ((33, 80), 0, 16, 7),
+    ((30, 260), 0, 192, 6),     # 128 disparities at K = 4, then 64 at K = 2
 ])
 def test_random_pairs_small(dev, shape, d_min, D, r):
     rng = np.random.default_rng(hash((shape, d_min, D, r)) & 0xFFFF)
@@ -86,6 +87,24 @@ def test_random_pairs_small(dev, shape, d_min, D, r):
     assert np.array_equal(np.isnan(g["cost"]), np.isnan(cv))
     ok = ~np.isnan(cv)
     assert np.max(np.abs(g["cost"][ok] - cv[ok])) <= 1e-6
+
+
+def test_binary_images_extreme_window_sums(dev):
+    """Pixels of 0 and 255 only, 15x15 windows: the window sums of products
+    of the integer cost form reach their largest magnitudes (every shifted
+    product is +-128*127 or 127^2 or 128^2), where an inexact sum would show."""
+    rng = np.random.default_rng(11)
+    L = (rng.integers(0, 2, (36, 120)) * 255).astype(np.uint8)
+    R = np.roll(L, -9, axis=1)
+    R[:, -12:] = (rng.integers(0, 2, (36, 12)) * 255).astype(np.uint8)
+    g = run_stage_match(dev, L, R, 0, 40, 7)
+    m = oracle.match(L, R, 0, 40, 7)
+    check_against_oracle(g, m, 40)
+    cv = oracle.cost_volume(L, R, 0, 40, 7)
+    ok = ~np.isnan(cv)
+    assert np.array_equal(np.isnan(g["cost"]), np.isnan(cv))
+    assert np.max(np.abs(g["cost"][ok] - cv[ok])) <= 1e-6
+    assert np.mean(g["dL"][7:-7, 30:-7] == 9) > 0.95          # the shift is found
 
 
 def test_perlin_pair_full(dev):
