@@ -57,7 +57,50 @@ struct FinStats {
     const float2* lstats;
     const float4* ustats;
     int ustride, ucol0;
+    // FULL sampling: the preparation kernel's byte images p - 128 (row
+    // strides and column offsets as the cost kernel's), or nullptr
+    const int8_t* L8; int l8stride, l8col0;
+    const int8_t* R8; int r8stride, r8col0;
 };
+
+// Window sums of products of shifted pixels for the right pixels u0 - 1, u0,
+// u0 + 1 of left pixel (x, y) (FULL sampling) from the byte images, four taps
+// per dp4a: s[0] for u0 + 1, s[1] for u0, s[2] for u0 - 1.  Words are read
+// 4-byte aligned and shifted into place; taps beyond the window meet zeroed
+// left bytes.  The byte images have margins around every row, so no read
+// leaves them.
+template <int R>
+__device__ __forceinline__ void slr3_i8(const FinStats& fs, int x, int y, int u0, int s[3]) {
+    constexpr int NW = (2 * R + 1 + 3) / 4;              // left words of a window row
+    s[0] = s[1] = s[2] = 0;
+#pragma unroll
+    for (int dy = -R; dy <= R; ++dy) {
+        const int8_t* lp = fs.L8 + (size_t)(y + dy) * fs.l8stride + fs.l8col0 + x - R;
+        const int8_t* rp = fs.R8 + (size_t)(y + dy) * fs.r8stride + fs.r8col0 + u0 - 1 - R;
+        const int lsh = (int)((uintptr_t)lp & 3) * 8, rsh = (int)((uintptr_t)rp & 3) * 8;
+        const uint32_t* lw = reinterpret_cast<const uint32_t*>((uintptr_t)lp & ~(uintptr_t)3);
+        const uint32_t* rw = reinterpret_cast<const uint32_t*>((uintptr_t)rp & ~(uintptr_t)3);
+        uint32_t la[NW + 1], ra[NW + 2];
+#pragma unroll
+        for (int i = 0; i <= NW; ++i) la[i] = __ldg(lw + i);
+#pragma unroll
+        for (int i = 0; i <= NW + 1; ++i) ra[i] = __ldg(rw + i);
+        uint32_t l[NW], r[NW + 1];
+#pragma unroll
+        for (int i = 0; i < NW; ++i) l[i] = __funnelshift_r(la[i], la[i + 1], lsh);
+        // zero the left bytes past the window (their taps drop out)
+        constexpr int REM = (2 * R + 1) % 4;
+        if (REM) l[NW - 1] &= (1u << (8 * REM)) - 1u;
+#pragma unroll
+        for (int i = 0; i <= NW; ++i) r[i] = __funnelshift_r(ra[i], ra[i + 1], rsh);
+#pragma unroll
+        for (int i = 0; i < NW; ++i) {
+            s[2] = __dp4a((int)l[i], (int)r[i], s[2]);                                  // from u0 - 1 - R
+            s[1] = __dp4a((int)l[i], (int)__funnelshift_r(r[i], r[i + 1], 8), s[1]);     // from u0 - R
+            s[0] = __dp4a((int)l[i], (int)__funnelshift_r(r[i], r[i + 1], 16), s[0]);    // from u0 + 1 - R
+        }
+    }
+}
 
 // c = 1 - rho at d-1, d, d+1 of left pixel (x, y) whose right pixel for d is
 // u0 = x - d, in the fused cost kernel's FP32 arithmetic: the window sum of
@@ -72,6 +115,13 @@ __device__ __forceinline__ void costs3_fp32(const uint8_t* __restrict__ L, const
                                             int W, int x, int y, int u0, const FinStats& fs, float c[3]) {
     int slr0 = 0, slr1 = 0, slr2 = 0;            // right pixel u0 + 1, u0, u0 - 1
     const int cl = max(u0 - R - 1, 0), cr = min(u0 + R + 1, W - 1);
+    if (!CB && fs.L8) {
+        int sv[3];
+        slr3_i8<R>(fs, x, y, u0, sv);
+        slr0 = sv[0];
+        slr1 = sv[1];
+        slr2 = sv[2];
+    } else
 #pragma unroll
     for (int dy = -R; dy <= R; ++dy) {
         const uint8_t* lp = L + (size_t)(y + dy) * W + x - R;

@@ -395,7 +395,10 @@ void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, in
     launch_cost(r, K, cdt, a, g_cost_rows, s, sampling);
     if (ev) cudaEventRecord(ev[3], s);
     launch_finalize(w.keys, w.keys + (size_t)W * H, W, H, d_min, D, lr_thresh, cost, cdt, gl, gr, r, sampling,
-                    FinStats{w.lstats, w.ustats, pr.ustride, pr.ucol0}, disp_left, disp_right, disp_sub, disp_lr,
+                    FinStats{w.lstats, w.ustats, pr.ustride, pr.ucol0,
+                             i8 ? reinterpret_cast<const int8_t*>(pl.img) : nullptr, pl.stride, pl.col0,
+                             i8 ? reinterpret_cast<const int8_t*>(pr.img) : nullptr, pr.stride, pr.col0},
+                    disp_left, disp_right, disp_sub, disp_lr,
                     s);
     counted();
 }
@@ -1100,7 +1103,10 @@ static void enqueue_batched(stereo_handle* h, const stereo_pair* pairs, int n, c
         PrepOut pl, prr;
         prep_layouts(q.W, q.d_min, q.D, K, q.w, pl, prr, true);
         launch_finalize(q.w.keys, q.w.keys + (size_t)q.W * q.H, q.W, q.H, q.d_min, q.D, h->p.lr_thresh, cost,
-                        cdt, q.gl, q.gr, q.r, h->p.sampling, FinStats{q.w.lstats, q.w.ustats, prr.ustride, prr.ucol0},
+                        cdt, q.gl, q.gr, q.r, h->p.sampling,
+                        FinStats{q.w.lstats, q.w.ustats, prr.ustride, prr.ucol0,
+                                 reinterpret_cast<const int8_t*>(pl.img), pl.stride, pl.col0,
+                                 reinterpret_cast<const int8_t*>(prr.img), prr.stride, prr.col0},
                         wta, nullptr, pr->disp_sub, q.w.lr, st);
         counted();
         if (pr->disp_lr)
