@@ -36,11 +36,14 @@ struct CostI8Smem {
     static constexpr int NLP = (NC + 3) / 4 * 4;                   // left pair words
     static constexpr int NRW = ((NC - 1 + K) >> 1) + 1;            // right words a lane reads
     static constexpr int OFF_RP = (G::RING * ROWB + 15) / 16 * 16;
-    static constexpr int OFF_LP = OFF_RP + NWP * 4;
+    static constexpr int OFF_LP = (OFF_RP + NWP * 4 + 15) / 16 * 16;   // read as uint4
     static constexpr int OFF_U = (OFF_LP + NLP * 4 + 15) / 16 * 16;
     static constexpr int OFF_LS = OFF_U + S::US * 4;
     static constexpr int OFF_EXIT = OFF_LS + S::LS * 4;
     static constexpr int BYTES = OFF_EXIT + 32 * 4;
+    // the vector reads of the staged rows need these alignments
+    static_assert(OFF_RP % 16 == 0 && OFF_LP % 16 == 0 && OFF_U % 16 == 0 && OFF_LS % 8 == 0,
+                  "shared-memory layout of the integer cost unit");
 };
 
 // Four bytes of shared memory from any byte offset.
