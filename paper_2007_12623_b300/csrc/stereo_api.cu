@@ -453,15 +453,17 @@ void run_fill_radial(const int16_t* in, int W, int H, int radius, int min_dirs, 
     counted();
 }
 
-// Disc fill: row prefixes of the packed map into the (otherwise unused
-// during post-processing) refinement row-sum buffer, then the queries.
-void run_fill_disc(const int16_t* in, int W, int H, int radius, int min_count, const PairWs& w, int16_t* out,
-                   cudaStream_t s) {
-    uint32_t* S = reinterpret_cast<uint32_t*>(w.rsC);
-    k_row_prefix<<<H, DISC_PREFIX_THREADS, 0, s>>>(in, W, S);
-    counted();
-    k_fill_disc_prefix<<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, s>>>(in, S, W, H, radius, min_count,
-                                                                              out);
+// Disc fill: one tile kernel (row prefixes of the tile's window in shared
+// memory, then the queries).
+void run_fill_disc(const int16_t* in, int W, int H, int radius, int min_count, int16_t* out, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_fill_disc_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)disc_local_smem(PT_MAX_HALO));
+        attr = true;
+    }
+    k_fill_disc_local<<<dim3((W + DL_TW - 1) / DL_TW, (H + DL_TH - 1) / DL_TH), DL_THREADS,
+                        disc_local_smem(radius), s>>>(in, W, H, radius, min_count, out);
     counted();
 }
 
@@ -480,7 +482,7 @@ void run_postprocess(const stereo_params& p, const int16_t* in, int W, int H, co
         run_outlier(cur, W, H, rad, p.outlier_thresh, w.masks, w.p, s);
         run_fill_radial(w.p, W, H, p.fill_radial_r, p.fill_radial_min_dirs, w.masks, w.q, s);
         int16_t* dst = (t == p.outlier_rounds - 1) ? out : w.t;
-        run_fill_disc(w.q, W, H, p.fill_disc_r, min_count, w, dst, s);
+        run_fill_disc(w.q, W, H, p.fill_disc_r, min_count, dst, s);
         cur = dst;
     }
 }
@@ -868,8 +870,7 @@ stereo_status stereo_stage_fill_disc(stereo_handle* h, const int16_t* in, int32_
         return STEREO_ERR_INVALID_ARG;
     if (W > h->p.max_width || H > h->p.max_height) return STEREO_ERR_TOO_LARGE;
     if (min_count < 0) min_count = (disc_area(radius) + 3) / 4;
-    PairWs w = carve(h->ws, (size_t)W * H, h->p.num_disp, h->p.cost_dtype, h->p.max_width, h->p.max_height);
-    run_fill_disc(in, W, H, radius, min_count, w, out, S(stream));
+    run_fill_disc(in, W, H, radius, min_count, out, S(stream));
     return last_error();
 }
 

@@ -92,6 +92,22 @@ def test_fill_disc(dev, radius):
     assert np.array_equal(to_np(out), want)
 
 
+def test_fill_disc_sparse_holes(dev):
+    """Holes in a few tiles only (a patch, isolated pixels, the image
+    corners): tiles without a hole copy their pixels, the others fill from
+    windows that reach into hole-free tiles and past the image border."""
+    rng = np.random.default_rng(21)
+    m = rng.integers(0, 90, (100, 203)).astype(np.int16)
+    m[40:52, 70:85] = INV
+    m[0, 0] = m[-1, -1] = m[0, -1] = m[-1, 0] = INV
+    m[rng.integers(0, 100, 12), rng.integers(0, 203, 12)] = INV
+    for radius in (3, 20, 56):
+        out = torch.empty_like(T(m, dev))
+        st.stereo_stage_fill_disc(_handle(*m.shape), T(m, dev), radius, -1, out)
+        want = oracle.fill_disc(m, radius)
+        assert np.array_equal(to_np(out), want), radius
+
+
 def test_fill_disc_wide_rows_large_values(dev):
     """1920-wide rows of disparities near 4300 (the row prefixes wrap around
     32 bits; every disc span stays exact) and negative values."""
