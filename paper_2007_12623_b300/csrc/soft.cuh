@@ -420,13 +420,35 @@ __global__ void __launch_bounds__(256) k_l1_partial(const float* __restrict__ ds
     if (threadIdx.x == 0) { part[2 * blockIdx.x] = ss[0]; part[2 * blockIdx.x + 1] = sc[0]; }
 }
 
-__global__ void k_l1_final(const double* __restrict__ part, int nparts, float* __restrict__ loss,
-                           double* __restrict__ count) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One block of 1024 threads adds the partial sums: strided per-thread sums,
+// then a tree in shared memory (the order is fixed, so the result is
+// deterministic).
+constexpr int L1_FINAL_THREADS = 1024;
+
+__global__ void __launch_bounds__(L1_FINAL_THREADS) k_l1_final(const double* __restrict__ part, int nparts,
+                                                             float* __restrict__ loss,
+                                                             double* __restrict__ count) {
+    __shared__ double ss[L1_FINAL_THREADS];
+    __shared__ double sc[L1_FINAL_THREADS];
     double s = 0.0, c = 0.0;
-    for (int i = 0; i < nparts; ++i) { s += part[2 * i]; c += part[2 * i + 1]; }
-    *loss = c > 0 ? (float)(s / c) : 0.f;
-    *count = c;
+    for (int i = threadIdx.x; i < nparts; i += L1_FINAL_THREADS) {
+        s += part[2 * i];
+        c += part[2 * i + 1];
+    }
+    ss[threadIdx.x] = s;
+    sc[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = L1_FINAL_THREADS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            ss[threadIdx.x] += ss[threadIdx.x + o];
+            sc[threadIdx.x] += sc[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *loss = sc[0] > 0 ? (float)(ss[0] / sc[0]) : 0.f;
+        *count = sc[0];
+    }
 }
 
 __global__ void __launch_bounds__(256) k_l1_grad(const float* __restrict__ ds, const float* __restrict__ gt,

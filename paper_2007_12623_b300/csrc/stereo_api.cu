@@ -1301,7 +1301,7 @@ stereo_status stereo_l1_loss(stereo_handle* h, const float* d_soft, const float*
     k_l1_partial<<<parts, 256, 0, s>>>(d_soft, gt, n, w.l1part);
     counted();
     double* count = w.l1part + 2 * (L1_PARTS - 1);
-    k_l1_final<<<1, 32, 0, s>>>(w.l1part, parts, loss, count);
+    k_l1_final<<<1, L1_FINAL_THREADS, 0, s>>>(w.l1part, parts, loss, count);
     counted();
     if (grad) {
         k_l1_grad<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_soft, gt, n, count, grad);
