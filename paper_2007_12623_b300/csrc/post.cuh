@@ -346,21 +346,30 @@ __global__ void __launch_bounds__(256) k_line_masks_tiled(const int16_t* __restr
     const int bc = blockIdx.x, br = (int)blockIdx.y - 1;
     const int X0 = 32 * bc, Y0 = 32 * br - 1;            // staged row 0 is image row Y0
     const bool pairs = (m.W & 1) == 0 && (reinterpret_cast<uintptr_t>(in) & 3) == 0;
-    for (int i = threadIdx.x; i < LM_ROWS * (LM_COLS / 2); i += 256) {
+    // all staging loads of a thread go out before their values are stored
+    constexpr int NPAIR = LM_ROWS * (LM_COLS / 2), NIT = (NPAIR + 255) / 256;
+    uint32_t v[NIT];
+#pragma unroll
+    for (int k = 0; k < NIT; ++k) {
+        const int i = threadIdx.x + 256 * k;
         const int ly = i / (LM_COLS / 2), cp = i % (LM_COLS / 2);
         const int gx = X0 + 2 * cp, gy = Y0 + ly;
-        uint32_t v = 0x80008000u;                        // two ST_INVALID
-        if (gy >= 0 && gy < m.H) {
+        v[k] = 0x80008000u;                              // two ST_INVALID
+        if (i < NPAIR && gy >= 0 && gy < m.H) {
             const int16_t* row = in + (size_t)gy * m.W;
             if (pairs && gx + 1 < m.W) {
-                v = __ldg(reinterpret_cast<const uint32_t*>(row + gx));
+                v[k] = __ldg(reinterpret_cast<const uint32_t*>(row + gx));
             } else {
                 const uint32_t a = gx < m.W ? (uint16_t)row[gx] : 0x8000u;
                 const uint32_t b = gx + 1 < m.W ? (uint16_t)row[gx + 1] : 0x8000u;
-                v = a | (b << 16);
+                v[k] = a | (b << 16);
             }
         }
-        *reinterpret_cast<uint32_t*>(&t[ly][2 * cp]) = v;
+    }
+#pragma unroll
+    for (int k = 0; k < NIT; ++k) {
+        const int i = threadIdx.x + 256 * k;
+        if (i < NPAIR) *reinterpret_cast<uint32_t*>(&t[i / (LM_COLS / 2)][2 * (i % (LM_COLS / 2))]) = v[k];
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5;

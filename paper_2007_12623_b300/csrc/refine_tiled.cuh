@@ -56,33 +56,58 @@ __device__ __forceinline__ void rb_stage(const S* __restrict__ src, int W, int H
     const int rows = rb_rows(rs);
     const int gx0 = x0 - SPAD;
     const bool vec = !CONV && gx0 >= 0 && gx0 + SW <= W && (W & 3) == 0;
+    // loads go out in batches of 4 (vector) or 8 (scalar) per thread before
+    // their values are stored
     if (vec) {
-        for (int i = threadIdx.x; i < rows * (SW / 4); i += RB_THREADS) {
-            const int ry = i / (SW / 4), c4 = i % (SW / 4);
-            const int gy = y0 - rs + ry;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (gy >= 0 && gy < H)
-                v = __ldg(reinterpret_cast<const uint4*>(src + (size_t)gy * W + gx0) + c4);
-            T* d = tile + ry * SWP + 4 * c4;
-            d[0] = *reinterpret_cast<T*>(&v.x);
-            d[1] = *reinterpret_cast<T*>(&v.y);
-            d[2] = *reinterpret_cast<T*>(&v.z);
-            d[3] = *reinterpret_cast<T*>(&v.w);
+        const int total = rows * (SW / 4);
+        for (int i0 = threadIdx.x; i0 < total; i0 += 4 * RB_THREADS) {
+            uint4 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int i = i0 + k * RB_THREADS;
+                const int ry = i / (SW / 4), c4 = i % (SW / 4);
+                const int gy = y0 - rs + ry;
+                v[k] = make_uint4(0u, 0u, 0u, 0u);
+                if (i < total && gy >= 0 && gy < H)
+                    v[k] = __ldg(reinterpret_cast<const uint4*>(src + (size_t)gy * W + gx0) + c4);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int i = i0 + k * RB_THREADS;
+                if (i >= total) break;
+                const int ry = i / (SW / 4), c4 = i % (SW / 4);
+                T* d = tile + ry * SWP + 4 * c4;
+                d[0] = *reinterpret_cast<T*>(&v[k].x);
+                d[1] = *reinterpret_cast<T*>(&v[k].y);
+                d[2] = *reinterpret_cast<T*>(&v[k].z);
+                d[3] = *reinterpret_cast<T*>(&v[k].w);
+            }
         }
     } else {
-        for (int i = threadIdx.x; i < rows * SW; i += RB_THREADS) {
-            const int ry = i / SW, cx = i % SW;
-            const int gy = y0 - rs + ry, gx = gx0 + cx;
-            T v = T(0);
-            if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-                if (CONV) {
-                    const uint32_t p = pack_o(src[(size_t)gy * W + gx], d_min);
-                    v = *reinterpret_cast<const T*>(&p);
-                } else {
-                    v = *reinterpret_cast<const T*>(src + (size_t)gy * W + gx);
+        const int total = rows * SW;
+        for (int i0 = threadIdx.x; i0 < total; i0 += 8 * RB_THREADS) {
+            T v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int i = i0 + k * RB_THREADS;
+                const int ry = i / SW, cx = i % SW;
+                const int gy = y0 - rs + ry, gx = gx0 + cx;
+                v[k] = T(0);
+                if (i < total && gy >= 0 && gy < H && gx >= 0 && gx < W) {
+                    if (CONV) {
+                        const uint32_t p = pack_o(src[(size_t)gy * W + gx], d_min);
+                        v[k] = *reinterpret_cast<const T*>(&p);
+                    } else {
+                        v[k] = *reinterpret_cast<const T*>(src + (size_t)gy * W + gx);
+                    }
                 }
             }
-            tile[ry * SWP + cx] = v;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int i = i0 + k * RB_THREADS;
+                if (i >= total) break;
+                tile[(i / SW) * SWP + i % SW] = v[k];
+            }
         }
     }
 }
