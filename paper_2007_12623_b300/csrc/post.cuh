@@ -216,20 +216,28 @@ __global__ void __launch_bounds__(256) k_outlier_masks32(const int16_t* __restri
     const int pix = blockIdx.x * blockDim.x + threadIdx.x;
     if (pix >= m.W * m.H) return;
     const int y = pix / m.W, x = pix - y * m.W;
+    // the word loads depend on (x, y) only: they go out with the pixel's own
     const int v = in[pix];
+    uint32_t a[4][3];
+    int o[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        int line, pos;
+        fam_coords(m, f, x, y, line, pos);
+        const uint32_t L = (uint32_t)m.lines(f);
+        const uint32_t* w = m.words + (uint32_t)m.off[f] + (uint32_t)((pos >> 5) + LM_PAD_LO - 1) * L + line;
+        a[f][0] = __ldg(w);
+        a[f][1] = __ldg(w + L);
+        a[f][2] = __ldg(w + 2 * L);
+        o[f] = pos & 31;
+    }
     bool keep = radius == 0;
     if (v != ST_INVALID && radius > 0) {
         const uint32_t need = radius >= 32 ? 0xffffffffu : ((1u << radius) - 1u);
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
-            int line, pos;
-            fam_coords(m, f, x, y, line, pos);
-            const uint32_t L = (uint32_t)m.lines(f);
-            const uint32_t* w = m.words + (uint32_t)m.off[f] + (uint32_t)((pos >> 5) + LM_PAD_LO - 1) * L + line;
-            const uint32_t a0 = __ldg(w), a1 = __ldg(w + L), a2 = __ldg(w + 2 * L);
-            const int o = pos & 31;
-            const uint32_t fw = __funnelshift_r(a1, a2, o);          // edge bits pos .. pos + 31
-            const uint32_t bw = __funnelshift_r(a0, a1, o);          // edge bits pos - 32 .. pos - 1
+            const uint32_t fw = __funnelshift_r(a[f][1], a[f][2], o[f]);   // edge bits pos .. pos + 31
+            const uint32_t bw = __funnelshift_r(a[f][0], a[f][1], o[f]);   // edge bits pos - 32 .. pos - 1
             keep |= (fw & need) == need;
             keep |= (bw >> (32 - radius)) == need;
         }
