@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(256) k_soft_fwd(SoftArgs a, float* __restrict_
         for (int j = 0; j < 16; ++j) {
             const float rho = 1.f - v[j];
             const bool ok = x0 + h + j < a.W && k < a.D && rho == rho;   // valid candidate
-            const float e = ok ? exp2f((rho - 1.f) * k2) : 0.f;          // exp((rho - 1) / tau) <= 1
+            float e = 0.f;                                                // exp((rho - 1) / tau) <= 1
+            if (ok) asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"((rho - 1.f) * k2));
             t0[(h + j) * 33 + lane] = e;
             t1[(h + j) * 33 + lane] = dv * e;
         }
@@ -155,10 +156,16 @@ __global__ void __launch_bounds__(256) k_soft_dA(SoftArgs a, const float* __rest
     const size_t mypix = row + min(x0 + lane, a.W - 1);     // this lane's pixel x0 + lane
     // G = g p_d (d - ds) / tau with p_d = exp(rho / tau - lse): per pixel
     // g N / tau and lse log2(e) are folded in
-    const float my_gs = x0 + lane < a.W ? __ldg(g + mypix) * N * inv_tau : 0.f;
-    const float my_ds = __ldg(dsoft + mypix);
-    const float my_l2 = __ldg(lse + mypix) * 1.4426950408889634f;
-    const float2 my_sl = __ldg(a.lstats + mypix);
+    // the run's per-pixel inputs, read by every warp as shared-memory broadcasts
+    __shared__ float4 px4[SOFT_RUN];
+    __shared__ float pxi[SOFT_RUN];
+    if (c == 0) {
+        const float2 sl = __ldg(a.lstats + mypix);
+        px4[lane] = make_float4(x0 + lane < a.W ? __ldg(g + mypix) * N * inv_tau : 0.f, __ldg(dsoft + mypix),
+                                __ldg(lse + mypix) * 1.4426950408889634f, sl.x);
+        pxi[lane] = sl.y;
+    }
+    __syncthreads();
     const int k = c * 32 + lane;
     const int kc = min(k, a.cs - 1);
     const int d = a.d_min + k;
@@ -180,16 +187,15 @@ __global__ void __launch_bounds__(256) k_soft_dA(SoftArgs a, const float* __rest
 #pragma unroll
         for (int j = 0; j < HALF; ++j) {
             const int x = x0 + h + j;
-            const float gs = __shfl_sync(0xffffffffu, my_gs, h + j);
-            const float ds = __shfl_sync(0xffffffffu, my_ds, h + j);
-            const float l2 = __shfl_sync(0xffffffffu, my_l2, h + j);
-            const float slx = __shfl_sync(0xffffffffu, my_sl.x, h + j);
-            const float isl = __shfl_sync(0xffffffffu, my_sl.y, h + j);
+            const float4 pv = px4[h + j];
+            const float gs = pv.x, ds = pv.y, l2 = pv.z, slx = pv.w;
+            const float isl = pxi[h + j];
             const float rho = 1.f - cv[j];
             const float isr = ur[j].z;
             float av = 0.f, v1 = 0.f, v2 = 0.f;
             if (x < a.W && k < a.D && gs != 0.f && isl != 0.f && rho == rho && isr != 0.f) {
-                const float pd = exp2f(fmaf(rho, l2e_tau, -l2));
+                float pd;                                          // 2^x, x <= 0
+                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(pd) : "f"(fmaf(rho, l2e_tau, -l2)));
                 const float Gn = gs * pd * ((float)d - ds);       // G N
                 av = Gn * isl * isr;                               // A = G N isl isr
                 const float ng = av * invN;                        // G isl isr
