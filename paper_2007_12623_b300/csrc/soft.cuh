@@ -344,8 +344,15 @@ inline int soft_box_rows(int W, int H, int nch, int sms) {
 }
 
 // Final gradients: box sums over the (2r+1)^2 window of the six per-pixel
-// maps and the combination of the formulas above.  One block per 32x32 tile.
+// maps and the combination of the formulas above.  One block per 32x32 tile
+// and image (blockIdx.z = 0: P1, P2, mu_l P2 -> dL; 1: Q1, Q2, mu_r Q2 ->
+// dR); the box sums slide along 8-output row segments and 4-output column
+// segments (one initial window sum each).
 constexpr int SF_T = 32;
+inline size_t soft_final_smem(int r) {
+    const size_t span = SF_T + 2 * r;
+    return (3 * span * span + 3 * span * SF_T) * 4;
+}
 
 __global__ void __launch_bounds__(256) k_soft_final(const float* __restrict__ T1L, const float* __restrict__ T1R,
                                                     const float* __restrict__ P1, const float* __restrict__ P2,
@@ -358,50 +365,88 @@ __global__ void __launch_bounds__(256) k_soft_final(const float* __restrict__ T1
     const int r = a.r, W = a.W, H = a.H;
     const int span = SF_T + 2 * r;
     const float N = (float)((2 * r + 1) * (2 * r + 1));
-    float* f = soft_sm;                     // [6][span][span] inputs
-    float* rs = soft_sm + 6 * span * span;  // [6][span][SF_T] row sums
+    const bool left = blockIdx.z == 0;
+    const float* X1 = left ? P1 : Q1;
+    const float* X2 = left ? P2 : Q2;
+    float* f = soft_sm;                     // [3][span][span] inputs
+    float* rs = soft_sm + 3 * span * span;  // [3][span][SF_T] row sums
+    float* box = soft_sm;                   // [3][SF_T][SF_T + 1] window sums (reuses f)
     const int x0 = blockIdx.x * SF_T - r, y0 = blockIdx.y * SF_T - r;
-    for (int i = threadIdx.x; i < span * span; i += 256) {
-        const int lx = i % span, ly = i / span;
-        const int gx = x0 + lx, gy = y0 + ly;
-        float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-            const size_t p = (size_t)gy * W + gx;
-            const float p2 = P2[p], q2 = Q2[p];
-            const float mul = lstats[p].x / N;
-            const float4 ur = __ldg(a.ustats + (size_t)gy * a.ustride + a.ucol0 + gx);
-            const float mur = (ur.x + ur.y) / N;
-            v[0] = P1[p]; v[1] = p2; v[2] = mul * p2;
-            v[3] = Q1[p]; v[4] = q2; v[5] = mur * q2;
+    // inputs, 4 pixels' loads in flight per thread
+    for (int i0 = threadIdx.x; i0 < span * span; i0 += 4 * 256) {
+        float v[4][3];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k * 256;
+            const int lx = i % span, ly = i / span;
+            const int gx = x0 + lx, gy = y0 + ly;
+            v[k][0] = v[k][1] = v[k][2] = 0.f;
+            if (i < span * span && gx >= 0 && gx < W && gy >= 0 && gy < H) {
+                const size_t p = (size_t)gy * W + gx;
+                const float x2 = X2[p];
+                float mu;
+                if (left) {
+                    mu = lstats[p].x / N;
+                } else {
+                    const float4 ur = __ldg(a.ustats + (size_t)gy * a.ustride + a.ucol0 + gx);
+                    mu = (ur.x + ur.y) / N;
+                }
+                v[k][0] = X1[p]; v[k][1] = x2; v[k][2] = mu * x2;
+            }
         }
 #pragma unroll
-        for (int m = 0; m < 6; ++m) f[m * span * span + i] = v[m];
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k * 256;
+            if (i < span * span) {
+#pragma unroll
+                for (int m = 0; m < 3; ++m) f[m * span * span + i] = v[k][m];
+            }
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 6 * span * SF_T; i += 256) {
-        const int m = i / (span * SF_T), rem = i % (span * SF_T);
-        const int ly = rem / SF_T, lx = rem % SF_T;
-        const float* row = f + m * span * span + ly * span + lx;
-        float s = 0.f;
-        for (int j = 0; j <= 2 * r; ++j) s += row[j];
-        rs[m * span * SF_T + ly * SF_T + lx] = s;
+    // row sums: thread = (map, staged row, segment of 8 outputs), sliding
+    for (int job = threadIdx.x; job < 3 * span * (SF_T / 8); job += 256) {
+        const int m = job / (span * (SF_T / 8)), rem = job % (span * (SF_T / 8));
+        const int ly = rem / (SF_T / 8), xs = (rem % (SF_T / 8)) * 8;
+        const float* row = f + m * span * span + ly * span + xs;
+        float sacc = 0.f;
+        for (int j = 0; j <= 2 * r; ++j) sacc += row[j];
+        float* o = rs + m * span * SF_T + ly * SF_T + xs;
+        o[0] = sacc;
+#pragma unroll
+        for (int j = 1; j < 8; ++j) {
+            sacc += row[j + 2 * r] - row[j - 1];
+            o[j] = sacc;
+        }
     }
     __syncthreads();
+    // column sums: thread = (map, column, segment of 4 outputs), sliding
+    for (int job = threadIdx.x; job < 3 * SF_T * (SF_T / 4); job += 256) {
+        const int m = job / (SF_T * (SF_T / 4)), rem = job % (SF_T * (SF_T / 4));
+        const int lx = rem % SF_T, ys = (rem / SF_T) * 4;
+        const float* col = rs + m * span * SF_T + ys * SF_T + lx;
+        float sacc = 0.f;
+        for (int j = 0; j <= 2 * r; ++j) sacc += col[j * SF_T];
+        float* o = box + m * SF_T * (SF_T + 1) + ys * (SF_T + 1) + lx;
+        o[0] = sacc;
+#pragma unroll
+        for (int j = 1; j < 4; ++j) {
+            sacc += col[(j + 2 * r) * SF_T] - col[(j - 1) * SF_T];
+            o[j * (SF_T + 1)] = sacc;
+        }
+    }
+    __syncthreads();
+    const float* T1 = left ? T1L : T1R;
+    const float* img = left ? Limg : Rimg;
+    float* gout = left ? gL : gR;
     for (int i = threadIdx.x; i < SF_T * SF_T; i += 256) {
         const int lx = i % SF_T, ly = i / SF_T;
         const int gx = blockIdx.x * SF_T + lx, gy = blockIdx.y * SF_T + ly;
         if (gx >= W || gy >= H) continue;
-        float b[6];
-#pragma unroll
-        for (int m = 0; m < 6; ++m) {
-            const float* col = rs + m * span * SF_T + ly * SF_T + lx;
-            float s = 0.f;
-            for (int j = 0; j <= 2 * r; ++j) s += col[j * SF_T];
-            b[m] = s;
-        }
+        const int o = ly * (SF_T + 1) + lx;
+        const float b0 = box[o], b1 = box[SF_T * (SF_T + 1) + o], b2 = box[2 * SF_T * (SF_T + 1) + o];
         const size_t p = (size_t)gy * W + gx;
-        gL[p] = T1L[p] - b[0] - Limg[p] * b[1] + b[2];
-        gR[p] = T1R[p] - b[3] - Rimg[p] * b[4] + b[5];
+        gout[p] = T1[p] - b0 - img[p] * b1 + b2;
     }
 }
 

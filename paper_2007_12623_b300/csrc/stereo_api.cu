@@ -1281,9 +1281,7 @@ stereo_status stereo_softargmin_bwd(stereo_handle* h, const float* left, const f
         launch_soft_box_t1(r, w.softA, L, R, W, H, nch, sa.cs, d_min, ty, w.sT1L, w.sT1R, s);
         counted();
         if (timed) { mark(h, 4, s); mark(h, 5, s); }
-        const int span = SF_T + 2 * r;
-        const size_t fsm = (size_t)(6 * span * span + 6 * span * SF_T) * 4;
-        k_soft_final<<<dim3((W + SF_T - 1) / SF_T, (H + SF_T - 1) / SF_T), 256, fsm, s>>>(
+        k_soft_final<<<dim3((W + SF_T - 1) / SF_T, (H + SF_T - 1) / SF_T, 2), 256, soft_final_smem(r), s>>>(
             w.sT1L, w.sT1R, w.sP1, w.sP2, w.sQ1, w.sQ2, w.lstats, sa, L, R, grad_left + b * npix,
             grad_right + b * npix);
         counted();
