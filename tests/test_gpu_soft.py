@@ -84,6 +84,28 @@ def test_backward_matches_oracle_gradient(dev, r, D):
     h.close()
 
 
+def test_l1_loss_many_partial_sums(dev):
+    """Three 960x540 maps (1.55 M values, the largest number of partial sums)
+    with a tenth of the pixels without a valid candidate: loss and gradient
+    against the oracle."""
+    rng = np.random.default_rng(3)
+    shape = (3, 540, 960)
+    ds = rng.uniform(0, 128, shape).astype(np.float32)
+    ds[rng.random(shape) < 0.1] = np.nan
+    gt = rng.uniform(0, 128, shape).astype(np.float32)
+    hv = ~np.isnan(ds)
+    h = _handle(32, 32, 16)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    g = torch.empty(shape, dtype=torch.float32, device=dev)
+    st.stereo_l1_loss(h, _T(ds, dev), _T(gt, dev), loss, g)
+    torch.cuda.synchronize()
+    loss_ref, g_ref = oracle.l1_loss(np.where(hv, ds, 0).astype(np.float64), hv, gt)
+    assert abs(loss.item() - loss_ref) <= 1e-5 * max(1.0, loss_ref)
+    kinks = np.abs(ds.astype(np.float64) - gt) == 0
+    assert np.all((g.cpu().numpy() == g_ref.astype(np.float32)) | kinks)
+    h.close()
+
+
 def test_autograd_l1_loss(dev):
     """torch.autograd through SoftArgminZNCC with the library's L1 loss
     reproduces the oracle's loss and gradients (batch of two crops)."""
