@@ -82,7 +82,8 @@ COST_CODE = {"none": 0, "f32": 1, "f16": 2, "bf16": 3}
 # DRAM bytes (read + write) of one launch of the workload's dominant kernel
 # from an ncu capture of the current kernel (profiles/<kernel>_<workload>.md);
 # absent where no capture of the current kernel exists.
-KERNEL_TRAFFIC = {"tissue960": 221.5e6}
+KERNEL_TRAFFIC = {"tissue960": 221.5e6,
+                  "soft8": {"k_soft_box_t1": 514.1e6, "k_soft_dA": 525.1e6}}
 COST_BYTES = {"none": 0, "f32": 4, "f16": 2, "bf16": 2}
 METRIC = "Gpix*disp/s and ms per 960x540 pair (1 B300), % of roofline, vs oracle"
 DATA = "synthetic (seeded tissue-texture generator standing in for the paper's videos)"
@@ -239,6 +240,8 @@ def soft_roofline(stage_ms, W, H, D, peaks, traffic=None):
         name, ms, b = "k_soft_dA", stage_ms["dA"], 8 * P + 36 * npix
     else:
         name, ms, b = "k_soft_box_t1", stage_ms["box_t1"], 4 * P + 16 * npix
+    if isinstance(traffic, dict):
+        traffic = traffic.get(name)
     achieved = b / (ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic, "kernel": name,
