@@ -20,6 +20,7 @@
 // 0 and contributes nothing.
 #pragma once
 #include "common.cuh"
+#include "cost.cuh"            // cp.async helpers
 
 struct SoftArgs {
     const float* cost;       // [H][W][cs] c = 1 - rho (NaN invalid)
@@ -253,8 +254,15 @@ __global__ void __launch_bounds__(256) k_soft_dA(SoftArgs a, const float* __rest
 // chunk of 32 disparities; it keeps the vertical window sums of its 32 + 2R
 // columns in registers and slides them down one row at a time (add the
 // entering row, subtract the leaving one), and the horizontal sum along the
-// run.  The T1L terms of a row go through the warp's shared tile.
+// run.  The two rows of a slide are copied into the warp's shared buffers
+// with cp.async one output row ahead, so their loads overlap the previous
+// row's horizontal pass (the window's first rows go through the same two
+// buffers alternately).  The T1L terms of a row go through the warp's
+// shared tile.
 constexpr int SOFT_BOX_THREADS = 128;
+
+__host__ __device__ constexpr int soft_box_warp_floats(int R) { return SOFT_TILE + 2 * (SOFT_RUN + 2 * R) * 32; }
+inline size_t soft_box_smem(int R) { return (size_t)(SOFT_BOX_THREADS / 32) * soft_box_warp_floats(R) * 4; }
 
 template <int R>
 __global__ void __launch_bounds__(SOFT_BOX_THREADS, 3) k_soft_box_t1(const float* __restrict__ A, const float* __restrict__ Limg,
@@ -262,9 +270,11 @@ __global__ void __launch_bounds__(SOFT_BOX_THREADS, 3) k_soft_box_t1(const float
                                                      int cs, int d_min, int ty, float* __restrict__ T1L,
                                                      float* __restrict__ T1R) {
     constexpr int NCOL = SOFT_RUN + 2 * R;
-    __shared__ float tiles[SOFT_BOX_THREADS / 32][SOFT_TILE];
+    extern __shared__ __align__(16) float box_sm[];
     const int lane = threadIdx.x & 31;
-    float* tl = tiles[threadIdx.x >> 5];
+    float* tl = box_sm + (threadIdx.x >> 5) * soft_box_warp_floats(R);
+    float* bufA = tl + SOFT_TILE;             // [NCOL][32]
+    float* bufB = bufA + NCOL * 32;           // [NCOL][32]
     const long wid = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nrun = (W + SOFT_RUN - 1) / SOFT_RUN, nband = (H + ty - 1) / ty;
     if (wid >= (long)nrun * nband * nch) return;
@@ -277,28 +287,51 @@ __global__ void __launch_bounds__(SOFT_BOX_THREADS, 3) k_soft_box_t1(const float
     float V[NCOL];
 #pragma unroll
     for (int c = 0; c < NCOL; ++c) V[c] = 0.f;
-    // adds (sign +1) or subtracts (sign -1) row yy of A (columns x0 - R ..
-    // x0 + 31 + R; the zero padding covers those outside the image, and lanes
-    // beyond cs hold zeros)
-    auto slide = [&](int yy, float sign) {
-        const float* rp = A + soft_ablk(W, nch, yy, chunk, x0 - R) + lane;
-        constexpr int B = (NCOL + 1) / 2;
-#pragma unroll
-        for (int c0 = 0; c0 < NCOL; c0 += B) {
-            float v[B];
-#pragma unroll
-            for (int c = 0; c < B; ++c)
-                if (c0 + c < NCOL) v[c] = __ldg(rp + (c0 + c) * 32);
-#pragma unroll
-            for (int c = 0; c < B; ++c)
-                if (c0 + c < NCOL) V[c0 + c] = fmaf(sign, v[c], V[c0 + c]);
-        }
+    // row yy of A (columns x0 - R .. x0 + 31 + R; the zero padding covers
+    // those outside the image, and lanes beyond cs hold zeros): NCOL x 128
+    // contiguous bytes, copied 16 bytes per lane and instruction
+    auto stage = [&](int yy, float* buf) {
+        const float* src = A + soft_ablk(W, nch, yy, chunk, x0 - R);
+        for (int i = lane; i < NCOL * 8; i += 32) cp_async16(buf + 4 * i, src + 4 * i);
     };
-    for (int yy = max(0, y0 - R); yy < min(H, y0 + R); ++yy) slide(yy, 1.f);
+    auto add_row = [&](const float* buf, float sign) {
+#pragma unroll
+        for (int c = 0; c < NCOL; ++c) V[c] = fmaf(sign, buf[c * 32 + lane], V[c]);
+    };
+    // the window's first rows y0 - R .. y0 + R - 1, two buffers in turn
+    {
+        const int ya = max(0, y0 - R), yb = min(H, y0 + R);
+        if (ya < yb) stage(ya, bufA);
+        cp_async_commit();
+        for (int yy = ya; yy < yb; ++yy) {
+            float* cur = ((yy - ya) & 1) ? bufB : bufA;
+            float* nxt = ((yy - ya) & 1) ? bufA : bufB;
+            if (yy + 1 < yb) stage(yy + 1, nxt);
+            cp_async_commit();
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+            __syncwarp();
+            add_row(cur, 1.f);
+            __syncwarp();
+        }
+        cp_async_wait_all();
+        __syncwarp();
+    }
     const int y1 = min(y0 + ty, H);
     const int d0 = d_min + chunk * 32;
+    // rows of the first output row: y0 + R enters (nothing leaves yet)
+    if (y0 + R < H) stage(y0 + R, bufA);
+    cp_async_commit();
     for (int y = y0; y < y1; ++y) {
-        if (y + R < H) slide(y + R, 1.f);
+        cp_async_wait_all();
+        __syncwarp();
+        if (y + R < H) add_row(bufA, 1.f);
+        if (y > y0 && y - R - 1 >= 0) add_row(bufB, -1.f);
+        __syncwarp();
+        if (y + 1 < y1) {                     // the next output row's two rows
+            if (y + 1 + R < H) stage(y + 1 + R, bufA);
+            if (y - R >= 0) stage(y - R, bufB);
+        }
+        cp_async_commit();
         const float* Lrow = Limg + (size_t)y * W;
         const float* Rrow = Rimg + (size_t)y * W;
         const float my_l = __ldg(Lrow + min(x0 + lane, W - 1));
@@ -332,8 +365,8 @@ __global__ void __launch_bounds__(SOFT_BOX_THREADS, 3) k_soft_box_t1(const float
         const float t = tile_row_sum(tl, lane);
         if (x0 + lane < W) atomicAdd(T1L + (size_t)y * W + x0 + lane, t);
         __syncwarp();
-        if (y - R >= 0) slide(y - R, -1.f);
     }
+    cp_async_wait_all();
 }
 
 // Band height of k_soft_box_t1: short bands while the grid would otherwise

@@ -1174,8 +1174,18 @@ static void launch_soft_box_t1(int r, const float* A, const float* L, const floa
                                int cs, int d_min, int ty, float* T1L, float* T1R, cudaStream_t s) {
     const long warps = (long)((W + SOFT_RUN - 1) / SOFT_RUN) * ((H + ty - 1) / ty) * nch;
     const unsigned g = (unsigned)((warps * 32 + SOFT_BOX_THREADS - 1) / SOFT_BOX_THREADS);
-#define SBT_CASE(RV) \
-    case RV: k_soft_box_t1<RV><<<g, SOFT_BOX_THREADS, 0, s>>>(A, L, R, W, H, nch, cs, d_min, ty, T1L, T1R); break;
+#define SBT_CASE(RV)                                                                                        \
+    case RV: {                                                                                               \
+        static bool attr = false;                                                                            \
+        if (!attr) {                                                                                         \
+            cudaFuncSetAttribute(k_soft_box_t1<RV>, cudaFuncAttributeMaxDynamicSharedMemorySize,             \
+                                 (int)soft_box_smem(RV));                                                    \
+            attr = true;                                                                                     \
+        }                                                                                                    \
+        k_soft_box_t1<RV><<<g, SOFT_BOX_THREADS, soft_box_smem(RV), s>>>(A, L, R, W, H, nch, cs, d_min, ty, T1L, \
+                                                                          T1R);                              \
+        break;                                                                                               \
+    }
     switch (r) {
         SBT_CASE(1) SBT_CASE(2) SBT_CASE(3) SBT_CASE(4) SBT_CASE(5) SBT_CASE(6) default: SBT_CASE(7)
     }
