@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(256) k_soft_dA(SoftArgs a, const float* __rest
 // shared tile.
 constexpr int SOFT_BOX_THREADS = 128;
 
-__host__ __device__ constexpr int soft_box_warp_floats(int R) { return SOFT_TILE + 2 * (SOFT_RUN + 2 * R) * 32; }
+__host__ __device__ constexpr int soft_box_warp_floats(int R) { return SOFT_TILE + 2 * (SOFT_RUN + 2 * R) * 32 + 96; }
 inline size_t soft_box_smem(int R) { return (size_t)(SOFT_BOX_THREADS / 32) * soft_box_warp_floats(R) * 4; }
 
 template <int R>
@@ -275,6 +275,8 @@ __global__ void __launch_bounds__(SOFT_BOX_THREADS, 3) k_soft_box_t1(const float
     float* tl = box_sm + (threadIdx.x >> 5) * soft_box_warp_floats(R);
     float* bufA = tl + SOFT_TILE;             // [NCOL][32]
     float* bufB = bufA + NCOL * 32;           // [NCOL][32]
+    float* rrow = bufB + NCOL * 32;           // [64] R(x0 - d0 - 31 + i), clamped into the row
+    float* rexit = rrow + 64;                 // [32] T1R sums leaving lane 31
     const long wid = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nrun = (W + SOFT_RUN - 1) / SOFT_RUN, nband = (H + ty - 1) / ty;
     if (wid >= (long)nrun * nband * nch) return;
@@ -335,11 +337,13 @@ __global__ void __launch_bounds__(SOFT_BOX_THREADS, 3) k_soft_box_t1(const float
         const float* Lrow = Limg + (size_t)y * W;
         const float* Rrow = Rimg + (size_t)y * W;
         const float my_l = __ldg(Lrow + min(x0 + lane, W - 1));
-        // R(x - d) moves one lane up per column: lane l at column x needs the
-        // value lane l - 1 used at column x - 1; lane 0 takes R(x - d_0) from
-        // a run-wide load (lane j holds R(x0 + j - d_0)).
-        const float r_lane0 = __ldg(Rrow + min(max(x0 + lane - d0, 0), W - 1));
-        float rcur = __ldg(Rrow + min(max(x0 - d, 0), W - 1));
+        // lane l at column x = x0 + j needs R(x - d), d = d0 + l: entry
+        // j - l + 31 of the run's row of R values
+        rrow[lane] = __ldg(Rrow + min(max(x0 - d0 - 31 + lane, 0), W - 1));
+        rrow[32 + lane] = __ldg(Rrow + min(max(x0 - d0 + 1 + lane, 0), W - 1));
+        // columns j with a valid candidate: x < W, 0 <= x - d < W
+        const int jlo = kin ? max(0, d - x0) : SOFT_RUN, jhi = min(W - x0, W - x0 + d);
+        __syncwarp();
         float acc = 0.f;                      // T1R partial for u = x - d
         float h = 0.f;
 #pragma unroll
@@ -347,17 +351,20 @@ __global__ void __launch_bounds__(SOFT_BOX_THREADS, 3) k_soft_box_t1(const float
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
             if (j > 0) h += V[j + 2 * R] - V[j - 1];
-            const int x = x0 + j, u = x - d;
             const float lx = __shfl_sync(0xffffffffu, my_l, j);
-            const bool ok = kin && x < W && u >= 0 && u < W;
-            tl[j * 33 + lane] = ok ? rcur * h : 0.f;
-            rcur = __shfl_up_sync(0xffffffffu, rcur, 1);
-            const float r0 = __shfl_sync(0xffffffffu, r_lane0, (j + 1) & 31);
-            if (lane == 0) rcur = r0;
+            const bool ok = j >= jlo && j < jhi;
+            tl[j * 33 + lane] = ok ? rrow[j - lane + 31] * h : 0.f;
             acc = ok ? fmaf(lx, h, acc) : acc;
-            if (lane == 31 && acc != 0.f && u >= 0 && u < W) atomicAdd(T1R + (size_t)y * W + u, acc);
+            // the sum for u = x0 + j - d0 - 31 is complete in lane 31
+            if (lane == 31) rexit[j] = acc;
             acc = __shfl_up_sync(0xffffffffu, acc, 1);
             if (lane == 0) acc = 0.f;
+        }
+        __syncwarp();
+        {
+            const float e = rexit[lane];
+            const int u = x0 + lane - d0 - 31;
+            if (e != 0.f && u >= 0 && u < W) atomicAdd(T1R + (size_t)y * W + u, e);
         }
         const int u = x0 + SOFT_RUN - d;
         if (lane > 0 && acc != 0.f && u >= 0 && u < W) atomicAdd(T1R + (size_t)y * W + u, acc);
