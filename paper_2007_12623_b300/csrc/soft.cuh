@@ -323,6 +323,17 @@ __global__ void __launch_bounds__(SOFT_BOX_THREADS, 3) k_soft_box_t1(const float
     // rows of the first output row: y0 + R enters (nothing leaves yet)
     if (y0 + R < H) stage(y0 + R, bufA);
     cp_async_commit();
+    // the row's image values (L at the run's columns; R(x0 - d0 - 31 + i),
+    // i < 64, clamped into the row), loaded one output row ahead
+    auto img_loads = [&](int yy, float& l, float& ra, float& rb) {
+        const float* Lrow = Limg + (size_t)yy * W;
+        const float* Rrow = Rimg + (size_t)yy * W;
+        l = __ldg(Lrow + min(x0 + lane, W - 1));
+        ra = __ldg(Rrow + min(max(x0 - d0 - 31 + lane, 0), W - 1));
+        rb = __ldg(Rrow + min(max(x0 - d0 + 1 + lane, 0), W - 1));
+    };
+    float nl = 0.f, nra = 0.f, nrb = 0.f;
+    if (y0 < y1) img_loads(y0, nl, nra, nrb);
     for (int y = y0; y < y1; ++y) {
         cp_async_wait_all();
         __syncwarp();
@@ -334,13 +345,12 @@ __global__ void __launch_bounds__(SOFT_BOX_THREADS, 3) k_soft_box_t1(const float
             if (y - R >= 0) stage(y - R, bufB);
         }
         cp_async_commit();
-        const float* Lrow = Limg + (size_t)y * W;
-        const float* Rrow = Rimg + (size_t)y * W;
-        const float my_l = __ldg(Lrow + min(x0 + lane, W - 1));
+        const float my_l = nl;
         // lane l at column x = x0 + j needs R(x - d), d = d0 + l: entry
         // j - l + 31 of the run's row of R values
-        rrow[lane] = __ldg(Rrow + min(max(x0 - d0 - 31 + lane, 0), W - 1));
-        rrow[32 + lane] = __ldg(Rrow + min(max(x0 - d0 + 1 + lane, 0), W - 1));
+        rrow[lane] = nra;
+        rrow[32 + lane] = nrb;
+        if (y + 1 < y1) img_loads(y + 1, nl, nra, nrb);
         // columns j with a valid candidate: x < W, 0 <= x - d < W
         const int jlo = kin ? max(0, d - x0) : SOFT_RUN, jhi = min(W - x0, W - x0 + d);
         __syncwarp();
