@@ -173,6 +173,8 @@ __global__ void __launch_bounds__(256) k_soft_dA(SoftArgs a, const float* __rest
     const float* crow = a.cost + row * a.cs + kc;
     float* arow = A + soft_ablk(a.W, nch, y, c, 0) + lane;
     float q1 = 0.f, q2 = 0.f;                     // diagonal sums for s = x - d
+    __shared__ float qexit[SOFT_MAX_CHUNKS][2][SOFT_RUN];   // sums leaving lane 31, per column
+    const bool kD = k < a.D;
 #pragma unroll
     for (int h = 0; h < 32; h += HALF) {
         float cv[HALF];
@@ -194,7 +196,9 @@ __global__ void __launch_bounds__(256) k_soft_dA(SoftArgs a, const float* __rest
             const float rho = 1.f - cv[j];
             const float isr = ur[j].z;
             float av = 0.f, v1 = 0.f, v2 = 0.f;
-            if (x < a.W && k < a.D && gs != 0.f && isl != 0.f && rho == rho && isr != 0.f) {
+            // a zero loss gradient or a window with zero variance (1/sqrt(B)
+            // = 0, rho = 0) makes every term below exactly 0
+            if (kD && x < a.W && rho == rho) {
                 float pd;                                          // 2^x, x <= 0
                 asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(pd) : "f"(fmaf(rho, l2e_tau, -l2)));
                 const float Gn = gs * pd * ((float)d - ds);       // G N
@@ -208,16 +212,23 @@ __global__ void __launch_bounds__(256) k_soft_dA(SoftArgs a, const float* __rest
             t1[(h + j) * 33 + lane] = v1;
             t2[(h + j) * 33 + lane] = v2;
             arow[(size_t)x * 32] = av;                        // 0 beyond column W - 1
-            if (lane == 31 && (q1 != 0.f || q2 != 0.f)) {
-                const int s = x - d;
-                if (s >= 0 && s < a.W) {
-                    atomicAdd(Q1 + row + s, q1);
-                    atomicAdd(Q2 + row + s, q2);
-                }
+            if (lane == 31) {                                  // complete for s = x - d
+                qexit[c][0][h + j] = q1;
+                qexit[c][1][h + j] = q2;
             }
             q1 = __shfl_up_sync(0xffffffffu, q1, 1);
             q2 = __shfl_up_sync(0xffffffffu, q2, 1);
             if (lane == 0) { q1 = 0.f; q2 = 0.f; }
+        }
+    }
+    __syncwarp();
+    {
+        // the complete sums of lane 31, column x0 + lane: s = x0 + lane - d_31
+        const float e1 = qexit[c][0][lane], e2 = qexit[c][1][lane];
+        const int se = x0 + lane - (a.d_min + c * 32 + 31);
+        if ((e1 != 0.f || e2 != 0.f) && se >= 0 && se < a.W) {
+            atomicAdd(Q1 + row + se, e1);
+            atomicAdd(Q2 + row + se, e2);
         }
     }
     // partial diagonal sums still in flight: lane l holds s = x0 + 32 - d
