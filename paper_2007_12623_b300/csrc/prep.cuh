@@ -246,23 +246,38 @@ __global__ void k_cost_border_nan(void* __restrict__ cost, int cdt, int W, int H
 // (float copy with zero padding, {S, 1/sqrt(B)} or {S_hi, S_lo, 1/sqrt(B),
 // valid}), from a float image.  Window sums in FP32 (exact for
 // integer-valued images), B = N SS - S^2 in FP64, S_lo = S mod 256.
-__global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ img, int W, int H, int r,
-                                                  PrepOut out) {
+template <int R>
+__global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ img, int W, int H, PrepOut out) {
+    constexpr int r = R;
     __shared__ float t[PSPAN][PSPAN + 1];
     __shared__ float rs[PSPAN][PT + 1];
     __shared__ float rss[PSPAN][PT + 1];
     const int x0 = blockIdx.x * PT, y0 = blockIdx.y * PT;
-    const int span = PT + 2 * r;
+    constexpr int span = PT + 2 * r;
     const int tid = threadIdx.x;
-    for (int i = tid; i < span * span; i += 256) {
-        const int ly = i / span, lx = i % span;
-        const int gx = x0 - r + lx, gy = y0 - r + ly;
-        t[ly][lx] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? img[(size_t)gy * W + gx] : 0.f;
+    {
+        // every load of the staged window issued before the first is stored
+        constexpr int NS = (span * span + 255) / 256;
+        float v[NS];
+#pragma unroll
+        for (int it = 0; it < NS; ++it) {
+            const int i = tid + it * 256;
+            const int ly = i / span, lx = i % span;
+            const int gx = x0 - r + lx, gy = y0 - r + ly;
+            v[it] = (i < span * span && gx >= 0 && gx < W && gy >= 0 && gy < H) ? img[(size_t)gy * W + gx] : 0.f;
+        }
+#pragma unroll
+        for (int it = 0; it < NS; ++it) {
+            const int i = tid + it * 256;
+            if (i < span * span) t[i / span][i % span] = v[it];
+        }
     }
     __syncthreads();
+#pragma unroll 2
     for (int i = tid; i < span * PT; i += 256) {
         const int ly = i / PT, lx = i % PT;
         float s = 0.f, ss = 0.f;
+#pragma unroll
         for (int k = 0; k <= 2 * r; ++k) {
             const float v = t[ly][lx + k];
             s += v;
@@ -284,6 +299,7 @@ __global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ img,
         const bool interior = gx >= r && gx < W - r && gy >= r && gy < H - r;
         if (interior) {
             float ss = 0.f;
+#pragma unroll
             for (int k = 0; k <= 2 * r; ++k) { s += rs[ly + k][lx]; ss += rss[ly + k][lx]; }
             B = N * (double)ss - (double)s * (double)s;
         }
@@ -300,22 +316,18 @@ __global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ img,
                 make_float4(s - lo, lo, is, interior ? 1.f : 0.f);
         }
     }
-    if (blockIdx.x == 0) {
-        const int npad = out.stride - W;
-        for (int i = tid; i < PT * npad; i += 256) {
-            const int gy = y0 + i / npad, m = i % npad;
-            if (gy >= H) break;
-            const int col = m < out.col0 ? m : W + m;
-            out.img[(size_t)gy * out.stride + col] = 0.f;
-        }
-        if (out.ustats) {
-            const int upad = out.ustride - W;
-            for (int i = tid; i < PT * upad; i += 256) {
-                const int gy = y0 + i / upad, m = i % upad;
-                if (gy >= H) break;
-                const int col = m < out.ucol0 ? m : W + m;
-                out.ustats[(size_t)gy * out.ustride + col] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+    // padding columns of rows y0 .. y0 + 31, shared among the tile row's blocks
+    const int rows = min(PT, H - y0);
+    const int npad = out.stride - W;
+    for (int i = blockIdx.x * 256 + tid; i < rows * npad; i += gridDim.x * 256) {
+        const int gy = y0 + i / npad, m = i % npad;
+        out.img[(size_t)gy * out.stride + (m < out.col0 ? m : W + m)] = 0.f;
+    }
+    if (out.ustats) {
+        const int upad = out.ustride - W;
+        for (int i = blockIdx.x * 256 + tid; i < rows * upad; i += gridDim.x * 256) {
+            const int gy = y0 + i / upad, m = i % upad;
+            out.ustats[(size_t)gy * out.ustride + (m < out.ucol0 ? m : W + m)] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
 }

@@ -1213,10 +1213,20 @@ static void soft_prepare(stereo_handle* h, const PairWs& w, const float* L, cons
     prep_layouts(W, d_min, D, K, w, pl, pr);
     dim3 sg((W + PT - 1) / PT, (H + PT - 1) / PT);
     if (timed) mark(h, 0, s);
-    k_prep_f32<<<sg, 256, 0, s>>>(L, W, H, r, pl);
-    counted();
-    k_prep_f32<<<sg, 256, 0, s>>>(R, W, H, r, pr);
-    counted();
+    for (int side = 0; side < 2; ++side) {
+        const float* img = side ? R : L;
+        const PrepOut& po = side ? pr : pl;
+        switch (r) {
+            case 1: k_prep_f32<1><<<sg, 256, 0, s>>>(img, W, H, po); break;
+            case 2: k_prep_f32<2><<<sg, 256, 0, s>>>(img, W, H, po); break;
+            case 3: k_prep_f32<3><<<sg, 256, 0, s>>>(img, W, H, po); break;
+            case 4: k_prep_f32<4><<<sg, 256, 0, s>>>(img, W, H, po); break;
+            case 5: k_prep_f32<5><<<sg, 256, 0, s>>>(img, W, H, po); break;
+            case 6: k_prep_f32<6><<<sg, 256, 0, s>>>(img, W, H, po); break;
+            default: k_prep_f32<7><<<sg, 256, 0, s>>>(img, W, H, po); break;
+        }
+        counted();
+    }
     if (timed) mark(h, 1, s);
     const int cs = cost_stride(D);
     const long nb = (W <= 2 * r || H <= 2 * r) ? (long)W * H : 2L * r * W + 2L * r * (H - 2 * r);
