@@ -515,51 +515,65 @@ __global__ void __launch_bounds__(256) k_soft_final(const float* __restrict__ T1
 // loss = mean |d_soft - gt|, grad = sign(d_soft - gt) / count (0 off V).
 __global__ void __launch_bounds__(256) k_l1_partial(const float* __restrict__ ds, const float* __restrict__ gt,
                                                     long n, double* __restrict__ part) {
-    __shared__ double ss[256];
-    __shared__ double sc[256];
-    double s = 0.0, c = 0.0;
+    __shared__ double ws[8];
+    __shared__ int wc[8];
+    // per-thread and per-warp partial sums in FP32 (a few hundred terms at
+    // most; FP64 arithmetic is slow on this part), the block's eight warp
+    // sums in FP64
+    float s = 0.f;
+    int c = 0;
     for (long i = (long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long)gridDim.x * 256) {
         const float d = ds[i];
-        if (d == d) { s += fabs((double)d - (double)gt[i]); c += 1.0; }
+        if (d == d) { s += fabsf(d - gt[i]); ++c; }
     }
-    ss[threadIdx.x] = s;
-    sc[threadIdx.x] = c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        ws[threadIdx.x >> 5] = s;
+        wc[threadIdx.x >> 5] = c;
+    }
     __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) { ss[threadIdx.x] += ss[threadIdx.x + o]; sc[threadIdx.x] += sc[threadIdx.x + o]; }
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        double ts = 0.0, tc = 0.0;
+        for (int w = 0; w < 8; ++w) { ts += ws[w]; tc += wc[w]; }
+        part[2 * blockIdx.x] = ts;
+        part[2 * blockIdx.x + 1] = tc;
     }
-    if (threadIdx.x == 0) { part[2 * blockIdx.x] = ss[0]; part[2 * blockIdx.x + 1] = sc[0]; }
 }
 
-// One block of 1024 threads adds the partial sums: strided per-thread sums,
-// then a tree in shared memory (the order is fixed, so the result is
-// deterministic).
+// One block of 1024 threads adds the partial sums: one partial per thread,
+// warp shuffles, then thread 0 over the 32 warp sums (a fixed order: the
+// result is deterministic).
 constexpr int L1_FINAL_THREADS = 1024;
 
 __global__ void __launch_bounds__(L1_FINAL_THREADS) k_l1_final(const double* __restrict__ part, int nparts,
                                                              float* __restrict__ loss,
                                                              double* __restrict__ count) {
-    __shared__ double ss[L1_FINAL_THREADS];
-    __shared__ double sc[L1_FINAL_THREADS];
+    __shared__ double ws[L1_FINAL_THREADS / 32];
+    __shared__ double wc[L1_FINAL_THREADS / 32];
     double s = 0.0, c = 0.0;
     for (int i = threadIdx.x; i < nparts; i += L1_FINAL_THREADS) {
         s += part[2 * i];
         c += part[2 * i + 1];
     }
-    ss[threadIdx.x] = s;
-    sc[threadIdx.x] = c;
-    __syncthreads();
-    for (int o = L1_FINAL_THREADS / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            ss[threadIdx.x] += ss[threadIdx.x + o];
-            sc[threadIdx.x] += sc[threadIdx.x + o];
-        }
-        __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
     }
+    if ((threadIdx.x & 31) == 0) {
+        ws[threadIdx.x >> 5] = s;
+        wc[threadIdx.x >> 5] = c;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        *loss = sc[0] > 0 ? (float)(ss[0] / sc[0]) : 0.f;
-        *count = sc[0];
+        double ts = 0.0, tc = 0.0;
+        for (int w = 0; w < L1_FINAL_THREADS / 32; ++w) { ts += ws[w]; tc += wc[w]; }
+        *loss = tc > 0 ? (float)(ts / tc) : 0.f;
+        *count = tc;
     }
 }
 
