@@ -100,7 +100,8 @@ __device__ __forceinline__ void load_slot(const float4* U, int i, float& h, floa
 // i.e. the pixels of the centre's colour on the chessboard of (x + y) & 1.
 // The vertical sums are kept per colour (V: colour 0, V2: colour 1) and so
 // are the horizontal ones; an output pixel takes the pair of its own colour.
-template <int R, int K, int CDT, bool PARTIAL, bool CB = false>
+// WTA = false: the cost volume alone (no keys, no winner bookkeeping).
+template <int R, int K, int CDT, bool PARTIAL, bool CB = false, bool WTA = true>
 __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0, int y0, int chunk) {
     static_assert(!CB || K == 2, "the CHESSBOARD form keeps two colours of sums: K = 2");
     typedef CostGeom<R> G;
@@ -306,11 +307,13 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
                 const float hsum = CB ? (((j + qbase) & 1) ? Hs2[k] : Hs[k]) : Hs[k];
                 const float num = fmaf(-sl.x, ul[s], fmaf(Nf, hsum, -t1));
                 const float av = num * sl.y;
-                const float t = fmaf(av, ui[s], ko[s]);
-                const uint32_t key = __float_as_uint(t) * mulk[k] + idxc[k];
                 cv[k] = fmaf(-av, ui[s], cf[s]);
-                best = max(best, key);
-                acc[s] = max(acc[s], key);
+                if (WTA) {
+                    const float t = fmaf(av, ui[s], ko[s]);
+                    const uint32_t key = __float_as_uint(t) * mulk[k] + idxc[k];
+                    best = max(best, key);
+                    acc[s] = max(acc[s], key);
+                }
             }
             if (CDT != CDT_NONE && do_store) {
                 if (CDT == CDT_F32) {
@@ -336,16 +339,18 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
                 }
             }
             crow += (size_t)cstride * ESZ;
-            const uint32_t red = __reduce_max_sync(0xffffffffu, best);
-            if (lane == j) myLeft = red;
-            // the oldest slot (register (j+1) mod K) moves on to the next lane
-            const int so = (j + 1) % K;
-            const uint32_t in = __shfl_sync(0xffffffffu, acc[so], (lane + 31) & 31);
-            acc[so] = lane == 0 ? 0u : in;
-            if (lane == 0) sExit[j] = in;
+            if (WTA) {
+                const uint32_t red = __reduce_max_sync(0xffffffffu, best);
+                if (lane == j) myLeft = red;
+                // the oldest slot (register (j+1) mod K) moves on to the next lane
+                const int so = (j + 1) % K;
+                const uint32_t in = __shfl_sync(0xffffffffu, acc[so], (lane + 31) & 31);
+                acc[so] = lane == 0 ? 0u : in;
+                if (lane == 0) sExit[j] = in;
+            }
         }
         __syncwarp();
-        if (lane < nsteps) {
+        if (WTA && lane < nsteps) {
             atomicMax(a.keyL + (size_t)y * W + x0 + lane, myLeft);
             const int u = x0 + lane - dc0 - 32 * K + 1;
             const uint32_t e = sExit[lane];
@@ -362,7 +367,7 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
             const int si = ((PARTIAL ? nsteps : TW) - k + 4 * K) % K;
 #pragma unroll
             for (int q = 0; q < K; ++q) e = (q == si) ? acc[q] : e;
-            if (e && u >= 0 && u < W) atomicMax(a.keyR + (size_t)y * W + u, e);
+            if (WTA && e && u >= 0 && u < W) atomicMax(a.keyR + (size_t)y * W + u, e);
         }
         cp_async_wait_all();
         __syncwarp();
@@ -376,7 +381,7 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
 // otherwise it runs as a partial unit.  The last band is likewise moved up.
 // Overlapping columns/rows are computed twice with identical results, which
 // the max-combining key maps and the plain cost stores absorb.
-template <int R, int K, int CDT, int MINB, bool CB = false>
+template <int R, int K, int CDT, int MINB, bool CB = false, bool WTA = true>
 __global__ void __launch_bounds__(32, MINB) k_cost_wta(CostArgs a) {
     extern __shared__ __align__(16) float smem[];
     typedef CostGeom<R> G;
@@ -391,8 +396,8 @@ __global__ void __launch_bounds__(32, MINB) k_cost_wta(CostArgs a) {
         else partial = true;
     }
     if (inner_h >= a.rows) y0 = min(y0, a.H - R - a.rows);
-    if (partial) cost_unit<R, K, CDT, true, CB>(a, smem, x0, y0, blockIdx.z);
-    else cost_unit<R, K, CDT, false, CB>(a, smem, x0, y0, blockIdx.z);
+    if (partial) cost_unit<R, K, CDT, true, CB, WTA>(a, smem, x0, y0, blockIdx.z);
+    else cost_unit<R, K, CDT, false, CB, WTA>(a, smem, x0, y0, blockIdx.z);
 }
 
 // Host-side launch for one window radius, explicitly instantiated per radius

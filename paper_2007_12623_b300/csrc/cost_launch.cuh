@@ -45,8 +45,15 @@ void launch_cost_rkc(CostArgs a, int rows_override, cudaStream_t s) {
     }
     a.rows = rows_override > 0 ? rows_override : cost_choose_rows(nx, nz, a.H - 2 * R, cap);
     const int ny = (a.H - 2 * R + a.rows - 1) / a.rows;
-    if constexpr (I8) k_cost_wta_i8<R, K, CDT, MINB><<<dim3(nx, ny, nz), 32, BYTES, s>>>(a);
-    else k_cost_wta<R, K, CDT, MINB, CB><<<dim3(nx, ny, nz), 32, BYTES, s>>>(a);
+    if constexpr (I8) {
+        k_cost_wta_i8<R, K, CDT, MINB><<<dim3(nx, ny, nz), 32, BYTES, s>>>(a);
+    } else if constexpr (!CB && CDT == CDT_F32) {
+        // without key maps: the cost volume alone
+        if (a.keyL) k_cost_wta<R, K, CDT, MINB, CB><<<dim3(nx, ny, nz), 32, BYTES, s>>>(a);
+        else k_cost_wta<R, K, CDT, MINB, CB, false><<<dim3(nx, ny, nz), 32, BYTES, s>>>(a);
+    } else {
+        k_cost_wta<R, K, CDT, MINB, CB><<<dim3(nx, ny, nz), 32, BYTES, s>>>(a);
+    }
 }
 
 template <int R, int K>

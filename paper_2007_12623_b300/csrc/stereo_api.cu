@@ -1233,8 +1233,9 @@ static void soft_prepare(stereo_handle* h, const PairWs& w, const float* L, cons
     k_cost_border_nan<<<(int)std::max<long>(1, std::min<long>(4096, (nb * cs + 255) / 256)), 256, 0, s>>>(
         w.cost, CDT_F32, W, H, r, cs);
     counted();
+    // the volume alone: no key maps
     CostArgs a{pl.img, pl.stride, pl.col0, pr.img, pr.stride, pr.col0, 0, w.lstats, w.ustats,
-               pr.ustride, pr.ucol0, w.keys, w.keys + (size_t)W * H, w.cost, CDT_F32, W, H, d_min, D, 0, 0, D};
+               pr.ustride, pr.ucol0, nullptr, nullptr, w.cost, CDT_F32, W, H, d_min, D, 0, 0, D};
     launch_cost(r, K, CDT_F32, a, g_cost_rows, s);
     if (timed) mark(h, 2, s);
     sa = SoftArgs{reinterpret_cast<const float*>(w.cost), cs, w.lstats, w.ustats, pr.ustride, pr.ucol0,
