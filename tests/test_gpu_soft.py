@@ -59,10 +59,13 @@ def test_forward_matches_oracle(dev, r, D, tau):
     h.close()
 
 
-@pytest.mark.parametrize("r,D", [(5, 16), (3, 12)])
-def test_backward_matches_oracle_gradient(dev, r, D):
-    """64x64 crop, candidates 0..D-1, tau = 0.1, random upstream gradient."""
-    H, W, tau = 64, 64, 0.1
+@pytest.mark.parametrize("r,D,H,W", [(5, 16, 64, 64), (3, 12, 64, 64),
+                                     (7, 40, 50, 70),    # two disparity chunks, ragged last run
+                                     (1, 33, 48, 45)])
+def test_backward_matches_oracle_gradient(dev, r, D, H, W):
+    """Crop of a tissue pair, candidates 0..D-1, tau = 0.1, random upstream
+    gradient."""
+    tau = 0.1
     L, R, gt = _crop_pair(synth.seed_for(4, 1), 30, 100, H, W)
     rng = np.random.default_rng(11)
     ds_ref, lse_ref, hv = oracle.softargmin_fwd(L, R, 0, D, r, tau)
