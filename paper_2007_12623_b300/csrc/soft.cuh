@@ -124,10 +124,6 @@ __global__ void __launch_bounds__(256) k_soft_fwd(SoftArgs a, float* __restrict_
     }
 }
 
-__device__ __forceinline__ float4 ustat(const SoftArgs& a, int y, int u) {
-    return __ldg(a.ustats + (size_t)y * a.ustride + a.ucol0 + u);
-}
-
 // A(p,d) = G alpha (stored chunk-blocked, 0 for invalid candidates), the
 // left-pixel sums P1, P2 (stored) and the right-pixel sums Q1, Q2 (added
 // into zeroed maps).  With alpha = N isl isr (isl, isr = 1/sqrt(B) of the two
@@ -175,17 +171,19 @@ __global__ void __launch_bounds__(256) k_soft_dA(SoftArgs a, const float* __rest
     float q1 = 0.f, q2 = 0.f;                     // diagonal sums for s = x - d
     __shared__ float qexit[SOFT_MAX_CHUNKS][2][SOFT_RUN];   // sums leaving lane 31, per column
     const bool kD = k < a.D;
+    // the run's 32 columns unclamped: columns past W - 1 read the next row
+    // (or the volume's slack) and the statistics rows' padding, and are
+    // masked below; lanes beyond cs read candidate cs - 1
+    const float* cptr = crow + (size_t)x0 * a.cs;
+    const float4* uptr = a.ustats + (size_t)y * a.ustride + a.ucol0 + x0 - (a.d_min + kc);
 #pragma unroll
     for (int h = 0; h < 32; h += HALF) {
         float cv[HALF];
         float4 ur[HALF];
 #pragma unroll
         for (int j = 0; j < HALF; ++j) {
-            const int x = min(x0 + h + j, a.W - 1);
-            cv[j] = __ldg(crow + (size_t)x * a.cs);
-            // right pixel x - d lies in the padded statistics rows for every
-            // candidate index below cs; lanes beyond it read pixel x - d_min
-            ur[j] = ustat(a, y, k < a.cs ? x - d : x - a.d_min);
+            cv[j] = __ldg(cptr + (size_t)(h + j) * a.cs);
+            ur[j] = __ldg(uptr + h + j);
         }
 #pragma unroll
         for (int j = 0; j < HALF; ++j) {

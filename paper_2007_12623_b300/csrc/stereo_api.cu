@@ -124,7 +124,8 @@ PairWs carve(uint8_t* base, size_t npix, int D, int cdt, int maxW, int maxH, int
     w.gl = take(npix);
     w.gr = take(npix);
     w.keys = reinterpret_cast<uint32_t*>(take(npix * 8));
-    w.cost = take(npix * (size_t)cost_stride(D) * elem_size(cdt));
+    // 32 pixels of slack: the soft-argmin kernels read whole 32-column runs
+    w.cost = take((npix + 32) * (size_t)cost_stride(D) * elem_size(cdt));
     w.wta = reinterpret_cast<int16_t*>(take(npix * 2));
     w.lr = reinterpret_cast<int16_t*>(take(npix * 2));
     w.p = reinterpret_cast<int16_t*>(take(npix * 2));
