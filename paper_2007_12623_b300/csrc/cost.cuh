@@ -385,7 +385,7 @@ template <int R, int K, int CDT, int MINB, bool CB = false, bool WTA = true>
 __global__ void __launch_bounds__(32, MINB) k_cost_wta(CostArgs a) {
     extern __shared__ __align__(16) float smem[];
     typedef CostGeom<R> G;
-    const int inner_w = a.W - 2 * R, inner_h = a.H - 2 * R;
+    const int inner_h = a.H - 2 * R;
     int x0 = R + blockIdx.x * G::TW;
     int y0 = R + blockIdx.y * a.rows;
     if (x0 >= a.W - R || y0 >= a.H - R) return;

@@ -27,8 +27,6 @@
 
 namespace {
 
-constexpr int kTH = 16;   // rows per cost work unit
-
 // Number of kernels this library has enqueued (all handles, all streams).
 std::atomic<unsigned long long> g_launches{0};
 inline void counted(int n = 1) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
