@@ -37,14 +37,30 @@ struct CostI8Smem {
     static constexpr int NRW = ((NC - 1 + K) >> 1) + 1;            // right words a lane reads
     static constexpr int OFF_RP = (G::RING * ROWB + 15) / 16 * 16;
     static constexpr int OFF_LP = (OFF_RP + NWP * 4 + 15) / 16 * 16;   // read as uint4
+    // right-pixel statistics: element i at float4 slot i + (i >> PS), K = 2^PS:
+    // lane l reads element c - K l at slot c + (c >> PS) - (K + 1) l, an
+    // offset fixed at compile time from a per-lane base, and the 8 lanes of a
+    // 16-byte access phase fall on distinct bank groups
+    static constexpr int PS = K == 4 ? 2 : 1;
+    static constexpr int NUPK = S::NU4 + (S::NU4 >> PS) + 1;
     static constexpr int OFF_U = (OFF_LP + NLP * 4 + 15) / 16 * 16;
-    static constexpr int OFF_LS = OFF_U + S::US * 4;
+    static constexpr int OFF_LS = OFF_U + 2 * NUPK * 16;
     static constexpr int OFF_EXIT = OFF_LS + S::LS * 4;
     static constexpr int BYTES = OFF_EXIT + 32 * 4;
     // the vector reads of the staged rows need these alignments
     static_assert(OFF_RP % 16 == 0 && OFF_LP % 16 == 0 && OFF_U % 16 == 0 && OFF_LS % 8 == 0,
                   "shared-memory layout of the integer cost unit");
 };
+
+// The fields of one right-pixel statistics slot (see load_slot).
+__device__ __forceinline__ void slot_fields(const float4 q, float& h, float& l, float& is, float& ko, float& cf) {
+    h = q.x;
+    l = q.y;
+    is = q.z;
+    const bool ok = q.w != 0.f;
+    ko = ok ? KEY_T_OFFSET : KEY_T_INVALID;
+    cf = ok ? 1.0f : __int_as_float(0x7fc00000);
+}
 
 // Four bytes of shared memory from any byte offset.
 __device__ __forceinline__ uint32_t lds_u32_unaligned(const int8_t* base, int o) {
@@ -72,7 +88,7 @@ __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, i
     typedef CostSmem<R, K> S;
     typedef CostI8Smem<R, K> S8;
     constexpr int TW = G::TW, NC = G::NC, RING = G::RING;
-    constexpr int ROWB = S8::ROWB, LWB = S8::LWB, NUP = S::NUP, NU4 = S::NU4;
+    constexpr int ROWB = S8::ROWB, LWB = S8::LWB, NUP = S8::NUPK, NU4 = S::NU4, PS = S8::PS;
     uint8_t* sm = reinterpret_cast<uint8_t*>(smem_f);
     int8_t* sImg = reinterpret_cast<int8_t*>(sm);                                   // [RING][ROWB]
     uint32_t* sRp = reinterpret_cast<uint32_t*>(sm + S8::OFF_RP);                   // [NWP]
@@ -102,7 +118,7 @@ __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, i
     auto stage_stats_row = [&](int gy, int buf) {
         const float4* usrc = a.ustats + (size_t)gy * a.ustride + a.ucol0 + ustart;
         float4* ud = sU + buf * NUP;
-        for (int i = lane; i < NU4; i += 32) cp_async16(ud + i + (i >> 3), usrc + i);
+        for (int i = lane; i < NU4; i += 32) cp_async16(ud + i + (i >> PS), usrc + i);
         const float2* lsrc = a.lstats + (size_t)gy * W + x0;
         float2* ld = sLs + buf * TW;
         for (int i = lane; i < TW; i += 32) cp_async8(ld + i, lsrc + min(i, W - 1 - x0));
@@ -197,13 +213,13 @@ __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, i
         }
         cp_async_commit();
 
-        const float4* U = sU + buf * NUP;
+        const float4* Ul = sU + buf * NUP - (K + 1) * lane;   // per-lane base of the slots
         const float2* Ls = sLs + buf * TW;
         float uh[K], ul[K], ui[K], ko[K], cf[K];
 #pragma unroll
         for (int k = 1; k < K; ++k) {
             const int s = (K - k) % K;
-            load_slot(U, 32 * K - 1 - K * lane - k, uh[s], ul[s], ui[s], ko[s], cf[s]);
+            slot_fields(Ul[(32 * K - 1 - k) + ((32 * K - 1 - k) >> PS)], uh[s], ul[s], ui[s], ko[s], cf[s]);
         }
         uint32_t acc[K];
 #pragma unroll
@@ -226,7 +242,8 @@ __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, i
                 for (int k = 0; k < K; ++k) Hb[k] += V[j + 2 * R][k] - V[j - 1][k];
             }
             if (PARTIAL && j >= nsteps) continue;
-            load_slot(U, j + 32 * K - 1 - K * lane, uh[j % K], ul[j % K], ui[j % K], ko[j % K], cf[j % K]);
+            slot_fields(Ul[(j + 32 * K - 1) + ((j + 32 * K - 1) >> PS)], uh[j % K], ul[j % K], ui[j % K], ko[j % K],
+                        cf[j % K]);
             const float2 sl = Ls[j];
             uint32_t best = 0u;
             float cv[K];
