@@ -381,14 +381,29 @@ __global__ void __launch_bounds__(RB_THREADS) k_refine_eq34(RefineArgs a, float*
     // [32 pixels][5 x 16 bytes]: the 80-byte pixel stride keeps the 16-byte
     // writes and reads of each quarter warp on distinct banks
     uint4* run = reinterpret_cast<uint4*>(fsm) + warp * 32 * 5;
+    // the rounds run as a loop (a smaller kernel body): round q's entries of
+    // the per-pixel arrays are picked with selects, not dynamic indexes
+    auto pick_pk = [&](int q) {
+        uint32_t v = pkv[0];
+#pragma unroll
+        for (int i = 1; i < NQ; ++i) v = q == i ? pkv[i] : v;
+        return v;
+    };
+    auto pick_d = [&](int q) {
+        float v = dv[0];
+#pragma unroll
+        for (int i = 1; i < NQ; ++i) v = q == i ? dv[i] : v;
+        return v;
+    };
     auto issue = [&](int q, int& lo, int& n, int& k0, uint4 (&ld)[4]) {
         const int gx = x0 + lane, gy = y0 + warp + 8 * q;
-        const bool live = gx < a.W && gy < a.H && pkv[q] != 0u;
+        const bool live = gx < a.W && gy < a.H && pick_pk(q) != 0u;
         int hi = -1;
         lo = 0;
         if (live) {
-            lo = max((int)ceilf(dv[q] - (float)a.search), a.d_min);
-            hi = min((int)floorf(dv[q] + (float)a.search), a.d_min + a.D - 1);
+            const float dq = pick_d(q);
+            lo = max((int)ceilf(dq - (float)a.search), a.d_min);
+            hi = min((int)floorf(dq + (float)a.search), a.d_min + a.D - 1);
         }
         n = live ? hi - lo + 1 : 0;
         const int kb = (lo - a.d_min) & ~3;
@@ -410,7 +425,7 @@ __global__ void __launch_bounds__(RB_THREADS) k_refine_eq34(RefineArgs a, float*
     int lo_c, n_c, k0_c, lo_n = 0, n_n = 0, k0_n = 0;
     uint4 ld_c[4], ld_n[4];
     issue(0, lo_c, n_c, k0_c, ld_c);
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < NQ; ++q) {
         if (q + 1 < NQ) issue(q + 1, lo_n, n_n, k0_n, ld_n);        // next round's loads in flight
         __syncwarp();
@@ -456,8 +471,8 @@ __global__ void __launch_bounds__(RB_THREADS) k_refine_eq34(RefineArgs a, float*
             // candidates lo .. lo + n - 1 in increasing order: a smaller f
             // wins, then (equal f) the one nearer to d; invalid candidates
             // and ZNCC <= 0 never win
-            const float base = (float)lo_c - dv[q];
-            int on = unpack_o(pkv[q], a.d_min);
+            const float base = (float)lo_c - pick_d(q);
+            int on = unpack_o(pick_pk(q), a.d_min);
             float bf = __int_as_float(0x7f800000), bdist = -1.f;
 #pragma unroll
             for (int j = 0; j < 11; ++j) {
