@@ -31,9 +31,9 @@ struct PrepIn {
 // writes the float image and the statistics; the padding columns of its
 // tile row are shared out among the blocks of that row.  The left image's
 // blocks also clear the winner-take-all key maps (key_clear, 2 W H words)
-// and, in tiles that touch the image border, set the cost slices of the
-// pixels whose window leaves the image to NaN (the cost kernel never visits
-// them: no candidate is valid there).
+// and set the cost slices of the pixels whose window leaves the image to NaN
+// (the cost kernel never visits them: no candidate is valid there), those
+// pixels shared out among all of the left image's blocks.
 constexpr int PT = 32;
 constexpr int PMAXR = 7;
 constexpr int PSPAN = PT + 2 * PMAXR;
@@ -186,27 +186,35 @@ __global__ void __launch_bounds__(256) k_prep(PrepIn in0, PrepIn in1, int W, int
             out.ustats[(size_t)gy * out.ustride + (m < out.ucol0 ? m : W + m)] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
-    if (left && cost && (x0 < R || x0 + PT > W - R || y0 < R || y0 + PT > H - R)) {
-        // the tile's border pixels: whole rows above R / below H - R, else the
-        // columns left of R and right of W - R; one warp per pixel
+    if (left && cost) {
+        // the cost slices of the border pixels (window leaving the image),
+        // shared out warp by warp among all blocks of the left image; 16-byte
+        // stores, lane = chunk
+        const bool all = W <= 2 * R || H <= 2 * R;         // every pixel is a border pixel
+        const int nb = all ? W * H : 2 * R * W + 2 * R * (H - 2 * R);
         const int warp = tid >> 5, lane = tid & 31;
         const int esz = cdt == CDT_F32 ? 4 : 2;
         const int nvec = cs * esz / 16;                  // 16-byte chunks per pixel (cs is a multiple of 8)
         const uint32_t nan = cdt == CDT_F32 ? 0x7fc00000u : (cdt == CDT_F16 ? 0x7e007e00u : 0x7fc07fc0u);
         const uint4 nv = make_uint4(nan, nan, nan, nan);
-        const int xl = min(max(R - x0, 0), PT);          // tile columns [0, xl) lie left of R
-        const int xr = min(max(W - R - x0, xl), PT);     // tile columns [xr, 32) lie right of W - R
-        for (int ly = warp; ly < rows; ly += 8) {
-            const int gy = y0 + ly;
-            const bool full = gy < R || gy >= H - R;
-            const int nl = full ? min(PT, W - x0) : xl;
-            const int nr = full ? 0 : max(0, min(PT, W - x0) - xr);
-            for (int q = 0; q < nl + nr; ++q) {
-                const int lx = q < nl ? q : xr + (q - nl);
-                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<char*>(cost) +
-                                                      ((size_t)gy * W + x0 + lx) * cs * esz);
-                for (int c = lane; c < nvec; c += 32) dst[c] = nv;
+        const int nwarps = gridDim.x * gridDim.y * 8;
+        for (int bi = (blockIdx.y * gridDim.x + blockIdx.x) * 8 + warp; bi < nb; bi += nwarps) {
+            int x, y;
+            if (all) {
+                x = bi % W;
+                y = bi / W;
+            } else if (bi < 2 * R * W) {                 // top and bottom rows
+                const int row = bi / W;
+                y = row < R ? row : H - 2 * R + row;
+                x = bi % W;
+            } else {                                     // left and right columns of the middle rows
+                const int m = bi - 2 * R * W;
+                y = R + m / (2 * R);
+                const int c = m % (2 * R);
+                x = c < R ? c : W - 2 * R + c;
             }
+            uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<char*>(cost) + ((size_t)y * W + x) * cs * esz);
+            for (int c = lane; c < nvec; c += 32) dst[c] = nv;
         }
     }
 }
