@@ -255,8 +255,8 @@ stereo_status stereo_stage_fill_radial(stereo_handle* h, const int16_t* in, int3
 /* Sec. II-B second hole-filling method (disc), radius <= 56: a hole takes
  * the mean (rounded half up) of the valid pixels within Euclidean distance
  * `radius` when there are at least min_count of them.  min_count < 0 means a
- * quarter of the disc's pixel count, rounded up.  Uses the handle's
- * workspace (width/height must fit the handle). */
+ * quarter of the disc's pixel count, rounded up.  Uses no workspace memory
+ * (width/height must still fit the handle). */
 stereo_status stereo_stage_fill_disc(stereo_handle* h, const int16_t* in, int32_t width, int32_t height,
                                      int32_t radius, int32_t min_count, int16_t* out,
                                      void* stream);
