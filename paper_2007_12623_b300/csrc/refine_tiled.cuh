@@ -415,7 +415,8 @@ __global__ void __launch_bounds__(RB_THREADS) k_refine_eq34(RefineArgs a, float*
             const int pn = __shfl_sync(0xffffffffu, n, p);
             const int kc = pk0 + ch * (16 / esz);                     // first cost index of the chunk
             ld[i] = make_uint4(0u, 0u, 0u, 0u);
-            if (pn > 0 && kc < cs) {
+            // 16-bit costs: the candidates lie in the run's first 48 bytes
+            if (pn > 0 && kc < cs && (esz == 4 || ch < 3)) {
                 const size_t gp = (size_t)gy * a.W + x0 + p;
                 ld[i] = __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(a.cost) +
                                                              (gp * (size_t)cs + kc) * esz));
