@@ -408,15 +408,17 @@ __global__ void __launch_bounds__(RB_THREADS) k_refine_eq34(RefineArgs a, float*
         n = live ? hi - lo + 1 : 0;
         const int kb = (lo - a.d_min) & ~3;
         k0 = esz == 4 ? kb : (kb & ~7);
+        // last candidate index (-1: none); a chunk is fetched only when it
+        // starts at or before it (the first candidate is always in chunk 0)
+        const int last = n > 0 ? lo - a.d_min + n - 1 : -1;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int p = 8 * i + (lane >> 2), ch = lane & 3;
             const int pk0 = __shfl_sync(0xffffffffu, k0, p);
-            const int pn = __shfl_sync(0xffffffffu, n, p);
+            const int plast = __shfl_sync(0xffffffffu, last, p);
             const int kc = pk0 + ch * (16 / esz);                     // first cost index of the chunk
             ld[i] = make_uint4(0u, 0u, 0u, 0u);
-            // 16-bit costs: the candidates lie in the run's first 48 bytes
-            if (pn > 0 && kc < cs && (esz == 4 || ch < 3)) {
+            if (kc <= plast) {
                 const size_t gp = (size_t)gy * a.W + x0 + p;
                 ld[i] = __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(a.cost) +
                                                              (gp * (size_t)cs + kc) * esz));
