@@ -66,9 +66,10 @@ __device__ __forceinline__ size_t soft_ablk(int W, int nch, int y, int c, int x)
     return (((size_t)y * nch + c) * soft_apitch(W) + SOFT_APAD + x) * 32;
 }
 
-// Dynamic shared memory of k_soft_fwd / k_soft_dA: two tiles per warp and
-// the cross-warp partial sums.
+// Dynamic shared memory of k_soft_dA: two tiles per warp and the cross-warp
+// partial sums; k_soft_fwd: one tile per warp.
 inline size_t soft_run_smem(int nch) { return (size_t)(2 * nch * SOFT_TILE + 2 * nch * 32) * 4; }
+inline size_t soft_fwd_smem(int nch) { return (size_t)(nch * SOFT_TILE + 2 * nch * 32) * 4; }
 
 // Lane j: sum of row j of the warp's tile.
 __device__ __forceinline__ float tile_row_sum(const float* t, int lane) {
@@ -82,15 +83,13 @@ __global__ void __launch_bounds__(256) k_soft_fwd(SoftArgs a, float* __restrict_
                                                   float* __restrict__ lse) {
     extern __shared__ float soft_run_sm[];
     const int lane = threadIdx.x & 31, c = threadIdx.x >> 5, nch = blockDim.x >> 5;
-    float* t0 = soft_run_sm + (2 * c) * SOFT_TILE;
-    float* t1 = t0 + SOFT_TILE;
-    float* red = soft_run_sm + 2 * nch * SOFT_TILE;           // [2][nch][32]
+    float* t0 = soft_run_sm + c * SOFT_TILE;                  // one tile per warp
+    float* red = soft_run_sm + nch * SOFT_TILE;               // [2][nch][32]
     const int nrun = (a.W + SOFT_RUN - 1) / SOFT_RUN;
     const int y = blockIdx.x / nrun, x0 = (blockIdx.x % nrun) * SOFT_RUN;
     const float k2 = 1.4426950408889634f / a.tau;           // log2(e) / tau
     const int k = c * 32 + lane;
     const int kc = min(k, a.cs - 1);
-    const float dv = (float)(a.d_min + k);
     const float* row = a.cost + (size_t)y * a.W * a.cs + kc;
 #pragma unroll
     for (int h = 0; h < 32; h += 16) {
@@ -104,12 +103,23 @@ __global__ void __launch_bounds__(256) k_soft_fwd(SoftArgs a, float* __restrict_
             float e = 0.f;                                                // exp((rho - 1) / tau) <= 1
             if (ok) asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"((rho - 1.f) * k2));
             t0[(h + j) * 33 + lane] = e;
-            t1[(h + j) * 33 + lane] = dv * e;
         }
     }
     __syncwarp();
-    red[c * 32 + lane] = tile_row_sum(t0, lane);
-    red[(nch + c) * 32 + lane] = tile_row_sum(t1, lane);
+    {
+        // lane j: the sums over its pixel's row of weights, plain and times
+        // the candidate disparity (the column's d)
+        const float dbase = (float)(a.d_min + c * 32);
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll 8
+        for (int i = 0; i < 32; ++i) {
+            const float e = t0[lane * 33 + i];
+            s0 += e;
+            s1 = fmaf(dbase + (float)i, e, s1);
+        }
+        red[c * 32 + lane] = s0;
+        red[(nch + c) * 32 + lane] = s1;
+    }
     __syncthreads();
     if (c == 0) {
         float s0 = 0.f, s1 = 0.f;

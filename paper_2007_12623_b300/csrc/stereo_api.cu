@@ -1258,7 +1258,7 @@ stereo_status stereo_softargmin_fwd(stereo_handle* h, const float* left, const f
         sa.tau = tau;
         const unsigned runs = (unsigned)(((width + SOFT_RUN - 1) / SOFT_RUN) * height);
         const int nch = (num_disp + 31) / 32;
-        k_soft_fwd<<<runs, 32 * nch, soft_run_smem(nch), s>>>(sa, d_soft + b * npix, lse + b * npix);
+        k_soft_fwd<<<runs, 32 * nch, soft_fwd_smem(nch), s>>>(sa, d_soft + b * npix, lse + b * npix);
         counted();
         if (timed)
             for (int k = 3; k <= STEREO_NUM_STAGES; ++k) mark(h, k, s);
