@@ -278,11 +278,14 @@ void launch_cost(int r, int K, int cdt, const CostArgs& a, int rows, cudaStream_
     counted();
 }
 
-// Opts the tiled kernels into more than 48 KB of dynamic shared memory.
+// Opts the tiled kernels into more than 48 KB of dynamic shared memory, once
+// per device (the attribute belongs to the device's context).
 void set_smem_attributes() {
-    static bool done = false;
-    if (done) return;
-    done = true;
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (bit && (done.load() & bit)) return;
     cudaFuncSetAttribute(k_refine_eq12<true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_refine_eq12<false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_refine_eq12<true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -295,6 +298,16 @@ void set_smem_attributes() {
     cudaFuncSetAttribute(k_soft_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_vote_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, VOTE_MAX_N * 8);
     cudaFuncSetAttribute(k_soft_dA, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_fill_disc_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)disc_local_smem(PT_MAX_HALO));
+    cudaFuncSetAttribute(k_soft_box_t1<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)soft_box_smem(1));
+    cudaFuncSetAttribute(k_soft_box_t1<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)soft_box_smem(2));
+    cudaFuncSetAttribute(k_soft_box_t1<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)soft_box_smem(3));
+    cudaFuncSetAttribute(k_soft_box_t1<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)soft_box_smem(4));
+    cudaFuncSetAttribute(k_soft_box_t1<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)soft_box_smem(5));
+    cudaFuncSetAttribute(k_soft_box_t1<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)soft_box_smem(6));
+    cudaFuncSetAttribute(k_soft_box_t1<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)soft_box_smem(7));
+    done.fetch_or(bit);
 }
 
 // Disparities per lane of the cost kernel for a sampling: the integer form
@@ -455,12 +468,6 @@ void run_fill_radial(const int16_t* in, int W, int H, int radius, int min_dirs, 
 // Disc fill: one tile kernel (row prefixes of the tile's window in shared
 // memory, then the queries).
 void run_fill_disc(const int16_t* in, int W, int H, int radius, int min_count, int16_t* out, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_fill_disc_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)disc_local_smem(PT_MAX_HALO));
-        attr = true;
-    }
     k_fill_disc_local<<<dim3((W + DL_TW - 1) / DL_TW, (H + DL_TH - 1) / DL_TH), DL_THREADS,
                         disc_local_smem(radius), s>>>(in, W, H, radius, min_count, out);
     counted();
@@ -1175,12 +1182,6 @@ static void launch_soft_box_t1(int r, const float* A, const float* L, const floa
     const unsigned g = (unsigned)((warps * 32 + SOFT_BOX_THREADS - 1) / SOFT_BOX_THREADS);
 #define SBT_CASE(RV)                                                                                        \
     case RV: {                                                                                               \
-        static bool attr = false;                                                                            \
-        if (!attr) {                                                                                         \
-            cudaFuncSetAttribute(k_soft_box_t1<RV>, cudaFuncAttributeMaxDynamicSharedMemorySize,             \
-                                 (int)soft_box_smem(RV));                                                    \
-            attr = true;                                                                                     \
-        }                                                                                                    \
         k_soft_box_t1<RV><<<g, SOFT_BOX_THREADS, soft_box_smem(RV), s>>>(A, L, R, W, H, nch, cs, d_min, ty, T1L, \
                                                                           T1R);                              \
         break;                                                                                               \
