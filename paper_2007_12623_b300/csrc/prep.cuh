@@ -38,6 +38,39 @@ constexpr int PT = 32;
 constexpr int PMAXR = 7;
 constexpr int PSPAN = PT + 2 * PMAXR;
 
+// The cost slices of the border pixels (window of radius R leaving the
+// image) set to NaN, shared out warp by warp among `nblocks` blocks of 256
+// threads (this one is block `bid`); 16-byte stores, lane = chunk.
+template <int R>
+__device__ __forceinline__ void border_nan_slices(void* __restrict__ cost, int cdt, int cs, int W, int H, int bid,
+                                                  int nblocks) {
+    const bool all = W <= 2 * R || H <= 2 * R;             // every pixel is a border pixel
+    const int nb = all ? W * H : 2 * R * W + 2 * R * (H - 2 * R);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int esz = cdt == CDT_F32 ? 4 : 2;
+    const int nvec = cs * esz / 16;                      // 16-byte chunks per pixel (cs is a multiple of 8)
+    const uint32_t nan = cdt == CDT_F32 ? 0x7fc00000u : (cdt == CDT_F16 ? 0x7e007e00u : 0x7fc07fc0u);
+    const uint4 nv = make_uint4(nan, nan, nan, nan);
+    for (int bi = bid * 8 + warp; bi < nb; bi += nblocks * 8) {
+        int x, y;
+        if (all) {
+            x = bi % W;
+            y = bi / W;
+        } else if (bi < 2 * R * W) {                     // top and bottom rows
+            const int row = bi / W;
+            y = row < R ? row : H - 2 * R + row;
+            x = bi % W;
+        } else {                                         // left and right columns of the middle rows
+            const int m = bi - 2 * R * W;
+            y = R + m / (2 * R);
+            const int c = m % (2 * R);
+            x = c < R ? c : W - 2 * R + c;
+        }
+        uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<char*>(cost) + ((size_t)y * W + x) * cs * esz);
+        for (int c = lane; c < nvec; c += 32) dst[c] = nv;
+    }
+}
+
 //
 // CHESSBOARD sampling (CB): the window keeps the offsets (dx, dy) with dx + dy
 // even, centre included, N = ((2r+1)^2 + 1) / 2 samples; the row pass keeps
@@ -186,76 +219,18 @@ __global__ void __launch_bounds__(256) k_prep(PrepIn in0, PrepIn in1, int W, int
             out.ustats[(size_t)gy * out.ustride + (m < out.ucol0 ? m : W + m)] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
-    if (left && cost) {
-        // the cost slices of the border pixels (window leaving the image),
-        // shared out warp by warp among all blocks of the left image; 16-byte
-        // stores, lane = chunk
-        const bool all = W <= 2 * R || H <= 2 * R;         // every pixel is a border pixel
-        const int nb = all ? W * H : 2 * R * W + 2 * R * (H - 2 * R);
-        const int warp = tid >> 5, lane = tid & 31;
-        const int esz = cdt == CDT_F32 ? 4 : 2;
-        const int nvec = cs * esz / 16;                  // 16-byte chunks per pixel (cs is a multiple of 8)
-        const uint32_t nan = cdt == CDT_F32 ? 0x7fc00000u : (cdt == CDT_F16 ? 0x7e007e00u : 0x7fc07fc0u);
-        const uint4 nv = make_uint4(nan, nan, nan, nan);
-        const int nwarps = gridDim.x * gridDim.y * 8;
-        for (int bi = (blockIdx.y * gridDim.x + blockIdx.x) * 8 + warp; bi < nb; bi += nwarps) {
-            int x, y;
-            if (all) {
-                x = bi % W;
-                y = bi / W;
-            } else if (bi < 2 * R * W) {                 // top and bottom rows
-                const int row = bi / W;
-                y = row < R ? row : H - 2 * R + row;
-                x = bi % W;
-            } else {                                     // left and right columns of the middle rows
-                const int m = bi - 2 * R * W;
-                y = R + m / (2 * R);
-                const int c = m % (2 * R);
-                x = c < R ? c : W - 2 * R + c;
-            }
-            uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<char*>(cost) + ((size_t)y * W + x) * cs * esz);
-            for (int c = lane; c < nvec; c += 32) dst[c] = nv;
-        }
-    }
-}
-
-// Cost slices of the pixels whose window leaves the image (the cost kernel
-// never visits them) are set to NaN: no candidate is valid there.  One warp
-// per border pixel, 16-byte stores.
-__global__ void k_cost_border_nan(void* __restrict__ cost, int cdt, int W, int H, int r, int cs) {
-    const bool all = W <= 2 * r || H <= 2 * r;             // every pixel is a border pixel
-    const int nb = all ? W * H : 2 * r * W + 2 * r * (H - 2 * r);
-    const int esz = cdt == CDT_F32 ? 4 : 2;
-    const int nvec = cs * esz / 16;
-    const uint32_t nan = cdt == CDT_F32 ? 0x7fc00000u : (cdt == CDT_F16 ? 0x7e007e00u : 0x7fc07fc0u);
-    const uint4 nv = make_uint4(nan, nan, nan, nan);
-    const int lane = threadIdx.x & 31;
-    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += (gridDim.x * blockDim.x) >> 5) {
-        int x, y;
-        if (all) {
-            x = b % W;
-            y = b / W;
-        } else if (b < 2 * r * W) {              // top and bottom rows
-            const int row = b / W;
-            y = row < r ? row : H - 2 * r + row;
-            x = b % W;
-        } else {                                 // left and right columns of the middle rows
-            const int m = b - 2 * r * W;
-            y = r + m / (2 * r);
-            const int c = m % (2 * r);
-            x = c < r ? c : W - 2 * r + c;
-        }
-        uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<char*>(cost) + ((size_t)y * W + x) * cs * esz);
-        for (int c = lane; c < nvec; c += 32) dst[c] = nv;
-    }
+    if (left && cost) border_nan_slices<R>(cost, cdt, cs, W, H, blockIdx.y * gridDim.x + blockIdx.x,
+                                           gridDim.x * gridDim.y);
 }
 
 // Float-image preparation for the soft-argmin path: same outputs as k_prep
 // (float copy with zero padding, {S, 1/sqrt(B)} or {S_hi, S_lo, 1/sqrt(B),
-// valid}), from a float image.  Window sums in FP32 (exact for
+// valid}, and, given `cost`, the border pixels' NaN slices of the FP32
+// volume), from a float image.  Window sums in FP32 (exact for
 // integer-valued images), B = N SS - S^2 in FP64, S_lo = S mod 256.
 template <int R>
-__global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ img, int W, int H, PrepOut out) {
+__global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ img, int W, int H, PrepOut out,
+                                                  void* __restrict__ cost, int cs) {
     constexpr int r = R;
     __shared__ float t[PSPAN][PSPAN + 1];
     __shared__ float rs[PSPAN][PT + 1];
@@ -338,4 +313,6 @@ __global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ img,
             out.ustats[(size_t)gy * out.ustride + (m < out.ucol0 ? m : W + m)] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
+    // the left image's launch: NaN cost slices of the border pixels (FP32 volume)
+    if (cost) border_nan_slices<R>(cost, CDT_F32, cs, W, H, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
 }
