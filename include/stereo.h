@@ -286,7 +286,10 @@ stereo_status stereo_stage_refine(stereo_handle* h, const int16_t* o_in, const v
  * win_radius <= 7.  Pixels without a valid candidate get NaN.
  * ---------------------------------------------------------------------- */
 
-/* Forward: d_soft and the log-sum-exp of the logits (both float B*H*W). */
+/* Forward: d_soft and the log-sum-exp of the logits (both float B*H*W).
+ * With num_disp <= 128 (one chunk of the cost kernel) the weights are summed
+ * inside the cost kernel and no cost volume is written; larger num_disp
+ * goes through the FP32 volume in the handle's workspace. */
 stereo_status stereo_softargmin_fwd(stereo_handle* h, const float* left, const float* right,
                                     int32_t batch, int32_t width, int32_t height, int32_t d_min,
                                     int32_t num_disp, int32_t win_radius, float tau, float* d_soft,

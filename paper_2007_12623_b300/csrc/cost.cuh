@@ -51,6 +51,8 @@ struct CostSmem {
     static constexpr int US = 2 * NUP * 4;             // floats (two padded rows of float4)
     static constexpr int LS = 2 * G::TW * 2;           // floats (two rows of float2)
     static constexpr int BYTES = (IMG + US + LS + 32) * 4;
+    // soft-argmin form: two [TW][33] tiles of per-lane partial sums
+    static constexpr int SOFT_BYTES = BYTES + 2 * G::TW * 33 * 4;
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -80,6 +82,12 @@ struct CostArgs {
     int W, H, d_min, D;
     int rows;                                     // output rows per work unit
     int dbase, dcount;                            // this launch covers disparities d_min + [dbase, dbase + dcount)
+    // soft-argmin form (all candidates in one chunk): per pixel the
+    // disparity expectation and the log-sum-exp instead of a stored volume
+    float* sds = nullptr;
+    float* slse = nullptr;
+    float sk2 = 0.f;                              // log2(e) / tau
+    float sinvtau = 0.f;                          // 1 / tau
 };
 
 // Statistics of right pixel i of a staged row (stored at float4 slot
@@ -101,9 +109,15 @@ __device__ __forceinline__ void load_slot(const float4* U, int i, float& h, floa
 // The vertical sums are kept per colour (V: colour 0, V2: colour 1) and so
 // are the horizontal ones; an output pixel takes the pair of its own colour.
 // WTA = false: the cost volume alone (no keys, no winner bookkeeping).
-template <int R, int K, int CDT, bool PARTIAL, bool CB = false, bool WTA = true>
+// SOFT: no volume either; each lane turns its K costs into soft-argmin
+// weights exp(-cost / tau) (0 for an invalid candidate or one beyond D) and
+// leaves their sum and disparity-weighted sum in a shared tile, and after
+// each row lane j adds up pixel j's 32 partial sums into d_soft and the
+// log-sum-exp (all candidates of a pixel in this one unit).
+template <int R, int K, int CDT, bool PARTIAL, bool CB = false, bool WTA = true, bool SOFT = false>
 __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0, int y0, int chunk) {
     static_assert(!CB || K == 2, "the CHESSBOARD form keeps two colours of sums: K = 2");
+    static_assert(!SOFT || (!WTA && !CB && CDT == CDT_NONE), "the soft form stores neither keys nor costs");
     typedef CostGeom<R> G;
     typedef CostSmem<R, K> S;
     constexpr int TW = G::TW, NC = G::NC, NCH = G::NCH, RING = G::RING;
@@ -112,6 +126,8 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
     float4* sU = reinterpret_cast<float4*>(smem + S::IMG);            // [2][NUP]
     float2* sLs = reinterpret_cast<float2*>(smem + S::IMG + S::US);   // [2][TW]
     uint32_t* sExit = reinterpret_cast<uint32_t*>(smem + S::IMG + S::US + S::LS);
+    float* sS0 = smem + S::IMG + S::US + S::LS + 32;                 // SOFT: [TW][33] weight sums
+    float* sS1 = sS0 + TW * 33;                                       // SOFT: [TW][33] weighted d sums
 
     const int lane = threadIdx.x & 31;
     const int W = a.W, H = a.H;
@@ -157,6 +173,10 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
     const int cstride = cost_stride(a.D);
     constexpr int ESZ = CDT == CDT_F32 ? 4 : 2;
     const int lbase = K * (31 - lane);
+    uint32_t inD = 0u;                                 // SOFT: bit k set when candidate k is within D
+#pragma unroll
+    for (int k = 0; k < K; ++k) inD |= (idx0 + k < a.D ? 1u : 0u) << k;
+    const float dl = (float)(dc0 + K * lane);          // SOFT: disparity of candidate k = 0
 
     float V[NC][K];
     float V2[CB ? NC : 1][K];
@@ -315,6 +335,21 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
                     acc[s] = max(acc[s], key);
                 }
             }
+            if (SOFT) {
+                float pe = 0.f, qk = 0.f;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    // exp(-cost / tau) = exp((rho - 1) / tau) <= 1; ex2(-inf) = 0
+                    const bool ok = ((inD >> k) & 1u) && cv[k] == cv[k];
+                    const float x = ok ? -cv[k] * a.sk2 : __int_as_float(0xff800000);
+                    float e;
+                    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(x));
+                    pe += e;
+                    qk = fmaf((float)k, e, qk);
+                }
+                sS0[j * 33 + lane] = pe;
+                sS1[j * 33 + lane] = fmaf(dl, pe, qk);
+            }
             if (CDT != CDT_NONE && do_store) {
                 if (CDT == CDT_F32) {
                     float* cp = reinterpret_cast<float*>(crow);
@@ -350,6 +385,18 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
             }
         }
         __syncwarp();
+        if (SOFT && lane < nsteps) {
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll 8
+            for (int i = 0; i < 32; ++i) {
+                s0 += sS0[lane * 33 + i];
+                s1 += sS1[lane * 33 + i];
+            }
+            const size_t pix = (size_t)y * W + x0 + lane;
+            const bool any = s0 > 0.f;
+            a.sds[pix] = any ? s1 / s0 : __int_as_float(0x7fc00000);
+            a.slse[pix] = any ? logf(s0) + a.sinvtau : __int_as_float(0x7fc00000);
+        }
         if (WTA && lane < nsteps) {
             atomicMax(a.keyL + (size_t)y * W + x0 + lane, myLeft);
             const int u = x0 + lane - dc0 - 32 * K + 1;
@@ -381,7 +428,7 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
 // otherwise it runs as a partial unit.  The last band is likewise moved up.
 // Overlapping columns/rows are computed twice with identical results, which
 // the max-combining key maps and the plain cost stores absorb.
-template <int R, int K, int CDT, int MINB, bool CB = false, bool WTA = true>
+template <int R, int K, int CDT, int MINB, bool CB = false, bool WTA = true, bool SOFT = false>
 __global__ void __launch_bounds__(32, MINB) k_cost_wta(CostArgs a) {
     extern __shared__ __align__(16) float smem[];
     typedef CostGeom<R> G;
@@ -396,8 +443,8 @@ __global__ void __launch_bounds__(32, MINB) k_cost_wta(CostArgs a) {
         else partial = true;
     }
     if (inner_h >= a.rows) y0 = min(y0, a.H - R - a.rows);
-    if (partial) cost_unit<R, K, CDT, true, CB, WTA>(a, smem, x0, y0, blockIdx.z);
-    else cost_unit<R, K, CDT, false, CB, WTA>(a, smem, x0, y0, blockIdx.z);
+    if (partial) cost_unit<R, K, CDT, true, CB, WTA, SOFT>(a, smem, x0, y0, blockIdx.z);
+    else cost_unit<R, K, CDT, false, CB, WTA, SOFT>(a, smem, x0, y0, blockIdx.z);
 }
 
 // Host-side launch for one window radius, explicitly instantiated per radius

@@ -1206,9 +1206,14 @@ static stereo_status check_soft(const stereo_handle* h, int B, int W, int H, int
 
 // Float window statistics + fused cost kernel (rho into the handle's cost
 // volume) for one pair of float images.
+// ds, lse != nullptr: the soft-argmin forward form of the cost kernel, which
+// writes d_soft and the log-sum-exp of the interior pixels and no volume
+// (all candidates in one chunk of 32 K); otherwise the FP32 volume.
 static void soft_prepare(stereo_handle* h, const PairWs& w, const float* L, const float* R, int W, int H,
-                         int d_min, int D, int r, SoftArgs& sa, cudaStream_t s, bool timed) {
+                         int d_min, int D, int r, SoftArgs& sa, cudaStream_t s, bool timed,
+                         float* ds = nullptr, float* lse = nullptr, float tau = 0.f) {
     const int K = pick_k(D);
+    const bool fused = ds != nullptr;
     PrepOut pl, pr;
     prep_layouts(W, d_min, D, K, w, pl, pr);
     dim3 sg((W + PT - 1) / PT, (H + PT - 1) / PT);
@@ -1217,7 +1222,7 @@ static void soft_prepare(stereo_handle* h, const PairWs& w, const float* L, cons
     for (int side = 0; side < 2; ++side) {
         const float* img = side ? R : L;
         const PrepOut& po = side ? pr : pl;
-        void* vol = side ? nullptr : w.cost;          // the left launch writes the NaN border slices
+        void* vol = side || fused ? nullptr : w.cost;   // the left launch writes the NaN border slices
         switch (r) {
             case 1: k_prep_f32<1><<<sg, 256, 0, s>>>(img, W, H, po, vol, cs); break;
             case 2: k_prep_f32<2><<<sg, 256, 0, s>>>(img, W, H, po, vol, cs); break;
@@ -1232,8 +1237,15 @@ static void soft_prepare(stereo_handle* h, const PairWs& w, const float* L, cons
     if (timed) mark(h, 1, s);
     // the volume alone: no key maps
     CostArgs a{pl.img, pl.stride, pl.col0, pr.img, pr.stride, pr.col0, 0, w.lstats, w.ustats,
-               pr.ustride, pr.ucol0, nullptr, nullptr, w.cost, CDT_F32, W, H, d_min, D, 0, 0, D};
-    launch_cost(r, K, CDT_F32, a, g_cost_rows, s);
+               pr.ustride, pr.ucol0, nullptr, nullptr, fused ? nullptr : w.cost, fused ? CDT_NONE : CDT_F32,
+               W, H, d_min, D, 0, 0, D};
+    if (fused) {
+        a.sds = ds;
+        a.slse = lse;
+        a.sk2 = 1.4426950408889634f / tau;
+        a.sinvtau = 1.f / tau;
+    }
+    launch_cost(r, K, a.cdt, a, g_cost_rows, s);
     if (timed) mark(h, 2, s);
     sa = SoftArgs{reinterpret_cast<const float*>(w.cost), cs, w.lstats, w.ustats, pr.ustride, pr.ucol0,
                   W, H, d_min, D, r, 0.f};
@@ -1248,9 +1260,22 @@ stereo_status stereo_softargmin_fwd(stereo_handle* h, const float* left, const f
     cudaStream_t s = S(stream);
     const size_t npix = (size_t)width * height;
     PairWs w = carve(h->ws, npix, h->p.num_disp, h->p.cost_dtype, h->p.max_width, h->p.max_height, 1);
+    // one disparity chunk: the cost kernel's soft form (border pixels NaN)
+    const bool fused = num_disp <= 32 * pick_k(num_disp);
+    if (fused) {
+        cudaMemsetAsync(d_soft, 0xff, (size_t)batch * npix * 4, s);
+        cudaMemsetAsync(lse, 0xff, (size_t)batch * npix * 4, s);
+    }
     for (int b = 0; b < batch; ++b) {
         const bool timed = h->timing && h->ev_ready && b == batch - 1;
         SoftArgs sa;
+        if (fused) {
+            soft_prepare(h, w, left + b * npix, right + b * npix, width, height, d_min, num_disp, win_radius, sa,
+                         s, timed, d_soft + b * npix, lse + b * npix, tau);
+            if (timed)
+                for (int k = 3; k <= STEREO_NUM_STAGES; ++k) mark(h, k, s);
+            continue;
+        }
         soft_prepare(h, w, left + b * npix, right + b * npix, width, height, d_min, num_disp, win_radius, sa, s,
                      timed);
         sa.tau = tau;

@@ -59,6 +59,25 @@ def test_forward_matches_oracle(dev, r, D, tau):
     h.close()
 
 
+def test_forward_two_chunks_matches_oracle(dev):
+    """num_disp > 128: the forward reads the FP32 volume (two disparity
+    chunks) instead of summing inside the cost kernel."""
+    H, W, D, r, tau = 40, 232, 150, 3, 0.1
+    L, R, gt = _crop_pair(synth.seed_for(4), 30, 40, H, W)
+    ds_ref, lse_ref, hv = oracle.softargmin_fwd(L, R, 0, D, r, tau)
+    assert hv.sum() > 1000
+    h = _handle(H, W, D)
+    ds = torch.empty((H, W), dtype=torch.float32, device=dev)
+    lse = torch.empty_like(ds)
+    st.stereo_softargmin_fwd(h, _T(L, dev), _T(R, dev), 0, D, r, tau, ds, lse)
+    torch.cuda.synchronize()
+    ds, lse = ds.cpu().numpy(), lse.cpu().numpy()
+    assert np.array_equal(np.isnan(ds), ~hv)
+    assert np.max(np.abs(ds[hv] - ds_ref[hv])) <= 1e-4
+    assert np.max(np.abs(lse[hv] - lse_ref[hv]) / np.maximum(1.0, np.abs(lse_ref[hv]))) <= 1e-5
+    h.close()
+
+
 @pytest.mark.parametrize("r,D,H,W", [(5, 16, 64, 64), (3, 12, 64, 64),
                                      (7, 40, 50, 70),    # two disparity chunks, ragged last run
                                      (1, 33, 48, 45)])
