@@ -51,8 +51,13 @@ struct CostSmem {
     static constexpr int US = 2 * NUP * 4;             // floats (two padded rows of float4)
     static constexpr int LS = 2 * G::TW * 2;           // floats (two rows of float2)
     static constexpr int BYTES = (IMG + US + LS + 32) * 4;
-    // soft-argmin form: two [TW][33] tiles of per-lane partial sums
+    // soft-argmin forward: two [TW][33] tiles of per-lane partial sums;
+    // backward: the row's costs [TW][CVS] (each lane's K values, later its
+    // two partial sums), the exit slots of the diagonal sums [2][32] and the
+    // per-pixel inputs of two rows [2][3][TW]
     static constexpr int SOFT_BYTES = BYTES + 2 * G::TW * 33 * 4;
+    static constexpr int CVS = K >= 2 ? 32 * K + 4 : 68;
+    static constexpr int SOFT_BWD_BYTES = BYTES + (G::TW * CVS + 64 + 6 * G::TW) * 4;
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -62,6 +67,10 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
@@ -82,13 +91,24 @@ struct CostArgs {
     int W, H, d_min, D;
     int rows;                                     // output rows per work unit
     int dbase, dcount;                            // this launch covers disparities d_min + [dbase, dbase + dcount)
-    // soft-argmin form (all candidates in one chunk): per pixel the
-    // disparity expectation and the log-sum-exp instead of a stored volume
-    float* sds = nullptr;
-    float* slse = nullptr;
+    // soft-argmin forms (all candidates in one chunk, no stored volume):
+    // SOFT_FWD writes d_soft and the log-sum-exp, SOFT_BWD reads them with
+    // the loss gradient and writes the backward pass's A volume and its
+    // per-pixel sums P1, P2 (stores) and Q1, Q2 (added into zeroed maps)
+    float* sds = nullptr;                         // d_soft (FWD: out, BWD: in)
+    float* slse = nullptr;                        // log-sum-exp (FWD: out, BWD: in)
+    const float* sgrad = nullptr;                 // BWD: dLoss / d d_soft
+    float* sA = nullptr;                          // BWD: A[y][chunk][pad + x][32]
+    int snch = 0, sapitch = 0, sapad = 0;         // BWD: chunks, columns per A row, left pad
+    float* sP1 = nullptr;
+    float* sP2 = nullptr;
+    float* sQ1 = nullptr;
+    float* sQ2 = nullptr;
     float sk2 = 0.f;                              // log2(e) / tau
     float sinvtau = 0.f;                          // 1 / tau
 };
+
+constexpr int SOFT_NONE = 0, SOFT_FWD = 1, SOFT_BWD = 2;
 
 // Statistics of right pixel i of a staged row (stored at float4 slot
 // i + i/8): window-sum split, 1/sqrt(B), and the key offset / cost value that
@@ -109,15 +129,24 @@ __device__ __forceinline__ void load_slot(const float4* U, int i, float& h, floa
 // The vertical sums are kept per colour (V: colour 0, V2: colour 1) and so
 // are the horizontal ones; an output pixel takes the pair of its own colour.
 // WTA = false: the cost volume alone (no keys, no winner bookkeeping).
-// SOFT: no volume either; each lane turns its K costs into soft-argmin
-// weights exp(-cost / tau) (0 for an invalid candidate or one beyond D) and
-// leaves their sum and disparity-weighted sum in a shared tile, and after
-// each row lane j adds up pixel j's 32 partial sums into d_soft and the
-// log-sum-exp (all candidates of a pixel in this one unit).
-template <int R, int K, int CDT, bool PARTIAL, bool CB = false, bool WTA = true, bool SOFT = false>
+// SOFT = SOFT_FWD: no volume either; each lane turns its K costs into
+// soft-argmin weights exp(-cost / tau) (0 for an invalid candidate or one
+// beyond D) and leaves their sum and disparity-weighted sum in a shared
+// tile, and after each row lane j adds up pixel j's 32 partial sums into
+// d_soft and the log-sum-exp (all candidates of a pixel in this one unit).
+// SOFT = SOFT_BWD: the unrolled pass parks each row's costs in shared
+// memory, and a second pass over the row (a loop unrolled K times only,
+// which keeps the kernel body small) forms the backward terms of each
+// candidate (soft.cuh gives the formulas): A is stored, the left-pixel sums
+// P1, P2 go through the parked row (each lane overwrites its own costs with
+// its two partial sums), and the right-pixel (diagonal) sums Q1, Q2 move
+// from lane to lane like the right winner keys, added into Q1, Q2 when they
+// leave the warp.  Units must not overlap in this form.
+template <int R, int K, int CDT, bool PARTIAL, bool CB = false, bool WTA = true, int SOFT = SOFT_NONE>
 __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0, int y0, int chunk) {
     static_assert(!CB || K == 2, "the CHESSBOARD form keeps two colours of sums: K = 2");
-    static_assert(!SOFT || (!WTA && !CB && CDT == CDT_NONE), "the soft form stores neither keys nor costs");
+    static_assert(SOFT == SOFT_NONE || (!WTA && !CB && CDT == CDT_NONE),
+                  "the soft forms store neither keys nor costs");
     typedef CostGeom<R> G;
     typedef CostSmem<R, K> S;
     constexpr int TW = G::TW, NC = G::NC, NCH = G::NCH, RING = G::RING;
@@ -126,8 +155,12 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
     float4* sU = reinterpret_cast<float4*>(smem + S::IMG);            // [2][NUP]
     float2* sLs = reinterpret_cast<float2*>(smem + S::IMG + S::US);   // [2][TW]
     uint32_t* sExit = reinterpret_cast<uint32_t*>(smem + S::IMG + S::US + S::LS);
-    float* sS0 = smem + S::IMG + S::US + S::LS + 32;                 // SOFT: [TW][33] weight sums
-    float* sS1 = sS0 + TW * 33;                                       // SOFT: [TW][33] weighted d sums
+    float* sS0 = smem + S::IMG + S::US + S::LS + 32;                 // SOFT: [TW][33] weight sums (P1)
+    float* sS1 = sS0 + TW * 33;                                       // SOFT: [TW][33] weighted d sums (P2)
+    constexpr int CVS = S::CVS;
+    float* sCv = sS0;                                                 // SOFT_BWD: [TW][CVS] parked costs
+    float* sQx = sCv + TW * CVS;                                      // SOFT_BWD: [2][32] Q1, Q2 exits
+    float* sPx = sQx + 64;                                            // SOFT_BWD: [2][3][TW] g, d_soft, lse
 
     const int lane = threadIdx.x & 31;
     const int W = a.W, H = a.H;
@@ -153,6 +186,13 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
         const float2* lsrc = a.lstats + (size_t)gy * W + x0;
         float2* ld = sLs + buf * TW;
         for (int i = lane; i < TW; i += 32) cp_async8(ld + i, lsrc + min(i, W - 1 - x0));
+        if (SOFT == SOFT_BWD && lane < TW) {
+            const size_t pix = (size_t)gy * W + x0 + min(lane, W - 1 - x0);
+            float* pd = sPx + buf * 3 * TW + lane;
+            cp_async4(pd, a.sgrad + pix);
+            cp_async4(pd + TW, a.sds + pix);
+            cp_async4(pd + 2 * TW, a.slse + pix);
+        }
     };
 
     // the first 2R+1 rows and the first statistics row
@@ -177,6 +217,14 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
 #pragma unroll
     for (int k = 0; k < K; ++k) inD |= (idx0 + k < a.D ? 1u : 0u) << k;
     const float dl = (float)(dc0 + K * lane);          // SOFT: disparity of candidate k = 0
+    float q1[K], q2[K];                                // SOFT_BWD: diagonal sums in flight
+#pragma unroll
+    for (int k = 0; k < K; ++k) { q1[k] = 0.f; q2[k] = 0.f; }
+    // SOFT_BWD: A pointer of candidate k = 0 at column x0 (chunk-blocked rows)
+    const int achunk = idx0 >> 5;
+    const bool do_astore = SOFT == SOFT_BWD && achunk < a.snch;
+    const float NoverTau = Nf * a.sinvtau, invN = 1.f / Nf;
+    const float l2e = 1.4426950408889634f;
 
     float V[NC][K];
     float V2[CB ? NC : 1][K];
@@ -335,7 +383,13 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
                     acc[s] = max(acc[s], key);
                 }
             }
-            if (SOFT) {
+            if (SOFT == SOFT_BWD) {
+                float* cvp = sCv + j * CVS + K * lane;
+                if (K == 4) *reinterpret_cast<float4*>(cvp) = make_float4(cv[0], cv[1 % K], cv[2 % K], cv[3 % K]);
+                else if (K == 2) *reinterpret_cast<float2*>(cvp) = make_float2(cv[0], cv[1 % K]);
+                else cvp[0] = cv[0];
+            }
+            if (SOFT == SOFT_FWD) {
                 float pe = 0.f, qk = 0.f;
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
@@ -385,7 +439,98 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
             }
         }
         __syncwarp();
-        if (SOFT && lane < nsteps) {
+        if (SOFT == SOFT_BWD) {
+            // the row again: slot k at step j holds the statistics of right
+            // pixel index j - K*lane - k + 32K - 1 in register (j-k) mod K
+            float bh[K], bl[K], bi[K], bko, bcf;
+#pragma unroll
+            for (int k = 1; k < K; ++k) {
+                const int s = (K - k) % K;
+                load_slot(U, 32 * K - 1 - K * lane - k, bh[s], bl[s], bi[s], bko, bcf);
+            }
+            float* arow = a.sA + (((size_t)y * a.snch + achunk) * a.sapitch + a.sapad + x0) * 32 + (idx0 & 31);
+#pragma unroll 1
+            for (int j0 = 0; j0 < TW; j0 += K) {
+#pragma unroll
+                for (int jj = 0; jj < K; ++jj) {
+                    const int j = j0 + jj;
+                    if (PARTIAL && j >= nsteps) break;
+                    load_slot(U, j + 32 * K - 1 - K * lane, bh[jj], bl[jj], bi[jj], bko, bcf);
+                    float* cvp = sCv + j * CVS + K * lane;
+                    float c4[K];
+                    if (K == 4) {
+                        const float4 t = *reinterpret_cast<const float4*>(cvp);
+                        c4[0] = t.x; c4[1 % K] = t.y; c4[2 % K] = t.z; c4[3 % K] = t.w;
+                    } else if (K == 2) {
+                        const float2 t = *reinterpret_cast<const float2*>(cvp);
+                        c4[0] = t.x; c4[1 % K] = t.y;
+                    } else {
+                        c4[0] = cvp[0];
+                    }
+                    const float2 sl = Ls[j];
+                    const float* px = sPx + buf * 3 * TW + j;
+                    const float gs = px[0] * NoverTau, ds = px[TW], l2 = px[2 * TW] * l2e;
+                    const float isl = sl.y, slx = sl.x, isl2 = isl * isl;
+                    float p1 = 0.f, p2 = 0.f, av[K];
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        const int s = (jj - k + 4 * K) % K;
+                        av[k] = 0.f;
+                        // a zero loss gradient or a zero-variance window (1/sqrt(B)
+                        // = 0, rho = 0) makes every term exactly 0
+                        if (((inD >> k) & 1u) && c4[k] == c4[k]) {
+                            const float rho = 1.f - c4[k];
+                            float pd;                                          // exp(rho / tau - lse)
+                            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(pd) : "f"(fmaf(rho, a.sk2, -l2)));
+                            const float Gn = gs * pd * ((dl + (float)k) - ds);  // G N
+                            const float isr = bi[s];
+                            av[k] = Gn * isl * isr;                            // A = G N isl isr
+                            const float ng = av[k] * invN;                     // G isl isr
+                            p1 = fmaf(ng, bh[s] + bl[s], p1);                  // A mu_r
+                            p2 = fmaf(Gn * isl2, rho, p2);                     // G rho / v_l
+                            q1[s] = fmaf(ng, slx, q1[s]);                      // A mu_l
+                            q2[s] = fmaf(Gn * isr * isr, rho, q2[s]);          // G rho / v_r
+                        }
+                    }
+                    cvp[0] = p1;                                   // this lane's own slots
+                    cvp[K >= 2 ? 1 : 32] = p2;
+                    if (do_astore) {
+                        float* ap = arow + (size_t)j * 32;
+                        if (K == 4) *reinterpret_cast<float4*>(ap) = make_float4(av[0], av[1 % K], av[2 % K], av[3 % K]);
+                        else if (K == 2) *reinterpret_cast<float2*>(ap) = make_float2(av[0], av[1 % K]);
+                        else ap[0] = av[0];
+                    }
+                    // the oldest slot moves on to the next lane; lane 0 keeps
+                    // the finished sums leaving lane 31
+                    const int so = (jj + 1) % K;
+                    const float i1 = __shfl_sync(0xffffffffu, q1[so], (lane + 31) & 31);
+                    const float i2 = __shfl_sync(0xffffffffu, q2[so], (lane + 31) & 31);
+                    q1[so] = lane == 0 ? 0.f : i1;
+                    q2[so] = lane == 0 ? 0.f : i2;
+                    if (lane == 0) { sQx[j] = i1; sQx[32 + j] = i2; }
+                }
+            }
+            __syncwarp();
+        }
+        if (SOFT == SOFT_BWD && lane < nsteps) {
+            float s0 = 0.f, s1 = 0.f;
+            const float* rowp = sCv + lane * CVS;
+#pragma unroll 8
+            for (int i = 0; i < 32; ++i) {
+                s0 += rowp[K * i];
+                s1 += rowp[K >= 2 ? K * i + 1 : 32 + i];
+            }
+            const size_t pix = (size_t)y * W + x0 + lane;
+            a.sP1[pix] = s0;
+            a.sP2[pix] = s1;
+            const int u = x0 + lane - dc0 - 32 * K + 1;
+            const float e1 = sQx[lane], e2 = sQx[32 + lane];
+            if (u >= 0 && u < W && (e1 != 0.f || e2 != 0.f)) {
+                atomicAdd(a.sQ1 + (size_t)y * W + u, e1);
+                atomicAdd(a.sQ2 + (size_t)y * W + u, e2);
+            }
+        }
+        if (SOFT == SOFT_FWD && lane < nsteps) {
             float s0 = 0.f, s1 = 0.f;
 #pragma unroll 8
             for (int i = 0; i < 32; ++i) {
@@ -415,6 +560,22 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
 #pragma unroll
             for (int q = 0; q < K; ++q) e = (q == si) ? acc[q] : e;
             if (WTA && e && u >= 0 && u < W) atomicMax(a.keyR + (size_t)y * W + u, e);
+            if (SOFT == SOFT_BWD) {
+                float e1 = 0.f, e2 = 0.f;
+#pragma unroll
+                for (int q = 0; q < K; ++q) {
+                    e1 = (q == si) ? q1[q] : e1;
+                    e2 = (q == si) ? q2[q] : e2;
+                }
+                if (u >= 0 && u < W && (e1 != 0.f || e2 != 0.f)) {
+                    atomicAdd(a.sQ1 + (size_t)y * W + u, e1);
+                    atomicAdd(a.sQ2 + (size_t)y * W + u, e2);
+                }
+            }
+        }
+        if (SOFT == SOFT_BWD) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) { q1[k] = 0.f; q2[k] = 0.f; }
         }
         cp_async_wait_all();
         __syncwarp();
@@ -428,7 +589,9 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
 // otherwise it runs as a partial unit.  The last band is likewise moved up.
 // Overlapping columns/rows are computed twice with identical results, which
 // the max-combining key maps and the plain cost stores absorb.
-template <int R, int K, int CDT, int MINB, bool CB = false, bool WTA = true, bool SOFT = false>
+// The soft backward form (sums added across units) runs a last run that
+// sticks out as a partial unit and does not move the last band.
+template <int R, int K, int CDT, int MINB, bool CB = false, bool WTA = true, int SOFT = SOFT_NONE>
 __global__ void __launch_bounds__(32, MINB) k_cost_wta(CostArgs a) {
     extern __shared__ __align__(16) float smem[];
     typedef CostGeom<R> G;
@@ -439,10 +602,10 @@ __global__ void __launch_bounds__(32, MINB) k_cost_wta(CostArgs a) {
     bool partial = false;
     if (x0 + G::TW > a.W - R) {
         const int shifted = a.W - R - G::TW;
-        if (shifted >= R && ((shifted - R) & 3) == 0) x0 = shifted;
+        if (SOFT != SOFT_BWD && shifted >= R && ((shifted - R) & 3) == 0) x0 = shifted;
         else partial = true;
     }
-    if (inner_h >= a.rows) y0 = min(y0, a.H - R - a.rows);
+    if (SOFT != SOFT_BWD && inner_h >= a.rows) y0 = min(y0, a.H - R - a.rows);
     if (partial) cost_unit<R, K, CDT, true, CB, WTA, SOFT>(a, smem, x0, y0, blockIdx.z);
     else cost_unit<R, K, CDT, false, CB, WTA, SOFT>(a, smem, x0, y0, blockIdx.z);
 }

@@ -1206,14 +1206,29 @@ static stereo_status check_soft(const stereo_handle* h, int B, int W, int H, int
 
 // Float window statistics + fused cost kernel (rho into the handle's cost
 // volume) for one pair of float images.
-// ds, lse != nullptr: the soft-argmin forward form of the cost kernel, which
-// writes d_soft and the log-sum-exp of the interior pixels and no volume
-// (all candidates in one chunk of 32 K); otherwise the FP32 volume.
+// The soft-argmin forms of the cost kernel (all candidates in one chunk of
+// 32 K, no volume): forward (A == nullptr) writes d_soft and the log-sum-exp
+// of the interior pixels; backward reads them with the loss gradient and
+// writes A, P1, P2 and adds into Q1, Q2.
+struct SoftForm {
+    float* ds;
+    float* lse;
+    const float* g;
+    float* A;
+    float *P1, *P2, *Q1, *Q2;
+    int nch;
+    float tau;
+};
+
+// All candidates in one cost-kernel chunk: the soft forms apply.
+static bool soft_fused(int D) { return D <= 32 * pick_k(D); }
+
+// f == nullptr: the FP32 volume (NaN border slices included).
 static void soft_prepare(stereo_handle* h, const PairWs& w, const float* L, const float* R, int W, int H,
                          int d_min, int D, int r, SoftArgs& sa, cudaStream_t s, bool timed,
-                         float* ds = nullptr, float* lse = nullptr, float tau = 0.f) {
+                         const SoftForm* f = nullptr) {
     const int K = pick_k(D);
-    const bool fused = ds != nullptr;
+    const bool fused = f != nullptr;
     PrepOut pl, pr;
     prep_layouts(W, d_min, D, K, w, pl, pr);
     dim3 sg((W + PT - 1) / PT, (H + PT - 1) / PT);
@@ -1240,10 +1255,19 @@ static void soft_prepare(stereo_handle* h, const PairWs& w, const float* L, cons
                pr.ustride, pr.ucol0, nullptr, nullptr, fused ? nullptr : w.cost, fused ? CDT_NONE : CDT_F32,
                W, H, d_min, D, 0, 0, D};
     if (fused) {
-        a.sds = ds;
-        a.slse = lse;
-        a.sk2 = 1.4426950408889634f / tau;
-        a.sinvtau = 1.f / tau;
+        a.sds = f->ds;
+        a.slse = f->lse;
+        a.sgrad = f->g;
+        a.sA = f->A;
+        a.snch = f->nch;
+        a.sapitch = soft_apitch(W);
+        a.sapad = SOFT_APAD;
+        a.sP1 = f->P1;
+        a.sP2 = f->P2;
+        a.sQ1 = f->Q1;
+        a.sQ2 = f->Q2;
+        a.sk2 = 1.4426950408889634f / f->tau;
+        a.sinvtau = 1.f / f->tau;
     }
     launch_cost(r, K, a.cdt, a, g_cost_rows, s);
     if (timed) mark(h, 2, s);
@@ -1261,7 +1285,7 @@ stereo_status stereo_softargmin_fwd(stereo_handle* h, const float* left, const f
     const size_t npix = (size_t)width * height;
     PairWs w = carve(h->ws, npix, h->p.num_disp, h->p.cost_dtype, h->p.max_width, h->p.max_height, 1);
     // one disparity chunk: the cost kernel's soft form (border pixels NaN)
-    const bool fused = num_disp <= 32 * pick_k(num_disp);
+    const bool fused = soft_fused(num_disp);
     if (fused) {
         cudaMemsetAsync(d_soft, 0xff, (size_t)batch * npix * 4, s);
         cudaMemsetAsync(lse, 0xff, (size_t)batch * npix * 4, s);
@@ -1270,8 +1294,10 @@ stereo_status stereo_softargmin_fwd(stereo_handle* h, const float* left, const f
         const bool timed = h->timing && h->ev_ready && b == batch - 1;
         SoftArgs sa;
         if (fused) {
+            const SoftForm f{d_soft + b * npix, lse + b * npix, nullptr, nullptr, nullptr, nullptr, nullptr,
+                             nullptr, 0, tau};
             soft_prepare(h, w, left + b * npix, right + b * npix, width, height, d_min, num_disp, win_radius, sa,
-                         s, timed, d_soft + b * npix, lse + b * npix, tau);
+                         s, timed, &f);
             if (timed)
                 for (int k = 3; k <= STEREO_NUM_STAGES; ++k) mark(h, k, s);
             continue;
@@ -1309,17 +1335,30 @@ stereo_status stereo_softargmin_bwd(stereo_handle* h, const float* left, const f
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int ty = soft_box_rows(W, H, nch, sms);
+    const bool fused = soft_fused(num_disp);
     for (int b = 0; b < batch; ++b) {
         const float* L = left + b * npix;
         const float* R = right + b * npix;
         const bool timed = h->timing && h->ev_ready && b == batch - 1;
         SoftArgs sa;
-        soft_prepare(h, w, L, R, W, H, d_min, num_disp, r, sa, s, timed);
+        if (fused) {
+            // A and the per-pixel sums from the cost kernel, the border of A zeroed
+            cudaMemsetAsync(w.sP1, 0, (size_t)((char*)w.sT1R - (char*)w.sP1) + npix * 4, s);   // P1..T1R
+            const SoftForm f{const_cast<float*>(d_soft + b * npix), const_cast<float*>(lse + b * npix),
+                             grad_dsoft + b * npix, w.softA, w.sP1, w.sP2, w.sQ1, w.sQ2, nch, tau};
+            soft_prepare(h, w, L, R, W, H, d_min, num_disp, r, sa, s, timed, &f);
+            k_soft_a_border<<<H, 256, 0, s>>>(w.softA, W, H, nch, r);
+            counted();
+        } else {
+            soft_prepare(h, w, L, R, W, H, d_min, num_disp, r, sa, s, timed);
+            sa.tau = tau;
+            cudaMemsetAsync(w.sP1, 0, (size_t)((char*)w.sT1R - (char*)w.sP1) + npix * 4, s);   // P1..T1R
+            k_soft_dA<<<runs, 32 * nch, soft_run_smem(nch), s>>>(sa, d_soft + b * npix, lse + b * npix,
+                                                                 grad_dsoft + b * npix, w.softA, w.sP1, w.sP2,
+                                                                 w.sQ1, w.sQ2);
+            counted();
+        }
         sa.tau = tau;
-        cudaMemsetAsync(w.sP1, 0, (size_t)((char*)w.sT1R - (char*)w.sP1) + npix * 4, s);   // P1..T1R
-        k_soft_dA<<<runs, 32 * nch, soft_run_smem(nch), s>>>(sa, d_soft + b * npix, lse + b * npix, grad_dsoft + b * npix, w.softA,
-                                     w.sP1, w.sP2, w.sQ1, w.sQ2);
-        counted();
         if (timed) mark(h, 3, s);
         launch_soft_box_t1(r, w.softA, L, R, W, H, nch, sa.cs, d_min, ty, w.sT1L, w.sT1R, s);
         counted();

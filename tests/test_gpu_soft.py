@@ -80,7 +80,8 @@ def test_forward_two_chunks_matches_oracle(dev):
 
 @pytest.mark.parametrize("r,D,H,W", [(5, 16, 64, 64), (3, 12, 64, 64),
                                      (7, 40, 50, 70),    # two disparity chunks, ragged last run
-                                     (1, 33, 48, 45)])
+                                     (1, 33, 48, 45),
+                                     (3, 150, 32, 212)])  # D > 128: through the FP32 volume
 def test_backward_matches_oracle_gradient(dev, r, D, H, W):
     """Crop of a tissue pair, candidates 0..D-1, tau = 0.1, random upstream
     gradient."""
