@@ -227,25 +227,43 @@ def cost_kernel_roofline(problems, cost_ms, peaks, sm_count, kernel, traffic=Non
             "peak_source": f"{sm_count} SMs x 128 lanes x {peaks['sm_max_mhz']:.0f} MHz"}
 
 
-def soft_roofline(stage_ms, W, H, D, peaks, traffic=None):
-    """Roofline of the dominant soft-argmin backward kernel (both are
-    HBM-bound streams):
-      k_soft_dA      reads the FP32 cost volume and writes the A volume
-                     (8 B per (p,d)), per pixel reads g, d_soft, lse and the
-                     left statistics (20 B) and writes P1, P2, Q1, Q2 (16 B);
+def soft_roofline(stage_ms, W, H, D, peaks, sm_count, traffic=None):
+    """Roofline of the dominant soft-argmin backward kernel.
+      cost kernel, backward form (D <= 128, stage "cost"): per (p,d) 25
+                     FP32 issue slots (9 for the ZNCC as in the cost kernel's
+                     count without the winner, 16 for the backward terms: the
+                     exponent and its argument, G, A, the two P and two Q
+                     terms) and the A store (4 B); per pixel it reads both
+                     images, both statistics maps, g, d_soft and lse and
+                     writes P1, P2 and adds into Q1, Q2 (60 B).  The bound is
+                     whichever of the ALU time (128 lanes per SM per clock)
+                     and the HBM time is longer.
+      k_soft_dA      (D > 128, stage "dA") reads the FP32 cost volume and
+                     writes the A volume (8 B per (p,d)), per pixel reads g,
+                     d_soft, lse and the left statistics (20 B) and writes
+                     P1, P2, Q1, Q2 (16 B);
       k_soft_box_t1  reads the A volume once (4 B per (p,d)), per pixel reads
                      both images (8 B) and adds into T1L, T1R (8 B)."""
     P, npix = W * H * D, W * H
-    if stage_ms["dA"] >= stage_ms["box_t1"]:
-        name, ms, b = "k_soft_dA", stage_ms["dA"], 8 * P + 36 * npix
-    else:
-        name, ms, b = "k_soft_box_t1", stage_ms["box_t1"], 4 * P + 16 * npix
+    fused = D <= 128
+    first = ("k_cost_wta (soft backward form)", stage_ms["cost"], 4 * P + 60 * npix, 25 * P) if fused else \
+        ("k_soft_dA", stage_ms["dA"], 8 * P + 36 * npix, 0)
+    second = ("k_soft_box_t1", stage_ms["box_t1"], 4 * P + 16 * npix, 0)
+    name, ms, b, ops = first if first[1] >= second[1] else second
     if isinstance(traffic, dict):
         traffic = traffic.get(name)
-    achieved = b / (ms * 1e-3) / 1e9
+    dur = ms * 1e-3
+    alu_peak = sm_count * 128 * peaks["sm_max_mhz"] * 1e6
+    if ops and ops / alu_peak > b / (peaks["hbm_gbs"] * 1e9):
+        achieved = ops / dur / 1e12
+        return {"bound": "alu", "achieved": round(achieved, 2), "peak": round(alu_peak / 1e12, 2),
+                "unit": "Tops/s", "frac": round(achieved / (alu_peak / 1e12), 4), "traffic": traffic,
+                "kernel": name, "algorithmic_ops": ops, "algorithmic_bytes": b, "kernel_ms": round(ms, 4),
+                "peak_source": f"{sm_count} SMs x 128 lanes x {peaks['sm_max_mhz']:.0f} MHz"}
+    achieved = b / dur / 1e9
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic, "kernel": name,
-            "algorithmic_bytes": b, "kernel_ms": round(ms, 4),
+            "algorithmic_bytes": b, "algorithmic_ops": ops, "kernel_ms": round(ms, 4),
             "peak_source": peaks["source"] + " (hbm_gbs)"}
 
 
@@ -667,7 +685,8 @@ def run_soft_step(args, wl, rank, world, dev):
     if rank != 0:
         return None
     peaks = load_peaks()
-    roof = soft_roofline(bwd_ms, W, H, D, peaks, KERNEL_TRAFFIC.get(args.workload))
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof = soft_roofline(bwd_ms, W, H, D, peaks, sm_count, KERNEL_TRAFFIC.get(args.workload))
     line = _base_line(args, world, value, t_max, "f32", {
         "workload": args.workload, "batch": B, "width": W, "height": H, "num_disp": D,
         "window": 2 * r + 1, "tau": tau, "loss": "L1(d_soft, ground truth), mean over valid pixels",

@@ -442,11 +442,18 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
         if (SOFT == SOFT_BWD) {
             // the row again: slot k at step j holds the statistics of right
             // pixel index j - K*lane - k + 32K - 1 in register (j-k) mod K
-            float bh[K], bl[K], bi[K], bko, bcf;
+            // (kept per slot: the window sum S_r, 1/sqrt(B_r) and its square)
+            float bS[K], bi[K], bi2[K], bko, bcf;
+            auto slot = [&](int i, float& S_, float& is_, float& is2_) {
+                float hh, ll;
+                load_slot(U, i, hh, ll, is_, bko, bcf);
+                S_ = hh + ll;
+                is2_ = is_ * is_;
+            };
 #pragma unroll
             for (int k = 1; k < K; ++k) {
                 const int s = (K - k) % K;
-                load_slot(U, 32 * K - 1 - K * lane - k, bh[s], bl[s], bi[s], bko, bcf);
+                slot(32 * K - 1 - K * lane - k, bS[s], bi[s], bi2[s]);
             }
             float* arow = a.sA + (((size_t)y * a.snch + achunk) * a.sapitch + a.sapad + x0) * 32 + (idx0 & 31);
 #pragma unroll 1
@@ -455,7 +462,7 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
                 for (int jj = 0; jj < K; ++jj) {
                     const int j = j0 + jj;
                     if (PARTIAL && j >= nsteps) break;
-                    load_slot(U, j + 32 * K - 1 - K * lane, bh[jj], bl[jj], bi[jj], bko, bcf);
+                    slot(j + 32 * K - 1 - K * lane, bS[jj], bi[jj], bi2[jj]);
                     float* cvp = sCv + j * CVS + K * lane;
                     float c4[K];
                     if (K == 4) {
@@ -469,8 +476,13 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
                     }
                     const float2 sl = Ls[j];
                     const float* px = sPx + buf * 3 * TW + j;
-                    const float gs = px[0] * NoverTau, ds = px[TW], l2 = px[2 * TW] * l2e;
-                    const float isl = sl.y, slx = sl.x, isl2 = isl * isl;
+                    // G N = p_d g N (d - d_soft) / tau with p_d = exp(rho / tau
+                    // - lse) = 2^(base - c log2(e) / tau), base = (1 / tau - lse)
+                    // log2(e), c = 1 - rho; the isl factors of P1, P2 are
+                    // applied once per pixel
+                    const float gs = px[0] * NoverTau, gsds = gs * px[TW];
+                    const float base = a.sk2 - px[2 * TW] * l2e;
+                    const float isl = sl.y, c1 = sl.x * isl * invN;   // S_l isl / N
                     float p1 = 0.f, p2 = 0.f, av[K];
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
@@ -479,21 +491,20 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
                         // a zero loss gradient or a zero-variance window (1/sqrt(B)
                         // = 0, rho = 0) makes every term exactly 0
                         if (((inD >> k) & 1u) && c4[k] == c4[k]) {
-                            const float rho = 1.f - c4[k];
                             float pd;                                          // exp(rho / tau - lse)
-                            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(pd) : "f"(fmaf(rho, a.sk2, -l2)));
-                            const float Gn = gs * pd * ((dl + (float)k) - ds);  // G N
-                            const float isr = bi[s];
-                            av[k] = Gn * isl * isr;                            // A = G N isl isr
-                            const float ng = av[k] * invN;                     // G isl isr
-                            p1 = fmaf(ng, bh[s] + bl[s], p1);                  // A mu_r
-                            p2 = fmaf(Gn * isl2, rho, p2);                     // G rho / v_l
-                            q1[s] = fmaf(ng, slx, q1[s]);                      // A mu_l
-                            q2[s] = fmaf(Gn * isr * isr, rho, q2[s]);          // G rho / v_r
+                            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(pd) : "f"(fmaf(c4[k], -a.sk2, base)));
+                            const float Gn = pd * fmaf(gs, dl + (float)k, -gsds);   // G N
+                            const float t = Gn * bi[s];                        // G N isr
+                            av[k] = t * isl;                                   // A = G N isl isr
+                            p1 = fmaf(t, bS[s], p1);                           // (A mu_r) N / isl
+                            q1[s] = fmaf(t, c1, q1[s]);                        // A mu_l
+                            const float u = fmaf(-Gn, c4[k], Gn);              // G N rho
+                            p2 += u;                                           // (G rho / v_l) / isl^2
+                            q2[s] = fmaf(u, bi2[s], q2[s]);                    // G rho / v_r
                         }
                     }
-                    cvp[0] = p1;                                   // this lane's own slots
-                    cvp[K >= 2 ? 1 : 32] = p2;
+                    cvp[0] = p1 * (isl * invN);                    // this lane's own slots
+                    cvp[K >= 2 ? 1 : 32] = p2 * (isl * isl);
                     if (do_astore) {
                         float* ap = arow + (size_t)j * 32;
                         if (K == 4) *reinterpret_cast<float4*>(ap) = make_float4(av[0], av[1 % K], av[2 % K], av[3 % K]);

@@ -1347,7 +1347,7 @@ stereo_status stereo_softargmin_bwd(stereo_handle* h, const float* left, const f
             const SoftForm f{const_cast<float*>(d_soft + b * npix), const_cast<float*>(lse + b * npix),
                              grad_dsoft + b * npix, w.softA, w.sP1, w.sP2, w.sQ1, w.sQ2, nch, tau};
             soft_prepare(h, w, L, R, W, H, d_min, num_disp, r, sa, s, timed, &f);
-            k_soft_a_border<<<H, 256, 0, s>>>(w.softA, W, H, nch, r);
+            k_soft_a_border<<<dim3(H, nch), 256, 0, s>>>(w.softA, W, H, nch, r);
             counted();
         } else {
             soft_prepare(h, w, L, R, W, H, d_min, num_disp, r, sa, s, timed);
