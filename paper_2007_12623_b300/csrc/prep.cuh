@@ -227,7 +227,9 @@ __global__ void __launch_bounds__(256) k_prep(PrepIn in0, PrepIn in1, int W, int
 // (float copy with zero padding, {S, 1/sqrt(B)} or {S_hi, S_lo, 1/sqrt(B),
 // valid}, and, given `cost`, the border pixels' NaN slices of the FP32
 // volume), from a float image.  Window sums in FP32 (exact for
-// integer-valued images), B = N SS - S^2 in FP64, S_lo = S mod 256.
+// integer-valued images), B = N SS - S^2 from the two products and their
+// exact rounding errors (fma; within about one rounding of the exact value,
+// without the slow FP64 pipe), S_lo = S mod 256.
 template <int R>
 __global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ img, int W, int H, PrepOut out,
                                                   void* __restrict__ cost, int cs) {
@@ -270,27 +272,26 @@ __global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ img,
         rss[ly][lx] = ss;
     }
     __syncthreads();
-    const double N = (double)((2 * r + 1) * (2 * r + 1));
+    constexpr float Nf = (float)((2 * r + 1) * (2 * r + 1));
     for (int i = tid; i < PT * PT; i += 256) {
         const int ly = i / PT, lx = i % PT;
         const int gx = x0 + lx, gy = y0 + ly;
         if (gx >= W || gy >= H) continue;
         const size_t gi = (size_t)gy * W + gx;
         out.img[(size_t)gy * out.stride + out.col0 + gx] = t[ly + r][lx + r];
-        float s = 0.f;
-        double B = 0.0;
+        float s = 0.f, B = 0.f;
         const bool interior = gx >= r && gx < W - r && gy >= r && gy < H - r;
         if (interior) {
             float ss = 0.f;
 #pragma unroll
             for (int k = 0; k <= 2 * r; ++k) { s += rs[ly + k][lx]; ss += rss[ly + k][lx]; }
-            B = N * (double)ss - (double)s * (double)s;
+            const float q = __fmul_rn(Nf, ss), p = __fmul_rn(s, s);   // not contracted into the fmas
+            B = __fsub_rn(q, p) + (fmaf(Nf, ss, -q) - fmaf(s, s, -p));
         }
         float is = 0.f;
-        if (B > 0.0) {
-            const float fb = (float)B;
-            const float y = rsqrtf(fb);
-            is = y * fmaf(-0.5f * fb * y, y, 1.5f);
+        if (B > 0.f) {
+            const float y = rsqrtf(B);
+            is = y * fmaf(-0.5f * B * y, y, 1.5f);
         }
         if (out.lstats) out.lstats[gi] = make_float2(s, is);
         if (out.ustats) {
