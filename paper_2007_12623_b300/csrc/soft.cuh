@@ -441,6 +441,7 @@ inline size_t soft_final_smem(int r) {
     return (3 * span * span + 3 * span * SF_T) * 4;
 }
 
+template <int R>
 __global__ void __launch_bounds__(256) k_soft_final(const float* __restrict__ T1L, const float* __restrict__ T1R,
                                                     const float* __restrict__ P1, const float* __restrict__ P2,
                                                     const float* __restrict__ Q1, const float* __restrict__ Q2,
@@ -449,9 +450,10 @@ __global__ void __launch_bounds__(256) k_soft_final(const float* __restrict__ T1
                                                     const float* __restrict__ Rimg,
                                                     float* __restrict__ gL, float* __restrict__ gR) {
     extern __shared__ __align__(16) float soft_sm[];
-    const int r = a.r, W = a.W, H = a.H;
-    const int span = SF_T + 2 * r;
-    const float N = (float)((2 * r + 1) * (2 * r + 1));
+    constexpr int r = R;
+    const int W = a.W, H = a.H;
+    constexpr int span = SF_T + 2 * r;
+    constexpr float invN = 1.f / (float)((2 * r + 1) * (2 * r + 1));
     const bool left = blockIdx.z == 0;
     const float* X1 = left ? P1 : Q1;
     const float* X2 = left ? P2 : Q2;
@@ -473,10 +475,10 @@ __global__ void __launch_bounds__(256) k_soft_final(const float* __restrict__ T1
                 const float x2 = X2[p];
                 float mu;
                 if (left) {
-                    mu = lstats[p].x / N;
+                    mu = lstats[p].x * invN;
                 } else {
                     const float4 ur = __ldg(a.ustats + (size_t)gy * a.ustride + a.ucol0 + gx);
-                    mu = (ur.x + ur.y) / N;
+                    mu = (ur.x + ur.y) * invN;
                 }
                 v[k][0] = X1[p]; v[k][1] = x2; v[k][2] = mu * x2;
             }

@@ -294,7 +294,6 @@ void set_smem_attributes() {
     cudaFuncSetAttribute(k_refine_eq34<false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_refine_eq34<true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_refine_eq34<false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_soft_final, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_soft_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_vote_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, VOTE_MAX_N * 8);
     cudaFuncSetAttribute(k_soft_dA, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -1315,6 +1314,27 @@ stereo_status stereo_softargmin_fwd(stereo_handle* h, const float* left, const f
     return last_error();
 }
 
+// k_soft_final for the window radius r (compile-time radius: unrolled sums).
+static void launch_soft_final(int r, dim3 grid, const PairWs& w, const SoftArgs& sa, const float* L, const float* R,
+                              float* gL, float* gR, cudaStream_t s) {
+#define SOFT_FINAL_CASE(RR)                                                                                  \
+    case RR:                                                                                                 \
+        k_soft_final<RR><<<grid, 256, soft_final_smem(RR), s>>>(w.sT1L, w.sT1R, w.sP1, w.sP2, w.sQ1, w.sQ2, \
+                                                                w.lstats, sa, L, R, gL, gR);                 \
+        break;
+    switch (r) {
+        SOFT_FINAL_CASE(1)
+        SOFT_FINAL_CASE(2)
+        SOFT_FINAL_CASE(3)
+        SOFT_FINAL_CASE(4)
+        SOFT_FINAL_CASE(5)
+        SOFT_FINAL_CASE(6)
+        default: k_soft_final<7><<<grid, 256, soft_final_smem(7), s>>>(w.sT1L, w.sT1R, w.sP1, w.sP2, w.sQ1, w.sQ2,
+                                                                     w.lstats, sa, L, R, gL, gR);
+    }
+#undef SOFT_FINAL_CASE
+}
+
 stereo_status stereo_softargmin_bwd(stereo_handle* h, const float* left, const float* right, int32_t batch,
                                     int32_t width, int32_t height, int32_t d_min, int32_t num_disp,
                                     int32_t win_radius, float tau, const float* d_soft, const float* lse,
@@ -1363,9 +1383,8 @@ stereo_status stereo_softargmin_bwd(stereo_handle* h, const float* left, const f
         launch_soft_box_t1(r, w.softA, L, R, W, H, nch, sa.cs, d_min, ty, w.sT1L, w.sT1R, s);
         counted();
         if (timed) { mark(h, 4, s); mark(h, 5, s); }
-        k_soft_final<<<dim3((W + SF_T - 1) / SF_T, (H + SF_T - 1) / SF_T, 2), 256, soft_final_smem(r), s>>>(
-            w.sT1L, w.sT1R, w.sP1, w.sP2, w.sQ1, w.sQ2, w.lstats, sa, L, R, grad_left + b * npix,
-            grad_right + b * npix);
+        launch_soft_final(r, dim3((W + SF_T - 1) / SF_T, (H + SF_T - 1) / SF_T, 2), w, sa, L, R, grad_left + b * npix,
+                          grad_right + b * npix, s);
         counted();
         if (timed) mark(h, 6, s);
     }
