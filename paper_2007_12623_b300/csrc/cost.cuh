@@ -480,28 +480,34 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
                     // - lse) = 2^(base - c log2(e) / tau), base = (1 / tau - lse)
                     // log2(e), c = 1 - rho; the isl factors of P1, P2 are
                     // applied once per pixel
-                    const float gs = px[0] * NoverTau, gsds = gs * px[TW];
+                    // a pixel without a valid candidate has d_soft = NaN: its
+                    // terms are all 0, so its gradient is taken as 0
+                    const float dsv = px[TW];
+                    const bool pv = dsv == dsv;
+                    const float gs = pv ? px[0] * NoverTau : 0.f, gsds = pv ? gs * dsv : 0.f;
                     const float base = a.sk2 - px[2 * TW] * l2e;
                     const float isl = sl.y, c1 = sl.x * isl * invN;   // S_l isl / N
                     float p1 = 0.f, p2 = 0.f, av[K];
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
                         const int s = (jj - k + 4 * K) % K;
-                        av[k] = 0.f;
-                        // a zero loss gradient or a zero-variance window (1/sqrt(B)
-                        // = 0, rho = 0) makes every term exactly 0
-                        if (((inD >> k) & 1u) && c4[k] == c4[k]) {
-                            float pd;                                          // exp(rho / tau - lse)
-                            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(pd) : "f"(fmaf(c4[k], -a.sk2, base)));
-                            const float Gn = pd * fmaf(gs, dl + (float)k, -gsds);   // G N
-                            const float t = Gn * bi[s];                        // G N isr
-                            av[k] = t * isl;                                   // A = G N isl isr
-                            p1 = fmaf(t, bS[s], p1);                           // (A mu_r) N / isl
-                            q1[s] = fmaf(t, c1, q1[s]);                        // A mu_l
-                            const float u = fmaf(-Gn, c4[k], Gn);              // G N rho
-                            p2 += u;                                           // (G rho / v_l) / isl^2
-                            q2[s] = fmaf(u, bi2[s], q2[s]);                    // G rho / v_r
-                        }
+                        // an invalid candidate (or one beyond D) gets the weight
+                        // 2^-inf = 0 and cost 0, so every term below is exactly 0
+                        // (the statistics of its right pixel are finite); so does a
+                        // zero-variance window (1/sqrt(B) = 0, rho = 0)
+                        const bool ok = ((inD >> k) & 1u) && c4[k] == c4[k];
+                        const float c = ok ? c4[k] : 0.f;
+                        float pd;                                              // exp(rho / tau - lse)
+                        asm("ex2.approx.ftz.f32 %0, %1;"
+                            : "=f"(pd) : "f"(ok ? fmaf(c, -a.sk2, base) : __int_as_float(0xff800000)));
+                        const float Gn = pd * fmaf(gs, dl + (float)k, -gsds);   // G N
+                        const float t = Gn * bi[s];                            // G N isr
+                        av[k] = t * isl;                                       // A = G N isl isr
+                        p1 = fmaf(t, bS[s], p1);                               // (A mu_r) N / isl
+                        q1[s] = fmaf(t, c1, q1[s]);                            // A mu_l
+                        const float u = fmaf(-Gn, c, Gn);                      // G N rho
+                        p2 += u;                                               // (G rho / v_l) / isl^2
+                        q2[s] = fmaf(u, bi2[s], q2[s]);                        // G rho / v_r
                     }
                     cvp[0] = p1 * (isl * invN);                    // this lane's own slots
                     cvp[K >= 2 ? 1 : 32] = p2 * (isl * isl);
