@@ -213,9 +213,11 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
     const int cstride = cost_stride(a.D);
     constexpr int ESZ = CDT == CDT_F32 ? 4 : 2;
     const int lbase = K * (31 - lane);
-    uint32_t inD = 0u;                                 // SOFT: bit k set when candidate k is within D
+    // SOFT: upper limit of candidate k's weight exponent: +inf within D,
+    // -inf beyond (weight 2^-inf = 0)
+    float xlim[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) inD |= (idx0 + k < a.D ? 1u : 0u) << k;
+    for (int k = 0; k < K; ++k) xlim[k] = __int_as_float(idx0 + k < a.D ? 0x7f800000 : 0xff800000);
     const float dl = (float)(dc0 + K * lane);          // SOFT: disparity of candidate k = 0
     float q1[K], q2[K];                                // SOFT_BWD: diagonal sums in flight
 #pragma unroll
@@ -394,8 +396,8 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
                     // exp(-cost / tau) = exp((rho - 1) / tau) <= 1; ex2(-inf) = 0
-                    const bool ok = ((inD >> k) & 1u) && cv[k] == cv[k];
-                    const float x = ok ? -cv[k] * a.sk2 : __int_as_float(0xff800000);
+                    // max(NaN, -inf) = -inf: an invalid candidate (NaN cost) gets weight 0
+                    const float x = fminf(fmaxf(-cv[k] * a.sk2, __int_as_float(0xff800000)), xlim[k]);
                     float e;
                     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(x));
                     pe += e;
@@ -491,15 +493,16 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
                         const int s = (jj - k + 4 * K) % K;
-                        // an invalid candidate (or one beyond D) gets the weight
-                        // 2^-inf = 0 and cost 0, so every term below is exactly 0
-                        // (the statistics of its right pixel are finite); so does a
-                        // zero-variance window (1/sqrt(B) = 0, rho = 0)
-                        const bool ok = ((inD >> k) & 1u) && c4[k] == c4[k];
-                        const float c = ok ? c4[k] : 0.f;
+                        // an invalid candidate (NaN cost: max(NaN, -inf) = -inf) or one
+                        // beyond D gets the weight 2^-inf = 0 and a finite cost
+                        // (min(NaN, 2) = 2; valid costs lie in [0, 2]), so every term
+                        // below is exactly 0 (the statistics of its right pixel are
+                        // finite); so does a zero-variance window (1/sqrt(B) = 0, rho = 0)
+                        const float c = fminf(c4[k], 2.f);
                         float pd;                                              // exp(rho / tau - lse)
                         asm("ex2.approx.ftz.f32 %0, %1;"
-                            : "=f"(pd) : "f"(ok ? fmaf(c, -a.sk2, base) : __int_as_float(0xff800000)));
+                            : "=f"(pd)
+                            : "f"(fminf(fmaxf(fmaf(c4[k], -a.sk2, base), __int_as_float(0xff800000)), xlim[k])));
                         const float Gn = pd * fmaf(gs, dl + (float)k, -gsds);   // G N
                         const float t = Gn * bi[s];                            // G N isr
                         av[k] = t * isl;                                       // A = G N isl isr
