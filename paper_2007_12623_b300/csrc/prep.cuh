@@ -226,14 +226,18 @@ __global__ void __launch_bounds__(256) k_prep(PrepIn in0, PrepIn in1, int W, int
 // Float-image preparation for the soft-argmin path: same outputs as k_prep
 // (float copy with zero padding, {S, 1/sqrt(B)} or {S_hi, S_lo, 1/sqrt(B),
 // valid}, and, given `cost`, the border pixels' NaN slices of the FP32
-// volume), from a float image.  Window sums in FP32 (exact for
+// volume), from a pair of float images (blockIdx.z = 0 left, 1 right).  Window sums in FP32 (exact for
 // integer-valued images), B = N SS - S^2 from the two products and their
 // exact rounding errors (fma; within about one rounding of the exact value,
 // without the slow FP64 pipe), S_lo = S mod 256.
 template <int R>
-__global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ img, int W, int H, PrepOut out,
+__global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ imgL, const float* __restrict__ imgR,
+                                                  int W, int H, PrepOut outL, PrepOut outR,
                                                   void* __restrict__ cost, int cs) {
     constexpr int r = R;
+    const bool right = blockIdx.z != 0;
+    const float* __restrict__ img = right ? imgR : imgL;
+    const PrepOut out = right ? outR : outL;
     __shared__ float t[PSPAN][PSPAN + 1];
     __shared__ float rs[PSPAN][PT + 1];
     __shared__ float rss[PSPAN][PT + 1];
@@ -314,6 +318,7 @@ __global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ img,
             out.ustats[(size_t)gy * out.ustride + (m < out.ucol0 ? m : W + m)] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
-    // the left image's launch: NaN cost slices of the border pixels (FP32 volume)
-    if (cost) border_nan_slices<R>(cost, CDT_F32, cs, W, H, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
+    // the left image's blocks: NaN cost slices of the border pixels (FP32 volume)
+    if (cost && !right)
+        border_nan_slices<R>(cost, CDT_F32, cs, W, H, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
 }

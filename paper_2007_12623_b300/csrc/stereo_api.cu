@@ -1230,24 +1230,20 @@ static void soft_prepare(stereo_handle* h, const PairWs& w, const float* L, cons
     const bool fused = f != nullptr;
     PrepOut pl, pr;
     prep_layouts(W, d_min, D, K, w, pl, pr);
-    dim3 sg((W + PT - 1) / PT, (H + PT - 1) / PT);
+    dim3 sg((W + PT - 1) / PT, (H + PT - 1) / PT, 2);
     if (timed) mark(h, 0, s);
     const int cs = cost_stride(D);
-    for (int side = 0; side < 2; ++side) {
-        const float* img = side ? R : L;
-        const PrepOut& po = side ? pr : pl;
-        void* vol = side || fused ? nullptr : w.cost;   // the left launch writes the NaN border slices
-        switch (r) {
-            case 1: k_prep_f32<1><<<sg, 256, 0, s>>>(img, W, H, po, vol, cs); break;
-            case 2: k_prep_f32<2><<<sg, 256, 0, s>>>(img, W, H, po, vol, cs); break;
-            case 3: k_prep_f32<3><<<sg, 256, 0, s>>>(img, W, H, po, vol, cs); break;
-            case 4: k_prep_f32<4><<<sg, 256, 0, s>>>(img, W, H, po, vol, cs); break;
-            case 5: k_prep_f32<5><<<sg, 256, 0, s>>>(img, W, H, po, vol, cs); break;
-            case 6: k_prep_f32<6><<<sg, 256, 0, s>>>(img, W, H, po, vol, cs); break;
-            default: k_prep_f32<7><<<sg, 256, 0, s>>>(img, W, H, po, vol, cs); break;
-        }
-        counted();
+    void* vol = fused ? nullptr : w.cost;               // the left image's blocks write the NaN border slices
+    switch (r) {
+        case 1: k_prep_f32<1><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs); break;
+        case 2: k_prep_f32<2><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs); break;
+        case 3: k_prep_f32<3><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs); break;
+        case 4: k_prep_f32<4><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs); break;
+        case 5: k_prep_f32<5><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs); break;
+        case 6: k_prep_f32<6><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs); break;
+        default: k_prep_f32<7><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs); break;
     }
+    counted();
     if (timed) mark(h, 1, s);
     // the volume alone: no key maps
     CostArgs a{pl.img, pl.stride, pl.col0, pr.img, pr.stride, pr.col0, 0, w.lstats, w.ustats,
