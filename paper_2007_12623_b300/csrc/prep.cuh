@@ -223,17 +223,43 @@ __global__ void __launch_bounds__(256) k_prep(PrepIn in0, PrepIn in1, int W, int
                                            gridDim.x * gridDim.y);
 }
 
+// Zeroes the entries of the soft-argmin A volume (per row and chunk `apitch`
+// columns of 32 floats, the first `apad` of them padding) that the cost
+// kernel's backward form does not write, for rows y0 .. y0 + rows - 1: whole
+// rows within R of the top or bottom edge, else the columns left of R and
+// from W - R on, padding included.  The band's (row, chunk) pairs go round
+// robin to its `nblocks` blocks (this one is `bid`).
+template <int R>
+__device__ __forceinline__ void soft_a_border_rows(float* __restrict__ A, int nch, int apitch, int apad, int W,
+                                                   int H, int y0, int rows, int bid, int nblocks) {
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int hi_beg = min(apitch, apad + max(W - R, R));
+    for (int pc = bid; pc < rows * nch; pc += nblocks) {
+        const int y = y0 + pc / nch, c = pc % nch;
+        const bool full = y < R || y >= H - R;
+        const int nlo = full ? apitch : apad + R;
+        const int nhi = full ? 0 : apitch - hi_beg;
+        float4* rowp = reinterpret_cast<float4*>(A + ((size_t)y * nch + c) * apitch * 32);
+        for (int i = threadIdx.x; i < nlo * 8; i += blockDim.x) rowp[i] = z;
+        float4* hp = rowp + (size_t)hi_beg * 8;
+        for (int i = threadIdx.x; i < nhi * 8; i += blockDim.x) hp[i] = z;
+    }
+}
+
 // Float-image preparation for the soft-argmin path: same outputs as k_prep
 // (float copy with zero padding, {S, 1/sqrt(B)} or {S_hi, S_lo, 1/sqrt(B),
 // valid}, and, given `cost`, the border pixels' NaN slices of the FP32
-// volume), from a pair of float images (blockIdx.z = 0 left, 1 right).  Window sums in FP32 (exact for
+// volume; given `A`, the border of the backward pass's A volume, see
+// soft_a_border_rows), from a pair of float images (blockIdx.z = 0 left,
+// 1 right).  Window sums in FP32 (exact for
 // integer-valued images), B = N SS - S^2 from the two products and their
 // exact rounding errors (fma; within about one rounding of the exact value,
 // without the slow FP64 pipe), S_lo = S mod 256.
 template <int R>
 __global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ imgL, const float* __restrict__ imgR,
                                                   int W, int H, PrepOut outL, PrepOut outR,
-                                                  void* __restrict__ cost, int cs) {
+                                                  void* __restrict__ cost, int cs, float* __restrict__ A,
+                                                  int anch, int apitch, int apad) {
     constexpr int r = R;
     const bool right = blockIdx.z != 0;
     const float* __restrict__ img = right ? imgR : imgL;
@@ -321,4 +347,5 @@ __global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ imgL
     // the left image's blocks: NaN cost slices of the border pixels (FP32 volume)
     if (cost && !right)
         border_nan_slices<R>(cost, CDT_F32, cs, W, H, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
+    if (A && !right) soft_a_border_rows<R>(A, anch, apitch, apad, W, H, y0, rows, blockIdx.x, gridDim.x);
 }

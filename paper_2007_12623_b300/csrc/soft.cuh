@@ -266,24 +266,6 @@ __global__ void __launch_bounds__(256) k_soft_dA(SoftArgs a, const float* __rest
     }
 }
 
-// Zeroes the parts of the A volume that the cost kernel's soft backward form
-// leaves alone: the rows within r of the top or bottom edge, and in the other
-// rows the columns left of r and from W - r on, with the padding columns.
-// One block per row (blockIdx.x) and chunk (blockIdx.y).
-__global__ void __launch_bounds__(256) k_soft_a_border(float* __restrict__ A, int W, int H, int nch, int r) {
-    const int y = blockIdx.x, c = blockIdx.y;
-    const int pitch = soft_apitch(W);
-    const bool full = y < r || y >= H - r;
-    const int hi_beg = min(pitch, SOFT_APAD + max(W - r, r));   // padded columns [hi_beg, pitch)
-    const int nlo = full ? pitch : SOFT_APAD + r;               // padded columns [0, nlo)
-    const int nhi = full ? 0 : pitch - hi_beg;
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4* rowp = reinterpret_cast<float4*>(A + ((size_t)y * nch + c) * pitch * 32);
-    for (int i = threadIdx.x; i < nlo * 8; i += blockDim.x) rowp[i] = z;
-    float4* hp = rowp + (size_t)hi_beg * 8;
-    for (int i = threadIdx.x; i < nhi * 8; i += blockDim.x) hp[i] = z;
-}
-
 // M(q,d) = sum over the (2r+1)^2 window around q of A(., d), consumed on
 // the fly (never stored):
 //   T1L(q) = sum_d R(q-d) M(q,d),   T1R(u) = sum_d L(u+d) M(u+d,d),

@@ -1234,14 +1234,17 @@ static void soft_prepare(stereo_handle* h, const PairWs& w, const float* L, cons
     if (timed) mark(h, 0, s);
     const int cs = cost_stride(D);
     void* vol = fused ? nullptr : w.cost;               // the left image's blocks write the NaN border slices
+    // backward form: the left image's blocks also zero the border of A
+    float* A = fused ? f->A : nullptr;
+    const int anch = fused ? f->nch : 0, apitch = soft_apitch(W);
     switch (r) {
-        case 1: k_prep_f32<1><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs); break;
-        case 2: k_prep_f32<2><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs); break;
-        case 3: k_prep_f32<3><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs); break;
-        case 4: k_prep_f32<4><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs); break;
-        case 5: k_prep_f32<5><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs); break;
-        case 6: k_prep_f32<6><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs); break;
-        default: k_prep_f32<7><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs); break;
+        case 1: k_prep_f32<1><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs, A, anch, apitch, SOFT_APAD); break;
+        case 2: k_prep_f32<2><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs, A, anch, apitch, SOFT_APAD); break;
+        case 3: k_prep_f32<3><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs, A, anch, apitch, SOFT_APAD); break;
+        case 4: k_prep_f32<4><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs, A, anch, apitch, SOFT_APAD); break;
+        case 5: k_prep_f32<5><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs, A, anch, apitch, SOFT_APAD); break;
+        case 6: k_prep_f32<6><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs, A, anch, apitch, SOFT_APAD); break;
+        default: k_prep_f32<7><<<sg, 256, 0, s>>>(L, R, W, H, pl, pr, vol, cs, A, anch, apitch, SOFT_APAD); break;
     }
     counted();
     if (timed) mark(h, 1, s);
@@ -1358,13 +1361,12 @@ stereo_status stereo_softargmin_bwd(stereo_handle* h, const float* left, const f
         const bool timed = h->timing && h->ev_ready && b == batch - 1;
         SoftArgs sa;
         if (fused) {
-            // A and the per-pixel sums from the cost kernel, the border of A zeroed
+            // A and the per-pixel sums from the cost kernel, the border of A
+            // zeroed by the preparation kernel
             cudaMemsetAsync(w.sP1, 0, (size_t)((char*)w.sT1R - (char*)w.sP1) + npix * 4, s);   // P1..T1R
             const SoftForm f{const_cast<float*>(d_soft + b * npix), const_cast<float*>(lse + b * npix),
                              grad_dsoft + b * npix, w.softA, w.sP1, w.sP2, w.sQ1, w.sQ2, nch, tau};
             soft_prepare(h, w, L, R, W, H, d_min, num_disp, r, sa, s, timed, &f);
-            k_soft_a_border<<<dim3(H, nch), 256, 0, s>>>(w.softA, W, H, nch, r);
-            counted();
         } else {
             soft_prepare(h, w, L, R, W, H, d_min, num_disp, r, sa, s, timed);
             sa.tau = tau;
