@@ -530,11 +530,22 @@ __global__ void __launch_bounds__(256) k_l1_partial(const float* __restrict__ ds
     // per-thread and per-warp partial sums in FP32 (a few hundred terms at
     // most; FP64 arithmetic is slow on this part), the block's eight warp
     // sums in FP64
+    // (four elements' loads in flight per thread)
     float s = 0.f;
     int c = 0;
-    for (long i = (long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long)gridDim.x * 256) {
-        const float d = ds[i];
-        if (d == d) { s += fabsf(d - gt[i]); ++c; }
+    const long stride = (long)gridDim.x * 256;
+    for (long i0 = (long)blockIdx.x * 256 + threadIdx.x; i0 < n; i0 += 4 * stride) {
+        float d[4], g[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long i = min(i0 + k * stride, n - 1);
+            d[k] = ds[i];
+            g[k] = gt[i];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (i0 + k * stride < n && d[k] == d[k]) { s += fabsf(d[k] - g[k]); ++c; }
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -584,20 +595,18 @@ __global__ void __launch_bounds__(L1_FINAL_THREADS) k_l1_final(const double* __r
         for (int w = 0; w < L1_FINAL_THREADS / 32; ++w) { ts += ws[w]; tc += wc[w]; }
         *loss = tc > 0 ? (float)(ts / tc) : 0.f;
         *count = tc;
+        // the gradient's magnitude 1 / count, as the gradient kernel uses it
+        *reinterpret_cast<float*>(count + 1) = tc > 0 ? 1.f / (float)tc : 0.f;
     }
 }
 
 __global__ void __launch_bounds__(256) k_l1_grad(const float* __restrict__ ds, const float* __restrict__ gt,
-                                                 long n, const double* __restrict__ count,
+                                                 long n, const float* __restrict__ inv_count,
                                                  float* __restrict__ grad) {
     const long i = (long)blockIdx.x * 256 + threadIdx.x;
     if (i >= n) return;
     const float d = ds[i];
-    const double c = *count;
-    float g = 0.f;
-    if (d == d && c > 0) {
-        const float e = d - gt[i];
-        g = (e > 0.f ? 1.f : (e < 0.f ? -1.f : 0.f)) / (float)c;
-    }
-    grad[i] = g;
+    const float e = d - gt[i];
+    const float inv = *inv_count;                     // 1 / count (0 when count = 0)
+    grad[i] = d == d ? (e > 0.f ? inv : (e < 0.f ? -inv : 0.f)) : 0.f;
 }

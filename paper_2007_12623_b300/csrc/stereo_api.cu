@@ -1401,7 +1401,8 @@ stereo_status stereo_l1_loss(stereo_handle* h, const float* d_soft, const float*
     k_l1_final<<<1, L1_FINAL_THREADS, 0, s>>>(w.l1part, parts, loss, count);
     counted();
     if (grad) {
-        k_l1_grad<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_soft, gt, n, count, grad);
+        k_l1_grad<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_soft, gt, n, reinterpret_cast<const float*>(count + 1),
+                                                              grad);
         counted();
     }
     return last_error();
