@@ -299,8 +299,8 @@ stereo_status stereo_softargmin_fwd(stereo_handle* h, const float* left, const f
  * (float B*H*W), writes dLoss/dleft and dLoss/dright (float B*H*W).  Window
  * statistics and ZNCC are recomputed, not taken from the forward call (with
  * num_disp <= 128 inside the kernel that forms the backward terms; larger
- * num_disp through the FP32 volume).  A pixel whose d_soft is NaN (no valid
- * candidate) contributes nothing, whatever its grad_dsoft. */
+ * num_disp through the FP32 volume).  A pixel whose d_soft is NaN (the
+ * forward found no valid candidate) contributes nothing. */
 stereo_status stereo_softargmin_bwd(stereo_handle* h, const float* left, const float* right,
                                     int32_t batch, int32_t width, int32_t height, int32_t d_min,
                                     int32_t num_disp, int32_t win_radius, float tau,

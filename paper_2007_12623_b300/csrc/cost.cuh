@@ -54,10 +54,10 @@ struct CostSmem {
     // soft-argmin forward: two [TW][33] tiles of per-lane partial sums;
     // backward: the row's costs [TW][CVS] (each lane's K values, later its
     // two partial sums), the exit slots of the diagonal sums [2][32] and the
-    // per-pixel inputs of two rows [2][3][TW]
+    // per-pixel inputs of two rows [2][3][TW] and the row's per-pixel factors [TW][8]
     static constexpr int SOFT_BYTES = BYTES + 2 * G::TW * 33 * 4;
     static constexpr int CVS = K >= 2 ? 32 * K + 4 : 68;
-    static constexpr int SOFT_BWD_BYTES = BYTES + (G::TW * CVS + 64 + 6 * G::TW) * 4;
+    static constexpr int SOFT_BWD_BYTES = BYTES + (G::TW * CVS + 64 + 6 * G::TW + 8 * G::TW) * 4;
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -161,6 +161,7 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
     float* sCv = sS0;                                                 // SOFT_BWD: [TW][CVS] parked costs
     float* sQx = sCv + TW * CVS;                                      // SOFT_BWD: [2][32] Q1, Q2 exits
     float* sPx = sQx + 64;                                            // SOFT_BWD: [2][3][TW] g, d_soft, lse
+    float* sPre = sPx + 6 * TW;                                       // SOFT_BWD: [TW][8] per-pixel factors
 
     const int lane = threadIdx.x & 31;
     const int W = a.W, H = a.H;
@@ -458,6 +459,23 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
                 slot(32 * K - 1 - K * lane - k, bS[s], bi[s], bi2[s]);
             }
             float* arow = a.sA + (((size_t)y * a.snch + achunk) * a.sapitch + a.sapad + x0) * 32 + (idx0 & 31);
+            // G N = p_d g N (d - d_soft) / tau with p_d = exp(rho / tau - lse)
+            // = 2^(base - c log2(e) / tau), base = (1 / tau - lse) log2(e),
+            // c = 1 - rho.  Lane j < TW puts pixel j's factors in shared
+            // memory: {g N / tau, g N d_soft / tau, base, S_l isl / N} and
+            // {isl, isl / N, isl^2}.  A pixel without a valid candidate has
+            // d_soft = NaN: its terms are all 0, so its scale is taken as 0.
+            if (lane < TW) {
+                const float* px = sPx + buf * 3 * TW + lane;
+                const float2 sl = Ls[lane];
+                const float dsv = px[TW];
+                const bool pv = dsv == dsv;
+                const float gs = pv ? px[0] * NoverTau : 0.f;
+                float4* pre = reinterpret_cast<float4*>(sPre + lane * 8);
+                pre[0] = make_float4(gs, pv ? gs * dsv : 0.f, a.sk2 - px[2 * TW] * l2e, sl.x * sl.y * invN);
+                pre[1] = make_float4(sl.y, sl.y * invN, sl.y * sl.y, 0.f);
+            }
+            __syncwarp();
 #pragma unroll 1
             for (int j0 = 0; j0 < TW; j0 += K) {
 #pragma unroll
@@ -476,19 +494,9 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
                     } else {
                         c4[0] = cvp[0];
                     }
-                    const float2 sl = Ls[j];
-                    const float* px = sPx + buf * 3 * TW + j;
-                    // G N = p_d g N (d - d_soft) / tau with p_d = exp(rho / tau
-                    // - lse) = 2^(base - c log2(e) / tau), base = (1 / tau - lse)
-                    // log2(e), c = 1 - rho; the isl factors of P1, P2 are
-                    // applied once per pixel
-                    // a pixel without a valid candidate has d_soft = NaN: its
-                    // terms are all 0, so its gradient is taken as 0
-                    const float dsv = px[TW];
-                    const bool pv = dsv == dsv;
-                    const float gs = pv ? px[0] * NoverTau : 0.f, gsds = pv ? gs * dsv : 0.f;
-                    const float base = a.sk2 - px[2 * TW] * l2e;
-                    const float isl = sl.y, c1 = sl.x * isl * invN;   // S_l isl / N
+                    const float4 f0 = *reinterpret_cast<const float4*>(sPre + j * 8);
+                    const float4 f1 = *reinterpret_cast<const float4*>(sPre + j * 8 + 4);
+                    const float gs = f0.x, gsds = f0.y, base = f0.z, c1 = f0.w, isl = f1.x;
                     float p1 = 0.f, p2 = 0.f, av[K];
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
@@ -512,8 +520,8 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
                         p2 += u;                                               // (G rho / v_l) / isl^2
                         q2[s] = fmaf(u, bi2[s], q2[s]);                        // G rho / v_r
                     }
-                    cvp[0] = p1 * (isl * invN);                    // this lane's own slots
-                    cvp[K >= 2 ? 1 : 32] = p2 * (isl * isl);
+                    cvp[0] = p1 * f1.y;                            // this lane's own slots (the isl
+                    cvp[K >= 2 ? 1 : 32] = p2 * f1.z;              // factors once per pixel)
                     if (do_astore) {
                         float* ap = arow + (size_t)j * 32;
                         if (K == 4) *reinterpret_cast<float4*>(ap) = make_float4(av[0], av[1 % K], av[2 % K], av[3 % K]);
