@@ -304,7 +304,6 @@ __global__ void __launch_bounds__(SOFT_BOX_THREADS, 3) k_soft_box_t1(const float
     const int chunk = (int)(wid / ((long)nrun * nband));
     const int x0 = run * SOFT_RUN, y0 = band * ty;
     const int k = chunk * 32 + lane, d = d_min + k;
-    const bool kin = k < cs;
     float V[NCOL];
 #pragma unroll
     for (int c = 0; c < NCOL; ++c) V[c] = 0.f;
@@ -343,13 +342,16 @@ __global__ void __launch_bounds__(SOFT_BOX_THREADS, 3) k_soft_box_t1(const float
     if (y0 + R < H) stage(y0 + R, bufA);
     cp_async_commit();
     // the row's image values (L at the run's columns; R(x0 - d0 - 31 + i),
-    // i < 64, clamped into the row), loaded one output row ahead
+    // i < 64), loaded one output row ahead; 0 outside the image, which
+    // removes the terms of columns x >= W and of right pixels x - d outside
+    // the image without a test (sums for such u are dropped at the atomics)
     auto img_loads = [&](int yy, float& l, float& ra, float& rb) {
         const float* Lrow = Limg + (size_t)yy * W;
         const float* Rrow = Rimg + (size_t)yy * W;
-        l = __ldg(Lrow + min(x0 + lane, W - 1));
-        ra = __ldg(Rrow + min(max(x0 - d0 - 31 + lane, 0), W - 1));
-        rb = __ldg(Rrow + min(max(x0 - d0 + 1 + lane, 0), W - 1));
+        const int xl = x0 + lane, ca = x0 - d0 - 31 + lane, cb = x0 - d0 + 1 + lane;
+        l = xl < W ? __ldg(Lrow + xl) : 0.f;
+        ra = ca >= 0 && ca < W ? __ldg(Rrow + ca) : 0.f;
+        rb = cb >= 0 && cb < W ? __ldg(Rrow + cb) : 0.f;
     };
     float nl = 0.f, nra = 0.f, nrb = 0.f;
     if (y0 < y1) img_loads(y0, nl, nra, nrb);
@@ -370,8 +372,6 @@ __global__ void __launch_bounds__(SOFT_BOX_THREADS, 3) k_soft_box_t1(const float
         rrow[lane] = nra;
         rrow[32 + lane] = nrb;
         if (y + 1 < y1) img_loads(y + 1, nl, nra, nrb);
-        // columns j with a valid candidate: x < W, 0 <= x - d < W
-        const int jlo = kin ? max(0, d - x0) : SOFT_RUN, jhi = min(W - x0, W - x0 + d);
         __syncwarp();
         float acc = 0.f;                      // T1R partial for u = x - d
         float h = 0.f;
@@ -381,9 +381,8 @@ __global__ void __launch_bounds__(SOFT_BOX_THREADS, 3) k_soft_box_t1(const float
         for (int j = 0; j < 32; ++j) {
             if (j > 0) h += V[j + 2 * R] - V[j - 1];
             const float lx = __shfl_sync(0xffffffffu, my_l, j);
-            const bool ok = j >= jlo && j < jhi;
-            tl[j * 33 + lane] = ok ? rrow[j - lane + 31] * h : 0.f;
-            acc = ok ? fmaf(lx, h, acc) : acc;
+            tl[j * 33 + lane] = rrow[j - lane + 31] * h;
+            acc = fmaf(lx, h, acc);
             // the sum for u = x0 + j - d0 - 31 is complete in lane 31
             if (lane == 31) rexit[j] = acc;
             acc = __shfl_up_sync(0xffffffffu, acc, 1);
