@@ -278,13 +278,13 @@ __global__ void __launch_bounds__(256) k_soft_dA(SoftArgs a, const float* __rest
 // row's horizontal pass (the window's first rows go through the same two
 // buffers alternately).  The T1L terms of a row go through the warp's
 // shared tile.
-constexpr int SOFT_BOX_THREADS = 128;
+constexpr int SOFT_BOX_THREADS = 64;
 
 __host__ __device__ constexpr int soft_box_warp_floats(int R) { return SOFT_TILE + 2 * (SOFT_RUN + 2 * R) * 32 + 96; }
 inline size_t soft_box_smem(int R) { return (size_t)(SOFT_BOX_THREADS / 32) * soft_box_warp_floats(R) * 4; }
 
 template <int R>
-__global__ void __launch_bounds__(SOFT_BOX_THREADS, 3) k_soft_box_t1(const float* __restrict__ A, const float* __restrict__ Limg,
+__global__ void __launch_bounds__(SOFT_BOX_THREADS, 7) k_soft_box_t1(const float* __restrict__ A, const float* __restrict__ Limg,
                                                      const float* __restrict__ Rimg, int W, int H, int nch,
                                                      int cs, int d_min, int ty, float* __restrict__ T1L,
                                                      float* __restrict__ T1R) {
