@@ -79,9 +79,9 @@ WORKLOADS = {
                       seed=synth.seed_for(0), disp=None),
 }
 COST_CODE = {"none": 0, "f32": 1, "f16": 2, "bf16": 3}
-# DRAM bytes (read + write) of one launch of the workload's dominant kernel
-# from an ncu capture of the current kernel (profiles/<kernel>_<workload>.md);
-# absent where no capture of the current kernel exists.
+# DRAM bytes (read + write) of one launch of the workload's dominant kernel,
+# read from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the kernel as it is built now; absent where no such capture exists.
 KERNEL_TRAFFIC = {"tissue960": 221.4e6,
                   "soft8": {"k_soft_box_t1": 569.0e6, "k_cost_wta (soft backward form)": 235.5e6}}
 COST_BYTES = {"none": 0, "f32": 4, "f16": 2, "bf16": 2}

@@ -78,28 +78,40 @@ def test_forward_two_chunks_matches_oracle(dev):
     h.close()
 
 
-@pytest.mark.parametrize("r,D,H,W", [(5, 16, 64, 64), (3, 12, 64, 64),
-                                     (7, 40, 50, 70),    # two disparity chunks, ragged last run
-                                     (1, 33, 48, 45),
-                                     (3, 150, 32, 212)])  # D > 128: through the FP32 volume
-def test_backward_matches_oracle_gradient(dev, r, D, H, W):
-    """Crop of a tissue pair, candidates 0..D-1, tau = 0.1, random upstream
-    gradient."""
+@pytest.mark.parametrize("r,D,H,W,d_min", [
+    (5, 16, 64, 64, 0), (3, 12, 64, 64, 0),
+    (7, 40, 50, 70, 0),      # K = 2: two disparity chunks, ragged last run
+    (1, 33, 48, 45, 0),
+    (5, 100, 48, 200, 0),    # K = 4, one chunk of 128 with 28 lanes' candidates beyond D
+    (7, 128, 40, 220, 0),    # K = 4, all 128 candidates of the batch form's range (r = 7)
+    (5, 128, 24, 200, 0),    # the differentiation workload's D = 128, r = 5
+    (5, 128, 30, 210, -6),   # K = 4 with a negative first disparity
+    (3, 150, 32, 212, 0)])   # D > 128: through the FP32 volume
+def test_backward_matches_oracle_gradient(dev, r, D, H, W, d_min):
+    """Crop of a tissue pair, candidates d_min..d_min+D-1, tau = 0.1, random
+    upstream gradient.  The crops are wide enough that pixels near the right
+    edge have every candidate valid.  Forward compared element by element on
+    the same crop."""
     tau = 0.1
     L, R, gt = _crop_pair(synth.seed_for(4, 1), 30, 100, H, W)
     rng = np.random.default_rng(11)
-    ds_ref, lse_ref, hv = oracle.softargmin_fwd(L, R, 0, D, r, tau)
+    ds_ref, lse_ref, hv = oracle.softargmin_fwd(L, R, d_min, D, r, tau)
+    assert hv.sum() > 200
     g = np.where(hv, rng.normal(0, 1, (H, W)), 0.0)
-    gL_ref, gR_ref = oracle.softargmin_bwd(L, R, 0, D, r, tau, g)
+    gL_ref, gR_ref = oracle.softargmin_bwd(L, R, d_min, D, r, tau, g)
     h = _handle(H, W, D)
     tL, tR = _T(L, dev), _T(R, dev)
     ds = torch.empty((H, W), dtype=torch.float32, device=dev)
     lse = torch.empty_like(ds)
-    st.stereo_softargmin_fwd(h, tL, tR, 0, D, r, tau, ds, lse)
+    st.stereo_softargmin_fwd(h, tL, tR, d_min, D, r, tau, ds, lse)
     gL = torch.empty_like(ds)
     gR = torch.empty_like(ds)
-    st.stereo_softargmin_bwd(h, tL, tR, 0, D, r, tau, ds, lse, _T(g, dev), gL, gR)
+    st.stereo_softargmin_bwd(h, tL, tR, d_min, D, r, tau, ds, lse, _T(g, dev), gL, gR)
     torch.cuda.synchronize()
+    dsn, lsen = ds.cpu().numpy(), lse.cpu().numpy()
+    assert np.array_equal(np.isnan(dsn), ~hv)
+    assert np.max(np.abs(dsn[hv] - ds_ref[hv])) <= 1e-4
+    assert np.max(np.abs(lsen[hv] - lse_ref[hv]) / np.maximum(1.0, np.abs(lse_ref[hv]))) <= 1e-5
     for got, ref in ((gL.cpu().numpy(), gL_ref), (gR.cpu().numpy(), gR_ref)):
         rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         print(f"grad rel L2 {rel:.2e}, max abs err {np.max(np.abs(got - ref)):.2e} (max |g| {np.max(np.abs(ref)):.2e})")

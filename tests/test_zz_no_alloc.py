@@ -48,19 +48,23 @@ def _with_handle(tL, tR, d_min, D, r):
     return dl, dr, sub
 
 
-@pytest.mark.parametrize("case", ["perlin320", "tissue640"])
-def test_noalloc_matches_stage_match_twice(case):
+@pytest.mark.parametrize("case,d_min", [("perlin320", 0), ("tissue640", -4),
+                                        ("tissue640", 64), ("tissue640", -64)])
+def test_noalloc_matches_stage_match_twice(case, d_min):
+    """The 640x480 cases are the largest size the fixed scratch accepts, with
+    D = 128 and r = 7; d_min = +64 and -64 are the extremes of the accepted
+    range, which put the staged rows' column offsets at their largest."""
     assert torch.cuda.is_available()
     dev = torch.device("cuda:0")
     if case == "perlin320":
         L, R, _ = synth.perlin_pair(synth.seed_for(0))
-        d_min, D, r = 0, 32, 5
-    else:                                  # the largest size the fixed scratch accepts
+        D, r = 32, 5
+    else:
         Lrgb, Rrgb, _ = synth.tissue_pair(synth.seed_for(1), 640, 480)
         w = np.array([77, 150, 29])
         L = ((Lrgb.astype(np.int32) @ w + 128) >> 8).astype(np.uint8)
         R = ((Rrgb.astype(np.int32) @ w + 128) >> 8).astype(np.uint8)
-        d_min, D, r = -4, 128, 7
+        D, r = 128, 7
     tL = torch.from_numpy(np.ascontiguousarray(L)).to(dev)
     tR = torch.from_numpy(np.ascontiguousarray(R)).to(dev)
     want = _with_handle(tL, tR, d_min, D, r)
