@@ -68,7 +68,8 @@ def lib():
         sig = {
             "or_vote_nbins": (i, [C.c_float, C.c_float]),
             "or_vote_matches": (None, [P, P, i, C.c_float, C.c_float, P, P, P]),
-            "or_mosaic_frame": (i, [P, P, P, P, P, i, P, P, i, i, C.c_float, C.c_float, C.c_float, P, P, C.c_float, C.c_float, C.c_float]),
+            "or_mosaic_frame": (i, [P, P, P, P, P, i, P, P, i, i, C.c_float, C.c_float, C.c_float, P, P,
+                                    C.c_float, C.c_float, C.c_float, d, d, P, P, P]),
             "or_depth_points": (None, [P, i, i, d, d, d, d, d, P, P]),
             "or_gray": (None, [P, i, i, P]),
             "or_candidate_valid": (i, [i, i, i, i, i, i]),
@@ -348,20 +349,37 @@ class PointModel:
         self.capacity = capacity
 
 
-def mosaic_frame(model: PointModel, xyz, img, f, cx, cy, R, t, tau, r0=0.5, gmin=0.1) -> int:
-    """Point-based TSDF mosaicking of one frame (Sec. II); updates `model` in
-    place and returns the number of appends that did not fit."""
+def mosaic_frame(model: PointModel, xyz, img, f, cx, cy, R, t, tau, r0=0.5, gmin=0.1, margins=None):
+    """Point-based TSDF mosaicking of one frame (Sec. II), in double
+    precision; updates `model` in place and returns the number of appends
+    that did not fit.
+
+    margins=(eps_pix, eps_rel) also returns the decision margins as a second
+    value: dict(fragile_pix [H, W] bool, fragile_pt [n] bool for the points
+    the model held before the frame, src_pixel [count] int: the pixel each
+    appended point came from, -1 for older points)."""
     xyz = np.ascontiguousarray(xyz, np.float32)
     img = np.ascontiguousarray(img, np.uint8)
     H, W = xyz.shape[:2]
     R = np.ascontiguousarray(R, np.float32).reshape(9)
     t = np.ascontiguousarray(t, np.float32).reshape(3)
+    n0 = model.count
     cnt = C.c_int(model.count)
+    fp = fq = src = None
+    eps_pix, eps_rel = margins if margins is not None else (0.0, 0.0)
+    if margins is not None:
+        fp = np.zeros((H, W), np.uint8)
+        fq = np.zeros(max(n0, 1), np.uint8)
+        src = np.full(model.capacity, -1, np.int32)
     dropped = lib().or_mosaic_frame(_p(model.pos), _p(model.rgb), _p(model.wpos), _p(model.wrgb),
                                     C.byref(cnt), model.capacity, _p(xyz), _p(img), W, H, float(f),
-                                    float(cx), float(cy), _p(R), _p(t), float(tau), float(r0), float(gmin))
+                                    float(cx), float(cy), _p(R), _p(t), float(tau), float(r0), float(gmin),
+                                    float(eps_pix), float(eps_rel), _p(fp), _p(fq), _p(src))
     model.count = cnt.value
-    return dropped
+    if margins is None:
+        return dropped
+    return dropped, dict(fragile_pix=fp.astype(bool), fragile_pt=fq[:n0].astype(bool),
+                         src_pixel=src[:model.count])
 
 
 def vote_matches(uv1, uv2, bin=4.0, range_=128.0):

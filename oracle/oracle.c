@@ -725,13 +725,12 @@ void or_depth_points(const double* d, int W, int H, double f, double cx, double 
  * Point-based TSDF mosaicking of one key frame into the surface model
  * (Sec. II, GPU-based TSDF mosaicking).  The model is a list of points with
  * a world position, an RGB colour, a position weight and a colour weight.
+ * Every quantity below is evaluated in double precision.
  *
  *  1. Rasterise the model into the current image: X = R P + t (world ->
  *     camera); a point with X.z > 0 lands on pixel u = floor(f X.x / X.z + cx
  *     + 1/2), v = floor(f X.y / X.z + cy + 1/2); per pixel the nearest point
- *     (smallest X.z, ties -> smallest index) is kept.  These decisions are
- *     taken in single precision with a fixed operation order (the same
- *     decisions as the GPU's).
+ *     (smallest X.z, ties -> smallest index) is kept.
  *  2. Every pixel with a valid stereo point Q (camera frame) whose kept
  *     model point lies within the truncation distance (|Q.z - X.z| <= tau)
  *     merges into it: P <- (w P + Pw) / (w + 1), w <- w + 1 with Pw = R^T
@@ -742,60 +741,99 @@ void or_depth_points(const double* d, int W, int H, double f, double cx, double 
  *  3. Every other pixel with a valid point is appended as a new point
  *     (Pw, I, w = 1, c = g), in row-major pixel order, while capacity lasts.
  * Returns the number of appends that did not fit (0 normally).
- * pos/rgb: [capacity][3]; wpos/wrgb: [capacity]; *count in/out. */
-static float or_f32_dot3(const float* r, float a, float b, float c) {
-    float s = r[0] * a;
-    s = s + r[1] * b;
-    s = s + r[2] * c;
-    return s;
+ * pos/rgb: [capacity][3]; wpos/wrgb: [capacity]; *count in/out.
+ *
+ * Decision margins (optional outputs, NULL to skip).  A computation in a
+ * narrower precision may decide differently where a decision lies within
+ * its rounding of an edge; the oracle marks those places:
+ *   fragile_pix[W*H]: pixel k is marked when a point's projection lies
+ *     within eps_pix pixels of a rounding edge (u + 1/2 or v + 1/2 within
+ *     eps_pix of an integer; the pixels on both sides are marked), when the
+ *     two nearest points of k differ in depth by at most eps_rel times the
+ *     nearer depth, or when k's merge test is within eps_rel * (|Q.z| + tau)
+ *     of its threshold;
+ *   fragile_pt[n]: model point i is marked when its projection is near an
+ *     edge or it lands on a marked pixel;
+ *   src_pixel[capacity]: for every appended point, the pixel it came from. */
+static void or_mark(uint8_t* fp, int W, int H, double fu, double fv) {
+    if (fu >= 0.0 && fu < (double)W && fv >= 0.0 && fv < (double)H) fp[(size_t)fv * W + (size_t)fu] = 1;
 }
 
 int or_mosaic_frame(double* pos, double* rgb, double* wpos, double* wrgb, int* count, int capacity,
                     const float* xyz, const uint8_t* img, int W, int H, float f, float cx, float cy,
-                    const float* R, const float* t, float tau, float r0, float gmin) {
+                    const float* R, const float* t, float tau, float r0, float gmin,
+                    double eps_pix, double eps_rel, uint8_t* fragile_pix, uint8_t* fragile_pt, int* src_pixel) {
     const int n = *count;
-    int* win = (int*)malloc(sizeof(int) * (size_t)W * H);
-    float* winz = (float*)malloc(sizeof(float) * (size_t)W * H);
-    for (size_t k = 0; k < (size_t)W * H; ++k) win[k] = -1;
+    const size_t np = (size_t)W * H;
+    int* win = (int*)malloc(sizeof(int) * np);
+    double* winz = (double*)malloc(sizeof(double) * np);
+    double* z2nd = (double*)malloc(sizeof(double) * np);   /* second-nearest depth per pixel */
+    long long* land = (long long*)malloc(sizeof(long long) * (size_t)(n > 0 ? n : 1));
+    double Rd[9], td[3];
+    for (int a = 0; a < 9; ++a) Rd[a] = R[a];
+    for (int a = 0; a < 3; ++a) td[a] = t[a];
+    for (size_t k = 0; k < np; ++k) {
+        win[k] = -1;
+        z2nd[k] = INFINITY;
+    }
+    if (fragile_pix) memset(fragile_pix, 0, np);
+    if (fragile_pt) memset(fragile_pt, 0, (size_t)n);
     for (int i = 0; i < n; ++i) {
-        const float P0 = (float)pos[3 * (size_t)i], P1 = (float)pos[3 * (size_t)i + 1],
-                    P2 = (float)pos[3 * (size_t)i + 2];
-        const float X0 = or_f32_dot3(R, P0, P1, P2) + t[0];
-        const float X1 = or_f32_dot3(R + 3, P0, P1, P2) + t[1];
-        const float X2 = or_f32_dot3(R + 6, P0, P1, P2) + t[2];
-        if (!(X2 > 0.0f)) continue;
-        float pu = f * X0;
-        pu = pu / X2;
-        pu = pu + cx;
-        float pv = f * X1;
-        pv = pv / X2;
-        pv = pv + cy;
-        const float fu = floorf(pu + 0.5f), fv = floorf(pv + 0.5f);
-        if (!(fu >= 0.0f && fu < (float)W && fv >= 0.0f && fv < (float)H)) continue;
+        land[i] = -1;
+        const double* P = pos + 3 * (size_t)i;
+        double X[3];
+        for (int a = 0; a < 3; ++a) X[a] = Rd[3 * a] * P[0] + Rd[3 * a + 1] * P[1] + Rd[3 * a + 2] * P[2] + td[a];
+        if (!(X[2] > 0.0)) continue;
+        const double pu = (double)f * X[0] / X[2] + (double)cx + 0.5;
+        const double pv = (double)f * X[1] / X[2] + (double)cy + 0.5;
+        const double fu = floor(pu), fv = floor(pv);
+        if (fragile_pix) {
+            /* near a rounding edge: mark the pixel and its neighbour across the edge */
+            const double eu = pu - fu, ev = pv - fv;
+            int near_edge = 0;
+            if (eu < eps_pix) { or_mark(fragile_pix, W, H, fu - 1, fv); near_edge = 1; }
+            if (eu > 1.0 - eps_pix) { or_mark(fragile_pix, W, H, fu + 1, fv); near_edge = 1; }
+            if (ev < eps_pix) { or_mark(fragile_pix, W, H, fu, fv - 1); near_edge = 1; }
+            if (ev > 1.0 - eps_pix) { or_mark(fragile_pix, W, H, fu, fv + 1); near_edge = 1; }
+            if (near_edge) {
+                or_mark(fragile_pix, W, H, fu, fv);
+                if (fragile_pt) fragile_pt[i] = 1;
+            }
+        }
+        if (!(fu >= 0.0 && fu < (double)W && fv >= 0.0 && fv < (double)H)) continue;
         const size_t k = (size_t)fv * W + (size_t)fu;
-        if (win[k] < 0 || X2 < winz[k]) {     /* equal depth: the smaller index stays */
+        land[i] = (long long)k;
+        if (win[k] < 0 || X[2] < winz[k]) {     /* equal depth: the smaller index stays */
+            if (win[k] >= 0) z2nd[k] = winz[k];
             win[k] = i;
-            winz[k] = X2;
+            winz[k] = X[2];
+        } else if (X[2] < z2nd[k]) {
+            z2nd[k] = X[2];
         }
     }
+    if (fragile_pix)
+        for (size_t k = 0; k < np; ++k)
+            if (win[k] >= 0 && z2nd[k] - winz[k] <= eps_rel * winz[k]) fragile_pix[k] = 1;
     const double cxc = (W - 1) / 2.0, cyc = (H - 1) / 2.0;
     int appended = 0, dropped = 0;
     for (int v = 0; v < H; ++v)
         for (int u = 0; u < W; ++u) {
             const size_t k = (size_t)v * W + u;
-            const float Qx = xyz[3 * k], Qy = xyz[3 * k + 1], Qz = xyz[3 * k + 2];
-            if (isnan(Qz) || !(Qz > 0.0f)) continue;
+            const double Qx = xyz[3 * k], Qy = xyz[3 * k + 1], Qz = xyz[3 * k + 2];
+            if (isnan(Qz) || !(Qz > 0.0)) continue;
             /* world point R^T (Q - t) */
-            const double q0 = (double)Qx - t[0], q1 = (double)Qy - t[1], q2 = (double)Qz - t[2];
+            const double q0 = Qx - td[0], q1 = Qy - td[1], q2 = Qz - td[2];
             double Pw[3];
-            for (int a = 0; a < 3; ++a) Pw[a] = R[a] * q0 + R[3 + a] * q1 + R[6 + a] * q2;
+            for (int a = 0; a < 3; ++a) Pw[a] = Rd[a] * q0 + Rd[3 + a] * q1 + Rd[6 + a] * q2;
             const double du = (u - cxc) / (W / 2.0), dv = (v - cyc) / (H / 2.0);
             const double rr = sqrt(du * du + dv * dv) / sqrt(2.0);
             double g = 1.0;
             if (rr > r0) g = 1.0 - (1.0 - gmin) * (rr - r0) / (1.0 - r0);
             if (g < gmin) g = gmin;
             const int i = win[k];
-            if (i >= 0 && fabsf(Qz - winz[k]) <= tau) {
+            if (i >= 0 && fragile_pix && fabs(fabs(Qz - winz[k]) - (double)tau) <= eps_rel * (fabs(Qz) + tau))
+                fragile_pix[k] = 1;
+            if (i >= 0 && fabs(Qz - winz[k]) <= (double)tau) {
                 const double w = wpos[i], c = wrgb[i];
                 for (int a = 0; a < 3; ++a) {
                     pos[3 * (size_t)i + a] = (w * pos[3 * (size_t)i + a] + Pw[a]) / (w + 1.0);
@@ -813,11 +851,17 @@ int or_mosaic_frame(double* pos, double* rgb, double* wpos, double* wrgb, int* c
             }
             wpos[j] = 1.0;
             wrgb[j] = g;
+            if (src_pixel) src_pixel[j] = (int)k;
             ++appended;
         }
+    if (fragile_pt && fragile_pix)
+        for (int i = 0; i < n; ++i)
+            if (land[i] >= 0 && fragile_pix[land[i]]) fragile_pt[i] = 1;
     *count = n + appended;
     free(win);
     free(winz);
+    free(z2nd);
+    free(land);
     return dropped;
 }
 

@@ -77,6 +77,7 @@ void or_vote_matches(const float* uv1, const float* uv2, int n, float bin, float
                      int* score, int* order);
 int or_mosaic_frame(double* pos, double* rgb, double* wpos, double* wrgb, int* count, int capacity,
                     const float* xyz, const uint8_t* img, int W, int H, float f, float cx, float cy,
-                    const float* R, const float* t, float tau, float r0, float gmin);
+                    const float* R, const float* t, float tau, float r0, float gmin,
+                    double eps_pix, double eps_rel, uint8_t* fragile_pix, uint8_t* fragile_pt, int* src_pixel);
 
 #endif

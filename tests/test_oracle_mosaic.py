@@ -103,3 +103,57 @@ def test_capacity_limit_drops_appends():
     assert oracle.mosaic_frame(m, xyz, img, f, 2.5, 1.5, I3, Z3, 0.5) == W * H - 10
     assert m.count == 10
     assert np.allclose(m.pos[:10], xyz.reshape(-1, 3)[:10])
+
+
+def test_equal_depth_tie_goes_to_the_smaller_index():
+    """Two model points at the same depth on the centre ray: the one with the
+    smaller index is kept and merges (hand-derived)."""
+    W, H, f, cx, cy = 5, 5, 10.0, 2.0, 2.0
+    m = oracle.PointModel(10)
+    m.pos[0] = [0.0, 0.0, 10.0]
+    m.pos[1] = [0.0, 0.0, 10.0]
+    m.wpos[:2] = 1.0
+    m.wrgb[:2] = 1.0
+    m.count = 2
+    xyz = np.full((H, W, 3), np.nan, np.float32)
+    xyz[2, 2] = [0.0, 0.0, 10.2]
+    img = np.zeros((H, W, 3), np.uint8)
+    _, mg = oracle.mosaic_frame(m, xyz, img, f, cx, cy, I3, Z3, 0.5, margins=(1e-3, 1e-6))
+    assert m.count == 2 and m.wpos[0] == 2.0 and m.wpos[1] == 1.0
+    assert abs(m.pos[0, 2] - (10.0 + float(np.float32(10.2))) / 2) < 1e-12
+    # the tie itself is a decision a narrower precision could take differently
+    assert mg["fragile_pix"][2, 2] and mg["fragile_pt"].all()
+
+
+def test_decision_margins():
+    """Margins: a point whose projection lies on a rounding edge marks both
+    pixels of the edge; a merge test at its threshold marks its pixel;
+    decisions far from any edge mark nothing."""
+    W, H, f, cx, cy = 8, 6, 10.0, 3.0, 2.0
+    m = oracle.PointModel(20)
+    # pixel (u, v) = (5, 2): X/Z * f + cx = 5 -> X = 2 Z / f; exactly centred
+    m.pos[0] = [2.0, 0.0, 10.0]
+    # u + 1/2 = 3.5 + 1/2 = 4: on the edge between pixels 3 and 4 of row 3
+    m.pos[1] = [0.5, 1.0, 10.0]
+    m.wpos[:2] = 1.0
+    m.wrgb[:2] = 1.0
+    m.count = 2
+    xyz = np.full((H, W, 3), np.nan, np.float32)
+    xyz[2, 5] = [2.0, 0.0, 10.5]          # |Q.z - X.z| = 0.5 = tau exactly
+    img = np.zeros((H, W, 3), np.uint8)
+    _, mg = oracle.mosaic_frame(m, xyz, img, f, cx, cy, I3, Z3, 0.5, margins=(1e-3, 1e-6))
+    fp = mg["fragile_pix"]
+    assert fp[2, 5]                                        # merge test at its threshold
+    assert fp[3, 3] and fp[3, 4]                           # both sides of the rounding edge
+    assert fp.sum() == 3
+    assert mg["fragile_pt"].tolist() == [True, True]
+    assert m.wpos[0] == 2.0                                # |dz| <= tau merges
+    # away from the edges nothing is marked
+    m2 = oracle.PointModel(20)
+    m2.pos[0] = [2.0, 0.0, 10.0]
+    m2.wpos[0] = m2.wrgb[0] = 1.0
+    m2.count = 1
+    xyz[2, 5] = [2.0, 0.0, 10.2]
+    _, mg = oracle.mosaic_frame(m2, xyz, img, f, cx, cy, I3, Z3, 0.5, margins=(1e-3, 1e-6))
+    assert not mg["fragile_pix"].any() and not mg["fragile_pt"].any()
+    assert m2.count == 1 and m2.wpos[0] == 2.0
