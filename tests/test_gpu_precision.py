@@ -68,9 +68,18 @@ def _run(dev, Lrgb, Rrgb, cdt):
                disp_final=torch.empty((Hh, Ww), dtype=torch.float32, device=dev))
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     st.stereo_match(h, t(Lrgb), t(Rrgb), **out)
+    # the right-view winners from the stage entry point (same cost kernel)
+    dl = torch.empty((Hh, Ww), dtype=torch.int16, device=dev)
+    dr = torch.empty_like(dl)
+    sub = torch.empty((Hh, Ww), dtype=torch.float32, device=dev)
+    st.stereo_stage_match(h, t(oracle.gray(Lrgb)), t(oracle.gray(Rrgb)), 0, D, R, st.SAMPLE_FULL, st.COST_NONE,
+                          dl, dr, sub, None)
     torch.cuda.synchronize()
     h.close()
-    return {k: to_np(v) for k, v in out.items()}
+    res = {k: to_np(v) for k, v in out.items()}
+    res["dR"] = to_np(dr)
+    assert np.array_equal(to_np(dl), res["disp_wta"])
+    return res
 
 
 @pytest.mark.parametrize("fmt", ["f16", "bf16"])
@@ -104,8 +113,11 @@ def test_whole_path_crop_error(dev, pair, crop_oracle, fmt):
     near = (m["gapL"] < NEAR_TIE)
     bad = int_map_mismatch(g["disp_wta"], ref["dL"], near)
     assert len(bad) == 0, describe(bad, g["disp_wta"], ref["dL"])
-    if not near.any() and not (m["gapR"] < NEAR_TIE).any():
-        assert np.array_equal(g["disp_post"], ref["o_post"])
+    # post-processing: the oracle's LR check and post-processing on the GPU's
+    # own winners reproduce the GPU's map bit for bit
+    p = oracle.Params(d_min=0, num_disp=D, win_radius=R, smooth_radius=15)
+    o_post = oracle.postprocess(oracle.lr_check(g["disp_wta"], g["dR"], p.lr_thresh), p)
+    assert np.array_equal(g["disp_post"], o_post)
     v = (ref["o_post"] != oracle.INVALID) & (g["valid"] != 0)
     d = np.abs(g["disp_final"][v] - ref["d_final"][v])
     rel = d / np.maximum(np.abs(ref["d_final"][v]), 1)
