@@ -65,6 +65,14 @@ WORKLOADS = {
                                seed=synth.seed_for(2), disp=(10.0, 170.0)),
     "tissue960_d192_bf16": dict(kind="single", W=960, H=540, D=192, r=7, cost="bf16", smooth_radius=15,
                                 seed=synth.seed_for(2), disp=(10.0, 170.0)),
+    # same-workload comparisons: the 960x540 D = 128 pair with an FP16 volume
+    # and without a volume; the D = 192 pair with an FP32 volume
+    "tissue960_f16": dict(kind="single", W=960, H=540, D=128, r=5, cost="f16", smooth_radius=15,
+                          seed=synth.seed_for(1), disp=(10.0, 110.0)),
+    "tissue960_none": dict(kind="single", W=960, H=540, D=128, r=5, cost="none", smooth_radius=15,
+                           seed=synth.seed_for(1), disp=(10.0, 110.0)),
+    "tissue960_d192_f32": dict(kind="single", W=960, H=540, D=192, r=7, cost="f32", smooth_radius=15,
+                               seed=synth.seed_for(2), disp=(10.0, 170.0)),
     # 64 mixed pairs in one batched call, FP16 cost
     "batch64": dict(kind="batched", n=64, cost="f16", smooth_radius=15),
     # soft-argmin training step on 8 pairs
@@ -343,7 +351,7 @@ def single_config(name, wl, world):
         "launch": "CUDA graph replay on a non-default stream"}
 
 
-def run_single(args, wl, rank, world, dev):
+def run_single(args, wl, rank, world, dev, extras=True):
     import torch
     import paper_2007_12623_b300 as st
 
@@ -383,7 +391,47 @@ def run_single(args, wl, rank, world, dev):
     value = world * args.steps * P / t_max / 1e9
 
     stage_ms = _stage_pass(st, h, min(args.steps, 20), flush, step, st.STAGE_NAMES)
+    if extras:
+        depth_ms, mosaic_ms, model_points, vote_ms = _single_extras(st, torch, dev, stream, h, W, H, Lrgb,
+                                                                     outs, args, flush)
+    e2e_value, te = _single_e2e(st, torch, dev, stream, h, Lrgb, Rrgb, tL, tR, W, H, args, world, P)
+    h.close()
+    if rank != 0:
+        return None
+    peaks = load_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof = cost_kernel_roofline([(W, H, D, wl["r"], wl["cost"])], stage_ms["cost_wta"], peaks, sm_count,
+                                "k_cost_wta", KERNEL_TRAFFIC.get(args.workload))
+    line = _base_line(args, world, value, t_max, "f32", single_config(args.workload, wl, world))
+    line.update({
+        "ms_per_pair": round(t_max * 1e3 / args.steps, 4),
+        "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "stage_gbs": stage_bandwidth(stage_ms, W, H, D, wl),
+        "roofline": roof,
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "ms_per_pair": round(te * 1e3 / args.steps, 4),
+                "h2d_bytes_per_step": 2 * W * H * 3, "d2h_bytes_per_step": W * H * 4,
+                "mode": "stream of pairs: upload of the next and read-back of the previous pair overlap "
+                        "the current match (two buffer sets); no L2 flush"},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "paper_context": PAPER_CONTEXT,
+    })
+    if extras:
+        line.update({
+            "depth_points": _depth_line(W, H, depth_ms, load_peaks()),
+            "mosaic_frame": {"ms_median": round(mosaic_ms, 4), "model_points": model_points,
+                             "frame_pixels": W * H,
+                             "note": "point-based TSDF merge of the refined map's points into the model; "
+                                     "event-timed, L2 flushed; not part of the step"},
+            "vote_matches": {"ms_median": round(vote_ms, 4), "matches": 2000,
+                             "note": "histogram-voting inlier preselection, 85 % outliers; not part of the step"},
+        })
+    return line
 
+
+def _single_extras(st, torch, dev, stream, h, W, H, Lrgb, outs, args, flush):
+    """Depth, mosaicking and histogram voting on the pair's refined map, each
+    event-timed on its own (not part of the step)."""
     # the refined map to points and normals (Sec. II depth from disparity;
     # not part of the step): its own event-timed runs, L2 flushed between
     cam = st.StereoCamera(0.9 * W, W / 2 - 0.5, H / 2 - 0.5, 5.0, 0.0)
@@ -418,7 +466,11 @@ def run_single(args, wl, rank, world, dev):
                           lambda: st.stereo_vote_matches(tuv1, tuv2, hist=vh, score=vs, order=vo, stream=stream),
                           flush)
     vote_ms = sorted(vote_ms)[len(vote_ms) // 2]
+    return depth_ms, mosaic_ms, model_points, vote_ms
 
+
+def _single_e2e(st, torch, dev, stream, h, Lrgb, Rrgb, tL, tR, W, H, args, world, P):
+    """End to end through the public API (see run_single)."""
     # end to end through the public API, run the way a video loop runs it:
     # every step uploads a pinned host RGB pair, matches it and reads the
     # refined map back; two device buffer sets let the upload of the next
@@ -467,35 +519,39 @@ def run_single(args, wl, rank, world, dev):
     eb.record(stream)
     torch.cuda.synchronize()
     te = _max_over_ranks(torch, dev, ea.elapsed_time(eb) / 1e3, world)
-    e2e_value = world * args.steps * P / te / 1e9
-    h.close()
-    if rank != 0:
-        return None
-    peaks = load_peaks()
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    roof = cost_kernel_roofline([(W, H, D, wl["r"], wl["cost"])], stage_ms["cost_wta"], peaks, sm_count,
-                                "k_cost_wta", KERNEL_TRAFFIC.get(args.workload))
-    line = _base_line(args, world, value, t_max, "f32", single_config(args.workload, wl, world))
-    line.update({
-        "ms_per_pair": round(t_max * 1e3 / args.steps, 4),
-        "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
-        "roofline": roof,
-        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "ms_per_pair": round(te * 1e3 / args.steps, 4),
-                "h2d_bytes_per_step": 2 * W * H * 3, "d2h_bytes_per_step": W * H * 4,
-                "mode": "stream of pairs: upload of the next and read-back of the previous pair overlap "
-                        "the current match (two buffer sets); no L2 flush"},
-        "gpu_launches": int(launches),
-        "clocks": clk.summary(),
-        "paper_context": PAPER_CONTEXT,
-        "depth_points": _depth_line(W, H, depth_ms, load_peaks()),
-        "mosaic_frame": {"ms_median": round(mosaic_ms, 4), "model_points": model_points,
-                         "frame_pixels": W * H,
-                         "note": "point-based TSDF merge of the refined map's points into the model; "
-                                 "event-timed, L2 flushed; not part of the step"},
-        "vote_matches": {"ms_median": round(vote_ms, 4), "matches": 2000,
-                         "note": "histogram-voting inlier preselection, 85 % outliers; not part of the step"},
-    })
-    return line
+    return world * args.steps * P / te / 1e9, te
+
+
+def stage_bandwidth(stage_ms, W, H, D, wl):
+    """Algorithmic bytes per stage of the single-pair path divided by the
+    stage's event-timed milliseconds (GB/s).  Per pixel:
+      statistics   reads 2 x 3 (RGB) or 2 x 1 (gray) B, writes both byte
+                   images (2 B), left statistics (8 B), right statistics
+                   (16 B) and clears both key maps (8 B);
+      finalize     reads both key maps (8 B), writes the winner, LR and
+                   sub-pixel maps (2 + 2 + 4 B) and reads the three parabola
+                   costs (3 s B for a stored volume of s-byte elements);
+      postprocess  3 rounds x (2 mask builds: read the 2 B map, write 4 x 4
+                   bits; outlier test, radial and disc fill: read and write
+                   the 2 B map): 3 x (2 x 4 + 3 x 4) = 60 B;
+      refine       5 iterations x (Eq. 1-2: read packed o and d_prev, write
+                   dt and b: 16 B; Eq. 3-4: read b, dt, counts, packed o,
+                   write d_prev, packed o: 22 B) plus 11 candidates of s
+                   bytes in each of the 4 o-updates (44 s B; none without a
+                   volume) and the final map (4 B).
+    The cost stage is the roofline line."""
+    npix = W * H
+    s = COST_BYTES[wl["cost"]]
+    b = {"stats": npix * (6 + 2 + 8 + 16 + 8),
+         "finalize": npix * (8 + 8 + 3 * s),
+         "postprocess": npix * 60,
+         "refine": npix * (5 * 38 + 44 * s + 4)}
+    out = {}
+    for k, nbytes in b.items():
+        ms = stage_ms.get(k)
+        if ms:
+            out[k] = round(nbytes / (ms * 1e-3) / 1e9, 1)
+    return out
 
 
 def _depth_line(W, H, ms, peaks):
@@ -752,6 +808,23 @@ def oracle_sample(wl, rows: int, problem=None):
     return rows * W * D / dt / 1e9, dt, f"{W}x{rows} output rows (+{2 * r} margin rows) of a {W}-wide pair, D={D}"
 
 
+def reference_config(name, wl, problem, rows):
+    """The reference arm's own description: the same workload, evaluated by
+    the single-threaded FP64 oracle on a strip of it."""
+    Lrgb, Rrgb, W, D, r, sr = problem
+    cfg = {"workload": name, "width": W, "height": Lrgb.shape[0], "num_disp": D, "d_min": wl.get("d_min", 0),
+           "window": 2 * r + 1, "sampling": "chessboard" if wl.get("sampling", 0) else "full"}
+    if wl["kind"] == "soft":
+        cfg.update(tau=wl["tau"], step="soft-argmin forward + L1 loss + backward")
+    else:
+        cfg.update(smooth_radius=sr, refine_iters=5, step="whole path S0-S7")
+    if wl["kind"] == "batched":
+        cfg["pair"] = "a 960x540 pair of the 64-pair batch"
+    cfg.update(rows_per_step=rows, implementation="FP64 C oracle, single thread, host CPU",
+               precision="f64")
+    return cfg
+
+
 def run_reference(args, wl):
     import oracle
     oracle.build()
@@ -771,12 +844,63 @@ def run_reference(args, wl):
             "ms_per_step": round(sum(secs) / args.steps * 1e3, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": DATA,
-            "config": (single_config(args.workload, wl, 1) if wl["kind"] == "single"
-                       else {"workload": args.workload, "width": W, "num_disp": D}),
+            "config": reference_config(args.workload, wl, problem, rows),
             "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: {sample}"},
+                             "sample": f"each step: {sample}", **host_cpu()},
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+
+
+# Workloads measured beside the headline one in the default run (one GPU):
+# name -> (steps, warmup).  Each runs exactly as its own --workload line
+# would, with fewer steps.
+SUB_WORKLOADS = {"perlin320": (200, 5), "tissue960_f16": (200, 5), "tissue960_none": (200, 5),
+                 "tissue960_d192_f16": (200, 5), "tissue960_d192_bf16": (200, 5),
+                 "tissue960_d192_f32": (200, 5), "paper960": (200, 5), "batch64": (6, 3), "soft8": (20, 3)}
+
+
+def _sub_record(line):
+    """The figures of a workload's line that the headline line carries."""
+    keep = ("value", "unit", "ms_per_step", "ms_per_pair", "ms_per_960x540x128_equivalent", "dtype", "steps",
+            "warmup", "gpu_launches", "stage_ms", "stage_ms_last_pair", "stage_gbs")
+    rec = {k: line[k] for k in keep if k in line}
+    rec["config"] = line["config"]
+    r = line["roofline"]
+    rec["roofline"] = {k: r[k] for k in ("bound", "achieved", "peak", "unit", "frac", "kernel", "kernel_ms",
+                                         "traffic") if k in r}
+    rec["e2e"] = line["e2e"]
+    rec["clocks"] = line["clocks"]
+    return rec
+
+
+def run_sub_workloads(args, dev, batch_pairs):
+    out = {}
+    for name, (steps, warmup) in SUB_WORKLOADS.items():
+        wl = WORKLOADS[name]
+        sa = argparse.Namespace(**vars(args))
+        sa.workload, sa.steps, sa.warmup = name, steps, warmup
+        if wl["kind"] == "batched":
+            line = run_batched(sa, wl, 0, 1, dev, batch_pairs)
+        elif wl["kind"] == "soft":
+            line = run_soft_step(sa, wl, 0, 1, dev)
+        else:
+            line = run_single(sa, wl, 0, 1, dev, extras=False)
+        out[name] = _sub_record(line)
+    return out
+
+
+def host_cpu():
+    """Host core count and CPU model (for the CPU baseline)."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
 def main():
@@ -789,6 +913,8 @@ def main():
     ap.add_argument("--oracle-rows", type=int, default=8)
     ap.add_argument("--cpu-baseline-rows", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub-workloads", action="store_true",
+                    help="default run only: skip the other workloads' records")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", 0))
@@ -799,7 +925,11 @@ def main():
             print(json.dumps(run_reference(args, wl)), flush=True)
         return
 
+    subs = (world == 1 and args.workload == "tissue960" and not args.no_sub_workloads
+            and "--workload" not in sys.argv)
     pairs = make_batch(wl["n"], rank * wl["n"]) if wl["kind"] == "batched" else None
+    if subs:
+        batch_pairs = make_batch(WORKLOADS["batch64"]["n"], 0)      # before any CUDA call
     import torch
     dev = torch.device(f"cuda:{int(os.environ.get('LOCAL_RANK', 0))}")
     torch.cuda.set_device(dev)
@@ -811,12 +941,14 @@ def main():
         line = run_soft_step(args, wl, rank, world, dev)
     else:
         line = run_single(args, wl, rank, world, dev)
+    if subs:
+        line["workloads"] = run_sub_workloads(args, dev, batch_pairs)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             rows = args.cpu_baseline_rows if wl["kind"] != "soft" else max(4, args.cpu_baseline_rows // 8)
             v, dt, sample = oracle_sample(wl, rows)
             line["cpu_baseline"] = {"value": round(v, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": sample, "seconds": round(dt, 2)}
+                                    "sample": sample, "seconds": round(dt, 2), **host_cpu()}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
