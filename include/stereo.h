@@ -164,15 +164,36 @@ stereo_status stereo_match_batched(stereo_handle* h, const stereo_pair* pairs, i
                                    int32_t use_graph, void* stream);
 
 /* Batch configuration: output rows per work unit (0 = default 16) and
- * disparities per lane K (2 or 4; 0 = automatic: 2 when every pair has at
- * most 64 candidates, else 4). */
+ * disparities per lane K of the persistent cost launches (2 or 4 for every
+ * pair; 0 = per pair, as the single-pair path splits its range: K = 2 for
+ * D <= 64, K = 4 chunks of 128 disparities, and the rest of a range such as
+ * D = 192 in K = 2 chunks of 64).  The K = 4 units and the K = 2 units run
+ * as two persistent launches, one after the other. */
 stereo_status stereo_set_batch_config(stereo_handle* h, int32_t rows, int32_t K);
 
-/* Autotuner of the batched form: runs the batch once per candidate
- * configuration (K in {2, 4} x rows in {8, 12, 16, 24, 32, 48}), times the
- * persistent cost stage with CUDA events, and keeps the fastest in the
- * handle.  Synchronises `stream`; not allowed inside a capture.  Writes the
- * choice and its time (ms) when the pointers are non-NULL. */
+/* How the per-pair stages of a batch (preparation, finalize, the outlier /
+ * hole-filling rounds, the refinement iterations; Sec. II-B, II-C) run:
+ * mode 0 (default) -- each pair's launches on up to 8 parallel streams
+ * owned by the handle; mode 1 -- one launch per stage over all pairs of the
+ * batch (a flat grid of every pair's blocks; each block finds its pair in a
+ * table of cumulative block counts), with the per-pair launches as the
+ * fallback when the post-processing or refinement parameters exceed the
+ * tiled kernels' limits (outlier radius <= 64, radial fill radius <= 63,
+ * disc radius <= 56, smoothing radius <= 32).  Both modes give the same
+ * outputs bit for bit.  Returns STEREO_ERR_INVALID_ARG for another mode. */
+stereo_status stereo_set_batch_stages(stereo_handle* h, int32_t mode);
+
+/* The batch configuration in use: rows per unit, K (0 = per pair) and the
+ * stage mode (any pointer may be NULL). */
+stereo_status stereo_get_batch_config(const stereo_handle* h, int32_t* rows, int32_t* K, int32_t* stages);
+
+/* Autotuner of the batched form: runs the batch once per candidate unit
+ * configuration (K in {0 = per pair, 2, 4} x rows in {8, 12, 16, 24, 32,
+ * 48}) and times the persistent cost stage with CUDA events; then times
+ * whole passes in both stage modes with the fastest configuration, and keeps
+ * the choices in the handle.  Synchronises `stream`; not allowed inside a
+ * capture.  Writes the unit configuration and its cost-stage time (ms) when
+ * the pointers are non-NULL (stereo_get_batch_config reads the stage mode). */
 stereo_status stereo_autotune_batched(stereo_handle* h, const stereo_pair* pairs, int32_t n, void* stream,
                                       int32_t* best_rows, int32_t* best_K, float* best_ms);
 

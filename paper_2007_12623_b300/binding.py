@@ -21,6 +21,7 @@ __all__ = [
     "stereo_get_stage_times", "stereo_launch_count", "STAGE_NAMES", "stereo_set_tuning",
     "stereo_match_wta_noalloc", "stereo_softargmin_fwd", "stereo_softargmin_bwd", "stereo_l1_loss",
     "SoftArgminZNCC", "soft_argmin", "stereo_set_batch_config", "stereo_autotune_batched",
+    "stereo_set_batch_stages", "stereo_get_batch_config",
     "StereoCamera", "stereo_depth_points", "PointModel", "stereo_mosaic_frame", "stereo_vote_nbins",
     "stereo_vote_matches",
 ]
@@ -125,6 +126,8 @@ def lib():
             "stereo_mosaic_frame": (C.c_int, [P, P, P, P, i32, i32, P, P, P, C.c_float, C.c_float,
                                               C.c_float, P]),
             "stereo_set_batch_config": (C.c_int, [P, i32, i32]),
+            "stereo_set_batch_stages": (C.c_int, [P, i32]),
+            "stereo_get_batch_config": (C.c_int, [P, P, P, P]),
             "stereo_autotune_batched": (C.c_int, [P, P, i32, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -282,14 +285,26 @@ def stereo_set_batch_config(handle: Handle, rows: int = 0, K: int = 0):
     _check(lib().stereo_set_batch_config(handle.ptr, rows, K), "stereo_set_batch_config")
 
 
+def stereo_set_batch_stages(handle: Handle, mode: int = 0):
+    _check(lib().stereo_set_batch_stages(handle.ptr, mode), "stereo_set_batch_stages")
+
+
+def stereo_get_batch_config(handle: Handle) -> dict:
+    rows, K, stages = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().stereo_get_batch_config(handle.ptr, C.byref(rows), C.byref(K), C.byref(stages)),
+           "stereo_get_batch_config")
+    return dict(rows=rows.value, K=K.value, stages=stages.value)
+
+
 def stereo_autotune_batched(handle: Handle, pairs, stream=None):
-    """Times the batched cost stage for each candidate configuration and keeps
-    the fastest; returns dict(rows, K, ms)."""
+    """Times the batched cost stage for each candidate unit configuration and
+    both stage modes, and keeps the fastest; returns dict(rows, K, ms,
+    stages)."""
     arr = _pair_array(pairs)
     rows, K, ms = C.c_int32(), C.c_int32(), C.c_float()
     _check(lib().stereo_autotune_batched(handle.ptr, arr, len(pairs), _stream(stream), C.byref(rows),
                                          C.byref(K), C.byref(ms)), "stereo_autotune_batched")
-    return dict(rows=rows.value, K=K.value, ms=ms.value)
+    return dict(rows=rows.value, K=K.value, ms=ms.value, stages=stereo_get_batch_config(handle)["stages"])
 
 
 def stereo_get_device_error(handle: Handle, stream=None) -> int:

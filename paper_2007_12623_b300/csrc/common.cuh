@@ -53,6 +53,31 @@ __device__ __forceinline__ float cost_load(const void* base, int cdt, size_t idx
     return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(base)[idx]);
 }
 
+// Block coordinates of a kernel body: its block index and the grid's extent
+// in x and y.  A plain launch passes blockIdx and gridDim; a batched launch
+// (one grid over the blocks of many pairs) passes the block's coordinates
+// within its own pair's grid.
+struct VBlock {
+    int x, y, z, nx, ny;
+};
+__device__ __forceinline__ VBlock vblock() {
+    return VBlock{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x, (int)gridDim.y};
+}
+
+// Batched launches: the flat grid is the concatenation of the pairs' grids,
+// start[i] = first flat block of pair i (start[0] = 0, start[n] = total,
+// nondecreasing).  Returns the pair that owns flat block b < start[n]: the
+// largest i with start[i] <= b (a pair with an empty grid is never it).
+__device__ __forceinline__ int batch_pair(const int* __restrict__ start, int n, int b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(start + mid) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // floor(a / b) for b > 0.
 __device__ __forceinline__ int floordiv_pos(int a, int b) {
     int q = a / b;

@@ -167,15 +167,39 @@ __device__ __forceinline__ void costs3_fp32(const uint8_t* __restrict__ L, const
 // (no volume, or one stored in FP16/BF16 whose rounding would move the
 // offset by up to ~0.03 px) recomputes them with costs3_fp32 (R > 0) or, with
 // no statistics, by the direct definition (R = 0).
+struct FinArgs {
+    const uint32_t* keyL;
+    const uint32_t* keyR;
+    int W, H, d_min, D, lr_thresh;
+    const void* cost;
+    int cdt;
+    const uint8_t* L;
+    const uint8_t* Rm;
+    int r, sampling;
+    FinStats fs;
+    int16_t* disp_left;
+    int16_t* disp_right;
+    float* disp_sub;
+    int16_t* disp_lr;
+};
+
+// Row vb.y, columns 128 vb.x .. 128 vb.x + 127 (128 threads).
 template <int R, bool CB>
-__global__ void k_finalize(const uint32_t* __restrict__ keyL, const uint32_t* __restrict__ keyR,
-                           int W, int H, int d_min, int D, int lr_thresh, const void* __restrict__ cost,
-                           int cdt, const uint8_t* __restrict__ L, const uint8_t* __restrict__ Rm, int r,
-                           int sampling, FinStats fs, int16_t* __restrict__ disp_left,
-                           int16_t* __restrict__ disp_right, float* __restrict__ disp_sub,
-                           int16_t* __restrict__ disp_lr) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
+__device__ __forceinline__ void finalize_run(const FinArgs& f, VBlock vb) {
+    const uint32_t* __restrict__ keyL = f.keyL;
+    const uint32_t* __restrict__ keyR = f.keyR;
+    const int W = f.W, H = f.H, d_min = f.d_min, D = f.D, lr_thresh = f.lr_thresh, cdt = f.cdt, r = f.r,
+              sampling = f.sampling;
+    const void* __restrict__ cost = f.cost;
+    const uint8_t* __restrict__ L = f.L;
+    const uint8_t* __restrict__ Rm = f.Rm;
+    const FinStats& fs = f.fs;
+    int16_t* __restrict__ disp_left = f.disp_left;
+    int16_t* __restrict__ disp_right = f.disp_right;
+    float* __restrict__ disp_sub = f.disp_sub;
+    int16_t* __restrict__ disp_lr = f.disp_lr;
+    const int x = vb.x * 128 + threadIdx.x;
+    const int y = vb.y;
     if (x >= W) return;
     const size_t i = (size_t)y * W + x;
     const int dl = key_to_disp(keyL[i], d_min);
@@ -222,6 +246,11 @@ __global__ void k_finalize(const uint32_t* __restrict__ keyL, const uint32_t* __
     }
 }
 
+template <int R, bool CB>
+__global__ void __launch_bounds__(128) k_finalize(FinArgs f) {
+    finalize_run<R, CB>(f, vblock());
+}
+
 // Launches k_finalize for window radius r (FP32 recompute from the
 // preparation kernel's statistics of either sampling; the direct definition
 // when there are none).
@@ -231,9 +260,10 @@ static void launch_finalize(const uint32_t* keyL, const uint32_t* keyR, int W, i
                             float* disp_sub, int16_t* disp_lr, cudaStream_t s) {
     const dim3 g((W + 127) / 128, H);
     const int rr = fs.lstats ? r : 0;
+    const FinArgs f{keyL, keyR, W, H, d_min, D, lr_thresh, cost, cdt, L, Rm, r, sampling, fs,
+                    disp_left, disp_right, disp_sub, disp_lr};
 #define FIN_CASE(RV, CBV) \
-    case RV: k_finalize<RV, CBV><<<g, 128, 0, s>>>(keyL, keyR, W, H, d_min, D, lr_thresh, cost, cdt, L, Rm, r, \
-                                                  sampling, fs, disp_left, disp_right, disp_sub, disp_lr); break;
+    case RV: k_finalize<RV, CBV><<<g, 128, 0, s>>>(f); break;
     if (sampling == 1) {
         switch (rr) {
             FIN_CASE(1, true) FIN_CASE(2, true) FIN_CASE(3, true) FIN_CASE(4, true) FIN_CASE(5, true)

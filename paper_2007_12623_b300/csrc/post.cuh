@@ -186,9 +186,8 @@ __device__ __forceinline__ uint64_t low_bits(int n) { return n >= 64 ? ~0ull : (
 // Outlier test (radius <= 64) from smooth-edge masks: direction +step from
 // position pos needs the edge bits pos .. pos+r-1, direction -step the bits
 // pos-r .. pos-1.
-__global__ void __launch_bounds__(256) k_outlier_masks(const int16_t* __restrict__ in, LineMasks m,
-                                                       int radius, int16_t* __restrict__ out) {
-    const long pix = (long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void outlier_masks_px(const int16_t* __restrict__ in, const LineMasks& m, int radius,
+                                                 int16_t* __restrict__ out, long pix) {
     if (pix >= (long)m.W * m.H) return;
     const int x = (int)(pix % m.W), y = (int)(pix / m.W);
     const int v = in[pix];
@@ -207,13 +206,17 @@ __global__ void __launch_bounds__(256) k_outlier_masks(const int16_t* __restrict
     out[pix] = keep ? (int16_t)v : (int16_t)ST_INVALID;
 }
 
+__global__ void __launch_bounds__(256) k_outlier_masks(const int16_t* __restrict__ in, LineMasks m,
+                                                       int radius, int16_t* __restrict__ out) {
+    outlier_masks_px(in, m, radius, out, (long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // The same test for radius <= 32 (the paper's radii): per family, the three
 // words around the pixel's position give the 32 edge bits from pos (forward
 // ray) and the 32 before pos (backward ray) with one funnel shift each;
 // 32-bit word offsets (a mask buffer holds fewer than 2^32 words).
-__global__ void __launch_bounds__(256) k_outlier_masks32(const int16_t* __restrict__ in, LineMasks m,
-                                                         int radius, int16_t* __restrict__ out) {
-    const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void outlier_masks32_px(const int16_t* __restrict__ in, const LineMasks& m, int radius,
+                                                   int16_t* __restrict__ out, int pix) {
     if (pix >= m.W * m.H) return;
     const int y = pix / m.W, x = pix - y * m.W;
     // the word loads depend on (x, y) only: they go out with the pixel's own
@@ -243,6 +246,11 @@ __global__ void __launch_bounds__(256) k_outlier_masks32(const int16_t* __restri
         }
     }
     out[pix] = keep ? (int16_t)v : (int16_t)ST_INVALID;
+}
+
+__global__ void __launch_bounds__(256) k_outlier_masks32(const int16_t* __restrict__ in, LineMasks m,
+                                                         int radius, int16_t* __restrict__ out) {
+    outlier_masks32_px(in, m, radius, out, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // First hole-filling method (radius <= 63) from valid masks: the nearest
@@ -281,13 +289,17 @@ __device__ __forceinline__ int radial_fill_at(const int16_t* __restrict__ in, co
     return (found >= min_dirs && den > 0) ? round_half_up_i(num, den) : ST_INVALID;
 }
 
-__global__ void __launch_bounds__(256) k_fill_radial_masks(const int16_t* __restrict__ in, LineMasks m,
-                                                           int radius, int min_dirs,
-                                                           int16_t* __restrict__ out) {
-    const long pix = (long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void fill_radial_masks_px(const int16_t* __restrict__ in, const LineMasks& m, int radius,
+                                                     int min_dirs, int16_t* __restrict__ out, long pix) {
     if (pix >= (long)m.W * m.H) return;
     const int x = (int)(pix % m.W), y = (int)(pix / m.W);
     out[pix] = (int16_t)radial_fill_at(in, m, radius, min_dirs, x, y, in[pix]);
+}
+
+__global__ void __launch_bounds__(256) k_fill_radial_masks(const int16_t* __restrict__ in, LineMasks m,
+                                                           int radius, int min_dirs,
+                                                           int16_t* __restrict__ out) {
+    fill_radial_masks_px(in, m, radius, min_dirs, out, (long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Tiled build of the line bitmasks: block (bc, br) stages image columns
@@ -348,10 +360,11 @@ __device__ __forceinline__ void line_mask_words(const int16_t (*t)[LM_COLS], con
     }
 }
 
-__global__ void __launch_bounds__(256) k_line_masks_tiled(const int16_t* __restrict__ in, LineMasks m,
-                                                          int mode, int ithr) {
+// Block (vb.x, vb.y) of the grid ((W + 31) / 32, (H + 31) / 32 + 1).
+__device__ __forceinline__ void line_masks_tile(const int16_t* __restrict__ in, const LineMasks& m, int mode,
+                                                int ithr, VBlock vb) {
     __shared__ __align__(4) int16_t t[LM_ROWS][LM_COLS];
-    const int bc = blockIdx.x, br = (int)blockIdx.y - 1;
+    const int bc = vb.x, br = vb.y - 1;
     const int X0 = 32 * bc, Y0 = 32 * br - 1;            // staged row 0 is image row Y0
     const bool pairs = (m.W & 1) == 0 && (reinterpret_cast<uintptr_t>(in) & 3) == 0;
     // all staging loads of a thread go out before their values are stored
@@ -387,4 +400,9 @@ __global__ void __launch_bounds__(256) k_line_masks_tiled(const int16_t* __restr
         case 2: line_mask_words<2>(t, m, mode, ithr, bc, br); break;
         default: line_mask_words<3>(t, m, mode, ithr, bc, br); break;
     }
+}
+
+__global__ void __launch_bounds__(256) k_line_masks_tiled(const int16_t* __restrict__ in, LineMasks m,
+                                                          int mode, int ithr) {
+    line_masks_tile(in, m, mode, ithr, vblock());
 }

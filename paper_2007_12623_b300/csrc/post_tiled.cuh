@@ -30,9 +30,9 @@ inline size_t disc_local_smem(int r) {
     return ((size_t)(DL_TH + 2 * r) * (DL_TW + 2 * r + 1) + 2 * r + 1) * 4;
 }
 
-__global__ void __launch_bounds__(DL_THREADS, 4) k_fill_disc_local(const int16_t* __restrict__ in, int W, int H,
-                                                                int r, int min_count,
-                                                                int16_t* __restrict__ out) {
+// Tile (vb.x, vb.y) of the grid ((W + DL_TW - 1) / DL_TW, (H + DL_TH - 1) / DL_TH).
+__device__ __forceinline__ void fill_disc_tile(const int16_t* __restrict__ in, int W, int H, int r, int min_count,
+                                               int16_t* __restrict__ out, VBlock vb) {
     extern __shared__ uint32_t dsm[];
     const int n = DL_TW + 2 * r;              // staged columns
     const int P = n + 1;                      // prefix row pitch
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(DL_THREADS, 4) k_fill_disc_local(const int16_t
     uint32_t* pre = dsm;                      // [SR][P]
     int* wtab = reinterpret_cast<int*>(dsm + (size_t)SR * P);   // [2 r + 1]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int x0 = blockIdx.x * DL_TW, y0 = blockIdx.y * DL_TH;
+    const int x0 = vb.x * DL_TW, y0 = vb.y * DL_TH;
     const int x = x0 + lane;
     int v[DL_PPT];
     bool hole[DL_PPT], any = false;
@@ -143,4 +143,10 @@ __global__ void __launch_bounds__(DL_THREADS, 4) k_fill_disc_local(const int16_t
         out[(size_t)y * W + x] = (cnt >= min_count && cnt > 0) ? (int16_t)round_half_up_i(sum, cnt)
                                                               : (int16_t)ST_INVALID;
     }
+}
+
+__global__ void __launch_bounds__(DL_THREADS, 4) k_fill_disc_local(const int16_t* __restrict__ in, int W, int H,
+                                                                int r, int min_count,
+                                                                int16_t* __restrict__ out) {
+    fill_disc_tile(in, W, H, r, min_count, out, vblock());
 }

@@ -76,19 +76,31 @@ __device__ __forceinline__ void border_nan_slices(void* __restrict__ cost, int c
 // even, centre included, N = ((2r+1)^2 + 1) / 2 samples; the row pass keeps
 // the sums over even and over odd dx apart and the column pass takes the
 // even-dx sum on rows with even dy and the odd-dx sum on the others.
+struct PrepArgs {
+    PrepIn in0, in1;
+    int W, H;
+    PrepOut out0, out1;
+    uint32_t* key_clear;
+    void* cost;
+    int cdt, cs;
+};
+
+// Tile (vb.x, vb.y) of image vb.z (0 left, 1 right) in the grid
+// ((W + PT - 1) / PT, (H + PT - 1) / PT, 2).
 template <bool CB, int R>
-__global__ void __launch_bounds__(256) k_prep(PrepIn in0, PrepIn in1, int W, int H, PrepOut out0, PrepOut out1,
-                                              uint32_t* __restrict__ key_clear, void* __restrict__ cost, int cdt,
-                                              int cs) {
+__device__ __forceinline__ void prep_tile(const PrepArgs& pa, VBlock vb) {
     constexpr int NP = CB ? 2 : 1;
     constexpr int SPAN = PT + 2 * R;
     __shared__ uint16_t t[SPAN][SPAN + 1];
     __shared__ uint32_t rs[NP][SPAN][PT + 1];
     __shared__ uint32_t rss[NP][SPAN][PT + 1];
-    const bool left = blockIdx.z == 0;
-    const PrepIn in = left ? in0 : in1;
-    const PrepOut out = left ? out0 : out1;
-    const int x0 = blockIdx.x * PT, y0 = blockIdx.y * PT;
+    const int W = pa.W, H = pa.H, cdt = pa.cdt, cs = pa.cs;
+    uint32_t* __restrict__ key_clear = pa.key_clear;
+    void* __restrict__ cost = pa.cost;
+    const bool left = vb.z == 0;
+    const PrepIn in = left ? pa.in0 : pa.in1;
+    const PrepOut out = left ? pa.out0 : pa.out1;
+    const int x0 = vb.x * PT, y0 = vb.y * PT;
     const int tid = threadIdx.x;
     for (int i = tid; i < SPAN * SPAN; i += 256) {
         const int ly = i / SPAN, lx = i % SPAN;
@@ -206,7 +218,7 @@ __global__ void __launch_bounds__(256) k_prep(PrepIn in0, PrepIn in1, int W, int
     // padding columns of rows y0 .. y0 + 31, shared among the tile row's blocks
     const int rows = min(PT, H - y0);
     const int npad = out.stride - W;
-    for (int i = blockIdx.x * 256 + tid; i < rows * npad; i += gridDim.x * 256) {
+    for (int i = vb.x * 256 + tid; i < rows * npad; i += vb.nx * 256) {
         const int gy = y0 + i / npad, m = i % npad;
         const size_t o = (size_t)gy * out.stride + (m < out.col0 ? m : W + m);
         if (CB) out.img[o] = 0.f;
@@ -214,13 +226,17 @@ __global__ void __launch_bounds__(256) k_prep(PrepIn in0, PrepIn in1, int W, int
     }
     if (out.ustats) {
         const int upad = out.ustride - W;
-        for (int i = blockIdx.x * 256 + tid; i < rows * upad; i += gridDim.x * 256) {
+        for (int i = vb.x * 256 + tid; i < rows * upad; i += vb.nx * 256) {
             const int gy = y0 + i / upad, m = i % upad;
             out.ustats[(size_t)gy * out.ustride + (m < out.ucol0 ? m : W + m)] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
-    if (left && cost) border_nan_slices<R>(cost, cdt, cs, W, H, blockIdx.y * gridDim.x + blockIdx.x,
-                                           gridDim.x * gridDim.y);
+    if (left && cost) border_nan_slices<R>(cost, cdt, cs, W, H, vb.y * vb.nx + vb.x, vb.nx * vb.ny);
+}
+
+template <bool CB, int R>
+__global__ void __launch_bounds__(256) k_prep(PrepArgs pa) {
+    prep_tile<CB, R>(pa, vblock());
 }
 
 // Zeroes the entries of the soft-argmin A volume (per row and chunk `apitch`

@@ -250,15 +250,15 @@ struct RefineArgs {
 // kernel also writes the packed map, the counts and the valid mask.  The
 // per-pixel loads of the epilogue are issued before the box sums.
 template <bool FIRST, int SPAD>
-__global__ void __launch_bounds__(RB_THREADS) k_refine_eq12(RefineArgs a, const int16_t* __restrict__ o_in,
-                                                            uint8_t* __restrict__ valid) {
+__device__ __forceinline__ void refine_eq12_tile(const RefineArgs& a, const int16_t* __restrict__ o_in,
+                                                 uint8_t* __restrict__ valid, VBlock vb) {
     extern __shared__ __align__(16) uint32_t rsm[];
     constexpr int SWP = RB_T + 2 * SPAD + 1;
     const int rows = rb_rows(a.rs);
     uint32_t* tile = rsm;
     uint32_t* hsum = tile + rows * SWP;
     uint32_t* box = hsum + rows * (RB_T + 1);
-    const int x0 = blockIdx.x * RB_T, y0 = blockIdx.y * RB_T;
+    const int x0 = vb.x * RB_T, y0 = vb.y * RB_T;
     constexpr int NQ = RB_T * RB_T / RB_THREADS;
     float dpv[NQ];
 #pragma unroll
@@ -301,18 +301,24 @@ __global__ void __launch_bounds__(RB_THREADS) k_refine_eq12(RefineArgs a, const 
     }
 }
 
+template <bool FIRST, int SPAD>
+__global__ void __launch_bounds__(RB_THREADS) k_refine_eq12(RefineArgs a, const int16_t* __restrict__ o_in,
+                                                            uint8_t* __restrict__ valid) {
+    refine_eq12_tile<FIRST, SPAD>(a, o_in, valid, vblock());
+}
+
 // Eqs. (3)-(4).  UPDATE: run the o-update (skipped after the last iteration
 // unless the caller reads o); o_out: int16 copy of the new o (or nullptr).
 template <bool UPDATE, int SPAD>
-__global__ void __launch_bounds__(RB_THREADS) k_refine_eq34(RefineArgs a, float* __restrict__ d_out,
-                                                            int16_t* __restrict__ o_out) {
+__device__ __forceinline__ void refine_eq34_tile(const RefineArgs& a, float* __restrict__ d_out,
+                                                 int16_t* __restrict__ o_out, VBlock vb) {
     extern __shared__ __align__(16) float fsm[];
     constexpr int SWP = RB_T + 2 * SPAD + 1;
     const int rows = rb_rows(a.rs);
     float* tile = fsm;
     float* hsum = tile + rows * SWP;
     float* box = hsum + rows * (RB_T + 1);
-    const int x0 = blockIdx.x * RB_T, y0 = blockIdx.y * RB_T;
+    const int x0 = vb.x * RB_T, y0 = vb.y * RB_T;
     constexpr int NQ = RB_T * RB_T / RB_THREADS;
     uint32_t pkv[NQ];
     float dtv[NQ], cntv[NQ], dv[NQ];
@@ -503,5 +509,8 @@ __global__ void __launch_bounds__(RB_THREADS) k_refine_eq34(RefineArgs a, float*
     }
 }
 
-
-
+template <bool UPDATE, int SPAD>
+__global__ void __launch_bounds__(RB_THREADS) k_refine_eq34(RefineArgs a, float* __restrict__ d_out,
+                                                            int16_t* __restrict__ o_out) {
+    refine_eq34_tile<UPDATE, SPAD>(a, d_out, o_out, vblock());
+}

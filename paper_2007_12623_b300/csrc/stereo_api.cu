@@ -21,6 +21,7 @@
 #include "refine_tiled.cuh"
 #include "soft.cuh"
 #include "batch.cuh"
+#include "batch_stages.cuh"
 #include "depth.cuh"
 #include "mosaic.cuh"
 #include "vote.cuh"
@@ -193,6 +194,38 @@ struct GraphCache {
 
 constexpr int BATCH_STREAMS = 8;
 
+// Device tables of the batched stage launches of one batch (carved from the
+// handle's btab buffer by build_batch_tables): per window radius present,
+// the preparation and finalize jobs; per post-processing round, three map
+// jobs (input -> p, p -> q, q -> round output); the refinement jobs; and
+// the cumulative block counts of every launch geometry.
+constexpr int BST_MAX_ROUNDS = 8;
+struct BatchStages {
+    bool ok = false;                 // the batched stage launches apply (else per-pair launches)
+    int n = 0;
+    int ngrp = 0;                    // radius groups
+    int grp_r[STEREO_MAX_WIN_RADIUS];
+    int grp_n[STEREO_MAX_WIN_RADIUS];
+    PrepArgs* prep[STEREO_MAX_WIN_RADIUS];
+    FinArgs* fin[STEREO_MAX_WIN_RADIUS];
+    int* st_prep[STEREO_MAX_WIN_RADIUS];
+    int* st_fin[STEREO_MAX_WIN_RADIUS];
+    int tot_prep[STEREO_MAX_WIN_RADIUS];
+    int tot_fin[STEREO_MAX_WIN_RADIUS];
+    MapJob* map[3 * BST_MAX_ROUNDS];
+    RefJob* ref = nullptr;
+    int *st_mask = nullptr, *st_pix = nullptr, *st_disc = nullptr, *st_ref = nullptr;
+    int tot_mask = 0, tot_pix = 0, tot_disc = 0, tot_ref = 0;
+};
+
+// Bytes of the batched stage tables of up to n pairs (an upper bound).
+size_t batch_stage_bytes(int n) {
+    const size_t a = 256;
+    return STEREO_MAX_WIN_RADIUS * (2 * ((size_t)(n + 1) * 4 + a)) + (size_t)n * (sizeof(PrepArgs) + sizeof(FinArgs)) +
+           STEREO_MAX_WIN_RADIUS * 2 * a + 3 * BST_MAX_ROUNDS * ((size_t)n * sizeof(MapJob) + a) +
+           (size_t)n * sizeof(RefJob) + a + 4 * ((size_t)(n + 1) * 4 + a);
+}
+
 struct stereo_handle {
     stereo_params p;
     GraphCache single;   // stereo_match
@@ -204,15 +237,20 @@ struct stereo_handle {
     int32_t* dev_err;    // device error word
     // batched form: unit / pair tables (device) and the tuned configuration
     int4* units = nullptr;
-    CostArgs* pair_args = nullptr;
+    CostArgs* pair_args = nullptr;   // [2][max_batch]: the K = 4 units' arguments, then the K = 2 units'
     int* pair_radius = nullptr;
-    int* counter = nullptr;
+    int* counter = nullptr;          // [2]: the K = 4 and K = 2 persistent launches
     size_t max_units = 0;
     int batch_rows = 0;          // 0 = automatic
-    int batch_K = 0;             // 0 = automatic
+    int batch_K = 0;             // 0 = per pair (pick_k), else 2 or 4 for every pair
     std::vector<uint8_t> table_key;
-    int n_units = 0;
-    int tables_K = 4;
+    int n_units4 = 0, n_units2 = 0;   // units[0, n_units4) at K = 4, then n_units2 at K = 2
+    std::vector<int> pair_klayout;    // per pair: K of its staged-row layout
+    int batch_stages = 0;             // 0: per-pair stage launches on parallel streams, 1: batched launches
+    // batched stage launches (tables in btab)
+    uint8_t* btab = nullptr;
+    size_t btab_bytes = 0;
+    BatchStages bst;
     // parallel streams for the per-pair stages of a batch
     int n_aux = 0;
     cudaStream_t aux[BATCH_STREAMS] = {};
@@ -299,6 +337,16 @@ void set_smem_attributes() {
     cudaFuncSetAttribute(k_soft_dA, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_fill_disc_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)disc_local_smem(PT_MAX_HALO));
+    cudaFuncSetAttribute(k_fill_disc_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)disc_local_smem(PT_MAX_HALO));
+    cudaFuncSetAttribute(k_refine_eq12_batched<true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_refine_eq12_batched<false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_refine_eq12_batched<true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_refine_eq12_batched<false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_refine_eq34_batched<true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_refine_eq34_batched<false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_refine_eq34_batched<true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_refine_eq34_batched<false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_soft_box_t1<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)soft_box_smem(1));
     cudaFuncSetAttribute(k_soft_box_t1<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)soft_box_smem(2));
     cudaFuncSetAttribute(k_soft_box_t1<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)soft_box_smem(3));
@@ -357,14 +405,15 @@ template <bool CB>
 void launch_prep_cb(int r, const PrepIn& inL, const PrepIn& inR, int W, int H, const PrepOut& pl,
                     const PrepOut& pr, uint32_t* keys, void* cost, int cdt, int cs, cudaStream_t s) {
     dim3 g((W + PT - 1) / PT, (H + PT - 1) / PT, 2);
+    const PrepArgs pa{inL, inR, W, H, pl, pr, keys, cost, cdt, cs};
     switch (r) {
-        case 1: k_prep<CB, 1><<<g, 256, 0, s>>>(inL, inR, W, H, pl, pr, keys, cost, cdt, cs); break;
-        case 2: k_prep<CB, 2><<<g, 256, 0, s>>>(inL, inR, W, H, pl, pr, keys, cost, cdt, cs); break;
-        case 3: k_prep<CB, 3><<<g, 256, 0, s>>>(inL, inR, W, H, pl, pr, keys, cost, cdt, cs); break;
-        case 4: k_prep<CB, 4><<<g, 256, 0, s>>>(inL, inR, W, H, pl, pr, keys, cost, cdt, cs); break;
-        case 5: k_prep<CB, 5><<<g, 256, 0, s>>>(inL, inR, W, H, pl, pr, keys, cost, cdt, cs); break;
-        case 6: k_prep<CB, 6><<<g, 256, 0, s>>>(inL, inR, W, H, pl, pr, keys, cost, cdt, cs); break;
-        case 7: k_prep<CB, 7><<<g, 256, 0, s>>>(inL, inR, W, H, pl, pr, keys, cost, cdt, cs); break;
+        case 1: k_prep<CB, 1><<<g, 256, 0, s>>>(pa); break;
+        case 2: k_prep<CB, 2><<<g, 256, 0, s>>>(pa); break;
+        case 3: k_prep<CB, 3><<<g, 256, 0, s>>>(pa); break;
+        case 4: k_prep<CB, 4><<<g, 256, 0, s>>>(pa); break;
+        case 5: k_prep<CB, 5><<<g, 256, 0, s>>>(pa); break;
+        case 6: k_prep<CB, 6><<<g, 256, 0, s>>>(pa); break;
+        case 7: k_prep<CB, 7><<<g, 256, 0, s>>>(pa); break;
         default: return;
     }
     counted();
@@ -749,12 +798,15 @@ stereo_status stereo_create(const stereo_params* p, int32_t max_batch, stereo_ha
         // runs x ceil(H/8) bands x ceil(D/64) chunks per pair
         h->max_units = (size_t)max_batch * ((p->max_width + 15) / 16) * ((p->max_height + 7) / 8) *
                        ((p->num_disp + 63) / 64);
+        h->btab_bytes = batch_stage_bytes(max_batch);
         if (cudaMalloc(&h->units, h->max_units * sizeof(int4)) != cudaSuccess ||
-            cudaMalloc(&h->pair_args, (size_t)max_batch * sizeof(CostArgs)) != cudaSuccess ||
+            cudaMalloc(&h->pair_args, 2 * (size_t)max_batch * sizeof(CostArgs)) != cudaSuccess ||
             cudaMalloc(&h->pair_radius, (size_t)max_batch * sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&h->counter, sizeof(int)) != cudaSuccess) {
+            cudaMalloc(&h->counter, 2 * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&h->btab, h->btab_bytes) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(h->units); cudaFree(h->pair_args); cudaFree(h->pair_radius); cudaFree(h->counter);
+            cudaFree(h->btab);
             cudaFree(h->ws);
             cudaFree(h->dev_err);
             delete h;
@@ -794,6 +846,7 @@ stereo_status stereo_destroy(stereo_handle* h) {
     if (h->pair_args) cudaFree(h->pair_args);
     if (h->pair_radius) cudaFree(h->pair_radius);
     if (h->counter) cudaFree(h->counter);
+    if (h->btab) cudaFree(h->btab);
     for (int i = 0; i < BATCH_STREAMS; ++i) {
         if (h->aux[i]) cudaStreamDestroy(h->aux[i]);
         if (h->join_ev[i]) cudaEventDestroy(h->join_ev[i]);
@@ -948,52 +1001,77 @@ stereo_status stereo_set_tuning(const char* name, int32_t value) {
 // when set, else K = 4 unless every pair has at most 64 candidates, and a
 // height from the wave estimate of the largest pair.
 static void batch_config(const stereo_handle* h, const stereo_pair* pairs, int n, int& K, int& rows) {
-    int maxD = 0;
-    for (int i = 0; i < n; ++i) {
-        int d_min, D, r;
-        resolve_pair(h, &pairs[i], d_min, D, r);
-        maxD = std::max(maxD, D);
-    }
-    K = h->batch_K ? h->batch_K : (maxD <= 64 ? 2 : 4);
+    (void)pairs;
+    (void)n;
+    K = h->batch_K;                        // 0: per pair
     rows = h->batch_rows ? h->batch_rows : 16;
 }
 
-// Builds the unit table and the per-pair kernel arguments for a batch and
-// uploads them (stream-ordered on s; must not run inside a capture).
-static stereo_status build_batch_tables(stereo_handle* h, const stereo_pair* pairs, int n, int K, int rows,
+// Whether the post-processing and refinement of a batch run as batched
+// launches (the tile and mask kernels' limits); otherwise they run per pair.
+static bool batch_stages_apply(const stereo_params& p) {
+    if (p.outlier_rounds < 1 || p.outlier_rounds > BST_MAX_ROUNDS) return false;
+    for (int t = 0; t < p.outlier_rounds; ++t)
+        if (p.r0 + t * p.dr > 64) return false;
+    return p.fill_radial_r <= 63 && p.fill_disc_r <= PT_MAX_HALO && p.smooth_radius <= RB_MAX_RS &&
+           p.smooth_iters >= 1;
+}
+
+// Builds the unit tables, the per-pair kernel arguments and the batched
+// stage tables for a batch and uploads them (stream-ordered on s; must not
+// run inside a capture).  Kforce = 0: every pair runs the disparities-per-
+// lane split of the single-pair path (K = 4 chunks of 128 and, for D = 192,
+// a K = 2 chunk of 64 for the rest; K = 2 for D <= 64), so each pair's costs
+// and winners are those of its single-pair run; Kforce = 2 or 4: one K for
+// every pair.
+static stereo_status build_batch_tables(stereo_handle* h, const stereo_pair* pairs, int n, int Kforce, int rows,
                                         cudaStream_t s) {
-    std::vector<int4> units;
-    std::vector<CostArgs> args(n);
-    std::vector<int> radius(n);
+    std::vector<int4> units4, units2;
+    std::vector<CostArgs> args(2 * (size_t)h->max_batch);
+    std::vector<int> radius(n), klay(n);
     std::vector<int> order(n);
+    const int cdt = h->p.cost_dtype;
     for (int i = 0; i < n; ++i) order[i] = i;
     std::sort(order.begin(), order.end(), [&](int a, int b) {
         return (long)pairs[a].width * pairs[a].height > (long)pairs[b].width * pairs[b].height;
     });
+    struct Geo {
+        int d_min, D, r, W, H;
+        PairWs w;
+        PrepOut pl, pr;
+        const uint8_t *gl, *gr;
+        bool converted;
+    };
+    std::vector<Geo> G(n);
     for (int i = 0; i < n; ++i) {
         const stereo_pair* pr = &pairs[i];
-        int d_min, D, r;
-        resolve_pair(h, pr, d_min, D, r);
-        const int W = pr->width, H = pr->height;
-        PairWs w = carve(h->ws + (size_t)i * h->pair_bytes, (size_t)W * H, h->p.num_disp, h->p.cost_dtype,
-                         h->p.max_width, h->p.max_height);
-        PrepOut pl, prr;
-        prep_layouts(W, d_min, D, K, w, pl, prr, true);
-        void* cost = h->p.cost_dtype != CDT_NONE ? w.cost : nullptr;
-        args[i] = CostArgs{pl.img, pl.stride, pl.col0, prr.img, prr.stride, prr.col0, 1, w.lstats, w.ustats,
-                           prr.ustride, prr.ucol0, w.keys, w.keys + (size_t)W * H, cost, h->p.cost_dtype,
-                           W, H, d_min, D, rows, 0, D};
-        radius[i] = r;
+        Geo& g = G[i];
+        resolve_pair(h, pr, g.d_min, g.D, g.r);
+        g.W = pr->width;
+        g.H = pr->height;
+        g.w = carve(h->ws + (size_t)i * h->pair_bytes, (size_t)g.W * g.H, h->p.num_disp, cdt, h->p.max_width,
+                    h->p.max_height);
+        klay[i] = Kforce ? Kforce : cost_k(g.D, STEREO_SAMPLE_FULL);
+        prep_layouts(g.W, g.d_min, g.D, klay[i], g.w, g.pl, g.pr, true);
+        g.converted = pr->channels == 3 || pr->pitch != g.W;
+        g.gl = g.converted ? g.w.gl : pr->left;
+        g.gr = g.converted ? g.w.gr : pr->right;
+        void* cost = cdt != CDT_NONE ? g.w.cost : nullptr;
+        const CostArgs a{g.pl.img, g.pl.stride, g.pl.col0, g.pr.img, g.pr.stride, g.pr.col0, 1, g.w.lstats,
+                         g.w.ustats, g.pr.ustride, g.pr.ucol0, g.w.keys, g.w.keys + (size_t)g.W * g.H, cost, cdt,
+                         g.W, g.H, g.d_min, g.D, rows, 0, g.D};
+        args[i] = a;                           // K = 4 units
+        args[h->max_batch + i] = a;            // K = 2 units
+        radius[i] = g.r;
     }
-    for (int oi = 0; oi < n; ++oi) {
-        const int i = order[oi];
+    auto add_units = [&](std::vector<int4>& out, int i, int K, int dbase, int dcount) {
         const CostArgs& a = args[i];
         const int r = radius[i];
         const int TW = cost_run_width(r);
         const int inner_w = a.W - 2 * r, inner_h = a.H - 2 * r;
-        if (inner_w <= 0 || inner_h <= 0) continue;
+        if (inner_w <= 0 || inner_h <= 0 || dcount <= 0) return;
         const int nx = (inner_w + TW - 1) / TW, ny = (inner_h + rows - 1) / rows;
-        const int nz = (a.D + 32 * K - 1) / (32 * K);
+        const int nz = (dcount + 32 * K - 1) / (32 * K);
         for (int bz = 0; bz < nz; ++bz)
             for (int by = 0; by < ny; ++by)
                 for (int bx = 0; bx < nx; ++bx) {
@@ -1005,19 +1083,141 @@ static stereo_status build_batch_tables(stereo_handle* h, const stereo_pair* pai
                         else partial = 1;
                     }
                     if (inner_h >= rows) y0 = std::min(y0, a.H - r - rows);
-                    units.push_back(make_int4(i, x0, y0, bz | (partial << 16)));
+                    out.push_back(make_int4(i, x0, y0, bz | (partial << 16)));
                 }
+    };
+    for (int oi = 0; oi < n; ++oi) {
+        const int i = order[oi];
+        const int D = G[i].D;
+        if (Kforce) {
+            add_units(Kforce == 4 ? units4 : units2, i, Kforce, 0, D);
+        } else if (klay[i] == 2 && D > 128) {
+            // as run_match: 128-disparity chunks at K = 4, the rest at K = 2
+            const int d4 = D / 128 * 128;
+            args[i].dcount = d4;
+            args[h->max_batch + i].dbase = d4;
+            args[h->max_batch + i].dcount = D - d4;
+            add_units(units4, i, 4, 0, d4);
+            add_units(units2, i, 2, d4, D - d4);
+        } else {
+            add_units(klay[i] == 4 ? units4 : units2, i, klay[i], 0, D);
+        }
     }
-    if (units.size() > h->max_units) return STEREO_ERR_TOO_LARGE;
+    if (units4.size() + units2.size() > h->max_units) return STEREO_ERR_TOO_LARGE;
+    std::vector<int4> units(units4);
+    units.insert(units.end(), units2.begin(), units2.end());
     if (!units.empty() &&
         cudaMemcpyAsync(h->units, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return last_error();
-    if (cudaMemcpyAsync(h->pair_args, args.data(), n * sizeof(CostArgs), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+    if (cudaMemcpyAsync(h->pair_args, args.data(), args.size() * sizeof(CostArgs), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
         cudaMemcpyAsync(h->pair_radius, radius.data(), n * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return last_error();
+
+    // ---- batched stage tables (host image of btab, then one upload)
+    BatchStages& B = h->bst;
+    B = BatchStages();
+    B.n = n;
+    std::vector<uint8_t> host(h->btab_bytes, 0);
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> size_t {
+        const size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    auto dev = [&](size_t o) { return h->btab + o; };
+    auto starts = [&](const std::vector<int>& ids, auto blocks_of, int*& dptr, int& total) {
+        const size_t o = take((ids.size() + 1) * sizeof(int));
+        int* hp = reinterpret_cast<int*>(host.data() + o);
+        int acc = 0;
+        for (size_t k = 0; k < ids.size(); ++k) {
+            hp[k] = acc;
+            acc += blocks_of(ids[k]);
+        }
+        hp[ids.size()] = acc;
+        dptr = reinterpret_cast<int*>(dev(o));
+        total = acc;
+    };
+    // radius groups (largest pairs first inside each)
+    for (int r = 1; r <= STEREO_MAX_WIN_RADIUS; ++r) {
+        std::vector<int> ids;
+        for (int oi = 0; oi < n; ++oi)
+            if (G[order[oi]].r == r) ids.push_back(order[oi]);
+        if (ids.empty()) continue;
+        const int g = B.ngrp++;
+        B.grp_r[g] = r;
+        B.grp_n[g] = (int)ids.size();
+        const size_t op = take(ids.size() * sizeof(PrepArgs)), of = take(ids.size() * sizeof(FinArgs));
+        for (size_t k = 0; k < ids.size(); ++k) {
+            const int i = ids[k];
+            const stereo_pair* pr = &pairs[i];
+            const Geo& q = G[i];
+            const PrepIn inL{pr->left, pr->pitch, pr->channels == 3, q.converted ? q.w.gl : nullptr};
+            const PrepIn inR{pr->right, pr->pitch, pr->channels == 3, q.converted ? q.w.gr : nullptr};
+            void* cost = cdt != CDT_NONE ? q.w.cost : nullptr;
+            reinterpret_cast<PrepArgs*>(host.data() + op)[k] =
+                PrepArgs{inL, inR, q.W, q.H, q.pl, q.pr, q.w.keys, cost, cdt, cost_stride(q.D)};
+            reinterpret_cast<FinArgs*>(host.data() + of)[k] = FinArgs{
+                q.w.keys, q.w.keys + (size_t)q.W * q.H, q.W, q.H, q.d_min, q.D, h->p.lr_thresh, cost, cdt, q.gl,
+                q.gr, q.r, STEREO_SAMPLE_FULL,
+                FinStats{q.w.lstats, q.w.ustats, q.pr.ustride, q.pr.ucol0, reinterpret_cast<const int8_t*>(q.pl.img),
+                         q.pl.stride, q.pl.col0, reinterpret_cast<const int8_t*>(q.pr.img), q.pr.stride,
+                         q.pr.col0},
+                pr->disp_wta ? pr->disp_wta : q.w.wta, nullptr, pr->disp_sub, q.w.lr};
+        }
+        B.prep[g] = reinterpret_cast<PrepArgs*>(dev(op));
+        B.fin[g] = reinterpret_cast<FinArgs*>(dev(of));
+        starts(ids, [&](int i) { return bgrid_prep_x(G[i].W) * bgrid_prep_y(G[i].H) * 2; }, B.st_prep[g],
+               B.tot_prep[g]);
+        starts(ids, [&](int i) { return bgrid_fin_x(G[i].W) * G[i].H; }, B.st_fin[g], B.tot_fin[g]);
+    }
+    B.ok = batch_stages_apply(h->p);
+    if (B.ok) {
+        std::vector<int> ids(order);
+        const int rounds = h->p.outlier_rounds;
+        for (int t = 0; t < rounds; ++t)
+            for (int k = 0; k < 3; ++k) {
+                const size_t o = take((size_t)n * sizeof(MapJob));
+                B.map[3 * t + k] = reinterpret_cast<MapJob*>(dev(o));
+                for (size_t j = 0; j < ids.size(); ++j) {
+                    const int i = ids[j];
+                    const stereo_pair* pr = &pairs[i];
+                    const Geo& q = G[i];
+                    int16_t* post_out = pr->disp_post ? pr->disp_post : q.w.post;
+                    const int16_t* cur = t == 0 ? q.w.lr : q.w.t;
+                    int16_t* dst = t == rounds - 1 ? post_out : q.w.t;
+                    const LineMasks m = make_line_masks(q.w.masks, q.W, q.H);
+                    MapJob mj{};
+                    if (k == 0) mj = MapJob{cur, q.w.p, m};
+                    else if (k == 1) mj = MapJob{q.w.p, q.w.q, m};
+                    else mj = MapJob{q.w.q, dst, m};
+                    reinterpret_cast<MapJob*>(host.data() + o)[j] = mj;
+                }
+            }
+        const size_t orf = take((size_t)n * sizeof(RefJob));
+        for (size_t j = 0; j < ids.size(); ++j) {
+            const int i = ids[j];
+            const stereo_pair* pr = &pairs[i];
+            const Geo& q = G[i];
+            const RefineArgs a{q.W, q.H, h->p.smooth_radius, q.d_min, q.D, h->p.alpha, h->p.eta, h->p.refine_search,
+                               cdt != CDT_NONE ? q.w.cost : nullptr, cdt, q.gl, q.gr, q.r, STEREO_SAMPLE_FULL,
+                               q.w.op, q.w.dprev, q.w.dt, q.w.b, q.w.cnt};
+            reinterpret_cast<RefJob*>(host.data() + orf)[j] =
+                RefJob{a, pr->disp_post ? pr->disp_post : q.w.post, pr->valid,
+                       pr->disp_final ? pr->disp_final : q.w.dfin, nullptr};
+        }
+        B.ref = reinterpret_cast<RefJob*>(dev(orf));
+        starts(ids, [&](int i) { return bgrid_mask_x(G[i].W) * bgrid_mask_y(G[i].H); }, B.st_mask, B.tot_mask);
+        starts(ids, [&](int i) { return (G[i].W * G[i].H + 255) / 256; }, B.st_pix, B.tot_pix);
+        starts(ids, [&](int i) { return bgrid_disc_x(G[i].W) * bgrid_disc_y(G[i].H); }, B.st_disc, B.tot_disc);
+        starts(ids, [&](int i) { return bgrid_ref_x(G[i].W) * bgrid_ref_y(G[i].H); }, B.st_ref, B.tot_ref);
+    }
+    if (off > h->btab_bytes) return STEREO_ERR_TOO_LARGE;
+    if (cudaMemcpyAsync(h->btab, host.data(), off, cudaMemcpyHostToDevice, s) != cudaSuccess) return last_error();
     cudaStreamSynchronize(s);           // host vectors go out of scope
-    h->n_units = (int)units.size();
-    h->tables_K = K;
+    h->n_units4 = (int)units4.size();
+    h->n_units2 = (int)units2.size();
+    h->pair_klayout = klay;
     return STEREO_OK;
 }
 
@@ -1057,16 +1257,89 @@ static void fan_out(stereo_handle* h, const stereo_pair* pairs, int n, cudaStrea
 
 extern "C" {
 
-// Whole path for a batch: per pair input conversion, statistics and border
-// costs; one persistent launch of the cost kernel over all pairs' units; then
-// per pair finalize, post-processing and refinement.  The per-pair work runs
-// on parallel streams; with stage timing on, every stage of every pair ends
-// before the next stage starts, and the handle's events bracket the stages.
+// Whole path for a batch.  With the batched stage tables (the usual case):
+// one launch per stage over all pairs -- preparation and finalize once per
+// window radius present, the persistent cost launches (K = 4 units, then
+// K = 2 units), the post-processing rounds and the refinement iterations.
+// Otherwise the per-pair stages run on parallel streams.  With stage timing
+// on, the handle's events bracket the stages.
+static void launch_prep_batched(const BatchStages& B, cudaStream_t s) {
+    for (int g = 0; g < B.ngrp; ++g) {
+        const dim3 grid((unsigned)B.tot_prep[g]);
+        if (!B.tot_prep[g]) continue;
+        switch (B.grp_r[g]) {
+            case 1: k_prep_batched<1><<<grid, 256, 0, s>>>(B.prep[g], B.st_prep[g], B.grp_n[g]); break;
+            case 2: k_prep_batched<2><<<grid, 256, 0, s>>>(B.prep[g], B.st_prep[g], B.grp_n[g]); break;
+            case 3: k_prep_batched<3><<<grid, 256, 0, s>>>(B.prep[g], B.st_prep[g], B.grp_n[g]); break;
+            case 4: k_prep_batched<4><<<grid, 256, 0, s>>>(B.prep[g], B.st_prep[g], B.grp_n[g]); break;
+            case 5: k_prep_batched<5><<<grid, 256, 0, s>>>(B.prep[g], B.st_prep[g], B.grp_n[g]); break;
+            case 6: k_prep_batched<6><<<grid, 256, 0, s>>>(B.prep[g], B.st_prep[g], B.grp_n[g]); break;
+            default: k_prep_batched<7><<<grid, 256, 0, s>>>(B.prep[g], B.st_prep[g], B.grp_n[g]); break;
+        }
+        counted();
+    }
+}
+
+static void launch_finalize_batched(const BatchStages& B, cudaStream_t s) {
+    for (int g = 0; g < B.ngrp; ++g) {
+        const dim3 grid((unsigned)B.tot_fin[g]);
+        if (!B.tot_fin[g]) continue;
+        switch (B.grp_r[g]) {
+            case 1: k_finalize_batched<1><<<grid, 128, 0, s>>>(B.fin[g], B.st_fin[g], B.grp_n[g]); break;
+            case 2: k_finalize_batched<2><<<grid, 128, 0, s>>>(B.fin[g], B.st_fin[g], B.grp_n[g]); break;
+            case 3: k_finalize_batched<3><<<grid, 128, 0, s>>>(B.fin[g], B.st_fin[g], B.grp_n[g]); break;
+            case 4: k_finalize_batched<4><<<grid, 128, 0, s>>>(B.fin[g], B.st_fin[g], B.grp_n[g]); break;
+            case 5: k_finalize_batched<5><<<grid, 128, 0, s>>>(B.fin[g], B.st_fin[g], B.grp_n[g]); break;
+            case 6: k_finalize_batched<6><<<grid, 128, 0, s>>>(B.fin[g], B.st_fin[g], B.grp_n[g]); break;
+            default: k_finalize_batched<7><<<grid, 128, 0, s>>>(B.fin[g], B.st_fin[g], B.grp_n[g]); break;
+        }
+        counted();
+    }
+}
+
+static void launch_post_batched(const stereo_params& p, const BatchStages& B, cudaStream_t s) {
+    const int n = B.n;
+    k_zero_masks_batched<<<dim3(32, n), 256, 0, s>>>(B.map[0], n);
+    counted();
+    const int min_count = p.fill_disc_min_count >= 0 ? p.fill_disc_min_count : (disc_area(p.fill_disc_r) + 3) / 4;
+    // integer disparities: |d| < thresh <=> |d| <= ceil(thresh) - 1
+    const int ithr = (int)std::min(ceilf(p.outlier_thresh), 65536.f) - 1;
+    for (int t = 0; t < p.outlier_rounds; ++t) {
+        const int rad = p.r0 + t * p.dr;
+        k_line_masks_batched<<<B.tot_mask, 256, 0, s>>>(B.map[3 * t], B.st_mask, n, 1, ithr);
+        if (rad <= 32) k_outlier_masks32_batched<<<B.tot_pix, 256, 0, s>>>(B.map[3 * t], B.st_pix, n, rad);
+        else k_outlier_masks_batched<<<B.tot_pix, 256, 0, s>>>(B.map[3 * t], B.st_pix, n, rad);
+        k_line_masks_batched<<<B.tot_mask, 256, 0, s>>>(B.map[3 * t + 1], B.st_mask, n, 0, 0);
+        k_fill_radial_masks_batched<<<B.tot_pix, 256, 0, s>>>(B.map[3 * t + 1], B.st_pix, n, p.fill_radial_r,
+                                                              p.fill_radial_min_dirs);
+        k_fill_disc_batched<<<B.tot_disc, DL_THREADS, disc_local_smem(p.fill_disc_r), s>>>(
+            B.map[3 * t + 2], B.st_disc, n, p.fill_disc_r, min_count);
+        counted(5);
+    }
+}
+
+}  // extern "C"
+
+template <int SPAD>
+static void launch_refine_batched_spad(const stereo_params& p, const BatchStages& B, cudaStream_t s) {
+    const size_t sm = refine_tile_smem(p.smooth_radius);
+    for (int k = 0; k < p.smooth_iters; ++k) {
+        const bool last = k == p.smooth_iters - 1;
+        if (k == 0) k_refine_eq12_batched<true, SPAD><<<B.tot_ref, RB_THREADS, sm, s>>>(B.ref, B.st_ref, B.n);
+        else k_refine_eq12_batched<false, SPAD><<<B.tot_ref, RB_THREADS, sm, s>>>(B.ref, B.st_ref, B.n);
+        if (!last) k_refine_eq34_batched<true, SPAD><<<B.tot_ref, RB_THREADS, sm, s>>>(B.ref, B.st_ref, B.n, 0);
+        else k_refine_eq34_batched<false, SPAD><<<B.tot_ref, RB_THREADS, sm, s>>>(B.ref, B.st_ref, B.n, 1);
+        counted(2);
+    }
+}
+
+extern "C" {
+
 static void enqueue_batched(stereo_handle* h, const stereo_pair* pairs, int n, cudaStream_t s,
                             bool cost_only = false) {
-    const int K = h->tables_K;
     const int cdt = h->p.cost_dtype;
     const bool timed = h->timing && h->ev_ready && !cost_only;
+    const BatchStages& B = h->bst;
     struct Pair {
         int d_min, D, r, W, H;
         PairWs w;
@@ -1087,36 +1360,10 @@ static void enqueue_batched(stereo_handle* h, const stereo_pair* pairs, int n, c
         q.gl = q.converted ? q.w.gl : pr->left;
         q.gr = q.converted ? q.w.gr : pr->right;
     }
-    // gray conversion (RGB or pitched input), statistics, key clearing and
-    // the NaN border slices: one preparation launch per pair
-    auto input = [&](int, cudaStream_t) {};
-    auto stats = [&](int i, cudaStream_t st) {
+    auto finalize_extra = [&](int i, cudaStream_t st) {     // LR map copy for callers that ask for it
         const stereo_pair* pr = &pairs[i];
-        const Pair& q = P[i];
-        PairWs w = q.w;
-        PrepOut pl, prr;
-        prep_layouts(q.W, q.d_min, q.D, K, w, pl, prr, true);
-        const PrepIn inL{pr->left, pr->pitch, pr->channels == 3, q.converted ? q.w.gl : nullptr};
-        const PrepIn inR{pr->right, pr->pitch, pr->channels == 3, q.converted ? q.w.gr : nullptr};
-        launch_prep(q.r, STEREO_SAMPLE_FULL, inL, inR, q.W, q.H, pl, prr, w.keys,
-                    cdt != CDT_NONE ? w.cost : nullptr, cdt, q.D, st);
-    };
-    auto finalize = [&](int i, cudaStream_t st) {
-        const stereo_pair* pr = &pairs[i];
-        const Pair& q = P[i];
-        void* cost = cdt != CDT_NONE ? q.w.cost : nullptr;
-        int16_t* wta = pr->disp_wta ? pr->disp_wta : q.w.wta;
-        PrepOut pl, prr;
-        prep_layouts(q.W, q.d_min, q.D, K, q.w, pl, prr, true);
-        launch_finalize(q.w.keys, q.w.keys + (size_t)q.W * q.H, q.W, q.H, q.d_min, q.D, h->p.lr_thresh, cost,
-                        cdt, q.gl, q.gr, q.r, h->p.sampling,
-                        FinStats{q.w.lstats, q.w.ustats, prr.ustride, prr.ucol0,
-                                 reinterpret_cast<const int8_t*>(pl.img), pl.stride, pl.col0,
-                                 reinterpret_cast<const int8_t*>(prr.img), prr.stride, prr.col0},
-                        wta, nullptr, pr->disp_sub, q.w.lr, st);
-        counted();
         if (pr->disp_lr)
-            cudaMemcpyAsync(pr->disp_lr, q.w.lr, (size_t)q.W * q.H * 2, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(pr->disp_lr, P[i].w.lr, (size_t)P[i].W * P[i].H * 2, cudaMemcpyDeviceToDevice, st);
     };
     auto post = [&](int i, cudaStream_t st) {
         const stereo_pair* pr = &pairs[i];
@@ -1131,24 +1378,65 @@ static void enqueue_batched(stereo_handle* h, const stereo_pair* pairs, int n, c
                    q.D, q.r, h->p.sampling, q.w, pr->disp_final ? pr->disp_final : q.w.dfin, nullptr, pr->valid,
                    st);
     };
+    const bool batched_stages = h->batch_stages == 1 && B.ok;
+    // per-pair preparation: gray conversion (RGB or pitched input),
+    // statistics, key clearing and the NaN border slices in one launch
+    auto stats = [&](int i, cudaStream_t st) {
+        const stereo_pair* pr = &pairs[i];
+        const Pair& q = P[i];
+        PrepOut pl, prr;
+        prep_layouts(q.W, q.d_min, q.D, h->pair_klayout[i], q.w, pl, prr, true);
+        const PrepIn inL{pr->left, pr->pitch, pr->channels == 3, q.converted ? q.w.gl : nullptr};
+        const PrepIn inR{pr->right, pr->pitch, pr->channels == 3, q.converted ? q.w.gr : nullptr};
+        launch_prep(q.r, STEREO_SAMPLE_FULL, inL, inR, q.W, q.H, pl, prr, q.w.keys,
+                    cdt != CDT_NONE ? q.w.cost : nullptr, cdt, q.D, st);
+    };
+    auto finalize = [&](int i, cudaStream_t st) {
+        const stereo_pair* pr = &pairs[i];
+        const Pair& q = P[i];
+        void* cost = cdt != CDT_NONE ? q.w.cost : nullptr;
+        int16_t* wta = pr->disp_wta ? pr->disp_wta : q.w.wta;
+        PrepOut pl, prr;
+        prep_layouts(q.W, q.d_min, q.D, h->pair_klayout[i], q.w, pl, prr, true);
+        launch_finalize(q.w.keys, q.w.keys + (size_t)q.W * q.H, q.W, q.H, q.d_min, q.D, h->p.lr_thresh, cost,
+                        cdt, q.gl, q.gr, q.r, STEREO_SAMPLE_FULL,
+                        FinStats{q.w.lstats, q.w.ustats, prr.ustride, prr.ucol0,
+                                 reinterpret_cast<const int8_t*>(pl.img), pl.stride, pl.col0,
+                                 reinterpret_cast<const int8_t*>(prr.img), prr.stride, prr.col0},
+                        wta, nullptr, pr->disp_sub, q.w.lr, st);
+        counted();
+        finalize_extra(i, st);
+    };
     if (!cost_only) {
-        if (timed) {
-            mark(h, 0, s);
-            fan_out(h, pairs, n, s, input);
-            mark(h, 1, s);
-            fan_out(h, pairs, n, s, stats);
-            mark(h, 2, s);
-        } else {
-            fan_out(h, pairs, n, s, [&](int i, cudaStream_t st) { input(i, st); stats(i, st); });
-        }
+        if (timed) { mark(h, 0, s); mark(h, 1, s); }
+        if (batched_stages) launch_prep_batched(B, s);
+        else fan_out(h, pairs, n, s, stats);
+        if (timed) mark(h, 2, s);
     }
-    cudaMemsetAsync(h->counter, 0, sizeof(int), s);
-    if (K == 4) launch_cost_batched_k4(cdt, h->pair_args, h->pair_radius, h->units, h->n_units, h->counter, s);
-    else launch_cost_batched_k2(cdt, h->pair_args, h->pair_radius, h->units, h->n_units, h->counter, s);
-    counted();
+    cudaMemsetAsync(h->counter, 0, 2 * sizeof(int), s);
+    if (h->n_units4) {
+        launch_cost_batched_k4(cdt, h->pair_args, h->pair_radius, h->units, h->n_units4, h->counter, s);
+        counted();
+    }
+    if (h->n_units2) {
+        launch_cost_batched_k2(cdt, h->pair_args + h->max_batch, h->pair_radius, h->units + h->n_units4,
+                               h->n_units2, h->counter + 1, s);
+        counted();
+    }
     if (cost_only) return;
+    if (timed) mark(h, 3, s);
+    if (batched_stages) {
+        launch_finalize_batched(B, s);
+        for (int i = 0; i < n; ++i) finalize_extra(i, s);
+        if (timed) mark(h, 4, s);
+        launch_post_batched(h->p, B, s);
+        if (timed) mark(h, 5, s);
+        if (rb_spad(h->p.smooth_radius) == 16) launch_refine_batched_spad<16>(h->p, B, s);
+        else launch_refine_batched_spad<32>(h->p, B, s);
+        if (timed) mark(h, 6, s);
+        return;
+    }
     if (timed) {
-        mark(h, 3, s);
         fan_out(h, pairs, n, s, finalize);
         mark(h, 4, s);
         fan_out(h, pairs, n, s, post);
@@ -1526,6 +1814,21 @@ stereo_status stereo_set_batch_config(stereo_handle* h, int32_t rows, int32_t K)
     return STEREO_OK;
 }
 
+stereo_status stereo_set_batch_stages(stereo_handle* h, int32_t mode) {
+    if (!h || (mode != 0 && mode != 1)) return STEREO_ERR_INVALID_ARG;
+    if (mode != h->batch_stages) h->batch.clear();     // captured sequences follow the old mode
+    h->batch_stages = mode;
+    return STEREO_OK;
+}
+
+stereo_status stereo_get_batch_config(const stereo_handle* h, int32_t* rows, int32_t* K, int32_t* stages) {
+    if (!h) return STEREO_ERR_INVALID_ARG;
+    if (rows) *rows = h->batch_rows;
+    if (K) *K = h->batch_K;
+    if (stages) *stages = h->batch_stages;
+    return STEREO_OK;
+}
+
 stereo_status stereo_autotune_batched(stereo_handle* h, const stereo_pair* pairs, int32_t n, void* stream,
                                       int32_t* best_rows, int32_t* best_K, float* best_ms) {
     if (!h || !pairs || n < 2 || n > h->max_batch || !h->units) return STEREO_ERR_INVALID_ARG;
@@ -1543,9 +1846,9 @@ stereo_status stereo_autotune_batched(stereo_handle* h, const stereo_pair* pairs
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int rows_c[] = {8, 12, 16, 24, 32, 48};
-    const int K_c[] = {2, 4};
+    const int K_c[] = {0, 2, 4};            // 0: each pair's own split (pick_k)
     float best = 1e30f;
-    int br = 16, bk = 4;
+    int br = 16, bk = 0;
     for (int K : K_c) {
         for (int rows : rows_c) {
             stereo_status st = build_batch_tables(h, pairs, n, K, rows, s);
@@ -1563,10 +1866,38 @@ stereo_status stereo_autotune_batched(stereo_handle* h, const stereo_pair* pairs
             if (sum / 3 < best) { best = sum / 3; br = rows; bk = K; }
         }
     }
+    // the per-pair stages: per-pair launches on parallel streams against one
+    // launch per stage over all pairs, whole passes timed with the chosen units
+    int bstages = 0;
+    {
+        stereo_status st = build_batch_tables(h, pairs, n, bk, br, s);
+        if (st != STEREO_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+        float tm[2] = {1e30f, 1e30f};
+        const int saved = h->batch_stages;
+        for (int mode = 0; mode < 2; ++mode) {
+            if (mode == 1 && !h->bst.ok) break;
+            h->batch_stages = mode;
+            enqueue_batched(h, pairs, n, s);               // warm
+            float ms = 0.f, sum = 0.f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, s);
+                enqueue_batched(h, pairs, n, s);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);
+                sum += ms;
+            }
+            tm[mode] = sum / 3;
+        }
+        h->batch_stages = saved;
+        bstages = tm[1] < tm[0] ? 1 : 0;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->batch_rows = br;
     h->batch_K = bk;
+    if (bstages != h->batch_stages) h->batch.clear();
+    h->batch_stages = bstages;
     h->table_key.clear();                                  // rebuild with the choice on next use
     if (best_rows) *best_rows = br;
     if (best_K) *best_K = bk;

@@ -13,7 +13,9 @@ pytestmark = pytest.mark.gpu
 
 import paper_2007_12623_b300 as st  # noqa: E402
 
-SHAPES = [(120, 200, 0, 64, 4), (90, 160, 0, 32, 5), (150, 260, 2, 96, 7), (70, 110, -3, 24, 3)]
+# (H, W, d_min, D, r): D = 160 runs 128 disparities at K = 4 and 32 at K = 2
+SHAPES = [(120, 200, 0, 64, 4), (90, 160, 0, 32, 5), (150, 260, 2, 96, 7), (70, 110, -3, 24, 3),
+          (64, 300, 0, 160, 5)]
 
 
 @pytest.fixture(scope="module")
@@ -39,18 +41,26 @@ def _outs(dev, H, W):
                 disp_final=torch.empty((H, W), dtype=torch.float32, device=dev))
 
 
-@pytest.mark.parametrize("cdt", [st.COST_F16, st.COST_F32])
-def test_batched_equals_single_pair_path(dev, cdt):
+@pytest.mark.parametrize("cdt,stages,smooth", [(st.COST_F16, 0, 15), (st.COST_F32, 0, 15), (st.COST_F16, 1, 15),
+                                                (st.COST_F32, 1, 15), (st.COST_F16, 1, 40)])
+def test_batched_equals_single_pair_path(dev, cdt, stages, smooth):
+    """Every output of every pair equals the single-pair path's, for the
+    per-pair K split and both forced K, in both stage modes (one launch per
+    stage over all pairs, or per-pair launches on parallel streams; a
+    smoothing radius beyond the tile kernels' limit falls back to per-pair
+    launches)."""
     pairs = _pairs(dev)
     maxH = max(s[0] for s in SHAPES)
     maxW = max(s[1] for s in SHAPES)
-    p = st.stereo_default_params(max_width=maxW, max_height=maxH, num_disp=96, cost_dtype=cdt,
-                                 smooth_radius=15)
+    p = st.stereo_default_params(max_width=maxW, max_height=maxH, num_disp=160, cost_dtype=cdt,
+                                 smooth_radius=smooth)
     hb = st.stereo_create(p, max_batch=len(pairs))
     hs = st.stereo_create(p)
+    st.stereo_set_batch_stages(hb, stages)
     s = torch.cuda.Stream()
     for rows, K in ((0, 0), (8, 2), (24, 4)):
         st.stereo_set_batch_config(hb, rows, K)
+        assert st.stereo_get_batch_config(hb) == dict(rows=rows, K=K, stages=stages)
         batch = []
         for d in pairs:
             H, W = d["left"].shape[:2]
@@ -75,7 +85,7 @@ def test_batched_matches_oracle_wta(dev):
     """Each pair's winner-take-all map from the batched launch against the
     oracle (near-ties exempt)."""
     pairs = _pairs(dev)
-    p = st.stereo_default_params(max_width=260, max_height=150, num_disp=96, cost_dtype=st.COST_F16)
+    p = st.stereo_default_params(max_width=300, max_height=150, num_disp=160, cost_dtype=st.COST_F16)
     hb = st.stereo_create(p, max_batch=len(pairs))
     batch = []
     for d in pairs:
@@ -94,7 +104,7 @@ def test_batched_matches_oracle_wta(dev):
 
 def test_autotuner_picks_a_configuration(dev):
     pairs = _pairs(dev)
-    p = st.stereo_default_params(max_width=260, max_height=150, num_disp=96, cost_dtype=st.COST_F16)
+    p = st.stereo_default_params(max_width=300, max_height=150, num_disp=160, cost_dtype=st.COST_F16)
     hb = st.stereo_create(p, max_batch=len(pairs))
     batch = []
     for d in pairs:
@@ -102,7 +112,8 @@ def test_autotuner_picks_a_configuration(dev):
         batch.append(dict(d, **_outs(dev, H, W)))
     s = torch.cuda.Stream()
     res = st.stereo_autotune_batched(hb, batch, stream=s)
-    assert res["K"] in (2, 4) and res["rows"] in (8, 12, 16, 24, 32, 48) and res["ms"] > 0
+    assert res["K"] in (0, 2, 4) and res["rows"] in (8, 12, 16, 24, 32, 48) and res["ms"] > 0
+    assert res["stages"] in (0, 1)
     with torch.cuda.stream(s):
         st.stereo_match_batched(hb, batch, stream=s)
     s.synchronize()

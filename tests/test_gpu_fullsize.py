@@ -242,6 +242,17 @@ def test_batched_size_classes_full_size(dev):
         with torch.cuda.stream(s):
             st.stereo_match_batched(hb, batch, use_graph=True, stream=s)
         s.synchronize()
+    # the other stage mode (one launch per stage over all pairs) gives the same maps
+    st.stereo_set_batch_stages(hb, 1)
+    keys = ("disp_wta", "disp_sub", "disp_post", "disp_final")
+    other = [dict(b, **{k: torch.empty_like(b[k]) for k in keys}) for b in batch]
+    for _ in range(2):
+        with torch.cuda.stream(s):
+            st.stereo_match_batched(hb, other, use_graph=True, stream=s)
+        s.synchronize()
+    for b, o in zip(batch, other):
+        for k in keys:
+            assert torch.equal(b[k].nan_to_num(-7), o[k].nan_to_num(-7)), k
     hb.close()
     for (L, R, gt, sp), b in zip(specs, batch):
         H, W, D, r = sp["H"], sp["W"], sp["D"], sp["r"]
