@@ -325,6 +325,10 @@ __device__ __forceinline__ void line_mask_words(const int16_t (*t)[LM_COLS], con
     const int X0 = 32 * bc;
     const uint32_t L = (uint32_t)m.lines(F);
     uint32_t* wf = m.words + (uint32_t)m.off[F];
+    // lane `it` keeps word `it`; the 16 words (consecutive lines, one word
+    // index) go out as one coalesced store at the end
+    uint32_t mine = 0u, dst = 0u;
+    bool have = false;
 #pragma unroll 4
     for (int it = 0; it < 16; ++it) {
         const int i = (warp & 1) * 16 + it;
@@ -356,8 +360,13 @@ __device__ __forceinline__ void line_mask_words(const int16_t (*t)[LM_COLS], con
             bit = bit && q != ST_INVALID && dlt <= ithr && -dlt <= ithr;
         }
         const uint32_t word = __ballot_sync(0xffffffffu, bit);
-        if (lane == 0) wf[(uint32_t)(wi + LM_PAD_LO) * L + (uint32_t)line] = word;
+        if (lane == it) {
+            mine = word;
+            dst = (uint32_t)(wi + LM_PAD_LO) * L + (uint32_t)line;
+            have = true;
+        }
     }
+    if (have) wf[dst] = mine;
 }
 
 // Block (vb.x, vb.y) of the grid ((W + 31) / 32, (H + 31) / 32 + 1).
