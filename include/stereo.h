@@ -34,9 +34,15 @@
  *  - Errors are returned as stereo_status; arguments are checked on the host
  *    before anything is enqueued, so a call that fails with
  *    STEREO_ERR_INVALID_ARG or STEREO_ERR_UNSUPPORTED has enqueued nothing.
- *    No C++ exception crosses this boundary.  Device-side problems (a bounded
- *    wait that gave up, a failed in-kernel bounds check in debug builds) set
- *    an error word in the handle, read with stereo_get_device_error().
+ *    No C++ exception crosses this boundary.  No kernel of this library waits
+ *    on another, so no call returns STEREO_ERR_TIMEOUT (kept for callers'
+ *    code).  The checked build of the library (libstereo_checked.so,
+ *    compiled with -DSTEREO_CHECKED, for testing) checks the index ranges of
+ *    its staged-row copies, cost stores, mask-word reads and writes,
+ *    candidate loads and preparation writes inside the kernels; a failed
+ *    check records ST_DEVERR_BOUNDS (0x1000) | site in a device error word
+ *    and skips the access (nothing traps), read and cleared with
+ *    stereo_get_device_error().
  *  - A handle is not thread-safe: one host thread at a time per handle.
  */
 #ifndef STEREO_H
@@ -59,7 +65,7 @@ typedef enum {
     STEREO_ERR_CUDA = 2,          /* a CUDA runtime call failed             */
     STEREO_ERR_OOM = 3,           /* workspace allocation failed            */
     STEREO_ERR_UNSUPPORTED = 4,   /* valid request this build cannot serve  */
-    STEREO_ERR_TIMEOUT = 5,       /* a bounded device wait gave up          */
+    STEREO_ERR_TIMEOUT = 5,       /* a bounded device wait gave up (unused) */
     STEREO_ERR_TOO_LARGE = 6      /* request exceeds the handle's capacity  */
 } stereo_status;
 
@@ -198,8 +204,29 @@ stereo_status stereo_autotune_batched(stereo_handle* h, const stereo_pair* pairs
                                       int32_t* best_rows, int32_t* best_K, float* best_ms);
 
 /* Reads (and clears) the handle's device error word; synchronises `stream`
- * first.  *err = 0 when no device-side error was recorded. */
+ * first.  *err = 0 when no device-side error was recorded.  In the checked
+ * build it also reads and clears the words of the in-kernel index checks
+ * (process-wide, one per translation unit of the library): the first failed
+ * check's 0x1000 | site. */
 stereo_status stereo_get_device_error(stereo_handle* h, int32_t* err, void* stream);
+
+/* 1 in the checked build (in-kernel index checks), 0 otherwise. */
+int32_t stereo_build_checked(void);
+
+/* Checked build only: launches one check that cannot pass (an index one past
+ * the end of a one-element buffer); its store is skipped and the error word
+ * records 0x1000 | 0xfff.  STEREO_ERR_UNSUPPORTED in the normal build. */
+stereo_status stereo_debug_check_selftest(void* stream);
+
+/* Test hooks for allocation failures: after stereo_debug_fail_alloc(n) the
+ * device allocation n + 1 calls later (counting every cudaMalloc that
+ * stereo_create makes) fails as if the device had no memory left, without
+ * calling cudaMalloc; n = -1 disarms.  stereo_create then returns
+ * STEREO_ERR_OOM with everything it had allocated freed.
+ * stereo_debug_live_allocations() counts the device allocations the
+ * library's handles hold. */
+stereo_status stereo_debug_fail_alloc(int32_t n);
+int64_t stereo_debug_live_allocations(void);
 
 const char* stereo_status_str(stereo_status s);
 

@@ -21,7 +21,8 @@ __all__ = [
     "stereo_get_stage_times", "stereo_launch_count", "STAGE_NAMES", "stereo_set_tuning",
     "stereo_match_wta_noalloc", "stereo_softargmin_fwd", "stereo_softargmin_bwd", "stereo_l1_loss",
     "SoftArgminZNCC", "soft_argmin", "stereo_set_batch_config", "stereo_autotune_batched",
-    "stereo_set_batch_stages", "stereo_get_batch_config",
+    "stereo_set_batch_stages", "stereo_get_batch_config", "checked_library", "stereo_debug_fail_alloc",
+    "stereo_debug_live_allocations",
     "StereoCamera", "stereo_depth_points", "PointModel", "stereo_mosaic_frame", "stereo_vote_nbins",
     "stereo_vote_matches",
 ]
@@ -79,21 +80,44 @@ class _PointModelC(C.Structure):
                 ("count", C.c_void_p), ("dropped", C.c_void_p), ("capacity", C.c_int32)]
 
 
-_lib = None
+
+
+
+_libs = {}
+_use_checked = False
 
 
 def lib_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECKED if _use_checked else _build.LIB
+
+
+class checked_library:
+    """Context in which every call of this binding goes to the checked build
+    (libstereo_checked.so: in-kernel index checks that record a failure in
+    the device error word and skip the access).  Handles belong to the
+    library that created them: create, use and close them inside the same
+    context."""
+
+    def __enter__(self):
+        global _use_checked
+        self._prev = _use_checked
+        _use_checked = True
+        return lib()
+
+    def __exit__(self, *exc):
+        global _use_checked
+        _use_checked = self._prev
 
 
 def lib():
-    """Loads libstereo.so; raises if it has not been built."""
-    global _lib
-    if _lib is None:
-        if not os.path.exists(_build.LIB):
-            raise RuntimeError(f"libstereo.so not built ({_build.LIB}); run "
+    """Loads libstereo.so (or, inside checked_library, libstereo_checked.so);
+    raises if it has not been built."""
+    path = lib_path()
+    if path not in _libs:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{os.path.basename(path)} not built ({path}); run "
                                "python -m paper_2007_12623_b300.build")
-        L = C.CDLL(_build.LIB)
+        L = C.CDLL(path)
         P, i32, f32 = C.c_void_p, C.c_int32, C.c_float
         sig = {
             "stereo_default_params": (None, [P]),
@@ -129,13 +153,17 @@ def lib():
             "stereo_set_batch_stages": (C.c_int, [P, i32]),
             "stereo_get_batch_config": (C.c_int, [P, P, P, P]),
             "stereo_autotune_batched": (C.c_int, [P, P, i32, P, P, P, P]),
+            "stereo_debug_fail_alloc": (C.c_int, [i32]),
+            "stereo_debug_live_allocations": (C.c_int64, []),
+            "stereo_build_checked": (i32, []),
+            "stereo_debug_check_selftest": (C.c_int, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
             f.restype = res
             f.argtypes = args
-        _lib = L
-    return _lib
+        _libs[path] = L
+    return _libs[path]
 
 
 def header_functions() -> list[str]:
@@ -205,10 +233,11 @@ class Handle:
         self.ptr = ptr
         self.params = params
         self.max_batch = max_batch
+        self._lib = lib()               # the library that created it destroys it
 
     def close(self):
         if self.ptr:
-            lib().stereo_destroy(self.ptr)
+            self._lib.stereo_destroy(self.ptr)
             self.ptr = None
 
     def __enter__(self):
@@ -312,6 +341,16 @@ def stereo_get_device_error(handle: Handle, stream=None) -> int:
     _check(lib().stereo_get_device_error(handle.ptr, C.byref(e), _stream(stream)),
            "stereo_get_device_error")
     return e.value
+
+
+def stereo_debug_fail_alloc(n: int):
+    """Test hook: the device allocation n + 1 calls later fails as if the
+    device were out of memory (-1 disarms)."""
+    _check(lib().stereo_debug_fail_alloc(n), "stereo_debug_fail_alloc")
+
+
+def stereo_debug_live_allocations() -> int:
+    return int(lib().stereo_debug_live_allocations())
 
 
 def stereo_status_str(status: int) -> str:

@@ -10,6 +10,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libstereo.so")
+# the checked build: in-kernel index checks that record failures in a device
+# error word instead of accessing memory (-DSTEREO_CHECKED), for tests
+LIB_CHECKED = os.path.join(HERE, "libstereo_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -18,10 +21,10 @@ def sources():
         os.path.join(ROOT, "include", "stereo.h")]
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+def needs_build(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(s) > t for s in sources())
 
 
@@ -29,15 +32,19 @@ def translation_units():
     return [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith(".cu")]
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compiles every translation unit (in parallel) and links libstereo.so."""
-    if not force and not needs_build():
-        return LIB
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compiles every translation unit (in parallel) and links libstereo.so
+    (checked=True: libstereo_checked.so with -DSTEREO_CHECKED)."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and not needs_build(lib):
+        return lib
     from concurrent.futures import ThreadPoolExecutor
     nvcc = os.environ.get("NVCC", "nvcc")
-    bdir = os.path.join(ROOT, "_build", "stereo")
+    bdir = os.path.join(ROOT, "_build", "stereo_checked" if checked else "stereo")
     os.makedirs(bdir, exist_ok=True)
     flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
+    if checked:
+        flags.append("-DSTEREO_CHECKED")
     if verbose:
         flags.append("-Xptxas=-v")
 
@@ -53,12 +60,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tus = translation_units()
     with ThreadPoolExecutor(max_workers=min(8, len(tus))) as ex:
         objs = list(ex.map(compile_one, tus))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs], cwd=CSRC)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build_all(force: bool = False) -> None:
+    build(force=force)
+    build(force=force, checked=True)
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

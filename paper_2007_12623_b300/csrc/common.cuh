@@ -8,6 +8,31 @@
 
 #define ST_INVALID (-32768)
 
+// ---------------------------------------------------------------------------
+// In-kernel index checks of the checked build (compiled with
+// -DSTEREO_CHECKED into libstereo_checked.so): a failed check records
+// ST_DEVERR_BOUNDS | site in a device-wide error word (the first failure
+// wins) and the guarded access is skipped; nothing traps.  The host reads
+// and clears the word with stereo_get_device_error.  In the normal build a
+// check is the constant true and costs nothing.
+// Without relocatable device code every translation unit has its own word;
+// each registers a reader of it with the library at load time.
+#define ST_DEVERR_BOUNDS 0x1000
+#ifdef STEREO_CHECKED
+static __device__ int g_stereo_check_err;
+__device__ __forceinline__ bool st_check(bool ok, int site) {
+    if (!ok) atomicCAS(&g_stereo_check_err, 0, ST_DEVERR_BOUNDS | site);
+    return ok;
+}
+#define ST_CHECK(cond, site) st_check((cond), (site))
+typedef cudaError_t (*st_check_word_fn)(void**);
+void st_register_check_word(st_check_word_fn fn);          // stereo_api.cu
+static cudaError_t st_this_unit_check_word(void** p) { return cudaGetSymbolAddress(p, g_stereo_check_err); }
+static const int st_check_word_registered = (st_register_check_word(st_this_unit_check_word), 0);
+#else
+#define ST_CHECK(cond, site) true
+#endif
+
 // Cost-volume element types (same numbering as stereo_cost_dtype).
 enum { CDT_NONE = 0, CDT_F32 = 1, CDT_F16 = 2, CDT_BF16 = 3 };
 

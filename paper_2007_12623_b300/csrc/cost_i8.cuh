@@ -112,10 +112,16 @@ __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, i
         int8_t* dst = sImg + ((gy - (y0 - R)) % RING) * ROWB;
         const int8_t* lsrc = L8 + (size_t)gy * a.lstride + la;
         const int8_t* rsrc = R8 + (size_t)gy * a.rstride + ra;
+        if (!ST_CHECK(gy >= 0 && gy < H && la >= 0 && la + LWB <= a.lstride && ra >= 0 &&
+                      ra + S8::RWB <= a.rstride, 1))
+            return;
         for (int i = lane; i < LWB / 16; i += 32) cp_async16(dst + 16 * i, lsrc + 16 * i);
         for (int i = lane; i < S8::RWB / 16; i += 32) cp_async16(dst + LWB + 16 * i, rsrc + 16 * i);
     };
     auto stage_stats_row = [&](int gy, int buf) {
+        if (!ST_CHECK(gy >= 0 && gy < H && a.ucol0 + ustart >= 0 && a.ucol0 + ustart + NU4 <= a.ustride &&
+                      x0 >= 0 && x0 < W, 2))
+            return;
         const float4* usrc = a.ustats + (size_t)gy * a.ustride + a.ucol0 + ustart;
         float4* ud = sU + buf * NUP;
         for (int i = lane; i < NU4; i += 32) cp_async16(ud + i + (i >> PS), usrc + i);
@@ -259,7 +265,7 @@ __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, i
                 best = max(best, key);
                 acc[s] = max(acc[s], key);
             }
-            if (CDT != CDT_NONE && do_store) {
+            if (CDT != CDT_NONE && do_store && ST_CHECK(x0 + j < W && idx0 + K <= cstride, 3)) {
                 if (CDT == CDT_F32) {
                     float* cp = reinterpret_cast<float*>(crow);
                     if (K == 4) *reinterpret_cast<float4*>(cp) = make_float4(cv[0], cv[1 % K], cv[2 % K], cv[3 % K]);

@@ -75,6 +75,11 @@ __device__ __forceinline__ void slr3_i8(const FinStats& fs, int x, int y, int u0
     s[0] = s[1] = s[2] = 0;
 #pragma unroll
     for (int dy = -R; dy <= R; ++dy) {
+        // the words read: 4 (NW + 1) bytes from the left window's first column
+        // and 4 (NW + 2) from the right one's, both rounded down to 4 bytes
+        if (!ST_CHECK(fs.l8col0 + x - R >= 0 && fs.l8col0 + x - R + 4 * (NW + 1) <= fs.l8stride &&
+                      fs.r8col0 + u0 - 1 - R >= 0 && fs.r8col0 + u0 - 1 - R + 4 * (NW + 2) <= fs.r8stride, 4))
+            continue;
         const int8_t* lp = fs.L8 + (size_t)(y + dy) * fs.l8stride + fs.l8col0 + x - R;
         const int8_t* rp = fs.R8 + (size_t)(y + dy) * fs.r8stride + fs.r8col0 + u0 - 1 - R;
         const int lsh = (int)((uintptr_t)lp & 3) * 8, rsh = (int)((uintptr_t)rp & 3) * 8;

@@ -177,6 +177,7 @@ __device__ __forceinline__ uint64_t mask_bits64(const LineMasks& m, int f, int l
     const int o = s & 31;
     const size_t L = (size_t)m.lines(f);
     const uint32_t* w = m.words + m.index(f, line, k);
+    if (!ST_CHECK(k >= -LM_PAD_LO && m.index(f, line, k) + 2 * L < m.total(), 6)) return 0ull;
     const uint32_t a0 = __ldg(w), a1 = __ldg(w + L), a2 = __ldg(w + 2 * L);
     const uint32_t lo = __funnelshift_r(a0, a1, o), hi = __funnelshift_r(a1, a2, o);
     return (uint64_t)lo | ((uint64_t)hi << 32);
@@ -229,6 +230,7 @@ __device__ __forceinline__ void outlier_masks32_px(const int16_t* __restrict__ i
         fam_coords(m, f, x, y, line, pos);
         const uint32_t L = (uint32_t)m.lines(f);
         const uint32_t* w = m.words + (uint32_t)m.off[f] + (uint32_t)((pos >> 5) + LM_PAD_LO - 1) * L + line;
+        if (!ST_CHECK((size_t)(w - m.words) + 2 * L < m.total(), 7)) { a[f][0] = a[f][1] = a[f][2] = 0u; continue; }
         a[f][0] = __ldg(w);
         a[f][1] = __ldg(w + L);
         a[f][2] = __ldg(w + 2 * L);
@@ -366,7 +368,7 @@ __device__ __forceinline__ void line_mask_words(const int16_t (*t)[LM_COLS], con
             have = true;
         }
     }
-    if (have) wf[dst] = mine;
+    if (have && ST_CHECK((size_t)m.off[F] + dst < m.total(), 5)) wf[dst] = mine;
 }
 
 // Block (vb.x, vb.y) of the grid ((W + 31) / 32, (H + 31) / 32 + 1).

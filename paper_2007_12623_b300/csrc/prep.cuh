@@ -127,6 +127,7 @@ __device__ __forceinline__ void prep_tile(const PrepArgs& pa, VBlock vb) {
         if (left && key_clear) { key_clear[gi] = 0u; key_clear[(size_t)W * H + gi] = 0u; }
         const uint32_t c = t[ly + R][lx + R];
         if (in.gray) in.gray[gi] = (uint8_t)c;
+        if (!ST_CHECK(out.col0 + gx < out.stride && (!out.ustats || out.ucol0 + gx < out.ustride), 9)) return;
         if (CB) out.img[(size_t)gy * out.stride + out.col0 + gx] = (float)c;
         else reinterpret_cast<int8_t*>(out.img)[(size_t)gy * out.stride + out.col0 + gx] = (int8_t)((int)c - 128);
         const bool interior = gx >= R && gx < W - R && gy >= R && gy < H - R;

@@ -424,7 +424,7 @@ __device__ __forceinline__ void refine_eq34_tile(const RefineArgs& a, float* __r
             const int plast = __shfl_sync(0xffffffffu, last, p);
             const int kc = pk0 + ch * (16 / esz);                     // first cost index of the chunk
             ld[i] = make_uint4(0u, 0u, 0u, 0u);
-            if (kc <= plast) {
+            if (kc <= plast && ST_CHECK(kc >= 0 && (kc + 16 / esz) <= cs && x0 + p < a.W && gy < a.H, 8)) {
                 const size_t gp = (size_t)gy * a.W + x0 + p;
                 ld[i] = __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(a.cost) +
                                                              (gp * (size_t)cs + kc) * esz));

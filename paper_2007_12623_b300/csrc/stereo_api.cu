@@ -727,6 +727,74 @@ static stereo_status run_with_graph(stereo_handle* h, GraphCache& gc, const void
     return last_error();
 }
 
+#ifdef STEREO_CHECKED
+// Readers of the checked build's error words, registered by every
+// translation unit at load time.
+static std::vector<st_check_word_fn>& check_word_readers() {
+    static std::vector<st_check_word_fn> v;
+    return v;
+}
+void st_register_check_word(st_check_word_fn fn) { check_word_readers().push_back(fn); }
+
+// A check that cannot pass, for the checked build's self-test: the store it
+// guards is skipped and the error word records site 0xfff.
+__global__ void k_check_selftest(int* out, int n) {
+    const int i = n;                                        // one past the end
+    if (ST_CHECK(i < n, 0xfff)) out[i] = 1;
+}
+#endif
+
+// Device allocations of the handles go through dev_alloc / dev_free, which
+// count the live ones and, for tests, can fail on purpose: after
+// stereo_debug_fail_alloc(n), the allocation n + 1 calls later fails as if
+// the device were out of memory (without calling cudaMalloc).
+static std::atomic<int> g_fail_alloc{-1};
+static std::atomic<long long> g_live_allocs{0};
+
+static cudaError_t dev_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    int n = g_fail_alloc.load();
+    while (n >= 0) {
+        if (g_fail_alloc.compare_exchange_weak(n, n - 1)) break;
+    }
+    if (n == 0) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return e;
+    }
+    g_live_allocs.fetch_add(1);
+    return cudaSuccess;
+}
+
+static void dev_free(void* p) {
+    if (!p) return;
+    cudaFree(p);
+    g_live_allocs.fetch_sub(1);
+}
+
+// Frees everything a handle holds (any subset of it may be allocated).
+static void release_handle(stereo_handle* h) {
+    h->single.clear();
+    h->batch.clear();
+    if (h->ev_ready)
+        for (int i = 0; i <= STEREO_NUM_STAGES; ++i) cudaEventDestroy(h->ev[i]);
+    dev_free(h->ws);
+    dev_free(h->dev_err);
+    dev_free(h->units);
+    dev_free(h->pair_args);
+    dev_free(h->pair_radius);
+    dev_free(h->counter);
+    dev_free(h->btab);
+    for (int i = 0; i < BATCH_STREAMS; ++i) {
+        if (h->aux[i]) cudaStreamDestroy(h->aux[i]);
+        if (h->join_ev[i]) cudaEventDestroy(h->join_ev[i]);
+    }
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    delete h;
+}
+
 extern "C" {
 
 void stereo_default_params(stereo_params* p) {
@@ -785,12 +853,9 @@ stereo_status stereo_create(const stereo_params* p, int32_t max_batch, stereo_ha
     h->dev_err = nullptr;
     h->timing = false;
     h->ev_ready = false;
-    if (cudaMalloc(&h->ws, h->pair_bytes * max_batch) != cudaSuccess ||
-        cudaMalloc(&h->dev_err, sizeof(int32_t)) != cudaSuccess) {
-        cudaGetLastError();
-        if (h->ws) cudaFree(h->ws);
-        if (h->dev_err) cudaFree(h->dev_err);
-        delete h;
+    if (dev_alloc(reinterpret_cast<void**>(&h->ws), h->pair_bytes * max_batch) != cudaSuccess ||
+        dev_alloc(reinterpret_cast<void**>(&h->dev_err), sizeof(int32_t)) != cudaSuccess) {
+        release_handle(h);
         return STEREO_ERR_OOM;
     }
     if (max_batch > 1) {
@@ -799,17 +864,13 @@ stereo_status stereo_create(const stereo_params* p, int32_t max_batch, stereo_ha
         h->max_units = (size_t)max_batch * ((p->max_width + 15) / 16) * ((p->max_height + 7) / 8) *
                        ((p->num_disp + 63) / 64);
         h->btab_bytes = batch_stage_bytes(max_batch);
-        if (cudaMalloc(&h->units, h->max_units * sizeof(int4)) != cudaSuccess ||
-            cudaMalloc(&h->pair_args, 2 * (size_t)max_batch * sizeof(CostArgs)) != cudaSuccess ||
-            cudaMalloc(&h->pair_radius, (size_t)max_batch * sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&h->counter, 2 * sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&h->btab, h->btab_bytes) != cudaSuccess) {
-            cudaGetLastError();
-            cudaFree(h->units); cudaFree(h->pair_args); cudaFree(h->pair_radius); cudaFree(h->counter);
-            cudaFree(h->btab);
-            cudaFree(h->ws);
-            cudaFree(h->dev_err);
-            delete h;
+        if (dev_alloc(reinterpret_cast<void**>(&h->units), h->max_units * sizeof(int4)) != cudaSuccess ||
+            dev_alloc(reinterpret_cast<void**>(&h->pair_args), 2 * (size_t)max_batch * sizeof(CostArgs)) !=
+                cudaSuccess ||
+            dev_alloc(reinterpret_cast<void**>(&h->pair_radius), (size_t)max_batch * sizeof(int)) != cudaSuccess ||
+            dev_alloc(reinterpret_cast<void**>(&h->counter), 2 * sizeof(int)) != cudaSuccess ||
+            dev_alloc(reinterpret_cast<void**>(&h->btab), h->btab_bytes) != cudaSuccess) {
+            release_handle(h);
             return STEREO_ERR_OOM;
         }
         // streams for the per-pair stages; without them the stages run in order on the caller's stream
@@ -824,9 +885,8 @@ stereo_status stereo_create(const stereo_params* p, int32_t max_batch, stereo_ha
         cudaGetLastError();
     }
     if (cudaMemset(h->dev_err, 0, sizeof(int32_t)) != cudaSuccess) {
-        cudaFree(h->ws);
-        cudaFree(h->dev_err);
-        delete h;
+        cudaGetLastError();
+        release_handle(h);
         return STEREO_ERR_CUDA;
     }
     *out = h;
@@ -836,24 +896,40 @@ stereo_status stereo_create(const stereo_params* p, int32_t max_batch, stereo_ha
 stereo_status stereo_destroy(stereo_handle* h) {
     if (!h) return STEREO_OK;
     cudaDeviceSynchronize();
-    h->single.clear();
-    h->batch.clear();
-    if (h->ev_ready)
-        for (int i = 0; i <= STEREO_NUM_STAGES; ++i) cudaEventDestroy(h->ev[i]);
-    cudaFree(h->ws);
-    cudaFree(h->dev_err);
-    if (h->units) cudaFree(h->units);
-    if (h->pair_args) cudaFree(h->pair_args);
-    if (h->pair_radius) cudaFree(h->pair_radius);
-    if (h->counter) cudaFree(h->counter);
-    if (h->btab) cudaFree(h->btab);
-    for (int i = 0; i < BATCH_STREAMS; ++i) {
-        if (h->aux[i]) cudaStreamDestroy(h->aux[i]);
-        if (h->join_ev[i]) cudaEventDestroy(h->join_ev[i]);
-    }
-    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
-    delete h;
+    release_handle(h);
     return STEREO_OK;
+}
+
+stereo_status stereo_debug_fail_alloc(int32_t n) {
+    if (n < -1) return STEREO_ERR_INVALID_ARG;
+    g_fail_alloc.store(n);
+    return STEREO_OK;
+}
+
+int64_t stereo_debug_live_allocations(void) { return g_live_allocs.load(); }
+
+int32_t stereo_build_checked(void) {
+#ifdef STEREO_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+stereo_status stereo_debug_check_selftest(void* stream) {
+#ifdef STEREO_CHECKED
+    int* buf = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&buf), sizeof(int), S(stream)) != cudaSuccess) {
+        cudaGetLastError();
+        return STEREO_ERR_OOM;
+    }
+    k_check_selftest<<<1, 1, 0, S(stream)>>>(buf, 1);
+    cudaFreeAsync(buf, S(stream));
+    return last_error();
+#else
+    (void)stream;
+    return STEREO_ERR_UNSUPPORTED;
+#endif
 }
 
 stereo_status stereo_get_device_error(stereo_handle* h, int32_t* err, void* stream) {
@@ -863,6 +939,22 @@ stereo_status stereo_get_device_error(stereo_handle* h, int32_t* err, void* stre
         cudaStreamSynchronize(S(stream)) != cudaSuccess ||
         cudaMemsetAsync(h->dev_err, 0, sizeof(int32_t), S(stream)) != cudaSuccess)
         return STEREO_ERR_CUDA;
+#ifdef STEREO_CHECKED
+    // the checked build's words (one per translation unit): the first
+    // failed check recorded, the words cleared
+    for (st_check_word_fn fn : check_word_readers()) {
+        void* addr = nullptr;
+        int32_t w = 0;
+        if (fn(&addr) != cudaSuccess || !addr ||
+            cudaMemcpyAsync(&w, addr, sizeof(w), cudaMemcpyDeviceToHost, S(stream)) != cudaSuccess ||
+            cudaMemsetAsync(addr, 0, sizeof(w), S(stream)) != cudaSuccess ||
+            cudaStreamSynchronize(S(stream)) != cudaSuccess) {
+            cudaGetLastError();
+            return STEREO_ERR_CUDA;
+        }
+        if (!v) v = w;
+    }
+#endif
     *err = v;
     return STEREO_OK;
 }

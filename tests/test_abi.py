@@ -62,3 +62,27 @@ def test_host_side_argument_checks(L):
     assert L.stereo_vote_nbins(4.0, 128.0) == 64 and L.stereo_vote_nbins(0.0, 1.0) == 0
     assert L.stereo_vote_matches(None, None, 10, 4.0, 128.0, None, None, None, None) == 1
     assert L.stereo_destroy(None) == 0
+
+
+def test_checked_build_loads_and_exports_everything(L):
+    stbuild.build(checked=True)
+    with st.checked_library() as LC:
+        assert LC.stereo_build_checked() == 1
+        missing = [n for n in st.header_functions() if not hasattr(LC, n)]
+        assert not missing, missing
+    assert L.stereo_build_checked() == 0
+    assert L.stereo_debug_check_selftest(None) == 4        # STEREO_ERR_UNSUPPORTED in the normal build
+
+
+def test_injected_allocation_failure_returns_oom_and_frees(L):
+    """The first device allocation of stereo_create fails by injection: the
+    call returns STEREO_ERR_OOM and holds nothing (no GPU needed: the
+    injected failure comes before any cudaMalloc)."""
+    live0 = st.stereo_debug_live_allocations()
+    st.stereo_debug_fail_alloc(0)
+    h = C.c_void_p()
+    p = st.stereo_default_params(max_width=64, max_height=32, num_disp=16)
+    assert L.stereo_create(C.byref(p), 1, C.byref(h)) == 3          # STEREO_ERR_OOM
+    assert st.stereo_debug_live_allocations() == live0
+    assert L.stereo_debug_fail_alloc(-2) == 1
+    st.stereo_debug_fail_alloc(-1)
