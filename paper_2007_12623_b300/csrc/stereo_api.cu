@@ -95,7 +95,7 @@ size_t pair_ws_bytes(size_t npix, int D, int cdt, int maxW = 0, int maxH = 0, in
     b += align_up(npix, 256) * 2;                 // gl, gr
     b += 0;                                       // image-shaped buffers: see carve()
     b += align_up(npix * 8, 256);                 // keys
-    b += align_up(npix * (size_t)cost_stride(D) * elem_size(cdt), 256);
+    b += align_up((npix + 32) * (size_t)cost_stride(D) * elem_size(cdt), 256);   // + 32 pixels of slack (carve)
     b += align_up(npix * 2, 256) * 8;             // wta lr p q o t post cnt
     b += align_up(mask_words(maxW, maxH) * 4, 256);   // line bitmasks
     b += align_up(npix * 4, 256) * 7;             // dprev dt b rsC rsO rsB dfin
