@@ -14,6 +14,9 @@ Other workloads (``--workload``):
                               volume stored in FP16 / BF16 (their disparity
                               error against the FP64 oracle is measured by
                               tests/test_gpu_precision.py).
+  tissue960_x4 / _x4_f16      4 pairs of the default workload's generator per
+                              stereo_match_batched call (a stream of pairs
+                              matched 4 at a time), FP32 / FP16 volume.
   batch64                     64 pairs of mixed sizes (16 each of 640x480,
                               960x540, 1280x720, 1920x1080), D in {64,128,192},
                               windows {9,11,15}, FP16 cost: one
@@ -75,6 +78,14 @@ WORKLOADS = {
                                seed=synth.seed_for(2), disp=(10.0, 170.0)),
     # 64 mixed pairs in one batched call, FP16 cost
     "batch64": dict(kind="batched", n=64, cost="f16", smooth_radius=15),
+    # a stream of 960x540 D = 128 pairs matched 4 at a time through the
+    # batched call (throughput form of the single-pair workload), FP32 / FP16
+    "tissue960_x4": dict(kind="batched", n=4, cost="f32", smooth_radius=15, same="tissue960"),
+    "tissue960_x4_f16": dict(kind="batched", n=4, cost="f16", smooth_radius=15, same="tissue960"),
+    # one pair of each size class of the 64-pair batch (a small batched case
+    # for profiling): 640x480 D192 r7, 960x540 D128 r5, 1280x720 D64 r7,
+    # 1920x1080 D192 r7
+    "batch4": dict(kind="batched", n=4, cost="f16", smooth_radius=15, pick=(3, 17, 39, 56)),
     # soft-argmin training step on 8 pairs
     "soft8": dict(kind="soft", B=8, W=960, H=540, D=128, r=5, tau=0.1, seed=synth.seed_for(4),
                   disp=(10.0, 110.0)),
@@ -91,6 +102,8 @@ COST_CODE = {"none": 0, "f32": 1, "f16": 2, "bf16": 3}
 # read from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of
 # the kernel as it is built now; absent where no such capture exists.
 KERNEL_TRAFFIC = {"tissue960": 221.4e6,
+                  # both launches of the D = 192 range (128 at K = 4, 64 at K = 2)
+                  "tissue960_d192_f16": 124.9e6,
                   "soft8": {"k_soft_box_t1": 569.0e6, "k_cost_wta (soft backward form)": 235.5e6}}
 COST_BYTES = {"none": 0, "f32": 4, "f16": 2, "bf16": 2}
 METRIC = "Gpix*disp/s and ms per 960x540 pair (1 B300), % of roofline, vs oracle"
@@ -124,13 +137,23 @@ def _batch_pair(i):
     return synth.batch_pair(i)
 
 
-def make_batch(n, first):
-    """Pairs first..first+n-1 of the mixed batch, generated by a spawn pool
-    (started before any CUDA call)."""
+def _same_pair(args):
+    name, i = args
+    wl = WORKLOADS[name]
+    L, R, gt = make_pair(wl, i)
+    return L, R, gt, dict(W=wl["W"], H=wl["H"], D=wl["D"], r=wl["r"])
+
+
+def make_batch(n, first, same=None, pick=None):
+    """Pairs first..first+n-1 of the mixed batch (or the pairs `pick` of it,
+    or, with `same`, pairs of that single-pair workload's generator),
+    generated by a spawn pool (started before any CUDA call)."""
     import multiprocessing as mp
     procs = max(1, min(n, os.cpu_count() or 1, 32))
     with mp.get_context("spawn").Pool(procs) as pool:
-        return pool.map(_batch_pair, range(first, first + n))
+        if same:
+            return pool.map(_same_pair, [(same, i) for i in range(first, first + n)])
+        return pool.map(_batch_pair, list(pick) if pick else range(first, first + n))
 
 
 class ClockSampler:
@@ -592,7 +615,8 @@ def run_batched(args, wl, rank, world, dev, pairs):
         host.append((torch.from_numpy(Lrgb).pin_memory(), torch.from_numpy(Rrgb).pin_memory(),
                      torch.empty((H, W), dtype=torch.float32).pin_memory()))
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    tune = st.stereo_autotune_batched(h, batch, stream=stream)
+    tune = (st.stereo_autotune_batched(h, batch, stream=stream) if not args.no_autotune
+            else dict(st.stereo_get_batch_config(h), note="default configuration, not tuned"))
 
     def step():
         st.stereo_match_batched(h, batch, use_graph=True, stream=stream)
@@ -634,9 +658,12 @@ def run_batched(args, wl, rank, world, dev, pairs):
                                 stage_ms["cost_wta"], peaks, sm_count, "k_cost_batched",
                                 KERNEL_TRAFFIC.get(args.workload))
     eq = 960 * 540 * 128 / P                      # one 960x540x128 pair's share of the work
+    same = wl.get("same")
     line = _base_line(args, world, value, t_max, "f32", {
         "workload": args.workload, "pairs": n,
-        "sizes": "16 each of 640x480, 960x540, 1280x720, 1920x1080",
+        "sizes": (f"{n} x {WORKLOADS[same]['W']}x{WORKLOADS[same]['H']} ({same} generator)" if same
+                  else ("pairs %s of the 64-pair batch" % (wl["pick"],) if wl.get("pick")
+                        else "16 each of 640x480, 960x540, 1280x720, 1920x1080")),
         "num_disp": sorted({s["D"] for s in specs}), "windows": sorted({2 * s["r"] + 1 for s in specs}),
         "cost_storage": wl["cost"], "smooth_radius": wl["smooth_radius"], "refine_iters": 5,
         "pix_disp_per_step": P, "parallelism": f"replicas x{world} (independent batches)",
@@ -644,6 +671,7 @@ def run_batched(args, wl, rank, world, dev, pairs):
         "launch": "one stereo_match_batched per step, CUDA graph replay, persistent cost launch",
         "autotuned": tune})
     line.update({
+        "ms_per_pair": round(t_max * 1e3 / args.steps / n, 4),
         "ms_per_960x540x128_equivalent": round(t_max * 1e3 / args.steps * eq, 4),
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "roofline": roof,
@@ -767,6 +795,8 @@ def run_soft_step(args, wl, rank, world, dev):
 
 def _oracle_problem(wl):
     """(Lrgb, Rrgb, W, D, r, smooth radius) of the workload's first pair."""
+    if wl["kind"] == "batched" and wl.get("same"):
+        return _oracle_problem(WORKLOADS[wl["same"]])
     if wl["kind"] == "batched":
         L, R, gt, s = synth.batch_pair(16)               # a 960x540 pair of the batch
         return L, R, s["W"], s["D"], s["r"], wl["smooth_radius"]
@@ -819,7 +849,8 @@ def reference_config(name, wl, problem, rows):
     else:
         cfg.update(smooth_radius=sr, refine_iters=5, step="whole path S0-S7")
     if wl["kind"] == "batched":
-        cfg["pair"] = "a 960x540 pair of the 64-pair batch"
+        cfg["pair"] = (f"a pair of the {wl['same']} workload (batched {wl['n']} at a time on the GPU)"
+                       if wl.get("same") else "a 960x540 pair of the 64-pair batch")
     cfg.update(rows_per_step=rows, implementation="FP64 C oracle, single thread, host CPU",
                precision="f64")
     return cfg
@@ -855,6 +886,7 @@ def run_reference(args, wl):
 # name -> (steps, warmup).  Each runs exactly as its own --workload line
 # would, with fewer steps.
 SUB_WORKLOADS = {"perlin320": (200, 5), "tissue960_f16": (200, 5), "tissue960_none": (200, 5),
+                 "tissue960_x4": (100, 5), "tissue960_x4_f16": (100, 5),
                  "tissue960_d192_f16": (200, 5), "tissue960_d192_bf16": (200, 5),
                  "tissue960_d192_f32": (200, 5), "paper960": (200, 5), "batch64": (6, 3), "soft8": (20, 3)}
 
@@ -880,7 +912,7 @@ def run_sub_workloads(args, dev, batch_pairs):
         sa = argparse.Namespace(**vars(args))
         sa.workload, sa.steps, sa.warmup = name, steps, warmup
         if wl["kind"] == "batched":
-            line = run_batched(sa, wl, 0, 1, dev, batch_pairs)
+            line = run_batched(sa, wl, 0, 1, dev, batch_pairs[name])
         elif wl["kind"] == "soft":
             line = run_soft_step(sa, wl, 0, 1, dev)
         else:
@@ -913,6 +945,8 @@ def main():
     ap.add_argument("--oracle-rows", type=int, default=8)
     ap.add_argument("--cpu-baseline-rows", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched workloads: the default unit configuration instead of the autotuner's")
     ap.add_argument("--no-sub-workloads", action="store_true",
                     help="default run only: skip the other workloads' records")
     args = ap.parse_args()
@@ -927,9 +961,11 @@ def main():
 
     subs = (world == 1 and args.workload == "tissue960" and not args.no_sub_workloads
             and "--workload" not in sys.argv)
-    pairs = make_batch(wl["n"], rank * wl["n"]) if wl["kind"] == "batched" else None
-    if subs:
-        batch_pairs = make_batch(WORKLOADS["batch64"]["n"], 0)      # before any CUDA call
+    pairs = (make_batch(wl["n"], rank * wl["n"], wl.get("same"), wl.get("pick")) if wl["kind"] == "batched"
+             else None)
+    if subs:                                                        # before any CUDA call
+        batch_pairs = {name: make_batch(WORKLOADS[name]["n"], 0, WORKLOADS[name].get("same"))
+                       for name in SUB_WORKLOADS if WORKLOADS[name]["kind"] == "batched"}
     import torch
     dev = torch.device(f"cuda:{int(os.environ.get('LOCAL_RANK', 0))}")
     torch.cuda.set_device(dev)
