@@ -330,8 +330,10 @@ stereo_status stereo_stage_refine(stereo_handle* h, const int16_t* o_in, const v
  * d_soft = sum_d d p_d.  Images are float (batch x height x width,
  * contiguous, row stride = width); the handle must have been created with
  * soft_argmin = 1 (and cost_dtype F32) and sized for width, height,
- * num_disp.  tau >= 0.025 (smaller values return STEREO_ERR_UNSUPPORTED);
- * win_radius <= 7.  Pixels without a valid candidate get NaN.
+ * num_disp.  Any tau > 0: below 0.025, where exp((ZNCC - 1) / tau) could
+ * underflow for every candidate, the forward pass takes each pixel's
+ * weights relative to its best candidate; win_radius <= 7.  Pixels without
+ * a valid candidate get NaN.
  * ---------------------------------------------------------------------- */
 
 /* Forward: d_soft and the log-sum-exp of the logits (both float B*H*W).

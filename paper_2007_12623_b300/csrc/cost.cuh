@@ -55,7 +55,7 @@ struct CostSmem {
     // backward: the row's costs [TW][CVS] (each lane's K values, later its
     // two partial sums), the exit slots of the diagonal sums [2][32] and the
     // per-pixel inputs of two rows [2][3][TW] and the row's per-pixel factors [TW][8]
-    static constexpr int SOFT_BYTES = BYTES + 2 * G::TW * 33 * 4;
+    static constexpr int SOFT_BYTES = BYTES + 2 * G::TW * 33 * 4 + G::TW * 4;   // + [TW] reference costs
     static constexpr int CVS = K >= 2 ? 32 * K + 4 : 68;
     static constexpr int SOFT_BWD_BYTES = BYTES + (G::TW * CVS + 64 + 6 * G::TW + 8 * G::TW) * 4;
 };
@@ -106,9 +106,13 @@ struct CostArgs {
     float* sQ2 = nullptr;
     float sk2 = 0.f;                              // log2(e) / tau
     float sinvtau = 0.f;                          // 1 / tau
+    int sshift = 0;                               // FWD: weights relative to each pixel's best candidate
 };
 
-constexpr int SOFT_NONE = 0, SOFT_FWD = 1, SOFT_BWD = 2;
+// SOFT_FWDS: the forward form with each pixel's weights taken relative to
+// its best candidate (for small temperatures, where exp(-cost / tau) of
+// every candidate would underflow).
+constexpr int SOFT_NONE = 0, SOFT_FWD = 1, SOFT_BWD = 2, SOFT_FWDS = 3;
 
 // Statistics of right pixel i of a staged row (stored at float4 slot
 // i + i/8): window-sum split, 1/sqrt(B), and the key offset / cost value that
@@ -134,6 +138,10 @@ __device__ __forceinline__ void load_slot(const float4* U, int i, float& h, floa
 // beyond D) and leaves their sum and disparity-weighted sum in a shared
 // tile, and after each row lane j adds up pixel j's 32 partial sums into
 // d_soft and the log-sum-exp (all candidates of a pixel in this one unit).
+// SOFT = SOFT_FWDS: the same with weights exp((c_min - cost) / tau), c_min
+// the pixel's smallest cost (a warp minimum per output column), so the best
+// candidate weighs 1 at any temperature; the log-sum-exp adds back
+// (1 - c_min) / tau.
 // SOFT = SOFT_BWD: the unrolled pass parks each row's costs in shared
 // memory, and a second pass over the row (a loop unrolled K times only,
 // which keeps the kernel body small) forms the backward terms of each
@@ -157,6 +165,7 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
     uint32_t* sExit = reinterpret_cast<uint32_t*>(smem + S::IMG + S::US + S::LS);
     float* sS0 = smem + S::IMG + S::US + S::LS + 32;                 // SOFT: [TW][33] weight sums (P1)
     float* sS1 = sS0 + TW * 33;                                       // SOFT: [TW][33] weighted d sums (P2)
+    float* sCm = sS1 + TW * 33;                                       // SOFT_FWDS: [TW] reference costs
     constexpr int CVS = S::CVS;
     float* sCv = sS0;                                                 // SOFT_BWD: [TW][CVS] parked costs
     float* sQx = sCv + TW * CVS;                                      // SOFT_BWD: [2][32] Q1, Q2 exits
@@ -392,13 +401,29 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
                 else if (K == 2) *reinterpret_cast<float2*>(cvp) = make_float2(cv[0], cv[1 % K]);
                 else cvp[0] = cv[0];
             }
-            if (SOFT == SOFT_FWD) {
-                float pe = 0.f, qk = 0.f;
+            if (SOFT == SOFT_FWD || SOFT == SOFT_FWDS) {
+                float pe = 0.f, qk = 0.f, cref = 0.f;
+                if (SOFT == SOFT_FWDS) {
+                    // the pixel's smallest valid cost: 1 + c lies in (0, 3] for a
+                    // valid candidate, so its float bits order like the value;
+                    // NaN (invalid) becomes -inf and a candidate beyond D +inf,
+                    // both with bits above every valid one
+                    uint32_t m = 0xffffffffu;
+#pragma unroll
+                    for (int k = 0; k < K; ++k)
+                        m = min(m, __float_as_uint(fmaxf(cv[k] + 1.f, -xlim[k])));
+                    m = __reduce_min_sync(0xffffffffu, m);
+                    cref = m <= 0x40400000u ? __uint_as_float(m) - 1.f : 0.f;   // 0x40400000 = 3.0
+                    if (lane == 0) sCm[j] = cref;
+                }
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
-                    // exp(-cost / tau) = exp((rho - 1) / tau) <= 1; ex2(-inf) = 0
+                    // exp(-cost / tau) = exp((rho - 1) / tau) <= 1 (SOFT_FWDS:
+                    // exp((c_min - cost) / tau), about 1 at most); ex2(-inf) = 0
                     // max(NaN, -inf) = -inf: an invalid candidate (NaN cost) gets weight 0
-                    const float x = fminf(fmaxf(-cv[k] * a.sk2, __int_as_float(0xff800000)), xlim[k]);
+                    const float x = fminf(fmaxf((SOFT == SOFT_FWDS ? cref - cv[k] : -cv[k]) * a.sk2,
+                                                __int_as_float(0xff800000)),
+                                          xlim[k]);
                     float e;
                     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(x));
                     pe += e;
@@ -558,7 +583,7 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
                 atomicAdd(a.sQ2 + (size_t)y * W + u, e2);
             }
         }
-        if (SOFT == SOFT_FWD && lane < nsteps) {
+        if ((SOFT == SOFT_FWD || SOFT == SOFT_FWDS) && lane < nsteps) {
             float s0 = 0.f, s1 = 0.f;
 #pragma unroll 8
             for (int i = 0; i < 32; ++i) {
@@ -567,8 +592,9 @@ __device__ __forceinline__ void cost_unit(const CostArgs& a, float* smem, int x0
             }
             const size_t pix = (size_t)y * W + x0 + lane;
             const bool any = s0 > 0.f;
+            const float shift = SOFT == SOFT_FWDS ? (1.f - sCm[lane]) * a.sinvtau : a.sinvtau;
             a.sds[pix] = any ? s1 / s0 : __int_as_float(0x7fc00000);
-            a.slse[pix] = any ? logf(s0) + a.sinvtau : __int_as_float(0x7fc00000);
+            a.slse[pix] = any ? logf(s0) + shift : __int_as_float(0x7fc00000);
         }
         if (WTA && lane < nsteps) {
             atomicMax(a.keyL + (size_t)y * W + x0 + lane, myLeft);

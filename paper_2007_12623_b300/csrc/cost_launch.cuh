@@ -51,6 +51,8 @@ void launch_cost_rkc(CostArgs a, int rows_override, cudaStream_t s) {
         // soft-argmin form: d_soft and the log-sum-exp instead of a volume
         if (a.sA)
             k_cost_wta<R, K, CDT, MINB, CB, false, SOFT_BWD><<<dim3(nx, ny, nz), 32, CostSmem<R, K>::SOFT_BWD_BYTES, s>>>(a);
+        else if (a.sds && a.sshift)
+            k_cost_wta<R, K, CDT, MINB, CB, false, SOFT_FWDS><<<dim3(nx, ny, nz), 32, CostSmem<R, K>::SOFT_BYTES, s>>>(a);
         else if (a.sds)
             k_cost_wta<R, K, CDT, MINB, CB, false, SOFT_FWD><<<dim3(nx, ny, nz), 32, CostSmem<R, K>::SOFT_BYTES, s>>>(a);
         else k_cost_wta<R, K, CDT, MINB, CB><<<dim3(nx, ny, nz), 32, BYTES, s>>>(a);

@@ -79,6 +79,10 @@ __device__ __forceinline__ float tile_row_sum(const float* t, int lane) {
     return s;
 }
 
+// SHIFT: the weights of a pixel relative to its best candidate,
+// exp((c_min - cost) / tau) (a minimum over the chunks' warps first), for
+// temperatures at which exp(-cost / tau) of every candidate would underflow.
+template <bool SHIFT>
 __global__ void __launch_bounds__(256) k_soft_fwd(SoftArgs a, float* __restrict__ dsoft,
                                                   float* __restrict__ lse) {
     extern __shared__ float soft_run_sm[];
@@ -91,6 +95,25 @@ __global__ void __launch_bounds__(256) k_soft_fwd(SoftArgs a, float* __restrict_
     const int k = c * 32 + lane;
     const int kc = min(k, a.cs - 1);
     const float* row = a.cost + (size_t)y * a.W * a.cs + kc;
+    float cref = 0.f;                                         // SHIFT: lane j's pixel's c_min
+    if (SHIFT) {
+        // per pixel the smallest valid cost of this chunk (1 + c in (0, 3]
+        // orders like its float bits; invalid -> +inf), then over the chunks
+        uint32_t mine = 0xffffffffu;
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+            const float v = __ldg(row + (size_t)min(x0 + j, a.W - 1) * a.cs);
+            const bool ok = x0 + j < a.W && k < a.D && v == v;
+            const uint32_t m = __reduce_min_sync(0xffffffffu, ok ? __float_as_uint(v + 1.f) : 0x7f800000u);
+            if (lane == j) mine = m;
+        }
+        red[c * 32 + lane] = __uint_as_float(mine);
+        __syncthreads();
+        uint32_t m = 0xffffffffu;
+        for (int w = 0; w < nch; ++w) m = min(m, __float_as_uint(red[w * 32 + lane]));
+        cref = m <= 0x40400000u ? __uint_as_float(m) - 1.f : 0.f;          // 0x40400000 = 3.0
+        __syncthreads();                                                  // red is reused below
+    }
 #pragma unroll
     for (int h = 0; h < 32; h += 16) {
         float v[16];
@@ -100,8 +123,10 @@ __global__ void __launch_bounds__(256) k_soft_fwd(SoftArgs a, float* __restrict_
         for (int j = 0; j < 16; ++j) {
             const float rho = 1.f - v[j];
             const bool ok = x0 + h + j < a.W && k < a.D && rho == rho;   // valid candidate
-            float e = 0.f;                                                // exp((rho - 1) / tau) <= 1
-            if (ok) asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"((rho - 1.f) * k2));
+            // exp((rho - 1) / tau) <= 1 (SHIFT: exp((c_min - cost) / tau))
+            const float xe = SHIFT ? (__shfl_sync(0xffffffffu, cref, h + j) - v[j]) * k2 : (rho - 1.f) * k2;
+            float e = 0.f;
+            if (ok) asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(xe));
             t0[(h + j) * 33 + lane] = e;
         }
     }
@@ -129,7 +154,7 @@ __global__ void __launch_bounds__(256) k_soft_fwd(SoftArgs a, float* __restrict_
             const size_t pix = (size_t)y * a.W + x;
             const bool any = s0 > 0.f;
             dsoft[pix] = any ? s1 / s0 : __int_as_float(0x7fc00000);
-            lse[pix] = any ? logf(s0) + 1.f / a.tau : __int_as_float(0x7fc00000);
+            lse[pix] = any ? logf(s0) + (SHIFT ? (1.f - cref) : 1.f) / a.tau : __int_as_float(0x7fc00000);
         }
     }
 }

@@ -332,7 +332,8 @@ void set_smem_attributes() {
     cudaFuncSetAttribute(k_refine_eq34<false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_refine_eq34<true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_refine_eq34<false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_soft_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_soft_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_soft_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_vote_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, VOTE_MAX_N * 8);
     cudaFuncSetAttribute(k_soft_dA, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_fill_disc_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1577,7 +1578,6 @@ static stereo_status check_soft(const stereo_handle* h, int B, int W, int H, int
         return STEREO_ERR_INVALID_ARG;
     if (!h->p.soft_argmin) return STEREO_ERR_INVALID_ARG;
     if (!(tau > 0.f)) return STEREO_ERR_INVALID_ARG;
-    if (tau < 0.025f) return STEREO_ERR_UNSUPPORTED;   // exp((rho - 1) / tau) would underflow
     if (d_min < -CMAX_DMIN || d_min > CMAX_DMIN) return STEREO_ERR_INVALID_ARG;
     if (W > h->p.max_width || H > h->p.max_height || D > h->p.num_disp) return STEREO_ERR_TOO_LARGE;
     return STEREO_OK;
@@ -1598,6 +1598,11 @@ struct SoftForm {
     int nch;
     float tau;
 };
+
+// Below this temperature exp((rho - 1) / tau) could underflow for every
+// candidate of a pixel (rho >= -1: the exponent reaches -2 / tau), so the
+// forward weights are taken relative to each pixel's best candidate.
+static bool soft_shift(float tau) { return tau < 0.025f; }
 
 // All candidates in one cost-kernel chunk: the soft forms apply.
 static bool soft_fused(int D) { return D <= 32 * pick_k(D); }
@@ -1646,6 +1651,7 @@ static void soft_prepare(stereo_handle* h, const PairWs& w, const float* L, cons
         a.sQ2 = f->Q2;
         a.sk2 = 1.4426950408889634f / f->tau;
         a.sinvtau = 1.f / f->tau;
+        a.sshift = soft_shift(f->tau);
     }
     launch_cost(r, K, a.cdt, a, g_cost_rows, s);
     if (timed) mark(h, 2, s);
@@ -1685,7 +1691,8 @@ stereo_status stereo_softargmin_fwd(stereo_handle* h, const float* left, const f
         sa.tau = tau;
         const unsigned runs = (unsigned)(((width + SOFT_RUN - 1) / SOFT_RUN) * height);
         const int nch = (num_disp + 31) / 32;
-        k_soft_fwd<<<runs, 32 * nch, soft_fwd_smem(nch), s>>>(sa, d_soft + b * npix, lse + b * npix);
+        if (soft_shift(tau)) k_soft_fwd<true><<<runs, 32 * nch, soft_fwd_smem(nch), s>>>(sa, d_soft + b * npix, lse + b * npix);
+        else k_soft_fwd<false><<<runs, 32 * nch, soft_fwd_smem(nch), s>>>(sa, d_soft + b * npix, lse + b * npix);
         counted();
         if (timed)
             for (int k = 3; k <= STEREO_NUM_STAGES; ++k) mark(h, k, s);

@@ -59,6 +59,66 @@ def test_forward_matches_oracle(dev, r, D, tau):
     h.close()
 
 
+@pytest.mark.parametrize("D,H,W", [(16, 64, 80), (100, 40, 200), (150, 40, 232)])
+@pytest.mark.parametrize("tau", [0.02, 0.005, 0.001])
+def test_forward_small_temperature(dev, D, H, W, tau):
+    """Temperatures below 0.025 (weights relative to each pixel's best
+    candidate, in the cost kernel's forward form for D <= 128 and in the
+    volume kernel above): d_soft and the log-sum-exp against the oracle.
+    FP32 ZNCC values carry up to ~1e-6 of error, which moves a weight by
+    ~1e-6 / tau relative, so the d_soft bar is 1e-4 + 4e-6 / tau * D px and
+    the log-sum-exp's 1e-5 relative + 2e-7 / tau; as
+    tau -> 0 d_soft tends to the winner-take-all disparity where the best
+    candidate leads the second by more than 20 tau (Sec. II-A winners)."""
+    L, R, gt = _crop_pair(synth.seed_for(4), 30, 40, H, W)
+    ds_ref, lse_ref, hv = oracle.softargmin_fwd(L, R, 0, D, 5, tau)
+    h = _handle(H, W, D)
+    ds = torch.empty((H, W), dtype=torch.float32, device=dev)
+    lse = torch.empty_like(ds)
+    st.stereo_softargmin_fwd(h, _T(L, dev), _T(R, dev), 0, D, 5, tau, ds, lse)
+    torch.cuda.synchronize()
+    ds, lse = ds.cpu().numpy(), lse.cpu().numpy()
+    h.close()
+    assert np.array_equal(np.isnan(ds), ~hv)
+    err = np.abs(ds[hv] - ds_ref[hv])
+    print(f"tau {tau}: max |d_soft - oracle| {err.max():.2e} px")
+    assert err.max() <= 1e-4 + 4e-6 / tau * D
+    # the log-sum-exp is about max(rho) / tau: an FP32 rho error of ~1e-7
+    # moves it by ~1e-7 / tau
+    lerr = np.abs(lse[hv] - lse_ref[hv]) - 1e-5 * np.maximum(1.0, np.abs(lse_ref[hv]))
+    assert np.max(lerr) <= 2e-7 / tau
+    if tau <= 0.001:
+        m = oracle.match(np.clip(np.rint(L), 0, 255).astype(np.uint8), np.clip(np.rint(R), 0, 255).astype(np.uint8),
+                         0, D, 5)
+        clear = hv & (m["gapL"] > 20 * tau) & (m["dL"] != oracle.INVALID)
+        assert clear.sum() > 100
+        assert np.max(np.abs(ds[clear] - m["dL"][clear])) <= 0.01
+
+
+def test_backward_small_temperature(dev):
+    """tau = 0.01: the backward pass uses the log-sum-exp of the shifted
+    forward; image gradients against the oracle's."""
+    H, W, D, r, tau = 48, 200, 100, 5, 0.01
+    L, R, gt = _crop_pair(synth.seed_for(4, 1), 30, 100, H, W)
+    rng = np.random.default_rng(12)
+    ds_ref, lse_ref, hv = oracle.softargmin_fwd(L, R, 0, D, r, tau)
+    g = np.where(hv, rng.normal(0, 1, (H, W)), 0.0)
+    gL_ref, gR_ref = oracle.softargmin_bwd(L, R, 0, D, r, tau, g)
+    h = _handle(H, W, D)
+    tL, tR = _T(L, dev), _T(R, dev)
+    ds = torch.empty((H, W), dtype=torch.float32, device=dev)
+    lse = torch.empty_like(ds)
+    st.stereo_softargmin_fwd(h, tL, tR, 0, D, r, tau, ds, lse)
+    gL, gR = torch.empty_like(ds), torch.empty_like(ds)
+    st.stereo_softargmin_bwd(h, tL, tR, 0, D, r, tau, ds, lse, _T(g, dev), gL, gR)
+    torch.cuda.synchronize()
+    h.close()
+    for got, ref in ((gL.cpu().numpy(), gL_ref), (gR.cpu().numpy(), gR_ref)):
+        rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        print(f"tau {tau}: grad rel L2 {rel:.2e}")
+        assert rel <= GRAD_RTOL
+
+
 def test_forward_two_chunks_matches_oracle(dev):
     """num_disp > 128: the forward reads the FP32 volume (two disparity
     chunks) instead of summing inside the cost kernel."""
