@@ -20,6 +20,7 @@
 #pragma once
 #include <algorithm>
 #include "common.cuh"
+#include "match.cuh"           // FinStats: the preparation kernel's byte images and statistics
 
 constexpr int RB_T = 32;            // output tile edge
 constexpr int RB_THREADS = 256;
@@ -244,7 +245,120 @@ struct RefineArgs {
     uint32_t* op;                         // packed o
     float* dprev; float* dt; float* b;
     int16_t* cnt;
+    // without a stored volume (FULL sampling): the preparation kernel's
+    // byte images and exact window statistics of the same pair, from which
+    // Eq. 4 recomputes its candidates' costs (fs.L8 == nullptr: the direct
+    // window sums instead)
+    FinStats fs = FinStats{};
 };
+
+// Costs c = 1 - rho of the n <= 11 consecutive candidates hi - n + 1 .. hi of
+// interior left pixel (x, y), in the integer cost kernel's FP32 arithmetic
+// (the values an FP32 volume would hold): per window row, the left window's
+// shifted bytes against the right ones, four taps per dp4a, candidate hi - b
+// at byte offset b of the row's right span.  cb[b] is the cost of candidate
+// hi - b (b < n).  The byte images have margins around every row, so no
+// read leaves them.
+template <int R>
+__device__ __forceinline__ void costs_i8_run(const FinStats& fs, int W, int x, int y, int hi, int n, float cb[11]) {
+    constexpr int NW = (2 * R + 1 + 3) / 4;               // left words of a window row
+    constexpr int NSPAN = (10 + 2 * R + 1 + 3) / 4 + 1;  // right words covering every candidate's window
+    int s[11];
+#pragma unroll
+    for (int b = 0; b < 11; ++b) s[b] = 0;
+#pragma unroll 1
+    for (int dy = -R; dy <= R; ++dy) {
+        const int8_t* lp = fs.L8 + (size_t)(y + dy) * fs.l8stride + fs.l8col0 + x - R;
+        const int8_t* rp = fs.R8 + (size_t)(y + dy) * fs.r8stride + fs.r8col0 + x - hi - R;
+        if (!ST_CHECK(fs.l8col0 + x - R >= 0 && fs.l8col0 + x - R + 4 * (NW + 1) <= fs.l8stride &&
+                      fs.r8col0 + x - hi - R >= 0 && fs.r8col0 + x - hi - R + 4 * (NSPAN + 1) <= fs.r8stride, 12))
+            continue;
+        const int lsh = (int)((uintptr_t)lp & 3) * 8, rsh = (int)((uintptr_t)rp & 3) * 8;
+        const uint32_t* lw = reinterpret_cast<const uint32_t*>((uintptr_t)lp & ~(uintptr_t)3);
+        const uint32_t* rw = reinterpret_cast<const uint32_t*>((uintptr_t)rp & ~(uintptr_t)3);
+        uint32_t la[NW + 1], ra[NSPAN + 1];
+#pragma unroll
+        for (int i = 0; i <= NW; ++i) la[i] = __ldg(lw + i);
+#pragma unroll
+        for (int i = 0; i <= NSPAN; ++i) ra[i] = __ldg(rw + i);
+        uint32_t l[NW], r[NSPAN];
+#pragma unroll
+        for (int i = 0; i < NW; ++i) l[i] = __funnelshift_r(la[i], la[i + 1], lsh);
+        constexpr int REM = (2 * R + 1) % 4;
+        if (REM) l[NW - 1] &= (1u << (8 * REM)) - 1u;        // taps past the window drop out
+#pragma unroll
+        for (int i = 0; i < NSPAN; ++i) r[i] = __funnelshift_r(ra[i], ra[i + 1], rsh);
+#pragma unroll
+        for (int b = 0; b < 11; ++b) {
+            if (b < n) {
+#pragma unroll
+                for (int i = 0; i < NW; ++i) {
+                    const int q = (b >> 2) + i;
+                    const uint32_t rv = (b & 3) ? __funnelshift_r(r[q], r[q + 1], (b & 3) * 8) : r[q];
+                    s[b] = __dp4a((int)l[i], (int)rv, s[b]);
+                }
+            }
+        }
+    }
+    const float2 sl = fs.lstats[(size_t)y * W + x];
+    constexpr float Nf = (float)((2 * R + 1) * (2 * R + 1));
+    const float t1base = Nf * I8_BIAS;
+    const float4* up = fs.ustats + (size_t)y * fs.ustride + fs.ucol0 + x - hi;
+#pragma unroll
+    for (int b = 0; b < 11; ++b) {
+        cb[b] = __int_as_float(0x7fc00000);
+        if (b < n) {
+            const float4 us = up[b];
+            const float t1 = fmaf(sl.x, us.x, t1base);
+            const float num = fmaf(-sl.x, us.y, fmaf(Nf, __int_as_float(s[b] + I8_BIAS_BITS), -t1));
+            const float av = num * sl.y;
+            cb[b] = us.w != 0.f ? fmaf(-av, us.z, 1.f) : __int_as_float(0x7fc00000);
+        }
+    }
+}
+
+// Eq. (4) of interior pixel (x, y) from recomputed candidate costs (see
+// costs_i8_run); candidates scanned from the highest, so an exact tie in f
+// and distance keeps the lower one.  1/rho is the correctly rounded
+// reciprocal, as in the other recomputing path.
+template <int R>
+__device__ __forceinline__ int oupdate_i8(const FinStats& fs, int W, int x, int y, int lo, int hi, float d,
+                                          float eta, int ov) {
+    const int n = hi - lo + 1;
+    float cb[11];
+    costs_i8_run<R>(fs, W, x, y, hi, n, cb);
+    int best = ST_INVALID;
+    float bf = 0.f, bdist = 0.f;
+#pragma unroll
+    for (int b = 0; b < 11; ++b) {
+        const float rho = 1.f - cb[b];
+        if (b < n && rho > 0.f) {
+            const int cand = hi - b;
+            const float diff = (float)cand - d;
+            const float f = __frcp_rn(rho) + eta * diff * diff;
+            const float dist = fabsf(diff);
+            if (best == ST_INVALID || f < bf || (f == bf && dist <= bdist)) {
+                best = cand;
+                bf = f;
+                bdist = dist;
+            }
+        }
+    }
+    return best != ST_INVALID ? best : ov;
+}
+
+__device__ __forceinline__ int oupdate_i8_r(const FinStats& fs, int r, int W, int x, int y, int lo, int hi, float d,
+                                            float eta, int ov) {
+    switch (r) {
+        case 1: return oupdate_i8<1>(fs, W, x, y, lo, hi, d, eta, ov);
+        case 2: return oupdate_i8<2>(fs, W, x, y, lo, hi, d, eta, ov);
+        case 3: return oupdate_i8<3>(fs, W, x, y, lo, hi, d, eta, ov);
+        case 4: return oupdate_i8<4>(fs, W, x, y, lo, hi, d, eta, ov);
+        case 5: return oupdate_i8<5>(fs, W, x, y, lo, hi, d, eta, ov);
+        case 6: return oupdate_i8<6>(fs, W, x, y, lo, hi, d, eta, ov);
+        default: return oupdate_i8<7>(fs, W, x, y, lo, hi, d, eta, ov);
+    }
+}
 
 // Eqs. (1)-(2).  FIRST: o comes from the int16 map o_in (d_prev = o); the
 // kernel also writes the packed map, the counts and the valid mask.  The
@@ -366,6 +480,25 @@ __device__ __forceinline__ void refine_eq34_tile(const RefineArgs& a, float* __r
     // next round's loads are issued before a round is evaluated.  1/ZNCC is
     // the hardware reciprocal (within 1 ulp).
     const bool fast = a.cdt != CDT_NONE && a.search <= 5;
+    if (!fast && a.cdt == CDT_NONE && a.fs.L8 && a.search <= 5) {
+        // no volume: the candidates' costs recomputed from the byte images
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int t = threadIdx.x + q * RB_THREADS;
+            const int gx = x0 + t % RB_T, gy = y0 + t / RB_T;
+            if (gx >= a.W || gy >= a.H || !pkv[q]) continue;
+            const size_t gi = (size_t)gy * a.W + gx;
+            const int ov = unpack_o(pkv[q], a.d_min);
+            int on = ov;
+            const int lo = max((int)ceilf(dv[q] - (float)a.search), a.d_min);
+            const int hi = min((int)floorf(dv[q] + (float)a.search), a.d_min + a.D - 1);
+            const bool interior = gx >= a.r && gx < a.W - a.r && gy >= a.r && gy < a.H - a.r;
+            if (lo <= hi && interior) on = oupdate_i8_r(a.fs, a.r, a.W, gx, gy, lo, hi, dv[q], a.eta, ov);
+            a.op[gi] = pack_o(on, a.d_min);
+            if (o_out) o_out[gi] = (int16_t)on;
+        }
+        return;
+    }
     if (!fast) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {

@@ -562,10 +562,13 @@ void launch_refine_tiled(const stereo_params& p, const RefineArgs& a, const int1
     }
 }
 
+// fs (optional): the preparation kernel's byte images and statistics of
+// this pair (FULL sampling), from which Eq. 4 recomputes its candidates when
+// there is no volume.
 void run_refine(const stereo_params& p, const int16_t* o_in, const void* cost, int cdt,
                 const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, int D, int r,
                 int sampling, const PairWs& w, float* d_out, int16_t* o_out, uint8_t* valid,
-                cudaStream_t s) {
+                cudaStream_t s, const FinStats* fs = nullptr) {
     const int n = W * H;
     const int rs = p.smooth_radius;
     const bool tiled = rs <= RB_MAX_RS;
@@ -580,6 +583,7 @@ void run_refine(const stereo_params& p, const int16_t* o_in, const void* cost, i
     if (tiled) {
         RefineArgs a{W, H, rs, d_min, D, p.alpha, p.eta, p.refine_search, cost, cdt, gl, gr, r, sampling,
                      w.op, w.dprev, w.dt, w.b, w.cnt};
+        if (fs && cdt == CDT_NONE && sampling == STEREO_SAMPLE_FULL) a.fs = *fs;
         if (rb_spad(rs) == 16) launch_refine_tiled<16>(p, a, o_in, d_out, o_out, valid, s);
         else launch_refine_tiled<32>(p, a, o_in, d_out, o_out, valid, s);
         return;
@@ -679,8 +683,12 @@ static void enqueue_match(stereo_handle* h, const stereo_pair* pr, int slot, cud
     run_postprocess(h->p, w.lr, W, H, w, post, s);
     if (timed) mark(h, 5, s);
     float* dfin = pr->disp_final ? pr->disp_final : w.dfin;
+    PrepOut pl, prr;
+    prep_layouts(W, d_min, D, cost_k(D, h->p.sampling), w, pl, prr, true);
+    const FinStats fs{w.lstats, w.ustats, prr.ustride, prr.ucol0, reinterpret_cast<const int8_t*>(pl.img), pl.stride,
+                      pl.col0, reinterpret_cast<const int8_t*>(prr.img), prr.stride, prr.col0};
     run_refine(h->p, post, cost, cdt, gl, gr, W, H, d_min, D, r, h->p.sampling, w, dfin, nullptr,
-               pr->valid, s);
+               pr->valid, s, h->p.sampling == STEREO_SAMPLE_FULL ? &fs : nullptr);
     if (timed) mark(h, 6, s);
 }
 
@@ -1292,9 +1300,13 @@ static stereo_status build_batch_tables(stereo_handle* h, const stereo_pair* pai
             const int i = ids[j];
             const stereo_pair* pr = &pairs[i];
             const Geo& q = G[i];
-            const RefineArgs a{q.W, q.H, h->p.smooth_radius, q.d_min, q.D, h->p.alpha, h->p.eta, h->p.refine_search,
-                               cdt != CDT_NONE ? q.w.cost : nullptr, cdt, q.gl, q.gr, q.r, STEREO_SAMPLE_FULL,
-                               q.w.op, q.w.dprev, q.w.dt, q.w.b, q.w.cnt};
+            RefineArgs a{q.W, q.H, h->p.smooth_radius, q.d_min, q.D, h->p.alpha, h->p.eta, h->p.refine_search,
+                         cdt != CDT_NONE ? q.w.cost : nullptr, cdt, q.gl, q.gr, q.r, STEREO_SAMPLE_FULL,
+                         q.w.op, q.w.dprev, q.w.dt, q.w.b, q.w.cnt};
+            if (cdt == CDT_NONE)
+                a.fs = FinStats{q.w.lstats, q.w.ustats, q.pr.ustride, q.pr.ucol0,
+                                reinterpret_cast<const int8_t*>(q.pl.img), q.pl.stride, q.pl.col0,
+                                reinterpret_cast<const int8_t*>(q.pr.img), q.pr.stride, q.pr.col0};
             reinterpret_cast<RefJob*>(host.data() + orf)[j] =
                 RefJob{a, pr->disp_post ? pr->disp_post : q.w.post, pr->valid,
                        pr->disp_final ? pr->disp_final : q.w.dfin, nullptr};
@@ -1467,9 +1479,13 @@ static void enqueue_batched(stereo_handle* h, const stereo_pair* pairs, int n, c
         const stereo_pair* pr = &pairs[i];
         const Pair& q = P[i];
         void* cost = cdt != CDT_NONE ? q.w.cost : nullptr;
+        PrepOut pl, prr;
+        prep_layouts(q.W, q.d_min, q.D, h->pair_klayout[i], q.w, pl, prr, true);
+        const FinStats fs{q.w.lstats, q.w.ustats, prr.ustride, prr.ucol0, reinterpret_cast<const int8_t*>(pl.img),
+                          pl.stride, pl.col0, reinterpret_cast<const int8_t*>(prr.img), prr.stride, prr.col0};
         run_refine(h->p, pr->disp_post ? pr->disp_post : q.w.post, cost, cdt, q.gl, q.gr, q.W, q.H, q.d_min,
                    q.D, q.r, h->p.sampling, q.w, pr->disp_final ? pr->disp_final : q.w.dfin, nullptr, pr->valid,
-                   st);
+                   st, &fs);
     };
     const bool batched_stages = h->batch_stages == 1 && B.ok;
     // per-pair preparation: gray conversion (RGB or pitched input),
