@@ -314,24 +314,6 @@ def _timed_loop(torch, stream, steps, step, flush):
     return [a.elapsed_time(b) for a, b in ev]
 
 
-def _e2e_loop(torch, stream, steps, warmup, step, flush):
-    for _ in range(max(1, warmup)):
-        step()
-    torch.cuda.synchronize()
-    out = []
-    for i in range(steps):
-        flush.fill_(float(i))
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        step()
-        b.record(stream)
-        b.synchronize()
-        out.append(a.elapsed_time(b))
-    return out
-
-
 def _max_over_ranks(torch, dev, x, world):
     t = torch.tensor([x], dtype=torch.float64, device=dev)
     if world > 1:
@@ -638,16 +620,65 @@ def run_batched(args, wl, rank, world, dev, pairs):
     value = world * args.steps * P / t_max / 1e9
     stage_ms = _stage_pass(st, h, min(args.steps, 5), flush, step, st.STAGE_NAMES)
 
-    def e2e_step():
-        for b, (hL, hR, _) in zip(batch, host):
-            b["left"].copy_(hL, non_blocking=True)
-            b["right"].copy_(hR, non_blocking=True)
-        st.stereo_match_batched(h, batch, use_graph=True, stream=stream)
-        for b, (_, _, ho) in zip(batch, host):
-            ho.copy_(b["disp_final"], non_blocking=True)
+    # end to end, as a stream of batches: the next batch's images go up from
+    # pinned host memory (copy stream) into a staging set while the current
+    # batch is matched, and the previous batch's refined maps come down from
+    # a staging set (second copy stream); each step moves its inputs from
+    # staging into the pairs' buffers and its outputs out of them with
+    # device-to-device copies (the pairs' buffers, and so the batch's tables
+    # and graph, stay the same)
+    up, down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    stage_in = [[(torch.empty_like(b["left"]), torch.empty_like(b["right"])) for b in batch] for _ in range(2)]
+    stage_out = [[torch.empty_like(b["disp_final"]) for b in batch] for _ in range(2)]
+    ev_up = [torch.cuda.Event() for _ in range(2)]
+    ev_used = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+    ev_down = [torch.cuda.Event() for _ in range(2)]
+    for e in ev_used + ev_down:
+        e.record(stream)
 
-    e_ms = _e2e_loop(torch, stream, args.steps, args.warmup, e2e_step, flush)
-    te = _max_over_ranks(torch, dev, sum(e_ms) / 1e3, world)
+    def upload(sl):
+        up.wait_event(ev_used[sl])                       # step sl - 2 has taken its inputs
+        with torch.cuda.stream(up):
+            for (sL, sR), (hL, hR, _) in zip(stage_in[sl], host):
+                sL.copy_(hL, non_blocking=True)
+                sR.copy_(hR, non_blocking=True)
+        ev_up[sl].record(up)
+
+    def e2e_batches(n):
+        upload(0)
+        for i in range(n):
+            sl = i % 2
+            if i + 1 < n:
+                upload((i + 1) % 2)
+            stream.wait_event(ev_up[sl])
+            for b, (sL, sR) in zip(batch, stage_in[sl]):
+                b["left"].copy_(sL, non_blocking=True)
+                b["right"].copy_(sR, non_blocking=True)
+            ev_used[sl].record(stream)
+            st.stereo_match_batched(h, batch, use_graph=True, stream=stream)
+            stream.wait_event(ev_down[sl])               # read-back i - 2 has left this staging set
+            for b, so in zip(batch, stage_out[sl]):
+                so.copy_(b["disp_final"], non_blocking=True)
+            ev_out[sl].record(stream)
+            down.wait_event(ev_out[sl])
+            with torch.cuda.stream(down):
+                for so, (_, _, ho) in zip(stage_out[sl], host):
+                    ho.copy_(so, non_blocking=True)
+            ev_down[sl].record(down)
+        for e in ev_down:
+            stream.wait_event(e)
+
+    e2e_batches(max(2, args.warmup))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    e2e_batches(args.steps)
+    eb.record(stream)
+    torch.cuda.synchronize()
+    te = _max_over_ranks(torch, dev, ea.elapsed_time(eb) / 1e3, world)
     e2e_value = world * args.steps * P / te / 1e9
     h.close()
     if rank != 0:
@@ -677,7 +708,9 @@ def run_batched(args, wl, rank, world, dev, pairs):
         "roofline": roof,
         "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "ms_per_step": round(te * 1e3 / args.steps, 4),
                 "h2d_bytes_per_step": sum(2 * s["W"] * s["H"] * 3 for s in specs),
-                "d2h_bytes_per_step": sum(s["W"] * s["H"] * 4 for s in specs)},
+                "d2h_bytes_per_step": sum(s["W"] * s["H"] * 4 for s in specs),
+                "mode": "stream of batches: upload of the next and read-back of the previous batch overlap the "
+                        "current one (staging sets, device-to-device moves in the step); no L2 flush"},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "paper_context": PAPER_CONTEXT,
@@ -752,18 +785,46 @@ def run_soft_step(args, wl, rank, world, dev):
                          lambda: st.stereo_softargmin_fwd(h, tL.detach(), tR.detach(), 0, D, r, tau, ds, lse),
                          ("stats", "cost", "soft_fwd", "_a", "_b", "_c"))
 
-    def e2e_step():
-        L = torch.empty_like(tL)
-        R = torch.empty_like(tR)
-        G = torch.empty_like(tG)
-        L.copy_(hL, non_blocking=True)
-        R.copy_(hR, non_blocking=True)
-        G.copy_(hG, non_blocking=True)
-        train_step(L, R, G)
-        hloss.copy_(loss, non_blocking=True)
+    # end to end, as a stream of training batches: the next batch's images
+    # and ground truth go up from pinned host memory (copy stream) into the
+    # other of two device sets while the current batch trains; every step
+    # reads its loss back to pinned host memory
+    up = torch.cuda.Stream(dev)
+    sets = [(torch.empty_like(tL), torch.empty_like(tR), torch.empty_like(tG)) for _ in range(2)]
+    ev_up = [torch.cuda.Event() for _ in range(2)]
+    ev_used = [torch.cuda.Event() for _ in range(2)]
+    for e in ev_used:
+        e.record(stream)
 
-    e_ms = _e2e_loop(torch, stream, args.steps, args.warmup, e2e_step, flush)
-    te = _max_over_ranks(torch, dev, sum(e_ms) / 1e3, world)
+    def upload(sl):
+        up.wait_event(ev_used[sl])                       # step sl - 2 is done with this set
+        with torch.cuda.stream(up), torch.no_grad():
+            for d_, h_ in zip(sets[sl], (hL, hR, hG)):
+                d_.copy_(h_, non_blocking=True)
+        ev_up[sl].record(up)
+
+    def e2e_steps(n):
+        upload(0)
+        for i in range(n):
+            sl = i % 2
+            if i + 1 < n:
+                upload((i + 1) % 2)
+            stream.wait_event(ev_up[sl])
+            L, R, G = sets[sl]
+            train_step(L, R, G)
+            hloss.copy_(loss, non_blocking=True)
+            ev_used[sl].record(stream)
+
+    e2e_steps(max(2, args.warmup))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    e2e_steps(args.steps)
+    eb.record(stream)
+    torch.cuda.synchronize()
+    te = _max_over_ranks(torch, dev, ea.elapsed_time(eb) / 1e3, world)
     e2e_value = world * args.steps * P / te / 1e9
     h.close()
     if rank != 0:
@@ -783,7 +844,9 @@ def run_soft_step(args, wl, rank, world, dev):
                                "backward": {k: round(v, 4) for k, v in bwd_ms.items() if k != "unused"}},
         "roofline": roof,
         "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "ms_per_step": round(te * 1e3 / args.steps, 4),
-                "h2d_bytes_per_step": 3 * B * W * H * 4, "d2h_bytes_per_step": 4},
+                "h2d_bytes_per_step": 3 * B * W * H * 4, "d2h_bytes_per_step": 4,
+                "mode": "stream of batches: upload of the next batch overlaps the current training step "
+                        "(two device sets); the loss is read back every step; no L2 flush"},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "paper_context": PAPER_CONTEXT,
