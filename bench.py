@@ -126,6 +126,20 @@ def load_peaks():
         return dict(hbm_gbs=6400.0, sm_max_mhz=2032.0, source="fallback")
 
 
+def rank_pair_ids(wl, rank):
+    """The pairs rank `rank` matches (replicas share nothing): single-pair
+    workloads take generator pair `rank`, batched ones pairs rank * n ..
+    rank * n + n - 1 of their generator (or the picked pairs), the
+    soft-argmin step pairs rank * B .. rank * B + B - 1."""
+    if wl["kind"] == "batched":
+        if wl.get("pick"):
+            return [p + 64 * rank for p in wl["pick"]]
+        return list(range(rank * wl["n"], rank * wl["n"] + wl["n"]))
+    if wl["kind"] == "soft":
+        return list(range(rank * wl["B"], rank * wl["B"] + wl["B"]))
+    return [rank]
+
+
 def make_pair(wl, pair_index=0):
     if wl["disp"] is None:
         L, R, gt = synth.perlin_pair(wl["seed"] + pair_index, wl["W"], wl["H"])
@@ -144,16 +158,16 @@ def _same_pair(args):
     return L, R, gt, dict(W=wl["W"], H=wl["H"], D=wl["D"], r=wl["r"])
 
 
-def make_batch(n, first, same=None, pick=None):
-    """Pairs first..first+n-1 of the mixed batch (or the pairs `pick` of it,
-    or, with `same`, pairs of that single-pair workload's generator),
-    generated by a spawn pool (started before any CUDA call)."""
+def make_batch(ids, same=None):
+    """Pairs `ids` of the mixed batch's generator (or, with `same`, of that
+    single-pair workload's generator), generated by a spawn pool (started
+    before any CUDA call)."""
     import multiprocessing as mp
-    procs = max(1, min(n, os.cpu_count() or 1, 32))
+    procs = max(1, min(len(ids), os.cpu_count() or 1, 32))
     with mp.get_context("spawn").Pool(procs) as pool:
         if same:
-            return pool.map(_same_pair, [(same, i) for i in range(first, first + n)])
-        return pool.map(_batch_pair, list(pick) if pick else range(first, first + n))
+            return pool.map(_same_pair, [(same, i) for i in ids])
+        return pool.map(_batch_pair, ids)
 
 
 class ClockSampler:
@@ -315,6 +329,7 @@ def _timed_loop(torch, stream, steps, step, flush):
 
 
 def _max_over_ranks(torch, dev, x, world):
+    """The largest x over all ranks (the slowest rank's time)."""
     t = torch.tensor([x], dtype=torch.float64, device=dev)
     if world > 1:
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -361,7 +376,7 @@ def run_single(args, wl, rank, world, dev, extras=True):
     import paper_2007_12623_b300 as st
 
     W, H, D = wl["W"], wl["H"], wl["D"]
-    Lrgb, Rrgb, gt = make_pair(wl, rank)
+    Lrgb, Rrgb, gt = make_pair(wl, rank_pair_ids(wl, rank)[0])
     stream = torch.cuda.Stream(dev)          # non-default stream: graph capture + replay
     torch.cuda.set_stream(stream)
     tL = torch.from_numpy(Lrgb).to(dev)
@@ -732,7 +747,7 @@ def run_soft_step(args, wl, rank, world, dev):
     B, W, H, D, r, tau = wl["B"], wl["W"], wl["H"], wl["D"], wl["r"], wl["tau"]
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    data = [synth.tissue_pair(wl["seed"] + rank * B + b, W, H, *wl["disp"]) for b in range(B)]
+    data = [synth.tissue_pair(wl["seed"] + i, W, H, *wl["disp"]) for i in rank_pair_ids(wl, rank)]
     hL = torch.from_numpy(np.stack([_gray_f32(d[0]) for d in data])).pin_memory()
     hR = torch.from_numpy(np.stack([_gray_f32(d[1]) for d in data])).pin_memory()
     hG = torch.from_numpy(np.stack([d[2].astype(np.float32) for d in data])).pin_memory()
@@ -1024,10 +1039,9 @@ def main():
 
     subs = (world == 1 and args.workload == "tissue960" and not args.no_sub_workloads
             and "--workload" not in sys.argv)
-    pairs = (make_batch(wl["n"], rank * wl["n"], wl.get("same"), wl.get("pick")) if wl["kind"] == "batched"
-             else None)
+    pairs = make_batch(rank_pair_ids(wl, rank), wl.get("same")) if wl["kind"] == "batched" else None
     if subs:                                                        # before any CUDA call
-        batch_pairs = {name: make_batch(WORKLOADS[name]["n"], 0, WORKLOADS[name].get("same"))
+        batch_pairs = {name: make_batch(rank_pair_ids(WORKLOADS[name], 0), WORKLOADS[name].get("same"))
                        for name in SUB_WORKLOADS if WORKLOADS[name]["kind"] == "batched"}
     import torch
     dev = torch.device(f"cuda:{int(os.environ.get('LOCAL_RANK', 0))}")
