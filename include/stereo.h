@@ -251,7 +251,9 @@ stereo_status stereo_get_stage_times(stereo_handle* h, float* ms, int32_t n);
 unsigned long long stereo_launch_count(void);
 
 /* Process-wide tuning knobs.  "cost_rows": output rows per work unit of the
- * cost kernel (1..4096; 0 = automatic).  "graphs": 1 (default) replays
+ * cost kernel (1..4096; 0 = automatic).  "soft_box_rows": output rows per
+ * warp of the soft-argmin backward's window-sum kernel (1..4096; 0 =
+ * automatic).  "graphs": 1 (default) replays
  * stereo_match / stereo_match_batched as captured CUDA graphs on non-default
  * streams, 0 launches kernels one by one.  Returns STEREO_ERR_INVALID_ARG
  * for an unknown name or value. */

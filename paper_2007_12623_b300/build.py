@@ -32,9 +32,30 @@ def translation_units():
     return [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith(".cu")]
 
 
+def _deps(src: str, seen=None) -> set:
+    """The file and every header it includes with quotes, transitively
+    (csrc/ and include/)."""
+    seen = set() if seen is None else seen
+    if src in seen or not os.path.exists(src):
+        return seen
+    seen.add(src)
+    with open(src) as f:
+        for line in f:
+            t = line.strip()
+            if t.startswith("#include \""):
+                name = t.split('"')[1]
+                for d in (os.path.dirname(src), CSRC, os.path.join(ROOT, "include")):
+                    cand = os.path.normpath(os.path.join(d, name))
+                    if os.path.exists(cand):
+                        _deps(cand, seen)
+                        break
+    return seen
+
+
 def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
-    """Compiles every translation unit (in parallel) and links libstereo.so
-    (checked=True: libstereo_checked.so with -DSTEREO_CHECKED)."""
+    """Compiles the translation units (in parallel) whose object is older
+    than one of its sources, and links libstereo.so (checked=True:
+    libstereo_checked.so with -DSTEREO_CHECKED)."""
     lib = LIB_CHECKED if checked else LIB
     if not force and not needs_build(lib):
         return lib
@@ -48,8 +69,15 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
     if verbose:
         flags.append("-Xptxas=-v")
 
+    stamp = os.path.join(bdir, "flags.txt")
+    same_flags = os.path.exists(stamp) and open(stamp).read() == " ".join(flags)
+
     def compile_one(src):
         obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
+        if not force and same_flags and os.path.exists(obj) and not verbose:
+            t = os.path.getmtime(obj)
+            if all(os.path.getmtime(d) <= t for d in _deps(src)):
+                return obj
         r = subprocess.run([nvcc, *flags, "-c", "-o", obj, src], cwd=CSRC, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
@@ -60,6 +88,8 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
     tus = translation_units()
     with ThreadPoolExecutor(max_workers=min(8, len(tus))) as ex:
         objs = list(ex.map(compile_one, tus))
+    with open(stamp, "w") as f:
+        f.write(" ".join(flags))
     tmp = lib + f".{os.getpid()}.tmp"
     subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs], cwd=CSRC)
     os.replace(tmp, lib)

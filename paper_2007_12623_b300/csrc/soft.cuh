@@ -19,6 +19,7 @@
 // centred values sum to zero.  A window with zero variance has rho fixed at
 // 0 and contributes nothing.
 #pragma once
+#include <algorithm>
 #include "common.cuh"
 #include "cost.cuh"            // cp.async helpers
 
@@ -429,11 +430,22 @@ __global__ void __launch_bounds__(SOFT_BOX_THREADS, 7) k_soft_box_t1(const float
     cp_async_wait_all();
 }
 
-// Band height of k_soft_box_t1: short bands while the grid would otherwise
-// give fewer than ~24 warps per SM.
-inline int soft_box_rows(int W, int H, int nch, int sms) {
-    const long per_row = (long)((W + SOFT_RUN - 1) / SOFT_RUN) * nch;
-    return per_row * ((H + 15) / 16) >= 24L * sms ? 16 : 8;
+// Band height of k_soft_box_t1: with `slots` warps resident on the GPU the
+// grid takes ceil(warps / slots) waves of warps costing about ty + r row
+// times each (the 2r prologue rows cost about half a row); pick the height
+// in [8, 64] that minimises that estimate (a full last wave matters most:
+// on 960 x 540 x 128, ty = 32 fills one wave of 14 warps per SM, 113 us,
+// against 123 us for two waves at ty = 16).
+inline int soft_box_rows(int W, int H, int nch, int r, long slots) {
+    const long per_band = (long)((W + SOFT_RUN - 1) / SOFT_RUN) * nch;
+    int best = 16;
+    long best_t = -1;
+    for (int ty = 8; ty <= 64; ++ty) {
+        const long warps = per_band * ((H + ty - 1) / ty);
+        const long t = (warps + slots - 1) / std::max(1L, slots) * (ty + r);
+        if (best_t < 0 || t < best_t) { best_t = t; best = ty; }
+    }
+    return best;
 }
 
 // Final gradients: box sums over the (2r+1)^2 window of the six per-pixel

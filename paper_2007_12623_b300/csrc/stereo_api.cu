@@ -34,6 +34,7 @@ inline void counted(int n = 1) { g_launches.fetch_add((unsigned long long)n, std
 
 // Tuning knobs (0 = automatic), set through stereo_set_tuning.
 int g_cost_rows = 0;
+int g_soft_box_rows = 0;
 int g_use_graphs = 1;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -1089,6 +1090,11 @@ stereo_status stereo_set_tuning(const char* name, int32_t value) {
         g_cost_rows = value;
         return STEREO_OK;
     }
+    if (!strcmp(name, "soft_box_rows")) {
+        if (value < 0 || value > 4096) return STEREO_ERR_INVALID_ARG;
+        g_soft_box_rows = value;
+        return STEREO_OK;
+    }
     if (!strcmp(name, "graphs")) {
         if (value < 0 || value > 1) return STEREO_ERR_INVALID_ARG;
         g_use_graphs = value;
@@ -1572,6 +1578,25 @@ stereo_status stereo_match(stereo_handle* h, const stereo_pair* pr, void* stream
 }
 
 // ---- soft-argmin -----------------------------------------------------------
+// Warps of k_soft_box_t1<R> resident per SM (occupancy query, cached).
+static int soft_box_warps_per_sm(int r) {
+    static int cached[STEREO_MAX_WIN_RADIUS + 1] = {0};
+    if (r < 1 || r > STEREO_MAX_WIN_RADIUS) return 1;
+    if (cached[r] == 0) {
+        int per_sm = 0;
+        switch (r) {
+#define SBX_OCC(RV)                                                                                              \
+    case RV:                                                                                                      \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft_box_t1<RV>, SOFT_BOX_THREADS, soft_box_smem(RV)); \
+        break;
+            SBX_OCC(1) SBX_OCC(2) SBX_OCC(3) SBX_OCC(4) SBX_OCC(5) SBX_OCC(6) SBX_OCC(7)
+#undef SBX_OCC
+        }
+        cached[r] = std::max(1, per_sm) * (SOFT_BOX_THREADS / 32);
+    }
+    return cached[r];
+}
+
 static void launch_soft_box_t1(int r, const float* A, const float* L, const float* R, int W, int H, int nch,
                                int cs, int d_min, int ty, float* T1L, float* T1R, cudaStream_t s) {
     const long warps = (long)((W + SOFT_RUN - 1) / SOFT_RUN) * ((H + ty - 1) / ty) * nch;
@@ -1756,7 +1781,8 @@ stereo_status stereo_softargmin_bwd(stereo_handle* h, const float* left, const f
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int ty = soft_box_rows(W, H, nch, sms);
+    const int ty = g_soft_box_rows > 0 ? std::min(g_soft_box_rows, H)
+                                       : soft_box_rows(W, H, nch, r, (long)sms * soft_box_warps_per_sm(r));
     const bool fused = soft_fused(num_disp);
     for (int b = 0; b < batch; ++b) {
         const float* L = left + b * npix;
