@@ -252,7 +252,7 @@ __device__ __forceinline__ void finalize_run(const FinArgs& f, VBlock vb) {
 }
 
 template <int R, bool CB>
-__global__ void __launch_bounds__(128) k_finalize(FinArgs f) {
+__global__ void __launch_bounds__(128, 16) k_finalize(FinArgs f) {
     finalize_run<R, CB>(f, vblock());
 }
 

@@ -236,7 +236,7 @@ __device__ __forceinline__ void prep_tile(const PrepArgs& pa, VBlock vb) {
 }
 
 template <bool CB, int R>
-__global__ void __launch_bounds__(256) k_prep(PrepArgs pa) {
+__global__ void __launch_bounds__(256, 8) k_prep(PrepArgs pa) {
     prep_tile<CB, R>(pa, vblock());
 }
 
