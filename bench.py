@@ -667,14 +667,17 @@ def run_batched(args, wl, rank, world, dev, pairs):
             if i + 1 < n:
                 upload((i + 1) % 2)
             stream.wait_event(ev_up[sl])
+            # device-to-device moves as elementwise kernels (x * 1, exact)
+            # rather than DMA copies, which would queue behind the host
+            # transfers on the copy engines (4 pairs: 1.135 -> 1.063 ms)
             for b, (sL, sR) in zip(batch, stage_in[sl]):
-                b["left"].copy_(sL, non_blocking=True)
-                b["right"].copy_(sR, non_blocking=True)
+                torch.mul(sL, 1, out=b["left"])
+                torch.mul(sR, 1, out=b["right"])
             ev_used[sl].record(stream)
             st.stereo_match_batched(h, batch, use_graph=True, stream=stream)
             stream.wait_event(ev_down[sl])               # read-back i - 2 has left this staging set
             for b, so in zip(batch, stage_out[sl]):
-                so.copy_(b["disp_final"], non_blocking=True)
+                torch.mul(b["disp_final"], 1, out=so)
             ev_out[sl].record(stream)
             down.wait_event(ev_out[sl])
             with torch.cuda.stream(down):
