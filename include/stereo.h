@@ -64,7 +64,7 @@ typedef enum {
     STEREO_ERR_INVALID_ARG = 1,   /* NULL/misaligned pointer, bad size ...  */
     STEREO_ERR_CUDA = 2,          /* a CUDA runtime call failed             */
     STEREO_ERR_OOM = 3,           /* workspace allocation failed            */
-    STEREO_ERR_UNSUPPORTED = 4,   /* valid request this build cannot serve  */
+    STEREO_ERR_UNSUPPORTED = 4,   /* valid request the library cannot serve */
     STEREO_ERR_TIMEOUT = 5,       /* a bounded device wait gave up (unused) */
     STEREO_ERR_TOO_LARGE = 6      /* request exceeds the handle's capacity  */
 } stereo_status;
