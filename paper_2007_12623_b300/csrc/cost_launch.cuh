@@ -22,12 +22,15 @@ inline int cost_choose_rows(int units_x, int nz, int rows_total, int cap) {
 }
 
 template <int K> struct CostMinBlocks { static constexpr int value = K == 4 ? 8 : (K == 2 ? 12 : 16); };
+// The integer form at K = 2 fits 128 registers (16 one-warp CTAs per SM)
+// without spills; the float form at K = 2 keeps 12.
+template <int K, bool I8> struct CostMinBlocksI { static constexpr int value = I8 && K == 2 ? 16 : CostMinBlocks<K>::value; };
 
 // I8: the integer form (cost_i8.cuh; K even, FULL sampling, 8-bit images).
 template <int R, int K, int CDT, bool CB = false, bool I8 = false>
 void launch_cost_rkc(CostArgs a, int rows_override, cudaStream_t s) {
     typedef CostGeom<R> G;
-    constexpr int MINB = CostMinBlocks<K>::value;
+    constexpr int MINB = CostMinBlocksI<K, I8>::value;
     constexpr int BYTES = I8 ? CostI8Smem<R, K>::BYTES : CostSmem<R, K>::BYTES;
     const int nx = (a.W - 2 * R + G::TW - 1) / G::TW;
     const int nz = (a.dcount + 32 * K - 1) / (32 * K);
