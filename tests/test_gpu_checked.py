@@ -3,8 +3,9 @@
   * The checked build (libstereo_checked.so, in-kernel index checks that
     record a failure in a device error word and skip the access) runs the
     whole path, the stage entry points and the batched form on odd sizes,
-    small and large windows and disparity ranges: the error word stays 0
-    and every output equals the normal build's bit for bit.
+    small and large windows and disparity ranges, and the whole path at the
+    benchmark sizes: the error word stays 0 and every output equals the
+    normal build's bit for bit.
   * Its self-test launches one check that cannot pass (its store is
     skipped): the error word reports the site, and reading it clears it.
   * Allocation failures injected at every device allocation of
@@ -77,6 +78,22 @@ CASES = [((37, 23), 0, 5, 1, st.COST_F32, 2),        # odd sizes, tiny range and
 def test_checked_build_whole_path(dev, size, d_min, D, r, cdt, smooth):
     W, H = size
     Lrgb, Rrgb, gt = synth.tissue_pair(synth.seed_for(8, W), W, H, max(1.0, d_min + 1.0), d_min + 0.7 * D)
+    err0, ref = _whole_path(dev, Lrgb, Rrgb, d_min, D, r, cdt, smooth)
+    assert err0 == 0
+    with st.checked_library():
+        err, got = _whole_path(dev, Lrgb, Rrgb, d_min, D, r, cdt, smooth)
+    assert err == 0, hex(err)
+    for k in ref:
+        assert np.array_equal(np.nan_to_num(ref[k], nan=-7), np.nan_to_num(got[k], nan=-7)), k
+
+
+@pytest.mark.parametrize("size,d_min,D,r,cdt,smooth", [((960, 540), 0, 128, 5, st.COST_F32, 15),
+                                                        ((960, 540), 0, 192, 7, st.COST_F16, 15)])
+def test_checked_build_whole_path_full_size(dev, size, d_min, D, r, cdt, smooth):
+    """The benchmark sizes (960x540 at D = 128, FP32, and D = 192, 15x15,
+    FP16): no failed index check, the normal build's outputs bit for bit."""
+    W, H = size
+    Lrgb, Rrgb, gt = synth.tissue_pair(synth.seed_for(1), W, H, 10.0, 0.85 * D)
     err0, ref = _whole_path(dev, Lrgb, Rrgb, d_min, D, r, cdt, smooth)
     assert err0 == 0
     with st.checked_library():
