@@ -547,8 +547,11 @@ __device__ __forceinline__ void refine_eq34_tile(const RefineArgs& a, float* __r
         n = live ? hi - lo + 1 : 0;
         const int kb = (lo - a.d_min) & ~3;
         k0 = esz == 4 ? kb : (kb & ~7);
-        // last candidate index (-1: none); a chunk is fetched only when it
-        // starts at or before it (the first candidate is always in chunk 0)
+        // last candidate index (-1: none); a chunk is fetched only when the
+        // pixel has candidates and the chunk starts at or before the last one
+        // (the first candidate is always in chunk 0).  A pixel without
+        // candidates fetches nothing: its k0 may be negative (lo = 0 with
+        // d_min > 0) and its row may lie below the image.
         const int last = n > 0 ? lo - a.d_min + n - 1 : -1;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -557,7 +560,8 @@ __device__ __forceinline__ void refine_eq34_tile(const RefineArgs& a, float* __r
             const int plast = __shfl_sync(0xffffffffu, last, p);
             const int kc = pk0 + ch * (16 / esz);                     // first cost index of the chunk
             ld[i] = make_uint4(0u, 0u, 0u, 0u);
-            if (kc <= plast && ST_CHECK(kc >= 0 && (kc + 16 / esz) <= cs && x0 + p < a.W && gy < a.H, 8)) {
+            if (plast >= 0 && kc <= plast &&
+                ST_CHECK(kc >= 0 && (kc + 16 / esz) <= cs && x0 + p < a.W && gy < a.H, 8)) {
                 const size_t gp = (size_t)gy * a.W + x0 + p;
                 ld[i] = __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(a.cost) +
                                                              (gp * (size_t)cs + kc) * esz));

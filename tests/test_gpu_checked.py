@@ -103,6 +103,38 @@ def test_checked_build_whole_path_full_size(dev, size, d_min, D, r, cdt, smooth)
         assert np.array_equal(np.nan_to_num(ref[k], nan=-7), np.nan_to_num(got[k], nan=-7)), k
 
 
+@pytest.mark.parametrize("size,d_min,D,r,cdt,smooth,sampling", [
+    ((101, 45), 6, 80, 5, st.COST_F32, 5, st.SAMPLE_FULL),        # first disparity > 0, FP32 volume
+    ((505, 29), 5, 225, 7, st.COST_F32, 5, st.SAMPLE_CHESSBOARD),  # short image: tile rows below it
+    ((662, 224), 6, 246, 7, st.COST_F32, 5, st.SAMPLE_FULL),
+    ((130, 50), 3, 70, 3, st.COST_F16, 15, st.SAMPLE_FULL)])
+def test_checked_build_positive_first_disparity(dev, size, d_min, D, r, cdt, smooth, sampling):
+    """A positive first disparity with a stored volume: the o-update's pixels
+    without candidates (invalid ones, and the tile rows below a short image)
+    fetch no candidate run (they once read from before their cost slice or
+    past the volume's end)."""
+    W, H = size
+    Lrgb, Rrgb, gt = synth.tissue_pair(synth.seed_for(8, 1000 + W), W, H, d_min + 1.0, d_min + 0.8 * D)
+
+    def run():
+        h = st.stereo_create(st.stereo_default_params(max_width=W, max_height=H, d_min=d_min, num_disp=D,
+                                                      win_radius=r, cost_dtype=cdt, smooth_radius=smooth,
+                                                      sampling=sampling))
+        o = _outs(dev, H, W)
+        st.stereo_match(h, T(Lrgb, dev), T(Rrgb, dev), **o)
+        torch.cuda.synchronize()
+        err = st.stereo_get_device_error(h)
+        h.close()
+        return err, {k: v.cpu().numpy() for k, v in o.items()}
+
+    err0, ref = run()
+    with st.checked_library():
+        err, got = run()
+    assert err0 == 0 and err == 0, hex(err)
+    for k in ref:
+        assert np.array_equal(np.nan_to_num(ref[k], nan=-7), np.nan_to_num(got[k], nan=-7)), k
+
+
 def test_checked_build_batched(dev):
     """A batch of odd-size pairs in both stage modes: no failed check, the
     normal build's outputs."""
