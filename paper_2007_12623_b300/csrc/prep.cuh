@@ -334,6 +334,11 @@ __global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ imgL
             for (int k = 0; k <= 2 * r; ++k) { s += rs[ly + k][lx]; ss += rss[ly + k][lx]; }
             const float q = __fmul_rn(Nf, ss), p = __fmul_rn(s, s);   // not contracted into the fmas
             B = __fsub_rn(q, p) + (fmaf(Nf, ss, -q) - fmaf(s, s, -p));
+            // a flat window leaves only the rounding of the FP32 sums s and
+            // ss (up to about N ulps of q, possibly a denormal whose
+            // reciprocal square root would be infinite): at or below
+            // N 2^-22 q the variance is zero as far as FP32 can tell
+            if (!(B > q * (Nf * 2.384185791015625e-7f))) B = 0.f;
         }
         float is = 0.f;
         if (B > 0.f) {

@@ -179,6 +179,48 @@ def test_backward_matches_oracle_gradient(dev, r, D, H, W, d_min):
     h.close()
 
 
+@pytest.mark.parametrize("r,tau", [(1, 0.1), (1, 0.01), (5, 0.1), (5, 0.01), (1, 0.001), (7, 0.001)])
+def test_flat_patches_of_float_images(dev, r, tau):
+    """Float images with non-integer values (the gray crop / 255) and
+    constant patches in the left one.  A patch's windows have zero variance:
+    the oracle's sums are exact and give 0; the FP32 sums leave a rounding
+    residue (once a denormal, whose reciprocal square root made the forward
+    infinite and the gradients NaN), which the preparation kernel now reads
+    as zero variance.  Forward and gradients finite everywhere, and at the
+    pixels whose left window lies inside a patch (rho = 0 for every
+    candidate) d_soft equal to the oracle's.  Elsewhere such low-texture
+    non-integer windows carry the FP32 limit of B = N SS - S^2 (relative
+    error about N 2^-24 SS / var), so the element-wise bars of the
+    integer-valued crops above do not apply."""
+    H, W, D = 48, 96, 16
+    L, R, gt = _crop_pair(synth.seed_for(4, 2), 20, 80, H, W)
+    L = (L / 255.0).astype(np.float32).astype(np.float64)
+    R = (R / 255.0).astype(np.float32).astype(np.float64)
+    L[12:30, 30:60] = L[12, 30]                       # a flat patch
+    L[36:44, 70:90] = np.float32(1.0 / 3.0)          # and one at a non-representable third
+    ds_ref, lse_ref, hv = oracle.softargmin_fwd(L, R, 0, D, r, tau)
+    inside = np.zeros((H, W), bool)
+    inside[12 + r:30 - r, 30 + r:60 - r] = True
+    inside[36 + r:44 - r, 70 + r:90 - r] = True
+    g = np.where(hv, np.random.default_rng(3).normal(0, 1, (H, W)), 0.0)
+    h = _handle(H, W, D)
+    tL, tR = _T(L, dev), _T(R, dev)
+    ds = torch.empty((H, W), dtype=torch.float32, device=dev)
+    lse = torch.empty_like(ds)
+    st.stereo_softargmin_fwd(h, tL, tR, 0, D, r, tau, ds, lse)
+    gL, gR = torch.empty_like(ds), torch.empty_like(ds)
+    st.stereo_softargmin_bwd(h, tL, tR, 0, D, r, tau, ds, lse, _T(g, dev), gL, gR)
+    torch.cuda.synchronize()
+    dsn, lsen = ds.cpu().numpy(), lse.cpu().numpy()
+    assert np.array_equal(np.isnan(dsn), ~hv)
+    assert np.all(np.isfinite(lsen[hv]))
+    flat = inside & hv
+    if flat.any():
+        assert np.max(np.abs(dsn[flat] - ds_ref[flat])) <= 1e-4
+    assert np.all(np.isfinite(gL.cpu().numpy())) and np.all(np.isfinite(gR.cpu().numpy()))
+    h.close()
+
+
 def test_l1_loss_many_partial_sums(dev):
     """Three 960x540 maps (1.55 M values, the largest number of partial sums)
     with a tenth of the pixels without a valid candidate: loss and gradient
