@@ -135,6 +135,42 @@ def test_checked_build_positive_first_disparity(dev, size, d_min, D, r, cdt, smo
         assert np.array_equal(np.nan_to_num(ref[k], nan=-7), np.nan_to_num(got[k], nan=-7)), k
 
 
+def test_maximum_size_pair(dev):
+    """The largest range and window at 3840x2160 (D = 256, 15x15, FP16
+    volume, 4.2 GB): no failed index check in the checked build, its outputs
+    equal to the normal build's, and the winners of a 12-row strip equal to
+    the oracle's (near-ties exempt)."""
+    from parity import NEAR_TIE, int_map_mismatch, oracle_match_rows
+    import oracle
+    W, H, D, r = 3840, 2160, 256, 7
+    Lrgb, Rrgb, gt = synth.tissue_pair(synth.seed_for(12, W), W, H, 10.0, 0.85 * D)
+
+    def run():
+        h = st.stereo_create(st.stereo_default_params(max_width=W, max_height=H, num_disp=D, win_radius=r,
+                                                      cost_dtype=st.COST_F16))
+        o = dict(disp_wta=torch.empty((H, W), dtype=torch.int16, device=dev),
+                 disp_post=torch.empty((H, W), dtype=torch.int16, device=dev),
+                 disp_final=torch.empty((H, W), dtype=torch.float32, device=dev))
+        s = torch.cuda.Stream()
+        st.stereo_match(h, T(Lrgb, dev), T(Rrgb, dev), **o, stream=s)
+        s.synchronize()
+        err = st.stereo_get_device_error(h)
+        h.close()
+        return err, {k: v.cpu().numpy() for k, v in o.items()}
+
+    with st.checked_library():
+        err, got = run()
+    assert err == 0, hex(err)
+    err0, ref = run()
+    assert err0 == 0
+    for k in ref:
+        assert np.array_equal(np.nan_to_num(ref[k], nan=-7), np.nan_to_num(got[k], nan=-7)), k
+    y0, y1 = 1400, 1412
+    m = oracle_match_rows(oracle.gray(Lrgb), oracle.gray(Rrgb), 0, D, r, 0, y0, y1)
+    bad = int_map_mismatch(ref["disp_wta"][y0:y1], m["dL"], m["gapL"] < NEAR_TIE)
+    assert len(bad) == 0
+
+
 def test_checked_build_batched(dev):
     """A batch of odd-size pairs in both stage modes: no failed check, the
     normal build's outputs."""
