@@ -456,7 +456,7 @@ inline int soft_box_rows(int W, int H, int nch, int r, long slots) {
 constexpr int SF_T = 32;
 inline size_t soft_final_smem(int r) {
     const size_t span = SF_T + 2 * r;
-    return (3 * span * span + 3 * span * SF_T) * 4;
+    return 3 * span * span * 4;
 }
 
 template <int R>
@@ -475,9 +475,11 @@ __global__ void __launch_bounds__(256) k_soft_final(const float* __restrict__ T1
     const bool left = blockIdx.z == 0;
     const float* X1 = left ? P1 : Q1;
     const float* X2 = left ? P2 : Q2;
-    float* f = soft_sm;                     // [3][span][span] inputs
-    float* rs = soft_sm + 3 * span * span;  // [3][span][SF_T] row sums
-    float* box = soft_sm;                   // [3][SF_T][SF_T + 1] window sums (reuses f)
+    // one [3][span][span] buffer for the inputs, then (in place) the row sums
+    // in columns 0 .. SF_T - 1, then the window sums in rows 0 .. SF_T - 1:
+    // each pass computes its outputs into registers, waits for every thread,
+    // then stores them over its inputs (21 KB at r = 5: 8 blocks per SM)
+    float* f = soft_sm;
     const int x0 = blockIdx.x * SF_T - r, y0 = blockIdx.y * SF_T - r;
     // inputs, 4 pixels' loads in flight per thread
     for (int i0 = threadIdx.x; i0 < span * span; i0 += 4 * 256) {
@@ -511,38 +513,73 @@ __global__ void __launch_bounds__(256) k_soft_final(const float* __restrict__ T1
         }
     }
     __syncthreads();
-    // row sums: thread = (map, staged row, segment of 8 outputs), sliding
-    for (int job = threadIdx.x; job < 3 * span * (SF_T / 8); job += 256) {
-        const int m = job / (span * (SF_T / 8)), rem = job % (span * (SF_T / 8));
-        const int ly = rem / (SF_T / 8), xs = (rem % (SF_T / 8)) * 8;
-        const float* row = f + m * span * span + ly * span + xs;
-        float sacc = 0.f;
-        for (int j = 0; j <= 2 * r; ++j) sacc += row[j];
-        float* o = rs + m * span * SF_T + ly * SF_T + xs;
-        o[0] = sacc;
+    // row sums: job = (map, staged row, segment of 8 outputs), sliding
+    {
+        constexpr int NJ = 3 * span * (SF_T / 8), PER = (NJ + 255) / 256;
+        float out[PER][8];
 #pragma unroll
-        for (int j = 1; j < 8; ++j) {
-            sacc += row[j + 2 * r] - row[j - 1];
-            o[j] = sacc;
+        for (int q = 0; q < PER; ++q) {
+            const int job = threadIdx.x + q * 256;
+            if (job >= NJ) break;
+            const int m = job / (span * (SF_T / 8)), rem = job % (span * (SF_T / 8));
+            const int ly = rem / (SF_T / 8), xs = (rem % (SF_T / 8)) * 8;
+            const float* row = f + m * span * span + ly * span + xs;
+            float sacc = 0.f;
+            for (int j = 0; j <= 2 * r; ++j) sacc += row[j];
+            out[q][0] = sacc;
+#pragma unroll
+            for (int j = 1; j < 8; ++j) {
+                sacc += row[j + 2 * r] - row[j - 1];
+                out[q][j] = sacc;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int job = threadIdx.x + q * 256;
+            if (job >= NJ) break;
+            const int m = job / (span * (SF_T / 8)), rem = job % (span * (SF_T / 8));
+            const int ly = rem / (SF_T / 8), xs = (rem % (SF_T / 8)) * 8;
+            float* o = f + m * span * span + ly * span + xs;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) o[j] = out[q][j];
         }
     }
     __syncthreads();
-    // column sums: thread = (map, column, segment of 4 outputs), sliding
-    for (int job = threadIdx.x; job < 3 * SF_T * (SF_T / 4); job += 256) {
-        const int m = job / (SF_T * (SF_T / 4)), rem = job % (SF_T * (SF_T / 4));
-        const int lx = rem % SF_T, ys = (rem / SF_T) * 4;
-        const float* col = rs + m * span * SF_T + ys * SF_T + lx;
-        float sacc = 0.f;
-        for (int j = 0; j <= 2 * r; ++j) sacc += col[j * SF_T];
-        float* o = box + m * SF_T * (SF_T + 1) + ys * (SF_T + 1) + lx;
-        o[0] = sacc;
+    // column sums: job = (map, column, segment of 4 outputs), sliding
+    {
+        constexpr int NJ = 3 * SF_T * (SF_T / 4), PER = (NJ + 255) / 256;
+        float out[PER][4];
 #pragma unroll
-        for (int j = 1; j < 4; ++j) {
-            sacc += col[(j + 2 * r) * SF_T] - col[(j - 1) * SF_T];
-            o[j * (SF_T + 1)] = sacc;
+        for (int q = 0; q < PER; ++q) {
+            const int job = threadIdx.x + q * 256;
+            if (job >= NJ) break;
+            const int m = job / (SF_T * (SF_T / 4)), rem = job % (SF_T * (SF_T / 4));
+            const int lx = rem % SF_T, ys = (rem / SF_T) * 4;
+            const float* col = f + m * span * span + ys * span + lx;
+            float sacc = 0.f;
+            for (int j = 0; j <= 2 * r; ++j) sacc += col[j * span];
+            out[q][0] = sacc;
+#pragma unroll
+            for (int j = 1; j < 4; ++j) {
+                sacc += col[(j + 2 * r) * span] - col[(j - 1) * span];
+                out[q][j] = sacc;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int job = threadIdx.x + q * 256;
+            if (job >= NJ) break;
+            const int m = job / (SF_T * (SF_T / 4)), rem = job % (SF_T * (SF_T / 4));
+            const int lx = rem % SF_T, ys = (rem / SF_T) * 4;
+            float* o = f + m * span * span + ys * span + lx;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) o[j * span] = out[q][j];
         }
     }
     __syncthreads();
+    float* box = f;                         // [3][span][span]: window sums at rows, columns 0 .. SF_T - 1
     const float* T1 = left ? T1L : T1R;
     const float* img = left ? Limg : Rimg;
     float* gout = left ? gL : gR;
@@ -550,8 +587,8 @@ __global__ void __launch_bounds__(256) k_soft_final(const float* __restrict__ T1
         const int lx = i % SF_T, ly = i / SF_T;
         const int gx = blockIdx.x * SF_T + lx, gy = blockIdx.y * SF_T + ly;
         if (gx >= W || gy >= H) continue;
-        const int o = ly * (SF_T + 1) + lx;
-        const float b0 = box[o], b1 = box[SF_T * (SF_T + 1) + o], b2 = box[2 * SF_T * (SF_T + 1) + o];
+        const int o = ly * span + lx;
+        const float b0 = box[o], b1 = box[span * span + o], b2 = box[2 * span * span + o];
         const size_t p = (size_t)gy * W + gx;
         gout[p] = T1[p] - b0 - img[p] * b1 + b2;
     }
