@@ -269,9 +269,9 @@ __device__ __forceinline__ void soft_a_border_rows(float* __restrict__ A, int nc
 // volume; given `A`, the border of the backward pass's A volume, see
 // soft_a_border_rows), from a pair of float images (blockIdx.z = 0 left,
 // 1 right).  Window sums in FP32 (exact for
-// integer-valued images), B = N SS - S^2 from the two products and their
-// exact rounding errors (fma; within about one rounding of the exact value,
-// without the slow FP64 pipe), S_lo = S mod 256.
+// integer-valued images up to 255), B = N SS - S^2 from the two products and
+// their exact rounding errors (fma; within about one rounding of the exact
+// value, without the slow FP64 pipe), S_lo = S mod 256.
 template <int R>
 __global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ imgL, const float* __restrict__ imgR,
                                                   int W, int H, PrepOut outL, PrepOut outR,
@@ -287,6 +287,13 @@ __global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ imgL
     const int x0 = blockIdx.x * PT, y0 = blockIdx.y * PT;
     constexpr int span = PT + 2 * r;
     const int tid = threadIdx.x;
+    constexpr float Nf = (float)((2 * r + 1) * (2 * r + 1));
+    // integer pixels of magnitude at most 255 keep every FP32 window sum
+    // exact (N 255^2 < 2^24 up to r = 7), and so B (within one rounding of
+    // an integer, zero exactly for a flat window)
+    static_assert((2 * R + 1) * (2 * R + 1) * 255 * 255 < (1 << 24), "exact window sums of 8-bit values");
+    constexpr float IMAX = 255.f;
+    bool exact = true;
     {
         // every load of the staged window issued before the first is stored
         constexpr int NS = (span * span + 255) / 256;
@@ -301,10 +308,11 @@ __global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ imgL
 #pragma unroll
         for (int it = 0; it < NS; ++it) {
             const int i = tid + it * 256;
+            exact = exact && v[it] == rintf(v[it]) && fabsf(v[it]) <= IMAX;
             if (i < span * span) t[i / span][i % span] = v[it];
         }
     }
-    __syncthreads();
+    exact = __syncthreads_and(exact) != 0;
 #pragma unroll 2
     for (int i = tid; i < span * PT; i += 256) {
         const int ly = i / PT, lx = i % PT;
@@ -319,7 +327,6 @@ __global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ imgL
         rss[ly][lx] = ss;
     }
     __syncthreads();
-    constexpr float Nf = (float)((2 * r + 1) * (2 * r + 1));
     for (int i = tid; i < PT * PT; i += 256) {
         const int ly = i / PT, lx = i % PT;
         const int gx = x0 + lx, gy = y0 + ly;
@@ -334,11 +341,13 @@ __global__ void __launch_bounds__(256) k_prep_f32(const float* __restrict__ imgL
             for (int k = 0; k <= 2 * r; ++k) { s += rs[ly + k][lx]; ss += rss[ly + k][lx]; }
             const float q = __fmul_rn(Nf, ss), p = __fmul_rn(s, s);   // not contracted into the fmas
             B = __fsub_rn(q, p) + (fmaf(Nf, ss, -q) - fmaf(s, s, -p));
-            // a flat window leaves only the rounding of the FP32 sums s and
-            // ss (up to about N ulps of q, possibly a denormal whose
-            // reciprocal square root would be infinite): at or below
-            // N 2^-22 q the variance is zero as far as FP32 can tell
-            if (!(B > q * (Nf * 2.384185791015625e-7f))) B = 0.f;
+            // with non-integer pixels a flat window leaves the rounding of
+            // the FP32 sums s and ss (up to about N ulps of q, possibly a
+            // denormal whose reciprocal square root would be infinite): at
+            // or below N 2^-22 q the variance is zero as far as FP32 can
+            // tell.  Exact sums need no such floor (the smallest nonzero B
+            // of integer pixels is N - 1).
+            if (!exact && !(B > q * (Nf * 2.384185791015625e-7f))) B = 0.f;
         }
         float is = 0.f;
         if (B > 0.f) {

@@ -221,6 +221,44 @@ def test_flat_patches_of_float_images(dev, r, tau):
     h.close()
 
 
+@pytest.mark.parametrize("r,tau", [(1, 0.1), (5, 0.1), (5, 0.01), (7, 0.1)])
+def test_nearly_flat_windows_of_integer_images(dev, r, tau):
+    """Integer-valued images (the 8-bit gray crop) with constant patches in
+    which single pixels sit one or two levels off: those windows have a small
+    but exact nonzero variance (B = N SS - S^2 >= N - 1 in integers) and a
+    well-defined ZNCC, which the FP32 sums of integer pixels compute exactly.
+    Their d_soft, log-sum-exp and gradients must match the oracle everywhere
+    (a variance floor meant for the rounding residue of non-integer sums once
+    zeroed them: rho = 0 for every candidate and d_soft off by tens of
+    pixels)."""
+    H, W, D = 48, 112, 24
+    L, R, gt = _crop_pair(synth.seed_for(4, 3), 20, 80, H, W)
+    L[10:34, 20:70] = L[10, 20]
+    L[10:34:7, 25:70:9] += 1.0                      # sparse one-level bumps
+    L[22, 40] += 2.0
+    R[10:34, 10:60] = R[10, 10]
+    R[14:34:6, 15:60:11] -= 1.0
+    L, R = np.clip(L, 0, 255), np.clip(R, 0, 255)
+    ds_ref, lse_ref, hv = oracle.softargmin_fwd(L, R, 0, D, r, tau)
+    g = np.where(hv, np.random.default_rng(4).normal(0, 1, (H, W)), 0.0)
+    gL_ref, gR_ref = oracle.softargmin_bwd(L, R, 0, D, r, tau, g)
+    h = _handle(H, W, D)
+    tL, tR = _T(L, dev), _T(R, dev)
+    ds = torch.empty((H, W), dtype=torch.float32, device=dev)
+    lse = torch.empty_like(ds)
+    st.stereo_softargmin_fwd(h, tL, tR, 0, D, r, tau, ds, lse)
+    gL, gR = torch.empty_like(ds), torch.empty_like(ds)
+    st.stereo_softargmin_bwd(h, tL, tR, 0, D, r, tau, ds, lse, _T(g, dev), gL, gR)
+    torch.cuda.synchronize()
+    dsn, lsen = ds.cpu().numpy(), lse.cpu().numpy()
+    assert np.array_equal(np.isnan(dsn), ~hv)
+    assert np.max(np.abs(dsn[hv] - ds_ref[hv])) <= 1e-4
+    assert np.max(np.abs(lsen[hv] - lse_ref[hv]) / np.maximum(1.0, np.abs(lse_ref[hv]))) <= 1e-5
+    for got, ref in ((gL.cpu().numpy(), gL_ref), (gR.cpu().numpy(), gR_ref)):
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= GRAD_RTOL
+    h.close()
+
+
 def test_l1_loss_many_partial_sums(dev):
     """Three 960x540 maps (1.55 M values, the largest number of partial sums)
     with a tenth of the pixels without a valid candidate: loss and gradient
