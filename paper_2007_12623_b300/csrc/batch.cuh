@@ -11,8 +11,8 @@
 template <int R, int K, int CDT>
 __device__ __forceinline__ void batched_unit(const CostArgs& a, float* smem, int4 u) {
     const int chunk = u.w & 0xffff;
-    if (u.w >> 16) cost_unit_i8<R, K, CDT, true>(a, smem, u.y, u.z, chunk);
-    else cost_unit_i8<R, K, CDT, false>(a, smem, u.y, u.z, chunk);
+    if (u.w >> 16) cost_unit_i8<R, K, CDT, true, I8_RUN_BATCHED>(a, smem, u.y, u.z, chunk);
+    else cost_unit_i8<R, K, CDT, false, I8_RUN_BATCHED>(a, smem, u.y, u.z, chunk);
 }
 
 template <int K, int CDT, int MINB>
@@ -46,18 +46,18 @@ __global__ void __launch_bounds__(32, MINB) k_cost_batched(const CostArgs* __res
 // The batched form runs the integer units (8-bit images, FULL sampling).
 template <int K> constexpr size_t batched_smem() {
     size_t m = 0;
-    m = CostI8Smem<1, K>::BYTES > m ? CostI8Smem<1, K>::BYTES : m;
-    m = CostI8Smem<2, K>::BYTES > m ? CostI8Smem<2, K>::BYTES : m;
-    m = CostI8Smem<3, K>::BYTES > m ? CostI8Smem<3, K>::BYTES : m;
-    m = CostI8Smem<4, K>::BYTES > m ? CostI8Smem<4, K>::BYTES : m;
-    m = CostI8Smem<5, K>::BYTES > m ? CostI8Smem<5, K>::BYTES : m;
-    m = CostI8Smem<6, K>::BYTES > m ? CostI8Smem<6, K>::BYTES : m;
-    m = CostI8Smem<7, K>::BYTES > m ? CostI8Smem<7, K>::BYTES : m;
+    m = CostI8Smem<1, K, I8_RUN_BATCHED>::BYTES > m ? CostI8Smem<1, K, I8_RUN_BATCHED>::BYTES : m;
+    m = CostI8Smem<2, K, I8_RUN_BATCHED>::BYTES > m ? CostI8Smem<2, K, I8_RUN_BATCHED>::BYTES : m;
+    m = CostI8Smem<3, K, I8_RUN_BATCHED>::BYTES > m ? CostI8Smem<3, K, I8_RUN_BATCHED>::BYTES : m;
+    m = CostI8Smem<4, K, I8_RUN_BATCHED>::BYTES > m ? CostI8Smem<4, K, I8_RUN_BATCHED>::BYTES : m;
+    m = CostI8Smem<5, K, I8_RUN_BATCHED>::BYTES > m ? CostI8Smem<5, K, I8_RUN_BATCHED>::BYTES : m;
+    m = CostI8Smem<6, K, I8_RUN_BATCHED>::BYTES > m ? CostI8Smem<6, K, I8_RUN_BATCHED>::BYTES : m;
+    m = CostI8Smem<7, K, I8_RUN_BATCHED>::BYTES > m ? CostI8Smem<7, K, I8_RUN_BATCHED>::BYTES : m;
     return m;
 }
 
-// Column-run width of radius R (host side).
-inline int cost_run_width(int r) { return (32 - 2 * r) & ~3; }
+// Column-run width of the integer units of radius r (host side).
+inline int cost_run_width(int r) { return cost_i8_tw(r, I8_RUN_BATCHED); }
 
 // Launch the persistent kernel (cost_batched_k<K>.cu): grid = all resident
 // warps of the device.

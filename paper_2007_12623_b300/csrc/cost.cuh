@@ -37,9 +37,9 @@ struct CostGeom {
     static constexpr int RING = 2 * R + 2;
 };
 
-template <int R, int K>
+template <int R, int K, typename GEOM = CostGeom<R>>
 struct CostSmem {
-    typedef CostGeom<R> G;
+    typedef GEOM G;
     static constexpr int LW = G::NCH * 4;              // staged left columns
     static constexpr int RWc = 32 * K + LW + 4;        // staged right columns
     static constexpr int NU = G::TW + 32 * K;          // right pixels touched per row

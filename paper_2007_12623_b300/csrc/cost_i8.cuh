@@ -23,11 +23,32 @@
 #pragma once
 #include "cost.cuh"
 
+// Column runs of the integer form: TW = (RUN - 2R) rounded down to a
+// multiple of 4 outputs per warp and row (at most 32: one lane per output
+// holds its left winner), NC = TW + 2R window columns.  The integer vertical
+// sums take one register per (window column, disparity), which leaves room
+// for wider runs than the float form's (RUN = 32); a wider run shares each
+// row's per-row work (pair words, statistics loads) among more outputs.  The
+// single-pair kernel runs RUN = 36 (960x540x128 cost stage 71.9 -> 69.4 us,
+// 960x540x192 FP16 123.9 -> 117.8 us, no spills); the persistent batched
+// kernel keeps 32 (more, smaller units balance its mixed batches better).
+constexpr int I8_RUN_SINGLE = 36, I8_RUN_BATCHED = 32;
+__host__ __device__ constexpr int cost_i8_tw(int r, int run) {
+    return ((run - 2 * r) & ~3) < 32 ? ((run - 2 * r) & ~3) : 32;
+}
+template <int R, int RUN = I8_RUN_SINGLE>
+struct CostGeomI8 {
+    static constexpr int TW = cost_i8_tw(R, RUN);
+    static constexpr int NC = TW + 2 * R;
+    static constexpr int NCH = (NC + 3) / 4;
+    static constexpr int RING = 2 * R + 2;
+};
 
-template <int R, int K>
+
+template <int R, int K, int RUN = I8_RUN_SINGLE>
 struct CostI8Smem {
-    typedef CostGeom<R> G;
-    typedef CostSmem<R, K> S;                            // statistics staging as the float form
+    typedef CostGeomI8<R, RUN> G;
+    typedef CostSmem<R, K, G> S;                         // statistics staging as the float form
     static constexpr int NC = G::NC;
     static constexpr int LWB = (NC + 15 + 15) / 16 * 16;          // staged left bytes
     static constexpr int NWP = (32 * K + NC + 3) / 4 * 2;         // right pair words per row
@@ -81,12 +102,12 @@ __device__ __forceinline__ int dp2a_s(uint32_t a, uint32_t b, int c) {
 // before x0 - R, right bytes from the aligned column at or before
 // P0 = x0 - R - dc0 - 32K (relative right position p = u - P0 of lane l,
 // window column c, slot k is K (32 - l) + c - k, in [1, 32K + NC - 1]).
-template <int R, int K, int CDT, bool PARTIAL>
+template <int R, int K, int CDT, bool PARTIAL, int RUN = I8_RUN_SINGLE>
 __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, int x0, int y0, int chunk) {
     static_assert(K == 2 || K == 4, "the integer form keeps an even number of disparities per lane");
-    typedef CostGeom<R> G;
-    typedef CostSmem<R, K> S;
-    typedef CostI8Smem<R, K> S8;
+    typedef CostGeomI8<R, RUN> G;
+    typedef CostSmem<R, K, G> S;
+    typedef CostI8Smem<R, K, RUN> S8;
     constexpr int TW = G::TW, NC = G::NC, RING = G::RING;
     constexpr int ROWB = S8::ROWB, LWB = S8::LWB, NUP = S8::NUPK, NU4 = S::NU4, PS = S8::PS;
     uint8_t* sm = reinterpret_cast<uint8_t*>(smem_f);
@@ -323,7 +344,7 @@ __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, i
 template <int R, int K, int CDT, int MINB>
 __global__ void __launch_bounds__(32, MINB) k_cost_wta_i8(CostArgs a) {
     extern __shared__ __align__(16) float smem[];
-    typedef CostGeom<R> G;
+    typedef CostGeomI8<R> G;
     const int inner_h = a.H - 2 * R;
     int x0 = R + blockIdx.x * G::TW;
     int y0 = R + blockIdx.y * a.rows;

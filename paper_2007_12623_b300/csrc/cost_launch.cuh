@@ -29,10 +29,10 @@ template <int K, bool I8> struct CostMinBlocksI { static constexpr int value = I
 // I8: the integer form (cost_i8.cuh; K even, FULL sampling, 8-bit images).
 template <int R, int K, int CDT, bool CB = false, bool I8 = false>
 void launch_cost_rkc(CostArgs a, int rows_override, cudaStream_t s) {
-    typedef CostGeom<R> G;
+    constexpr int TW = I8 ? CostGeomI8<R>::TW : CostGeom<R>::TW;
     constexpr int MINB = CostMinBlocksI<K, I8>::value;
     constexpr int BYTES = I8 ? CostI8Smem<R, K>::BYTES : CostSmem<R, K>::BYTES;
-    const int nx = (a.W - 2 * R + G::TW - 1) / G::TW;
+    const int nx = (a.W - 2 * R + TW - 1) / TW;
     const int nz = (a.dcount + 32 * K - 1) / (32 * K);
     if (nx <= 0 || a.H - 2 * R <= 0 || nz <= 0) return;
     static int cap = 0;
