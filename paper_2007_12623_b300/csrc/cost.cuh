@@ -107,6 +107,10 @@ struct CostArgs {
     float sk2 = 0.f;                              // log2(e) / tau
     float sinvtau = 0.f;                          // 1 / tau
     int sshift = 0;                               // FWD: weights relative to each pixel's best candidate
+    // integer form with the whole disparity range in one chunk: the sub-pixel
+    // disparity of every visited pixel (the winner's parabola, Sec. II-A),
+    // written here instead of by the finalize kernel; nullptr otherwise
+    float* sub = nullptr;
 };
 
 // SOFT_FWDS: the forward form with each pixel's weights taken relative to

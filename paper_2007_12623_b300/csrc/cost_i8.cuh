@@ -67,9 +67,14 @@ struct CostI8Smem {
     static constexpr int OFF_U = (OFF_LP + NLP * 4 + 15) / 16 * 16;
     static constexpr int OFF_LS = OFF_U + 2 * NUPK * 16;
     static constexpr int OFF_EXIT = OFF_LS + S::LS * 4;
-    static constexpr int BYTES = OFF_EXIT + 32 * 4;
+    // the row's FP32 costs [TW][CVS] for the in-kernel parabola (padded rows:
+    // the winners' reads of one row fall on few banks)
+    static constexpr int CVS = 32 * K + 4;
+    static constexpr int OFF_CV = (OFF_EXIT + 32 * 4 + 15) / 16 * 16;
+    static constexpr int BYTES = OFF_CV;                              // without the parked costs
+    static constexpr int BYTES_SUB = OFF_CV + G::TW * CVS * 4;
     // the vector reads of the staged rows need these alignments
-    static_assert(OFF_RP % 16 == 0 && OFF_LP % 16 == 0 && OFF_U % 16 == 0 && OFF_LS % 8 == 0,
+    static_assert(OFF_RP % 16 == 0 && OFF_LP % 16 == 0 && OFF_U % 16 == 0 && OFF_LS % 8 == 0 && OFF_CV % 16 == 0,
                   "shared-memory layout of the integer cost unit");
 };
 
@@ -102,7 +107,9 @@ __device__ __forceinline__ int dp2a_s(uint32_t a, uint32_t b, int c) {
 // before x0 - R, right bytes from the aligned column at or before
 // P0 = x0 - R - dc0 - 32K (relative right position p = u - P0 of lane l,
 // window column c, slot k is K (32 - l) + c - k, in [1, 32K + NC - 1]).
-template <int R, int K, int CDT, bool PARTIAL, int RUN = I8_RUN_SINGLE>
+// SUB: the code of the in-kernel parabola exists (taken when a.sub is set;
+// shared memory CostI8Smem::BYTES_SUB).
+template <int R, int K, int CDT, bool PARTIAL, int RUN = I8_RUN_SINGLE, bool SUB = true>
 __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, int x0, int y0, int chunk) {
     static_assert(K == 2 || K == 4, "the integer form keeps an even number of disparities per lane");
     typedef CostGeomI8<R, RUN> G;
@@ -117,6 +124,7 @@ __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, i
     float4* sU = reinterpret_cast<float4*>(sm + S8::OFF_U);                         // [2][NUP]
     float2* sLs = reinterpret_cast<float2*>(sm + S8::OFF_LS);                       // [2][TW]
     uint32_t* sExit = reinterpret_cast<uint32_t*>(sm + S8::OFF_EXIT);
+    float* sCv = reinterpret_cast<float*>(sm + S8::OFF_CV);                          // [TW][CVS]
 
     const int lane = threadIdx.x & 31;
     const int W = a.W, H = a.H;
@@ -308,6 +316,11 @@ __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, i
                 }
             }
             crow += (size_t)cstride * ESZ;
+            if (SUB && a.sub) {
+                float* cvp = sCv + j * S8::CVS + K * lane;
+                if (K == 4) *reinterpret_cast<float4*>(cvp) = make_float4(cv[0], cv[1 % K], cv[2 % K], cv[3 % K]);
+                else *reinterpret_cast<float2*>(cvp) = make_float2(cv[0], cv[1 % K]);
+            }
             const uint32_t red = __reduce_max_sync(0xffffffffu, best);
             if (lane == j) myLeft = red;
             // the oldest slot (register (j+1) mod K) moves on to the next lane
@@ -319,6 +332,23 @@ __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, i
         __syncwarp();
         if (lane < nsteps) {
             atomicMax(a.keyL + (size_t)y * W + x0 + lane, myLeft);
+            if (SUB && a.sub) {
+                // one chunk: myLeft is the pixel's final left key and the row's
+                // costs are parked; the finalize kernel's parabola (the same
+                // FP32 operations on the same values) without reading a volume
+                const int w = 255 - (int)(myLeft & 255u);
+                const bool inner = myLeft >= KEY_VALID_MIN && w > 0 && w < a.D - 1;
+                const float* cp = sCv + lane * S8::CVS + (inner ? w - 1 : 0);
+                const float c0 = cp[0], c1 = cp[1], c2 = cp[2];
+                float delta = 0.f;
+                const float den = c0 - 2.f * c1 + c2;
+                if (inner && !isnan(c0) && !isnan(c2) && den > 0.f) {
+                    delta = (c0 - c2) / (2.f * den);
+                    delta = fminf(0.5f, fmaxf(-0.5f, delta));
+                }
+                a.sub[(size_t)y * W + x0 + lane] =
+                    myLeft >= KEY_VALID_MIN ? (float)(a.d_min + w) + delta : __int_as_float(0x7fc00000);
+            }
             const int u = x0 + lane - dc0 - 32 * K + 1;
             const uint32_t e = sExit[lane];
             if (u >= 0 && u < W && e) atomicMax(a.keyR + (size_t)y * W + u, e);
@@ -341,7 +371,7 @@ __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, i
 // a.rows rows, .z = disparity chunk); the staging here needs no alignment of
 // the first column, so a last run that would stick out is always moved left
 // to be full.
-template <int R, int K, int CDT, int MINB>
+template <int R, int K, int CDT, int MINB, bool SUB = false>
 __global__ void __launch_bounds__(32, MINB) k_cost_wta_i8(CostArgs a) {
     extern __shared__ __align__(16) float smem[];
     typedef CostGeomI8<R> G;
@@ -356,6 +386,6 @@ __global__ void __launch_bounds__(32, MINB) k_cost_wta_i8(CostArgs a) {
         else partial = true;
     }
     if (inner_h >= a.rows) y0 = min(y0, a.H - R - a.rows);
-    if (partial) cost_unit_i8<R, K, CDT, true>(a, smem, x0, y0, blockIdx.z);
-    else cost_unit_i8<R, K, CDT, false>(a, smem, x0, y0, blockIdx.z);
+    if (partial) cost_unit_i8<R, K, CDT, true, I8_RUN_SINGLE, SUB>(a, smem, x0, y0, blockIdx.z);
+    else cost_unit_i8<R, K, CDT, false, I8_RUN_SINGLE, SUB>(a, smem, x0, y0, blockIdx.z);
 }

@@ -186,6 +186,7 @@ struct FinArgs {
     int16_t* disp_right;
     float* disp_sub;
     int16_t* disp_lr;
+    int sub_done;      // the cost kernel wrote disp_sub of the pixels it visits (window inside the image)
 };
 
 // Row vb.y, columns 128 vb.x .. 128 vb.x + 127 (128 threads).
@@ -221,7 +222,7 @@ __device__ __forceinline__ void finalize_run(const FinArgs& f, VBlock vb) {
         }
         disp_lr[i] = (int16_t)keep;
     }
-    if (disp_sub) {
+    if (disp_sub && !(f.sub_done && x >= r && x < W - r && y >= r && y < H - r)) {
         float s = __int_as_float(0x7fc00000);
         if (dl != ST_INVALID) {
             float delta = 0.f;
@@ -262,11 +263,11 @@ __global__ void __launch_bounds__(128, 16) k_finalize(FinArgs f) {
 static void launch_finalize(const uint32_t* keyL, const uint32_t* keyR, int W, int H, int d_min, int D,
                             int lr_thresh, const void* cost, int cdt, const uint8_t* L, const uint8_t* Rm,
                             int r, int sampling, const FinStats& fs, int16_t* disp_left, int16_t* disp_right,
-                            float* disp_sub, int16_t* disp_lr, cudaStream_t s) {
+                            float* disp_sub, int16_t* disp_lr, cudaStream_t s, bool sub_done = false) {
     const dim3 g((W + 127) / 128, H);
     const int rr = fs.lstats ? r : 0;
     const FinArgs f{keyL, keyR, W, H, d_min, D, lr_thresh, cost, cdt, L, Rm, r, sampling, fs,
-                    disp_left, disp_right, disp_sub, disp_lr};
+                    disp_left, disp_right, disp_sub, disp_lr, sub_done ? 1 : 0};
 #define FIN_CASE(RV, CBV) \
     case RV: k_finalize<RV, CBV><<<g, 128, 0, s>>>(f); break;
     if (sampling == 1) {

@@ -454,6 +454,11 @@ void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, in
         a.dbase = a4.dcount;
         a.dcount = D - a4.dcount;
     }
+    // the whole range in one chunk of the integer form and no FP32 volume:
+    // the cost kernel fits the parabola itself (the finalize kernel would
+    // recompute the winner's three costs)
+    const bool sub_in_cost = i8 && cdt != CDT_F32 && a.dbase == 0 && D <= 32 * K && disp_sub;
+    if (sub_in_cost) a.sub = disp_sub;
     launch_cost(r, K, cdt, a, g_cost_rows, s, sampling);
     if (ev) cudaEventRecord(ev[3], s);
     launch_finalize(w.keys, w.keys + (size_t)W * H, W, H, d_min, D, lr_thresh, cost, cdt, gl, gr, r, sampling,
@@ -461,7 +466,7 @@ void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, in
                              i8 ? reinterpret_cast<const int8_t*>(pl.img) : nullptr, pl.stride, pl.col0,
                              i8 ? reinterpret_cast<const int8_t*>(pr.img) : nullptr, pr.stride, pr.col0},
                     disp_left, disp_right, disp_sub, disp_lr,
-                    s);
+                    s, sub_in_cost);
     counted();
 }
 

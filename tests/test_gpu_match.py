@@ -154,6 +154,30 @@ def test_half_precision_cost_storage(dev):
         assert np.array_equal(np.isnan(g["cost"]), np.isnan(cv))
 
 
+@pytest.mark.parametrize("shape,d_min,D,r", [((72, 200), 0, 64, 5), ((90, 240), -8, 128, 7),
+                                             ((61, 173), 3, 100, 3), ((40, 300), -20, 128, 1)])
+def test_subpixel_in_cost_kernel_matches_finalize(dev, shape, d_min, D, r):
+    """With the whole disparity range in one chunk and no FP32 volume
+    (FP16, BF16 or none) the integer cost kernel fits the parabola itself,
+    from its FP32 costs parked in shared memory; with an FP32 volume the
+    finalize kernel reads the three costs back.  Both are the same FP32
+    operations on the same values: winners and sub-pixel disparities
+    bit-identical across the four storage types (NaN at the same pixels),
+    and within the bar against the oracle."""
+    H, W = shape
+    L, R, gt = synth.tissue_pair(synth.seed_for(11, D + r), 320, 180, 2.0, 14.0)
+    L, R = oracle.gray(L)[:H, :W], oracle.gray(R)[:H, :W]
+    ref = run_stage_match(dev, L, R, d_min, D, r, st.COST_F32)
+    m = oracle.match(L, R, d_min, D, r)
+    check_against_oracle(ref, m, D)
+    for cdt in (st.COST_F16, st.COST_BF16, st.COST_NONE):
+        g = run_stage_match(dev, L, R, d_min, D, r, cdt)
+        assert np.array_equal(g["dL"], ref["dL"]) and np.array_equal(g["dR"], ref["dR"])
+        assert np.array_equal(np.isnan(g["sub"]), np.isnan(ref["sub"]))
+        ok = ~np.isnan(ref["sub"])
+        assert np.array_equal(g["sub"][ok].view(np.uint32), ref["sub"][ok].view(np.uint32))
+
+
 def test_deterministic(dev):
     L, R, gt = synth.perlin_pair(synth.seed_for(0))
     a = run_stage_match(dev, L, R, 0, 32, 5)
