@@ -11,8 +11,8 @@
 template <int R, int K, int CDT>
 __device__ __forceinline__ void batched_unit(const CostArgs& a, float* smem, int4 u) {
     const int chunk = u.w & 0xffff;
-    if (u.w >> 16) cost_unit_i8<R, K, CDT, true, I8_RUN_BATCHED, false>(a, smem, u.y, u.z, chunk);
-    else cost_unit_i8<R, K, CDT, false, I8_RUN_BATCHED, false>(a, smem, u.y, u.z, chunk);
+    if (u.w >> 16) cost_unit_i8<R, K, CDT, true, I8_RUN_BATCHED, 0>(a, smem, u.y, u.z, chunk);
+    else cost_unit_i8<R, K, CDT, false, I8_RUN_BATCHED, 0>(a, smem, u.y, u.z, chunk);
 }
 
 template <int K, int CDT, int MINB>

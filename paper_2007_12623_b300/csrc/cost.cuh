@@ -111,6 +111,14 @@ struct CostArgs {
     // disparity of every visited pixel (the winner's parabola, Sec. II-A),
     // written here instead of by the finalize kernel; nullptr otherwise
     float* sub = nullptr;
+    // several chunks (integer form, no FP32 volume): per chunk, the FP32
+    // costs of its own winner's candidates w - 1, w, w + 1 (+inf where one
+    // lies outside the chunk), planes (3 slot + t) * subc_plane floats from
+    // subc, slot = subc_slot0 + chunk; the finalize kernel takes the slot of
+    // the final winner's chunk instead of recomputing the three costs
+    float* subc = nullptr;
+    long subc_plane = 0;
+    int subc_slot0 = 0;
 };
 
 // SOFT_FWDS: the forward form with each pixel's weights taken relative to

@@ -107,9 +107,9 @@ __device__ __forceinline__ int dp2a_s(uint32_t a, uint32_t b, int c) {
 // before x0 - R, right bytes from the aligned column at or before
 // P0 = x0 - R - dc0 - 32K (relative right position p = u - P0 of lane l,
 // window column c, slot k is K (32 - l) + c - k, in [1, 32K + NC - 1]).
-// SUB: the code of the in-kernel parabola exists (taken when a.sub is set;
-// shared memory CostI8Smem::BYTES_SUB).
-template <int R, int K, int CDT, bool PARTIAL, int RUN = I8_RUN_SINGLE, bool SUB = true>
+// SUB: 0 none, 1 the in-kernel parabola (a.sub), 2 the per-chunk winner
+// costs (a.subc); 1 and 2 park each row's costs (CostI8Smem::BYTES_SUB).
+template <int R, int K, int CDT, bool PARTIAL, int RUN = I8_RUN_SINGLE, int SUB = 0>
 __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, int x0, int y0, int chunk) {
     static_assert(K == 2 || K == 4, "the integer form keeps an even number of disparities per lane");
     typedef CostGeomI8<R, RUN> G;
@@ -316,7 +316,7 @@ __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, i
                 }
             }
             crow += (size_t)cstride * ESZ;
-            if (SUB && a.sub) {
+            if (SUB != 0) {
                 float* cvp = sCv + j * S8::CVS + K * lane;
                 if (K == 4) *reinterpret_cast<float4*>(cvp) = make_float4(cv[0], cv[1 % K], cv[2 % K], cv[3 % K]);
                 else *reinterpret_cast<float2*>(cvp) = make_float2(cv[0], cv[1 % K]);
@@ -332,7 +332,7 @@ __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, i
         __syncwarp();
         if (lane < nsteps) {
             atomicMax(a.keyL + (size_t)y * W + x0 + lane, myLeft);
-            if (SUB && a.sub) {
+            if (SUB == 1) {
                 // one chunk: myLeft is the pixel's final left key and the row's
                 // costs are parked; the finalize kernel's parabola (the same
                 // FP32 operations on the same values) without reading a volume
@@ -348,6 +348,16 @@ __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, i
                 }
                 a.sub[(size_t)y * W + x0 + lane] =
                     myLeft >= KEY_VALID_MIN ? (float)(a.d_min + w) + delta : __int_as_float(0x7fc00000);
+            } else if (SUB == 2) {
+                // several chunks: this chunk's winner's cost and its
+                // neighbours' (+inf where the neighbour is another chunk's)
+                const int wc = min(max(255 - (int)(myLeft & 255u) - (dc0 - a.d_min), 0), 32 * K - 1);
+                const float* cp = sCv + lane * S8::CVS + wc;
+                const float inf = __int_as_float(0x7f800000);
+                float* pl = a.subc + (size_t)(3 * (a.subc_slot0 + chunk)) * a.subc_plane + (size_t)y * W + x0 + lane;
+                pl[0] = wc >= 1 ? cp[-1] : inf;
+                pl[a.subc_plane] = cp[0];
+                pl[2 * a.subc_plane] = wc + 1 < 32 * K ? cp[1] : inf;
             }
             const int u = x0 + lane - dc0 - 32 * K + 1;
             const uint32_t e = sExit[lane];
@@ -371,7 +381,7 @@ __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, i
 // a.rows rows, .z = disparity chunk); the staging here needs no alignment of
 // the first column, so a last run that would stick out is always moved left
 // to be full.
-template <int R, int K, int CDT, int MINB, bool SUB = false>
+template <int R, int K, int CDT, int MINB, int SUB = 0>
 __global__ void __launch_bounds__(32, MINB) k_cost_wta_i8(CostArgs a) {
     extern __shared__ __align__(16) float smem[];
     typedef CostGeomI8<R> G;

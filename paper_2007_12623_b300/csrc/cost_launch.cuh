@@ -49,14 +49,18 @@ void launch_cost_rkc(CostArgs a, int rows_override, cudaStream_t s) {
     a.rows = rows_override > 0 ? rows_override : cost_choose_rows(nx, nz, a.H - 2 * R, cap);
     const int ny = (a.H - 2 * R + a.rows - 1) / a.rows;
     if constexpr (I8) {
-        // the parabola in the kernel (a.sub: one chunk, no FP32 volume, where
-        // the finalize kernel would otherwise recompute the winner's costs);
-        // an FP32 volume holds them already, and parking each row's costs in
-        // shared memory slowed the kernel more than the volume reads cost
-        // the finalize kernel
+        // the parabola in the kernel (a.sub: one chunk; a.subc: several, the
+        // winner's costs per chunk) where the finalize kernel would otherwise
+        // recompute the winner's costs (no FP32 volume); an FP32 volume holds
+        // them already, and parking each row's costs in shared memory slowed
+        // the kernel more than the volume reads cost the finalize kernel
         if constexpr (CDT != CDT_F32) {
             if (a.sub) {
-                k_cost_wta_i8<R, K, CDT, MINB, true><<<dim3(nx, ny, nz), 32, CostI8Smem<R, K>::BYTES_SUB, s>>>(a);
+                k_cost_wta_i8<R, K, CDT, MINB, 1><<<dim3(nx, ny, nz), 32, CostI8Smem<R, K>::BYTES_SUB, s>>>(a);
+                return;
+            }
+            if (a.subc) {
+                k_cost_wta_i8<R, K, CDT, MINB, 2><<<dim3(nx, ny, nz), 32, CostI8Smem<R, K>::BYTES_SUB, s>>>(a);
                 return;
             }
         }

@@ -187,6 +187,11 @@ struct FinArgs {
     float* disp_sub;
     int16_t* disp_lr;
     int sub_done;      // the cost kernel wrote disp_sub of the pixels it visits (window inside the image)
+    // the cost kernels' per-chunk winner costs (CostArgs::subc; slot = index
+    // of the winner / subc_split), or nullptr
+    const float* subc;
+    long subc_plane;
+    int subc_split;
 };
 
 // Row vb.y, columns 128 vb.x .. 128 vb.x + 127 (128 threads).
@@ -209,36 +214,54 @@ __device__ __forceinline__ void finalize_run(const FinArgs& f, VBlock vb) {
     if (x >= W) return;
     const size_t i = (size_t)y * W + x;
     const int dl = key_to_disp(keyL[i], d_min);
+    // every load that depends on the winner goes out before the first store
+    // (the stores could alias them as far as the compiler knows)
+    const int u = x - dl;
+    const uint32_t kru = disp_lr && dl != ST_INVALID && u >= 0 && u < W ? __ldg(keyR + (size_t)y * W + u) : 0u;
+    const uint32_t kr = disp_right ? __ldg(keyR + i) : 0u;
+    const bool want_sub = disp_sub && !(f.sub_done && x >= r && x < W - r && y >= r && y < H - r);
+    const bool fit = want_sub && dl != ST_INVALID && dl > d_min && dl < d_min + D - 1;
+    float c[3] = {0.f, 0.f, 0.f};
+    bool have = false;
+    if (fit && f.subc) {
+        // the winner's chunk kept its three costs (+inf: a neighbour in the
+        // other chunk, recomputed below)
+        const int slot = (dl - d_min) / f.subc_split;
+        const float* pl = f.subc + (size_t)(3 * slot) * f.subc_plane + i;
+        c[0] = __ldg(pl);
+        c[1] = __ldg(pl + f.subc_plane);
+        c[2] = __ldg(pl + 2 * f.subc_plane);
+        have = !isinf(c[0]) && !isinf(c[2]);
+    } else if (fit && cdt == CDT_F32) {
+        const size_t b = i * (size_t)cost_stride(D) + (dl - d_min);
+        c[0] = cost_load(cost, cdt, b - 1);
+        c[1] = cost_load(cost, cdt, b);
+        c[2] = cost_load(cost, cdt, b + 1);
+        have = true;
+    }
     if (disp_left) disp_left[i] = (int16_t)dl;
-    if (disp_right) disp_right[i] = (int16_t)key_to_disp(keyR[i], d_min);
+    if (disp_right) disp_right[i] = (int16_t)key_to_disp(kr, d_min);
     if (disp_lr) {
         int keep = ST_INVALID;
-        if (dl != ST_INVALID) {
-            const int u = x - dl;
-            if (u >= 0 && u < W) {
-                const int e = key_to_disp(keyR[(size_t)y * W + u], d_min);
-                if (e != ST_INVALID && abs(dl - e) <= lr_thresh) keep = dl;
-            }
+        if (dl != ST_INVALID && u >= 0 && u < W) {
+            const int e = key_to_disp(kru, d_min);
+            if (e != ST_INVALID && abs(dl - e) <= lr_thresh) keep = dl;
         }
         disp_lr[i] = (int16_t)keep;
     }
-    if (disp_sub && !(f.sub_done && x >= r && x < W - r && y >= r && y < H - r)) {
+    if (want_sub) {
         float s = __int_as_float(0x7fc00000);
         if (dl != ST_INVALID) {
             float delta = 0.f;
-            if (dl > d_min && dl < d_min + D - 1) {
-                float c[3];
-                if (cdt == CDT_F32) {
-                    const size_t b = i * (size_t)cost_stride(D) + (dl - d_min);
-                    c[0] = cost_load(cost, cdt, b - 1);
-                    c[1] = cost_load(cost, cdt, b);
-                    c[2] = cost_load(cost, cdt, b + 1);
-                } else if (R > 0) {
-                    costs3_fp32<R, CB>(L, Rm, W, x, y, x - dl, fs, c);
-                } else {
-                    c[0] = 1.f - zncc_direct(L, Rm, W, H, r, sampling, x, y, dl - 1);
-                    c[1] = 1.f - zncc_direct(L, Rm, W, H, r, sampling, x, y, dl);
-                    c[2] = 1.f - zncc_direct(L, Rm, W, H, r, sampling, x, y, dl + 1);
+            if (fit) {
+                if (!have) {
+                    if (R > 0) {
+                        costs3_fp32<R, CB>(L, Rm, W, x, y, x - dl, fs, c);
+                    } else {
+                        c[0] = 1.f - zncc_direct(L, Rm, W, H, r, sampling, x, y, dl - 1);
+                        c[1] = 1.f - zncc_direct(L, Rm, W, H, r, sampling, x, y, dl);
+                        c[2] = 1.f - zncc_direct(L, Rm, W, H, r, sampling, x, y, dl + 1);
+                    }
                 }
                 const float den = c[0] - 2.f * c[1] + c[2];
                 if (!isnan(c[0]) && !isnan(c[2]) && den > 0.f) {
@@ -263,11 +286,12 @@ __global__ void __launch_bounds__(128, 16) k_finalize(FinArgs f) {
 static void launch_finalize(const uint32_t* keyL, const uint32_t* keyR, int W, int H, int d_min, int D,
                             int lr_thresh, const void* cost, int cdt, const uint8_t* L, const uint8_t* Rm,
                             int r, int sampling, const FinStats& fs, int16_t* disp_left, int16_t* disp_right,
-                            float* disp_sub, int16_t* disp_lr, cudaStream_t s, bool sub_done = false) {
+                            float* disp_sub, int16_t* disp_lr, cudaStream_t s, bool sub_done = false,
+                            const float* subc = nullptr, long subc_plane = 0, int subc_split = 0) {
     const dim3 g((W + 127) / 128, H);
     const int rr = fs.lstats ? r : 0;
     const FinArgs f{keyL, keyR, W, H, d_min, D, lr_thresh, cost, cdt, L, Rm, r, sampling, fs,
-                    disp_left, disp_right, disp_sub, disp_lr, sub_done ? 1 : 0};
+                    disp_left, disp_right, disp_sub, disp_lr, sub_done ? 1 : 0, subc, subc_plane, subc_split};
 #define FIN_CASE(RV, CBV) \
     case RV: k_finalize<RV, CBV><<<g, 128, 0, s>>>(f); break;
     if (sampling == 1) {

@@ -72,6 +72,10 @@ struct PairWs {
     int* rsO;
     float* rsB;
     uint32_t* op;       // refinement on tiles: packed o (aliases rsO)
+    // dprev, dt, b, rsC, rsO, rsB are six consecutive planes of rplane
+    // floats; before the refinement runs they hold the multi-chunk cost
+    // kernels' winner costs (CostArgs::subc)
+    long rplane;
 };
 
 // Words of the line bitmasks for a W x H map (the largest W x H of a
@@ -143,6 +147,7 @@ PairWs carve(uint8_t* base, size_t npix, int D, int cdt, int maxW, int maxH, int
     w.rsO = reinterpret_cast<int*>(take(npix * 4));
     w.rsB = reinterpret_cast<float*>(take(npix * 4));
     w.op = reinterpret_cast<uint32_t*>(w.rsO);
+    w.rplane = (long)(align_up(npix * 4, 256) / 4);
     return w;
 }
 
@@ -445,6 +450,15 @@ void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, in
     if (ev) cudaEventRecord(ev[2], s);
     CostArgs a{pl.img, pl.stride, pl.col0, pr.img, pr.stride, pr.col0, i8 ? 1 : 0, w.lstats, w.ustats,
                pr.ustride, pr.ucol0, w.keys, w.keys + (size_t)W * H, cost, cdt, W, H, d_min, D, 0, 0, D};
+    // several chunks of the integer form and no FP32 volume: each chunk's
+    // kernel keeps its winner's three costs (two slots of three planes in the
+    // refinement's buffers, free until the refinement runs), and the finalize
+    // kernel reads the final winner's instead of recomputing them
+    const bool chunked_sub = i8 && cdt != CDT_F32 && D > 32 * K && D <= 256 && disp_sub;
+    if (chunked_sub) {
+        a.subc = w.dprev;
+        a.subc_plane = w.rplane;
+    }
     if (i8 && K == 2 && D > 128) {
         // 128-disparity chunks at K = 4 for the bulk of the range and 64-disparity
         // chunks at K = 2 for the rest (e.g. D = 192: 128 + 64 with no idle lane)
@@ -453,6 +467,7 @@ void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, in
         launch_cost(r, 4, cdt, a4, g_cost_rows, s, sampling);
         a.dbase = a4.dcount;
         a.dcount = D - a4.dcount;
+        a.subc_slot0 = a4.dcount / 128;
     }
     // the whole range in one chunk of the integer form and no FP32 volume:
     // the cost kernel fits the parabola itself (the finalize kernel would
@@ -466,7 +481,7 @@ void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, in
                              i8 ? reinterpret_cast<const int8_t*>(pl.img) : nullptr, pl.stride, pl.col0,
                              i8 ? reinterpret_cast<const int8_t*>(pr.img) : nullptr, pr.stride, pr.col0},
                     disp_left, disp_right, disp_sub, disp_lr,
-                    s, sub_in_cost);
+                    s, sub_in_cost, chunked_sub ? w.dprev : nullptr, w.rplane, 128);
     counted();
 }
 

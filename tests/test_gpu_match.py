@@ -155,15 +155,20 @@ def test_half_precision_cost_storage(dev):
 
 
 @pytest.mark.parametrize("shape,d_min,D,r", [((72, 200), 0, 64, 5), ((90, 240), -8, 128, 7),
-                                             ((61, 173), 3, 100, 3), ((40, 300), -20, 128, 1)])
+                                             ((61, 173), 3, 100, 3), ((40, 300), -20, 128, 1),
+                                             # several chunks; winners on both sides of index 128
+                                             ((90, 240), -120, 192, 7), ((72, 300), -124, 256, 5),
+                                             ((61, 173), -125, 160, 3)])
 def test_subpixel_in_cost_kernel_matches_finalize(dev, shape, d_min, D, r):
-    """With the whole disparity range in one chunk and no FP32 volume
-    (FP16, BF16 or none) the integer cost kernel fits the parabola itself,
-    from its FP32 costs parked in shared memory; with an FP32 volume the
-    finalize kernel reads the three costs back.  Both are the same FP32
-    operations on the same values: winners and sub-pixel disparities
-    bit-identical across the four storage types (NaN at the same pixels),
-    and within the bar against the oracle."""
+    """Without an FP32 volume (FP16, BF16 or none) the integer cost kernel
+    parks each row's FP32 costs in shared memory: with the whole range in one
+    chunk it fits the parabola itself; with several chunks each keeps its own
+    winner's three costs (+inf for a neighbour in the other chunk, which the
+    finalize kernel then recomputes) and the finalize kernel takes the final
+    winner's.  With an FP32 volume the finalize kernel reads the three costs
+    back.  All are the same FP32 operations on the same values: winners and
+    sub-pixel disparities bit-identical across the four storage types (NaN
+    at the same pixels), and within the bar against the oracle."""
     H, W = shape
     L, R, gt = synth.tissue_pair(synth.seed_for(11, D + r), 320, 180, 2.0, 14.0)
     L, R = oracle.gray(L)[:H, :W], oracle.gray(R)[:H, :W]
