@@ -39,10 +39,10 @@
  *    code).  The checked build of the library (libstereo_checked.so,
  *    compiled with -DSTEREO_CHECKED, for testing) checks the index ranges of
  *    its staged-row copies, cost stores, mask-word reads and writes,
- *    candidate loads and preparation writes inside the kernels; a failed
- *    check records ST_DEVERR_BOUNDS (0x1000) | site in a device error word
- *    and skips the access (nothing traps), read and cleared with
- *    stereo_get_device_error().
+ *    candidate loads, preparation writes and sub-pixel writes inside the
+ *    kernels; a failed check records ST_DEVERR_BOUNDS (0x1000) | site in a
+ *    device error word and skips the access (nothing traps), read and
+ *    cleared with stereo_get_device_error().
  *  - A handle is not thread-safe: one host thread at a time per handle.
  */
 #ifndef STEREO_H

@@ -346,8 +346,9 @@ __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, i
                     delta = (c0 - c2) / (2.f * den);
                     delta = fminf(0.5f, fmaxf(-0.5f, delta));
                 }
-                a.sub[(size_t)y * W + x0 + lane] =
-                    myLeft >= KEY_VALID_MIN ? (float)(a.d_min + w) + delta : __int_as_float(0x7fc00000);
+                if (ST_CHECK(x0 + lane < W && y < H, 10))
+                    a.sub[(size_t)y * W + x0 + lane] =
+                        myLeft >= KEY_VALID_MIN ? (float)(a.d_min + w) + delta : __int_as_float(0x7fc00000);
             } else if (SUB == 2) {
                 // several chunks: this chunk's winner's cost and its
                 // neighbours' (+inf where the neighbour is another chunk's)
@@ -355,9 +356,11 @@ __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, i
                 const float* cp = sCv + lane * S8::CVS + wc;
                 const float inf = __int_as_float(0x7f800000);
                 float* pl = a.subc + (size_t)(3 * (a.subc_slot0 + chunk)) * a.subc_plane + (size_t)y * W + x0 + lane;
-                pl[0] = wc >= 1 ? cp[-1] : inf;
-                pl[a.subc_plane] = cp[0];
-                pl[2 * a.subc_plane] = wc + 1 < 32 * K ? cp[1] : inf;
+                if (ST_CHECK(x0 + lane < W && y < H && a.subc_slot0 + chunk < 2 && (long)W * H <= a.subc_plane, 10)) {
+                    pl[0] = wc >= 1 ? cp[-1] : inf;
+                    pl[a.subc_plane] = cp[0];
+                    pl[2 * a.subc_plane] = wc + 1 < 32 * K ? cp[1] : inf;
+                }
             }
             const int u = x0 + lane - dc0 - 32 * K + 1;
             const uint32_t e = sExit[lane];

@@ -223,7 +223,7 @@ __device__ __forceinline__ void finalize_run(const FinArgs& f, VBlock vb) {
     const bool fit = want_sub && dl != ST_INVALID && dl > d_min && dl < d_min + D - 1;
     float c[3] = {0.f, 0.f, 0.f};
     bool have = false;
-    if (fit && f.subc) {
+    if (fit && f.subc && ST_CHECK((dl - d_min) / f.subc_split < 2, 10)) {
         // the winner's chunk kept its three costs (+inf: a neighbour in the
         // other chunk, recomputed below)
         const int slot = (dl - d_min) / f.subc_split;
