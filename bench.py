@@ -105,7 +105,9 @@ COST_CODE = {"none": 0, "f32": 1, "f16": 2, "bf16": 3}
 # DRAM bytes (read + write) of one launch of the workload's dominant kernel,
 # read from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of
 # the kernel as it is built now; absent where no such capture exists.
-KERNEL_TRAFFIC = {"tissue960": 222.2e6,
+KERNEL_TRAFFIC = {"tissue960": 222.2e6, "tissue960_f16": 94.4e6, "tissue960_none": 18.6e6,
+                  # one persistent launch over the 4 pairs
+                  "tissue960_x4": 1062.8e6, "tissue960_x4_f16": 547.3e6,
                   # both launches of the D = 192 range (128 at K = 4, 64 at K = 2)
                   "tissue960_d192_f16": 130.0e6,
                   "soft8": {"k_soft_box_t1": 606.8e6, "k_cost_wta (soft backward form)": 235.5e6}}
