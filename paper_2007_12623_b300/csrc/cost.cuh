@@ -119,6 +119,13 @@ struct CostArgs {
     float* subc = nullptr;
     long subc_plane = 0;
     int subc_slot0 = 0;
+    // the two chunks of a split range (128 at K = 4 after the rest at K = 2,
+    // in that order of launch): 1 = the first chunk, which writes its last
+    // cost into subc_edge and leaves its c2 plane where its winner is its
+    // last candidate; 2 = the second chunk (launched first), which writes its
+    // first cost into the first chunk's c2 plane for every pixel
+    int subc_mode = 0;
+    float* subc_edge = nullptr;
 };
 
 // SOFT_FWDS: the forward form with each pixel's weights taken relative to

@@ -355,11 +355,15 @@ __device__ __forceinline__ void cost_unit_i8(const CostArgs& a, float* smem_f, i
                 const int wc = min(max(255 - (int)(myLeft & 255u) - (dc0 - a.d_min), 0), 32 * K - 1);
                 const float* cp = sCv + lane * S8::CVS + wc;
                 const float inf = __int_as_float(0x7f800000);
-                float* pl = a.subc + (size_t)(3 * (a.subc_slot0 + chunk)) * a.subc_plane + (size_t)y * W + x0 + lane;
+                const size_t px = (size_t)y * W + x0 + lane;
+                float* pl = a.subc + (size_t)(3 * (a.subc_slot0 + chunk)) * a.subc_plane + px;
                 if (ST_CHECK(x0 + lane < W && y < H && a.subc_slot0 + chunk < 2 && (long)W * H <= a.subc_plane, 10)) {
                     pl[0] = wc >= 1 ? cp[-1] : inf;
                     pl[a.subc_plane] = cp[0];
-                    pl[2 * a.subc_plane] = wc + 1 < 32 * K ? cp[1] : inf;
+                    if (wc + 1 < 32 * K) pl[2 * a.subc_plane] = cp[1];
+                    else if (a.subc_mode != 1) pl[2 * a.subc_plane] = inf;   // mode 1: the second chunk's first cost is there
+                    if (a.subc_mode == 1) a.subc_edge[px] = sCv[lane * S8::CVS + 32 * K - 1];
+                    if (a.subc_mode == 2) a.subc[2 * a.subc_plane + px] = sCv[lane * S8::CVS];
                 }
             }
             const int u = x0 + lane - dc0 - 32 * K + 1;

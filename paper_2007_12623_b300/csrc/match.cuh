@@ -192,6 +192,7 @@ struct FinArgs {
     const float* subc;
     long subc_plane;
     int subc_split;
+    const float* subc_edge;   // split range: the first chunk's last cost (slot 1's missing c0), or nullptr
 };
 
 // Row vb.y, columns 128 vb.x .. 128 vb.x + 127 (128 threads).
@@ -231,6 +232,7 @@ __device__ __forceinline__ void finalize_run(const FinArgs& f, VBlock vb) {
         c[0] = __ldg(pl);
         c[1] = __ldg(pl + f.subc_plane);
         c[2] = __ldg(pl + 2 * f.subc_plane);
+        if (slot == 1 && f.subc_edge && isinf(c[0])) c[0] = __ldg(f.subc_edge + i);
         have = !isinf(c[0]) && !isinf(c[2]);
     } else if (fit && cdt == CDT_F32) {
         const size_t b = i * (size_t)cost_stride(D) + (dl - d_min);
@@ -287,11 +289,13 @@ static void launch_finalize(const uint32_t* keyL, const uint32_t* keyR, int W, i
                             int lr_thresh, const void* cost, int cdt, const uint8_t* L, const uint8_t* Rm,
                             int r, int sampling, const FinStats& fs, int16_t* disp_left, int16_t* disp_right,
                             float* disp_sub, int16_t* disp_lr, cudaStream_t s, bool sub_done = false,
-                            const float* subc = nullptr, long subc_plane = 0, int subc_split = 0) {
+                            const float* subc = nullptr, long subc_plane = 0, int subc_split = 0,
+                            const float* subc_edge = nullptr) {
     const dim3 g((W + 127) / 128, H);
     const int rr = fs.lstats ? r : 0;
     const FinArgs f{keyL, keyR, W, H, d_min, D, lr_thresh, cost, cdt, L, Rm, r, sampling, fs,
-                    disp_left, disp_right, disp_sub, disp_lr, sub_done ? 1 : 0, subc, subc_plane, subc_split};
+                    disp_left, disp_right, disp_sub, disp_lr, sub_done ? 1 : 0, subc, subc_plane, subc_split,
+                    subc_edge};
 #define FIN_CASE(RV, CBV) \
     case RV: k_finalize<RV, CBV><<<g, 128, 0, s>>>(f); break;
     if (sampling == 1) {

@@ -459,29 +459,45 @@ void run_match(const uint8_t* gl, const uint8_t* gr, int W, int H, int d_min, in
         a.subc = w.dprev;
         a.subc_plane = w.rplane;
     }
+    bool split_edge = false;
     if (i8 && K == 2 && D > 128) {
         // 128-disparity chunks at K = 4 for the bulk of the range and 64-disparity
-        // chunks at K = 2 for the rest (e.g. D = 192: 128 + 64 with no idle lane)
+        // chunks at K = 2 for the rest (e.g. D = 192: 128 + 64 with no idle lane);
+        // with per-chunk winner costs the second part runs first, so that the
+        // first chunk's kernel finds the second chunk's first cost in place
+        // for a winner on its last candidate (and leaves its own last cost in
+        // dfin, free until the refinement, for a winner on the second chunk's
+        // first candidate)
         CostArgs a4 = a;
         a4.dcount = D / 128 * 128;
-        launch_cost(r, 4, cdt, a4, g_cost_rows, s, sampling);
         a.dbase = a4.dcount;
         a.dcount = D - a4.dcount;
         a.subc_slot0 = a4.dcount / 128;
+        if (chunked_sub && a4.dcount == 128) {
+            split_edge = true;
+            a.subc_mode = 2;
+            a4.subc_mode = 1;
+            a4.subc_edge = w.dfin;
+            launch_cost(r, K, cdt, a, g_cost_rows, s, sampling);
+            launch_cost(r, 4, cdt, a4, g_cost_rows, s, sampling);
+        } else {
+            launch_cost(r, 4, cdt, a4, g_cost_rows, s, sampling);
+        }
     }
     // the whole range in one chunk of the integer form and no FP32 volume:
     // the cost kernel fits the parabola itself (the finalize kernel would
     // recompute the winner's three costs)
     const bool sub_in_cost = i8 && cdt != CDT_F32 && a.dbase == 0 && D <= 32 * K && disp_sub;
     if (sub_in_cost) a.sub = disp_sub;
-    launch_cost(r, K, cdt, a, g_cost_rows, s, sampling);
+    if (!split_edge) launch_cost(r, K, cdt, a, g_cost_rows, s, sampling);
     if (ev) cudaEventRecord(ev[3], s);
     launch_finalize(w.keys, w.keys + (size_t)W * H, W, H, d_min, D, lr_thresh, cost, cdt, gl, gr, r, sampling,
                     FinStats{w.lstats, w.ustats, pr.ustride, pr.ucol0,
                              i8 ? reinterpret_cast<const int8_t*>(pl.img) : nullptr, pl.stride, pl.col0,
                              i8 ? reinterpret_cast<const int8_t*>(pr.img) : nullptr, pr.stride, pr.col0},
                     disp_left, disp_right, disp_sub, disp_lr,
-                    s, sub_in_cost, chunked_sub ? w.dprev : nullptr, w.rplane, 128);
+                    s, sub_in_cost, chunked_sub ? w.dprev : nullptr, w.rplane, 128,
+                    split_edge ? w.dfin : nullptr);
     counted();
 }
 
