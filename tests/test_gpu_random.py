@@ -11,6 +11,9 @@ other tests.
     checked build (in-kernel index checks): no failed check, and the normal
     build's outputs bit for bit.  The checked build runs first, so a failed
     check is reported before the normal build makes the access.
+  * test_random_subpixel_across_cost_types: the cost/WTA stage for the four
+    cost formats (three ways of fitting the sub-pixel parabola), winners and
+    sub-pixel disparities bit-identical, checked and normal builds.
 """
 import numpy as np
 import pytest
@@ -121,3 +124,53 @@ def test_random_checked(dev, case):
     assert err0 == 0
     for k in ref:
         assert np.array_equal(np.nan_to_num(ref[k], nan=-7), np.nan_to_num(got[k], nan=-7)), k
+
+
+def _stage_match(dev, L, R, d_min, D, r, cdt):
+    H, W = L.shape
+    p = st.stereo_default_params(max_width=W, max_height=H, num_disp=D, d_min=d_min, win_radius=r,
+                                 cost_dtype=cdt)
+    h = st.stereo_create(p)
+    dl = torch.empty((H, W), dtype=torch.int16, device=dev)
+    dr = torch.empty_like(dl)
+    sub = torch.empty((H, W), dtype=torch.float32, device=dev)
+    cost = None
+    if cdt != st.COST_NONE:
+        tdt = {st.COST_F32: torch.float32, st.COST_F16: torch.float16, st.COST_BF16: torch.bfloat16}[cdt]
+        cost = torch.zeros((H, W, st.cost_stride(D)), dtype=tdt, device=dev)
+    st.stereo_stage_match(h, T(L, dev), T(R, dev), d_min, D, r, st.SAMPLE_FULL, cdt, dl, dr, sub, cost)
+    torch.cuda.synchronize()
+    err = st.stereo_get_device_error(h)
+    h.close()
+    return err, dl.cpu().numpy(), dr.cpu().numpy(), sub.cpu().numpy()
+
+
+@pytest.mark.parametrize("case", range(16))
+def test_random_subpixel_across_cost_types(dev, case):
+    """Random sizes, windows and ranges up to 256 disparities (one chunk, a
+    split range, two chunks), first disparities down to -130 so that winners
+    fall on both sides of the chunk edge: the sub-pixel parabola fitted by
+    the finalize kernel from an FP32 volume, by the cost kernel itself (one
+    chunk), or from the per-chunk winner costs (several chunks) gives the
+    same winners and bit-identical sub-pixel disparities for the four cost
+    types, in the checked build (no failed index check) and the normal one."""
+    rng = np.random.default_rng(synth.seed_for(12, case))
+    W, H = int(rng.integers(20, 400)), int(rng.integers(16, 160))
+    r, D, d_min = int(rng.integers(1, 8)), int(rng.integers(1, 257)), int(rng.integers(-130, 40))
+    L, R = _images(rng, W, H, d_min, D)
+    ref = None
+    for checked in (True, False):
+        for cdt in (st.COST_F32, st.COST_F16, st.COST_BF16, st.COST_NONE):
+            if checked:
+                with st.checked_library():
+                    err, dl, dr, sub = _stage_match(dev, L, R, d_min, D, r, cdt)
+            else:
+                err, dl, dr, sub = _stage_match(dev, L, R, d_min, D, r, cdt)
+            assert err == 0, (hex(err), cdt, checked)
+            if ref is None:
+                ref = (dl, dr, sub)
+                continue
+            assert np.array_equal(dl, ref[0]) and np.array_equal(dr, ref[1]), (cdt, checked)
+            assert np.array_equal(np.isnan(sub), np.isnan(ref[2])), (cdt, checked)
+            ok = ~np.isnan(ref[2])
+            assert np.array_equal(sub[ok].view(np.uint32), ref[2][ok].view(np.uint32)), (cdt, checked)
