@@ -102,20 +102,31 @@ __device__ __forceinline__ void prep_tile(const PrepArgs& pa, VBlock vb) {
     const PrepOut out = left ? pa.out0 : pa.out1;
     const int x0 = vb.x * PT, y0 = vb.y * PT;
     const int tid = threadIdx.x;
-    for (int i = tid; i < SPAN * SPAN; i += 256) {
-        const int ly = i / SPAN, lx = i % SPAN;
-        const int gx = x0 - R + lx, gy = y0 - R + ly;
-        uint32_t v = 0;
-        if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-            const uint8_t* p = in.img + (size_t)gy * in.pitch;
-            if (in.rgb) {
-                p += 3 * gx;
-                v = (77u * p[0] + 150u * p[1] + 29u * p[2] + 128u) >> 8;
-            } else {
-                v = p[gx];
+    {
+        // thread = (column lx, first row ly0), rows ly0, ly0 + RS, ...: the
+        // column, its bounds and the row pointer are set up once
+        constexpr int RS = 256 / SPAN;                 // rows per pass
+        constexpr int NP = (SPAN + RS - 1) / RS;       // passes
+        const int lx = tid % SPAN, ly0 = tid / SPAN;
+        const int gx = x0 - R + lx;
+        const bool col_in = ly0 < RS && gx >= 0 && gx < W;
+        const size_t step = (size_t)RS * in.pitch;
+        const uint8_t* p = in.img + (size_t)(y0 - R + ly0) * in.pitch + (in.rgb ? 3 * gx : gx);
+        uint32_t v[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const int ly = ly0 + k * RS, gy = y0 - R + ly;
+            v[k] = 0u;
+            if (col_in && ly < SPAN && gy >= 0 && gy < H) {
+                const uint8_t* q = p + k * step;
+                v[k] = in.rgb ? (77u * q[0] + 150u * q[1] + 29u * q[2] + 128u) >> 8 : (uint32_t)q[0];
             }
         }
-        t[ly][lx] = (uint16_t)v;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const int ly = ly0 + k * RS;
+            if (ly0 < RS && ly < SPAN) t[ly][lx] = (uint16_t)v[k];
+        }
     }
     __syncthreads();
     const uint32_t N = (uint32_t)(CB ? ((2 * R + 1) * (2 * R + 1) + 1) / 2 : (2 * R + 1) * (2 * R + 1));
