@@ -116,6 +116,8 @@ METRIC = "Gpix*disp/s and ms per 960x540 pair (1 B300), % of roofline, vs oracle
 DATA = "synthetic (seeded tissue-texture generator standing in for the paper's videos)"
 UNIT = "Gpix*disp/s"
 L2_BYTES = 126 * 2 ** 20
+L2_NOTE = ("flushed between timed steps on the step's stream (252 MiB write, then a 126 MiB read "
+           "that leaves no dirty line of the flush; untimed)")
 PAPER_CONTEXT = {"ms_per_keyframe_whole_pipeline": 76.3, "stereo_stage_ms": 15.9,
                  "zncc_ms_960x540x100": 5.0,
                  "hardware": "NVIDIA Titan X + Xeon X5472 (paper, Table III)"}
@@ -320,13 +322,25 @@ def soft_roofline(stage_ms, W, H, D, peaks, sm_count, traffic=None):
 
 # ------------------------------------------------------------- helpers
 
+def _flush_l2(stream, flush, i):
+    """Evicts the previous step's data from L2 before the next timed step, on
+    the step's own stream (a flush on another stream would run alongside the
+    step): a write of a buffer twice the size of L2, then a read of its first
+    half, which was evicted first, so that the write's dirty lines are written
+    back here and not during the step's first kernels."""
+    import torch
+    with torch.cuda.stream(stream):
+        flush.fill_(float(i))
+        flush[: flush.numel() // 2].sum()
+
+
 def _timed_loop(torch, stream, steps, step, flush):
     """Times `steps` calls of step() on `stream` with CUDA events, flushing L2
     (untimed) before each; returns per-step ms."""
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
     for i in range(steps):
-        flush.fill_(float(i))
+        _flush_l2(stream, flush, i)
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
@@ -342,11 +356,11 @@ def _max_over_ranks(torch, dev, x, world):
     return float(t.item())
 
 
-def _stage_pass(st, h, n, flush, step, names):
+def _stage_pass(st, h, n, flush, step, names, stream):
     st.stereo_set_stage_timing(h, True)
     acc = {k: 0.0 for k in names}
     for i in range(n):
-        flush.fill_(float(i))
+        _flush_l2(stream, flush, i)
         step()
         ms = st.stereo_get_stage_times(h)
         for k, v in zip(names, ms.values()):
@@ -373,7 +387,7 @@ def single_config(name, wl, world):
         "window": 2 * wl["r"] + 1, "sampling": "chessboard" if wl.get("sampling", 0) else "full",
         "cost_storage": wl["cost"], "smooth_radius": wl["smooth_radius"], "refine_iters": 5,
         "pairs_per_gpu": 1, "parallelism": f"replicas x{world} (independent pairs)",
-        "l2": "flushed between timed steps (256 MB write, untimed)",
+        "l2": L2_NOTE,
         "launch": "CUDA graph replay on a non-default stream"}
 
 
@@ -416,7 +430,7 @@ def run_single(args, wl, rank, world, dev, extras=True):
     P = W * H * D
     value = world * args.steps * P / t_max / 1e9
 
-    stage_ms = _stage_pass(st, h, min(args.steps, 20), flush, step, st.STAGE_NAMES)
+    stage_ms = _stage_pass(st, h, min(args.steps, 20), flush, step, st.STAGE_NAMES, stream)
     if extras:
         depth_ms, mosaic_ms, model_points, vote_ms = _single_extras(st, torch, dev, stream, h, W, H, Lrgb,
                                                                      outs, args, flush)
@@ -639,7 +653,7 @@ def run_batched(args, wl, rank, world, dev, pairs):
     t_max = _max_over_ranks(torch, dev, sum(step_ms) / 1e3, world)
     P = sum(s["W"] * s["H"] * s["D"] for s in specs)
     value = world * args.steps * P / t_max / 1e9
-    stage_ms = _stage_pass(st, h, min(args.steps, 5), flush, step, st.STAGE_NAMES)
+    stage_ms = _stage_pass(st, h, min(args.steps, 5), flush, step, st.STAGE_NAMES, stream)
 
     # end to end, as a stream of batches: the next batch's images go up from
     # pinned host memory (copy stream) into a staging set while the current
@@ -722,7 +736,7 @@ def run_batched(args, wl, rank, world, dev, pairs):
         "num_disp": sorted({s["D"] for s in specs}), "windows": sorted({2 * s["r"] + 1 for s in specs}),
         "cost_storage": wl["cost"], "smooth_radius": wl["smooth_radius"], "refine_iters": 5,
         "pix_disp_per_step": P, "parallelism": f"replicas x{world} (independent batches)",
-        "l2": "flushed between timed steps (256 MB write, untimed); working set >> L2",
+        "l2": L2_NOTE + "; working set >> L2",
         "launch": "one stereo_match_batched per step, CUDA graph replay, persistent cost launch",
         "autotuned": tune})
     line.update({
@@ -804,10 +818,10 @@ def run_soft_step(args, wl, rank, world, dev):
     gl, gr = torch.empty_like(ds), torch.empty_like(ds)
     bwd_ms = _stage_pass(st, h, min(args.steps, 5), flush,
                          lambda: st.stereo_softargmin_bwd(h, tL.detach(), tR.detach(), 0, D, r, tau, ds, lse,
-                                                          g, gl, gr), names)
+                                                          g, gl, gr), names, stream)
     fwd_ms = _stage_pass(st, h, min(args.steps, 5), flush,
                          lambda: st.stereo_softargmin_fwd(h, tL.detach(), tR.detach(), 0, D, r, tau, ds, lse),
-                         ("stats", "cost", "soft_fwd", "_a", "_b", "_c"))
+                         ("stats", "cost", "soft_fwd", "_a", "_b", "_c"), stream)
 
     # end to end, as a stream of training batches: the next batch's images
     # and ground truth go up from pinned host memory (copy stream) into the
@@ -861,7 +875,7 @@ def run_soft_step(args, wl, rank, world, dev):
         "window": 2 * r + 1, "tau": tau, "loss": "L1(d_soft, ground truth), mean over valid pixels",
         "step": "forward + loss + backward to both images (torch.autograd)",
         "parallelism": f"replicas x{world} (independent batches)",
-        "l2": "flushed between timed steps (256 MB write, untimed); volumes >> L2"})
+        "l2": L2_NOTE + "; volumes >> L2"})
     line.update({
         "ms_per_pair": round(t_max * 1e3 / args.steps / B, 4),
         "stage_ms_last_pair": {"forward": {k: round(fwd_ms[k], 4) for k in ("stats", "cost", "soft_fwd")},
